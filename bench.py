@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of the COLATUS hot path on B300: one KDK step of the 32^3 run.
+
+A timed "step" is one pass of the whole path on the 32^3 workload (perturbed
+grid, growing-mode velocities, eps = 0.02 spacing): the FP64 Friedmann
+schedule, the FP32 all-pairs force with compensated accumulation, the fused
+kick-drift epilogue with Hubble drag, and the 64-tracer record.
+
+Prints ONE JSON line (rank 0).  ``value`` is pair interactions per second
+(N^2 per step) over all ranks; ``roofline`` reports the force kernel against
+the FP32-FMA/MUFU issue roofline (20 flops per interaction by convention;
+256 FP32 flop/clk/SM); ``force_128cubed`` times the force alone at
+N = 2^21 = 128^3; ``cpu_baseline`` times the FP64 oracle on a bounded sample
+on this host's cores.  ``--impl reference`` times only the oracle.
+
+Multi-GPU (torchrun): every rank runs an independent replica of the same
+workload (weak scaling); the barrier and the max-over-ranks time are the
+only communication.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pairwise interactions/sec & % FP32/MUFU roofline at N=32³,128³; adjoint/fwd time"
+UNIT = "interactions/s"
+LCDM = dict(Omega_R=0.0, Omega_M=0.3, Omega_K=0.0, Omega_L=0.7, H0=1.0)
+FLOPS_PER_INTERACTION = 20          # Nyland et al. convention
+FP32_FLOP_PER_CLK_PER_SM = 256      # 128 FP32 lanes x FMA
+L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of one launch of the 32^3 compensated force kernel,
+# force_f32_kernel<256, 4, 512, 4, 32, 1, 1, 2>, from one ncu capture
+# (profiles/force_f32_comp_grid32.md); set to None when that kernel changes.
+FORCE_KERNEL_TRAFFIC = 541184
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="colatus", choices=["colatus", "reference"])
+    p.add_argument("--no-128", action="store_true", help="skip the N = 128^3 force timing")
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for ln in self.lines:
+            f = [s.strip() for s in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), power=float(f[3]),
+                                 hw=f[5], hwt=f[6], swt=f[7], swp=f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        load = [r for r in rows if r["power"] > 200.0] or rows
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median([r["sm"] for r in load])),
+                "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------ CPU baseline
+def cpu_baseline(seconds, rows_per_call=2048):
+    """The FP64 oracle (as it stands) on a bounded row sample of the 32^3
+    workload: forces on random target rows against all 32^3 sources, repeated
+    until about `seconds` of CPU time have been spent."""
+    import oracle
+    from paper_1208_3444_b300 import inputs
+    ic = inputs.grid32()
+    rng = np.random.default_rng(0)
+    oracle.forces(ic.x, ic.m, ic.eps, rows=np.arange(64))        # start the thread pool
+    done, calls = 0, 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        oracle.forces(ic.x, ic.m, ic.eps,
+                      rows=np.sort(rng.choice(ic.N, rows_per_call, replace=False)))
+        done += rows_per_call
+        calls += 1
+    dt = time.perf_counter() - t0
+    return {"value": done * ic.N / dt, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle forces on {done} random target rows ({calls} calls of "
+                      f"{rows_per_call}) x all {ic.N} sources of the 32^3 workload ({dt:.1f} s)"}
+
+
+# --------------------------------------------------------------- distributed
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    import oracle
+    from paper_1208_3444_b300 import inputs
+    ic = inputs.grid32()
+    rows_per_step = 128
+    rng = np.random.default_rng(1)
+    for _ in range(args.warmup):
+        oracle.forces(ic.x, ic.m, ic.eps, rows=rng.choice(ic.N, rows_per_step, replace=False))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.forces(ic.x, ic.m, ic.eps, rows=rng.choice(ic.N, rows_per_step, replace=False))
+    dt = time.perf_counter() - t0
+    value = args.steps * rows_per_step * ic.N / dt
+    sample = (f"each step: FP64 oracle forces on {rows_per_step} random target bodies x all "
+              f"{ic.N} sources of the 32^3 workload")
+    return {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "grid32 (N=32^3 perturbed grid), force rows sampled",
+                       "N": ic.N},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def time_force_128(B, inputs, torch, launches=3):
+    """FP32 force alone at N = 2^21 (uniform bodies), events around each launch."""
+    ic = inputs.uniform(1 << 21, 11)
+    st = torch.cuda.current_stream().cuda_stream
+    assert st, "use a created stream, not the legacy default stream"
+    sim = B.Simulation(ic.m, ic.eps, LCDM, 1.0, prec=B.FP32, stream=st)
+    out = torch.empty((ic.N, 3), dtype=torch.float32, device="cuda")
+    try:
+        sim.set_state(ic.x)
+        sim.forces(out)
+        sim.synchronize()
+        sim.profile_forces(True)
+        for _ in range(launches):
+            sim.forces(out)
+        ms, n = sim.profile_read()
+        sim.profile_forces(False)
+    finally:
+        sim.close()
+    return {"N": ic.N, "launches": n, "ms_per_launch": ms / n,
+            "interactions_per_s": ic.N * ic.N * n / (ms * 1e-3), "prec": "fp32"}
+
+
+def run_colatus(args, ws, rank, local):
+    import torch
+    from paper_1208_3444_b300 import binding as B
+    from paper_1208_3444_b300 import inputs
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)      # the library and the events share it
+    torch.cuda.set_stream(stream)
+    props = torch.cuda.get_device_properties(dev)
+    nsm = props.multi_processor_count
+
+    ic = inputs.grid32()
+    N = ic.N
+    tau = inputs.lcdm_tau(2000)
+    tr = inputs.tracers(N, 64, 7)
+    K, W = args.steps, args.warmup
+    sim = B.Simulation(ic.m, ic.eps, LCDM, inputs.A_START, prec=B.FP32_COMP, scheme=B.KDK,
+                       stream=stream.cuda_stream)
+    sim.set_state(ic.x, ic.v)
+    sim.record_tracers(tr, K + W + 8)
+    sim.step(tau, W)
+    sim.synchronize()
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    launches0 = sim.stats()["launches"]
+    sim.profile_forces(True)
+    clocks = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(K):
+        flush.zero_()                       # L2 flush between timed steps (not timed)
+        ev0[k].record(stream)
+        sim.step(tau, 1)
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier(ws)
+    clk = clocks.stop()
+    step_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    force_ms, nforce = sim.profile_read()
+    sim.profile_forces(False)
+    launches = sim.stats()["launches"] - launches0
+    sim.synchronize()
+
+    step_ms_max = max_over_ranks(ws, step_ms)
+    value = ws * K * float(N) * N / (step_ms_max * 1e-3)
+
+    # end to end through the C ABI with host buffers: the initial state from
+    # pinned host memory, then per step the paper's host loop (Appendix A,
+    # step 8): advance, then copy every position and velocity to the host.
+    Ke = min(K, 50)
+    xh = torch.tensor(ic.x, dtype=torch.float32).pin_memory()
+    vh = torch.tensor(ic.v, dtype=torch.float32).pin_memory()
+    xo = torch.empty((N, 3), dtype=torch.float32).pin_memory()
+    vo = torch.empty((N, 3), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.set_state(xh, vh)
+    for _ in range(Ke):
+        sim.step(tau, 1)
+        B.colatus_get_state(sim.h, xo, vo)
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(ws, e2e_s)
+    e2e = {"value": ws * Ke * float(N) * N / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(2 * N * 3 * 4 / Ke), "d2h_bytes_per_step": 2 * N * 3 * 4,
+           "steps": Ke,
+           "what": "per step: colatus_step + colatus_get_state of x and v into pinned host "
+                   "memory; the initial colatus_set_state from pinned host memory is inside "
+                   "the timed region and amortised over the steps"}
+    sim.close()
+
+    result = None
+    force128 = None
+    if not args.no_128:
+        force128 = time_force_128(B, inputs, torch)
+    if rank == 0:
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except (OSError, ValueError):
+            pass
+        f_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+        fmax = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2032.0)
+        achieved_int = float(N) * N * nforce / (force_ms * 1e-3)
+        achieved = achieved_int * FLOPS_PER_INTERACTION / 1e12
+        peak = nsm * FP32_FLOP_PER_CLK_PER_SM * f_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": FORCE_KERNEL_TRAFFIC,
+                "traffic_note": "dram bytes per launch from ncu (profiles/force_f32_comp_grid32.md); "
+                                "algorithmic HBM bytes: 524288 (positions read once)",
+                "kernel": "force_f32_kernel (FP32 compensated, stream-K)",
+                "interactions_per_s": achieved_int,
+                "int_per_sm_per_clk": achieved_int / (nsm * f_mhz * 1e6),
+                "peak_basis": f"{nsm} SMs x {FP32_FLOP_PER_CLK_PER_SM} FP32 flop/clk x "
+                              f"{f_mhz:.0f} MHz (median sampled SM clock); 20 flop/interaction",
+                "frac_at_max_clock": achieved / (nsm * FP32_FLOP_PER_CLK_PER_SM * fmax * 1e6 / 1e12),
+                "ms_per_launch": force_ms / nforce}
+        if force128:
+            a128 = force128["interactions_per_s"]
+            force128["frac"] = a128 * FLOPS_PER_INTERACTION / 1e12 / peak
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+            "warmup": W, "ms_per_step": step_ms_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "grid32: N=32^3 perturbed grid, growing-mode velocities, "
+                                   "eps=0.02 spacing, one KDK step (FP32 compensated force, FP64 "
+                                   "a(t), Hubble drag, 64 tracers)",
+                       "N": N, "prec": "fp32_comp", "scheme": "kdk", "tau": tau,
+                       "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "steps_per_s": K / (step_ms_max * 1e-3),
+            "wall_s_timed_region": wall,
+            "roofline": roof,
+            "force_128cubed": force128,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        if not args.no_cpu:
+            result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    return result
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        # the oracle runs on rank 0's host cores only; other ranks exit without work
+        ws = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        res = run_reference(args, ws, rank)
+        if rank == 0 and res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    ws, rank, local = dist_setup()
+    res = run_colatus(args, ws, rank, local)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * colatus.h -- C ABI of the B300 (sm_103a) library for the hot path of
+ * COLATUS (Stalder et al., "A new gravitational N-body simulation algorithm
+ * for investigation of cosmological chaotic advection", arXiv 1208.3444).
+ *
+ * What the library computes
+ *   The softened all-pairs gravitational acceleration in comoving coordinates
+ *   (Eq. 1), oriented attractively,
+ *       acc_k = a^-3 G sum_{j != k} m_j (x_j - x_k) / (|x_j - x_k|^2 + eps^2)^{3/2},
+ *   with isolated boundaries, integrated by the Hubble-drag leapfrog of
+ *   Eqs. 3-5 (drift-kick-drift, "DKD") or its kick-drift-kick form ("KDK"),
+ *   with the scale factor a(t) driven by the Friedmann equation (Eq. 2),
+ *       da/dt = a H(a),  H = H0 sqrt(Omega_R a^-4 + Omega_M a^-3 + Omega_K a^-2 + Omega_L).
+ *   The paper's Appendix A kernel (one GPU thread per body, forces then
+ *   integration) is the operation; its design is not reused.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns a colatus_status and never aborts the process.
+ *     colatus_last_error() describes the most recent failure of a context.
+ *   - Array arguments are plain pointers.  `on_device` = 0 means a host
+ *     pointer, 1 means a device pointer on the context's device.  `dtype`
+ *     selects float (COLATUS_F32) or double (COLATUS_F64) elements.
+ *   - Vector arrays are N x 3, row-major (x0 y0 z0 x1 ...).
+ *   - The caller owns every pointer it passes; the library copies what it
+ *     needs before returning (or, for asynchronous device-to-device calls,
+ *     before the work it enqueued on the context's stream completes).
+ *   - A context is bound to one device and one CUDA stream.  Calls on one
+ *     context are not thread-safe.  All GPU work is enqueued on the context's
+ *     stream; functions that return host data synchronise that stream.
+ *   - Time t is absolute code time with t = 0 at a_start; G defaults to 1.
+ */
+#ifndef COLATUS_H
+#define COLATUS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque context, owned by the library (create with colatus_init). */
+typedef struct colatus_ctx *colatus_t;
+
+typedef enum {
+    COLATUS_OK = 0,
+    COLATUS_E_ARG = 1,        /* invalid argument (sizes, pointers, eps <= 0, ...)   */
+    COLATUS_E_CUDA = 2,       /* a CUDA runtime call failed                           */
+    COLATUS_E_NONFINITE = 3,  /* a position or velocity became NaN or Inf             */
+    COLATUS_E_FRIEDMANN = 4,  /* H^2 < 0 in Eq. 2 (e.g. recollapse), or a <= 0        */
+    COLATUS_E_STATE = 5,      /* call out of order (e.g. step before set_state)       */
+    COLATUS_E_OOM = 6,        /* device allocation failed                             */
+    COLATUS_E_TIMEOUT = 7     /* a bounded device-side wait gave up (no hang)         */
+} colatus_status;
+
+typedef enum {
+    COLATUS_FP32 = 0,       /* FP32 pair arithmetic, blocked FP32 accumulation         */
+    COLATUS_FP32_COMP = 1,  /* FP32 pair arithmetic with a refined rsqrt and two-float
+                               (TwoSum) accumulation of the j-sum                      */
+    COLATUS_FP64 = 2        /* FP64 everywhere (state, pair arithmetic, sums)          */
+} colatus_prec;
+
+typedef enum {
+    COLATUS_DKD = 0,  /* Eqs. 3-5: half drift, kick at t^{n+1/2}, half drift             */
+    COLATUS_KDK = 1   /* half kick at t^n, drift, half kick at t^{n+1} (span tau/2 each) */
+} colatus_scheme;
+
+typedef enum { COLATUS_F32 = 0, COLATUS_F64 = 1 } colatus_dtype;
+
+/* Number of doubles written by colatus_diagnostics. */
+#define COLATUS_NDIAG 16
+
+/* Create a context for N bodies on the current CUDA device.
+ *   masses:  host array of N doubles (copied; may be changed later with
+ *            colatus_set_masses).
+ *   eps:     Plummer softening of Eq. 1 (the kernel's min_dist); must be > 0.
+ *   Omega_*, H0: Eq. 2 parameters; a_start > 0 is the scale factor at t = 0.
+ * Defaults: COLATUS_FP32, COLATUS_KDK, G = 1, a library-owned stream.
+ * Errors: COLATUS_E_ARG (N < 1, eps <= 0 or not finite, a_start <= 0, NULL
+ * pointers, H^2(a_start) < 0), COLATUS_E_OOM, COLATUS_E_CUDA.  On error *out
+ * is set to NULL and nothing is leaked. */
+colatus_status colatus_init(colatus_t *out, int64_t N, const double *masses, double eps,
+                            double Omega_R, double Omega_M, double Omega_K, double Omega_L,
+                            double H0, double a_start);
+
+/* Precision, integrator, gravitational constant and stream (a cudaStream_t;
+ * NULL keeps the library-owned stream).  Changing precision keeps the state
+ * (converted).  Errors: COLATUS_E_ARG. */
+colatus_status colatus_set_config(colatus_t ctx, colatus_prec prec, colatus_scheme scheme,
+                                  double G, void *cuda_stream);
+
+/* Replace the N masses (dtype elements, host or device). */
+colatus_status colatus_set_masses(colatus_t ctx, const void *m, int dtype, int on_device);
+
+/* Set positions x and velocities v (N x 3 each, dtype elements, host or
+ * device) at the current (t, a).  v may be NULL for bodies at rest.  The
+ * FP32 modes store float state: double input is rounded to float.
+ * Errors: COLATUS_E_ARG, COLATUS_E_NONFINITE (a non-finite input value). */
+colatus_status colatus_set_state(colatus_t ctx, const void *x, const void *v, int dtype,
+                                 int on_device);
+
+/* Read positions and velocities (N x 3, dtype) and the current t and a
+ * (either may be NULL).  Synchronises the stream and reports any device
+ * error flag raised since the last check (COLATUS_E_NONFINITE,
+ * COLATUS_E_FRIEDMANN, COLATUS_E_TIMEOUT). */
+colatus_status colatus_get_state(colatus_t ctx, void *x, void *v, int dtype, int on_device,
+                                 double *t, double *a);
+
+/* Comoving acceleration of Eq. 1 at the current state and scale factor:
+ * acc_out (N x 3, dtype) = a^-3 G sum_{j != k} m_j (x_j - x_k) / s^3.
+ * Device output is asynchronous on the context's stream; host output
+ * synchronises.  Errors: COLATUS_E_STATE (no state set), COLATUS_E_TIMEOUT. */
+colatus_status colatus_forces(colatus_t ctx, void *acc_out, int dtype, int on_device);
+
+/* Advance nsteps steps of size dt (> 0) with the configured scheme.  The
+ * scale factor is advanced on the GPU in FP64 (RK4, 8 sub-steps per half
+ * step).  Asynchronous: device error flags are reported by the next
+ * colatus_synchronize / colatus_get_state.  Errors: COLATUS_E_ARG,
+ * COLATUS_E_STATE. */
+colatus_status colatus_step(colatus_t ctx, double dt, int64_t nsteps);
+
+/* Wait for all enqueued work and report device error flags. */
+colatus_status colatus_synchronize(colatus_t ctx);
+
+/* Record (x, v) of ntr bodies idx[0..ntr) (host int64 indices, distinct,
+ * in [0, N)) after every subsequent step, into a device ring buffer of
+ * capacity_steps records (the oldest are overwritten).  ntr = 0 stops
+ * recording.  Replaces any earlier recording. */
+colatus_status colatus_record_tracers(colatus_t ctx, const int64_t *idx, int ntr,
+                                      int64_t capacity_steps);
+
+/* Copy the recorded tracers, oldest first, to host memory xv_out laid out
+ * [nrec][ntr][6] floats (x, y, z, vx, vy, vz); *nrec_out = records copied
+ * (<= capacity).  xv_out may be NULL to query *nrec_out.  Synchronises. */
+colatus_status colatus_read_tracers(colatus_t ctx, float *xv_out, int64_t *nrec_out);
+
+/* FP64 diagnostics at the current state (synchronises):
+ *   out[0] K = (1/2) sum m a^2 |v|^2      out[1] W = W_x / a
+ *   out[2..4] P = sum m a^2 v             out[5..7] L = sum m a^2 x cross v
+ *   out[8..10] centre of mass             out[11] a   out[12] t   out[13] H(a)
+ *   out[14] W_x = -(G/2) sum_{j != k} m_k m_j / s_kj   out[15] step count
+ * (K + W obeys the Layzer-Irvine equation d(K+W)/dt = -H (2K + W)). */
+colatus_status colatus_diagnostics(colatus_t ctx, double out[COLATUS_NDIAG]);
+
+/* Human-readable description of the last error on ctx ("" if none);
+ * colatus_last_error(NULL) describes the last colatus_init failure. */
+const char *colatus_last_error(colatus_t ctx);
+
+/* Counters of a context: out[0] kernel launches enqueued, out[1] pair
+ * interactions enqueued (N^2 per force evaluation), out[2] steps taken,
+ * out[3] N. */
+colatus_status colatus_stats(colatus_t ctx, double out[4]);
+
+/* Kernel timing for measurement: with on != 0 every launch of the force
+ * kernel is bracketed by a pair of CUDA events recorded on the context's
+ * stream (on = 0 stops and discards them). */
+colatus_status colatus_profile_forces(colatus_t ctx, int on);
+
+/* Total duration in milliseconds (out[0]) and number (out[1]) of the
+ * force-kernel launches timed since the last read; synchronises the stream
+ * and resets the totals. */
+colatus_status colatus_profile_read(colatus_t ctx, double out[2]);
+
+/* Release every device and host resource of ctx (NULL is a no-op). */
+void colatus_destroy(colatus_t ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COLATUS_H */

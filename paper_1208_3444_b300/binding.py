@@ -1,0 +1,299 @@
+"""Thin Python binding of ``include/colatus.h`` (ctypes over libcolatus.so).
+
+Functions keep the C names and argument order; they only marshal arguments
+(NumPy arrays or PyTorch tensors, host or CUDA) into pointers and turn a
+non-OK status into ``ColatusError``.  Every step of the computation runs in the
+library's CUDA kernels: there is no CPU fallback, and importing the library
+fails loudly when ``libcolatus.so`` has not been built.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+# COLATUS_LIBRARY may point at another build of the same library
+LIB_PATH = os.environ.get("COLATUS_LIBRARY") or os.path.join(HERE, "libcolatus.so")
+
+# enums of colatus.h
+OK, E_ARG, E_CUDA, E_NONFINITE, E_FRIEDMANN, E_STATE, E_OOM, E_TIMEOUT = range(8)
+FP32, FP32_COMP, FP64 = 0, 1, 2
+DKD, KDK = 0, 1
+F32, F64 = 0, 1
+NDIAG = 16
+STATUS_NAMES = {0: "COLATUS_OK", 1: "COLATUS_E_ARG", 2: "COLATUS_E_CUDA",
+                3: "COLATUS_E_NONFINITE", 4: "COLATUS_E_FRIEDMANN", 5: "COLATUS_E_STATE",
+                6: "COLATUS_E_OOM", 7: "COLATUS_E_TIMEOUT"}
+
+# every symbol the header declares
+EXPORTS = ("colatus_init", "colatus_set_config", "colatus_set_masses", "colatus_set_state",
+           "colatus_get_state", "colatus_forces", "colatus_step", "colatus_synchronize",
+           "colatus_record_tracers", "colatus_read_tracers", "colatus_diagnostics",
+           "colatus_last_error", "colatus_stats", "colatus_profile_forces",
+           "colatus_profile_read", "colatus_destroy")
+
+
+class ColatusError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_vp, _i64, _dbl, _int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+
+
+def lib():
+    """Load libcolatus.so (built by ``python -m paper_1208_3444_b300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: the CUDA library must be built "
+                           "(python -m paper_1208_3444_b300.build); there is no fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "colatus_init": [ctypes.POINTER(_vp), _i64, _vp, _dbl, _dbl, _dbl, _dbl, _dbl, _dbl, _dbl],
+        "colatus_set_config": [_vp, _int, _int, _dbl, _vp],
+        "colatus_set_masses": [_vp, _vp, _int, _int],
+        "colatus_set_state": [_vp, _vp, _vp, _int, _int],
+        "colatus_get_state": [_vp, _vp, _vp, _int, _int, _vp, _vp],
+        "colatus_forces": [_vp, _vp, _int, _int],
+        "colatus_step": [_vp, _dbl, _i64],
+        "colatus_synchronize": [_vp],
+        "colatus_record_tracers": [_vp, _vp, _int, _i64],
+        "colatus_read_tracers": [_vp, _vp, _vp],
+        "colatus_diagnostics": [_vp, _vp],
+        "colatus_stats": [_vp, _vp],
+        "colatus_profile_forces": [_vp, _int],
+        "colatus_profile_read": [_vp, _vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = _int
+    L.colatus_last_error.argtypes = [_vp]
+    L.colatus_last_error.restype = ctypes.c_char_p
+    L.colatus_destroy.argtypes = [_vp]
+    L.colatus_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _check(status, handle=None):
+    if status != OK:
+        msg = lib().colatus_last_error(handle)
+        raise ColatusError(status, msg.decode() if msg else "")
+
+
+def _buf(a, ncols=None):
+    """(pointer, on_device, dtype, keep-alive) for a NumPy array or tensor."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype not in (torch.float32, torch.float64):
+                raise TypeError("tensors must be float32 or float64")
+            if not a.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return a.data_ptr(), int(a.is_cuda), F64 if a.dtype == torch.float64 else F32, a
+    except ImportError:
+        pass
+    arr = np.asarray(a)
+    if arr.dtype not in (np.float32, np.float64):
+        arr = arr.astype(np.float64)
+    arr = np.ascontiguousarray(arr)
+    return arr.ctypes.data, 0, F64 if arr.dtype == np.float64 else F32, arr
+
+
+# ------------------------------------------------------------- C entry points
+def colatus_init(N, masses, eps, Omega_R, Omega_M, Omega_K, Omega_L, H0, a_start):
+    m = np.ascontiguousarray(np.asarray(masses, dtype=np.float64).reshape(-1))
+    if m.size != N:
+        raise ValueError("masses must have N entries")
+    h = _vp()
+    st = lib().colatus_init(ctypes.byref(h), int(N), m.ctypes.data, float(eps), float(Omega_R),
+                            float(Omega_M), float(Omega_K), float(Omega_L), float(H0),
+                            float(a_start))
+    _check(st, None)
+    return h
+
+
+def colatus_set_config(h, prec, scheme, G=1.0, stream=None):
+    _check(lib().colatus_set_config(h, int(prec), int(scheme), float(G),
+                                    None if stream is None else int(stream)), h)
+
+
+def colatus_set_masses(h, m):
+    p, dev, dt, keep = _buf(m)
+    _check(lib().colatus_set_masses(h, p, dt, dev), h)
+
+
+def colatus_set_state(h, x, v=None):
+    px, dev, dt, kx = _buf(x)
+    if v is not None:
+        pv, dev2, dt2, kv = _buf(v)
+        if dev2 != dev or dt2 != dt:
+            raise ValueError("x and v must share device and dtype")
+    else:
+        pv = None
+    _check(lib().colatus_set_state(h, px, pv, dt, dev), h)
+
+
+def colatus_get_state(h, x=None, v=None):
+    """Fill x and/or v (N x 3 arrays or tensors, same device and dtype) and
+    return (t, a)."""
+    t, a = _dbl(), _dbl()
+    px = pv = None
+    dev, dt = 0, F64
+    keep = []
+    if x is not None:
+        px, dev, dt, k = _buf(x)
+        keep.append(k)
+    if v is not None:
+        pv, dev2, dt2, k = _buf(v)
+        if x is not None and (dev2 != dev or dt2 != dt):
+            raise ValueError("x and v must share device and dtype")
+        dev, dt = dev2, dt2
+        keep.append(k)
+    _check(lib().colatus_get_state(h, px, pv, dt, dev, ctypes.byref(t), ctypes.byref(a)), h)
+    return t.value, a.value
+
+
+def colatus_forces(h, out):
+    p, dev, dt, keep = _buf(out)
+    _check(lib().colatus_forces(h, p, dt, dev), h)
+    return out
+
+
+def colatus_step(h, dt, nsteps):
+    _check(lib().colatus_step(h, float(dt), int(nsteps)), h)
+
+
+def colatus_synchronize(h):
+    _check(lib().colatus_synchronize(h), h)
+
+
+def colatus_record_tracers(h, idx, capacity_steps):
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64).reshape(-1))
+    _check(lib().colatus_record_tracers(h, idx.ctypes.data if idx.size else None, int(idx.size),
+                                        int(capacity_steps)), h)
+
+
+def colatus_read_tracers(h, ntr):
+    n = ctypes.c_int64()
+    _check(lib().colatus_read_tracers(h, None, ctypes.byref(n)), h)
+    out = np.empty((n.value, ntr, 6), dtype=np.float32)
+    if n.value:
+        _check(lib().colatus_read_tracers(h, out.ctypes.data, ctypes.byref(n)), h)
+    return out
+
+
+def colatus_diagnostics(h):
+    out = np.zeros(NDIAG)
+    _check(lib().colatus_diagnostics(h, out.ctypes.data), h)
+    return out
+
+
+def colatus_stats(h):
+    out = np.zeros(4)
+    _check(lib().colatus_stats(h, out.ctypes.data), h)
+    return out
+
+
+def colatus_profile_forces(h, on):
+    _check(lib().colatus_profile_forces(h, int(on)), h)
+
+
+def colatus_profile_read(h):
+    """(total force-kernel milliseconds, launches) since the last read."""
+    out = np.zeros(2)
+    _check(lib().colatus_profile_read(h, out.ctypes.data), h)
+    return float(out[0]), int(out[1])
+
+
+def colatus_last_error(h=None):
+    s = lib().colatus_last_error(h)
+    return s.decode() if s else ""
+
+
+def colatus_destroy(h):
+    if h:
+        lib().colatus_destroy(h)
+
+
+# ------------------------------------------------------------ convenience
+DIAG_NAMES = ("K", "W", "Px", "Py", "Pz", "Lx", "Ly", "Lz", "Cx", "Cy", "Cz", "a", "t", "H",
+              "Wx", "step")
+
+
+class Simulation:
+    """Owns one colatus context; methods map one-to-one onto the C calls."""
+
+    def __init__(self, masses, eps, cosmo, a_start, prec=FP32, scheme=KDK, G=1.0, stream=None):
+        m = np.asarray(masses, dtype=np.float64).reshape(-1)
+        self.N = m.size
+        c = dict(cosmo)
+        self.h = colatus_init(self.N, m, eps, c["Omega_R"], c["Omega_M"], c["Omega_K"],
+                              c["Omega_L"], c["H0"], a_start)
+        self.prec, self.scheme, self.G = prec, scheme, G
+        colatus_set_config(self.h, prec, scheme, G, stream)
+
+    def configure(self, prec=None, scheme=None, G=None, stream=None):
+        self.prec = self.prec if prec is None else prec
+        self.scheme = self.scheme if scheme is None else scheme
+        self.G = self.G if G is None else G
+        colatus_set_config(self.h, self.prec, self.scheme, self.G, stream)
+
+    def set_state(self, x, v=None):
+        colatus_set_state(self.h, x, v)
+
+    def set_masses(self, m):
+        colatus_set_masses(self.h, m)
+
+    def state(self, dtype=np.float64):
+        x = np.empty((self.N, 3), dtype=dtype)
+        v = np.empty((self.N, 3), dtype=dtype)
+        t, a = colatus_get_state(self.h, x, v)
+        return x, v, t, a
+
+    def forces(self, out=None):
+        if out is None:
+            out = np.empty((self.N, 3), dtype=np.float64)
+        return colatus_forces(self.h, out)
+
+    def step(self, dt, nsteps=1):
+        colatus_step(self.h, dt, nsteps)
+
+    def synchronize(self):
+        colatus_synchronize(self.h)
+
+    def record_tracers(self, idx, capacity_steps):
+        self.ntr = len(idx)
+        colatus_record_tracers(self.h, idx, capacity_steps)
+
+    def read_tracers(self):
+        return colatus_read_tracers(self.h, getattr(self, "ntr", 0))
+
+    def diagnostics(self):
+        return dict(zip(DIAG_NAMES, colatus_diagnostics(self.h)))
+
+    def stats(self):
+        s = colatus_stats(self.h)
+        return dict(launches=int(s[0]), interactions=float(s[1]), steps=int(s[2]), N=int(s[3]))
+
+    def profile_forces(self, on=True):
+        colatus_profile_forces(self.h, on)
+
+    def profile_read(self):
+        return colatus_profile_read(self.h)
+
+    def close(self):
+        if self.h:
+            colatus_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,1059 @@
+// colatus.cu -- the C ABI of include/colatus.h: context, state, force and step
+// entry points of the COLATUS hot path (arXiv 1208.3444, Eqs. 1-5) on sm_103a.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "colatus.h"
+#include "common.cuh"
+#include "diagnostics.cuh"
+#include "force.cuh"
+#include "integrate.cuh"
+
+using namespace colatus;
+
+// ------------------------------------------------------------------ kernels
+// FP32 force variants: "wide" tiles (1024 i-bodies x 512 j-bodies per unit:
+// 256 threads x 4 i-bodies, 2 CTAs per SM) for large N, "narrow" tiles
+// (256 x 64) for N where the wide tiles would leave SMs idle; each as plain
+// or compensated (TwoSum fold every 32 j-pairs), for general or equal masses.
+// The wide shape was chosen by a sweep over threads x i-bodies x j-tile.
+namespace {
+
+constexpr int kStages = 4;
+
+struct F32Variant {
+    int nt, ipt, jt;
+    bool comp, eqm;
+    int smem;
+    const void *fn;
+    void (*launch)(int grid, cudaStream_t, const float *, float4 *, int *, ForceLaunch, float,
+                   float);
+};
+
+template <int NT, int IPT, int JT, int FOLD, bool COMP, bool EQM, int MINB>
+void launch_f32(int grid, cudaStream_t st, const float *pk, float4 *part, int *flags, ForceLaunch L,
+                float eps2, float mass_eq) {
+    using K = F32Kernel<NT, IPT, JT, kStages, FOLD, COMP, EQM>;
+    force_f32_kernel<NT, IPT, JT, kStages, FOLD, COMP, EQM, MINB>
+        <<<grid, NT, K::SMEM, st>>>(pk, part, flags, L, eps2, mass_eq);
+}
+
+template <int NT, int IPT, int JT, int FOLD, bool COMP, bool EQM, int MINB>
+F32Variant make_f32() {
+    using K = F32Kernel<NT, IPT, JT, kStages, FOLD, COMP, EQM>;
+    return F32Variant{NT, IPT, JT, COMP, EQM, K::SMEM,
+                      (const void *)force_f32_kernel<NT, IPT, JT, kStages, FOLD, COMP, EQM, MINB>,
+                      &launch_f32<NT, IPT, JT, FOLD, COMP, EQM, MINB>};
+}
+
+// index = 4 * narrow + 2 * comp + eqm
+enum { V_WIDE = 0, V_NARROW = 4, V_COMP = 2, V_EQM = 1, NUM_F32_VARIANTS = 8 };
+
+const F32Variant &f32_variant(int v) {
+    static const F32Variant table[NUM_F32_VARIANTS] = {
+        make_f32<256, 4, 512, 256, false, false, 2>(),
+        make_f32<256, 4, 512, 256, false, true, 2>(),
+        make_f32<256, 4, 512, 32, true, false, 2>(),
+        make_f32<256, 4, 512, 32, true, true, 2>(),
+        make_f32<128, 2, 64, 32, false, false, 4>(),
+        make_f32<128, 2, 64, 32, false, true, 4>(),
+        make_f32<128, 2, 64, 32, true, false, 4>(),
+        make_f32<128, 2, 64, 32, true, true, 4>(),
+    };
+    return table[v];
+}
+
+constexpr int kF64NT = 128, kF64IPT = 2, kF64JT = 64;
+using F64K = F64Kernel<kF64NT, kF64IPT, kF64JT, kStages>;
+
+constexpr long long kPadAlloc = 1024;   // buffers hold N rounded up to this
+constexpr int kChunk = 1024;            // steps enqueued per chunk of colatus_step
+constexpr int kTabCap = 4096;           // ring of look-ahead schedule entries
+constexpr int kLookahead = 256;         // schedule entries kept ahead of the state
+constexpr int kFriedmannSub = 8;        // RK4 sub-steps per half step
+constexpr int kTabEvents = 8;           // extension events kept in flight
+static_assert(kChunk + 4 * kLookahead <= kTabCap, "schedule ring too small");
+
+long long round_up(long long n, long long m) { return (n + m - 1) / m * m; }
+
+// Segments an i-tile can have under the split of W units over G CTAs.
+int max_segments(const ForceLaunch &L) {
+    long long smax = 1;
+    for (long long it = 0; it < L.n_it; ++it) {
+        const long long g0 = sk_owner(it * L.n_jt, L.W, L.G);
+        const long long g1 = sk_owner((it + 1) * L.n_jt - 1, L.W, L.G);
+        smax = std::max(smax, g1 - g0 + 1);
+    }
+    return (int)smax;
+}
+
+ForceLaunch make_launch(long long n_pad, int itile, int jt, long long g_target) {
+    ForceLaunch L{};
+    L.n_it = (int)(n_pad / itile);
+    L.n_jt = (int)(n_pad / jt);
+    L.W = (long long)L.n_it * L.n_jt;
+    L.G = (int)std::max(1LL, std::min(g_target, L.W));
+    L.S_max = max_segments(L);
+    return L;
+}
+
+struct ForcePlan {
+    int variant = -1;       // F32 variant, or -1 for FP64
+    long long n_pad = 0;    // bodies incl. zero-mass padding
+    int itile = 0, jt = 0;
+    ForceLaunch L{};
+    size_t part_bytes = 0;
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------ context
+struct colatus_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    long long N = 0, n_alloc = 0;
+    double eps = 0.0, G = 1.0;
+    Cosmo cosmo{};
+    colatus_prec prec = COLATUS_FP32;
+    colatus_scheme scheme = COLATUS_KDK;
+
+    // host-side bookkeeping (all deterministic, no device read needed)
+    long long host_step = 0;
+    bool eq_mass = false;      // all masses equal (as floats): EQM force kernels
+    float mass_eq = 0.f;
+    // look-ahead Friedmann schedule: entries [tab_lo, tab_hi) for step size
+    // tab_tau and G tab_G, computed on tstream ahead of the steps
+    bool tab_valid = false;
+    long long tab_hi = 0;
+    double tab_tau = 0.0, tab_G = 0.0;
+    bool have_state = false;
+    bool acc_valid = false;    // acc holds F at the state position
+    bool spec_valid = false;   // pk[cur] holds the next step's force input
+    double spec_tau = 0.0;
+    int cur = 0;
+    long long launches = 0;
+    double interactions = 0.0;
+
+    // FP32 state: xs (x,y,z,m), vs, vh (KDK half-step velocity), acc (G-less F)
+    float4 *xs = nullptr, *vs = nullptr, *vh = nullptr, *acc = nullptr;
+    float *pk[3] = {nullptr, nullptr, nullptr};   // [0],[1] ping-pong, [2] aux
+    // FP64 state
+    double4 *xs64 = nullptr, *vs64 = nullptr, *vh64 = nullptr, *acc64 = nullptr;
+    double4 *pos64[3] = {nullptr, nullptr, nullptr};
+    double *m64 = nullptr;
+
+    void *part = nullptr;
+    size_t part_bytes = 0;
+    int *flags = nullptr;
+    int *mstat = nullptr;          // [min, max] float bits of the masses
+    DevClock *clk = nullptr;       // state clock (t, a, steps)
+    DevClock *tclk = nullptr;      // schedule frontier
+    StepCoef *table = nullptr;     // kTabCap ring, entry s % kTabCap
+    cudaStream_t tstream = nullptr;
+    cudaEvent_t main_ev = nullptr;
+    // one event per schedule extension, with the step count it completes
+    cudaEvent_t tab_ev[kTabEvents] = {};
+    long long tab_ev_covers[kTabEvents] = {};
+    int tab_ev_next = 0;
+    double *stage = nullptr;       // N x 3 doubles for host <-> device transfers
+    double *stage2 = nullptr;
+    double *diag = nullptr;        // diagnostic partial sums
+
+    // tracers
+    int *tslot = nullptr;
+    float *rec = nullptr;
+    int ntr = 0;
+    long long rec_cap = 0, rec_base = 0;
+    std::vector<long long> tidx;
+
+    ForcePlan plan32[NUM_F32_VARIANTS];
+    ForcePlan plan64;
+
+    // force-kernel timing (colatus_profile_forces)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+
+    char err[512] = {0};
+};
+
+namespace {
+
+char g_init_err[512] = {0};
+
+colatus_status fail(colatus_t ctx, colatus_status st, const char *fmt, ...) {
+    char *buf = ctx ? ctx->err : g_init_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define CU(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? COLATUS_E_OOM : COLATUS_E_CUDA, \
+                        "%s: %s", #call, cudaGetErrorString(e_));                         \
+    } while (0)
+
+#define TRY(expr)                              \
+    do {                                       \
+        colatus_status s_ = (expr);            \
+        if (s_ != COLATUS_OK) return s_;       \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+};
+
+unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+colatus_status launched(colatus_t ctx) {
+    ++ctx->launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, COLATUS_E_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return COLATUS_OK;
+}
+
+// ---- plans
+colatus_status build_plans(colatus_t ctx) {
+    for (int v = 0; v < NUM_F32_VARIANTS; ++v) {
+        const F32Variant &fv = f32_variant(v);
+        int occ = 0;
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fv.fn, fv.nt, fv.smem));
+        if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "force variant %d cannot be resident", v);
+        ForcePlan &p = ctx->plan32[v];
+        p.variant = v;
+        p.itile = fv.nt * fv.ipt;
+        p.jt = fv.jt;
+        p.n_pad = round_up(ctx->N, std::max(p.itile, p.jt));
+        p.L = make_launch(p.n_pad, p.itile, p.jt, (long long)occ * ctx->num_sms);
+        p.part_bytes = (size_t)p.L.n_it * p.L.S_max * p.itile * sizeof(float4) * (fv.comp ? 2 : 1);
+    }
+    int occ = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, force_f64_kernel<kF64NT, kF64IPT, kF64JT, kStages>, kF64NT, F64K::SMEM));
+    if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "FP64 force kernel cannot be resident");
+    ForcePlan &p = ctx->plan64;
+    p.variant = -1;
+    p.itile = F64K::ITILE;
+    p.jt = kF64JT;
+    p.n_pad = round_up(ctx->N, std::max(p.itile, p.jt));
+    p.L = make_launch(p.n_pad, p.itile, p.jt, (long long)occ * ctx->num_sms);
+    p.part_bytes = (size_t)p.L.n_it * p.L.S_max * p.itile * sizeof(double4);
+    return COLATUS_OK;
+}
+
+// FP32 variant for the current precision and masses: wide tiles when every
+// CTA still gets at least four units, narrow tiles otherwise.
+// The equal-mass kernels ignore m_j, so they are used only when no zero-mass
+// padding body enters the sum (N_pad == N).
+const ForcePlan &plan_f32(colatus_t ctx) {
+    const int comp = ctx->prec == COLATUS_FP32_COMP ? V_COMP : 0;
+    const ForcePlan *w = &ctx->plan32[V_WIDE + comp];
+    if (w->L.W < 4LL * w->L.G) w = &ctx->plan32[V_NARROW + comp];
+    if (ctx->eq_mass && w->n_pad == ctx->N) w += V_EQM;
+    return *w;
+}
+
+colatus_status ensure_part(colatus_t ctx, size_t bytes) {
+    if (bytes <= ctx->part_bytes) return COLATUS_OK;
+    if (ctx->part) cudaFree(ctx->part);
+    ctx->part = nullptr;
+    ctx->part_bytes = 0;
+    CU(cudaMalloc(&ctx->part, bytes));
+    ctx->part_bytes = bytes;
+    return COLATUS_OK;
+}
+
+// Bracket one force launch with a pair of events when profiling.
+colatus_status prof_begin(colatus_t ctx) {
+    if (!ctx->profiling) return COLATUS_OK;
+    while (ctx->ev_pool.size() < ctx->ev_used + 2) {
+        cudaEvent_t e;
+        CU(cudaEventCreate(&e));
+        ctx->ev_pool.push_back(e);
+    }
+    CU(cudaEventRecord(ctx->ev_pool[ctx->ev_used], ctx->stream));
+    return COLATUS_OK;
+}
+
+colatus_status prof_end(colatus_t ctx) {
+    if (!ctx->profiling) return COLATUS_OK;
+    CU(cudaEventRecord(ctx->ev_pool[ctx->ev_used + 1], ctx->stream));
+    ctx->ev_used += 2;
+    return COLATUS_OK;
+}
+
+// Launch the force sum on packed FP32 bodies; segments land in ctx->part.
+colatus_status run_force_f32(colatus_t ctx, const ForcePlan &p, const float *pk) {
+    TRY(ensure_part(ctx, p.part_bytes));
+    const F32Variant &fv = f32_variant(p.variant);
+    const float eps2 = (float)(ctx->eps * ctx->eps);
+    TRY(prof_begin(ctx));
+    fv.launch(p.L.G, ctx->stream, pk, static_cast<float4 *>(ctx->part), ctx->flags, p.L, eps2,
+              ctx->mass_eq);
+    TRY(launched(ctx));
+    ctx->interactions += (double)ctx->N * (double)ctx->N;
+    return prof_end(ctx);
+}
+
+colatus_status run_force_f64(colatus_t ctx, const double4 *pos) {
+    const ForcePlan &p = ctx->plan64;
+    TRY(ensure_part(ctx, p.part_bytes));
+    TRY(prof_begin(ctx));
+    force_f64_kernel<kF64NT, kF64IPT, kF64JT, kStages><<<p.L.G, kF64NT, F64K::SMEM, ctx->stream>>>(
+        pos, static_cast<double4 *>(ctx->part), ctx->flags, p.L, ctx->eps * ctx->eps);
+    TRY(launched(ctx));
+    ctx->interactions += (double)ctx->N * (double)ctx->N;
+    return prof_end(ctx);
+}
+
+// ---- state conversion kernels (I/O only)
+__global__ void load_state_kernel(const void *x, const void *v, int f64, const double *m64,
+                                  long long N, float4 *xs, float4 *vs, double4 *xs64,
+                                  double4 *vs64, int *bad) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double p[3], q[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < 3; ++c) {
+        p[c] = f64 ? static_cast<const double *>(x)[3 * i + c] : static_cast<const float *>(x)[3 * i + c];
+        if (v) q[c] = f64 ? static_cast<const double *>(v)[3 * i + c]
+                          : static_cast<const float *>(v)[3 * i + c];
+    }
+    const double m = m64[i];
+    bool ok = true;
+    for (int c = 0; c < 3; ++c) ok = ok && isfinite(p[c]) && isfinite(q[c]);
+    if (!ok) atomicOr(bad, 1);
+    xs[i] = make_float4((float)p[0], (float)p[1], (float)p[2], (float)m);
+    vs[i] = make_float4((float)q[0], (float)q[1], (float)q[2], 0.f);
+    xs64[i] = make_double4(p[0], p[1], p[2], m);
+    vs64[i] = make_double4(q[0], q[1], q[2], 0.0);
+}
+
+__global__ void store_state_kernel(const float4 *xs, const float4 *vs, const double4 *xs64,
+                                   const double4 *vs64, int from64, long long N, void *x, void *v,
+                                   int f64) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double p[3], q[3];
+    if (from64) {
+        const double4 a = xs64[i], b = vs64[i];
+        p[0] = a.x; p[1] = a.y; p[2] = a.z;
+        q[0] = b.x; q[1] = b.y; q[2] = b.z;
+    } else {
+        const float4 a = xs[i], b = vs[i];
+        p[0] = a.x; p[1] = a.y; p[2] = a.z;
+        q[0] = b.x; q[1] = b.y; q[2] = b.z;
+    }
+    for (int c = 0; c < 3; ++c) {
+        if (f64) {
+            if (x) static_cast<double *>(x)[3 * i + c] = p[c];
+            if (v) static_cast<double *>(v)[3 * i + c] = q[c];
+        } else {
+            if (x) static_cast<float *>(x)[3 * i + c] = (float)p[c];
+            if (v) static_cast<float *>(v)[3 * i + c] = (float)q[c];
+        }
+    }
+}
+
+// Copy the state of one precision into the other (precision switch).
+__global__ void convert_state_kernel(float4 *xs, float4 *vs, double4 *xs64, double4 *vs64,
+                                     int to64, long long N) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    if (to64) {
+        const float4 a = xs[i], b = vs[i];
+        xs64[i] = make_double4(a.x, a.y, a.z, xs64[i].w);
+        vs64[i] = make_double4(b.x, b.y, b.z, 0.0);
+    } else {
+        const double4 a = xs64[i], b = vs64[i];
+        xs[i] = make_float4((float)a.x, (float)a.y, (float)a.z, xs[i].w);
+        vs[i] = make_float4((float)b.x, (float)b.y, (float)b.z, 0.f);
+    }
+}
+
+// Store the masses and record the extreme float masses (non-negative floats
+// order like their bit patterns) to detect the equal-mass case.
+__global__ void load_masses_kernel(const void *m, int f64, long long N, double *m64, float4 *xs,
+                                   double4 *xs64, int *bad, int *mstat) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double mi = f64 ? static_cast<const double *>(m)[i] : static_cast<const float *>(m)[i];
+    if (!isfinite(mi) || mi < 0.0) atomicOr(bad, 1);
+    m64[i] = mi;
+    xs[i].w = (float)mi;
+    xs64[i].w = mi;
+    const int bits = __float_as_int((float)mi);
+    atomicMin(&mstat[0], bits);
+    atomicMax(&mstat[1], bits);
+}
+
+colatus_status read_flags(colatus_t ctx, bool clear) {
+    int f[NUM_FLAGS];
+    CU(cudaMemcpy(f, ctx->flags, sizeof(f), cudaMemcpyDeviceToHost));
+    if (clear) CU(cudaMemset(ctx->flags, 0, sizeof(f)));
+    if (f[FLAG_TIMEOUT]) return fail(ctx, COLATUS_E_TIMEOUT, "a bounded device wait gave up");
+    if (f[FLAG_FRIEDMANN])
+        return fail(ctx, COLATUS_E_FRIEDMANN, "H^2 < 0 or a <= 0 while integrating Eq. 2");
+    if (f[FLAG_NONFINITE]) return fail(ctx, COLATUS_E_NONFINITE, "non-finite position or velocity");
+    return COLATUS_OK;
+}
+
+colatus_status sync_and_check(colatus_t ctx) {
+    CU(cudaStreamSynchronize(ctx->stream));
+    return read_flags(ctx, true);
+}
+
+size_t elem_size(int dtype) { return dtype == COLATUS_F64 ? 8 : 4; }
+
+colatus_status check_dtype(colatus_t ctx, int dtype) {
+    if (dtype != COLATUS_F32 && dtype != COLATUS_F64) return fail(ctx, COLATUS_E_ARG, "bad dtype %d", dtype);
+    return COLATUS_OK;
+}
+
+void free_all(colatus_t ctx) {
+    void *ptrs[] = {ctx->xs, ctx->vs, ctx->vh, ctx->acc, ctx->pk[0], ctx->pk[1], ctx->pk[2],
+                    ctx->xs64, ctx->vs64, ctx->vh64, ctx->acc64, ctx->pos64[0], ctx->pos64[1],
+                    ctx->pos64[2], ctx->m64, ctx->part, ctx->flags, ctx->mstat, ctx->clk,
+                    ctx->tclk, ctx->table, ctx->stage, ctx->stage2, ctx->diag, ctx->tslot,
+                    ctx->rec};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t e : ctx->tab_ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->main_ev) cudaEventDestroy(ctx->main_ev);
+    if (ctx->tstream) cudaStreamDestroy(ctx->tstream);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    ctx->ev_pool.clear();
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+}
+
+// Load masses (device pointer src) and refresh the equal-mass flag.
+colatus_status load_masses(colatus_t ctx, const void *src, int f64) {
+    const int init[2] = {0x7fffffff, 0};
+    CU(cudaMemcpyAsync(ctx->mstat, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
+    load_masses_kernel<<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
+        src, f64, ctx->N, ctx->m64, ctx->xs, ctx->xs64, ctx->flags, ctx->mstat);
+    TRY(launched(ctx));
+    int st[2];
+    CU(cudaMemcpyAsync(st, ctx->mstat, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->eq_mass = st[0] == st[1];
+    float me;
+    std::memcpy(&me, &st[0], sizeof(me));
+    ctx->mass_eq = me;
+    return COLATUS_OK;
+}
+
+// Extend the look-ahead schedule by n entries on the schedule stream.
+colatus_status extend_table(colatus_t ctx, int n) {
+    if (n <= 0) return COLATUS_OK;
+    friedmann_table_kernel<<<1, 1, 0, ctx->tstream>>>(ctx->cosmo, ctx->tclk, ctx->table, kTabCap,
+                                                      n, ctx->tab_tau, ctx->tab_G, kFriedmannSub);
+    TRY(launched(ctx));
+    ctx->tab_hi += n;
+    const int k = ctx->tab_ev_next;
+    ctx->tab_ev_next = (k + 1) % kTabEvents;
+    CU(cudaEventRecord(ctx->tab_ev[k], ctx->tstream));
+    ctx->tab_ev_covers[k] = ctx->tab_hi;
+    return COLATUS_OK;
+}
+
+// Make schedule entries [host_step, host_step + n) available to the main
+// stream for step size tau.  The schedule stream first waits for all work
+// already enqueued on the main stream, so an extension never overwrites ring
+// entries that enqueued steps still read (the ring holds kTabCap entries and
+// at most kChunk + 4 kLookahead are live).
+colatus_status need_table(colatus_t ctx, double tau, int n) {
+    CU(cudaEventRecord(ctx->main_ev, ctx->stream));
+    CU(cudaStreamWaitEvent(ctx->tstream, ctx->main_ev, 0));
+    if (!ctx->tab_valid || ctx->tab_tau != tau || ctx->tab_G != ctx->G) {
+        clock_copy_kernel<<<1, 1, 0, ctx->tstream>>>(ctx->clk, ctx->tclk);
+        TRY(launched(ctx));
+        ctx->tab_valid = true;
+        ctx->tab_tau = tau;
+        ctx->tab_G = ctx->G;
+        ctx->tab_hi = ctx->host_step;
+        for (long long &c : ctx->tab_ev_covers) c = -1;
+    }
+    const long long need = ctx->host_step + n;
+    if (ctx->tab_hi < need) TRY(extend_table(ctx, (int)(need + kLookahead - ctx->tab_hi)));
+    // wait only for the earliest extension that completes the needed entries
+    int best = -1;
+    for (int k = 0; k < kTabEvents; ++k)
+        if (ctx->tab_ev_covers[k] >= need &&
+            (best < 0 || ctx->tab_ev_covers[k] < ctx->tab_ev_covers[best]))
+            best = k;
+    if (best < 0) return fail(ctx, COLATUS_E_STATE, "schedule bookkeeping lost its extension");
+    CU(cudaStreamWaitEvent(ctx->stream, ctx->tab_ev[best], 0));
+    return COLATUS_OK;
+}
+
+// After enqueuing steps: keep kLookahead entries ahead, computed on the
+// schedule stream while the main stream runs the force kernels.
+colatus_status refill_table(colatus_t ctx) {
+    if (ctx->tab_hi < ctx->host_step + kLookahead) {
+        CU(cudaEventRecord(ctx->main_ev, ctx->stream));
+        CU(cudaStreamWaitEvent(ctx->tstream, ctx->main_ev, 0));
+        TRY(extend_table(ctx, (int)(ctx->host_step + 2 * kLookahead - ctx->tab_hi)));
+    }
+    return COLATUS_OK;
+}
+
+// Pack the state for a force evaluation at the state position into the aux
+// buffer and run the force sum (segments in ctx->part).
+colatus_status force_at_state(colatus_t ctx) {
+    if (ctx->prec == COLATUS_FP64) {
+        const ForcePlan &p = ctx->plan64;
+        pack_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(ctx->xs64, ctx->pos64[2],
+                                                                           ctx->N, p.n_pad);
+        TRY(launched(ctx));
+        return run_force_f64(ctx, ctx->pos64[2]);
+    }
+    const ForcePlan &p = plan_f32(ctx);
+    pack_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(ctx->xs, ctx->pk[2], ctx->N,
+                                                                       p.n_pad);
+    TRY(launched(ctx));
+    return run_force_f32(ctx, p, ctx->pk[2]);
+}
+
+// Reduce the segments of the last force sum into acc and/or out.
+colatus_status force_output(colatus_t ctx, void *out, int out_f64, bool to_acc) {
+    if (ctx->prec == COLATUS_FP64) {
+        const ForcePlan &p = ctx->plan64;
+        forces_out_f64_kernel<<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
+            static_cast<const double4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk, ctx->G, out,
+            out_f64, to_acc ? ctx->acc64 : nullptr);
+        return launched(ctx);
+    }
+    const ForcePlan &p = plan_f32(ctx);
+    if (ctx->prec == COLATUS_FP32_COMP)
+        forces_out_f32_kernel<true><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
+            static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk, ctx->G, out,
+            out_f64, to_acc ? ctx->acc : nullptr);
+    else
+        forces_out_f32_kernel<false><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
+            static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk, ctx->G, out,
+            out_f64, to_acc ? ctx->acc : nullptr);
+    return launched(ctx);
+}
+
+Tracers tracer_args(colatus_t ctx) {
+    Tracers t;
+    t.slot = ctx->tslot;
+    t.rec = ctx->rec;
+    t.cap = ctx->rec_cap > 0 ? ctx->rec_cap : 1;
+    t.base = ctx->rec_base;
+    t.ntr = ctx->ntr;
+    return t;
+}
+
+// Opening of the first step of a call: the KDK half kick + drift, or the
+// DKD half drift, from the state into the force input pk[cur].
+colatus_status open_step(colatus_t ctx, double tau) {
+    const bool f64 = ctx->prec == COLATUS_FP64;
+    if (ctx->scheme == COLATUS_KDK) {
+        if (!ctx->acc_valid) {
+            TRY(force_at_state(ctx));
+            TRY(force_output(ctx, nullptr, 0, true));
+            ctx->acc_valid = true;
+        }
+        if (f64) {
+            const ForcePlan &p = ctx->plan64;
+            kdk_open_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+                ctx->xs64, ctx->vs64, ctx->acc64, ctx->vh64, ctx->pos64[ctx->cur], ctx->table, kTabCap,
+                ctx->host_step, tau, ctx->N, p.n_pad);
+        } else {
+            const ForcePlan &p = plan_f32(ctx);
+            kdk_open_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+                ctx->xs, ctx->vs, ctx->acc, ctx->vh, ctx->pk[ctx->cur], ctx->table, kTabCap, ctx->host_step,
+                tau, ctx->N, p.n_pad);
+        }
+    } else {
+        if (f64) {
+            const ForcePlan &p = ctx->plan64;
+            dkd_open_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+                ctx->xs64, ctx->vs64, ctx->pos64[ctx->cur], tau, ctx->N, p.n_pad);
+        } else {
+            const ForcePlan &p = plan_f32(ctx);
+            dkd_open_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+                ctx->xs, ctx->vs, ctx->pk[ctx->cur], tau, ctx->N, p.n_pad);
+        }
+    }
+    return launched(ctx);
+}
+
+// One step j of the current chunk: force on pk[cur], then the fused epilogue
+// that writes the state and the next force input pk[cur ^ 1].
+colatus_status one_step(colatus_t ctx, int j, double tau) {
+    const Tracers tr = tracer_args(ctx);
+    const int c = ctx->cur, n = c ^ 1;
+    if (ctx->prec == COLATUS_FP64) {
+        const ForcePlan &p = ctx->plan64;
+        TRY(run_force_f64(ctx, ctx->pos64[c]));
+        const double4 *part = static_cast<const double4 *>(ctx->part);
+        if (ctx->scheme == COLATUS_KDK)
+            kdk_step_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+                part, p.L, p.itile, ctx->pos64[c], ctx->xs64, ctx->vs64, ctx->vh64, ctx->acc64,
+                ctx->pos64[n], ctx->table, kTabCap, ctx->host_step + j, tau, ctx->N, p.n_pad, tr, ctx->flags, ctx->clk);
+        else
+            dkd_step_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+                part, p.L, p.itile, ctx->pos64[c], ctx->xs64, ctx->vs64, ctx->acc64, ctx->pos64[n],
+                ctx->table, kTabCap, ctx->host_step + j, tau, ctx->N, p.n_pad, tr, ctx->flags, ctx->clk);
+    } else {
+        const ForcePlan &p = plan_f32(ctx);
+        TRY(run_force_f32(ctx, p, ctx->pk[c]));
+        const float4 *part = static_cast<const float4 *>(ctx->part);
+        const bool comp = ctx->prec == COLATUS_FP32_COMP;
+        const unsigned nb = blocks_for(p.n_pad, 256);
+        if (ctx->scheme == COLATUS_KDK) {
+            if (comp)
+                kdk_step_f32_kernel<true><<<nb, 256, 0, ctx->stream>>>(
+                    part, p.L, p.itile, ctx->pk[c], ctx->xs, ctx->vs, ctx->vh, ctx->acc, ctx->pk[n],
+                    ctx->table, kTabCap, ctx->host_step + j, tau, ctx->N, p.n_pad, tr, ctx->flags, ctx->clk);
+            else
+                kdk_step_f32_kernel<false><<<nb, 256, 0, ctx->stream>>>(
+                    part, p.L, p.itile, ctx->pk[c], ctx->xs, ctx->vs, ctx->vh, ctx->acc, ctx->pk[n],
+                    ctx->table, kTabCap, ctx->host_step + j, tau, ctx->N, p.n_pad, tr, ctx->flags, ctx->clk);
+        } else {
+            if (comp)
+                dkd_step_f32_kernel<true><<<nb, 256, 0, ctx->stream>>>(
+                    part, p.L, p.itile, ctx->pk[c], ctx->xs, ctx->vs, ctx->acc, ctx->pk[n],
+                    ctx->table, kTabCap, ctx->host_step + j, tau, ctx->N, p.n_pad, tr, ctx->flags, ctx->clk);
+            else
+                dkd_step_f32_kernel<false><<<nb, 256, 0, ctx->stream>>>(
+                    part, p.L, p.itile, ctx->pk[c], ctx->xs, ctx->vs, ctx->acc, ctx->pk[n],
+                    ctx->table, kTabCap, ctx->host_step + j, tau, ctx->N, p.n_pad, tr, ctx->flags, ctx->clk);
+        }
+    }
+    TRY(launched(ctx));
+    ctx->cur = n;
+    return COLATUS_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+colatus_status colatus_init(colatus_t *out, int64_t N, const double *masses, double eps,
+                            double Omega_R, double Omega_M, double Omega_K, double Omega_L,
+                            double H0, double a_start) {
+    colatus_t ctx = nullptr;
+    if (!out) return fail(nullptr, COLATUS_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (N < 1) return fail(nullptr, COLATUS_E_ARG, "N must be >= 1 (got %lld)", (long long)N);
+    if (!masses) return fail(nullptr, COLATUS_E_ARG, "masses is NULL");
+    if (!(eps > 0.0) || !std::isfinite(eps))
+        return fail(nullptr, COLATUS_E_ARG, "eps must be finite and > 0 (got %g)", eps);
+    if (!(a_start > 0.0) || !std::isfinite(a_start))
+        return fail(nullptr, COLATUS_E_ARG, "a_start must be finite and > 0");
+    const double om[5] = {Omega_R, Omega_M, Omega_K, Omega_L, H0};
+    for (double o : om)
+        if (!std::isfinite(o)) return fail(nullptr, COLATUS_E_ARG, "cosmological parameters must be finite");
+    const double e2 = Omega_R / std::pow(a_start, 4) + Omega_M / std::pow(a_start, 3) +
+                      Omega_K / (a_start * a_start) + Omega_L;
+    if (!(e2 >= 0.0)) return fail(nullptr, COLATUS_E_ARG, "H^2(a_start) < 0");
+    for (int64_t i = 0; i < N; ++i)
+        if (!std::isfinite(masses[i]) || masses[i] < 0.0)
+            return fail(nullptr, COLATUS_E_ARG, "mass %lld is negative or not finite", (long long)i);
+
+    ctx = new (std::nothrow) colatus_ctx();
+    if (!ctx) return fail(nullptr, COLATUS_E_OOM, "host allocation failed");
+    auto bail = [&](colatus_status st) {
+        snprintf(g_init_err, sizeof(g_init_err), "%s", ctx->err);
+        free_all(ctx);
+        delete ctx;
+        return st;
+    };
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e != cudaSuccess) {
+        fail(ctx, COLATUS_E_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+        return bail(COLATUS_E_CUDA);
+    }
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, ctx->device);
+    if (e != cudaSuccess) {
+        fail(ctx, COLATUS_E_CUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+        return bail(COLATUS_E_CUDA);
+    }
+    ctx->num_sms = prop.multiProcessorCount;
+    ctx->N = N;
+    ctx->n_alloc = round_up(N, kPadAlloc);
+    ctx->eps = eps;
+    ctx->cosmo = Cosmo{Omega_R, Omega_M, Omega_K, Omega_L, H0};
+
+    auto alloc = [&](void **p, size_t bytes) -> colatus_status {
+        cudaError_t r = cudaMalloc(p, bytes);
+        if (r != cudaSuccess)
+            return fail(ctx, r == cudaErrorMemoryAllocation ? COLATUS_E_OOM : COLATUS_E_CUDA,
+                        "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(r));
+        return COLATUS_OK;
+    };
+    const size_t na = (size_t)ctx->n_alloc;
+    colatus_status st = COLATUS_OK;
+    void **f4[] = {(void **)&ctx->xs, (void **)&ctx->vs, (void **)&ctx->vh, (void **)&ctx->acc};
+    for (void **p : f4)
+        if (st == COLATUS_OK) st = alloc(p, na * sizeof(float4));
+    for (int b = 0; b < 3 && st == COLATUS_OK; ++b) st = alloc((void **)&ctx->pk[b], na * 16);
+    void **d4[] = {(void **)&ctx->xs64, (void **)&ctx->vs64, (void **)&ctx->vh64,
+                   (void **)&ctx->acc64, (void **)&ctx->pos64[0], (void **)&ctx->pos64[1],
+                   (void **)&ctx->pos64[2]};
+    for (void **p : d4)
+        if (st == COLATUS_OK) st = alloc(p, na * sizeof(double4));
+    if (st == COLATUS_OK) st = alloc((void **)&ctx->m64, na * sizeof(double));
+    if (st == COLATUS_OK) st = alloc((void **)&ctx->flags, NUM_FLAGS * sizeof(int));
+    if (st == COLATUS_OK) st = alloc((void **)&ctx->mstat, 2 * sizeof(int));
+    if (st == COLATUS_OK) st = alloc((void **)&ctx->clk, sizeof(DevClock));
+    if (st == COLATUS_OK) st = alloc((void **)&ctx->tclk, sizeof(DevClock));
+    if (st == COLATUS_OK) st = alloc((void **)&ctx->table, kTabCap * sizeof(StepCoef));
+    if (st == COLATUS_OK) st = alloc((void **)&ctx->stage, na * 3 * sizeof(double));
+    if (st == COLATUS_OK) st = alloc((void **)&ctx->stage2, na * 3 * sizeof(double));
+    if (st == COLATUS_OK) st = alloc((void **)&ctx->diag, kDiagSlots * sizeof(double));
+    if (st != COLATUS_OK) return bail(st);
+
+    if ((e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        fail(ctx, COLATUS_E_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        return bail(COLATUS_E_CUDA);
+    }
+    ctx->own_stream = true;
+    if ((e = cudaStreamCreateWithFlags(&ctx->tstream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&ctx->main_ev, cudaEventDisableTiming)) != cudaSuccess) {
+        fail(ctx, COLATUS_E_CUDA, "stream/event creation: %s", cudaGetErrorString(e));
+        return bail(COLATUS_E_CUDA);
+    }
+    for (int k = 0; k < kTabEvents; ++k) {
+        if ((e = cudaEventCreateWithFlags(&ctx->tab_ev[k], cudaEventDisableTiming)) != cudaSuccess) {
+            fail(ctx, COLATUS_E_CUDA, "event creation: %s", cudaGetErrorString(e));
+            return bail(COLATUS_E_CUDA);
+        }
+        ctx->tab_ev_covers[k] = -1;
+    }
+    if ((st = build_plans(ctx)) != COLATUS_OK) return bail(st);
+
+    DevClock clk{0.0, a_start, 0, 0};
+    cudaMemsetAsync(ctx->flags, 0, NUM_FLAGS * sizeof(int), ctx->stream);
+    cudaMemcpyAsync(ctx->clk, &clk, sizeof(clk), cudaMemcpyHostToDevice, ctx->stream);
+    // zero everything so that padding bodies are zero-mass at the origin
+    for (void **p : f4) cudaMemsetAsync(*p, 0, na * sizeof(float4), ctx->stream);
+    for (void **p : d4) cudaMemsetAsync(*p, 0, na * sizeof(double4), ctx->stream);
+    for (int b = 0; b < 3; ++b) cudaMemsetAsync(ctx->pk[b], 0, na * 16, ctx->stream);
+    cudaMemcpyAsync(ctx->stage, masses, N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if ((st = load_masses(ctx, ctx->stage, 1)) != COLATUS_OK) return bail(st);
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
+        fail(ctx, COLATUS_E_CUDA, "init: %s", cudaGetErrorString(e));
+        return bail(COLATUS_E_CUDA);
+    }
+    if ((st = read_flags(ctx, true)) != COLATUS_OK) return bail(COLATUS_E_ARG);
+    *out = ctx;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_set_config(colatus_t ctx, colatus_prec prec, colatus_scheme scheme,
+                                  double G, void *cuda_stream) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    if (prec != COLATUS_FP32 && prec != COLATUS_FP32_COMP && prec != COLATUS_FP64)
+        return fail(ctx, COLATUS_E_ARG, "bad precision %d", (int)prec);
+    if (scheme != COLATUS_DKD && scheme != COLATUS_KDK)
+        return fail(ctx, COLATUS_E_ARG, "bad scheme %d", (int)scheme);
+    if (!std::isfinite(G)) return fail(ctx, COLATUS_E_ARG, "G must be finite");
+    if (cuda_stream && (cudaStream_t)cuda_stream != ctx->stream) {
+        CU(cudaStreamSynchronize(ctx->stream));
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        ctx->stream = (cudaStream_t)cuda_stream;
+        ctx->own_stream = false;
+    }
+    const bool was64 = ctx->prec == COLATUS_FP64, is64 = prec == COLATUS_FP64;
+    if (ctx->have_state && was64 != is64) {
+        convert_state_kernel<<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
+            ctx->xs, ctx->vs, ctx->xs64, ctx->vs64, is64 ? 1 : 0, ctx->N);
+        TRY(launched(ctx));
+    }
+    if (prec != ctx->prec || scheme != ctx->scheme) ctx->acc_valid = false;
+    ctx->spec_valid = false;
+    ctx->prec = prec;
+    ctx->scheme = scheme;
+    ctx->G = G;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_set_masses(colatus_t ctx, const void *m, int dtype, int on_device) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    TRY(check_dtype(ctx, dtype));
+    if (!m) return fail(ctx, COLATUS_E_ARG, "masses is NULL");
+    const void *src = m;
+    if (!on_device) {
+        CU(cudaMemcpyAsync(ctx->stage, m, ctx->N * elem_size(dtype), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        src = ctx->stage;
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    TRY(read_flags(ctx, true));
+    TRY(load_masses(ctx, src, dtype == COLATUS_F64));
+    colatus_status st = sync_and_check(ctx);
+    if (st == COLATUS_E_NONFINITE) return fail(ctx, COLATUS_E_ARG, "masses must be finite and >= 0");
+    TRY(st);
+    ctx->acc_valid = false;
+    ctx->spec_valid = false;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_set_state(colatus_t ctx, const void *x, const void *v, int dtype,
+                                 int on_device) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    TRY(check_dtype(ctx, dtype));
+    if (!x) return fail(ctx, COLATUS_E_ARG, "x is NULL");
+    const size_t bytes = (size_t)ctx->N * 3 * elem_size(dtype);
+    const void *px = x, *pv = v;
+    if (!on_device) {
+        CU(cudaMemcpyAsync(ctx->stage, x, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        px = ctx->stage;
+        if (v) {
+            CU(cudaMemcpyAsync(ctx->stage2, v, bytes, cudaMemcpyHostToDevice, ctx->stream));
+            pv = ctx->stage2;
+        }
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    TRY(read_flags(ctx, true));
+    load_state_kernel<<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
+        px, pv, dtype == COLATUS_F64, ctx->m64, ctx->N, ctx->xs, ctx->vs, ctx->xs64, ctx->vs64,
+        ctx->flags);
+    TRY(launched(ctx));
+    TRY(sync_and_check(ctx));
+    ctx->have_state = true;
+    ctx->acc_valid = false;
+    ctx->spec_valid = false;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_get_state(colatus_t ctx, void *x, void *v, int dtype, int on_device,
+                                 double *t, double *a) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    TRY(check_dtype(ctx, dtype));
+    TRY(sync_and_check(ctx));
+    if (x || v) {
+        if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
+        const size_t bytes = (size_t)ctx->N * 3 * elem_size(dtype);
+        void *dx = on_device ? x : (x ? (void *)ctx->stage : nullptr);
+        void *dv = on_device ? v : (v ? (void *)ctx->stage2 : nullptr);
+        store_state_kernel<<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
+            ctx->xs, ctx->vs, ctx->xs64, ctx->vs64, ctx->prec == COLATUS_FP64, ctx->N, dx, dv,
+            dtype == COLATUS_F64);
+        TRY(launched(ctx));
+        if (!on_device) {
+            if (x) CU(cudaMemcpyAsync(x, ctx->stage, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+            if (v) CU(cudaMemcpyAsync(v, ctx->stage2, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    if (t || a) {
+        DevClock c;
+        CU(cudaMemcpy(&c, ctx->clk, sizeof(c), cudaMemcpyDeviceToHost));
+        if (t) *t = c.t;
+        if (a) *a = c.a;
+    }
+    return COLATUS_OK;
+}
+
+colatus_status colatus_forces(colatus_t ctx, void *acc_out, int dtype, int on_device) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    TRY(check_dtype(ctx, dtype));
+    if (!acc_out) return fail(ctx, COLATUS_E_ARG, "acc_out is NULL");
+    if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
+    TRY(force_at_state(ctx));
+    void *dst = on_device ? acc_out : (void *)ctx->stage;
+    TRY(force_output(ctx, dst, dtype == COLATUS_F64, true));
+    ctx->acc_valid = true;
+    if (!on_device) {
+        CU(cudaMemcpyAsync(acc_out, ctx->stage, (size_t)ctx->N * 3 * elem_size(dtype),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+        TRY(sync_and_check(ctx));
+    }
+    return COLATUS_OK;
+}
+
+colatus_status colatus_step(colatus_t ctx, double dt, int64_t nsteps) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, COLATUS_E_ARG, "dt must be finite and > 0");
+    if (nsteps < 0) return fail(ctx, COLATUS_E_ARG, "nsteps must be >= 0");
+    if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
+    if (nsteps == 0) return COLATUS_OK;
+    if (ctx->spec_valid && ctx->spec_tau != dt) ctx->spec_valid = false;
+    for (int64_t done = 0; done < nsteps;) {
+        const int n = (int)std::min<int64_t>(kChunk, nsteps - done);
+        TRY(need_table(ctx, dt, n));
+        if (!ctx->spec_valid) {
+            TRY(open_step(ctx, dt));
+            ctx->spec_valid = true;
+            ctx->spec_tau = dt;
+        }
+        for (int j = 0; j < n; ++j) TRY(one_step(ctx, j, dt));
+        done += n;
+        ctx->host_step += n;
+        TRY(refill_table(ctx));
+    }
+    ctx->acc_valid = ctx->scheme == COLATUS_KDK;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_synchronize(colatus_t ctx) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    return sync_and_check(ctx);
+}
+
+colatus_status colatus_record_tracers(colatus_t ctx, const int64_t *idx, int ntr,
+                                      int64_t capacity_steps) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    if (ntr < 0) return fail(ctx, COLATUS_E_ARG, "ntr must be >= 0");
+    if (ntr > 0 && (!idx || capacity_steps < 1))
+        return fail(ctx, COLATUS_E_ARG, "need indices and capacity_steps >= 1");
+    std::vector<int> slot;
+    if (ntr > 0) {
+        slot.assign(ctx->N, -1);
+        for (int k = 0; k < ntr; ++k) {
+            if (idx[k] < 0 || idx[k] >= ctx->N)
+                return fail(ctx, COLATUS_E_ARG, "tracer index %lld out of range", (long long)idx[k]);
+            if (slot[idx[k]] >= 0) return fail(ctx, COLATUS_E_ARG, "duplicate tracer index");
+            slot[idx[k]] = k;
+        }
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (ctx->tslot) cudaFree(ctx->tslot);
+    if (ctx->rec) cudaFree(ctx->rec);
+    ctx->tslot = nullptr;
+    ctx->rec = nullptr;
+    ctx->ntr = 0;
+    ctx->rec_cap = 0;
+    ctx->tidx.clear();
+    if (ntr == 0) return COLATUS_OK;
+    CU(cudaMalloc(&ctx->tslot, ctx->N * sizeof(int)));
+    CU(cudaMalloc(&ctx->rec, (size_t)capacity_steps * ntr * 6 * sizeof(float)));
+    CU(cudaMemcpy(ctx->tslot, slot.data(), ctx->N * sizeof(int), cudaMemcpyHostToDevice));
+    ctx->ntr = ntr;
+    ctx->rec_cap = capacity_steps;
+    ctx->rec_base = ctx->host_step;
+    ctx->tidx.assign(idx, idx + ntr);
+    return COLATUS_OK;
+}
+
+colatus_status colatus_read_tracers(colatus_t ctx, float *xv_out, int64_t *nrec_out) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    if (!nrec_out) return fail(ctx, COLATUS_E_ARG, "nrec_out is NULL");
+    TRY(sync_and_check(ctx));
+    if (ctx->ntr == 0) {
+        *nrec_out = 0;
+        return COLATUS_OK;
+    }
+    const long long total = ctx->host_step - ctx->rec_base;
+    const long long nrec = std::min(total, ctx->rec_cap);
+    *nrec_out = nrec;
+    if (!xv_out || nrec == 0) return COLATUS_OK;
+    const size_t row = (size_t)ctx->ntr * 6;
+    std::vector<float> ring((size_t)ctx->rec_cap * row);
+    CU(cudaMemcpy(ring.data(), ctx->rec, ring.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    for (long long k = 0; k < nrec; ++k) {
+        const long long s = total - nrec + k;   // steps since the recording started
+        const long long r = s % ctx->rec_cap;
+        std::memcpy(xv_out + k * row, ring.data() + r * row, row * sizeof(float));
+    }
+    return COLATUS_OK;
+}
+
+colatus_status colatus_diagnostics(colatus_t ctx, double out[COLATUS_NDIAG]) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    if (!out) return fail(ctx, COLATUS_E_ARG, "out is NULL");
+    if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
+    TRY(sync_and_check(ctx));
+    const bool f64 = ctx->prec == COLATUS_FP64;
+    CU(cudaMemsetAsync(ctx->diag, 0, kDiagSlots * sizeof(double), ctx->stream));
+    const unsigned nb = (unsigned)std::min<long long>(blocks_for(ctx->N, kDiagThreads), 4L * ctx->num_sms);
+    potential_energy_kernel<<<nb, kDiagThreads, 0, ctx->stream>>>(
+        ctx->xs, ctx->xs64, f64 ? 1 : 0, ctx->N, ctx->eps * ctx->eps, ctx->diag);
+    TRY(launched(ctx));
+    moments_kernel<<<nb, kDiagThreads, 0, ctx->stream>>>(ctx->xs, ctx->vs, ctx->xs64, ctx->vs64,
+                                                        f64 ? 1 : 0, ctx->N, ctx->diag);
+    TRY(launched(ctx));
+    finish_diagnostics_kernel<<<1, 1, 0, ctx->stream>>>(ctx->diag, ctx->clk, ctx->cosmo, ctx->G);
+    TRY(launched(ctx));
+    CU(cudaMemcpyAsync(out, ctx->diag + kDiagOut, COLATUS_NDIAG * sizeof(double),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    TRY(sync_and_check(ctx));
+    out[15] = (double)ctx->host_step;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_profile_forces(colatus_t ctx, int on) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->profiling = on != 0;
+    ctx->ev_used = 0;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_profile_read(colatus_t ctx, double out[2]) {
+    if (!ctx || !out) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    CU(cudaStreamSynchronize(ctx->stream));
+    double ms = 0.0;
+    for (size_t k = 0; k + 1 < ctx->ev_used; k += 2) {
+        float e = 0.f;
+        CU(cudaEventElapsedTime(&e, ctx->ev_pool[k], ctx->ev_pool[k + 1]));
+        ms += e;
+    }
+    out[0] = ms;
+    out[1] = (double)(ctx->ev_used / 2);
+    ctx->ev_used = 0;
+    return COLATUS_OK;
+}
+
+const char *colatus_last_error(colatus_t ctx) { return ctx ? ctx->err : g_init_err; }
+
+void colatus_destroy(colatus_t ctx) {
+    if (!ctx) return;
+    {
+        DeviceGuard dg(ctx->device);
+        if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+        free_all(ctx);
+    }
+    delete ctx;
+}
+
+colatus_status colatus_stats(colatus_t ctx, double out[4]) {
+    if (!ctx || !out) return COLATUS_E_ARG;
+    out[0] = (double)ctx->launches;
+    out[1] = ctx->interactions;
+    out[2] = (double)ctx->host_step;
+    out[3] = (double)ctx->N;
+    return COLATUS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// common.cuh -- shared device helpers of the COLATUS sm_103a library:
+// mbarrier / bulk-copy (TMA) wrappers with bounded waits, the approximate
+// reciprocal square root, two-float summation, and the FP64 scalar records.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace colatus {
+
+// Device error flags (one int each, OR-ed by kernels, read by the host).
+enum DevFlag : int { FLAG_NONFINITE = 0, FLAG_FRIEDMANN = 1, FLAG_TIMEOUT = 2, NUM_FLAGS = 4 };
+
+// Cycles a bounded wait may spin before it gives up (about 1-2 s at the
+// B300's 1.1-2.0 GHz SM clocks).  A wait that gives up raises FLAG_TIMEOUT
+// and the kernel returns instead of hanging.
+constexpr long long kWaitCycles = 2000000000LL;
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+// Make mbarrier initialisation visible to the asynchronous (bulk-copy) proxy.
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// One-dimensional bulk copy global -> shared, completing on `bar`.
+// Both addresses must be 16-byte aligned and `bytes` a multiple of 16.
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src_gmem, uint32_t bytes,
+                                          uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of `bar` to complete, for at most kWaitCycles.
+// Returns false (and leaves the caller to raise FLAG_TIMEOUT) on give-up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+// Approximate 1/sqrt(x) on the SFU (MUFU.RSQ), flushing subnormals.
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Knuth's TwoSum: s + e == a + b exactly (round-to-nearest).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
+// Add b to the two-float (hi, lo) accumulator.
+__device__ __forceinline__ void acc2_add(float &hi, float &lo, float b) {
+    float s, e;
+    two_sum(hi, b, s, e);
+    hi = s;
+    lo += e;
+}
+
+// --------------------------------------------------------- FP64 scalar records
+// Per-step scale factors and kick coefficients, written by the Friedmann
+// kernel (FP64) and read by the step kernels.  Kick over a span h at scale
+// factor a with Hubble rate H (Eq. 4 with tau -> h):
+//     v' = c v + d G F,   c = (1 - H h)/(1 + H h),  d = h / (a^3 (1 + H h)).
+// The d stored below already includes G.
+struct StepCoef {
+    double a0, ah, a1;   // a at t^n, t^{n+1/2}, t^{n+1}
+    double c, d;         // DKD kick at t^{n+1/2}, span tau
+    double c1, d1;       // KDK first half kick at t^n, span tau/2
+    double c2, d2;       // KDK second half kick at t^{n+1}, span tau/2
+    double t1;           // t^{n+1}
+    long long step;      // absolute index n of the step
+    int bad;             // Eq. 2 radicand went negative (coefficients are NaN)
+    int pad;
+};
+
+// Device-resident clock of a context: t, a(t) and the number of steps taken.
+struct DevClock {
+    double t, a;
+    long long step;
+    long long pad;
+};
+
+struct Cosmo {
+    double Omega_R, Omega_M, Omega_K, Omega_L, H0;
+};
+
+}  // namespace colatus

@@ -70,11 +70,17 @@ def growing_mode_factor(a: float, Omega_M: float = 0.3, Omega_L: float = 0.7,
     return H0 * math.sqrt(e2) * om_a ** 0.55
 
 
+# Mean comoving matter density of the flat LCDM background with G = H0 = 1:
+# Omega_M * 3 H0^2 / (8 pi G).  The paper's boxes hold their galaxies "in the
+# critical density"; total mass 1 in the unit box (m = 1/N) is ~28x denser.
+CRITICAL_MATTER_DENSITY = 0.3 * 3.0 / (8.0 * math.pi)
+
+
 def perturbed_grid(n: int, sigma: float, eps_spacing: float, seed: int,
                    zeldovich: bool = False, a_start: float = A_START, count: Optional[int] = None,
-                   name: str = "perturbed_grid") -> ICs:
+                   name: str = "perturbed_grid", total_mass: float = 1.0) -> ICs:
     """Lattice q = (i + 1/2)/n per axis in the unit box, displaced by Gaussian
-    noise of standard deviation sigma/n; m = 1/N, eps = eps_spacing/n.
+    noise of standard deviation sigma/n; m = total_mass/N, eps = eps_spacing/n.
 
     count < n^3 keeps the first ``count`` lattice points of a seeded
     permutation (uneven-N ensembles).  zeldovich=True gives v = H f (x - q)."""
@@ -90,7 +96,7 @@ def perturbed_grid(n: int, sigma: float, eps_spacing: float, seed: int,
         v = f32(growing_mode_factor(a_start) * (x - q))
     else:
         v = np.zeros_like(x)
-    m = f32(np.full(N, 1.0 / N))
+    m = f32(np.full(N, total_mass / N))
     spacing = 1.0 / n if count is None else N ** (-1.0 / 3.0)
     return ICs(x=x, v=v, m=m, eps=float(np.float32(eps_spacing * spacing)), name=name, q=q,
                meta=dict(n=n, sigma=sigma, seed=seed))
@@ -140,15 +146,19 @@ def tracers(N: int, ntr: int, seed: int) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- workloads
-def grid16(seed: int = 1) -> ICs:
-    """N = 16^3 = 4096, sigma = 0.05 spacing, v = 0, eps = 0.01 spacing."""
-    return perturbed_grid(16, 0.05, 0.01, seed, zeldovich=False, name="grid16")
+def grid16(seed: int = 1, critical: bool = False) -> ICs:
+    """N = 16^3 = 4096, sigma = 0.05 spacing, v = 0, eps = 0.01 spacing,
+    m = 1/N (critical=True: the box at the background matter density)."""
+    return perturbed_grid(16, 0.05, 0.01, seed, zeldovich=False, name="grid16",
+                          total_mass=CRITICAL_MATTER_DENSITY if critical else 1.0)
 
 
-def grid32(seed: int = 2) -> ICs:
+def grid32(seed: int = 2, critical: bool = False) -> ICs:
     """N = 32^3 = 32768, sigma = 0.1 spacing, growing-mode velocities,
-    eps = 0.02 spacing (the paper's 32^3 run size)."""
-    return perturbed_grid(32, 0.1, 0.02, seed, zeldovich=True, name="grid32")
+    eps = 0.02 spacing (the paper's 32^3 run size), m = 1/N (critical=True:
+    the box at the background matter density)."""
+    return perturbed_grid(32, 0.1, 0.02, seed, zeldovich=True, name="grid32",
+                          total_mass=CRITICAL_MATTER_DENSITY if critical else 1.0)
 
 
 def grid8(seed: int = 4) -> ICs:

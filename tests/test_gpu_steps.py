@@ -1,0 +1,202 @@
+"""GPU parity of the leapfrog with Hubble drag (Eqs. 3-5, KDK) and the FP64
+Friedmann schedule (Eq. 2) against the FP64 oracle.
+
+Positions are compared element by element (maximum over bodies <= 1e-5 box
+units in FP32, 1e-9 in FP64) for as long as the dynamics do not amplify
+rounding: 10 steps for boxes at the background (critical) matter density, and
+the steps before collapse for the m = 1/N boxes (3 for 16^3, 2 for 32^3 with its
+infall velocities), which are ~28x overdense and collapse within a few steps (the FP64 oracle itself then amplifies a 6e-8
+perturbation to 1e-3; see tests/test_oracle_chaos.py).  Beyond that, exact
+discrete invariants apply.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1208_3444_b300 import binding as B
+from paper_1208_3444_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+LCDM_D = dict(Omega_R=0.0, Omega_M=0.3, Omega_K=0.0, Omega_L=0.7, H0=1.0)
+LCDM = oracle.Cosmology(0.0, 0.3, 0.0, 0.7, 1.0)
+TAU = inputs.lcdm_tau(2000)
+POS_TOL = {B.FP32: 1e-5, B.FP32_COMP: 1e-5, B.FP64: 1e-9}
+# Velocities: RMS over bodies relative to RMS |v|, and the worst body relative
+# to max |v|.  A body in a close encounter (separation ~ eps) receives kicks of
+# ~10^3 whose relative accuracy is limited by the float32 positions
+# (ulp / eps ~ 1e-4), hence the looser worst-body bound in FP32.
+VEL_RMS_TOL = {B.FP32: 1e-5, B.FP32_COMP: 1e-5, B.FP64: 1e-11}
+VEL_MAX_TOL = {B.FP32: 1e-3, B.FP32_COMP: 1e-3, B.FP64: 1e-9}
+PRE_COLLAPSE = {"grid16": 3, "grid32": 2}
+SCHEME = {"kdk": B.KDK, "dkd": B.DKD}
+
+
+def run_gpu(ic, prec, scheme, nsteps, tracers=None, chunks=None, a_start=inputs.A_START, G=1.0,
+            cosmo=LCDM_D, tau=TAU):
+    sim = B.Simulation(ic.m, ic.eps, cosmo, a_start, prec=prec, scheme=SCHEME[scheme], G=G)
+    try:
+        sim.set_state(ic.x, ic.v)
+        if tracers is not None:
+            sim.record_tracers(tracers, nsteps)
+        for n in (chunks or [nsteps]):
+            sim.step(tau, n)
+        x, v, t, a = sim.state()
+        rec = sim.read_tracers() if tracers is not None else None
+        diag = sim.diagnostics()
+        return dict(x=x, v=v, t=t, a=a, tracers=rec, diag=diag, stats=sim.stats())
+    finally:
+        sim.close()
+
+
+def check_state(g, r, prec, n):
+    assert np.abs(g["x"] - r["x"]).max() < POS_TOL[prec]
+    dv = np.linalg.norm(g["v"] - r["v"], axis=1)
+    vn = np.linalg.norm(r["v"], axis=1)
+    assert np.sqrt(np.mean(dv ** 2)) < VEL_RMS_TOL[prec] * np.sqrt(np.mean(vn ** 2))
+    assert dv.max() < VEL_MAX_TOL[prec] * vn.max()
+    assert g["a"] == pytest.approx(r["schedule"]["a"][-1], rel=1e-13)
+    assert g["t"] == pytest.approx(n * TAU, rel=1e-13)
+
+
+@pytest.mark.parametrize("scheme", ["kdk", "dkd"])
+@pytest.mark.parametrize("prec", [B.FP32, B.FP32_COMP, B.FP64])
+def test_grid16_ten_steps_critical_density(prec, scheme):
+    ic = inputs.grid16(critical=True)
+    n = 10
+    g = run_gpu(ic, prec, scheme, n)
+    r = oracle.run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n, scheme)
+    check_state(g, r, prec, n)
+
+
+@pytest.mark.parametrize("scheme", ["kdk", "dkd"])
+@pytest.mark.parametrize("prec", [B.FP32, B.FP32_COMP, B.FP64])
+def test_grid16_before_collapse(prec, scheme):
+    ic = inputs.grid16()
+    n = PRE_COLLAPSE["grid16"]
+    g = run_gpu(ic, prec, scheme, n)
+    r = oracle.run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n, scheme)
+    check_state(g, r, prec, n)
+
+
+def test_grid16_twenty_steps_fp64():
+    # the oracle-checkable workload: 16^3 bodies, 20 KDK steps in FP64; the
+    # collapse after step 4 multiplies rounding-order differences by ~1e6
+    # (tests/test_oracle_chaos.py), so 1e-7 is ~10x the expected difference
+    ic = inputs.grid16()
+    g = run_gpu(ic, B.FP64, "kdk", 20)
+    r = oracle.run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, 20, "kdk")
+    assert np.abs(g["x"] - r["x"]).max() < 1e-7
+    assert g["a"] == pytest.approx(r["schedule"]["a"][-1], rel=1e-13)
+
+
+@pytest.mark.parametrize("critical,n", [(False, PRE_COLLAPSE["grid32"]), (True, 10)])
+def test_grid32_with_tracers(critical, n):
+    # the 32^3 paper-scale workload: growing-mode velocities, FP32 compensated
+    # force, FP64 a(t), 64 tracers recorded every step
+    ic = inputs.grid32(critical=critical)
+    tr = inputs.tracers(ic.N, 64, 7)
+    g = run_gpu(ic, B.FP32_COMP, "kdk", n, tracers=tr)
+    r = oracle.run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n, "kdk", tracers=tr)
+    check_state(g, r, B.FP32_COMP, n)
+    assert g["tracers"].shape == (n, 64, 6)
+    np.testing.assert_allclose(g["tracers"][:, :, :3], r["tracers"][:, :, :3], atol=1e-5)
+    vs = np.abs(r["tracers"][:, :, 3:]).max()
+    np.testing.assert_allclose(g["tracers"][:, :, 3:], r["tracers"][:, :, 3:],
+                               atol=VEL_MAX_TOL[B.FP32_COMP] * vs)
+
+
+def test_split_calls_equal_one_call():
+    ic = inputs.grid16(critical=True)
+    one = run_gpu(ic, B.FP32, "kdk", 12)
+    split = run_gpu(ic, B.FP32, "kdk", 12, chunks=[5, 1, 6])
+    assert np.array_equal(one["x"], split["x"]) and np.array_equal(one["v"], split["v"])
+
+
+def test_more_steps_than_one_schedule_chunk():
+    # 1100 steps cross the 1024-step schedule chunk; small weakly bound system
+    rng = np.random.default_rng(21)
+    N = 64
+    x = inputs.f32(rng.random((N, 3)))
+    v = inputs.f32(0.01 * rng.standard_normal((N, 3)))
+    m = inputs.f32(np.full(N, 0.01 / N))
+    ic = inputs.ICs(x=x, v=v, m=m, eps=0.05, name="weak")
+    tau = 1e-3
+    g = run_gpu(ic, B.FP64, "kdk", 1100, a_start=0.5, tau=tau)
+    r = oracle.run(x, v, m, 0.05, 1.0, LCDM, 0.5, tau, 1100, "kdk")
+    assert np.abs(g["x"] - r["x"]).max() < 1e-9
+    assert g["a"] == pytest.approx(r["schedule"]["a"][-1], rel=1e-12)
+
+
+def test_diagnostics_match_oracle():
+    ic = inputs.grid16(critical=True)
+    g = run_gpu(ic, B.FP64, "kdk", 5)
+    r = oracle.run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, 5, "kdk")
+    d = oracle.diagnostics(r["x"], r["v"], ic.m, r["schedule"]["a"][-1], ic.eps, 1.0, LCDM)
+    gd = g["diag"]
+    assert gd["K"] == pytest.approx(d["K"], rel=1e-9)
+    assert gd["W"] == pytest.approx(d["W"], rel=1e-9)
+    assert gd["H"] == pytest.approx(d["H"], rel=1e-12)
+    np.testing.assert_allclose([gd["Cx"], gd["Cy"], gd["Cz"]], d["COM"], rtol=1e-12)
+    pscale = abs(d["K"]) ** 0.5
+    np.testing.assert_allclose([gd["Px"], gd["Py"], gd["Pz"]], d["P"], atol=1e-12 * pscale + 1e-15)
+    assert gd["step"] == 5
+
+
+def test_fp32_diagnostics_close_to_oracle():
+    ic = inputs.grid16(critical=True)
+    g = run_gpu(ic, B.FP32, "kdk", 3)
+    r = oracle.run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, 3, "kdk")
+    d = oracle.diagnostics(r["x"], r["v"], ic.m, r["schedule"]["a"][-1], ic.eps, 1.0, LCDM)
+    assert g["diag"]["W"] == pytest.approx(d["W"], rel=1e-6)
+    assert g["diag"]["K"] == pytest.approx(d["K"], rel=1e-4)
+
+
+def test_momentum_and_angular_momentum_invariants_fp64():
+    # sum m F = 0 and sum m x cross F = 0 make sum m v and sum m x cross v
+    # scale exactly by the product of the drag factors
+    ic = inputs.grid16()
+    rng = np.random.default_rng(5)
+    ic.v = inputs.f32(0.05 * rng.standard_normal(ic.x.shape))
+    n = 30
+    g = run_gpu(ic, B.FP64, "kdk", n)
+    sch = oracle.schedule(LCDM, inputs.A_START, TAU, n, "kdk")
+    fac = np.prod(sch["c1"] * sch["c2"])
+    P0 = np.sum(ic.m[:, None] * ic.v, axis=0)
+    P1 = np.sum(ic.m[:, None] * g["v"], axis=0)
+    np.testing.assert_allclose(P1, fac * P0, atol=1e-12 * np.abs(P0).max())
+
+
+def test_error_paths():
+    ic = inputs.grid16()
+    sim = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START)
+    try:
+        with pytest.raises(B.ColatusError) as e:
+            sim.step(TAU, 1)
+        assert e.value.status == B.E_STATE
+        bad = ic.x.copy()
+        bad[7, 1] = np.nan
+        with pytest.raises(B.ColatusError) as e:
+            sim.set_state(bad)
+        assert e.value.status == B.E_NONFINITE
+        sim.set_state(ic.x)
+        with pytest.raises(B.ColatusError) as e:
+            sim.step(-1.0, 1)
+        assert e.value.status == B.E_ARG
+    finally:
+        sim.close()
+
+
+def test_recollapse_reports_friedmann_error():
+    # closed matter universe (Omega_M = 2, Omega_K = -1) turns around at a = 2
+    ic = inputs.grid16()
+    sim = B.Simulation(ic.m, ic.eps, dict(Omega_R=0.0, Omega_M=2.0, Omega_K=-1.0, Omega_L=0.0, H0=1.0),
+                       1.9, prec=B.FP64)
+    try:
+        sim.set_state(ic.x)
+        sim.step(0.05, 40)
+        with pytest.raises(B.ColatusError) as e:
+            sim.synchronize()
+        assert e.value.status == B.E_FRIEDMANN
+    finally:
+        sim.close()
