@@ -160,6 +160,27 @@ colatus_status colatus_profile_forces(colatus_t ctx, int on);
  * and resets the totals. */
 colatus_status colatus_profile_read(colatus_t ctx, double out[2]);
 
+/* Allocation-free FP32 force, for callers that cannot call cudaMalloc (code
+ * running inside another framework's memory pool or under a fixed
+ * device-memory budget, or latency-bound loops that must not pay cudaMalloc's
+ * implicit device synchronisation).  The paper has no counterpart; it is the
+ * colatus_forces computation without a context:
+ *   acc_out[3k..3k+2] = G a^-3 sum_{j != k} m_j (x_j - x_k) / (|x_j - x_k|^2 + eps^2)^{3/2}
+ *   pos:     device array of N float4 (x, y, z, m), 16-byte aligned.
+ *   acc_out: device array of N x 3 floats.
+ *   N:       1 <= N <= 32768; eps > 0, a > 0, G finite (else COLATUS_E_ARG).
+ *   cuda_stream: the cudaStream_t to run on (NULL: the legacy default stream).
+ * It allocates nothing: its scratch (packed bodies, force segments, error
+ * flags) is one fixed static device array of about 8.6 MiB that every GPU
+ * loading the library holds until the process exits.  The first call on a
+ * device also resolves that array's device address (cudaGetSymbolAddress);
+ * make this first call before any stream capture.  Every call shares the
+ * scratch, so calls whose GPU work overlaps (different streams or threads)
+ * race: serialise them.  The call synchronises `cuda_stream` before it
+ * returns and reports a device-side wait that gave up as COLATUS_E_TIMEOUT. */
+colatus_status colatus_forces_noalloc(const float *pos, int64_t N, double eps, double G, double a,
+                                      float *acc_out, void *cuda_stream);
+
 /* Release every device and host resource of ctx (NULL is a no-op). */
 void colatus_destroy(colatus_t ctx);
 

@@ -30,7 +30,7 @@ EXPORTS = ("colatus_init", "colatus_set_config", "colatus_set_masses", "colatus_
            "colatus_get_state", "colatus_forces", "colatus_step", "colatus_synchronize",
            "colatus_record_tracers", "colatus_read_tracers", "colatus_diagnostics",
            "colatus_last_error", "colatus_stats", "colatus_profile_forces",
-           "colatus_profile_read", "colatus_destroy")
+           "colatus_profile_read", "colatus_forces_noalloc", "colatus_destroy")
 
 
 class ColatusError(RuntimeError):
@@ -67,6 +67,7 @@ def lib():
         "colatus_stats": [_vp, _vp],
         "colatus_profile_forces": [_vp, _int],
         "colatus_profile_read": [_vp, _vp],
+        "colatus_forces_noalloc": [_vp, _i64, _dbl, _dbl, _dbl, _vp, _vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -209,6 +210,20 @@ def colatus_profile_read(h):
     out = np.zeros(2)
     _check(lib().colatus_profile_read(h, out.ctypes.data), h)
     return float(out[0]), int(out[1])
+
+
+def colatus_forces_noalloc(pos, eps, G, a, acc_out, stream=None):
+    """Allocation-free force (see colatus.h): pos is a CUDA float32 tensor of
+    N x 4 (x, y, z, m), acc_out a CUDA float32 tensor of N x 3."""
+    for t, cols in ((pos, 4), (acc_out, 3)):
+        p, dev, dt, keep = _buf(t)
+        if not dev or dt != F32 or tuple(t.shape[1:]) != (cols,):
+            raise ValueError(f"expected a contiguous CUDA float32 tensor of N x {cols}")
+    st = lib().colatus_forces_noalloc(pos.data_ptr(), int(pos.shape[0]), float(eps), float(G),
+                                      float(a), acc_out.data_ptr(),
+                                      None if stream is None else int(stream))
+    if st != OK:
+        raise ColatusError(st, "colatus_forces_noalloc")
 
 
 def colatus_last_error(h=None):

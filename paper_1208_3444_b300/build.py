@@ -1,6 +1,7 @@
 """Build the sm_103a CUDA library ``libcolatus.so`` in-tree.
 
-``python -m paper_1208_3444_b300.build`` compiles ``csrc/colatus.cu`` with
+``python -m paper_1208_3444_b300.build`` compiles ``csrc/colatus.cu`` and
+``csrc/noalloc.cu`` with
 nvcc for ``sm_103a`` only (no PTX for other targets), the CUDA runtime linked
 statically, into ``paper_1208_3444_b300/libcolatus.so``.
 """
@@ -41,7 +42,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-Wno-deprecated-declarations", "-shared",
            "-cudart", "static", "-diag-suppress", "1444", "-I", INCLUDE, "-I", CSRC,
-           os.path.join(CSRC, "colatus.cu"), "-o", LIB + ".tmp"]
+           os.path.join(CSRC, "colatus.cu"), os.path.join(CSRC, "noalloc.cu"), "-o", LIB + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.check_call(cmd)
