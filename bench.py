@@ -220,6 +220,48 @@ def time_force_128(B, inputs, torch, launches=3):
             "interactions_per_s": ic.N * ic.N * n / (ms * 1e-3), "prec": "fp32"}
 
 
+def time_adjoint(B, inputs, torch, stream, nsteps=40, k=20):
+    """Adjoint vs forward step time on the 32^3 workload (FP32 compensated):
+    the backward per step without the checkpoint recomputation (one VJP + the
+    transposed update) over the forward step, and the total including it."""
+    ic = inputs.grid32()
+    tau = inputs.lcdm_tau(2000)
+    sim = B.Simulation(ic.m, ic.eps, LCDM, inputs.A_START, prec=B.FP32_COMP, scheme=B.KDK,
+                       stream=stream.cuda_stream)
+    try:
+        sim.set_state(ic.x, ic.v)
+        sim.step(tau, 3)
+        sim.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        sim.profile_forces(True)
+        ev[0].record(stream)
+        sim.adjoint_forward(tau, nsteps, k)
+        ev[1].record(stream)
+        gv = np.zeros((ic.N, 3))
+        gv[inputs.tracers(ic.N, 64, 7)] = 1.0
+        fwd = sim.profile_read_all()
+        ev[2].record(stream)
+        sim.adjoint_backward(None, gv)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        bwd = sim.profile_read_all()
+        sim.profile_forces(False)
+    finally:
+        sim.close()
+    f = ev[0].elapsed_time(ev[1]) / nsteps
+    b = ev[2].elapsed_time(ev[3]) / nsteps
+    rec = bwd["force"][0] / nsteps
+    vjp = bwd["vjp"][0] / bwd["vjp"][1]
+    return {"N": ic.N, "steps": nsteps, "checkpoint_every": k, "prec": "fp32_comp",
+            "forward_ms_per_step": f, "backward_ms_per_step": b,
+            "recompute_ms_per_step": rec, "vjp_ms_per_launch": vjp,
+            "force_ms_per_launch": fwd["force"][0] / fwd["force"][1],
+            "adjoint_step_over_forward_step": (b - rec) / f,
+            "backward_total_over_forward": b / f,
+            "vjp_interactions_per_sm_per_clk": ic.N * ic.N / (vjp * 1e-3) /
+            (torch.cuda.get_device_properties(0).multi_processor_count * 2.032e9)}
+
+
 def run_colatus(args, ws, rank, local):
     import torch
     from paper_1208_3444_b300 import binding as B
@@ -299,6 +341,7 @@ def run_colatus(args, ws, rank, local):
     force128 = None
     if not args.no_128:
         force128 = time_force_128(B, inputs, torch)
+    adjoint = time_adjoint(B, inputs, torch, stream)
     if rank == 0:
         peaks = {}
         try:
@@ -338,6 +381,7 @@ def run_colatus(args, ws, rank, local):
             "wall_s_timed_region": wall,
             "roofline": roof,
             "force_128cubed": force128,
+            "adjoint": adjoint,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,

@@ -155,10 +155,45 @@ colatus_status colatus_stats(colatus_t ctx, double out[4]);
  * stream (on = 0 stops and discards them). */
 colatus_status colatus_profile_forces(colatus_t ctx, int on);
 
-/* Total duration in milliseconds (out[0]) and number (out[1]) of the
- * force-kernel launches timed since the last read; synchronises the stream
- * and resets the totals. */
-colatus_status colatus_profile_read(colatus_t ctx, double out[2]);
+/* Durations since the last read, from the event pairs of
+ * colatus_profile_forces: out[0] total milliseconds and out[1] number of
+ * force-kernel launches, out[2] milliseconds and out[3] number of VJP-kernel
+ * launches.  Synchronises the stream and resets the totals. */
+colatus_status colatus_profile_read(colatus_t ctx, double out[4]);
+
+/* Vector-Jacobian product of the Eq. 1 acceleration at the current state:
+ * for a co-vector w (N x 3), gx = d(sum_k w_k . acc_k)/dx (N x 3) and
+ * gm = d(sum_k w_k . acc_k)/dm (N), with acc = G a^-3 F as in colatus_forces:
+ *     gx_i = G a^-3 sum_{j != i} J(d_ij) (m_i w_j - m_j w_i),
+ *     gm_i = -G a^-3 sum_{j != i} (w_j . d_ij) / s_ij^3,
+ * J(d) = I/s^3 - 3 d d^T/s^5 (the derivative of the Eq. 1 pair term).
+ * Either output may be NULL.  Same dtype / on_device conventions as
+ * colatus_forces (the precision is the context's). */
+colatus_status colatus_force_vjp(colatus_t ctx, const void *w, void *gx, void *gm, int dtype,
+                                 int on_device);
+
+/* Forward pass of the discrete adjoint (KDK only): advances the state by
+ * nsteps steps of size dt exactly as colatus_step does, keeping a checkpoint
+ * of (x, v) every checkpoint_every steps (device memory: nsteps /
+ * checkpoint_every checkpoints of N bodies, plus checkpoint_every positions
+ * for recomputation).  Errors: COLATUS_E_ARG (DKD scheme, sizes),
+ * COLATUS_E_STATE (no state). */
+colatus_status colatus_adjoint_forward(colatus_t ctx, double dt, int64_t nsteps,
+                                       int64_t checkpoint_every);
+
+/* Backward pass: given the gradient of a loss with respect to the final
+ * positions, velocities and masses (gx_T, gv_T: N x 3; gm_T: N; any may be
+ * NULL for zero), return its gradient with respect to the positions and
+ * velocities at the start of the forward pass and the masses (gx_0, gv_0:
+ * N x 3, gm: N; any may be NULL).  It is the exact transpose of the FP32 (or
+ * FP64) leapfrog that was run: each segment between checkpoints is
+ * recomputed with the forward's own kernels, then swept backwards with one
+ * VJP (colatus_force_vjp's kernel) per step.  The state (the forward's end)
+ * is left as it was.  Errors: COLATUS_E_STATE (no forward pass, or the state
+ * was stepped or reconfigured since). */
+colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const void *gv_T,
+                                        const void *gm_T, void *gx_0, void *gv_0, void *gm,
+                                        int dtype, int on_device);
 
 /* Allocation-free FP32 force, for callers that cannot call cudaMalloc (code
  * running inside another framework's memory pool or under a fixed

@@ -30,7 +30,8 @@ EXPORTS = ("colatus_init", "colatus_set_config", "colatus_set_masses", "colatus_
            "colatus_get_state", "colatus_forces", "colatus_step", "colatus_synchronize",
            "colatus_record_tracers", "colatus_read_tracers", "colatus_diagnostics",
            "colatus_last_error", "colatus_stats", "colatus_profile_forces",
-           "colatus_profile_read", "colatus_forces_noalloc", "colatus_destroy")
+           "colatus_profile_read", "colatus_force_vjp", "colatus_adjoint_forward",
+           "colatus_adjoint_backward", "colatus_forces_noalloc", "colatus_destroy")
 
 
 class ColatusError(RuntimeError):
@@ -68,6 +69,9 @@ def lib():
         "colatus_profile_forces": [_vp, _int],
         "colatus_profile_read": [_vp, _vp],
         "colatus_forces_noalloc": [_vp, _i64, _dbl, _dbl, _dbl, _vp, _vp],
+        "colatus_force_vjp": [_vp, _vp, _vp, _vp, _int, _int],
+        "colatus_adjoint_forward": [_vp, _dbl, _i64, _i64],
+        "colatus_adjoint_backward": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _int, _int],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -205,11 +209,56 @@ def colatus_profile_forces(h, on):
     _check(lib().colatus_profile_forces(h, int(on)), h)
 
 
-def colatus_profile_read(h):
-    """(total force-kernel milliseconds, launches) since the last read."""
-    out = np.zeros(2)
+def colatus_profile_read(h, vjp=False):
+    """(milliseconds, launches) of the force kernel (or of the VJP kernel with
+    vjp=True) since the last read; a read resets both totals."""
+    out = np.zeros(4)
     _check(lib().colatus_profile_read(h, out.ctypes.data), h)
-    return float(out[0]), int(out[1])
+    k = 2 if vjp else 0
+    return float(out[k]), int(out[k + 1])
+
+
+def colatus_profile_read_all(h):
+    """{'force': (ms, launches), 'vjp': (ms, launches)} since the last read."""
+    out = np.zeros(4)
+    _check(lib().colatus_profile_read(h, out.ctypes.data), h)
+    return {"force": (float(out[0]), int(out[1])), "vjp": (float(out[2]), int(out[3]))}
+
+
+def _same(*arrs):
+    bufs = [_buf(a) for a in arrs if a is not None]
+    if not bufs:
+        return 0, F64, []
+    devs = {b[1] for b in bufs}
+    dts = {b[2] for b in bufs}
+    if len(devs) != 1 or len(dts) != 1:
+        raise ValueError("arrays must share device and dtype")
+    return bufs[0][1], bufs[0][2], bufs
+
+
+def _ptr_or_none(a, bufs, k):
+    return None if a is None else bufs[k][0]
+
+
+def colatus_force_vjp(h, w, gx=None, gm=None):
+    dev, dt, bufs = _same(w, gx, gm)
+    ptrs = iter(b[0] for b in bufs)
+    pw = next(ptrs)
+    pgx = next(ptrs) if gx is not None else None
+    pgm = next(ptrs) if gm is not None else None
+    _check(lib().colatus_force_vjp(h, pw, pgx, pgm, dt, dev), h)
+
+
+def colatus_adjoint_forward(h, dt, nsteps, checkpoint_every):
+    _check(lib().colatus_adjoint_forward(h, float(dt), int(nsteps), int(checkpoint_every)), h)
+
+
+def colatus_adjoint_backward(h, gx_T=None, gv_T=None, gm_T=None, gx_0=None, gv_0=None, gm=None):
+    arrs = (gx_T, gv_T, gm_T, gx_0, gv_0, gm)
+    dev, dt, bufs = _same(*arrs)
+    it = iter(b[0] for b in bufs)
+    ptrs = [None if a is None else next(it) for a in arrs]
+    _check(lib().colatus_adjoint_backward(h, *ptrs, dt, dev), h)
 
 
 def colatus_forces_noalloc(pos, eps, G, a, acc_out, stream=None):
@@ -299,8 +348,28 @@ class Simulation:
     def profile_forces(self, on=True):
         colatus_profile_forces(self.h, on)
 
-    def profile_read(self):
-        return colatus_profile_read(self.h)
+    def profile_read(self, vjp=False):
+        return colatus_profile_read(self.h, vjp)
+
+    def profile_read_all(self):
+        return colatus_profile_read_all(self.h)
+
+    def force_vjp(self, w, dtype=np.float64):
+        gx = np.empty((self.N, 3), dtype=dtype)
+        gm = np.empty(self.N, dtype=dtype)
+        colatus_force_vjp(self.h, np.asarray(w, dtype=dtype), gx, gm)
+        return gx, gm
+
+    def adjoint_forward(self, dt, nsteps, checkpoint_every):
+        colatus_adjoint_forward(self.h, dt, nsteps, checkpoint_every)
+
+    def adjoint_backward(self, gx_T=None, gv_T=None, gm_T=None, dtype=np.float64):
+        gx = np.empty((self.N, 3), dtype=dtype)
+        gv = np.empty((self.N, 3), dtype=dtype)
+        gm = np.empty(self.N, dtype=dtype)
+        cast = (lambda a: None if a is None else np.ascontiguousarray(a, dtype=dtype))
+        colatus_adjoint_backward(self.h, cast(gx_T), cast(gv_T), cast(gm_T), gx, gv, gm)
+        return gx, gv, gm
 
     def close(self):
         if self.h:

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <vector>
 
+#include "adjoint.cuh"
 #include "colatus.h"
 #include "common.cuh"
 #include "diagnostics.cuh"
@@ -69,6 +70,12 @@ const F32Variant &f32_variant(int v) {
 
 constexpr int kF64NT = 128, kF64IPT = 2, kF64JT = 64;
 using F64K = F64Kernel<kF64NT, kF64IPT, kF64JT, kStages>;
+
+// VJP kernels: FP32 256 threads x 2 i-bodies, 256-body j-tiles; FP64 128 x 1, 32-body tiles
+constexpr int kVjpNT = 256, kVjpIPT = 2, kVjpJT = 256, kVjpMINB = 2;
+using VjpK = VjpKernel<kVjpNT, kVjpIPT, kVjpJT, kStages>;
+constexpr int kV64NT = 128, kV64JT = 32;
+using Vjp64K = Vjp64Kernel<kV64NT, kV64JT, kStages>;
 
 constexpr long long kPadAlloc = 1024;   // buffers hold N rounded up to this
 constexpr int kChunk = 1024;            // steps enqueued per chunk of colatus_step
@@ -175,10 +182,30 @@ struct colatus_ctx {
 
     ForcePlan plan32[NUM_F32_VARIANTS];
     ForcePlan plan64;
+    ForcePlan plan_vjp32, plan_vjp64;
+
+    // discrete adjoint (colatus_adjoint_forward / colatus_adjoint_backward)
+    struct Adjoint {
+        bool ready = false;
+        long long nsteps = 0, step0 = 0;
+        int k = 0, nck = 0;
+        double tau = 0.0;
+        colatus_prec prec = COLATUS_FP32;
+        size_t ck_bytes = 0, seg_bytes = 0, tab_bytes = 0;
+        void *ck_x = nullptr, *ck_v = nullptr;   // [nck][n_alloc] checkpoints (float4 / double4)
+        void *seg_x = nullptr;                   // [k][n_alloc] recomputed positions
+        StepCoef *table = nullptr;               // [nsteps] schedule of the forward
+        DevClock *rclk = nullptr;                // scratch clock
+        void *rvs = nullptr, *rvh = nullptr, *racc = nullptr;   // recompute state
+        void *rpk[2] = {nullptr, nullptr};       // recompute force inputs
+        void *lx = nullptr, *lv = nullptr, *lvh = nullptr, *lm = nullptr;   // adjoint variables
+        void *pkw = nullptr;                     // bodies + co-vector for the VJP
+    } adj;
 
     // force-kernel timing (colatus_profile_forces)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_cat;      // category of each event pair: 0 force, 1 VJP
     size_t ev_used = 0;
 
     char err[512] = {0};
@@ -258,6 +285,25 @@ colatus_status build_plans(colatus_t ctx) {
     p.n_pad = round_up(ctx->N, std::max(p.itile, p.jt));
     p.L = make_launch(p.n_pad, p.itile, p.jt, (long long)occ * ctx->num_sms);
     p.part_bytes = (size_t)p.L.n_it * p.L.S_max * p.itile * sizeof(double4);
+
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, vjp_f32_kernel<kVjpNT, kVjpIPT, kVjpJT, kStages, kVjpMINB>, kVjpNT, VjpK::SMEM));
+    if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "VJP kernel cannot be resident");
+    ForcePlan &v = ctx->plan_vjp32;
+    v.itile = VjpK::ITILE;
+    v.jt = kVjpJT;
+    v.n_pad = round_up(ctx->N, std::max(v.itile, v.jt));
+    v.L = make_launch(v.n_pad, v.itile, v.jt, (long long)occ * ctx->num_sms);
+    v.part_bytes = (size_t)v.L.n_it * v.L.S_max * v.itile * sizeof(float4);
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, vjp_f64_kernel<kV64NT, kV64JT, kStages>, kV64NT, Vjp64K::SMEM));
+    if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "FP64 VJP kernel cannot be resident");
+    ForcePlan &w = ctx->plan_vjp64;
+    w.itile = Vjp64K::ITILE;
+    w.jt = kV64JT;
+    w.n_pad = round_up(ctx->N, std::max(w.itile, w.jt));
+    w.L = make_launch(w.n_pad, w.itile, w.jt, (long long)occ * ctx->num_sms);
+    w.part_bytes = (size_t)w.L.n_it * w.L.S_max * w.itile * sizeof(double4);
     return COLATUS_OK;
 }
 
@@ -283,21 +329,24 @@ colatus_status ensure_part(colatus_t ctx, size_t bytes) {
     return COLATUS_OK;
 }
 
-// Bracket one force launch with a pair of events when profiling.
+// Bracket one force (cat 0) or VJP (cat 1) launch with a pair of events
+// when profiling.
 colatus_status prof_begin(colatus_t ctx) {
     if (!ctx->profiling) return COLATUS_OK;
     while (ctx->ev_pool.size() < ctx->ev_used + 2) {
         cudaEvent_t e;
         CU(cudaEventCreate(&e));
         ctx->ev_pool.push_back(e);
+        ctx->ev_cat.push_back(0);
     }
     CU(cudaEventRecord(ctx->ev_pool[ctx->ev_used], ctx->stream));
     return COLATUS_OK;
 }
 
-colatus_status prof_end(colatus_t ctx) {
+colatus_status prof_end(colatus_t ctx, int cat = 0) {
     if (!ctx->profiling) return COLATUS_OK;
     CU(cudaEventRecord(ctx->ev_pool[ctx->ev_used + 1], ctx->stream));
+    ctx->ev_cat[ctx->ev_used] = cat;
     ctx->ev_used += 2;
     return COLATUS_OK;
 }
@@ -437,6 +486,11 @@ void free_all(colatus_t ctx) {
                     ctx->rec};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    void *aptrs[] = {ctx->adj.ck_x, ctx->adj.ck_v, ctx->adj.seg_x, ctx->adj.table, ctx->adj.rclk,
+                     ctx->adj.rvs, ctx->adj.rvh, ctx->adj.racc, ctx->adj.rpk[0], ctx->adj.rpk[1],
+                     ctx->adj.lx, ctx->adj.lv, ctx->adj.lvh, ctx->adj.lm, ctx->adj.pkw};
+    for (void *p : aptrs)
+        if (p) cudaFree(p);
     for (cudaEvent_t e : ctx->tab_ev)
         if (e) cudaEventDestroy(e);
     if (ctx->main_ev) cudaEventDestroy(ctx->main_ev);
@@ -566,6 +620,92 @@ Tracers tracer_args(colatus_t ctx) {
     return t;
 }
 
+// Explicit buffers of one KDK/DKD trajectory: the context's own, or the
+// scratch of an adjoint recomputation.
+struct StepBufs {
+    float4 *xs, *vs, *vh, *acc;
+    float *pk[2];
+    double4 *xs64, *vs64, *vh64, *acc64;
+    double4 *pos64[2];
+    const StepCoef *table;
+    int tcap;
+    DevClock *clk;
+    Tracers tr;
+};
+
+StepBufs ctx_bufs(colatus_t ctx) {
+    StepBufs b;
+    b.xs = ctx->xs; b.vs = ctx->vs; b.vh = ctx->vh; b.acc = ctx->acc;
+    b.pk[0] = ctx->pk[0]; b.pk[1] = ctx->pk[1];
+    b.xs64 = ctx->xs64; b.vs64 = ctx->vs64; b.vh64 = ctx->vh64; b.acc64 = ctx->acc64;
+    b.pos64[0] = ctx->pos64[0]; b.pos64[1] = ctx->pos64[1];
+    b.table = ctx->table;
+    b.tcap = kTabCap;
+    b.clk = ctx->clk;
+    b.tr = tracer_args(ctx);
+    return b;
+}
+
+// KDK opening (half kick + drift) from (xs, vs) with F = acc into pk[c].
+colatus_status launch_kdk_open(colatus_t ctx, const StepBufs &b, int c, long long step, double tau) {
+    if (ctx->prec == COLATUS_FP64) {
+        const ForcePlan &p = ctx->plan64;
+        kdk_open_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+            b.xs64, b.vs64, b.acc64, b.vh64, b.pos64[c], b.table, b.tcap, step, tau, ctx->N, p.n_pad);
+    } else {
+        const ForcePlan &p = plan_f32(ctx);
+        kdk_open_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+            b.xs, b.vs, b.acc, b.vh, b.pk[c], b.table, b.tcap, step, tau, ctx->N, p.n_pad);
+    }
+    return launched(ctx);
+}
+
+// One step: force on pk[c], then the fused epilogue that writes the state
+// (xs, vs), the next force input pk[c ^ 1] and, for KDK, vh and acc.
+colatus_status launch_step(colatus_t ctx, const StepBufs &b, int c, long long step, double tau) {
+    const int n = c ^ 1;
+    const Tracers &tr = b.tr;
+    if (ctx->prec == COLATUS_FP64) {
+        const ForcePlan &p = ctx->plan64;
+        TRY(run_force_f64(ctx, b.pos64[c]));
+        const double4 *part = static_cast<const double4 *>(ctx->part);
+        if (ctx->scheme == COLATUS_KDK)
+            kdk_step_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+                part, p.L, p.itile, b.pos64[c], b.xs64, b.vs64, b.vh64, b.acc64, b.pos64[n], b.table,
+                b.tcap, step, tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk);
+        else
+            dkd_step_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+                part, p.L, p.itile, b.pos64[c], b.xs64, b.vs64, b.acc64, b.pos64[n], b.table, b.tcap,
+                step, tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk);
+    } else {
+        const ForcePlan &p = plan_f32(ctx);
+        TRY(run_force_f32(ctx, p, b.pk[c]));
+        const float4 *part = static_cast<const float4 *>(ctx->part);
+        const bool comp = ctx->prec == COLATUS_FP32_COMP;
+        const unsigned nb = blocks_for(p.n_pad, 256);
+        if (ctx->scheme == COLATUS_KDK) {
+            if (comp)
+                kdk_step_f32_kernel<true><<<nb, 256, 0, ctx->stream>>>(
+                    part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.vh, b.acc, b.pk[n], b.table, b.tcap,
+                    step, tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk);
+            else
+                kdk_step_f32_kernel<false><<<nb, 256, 0, ctx->stream>>>(
+                    part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.vh, b.acc, b.pk[n], b.table, b.tcap,
+                    step, tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk);
+        } else {
+            if (comp)
+                dkd_step_f32_kernel<true><<<nb, 256, 0, ctx->stream>>>(
+                    part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.acc, b.pk[n], b.table, b.tcap, step,
+                    tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk);
+            else
+                dkd_step_f32_kernel<false><<<nb, 256, 0, ctx->stream>>>(
+                    part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.acc, b.pk[n], b.table, b.tcap, step,
+                    tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk);
+        }
+    }
+    return launched(ctx);
+}
+
 // Opening of the first step of a call: the KDK half kick + drift, or the
 // DKD half drift, from the state into the force input pk[cur].
 colatus_status open_step(colatus_t ctx, double tau) {
@@ -576,77 +716,78 @@ colatus_status open_step(colatus_t ctx, double tau) {
             TRY(force_output(ctx, nullptr, 0, true));
             ctx->acc_valid = true;
         }
-        if (f64) {
-            const ForcePlan &p = ctx->plan64;
-            kdk_open_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
-                ctx->xs64, ctx->vs64, ctx->acc64, ctx->vh64, ctx->pos64[ctx->cur], ctx->table, kTabCap,
-                ctx->host_step, tau, ctx->N, p.n_pad);
-        } else {
-            const ForcePlan &p = plan_f32(ctx);
-            kdk_open_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
-                ctx->xs, ctx->vs, ctx->acc, ctx->vh, ctx->pk[ctx->cur], ctx->table, kTabCap, ctx->host_step,
-                tau, ctx->N, p.n_pad);
-        }
+        return launch_kdk_open(ctx, ctx_bufs(ctx), ctx->cur, ctx->host_step, tau);
+    }
+    if (f64) {
+        const ForcePlan &p = ctx->plan64;
+        dkd_open_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+            ctx->xs64, ctx->vs64, ctx->pos64[ctx->cur], tau, ctx->N, p.n_pad);
     } else {
-        if (f64) {
-            const ForcePlan &p = ctx->plan64;
-            dkd_open_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
-                ctx->xs64, ctx->vs64, ctx->pos64[ctx->cur], tau, ctx->N, p.n_pad);
-        } else {
-            const ForcePlan &p = plan_f32(ctx);
-            dkd_open_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
-                ctx->xs, ctx->vs, ctx->pk[ctx->cur], tau, ctx->N, p.n_pad);
-        }
+        const ForcePlan &p = plan_f32(ctx);
+        dkd_open_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+            ctx->xs, ctx->vs, ctx->pk[ctx->cur], tau, ctx->N, p.n_pad);
     }
     return launched(ctx);
 }
 
-// One step j of the current chunk: force on pk[cur], then the fused epilogue
-// that writes the state and the next force input pk[cur ^ 1].
+// One step j of the current chunk on the context's own buffers.
 colatus_status one_step(colatus_t ctx, int j, double tau) {
-    const Tracers tr = tracer_args(ctx);
-    const int c = ctx->cur, n = c ^ 1;
-    if (ctx->prec == COLATUS_FP64) {
-        const ForcePlan &p = ctx->plan64;
-        TRY(run_force_f64(ctx, ctx->pos64[c]));
-        const double4 *part = static_cast<const double4 *>(ctx->part);
-        if (ctx->scheme == COLATUS_KDK)
-            kdk_step_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
-                part, p.L, p.itile, ctx->pos64[c], ctx->xs64, ctx->vs64, ctx->vh64, ctx->acc64,
-                ctx->pos64[n], ctx->table, kTabCap, ctx->host_step + j, tau, ctx->N, p.n_pad, tr, ctx->flags, ctx->clk);
-        else
-            dkd_step_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
-                part, p.L, p.itile, ctx->pos64[c], ctx->xs64, ctx->vs64, ctx->acc64, ctx->pos64[n],
-                ctx->table, kTabCap, ctx->host_step + j, tau, ctx->N, p.n_pad, tr, ctx->flags, ctx->clk);
-    } else {
-        const ForcePlan &p = plan_f32(ctx);
-        TRY(run_force_f32(ctx, p, ctx->pk[c]));
-        const float4 *part = static_cast<const float4 *>(ctx->part);
-        const bool comp = ctx->prec == COLATUS_FP32_COMP;
-        const unsigned nb = blocks_for(p.n_pad, 256);
-        if (ctx->scheme == COLATUS_KDK) {
-            if (comp)
-                kdk_step_f32_kernel<true><<<nb, 256, 0, ctx->stream>>>(
-                    part, p.L, p.itile, ctx->pk[c], ctx->xs, ctx->vs, ctx->vh, ctx->acc, ctx->pk[n],
-                    ctx->table, kTabCap, ctx->host_step + j, tau, ctx->N, p.n_pad, tr, ctx->flags, ctx->clk);
-            else
-                kdk_step_f32_kernel<false><<<nb, 256, 0, ctx->stream>>>(
-                    part, p.L, p.itile, ctx->pk[c], ctx->xs, ctx->vs, ctx->vh, ctx->acc, ctx->pk[n],
-                    ctx->table, kTabCap, ctx->host_step + j, tau, ctx->N, p.n_pad, tr, ctx->flags, ctx->clk);
-        } else {
-            if (comp)
-                dkd_step_f32_kernel<true><<<nb, 256, 0, ctx->stream>>>(
-                    part, p.L, p.itile, ctx->pk[c], ctx->xs, ctx->vs, ctx->acc, ctx->pk[n],
-                    ctx->table, kTabCap, ctx->host_step + j, tau, ctx->N, p.n_pad, tr, ctx->flags, ctx->clk);
-            else
-                dkd_step_f32_kernel<false><<<nb, 256, 0, ctx->stream>>>(
-                    part, p.L, p.itile, ctx->pk[c], ctx->xs, ctx->vs, ctx->acc, ctx->pk[n],
-                    ctx->table, kTabCap, ctx->host_step + j, tau, ctx->N, p.n_pad, tr, ctx->flags, ctx->clk);
-        }
-    }
-    TRY(launched(ctx));
-    ctx->cur = n;
+    TRY(launch_step(ctx, ctx_bufs(ctx), ctx->cur, ctx->host_step + j, tau));
+    ctx->cur ^= 1;
     return COLATUS_OK;
+}
+
+
+// ------------------------------------------------------------------ adjoint
+// Allocate the fixed-size adjoint buffers (first use only).
+colatus_status adj_alloc(colatus_t ctx) {
+    auto &a = ctx->adj;
+    if (a.pkw) return COLATUS_OK;
+    const size_t na = (size_t)ctx->n_alloc;
+    void **bufs32[] = {&a.rvs, &a.rvh, &a.racc, &a.rpk[0], &a.rpk[1], &a.lx, &a.lv, &a.lvh};
+    for (void **b : bufs32) CU(cudaMalloc(b, na * 32));
+    CU(cudaMalloc(&a.lm, na * 8));
+    CU(cudaMalloc(&a.rclk, sizeof(DevClock)));
+    CU(cudaMalloc(&a.pkw, na * 64));
+    return COLATUS_OK;
+}
+
+colatus_status grow(colatus_t ctx, void **p, size_t *have, size_t need) {
+    if (need <= *have) return COLATUS_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+    CU(cudaMalloc(p, need));
+    *have = need;
+    return COLATUS_OK;
+}
+
+// One VJP launch on the packed bodies + co-vectors in adj.pkw.
+colatus_status run_vjp(colatus_t ctx) {
+    const bool f64 = ctx->prec == COLATUS_FP64;
+    const ForcePlan &p = f64 ? ctx->plan_vjp64 : ctx->plan_vjp32;
+    TRY(ensure_part(ctx, p.part_bytes));
+    TRY(prof_begin(ctx));
+    if (f64)
+        vjp_f64_kernel<kV64NT, kV64JT, kStages><<<p.L.G, kV64NT, Vjp64K::SMEM, ctx->stream>>>(
+            static_cast<const double4 *>(ctx->adj.pkw), static_cast<double4 *>(ctx->part),
+            ctx->flags, p.L, ctx->eps * ctx->eps);
+    else
+        vjp_f32_kernel<kVjpNT, kVjpIPT, kVjpJT, kStages, kVjpMINB>
+            <<<p.L.G, kVjpNT, VjpK::SMEM, ctx->stream>>>(
+                static_cast<const float *>(ctx->adj.pkw), static_cast<float4 *>(ctx->part),
+                ctx->flags, p.L, (float)(ctx->eps * ctx->eps));
+    TRY(launched(ctx));
+    ctx->interactions += (double)ctx->N * (double)ctx->N;
+    return prof_end(ctx, 1);
+}
+
+// N x 3 vectors (dtype, device) -> float4 / double4 per body.
+template <typename T4, typename T>
+__global__ void vec3_to4_kernel(const void *src, int f64, long long N, T4 *dst) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    dst[i] = load3<T4, T>(src, f64, i);
 }
 
 }  // namespace
@@ -1019,19 +1160,290 @@ colatus_status colatus_profile_forces(colatus_t ctx, int on) {
     return COLATUS_OK;
 }
 
-colatus_status colatus_profile_read(colatus_t ctx, double out[2]) {
+colatus_status colatus_profile_read(colatus_t ctx, double out[4]) {
     if (!ctx || !out) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
     CU(cudaStreamSynchronize(ctx->stream));
-    double ms = 0.0;
+    for (int k = 0; k < 4; ++k) out[k] = 0.0;
     for (size_t k = 0; k + 1 < ctx->ev_used; k += 2) {
         float e = 0.f;
         CU(cudaEventElapsedTime(&e, ctx->ev_pool[k], ctx->ev_pool[k + 1]));
-        ms += e;
+        const int c = ctx->ev_cat[k] ? 2 : 0;
+        out[c] += e;
+        out[c + 1] += 1.0;
     }
-    out[0] = ms;
-    out[1] = (double)(ctx->ev_used / 2);
     ctx->ev_used = 0;
+    return COLATUS_OK;
+}
+
+
+colatus_status colatus_force_vjp(colatus_t ctx, const void *w, void *gx, void *gm, int dtype,
+                                 int on_device) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    TRY(check_dtype(ctx, dtype));
+    if (!w || (!gx && !gm)) return fail(ctx, COLATUS_E_ARG, "need w and at least one output");
+    if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
+    TRY(adj_alloc(ctx));
+    const int f64in = dtype == COLATUS_F64;
+    const size_t vbytes = (size_t)ctx->N * 3 * elem_size(dtype);
+    const void *src = w;
+    if (!on_device) {
+        CU(cudaMemcpyAsync(ctx->stage, w, vbytes, cudaMemcpyHostToDevice, ctx->stream));
+        src = ctx->stage;
+    }
+    const unsigned nb = blocks_for(ctx->N, 256);
+    void *dgx = on_device ? gx : (gx ? (void *)ctx->stage : nullptr);
+    void *dgm = on_device ? gm : (gm ? (void *)ctx->stage2 : nullptr);
+    if (ctx->prec == COLATUS_FP64) {
+        const ForcePlan &p = ctx->plan_vjp64;
+        vec3_to4_kernel<double4, double><<<nb, 256, 0, ctx->stream>>>(
+            src, f64in, ctx->N, static_cast<double4 *>(ctx->adj.lx));
+        TRY(launched(ctx));
+        vjp_pack_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+            ctx->xs64, static_cast<const double4 *>(ctx->adj.lx), ctx->clk, ctx->G, 1,
+            static_cast<double4 *>(ctx->adj.pkw), ctx->N, p.n_pad);
+        TRY(launched(ctx));
+        TRY(run_vjp(ctx));
+        vjp_out_f64_kernel<<<nb, 256, 0, ctx->stream>>>(static_cast<const double4 *>(ctx->part), p.L,
+                                                        p.itile, ctx->N, dgx, dgm, f64in);
+    } else {
+        const ForcePlan &p = ctx->plan_vjp32;
+        vec3_to4_kernel<float4, float><<<nb, 256, 0, ctx->stream>>>(
+            src, f64in, ctx->N, static_cast<float4 *>(ctx->adj.lx));
+        TRY(launched(ctx));
+        vjp_pack_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+            ctx->xs, static_cast<const float4 *>(ctx->adj.lx), ctx->clk, ctx->G, 1,
+            static_cast<float *>(ctx->adj.pkw), ctx->N, p.n_pad);
+        TRY(launched(ctx));
+        TRY(run_vjp(ctx));
+        vjp_out_f32_kernel<<<nb, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part), p.L,
+                                                        p.itile, ctx->N, dgx, dgm, f64in);
+    }
+    TRY(launched(ctx));
+    if (!on_device) {
+        if (gx) CU(cudaMemcpyAsync(gx, ctx->stage, vbytes, cudaMemcpyDeviceToHost, ctx->stream));
+        if (gm)
+            CU(cudaMemcpyAsync(gm, ctx->stage2, (size_t)ctx->N * elem_size(dtype),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+        TRY(sync_and_check(ctx));
+    }
+    return COLATUS_OK;
+}
+
+colatus_status colatus_adjoint_forward(colatus_t ctx, double dt, int64_t nsteps,
+                                       int64_t checkpoint_every) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, COLATUS_E_ARG, "dt must be finite and > 0");
+    if (nsteps < 1 || checkpoint_every < 1)
+        return fail(ctx, COLATUS_E_ARG, "nsteps and checkpoint_every must be >= 1");
+    if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
+    if (ctx->scheme != COLATUS_KDK)
+        return fail(ctx, COLATUS_E_ARG, "the adjoint is built for the KDK scheme");
+    auto &a = ctx->adj;
+    a.ready = false;
+    TRY(adj_alloc(ctx));
+    const int k = (int)std::min<int64_t>(checkpoint_every, nsteps);
+    const int nck = (int)((nsteps + k - 1) / k);
+    const size_t body = ctx->prec == COLATUS_FP64 ? sizeof(double4) : sizeof(float4);
+    const size_t plane = (size_t)ctx->n_alloc * body;
+    if (a.ck_bytes < nck * plane) {
+        if (a.ck_x) cudaFree(a.ck_x);
+        if (a.ck_v) cudaFree(a.ck_v);
+        a.ck_x = a.ck_v = nullptr;
+        a.ck_bytes = 0;
+        CU(cudaMalloc(&a.ck_x, nck * plane));
+        CU(cudaMalloc(&a.ck_v, nck * plane));
+        a.ck_bytes = nck * plane;
+    }
+    TRY(grow(ctx, &a.seg_x, &a.seg_bytes, (size_t)k * plane));
+    TRY(grow(ctx, reinterpret_cast<void **>(&a.table), &a.tab_bytes, (size_t)nsteps * sizeof(StepCoef)));
+    // the forward's schedule, computed from the current clock exactly as the
+    // look-ahead schedule is (same kernel, same start): bitwise the same values
+    clock_copy_kernel<<<1, 1, 0, ctx->stream>>>(ctx->clk, a.rclk);
+    TRY(launched(ctx));
+    // index the forward's schedule by step within the pass (0 .. nsteps-1)
+    CU(cudaMemsetAsync(&a.rclk->step, 0, sizeof(a.rclk->step), ctx->stream));
+    friedmann_table_kernel<<<1, 1, 0, ctx->stream>>>(ctx->cosmo, a.rclk, a.table, (int)nsteps,
+                                                     (int)nsteps, dt, ctx->G, kFriedmannSub);
+    TRY(launched(ctx));
+    const long long step0 = ctx->host_step;
+    const bool f64 = ctx->prec == COLATUS_FP64;
+    for (int c = 0; c < nck; ++c) {
+        char *cx = static_cast<char *>(a.ck_x) + c * plane;
+        char *cv = static_cast<char *>(a.ck_v) + c * plane;
+        CU(cudaMemcpyAsync(cx, f64 ? (void *)ctx->xs64 : (void *)ctx->xs, (size_t)ctx->N * body,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(cv, f64 ? (void *)ctx->vs64 : (void *)ctx->vs, (size_t)ctx->N * body,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+        TRY(colatus_step(ctx, dt, std::min<int64_t>(k, nsteps - (int64_t)c * k)));
+    }
+    a.ready = true;
+    a.nsteps = nsteps;
+    a.step0 = step0;
+    a.k = k;
+    a.nck = nck;
+    a.tau = dt;
+    a.prec = ctx->prec;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const void *gv_T,
+                                        const void *gm_T, void *gx_0, void *gv_0, void *gm,
+                                        int dtype, int on_device) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    TRY(check_dtype(ctx, dtype));
+    auto &a = ctx->adj;
+    if (!a.ready) return fail(ctx, COLATUS_E_STATE, "no adjoint forward pass recorded");
+    if (ctx->host_step != a.step0 + a.nsteps || ctx->prec != a.prec)
+        return fail(ctx, COLATUS_E_STATE, "the state moved on since the adjoint forward pass");
+    const bool f64 = ctx->prec == COLATUS_FP64;
+    const int in64 = dtype == COLATUS_F64;
+    const size_t vbytes = (size_t)ctx->N * 3 * elem_size(dtype);
+    const size_t sbytes = (size_t)ctx->N * elem_size(dtype);
+    const void *sx = gx_T, *sv = gv_T, *sm = gm_T;
+    if (!on_device) {
+        if (gx_T) {
+            CU(cudaMemcpyAsync(ctx->stage, gx_T, vbytes, cudaMemcpyHostToDevice, ctx->stream));
+            sx = ctx->stage;
+        }
+        if (gv_T) {
+            CU(cudaMemcpyAsync(ctx->stage2, gv_T, vbytes, cudaMemcpyHostToDevice, ctx->stream));
+            sv = ctx->stage2;
+        }
+        if (gm_T) {
+            CU(cudaMemcpyAsync(a.rvs, gm_T, sbytes, cudaMemcpyHostToDevice, ctx->stream));
+            sm = a.rvs;
+        }
+    }
+    const size_t body = f64 ? sizeof(double4) : sizeof(float4);
+    const size_t plane = (size_t)ctx->n_alloc * body;
+    const ForcePlan &pv = f64 ? ctx->plan_vjp64 : ctx->plan_vjp32;
+    const long long NS = a.nsteps;
+    const unsigned nbv = blocks_for(pv.n_pad, 256);
+    if (f64)
+        adj_init_f64_kernel<<<nbv, 256, 0, ctx->stream>>>(
+            sx, sv, sm, in64, ctx->xs64, static_cast<double4 *>(a.lx), static_cast<double4 *>(a.lv),
+            static_cast<double *>(a.lm), a.table, NS - 1, static_cast<double4 *>(a.pkw), ctx->N, pv.n_pad);
+    else
+        adj_init_f32_kernel<<<nbv, 256, 0, ctx->stream>>>(
+            sx, sv, sm, in64, ctx->xs, static_cast<float4 *>(a.lx), static_cast<float4 *>(a.lv),
+            static_cast<float *>(a.lm), a.table, NS - 1, static_cast<float *>(a.pkw), ctx->N, pv.n_pad);
+    TRY(launched(ctx));
+
+    for (int c = a.nck - 1; c >= 0; --c) {
+        const long long s0 = (long long)c * a.k, s1 = std::min<long long>(s0 + a.k, NS);
+        char *ckx = static_cast<char *>(a.ck_x) + c * plane;
+        char *ckv = static_cast<char *>(a.ck_v) + c * plane;
+        auto pos = [&](long long n) -> void * {
+            return n == s0 ? (void *)ckx : (void *)(static_cast<char *>(a.seg_x) + (n - s0) * plane);
+        };
+        if (s1 - s0 > 1) {
+            // recompute x_{s0+1} .. x_{s1-1} with the forward's own kernels
+            StepBufs b;
+            b.xs = reinterpret_cast<float4 *>(ckx);
+            b.vs = reinterpret_cast<float4 *>(ckv);
+            b.vh = static_cast<float4 *>(a.rvh);
+            b.acc = static_cast<float4 *>(a.racc);
+            b.pk[0] = static_cast<float *>(a.rpk[0]);
+            b.pk[1] = static_cast<float *>(a.rpk[1]);
+            b.xs64 = reinterpret_cast<double4 *>(ckx);
+            b.vs64 = reinterpret_cast<double4 *>(ckv);
+            b.vh64 = static_cast<double4 *>(a.rvh);
+            b.acc64 = static_cast<double4 *>(a.racc);
+            b.pos64[0] = static_cast<double4 *>(a.rpk[0]);
+            b.pos64[1] = static_cast<double4 *>(a.rpk[1]);
+            b.table = a.table;
+            b.tcap = (int)NS;
+            b.clk = a.rclk;
+            b.tr = Tracers{nullptr, nullptr, 1, 0, 0};
+            // F at the checkpoint
+            if (f64) {
+                const ForcePlan &p = ctx->plan64;
+                pack_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+                    b.xs64, b.pos64[0], ctx->N, p.n_pad);
+                TRY(launched(ctx));
+                TRY(run_force_f64(ctx, b.pos64[0]));
+                forces_out_f64_kernel<<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
+                    static_cast<const double4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk, ctx->G,
+                    nullptr, 0, b.acc64);
+            } else {
+                const ForcePlan &p = plan_f32(ctx);
+                pack_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+                    b.xs, b.pk[0], ctx->N, p.n_pad);
+                TRY(launched(ctx));
+                TRY(run_force_f32(ctx, p, b.pk[0]));
+                if (ctx->prec == COLATUS_FP32_COMP)
+                    forces_out_f32_kernel<true><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
+                        static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk,
+                        ctx->G, nullptr, 0, b.acc);
+                else
+                    forces_out_f32_kernel<false><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
+                        static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk,
+                        ctx->G, nullptr, 0, b.acc);
+            }
+            TRY(launched(ctx));
+            TRY(launch_kdk_open(ctx, b, 1, s0, a.tau));
+            int cur = 1;
+            b.vs = static_cast<float4 *>(a.rvs);
+            b.vs64 = static_cast<double4 *>(a.rvs);
+            for (long long n = s0; n < s1 - 1; ++n) {
+                b.xs = static_cast<float4 *>(pos(n + 1));
+                b.xs64 = static_cast<double4 *>(pos(n + 1));
+                TRY(launch_step(ctx, b, cur, n, a.tau));
+                cur ^= 1;
+            }
+        }
+        for (long long n = s1 - 1; n >= s0; --n) {
+            TRY(run_vjp(ctx));
+            if (f64)
+                adj_step_f64_kernel<<<nbv, 256, 0, ctx->stream>>>(
+                    static_cast<const double4 *>(ctx->part), pv.L, pv.itile,
+                    static_cast<const double4 *>(pos(n)), static_cast<double4 *>(a.lx),
+                    static_cast<double4 *>(a.lv), static_cast<double4 *>(a.lvh),
+                    static_cast<double *>(a.lm), a.table, n, a.tau, static_cast<double4 *>(a.pkw),
+                    ctx->N, pv.n_pad);
+            else
+                adj_step_f32_kernel<<<nbv, 256, 0, ctx->stream>>>(
+                    static_cast<const float4 *>(ctx->part), pv.L, pv.itile,
+                    static_cast<const float4 *>(pos(n)), static_cast<float4 *>(a.lx),
+                    static_cast<float4 *>(a.lv), static_cast<float4 *>(a.lvh),
+                    static_cast<float *>(a.lm), a.table, n, a.tau, static_cast<float *>(a.pkw),
+                    ctx->N, pv.n_pad);
+            TRY(launched(ctx));
+        }
+    }
+    TRY(run_vjp(ctx));
+    const unsigned nb = blocks_for(ctx->N, 256);
+    void *dgx = on_device ? gx_0 : (gx_0 ? (void *)ctx->stage : nullptr);
+    void *dgv = on_device ? gv_0 : (gv_0 ? (void *)ctx->stage2 : nullptr);
+    void *dgm = on_device ? gm : (gm ? a.rvh : nullptr);
+    if (f64) {
+        adj_final_f64_kernel<<<nb, 256, 0, ctx->stream>>>(static_cast<const double4 *>(ctx->part),
+                                                          pv.L, pv.itile, static_cast<double4 *>(a.lx),
+                                                          static_cast<double *>(a.lm), ctx->N);
+        TRY(launched(ctx));
+        adj_store_kernel<double4, double><<<nb, 256, 0, ctx->stream>>>(
+            static_cast<const double4 *>(a.lx), static_cast<const double4 *>(a.lv),
+            static_cast<const double *>(a.lm), ctx->N, dgx, dgv, dgm, in64);
+    } else {
+        adj_final_f32_kernel<<<nb, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part),
+                                                          pv.L, pv.itile, static_cast<float4 *>(a.lx),
+                                                          static_cast<float *>(a.lm), ctx->N);
+        TRY(launched(ctx));
+        adj_store_kernel<float4, float><<<nb, 256, 0, ctx->stream>>>(
+            static_cast<const float4 *>(a.lx), static_cast<const float4 *>(a.lv),
+            static_cast<const float *>(a.lm), ctx->N, dgx, dgv, dgm, in64);
+    }
+    TRY(launched(ctx));
+    if (!on_device) {
+        if (gx_0) CU(cudaMemcpyAsync(gx_0, ctx->stage, vbytes, cudaMemcpyDeviceToHost, ctx->stream));
+        if (gv_0) CU(cudaMemcpyAsync(gv_0, ctx->stage2, vbytes, cudaMemcpyDeviceToHost, ctx->stream));
+        if (gm) CU(cudaMemcpyAsync(gm, a.rvh, sbytes, cudaMemcpyDeviceToHost, ctx->stream));
+        TRY(sync_and_check(ctx));
+    }
     return COLATUS_OK;
 }
 
