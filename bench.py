@@ -262,6 +262,35 @@ def time_adjoint(B, inputs, torch, stream, nsteps=40, k=20):
             (torch.cuda.get_device_properties(0).multi_processor_count * 2.032e9)}
 
 
+def time_ensemble(B, inputs, torch, stream, nsteps=48):
+    """The 64-realisation ensemble (N_r log-uniform in [1024, 32768]): KDK
+    steps under the library's captured 16-step graphs, aggregate throughput."""
+    ics = inputs.ensemble(64, seed=5)
+    Ns = np.array([ic.N for ic in ics])
+    ens = B.Ensemble(Ns, np.concatenate([ic.m for ic in ics]), [ic.eps for ic in ics], LCDM,
+                     inputs.A_START, stream=stream.cuda_stream)
+    try:
+        ens.set_state(np.concatenate([ic.x for ic in ics]), np.concatenate([ic.v for ic in ics]))
+        tau = inputs.lcdm_tau(2000)
+        ens.step(tau, 16)
+        ens.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = ens.stats()["launches"]
+        e0.record(stream)
+        ens.step(tau, nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = ens.stats()
+    finally:
+        ens.close()
+    ms = e0.elapsed_time(e1)
+    pairs = float(np.sum(Ns.astype(float) ** 2))
+    return {"realisations": len(ics), "N_total": int(Ns.sum()), "N_min": int(Ns.min()),
+            "N_max": int(Ns.max()), "interactions_per_step": pairs, "steps": nsteps,
+            "ms_per_step": ms / nsteps, "interactions_per_s": pairs * nsteps / (ms * 1e-3),
+            "graph_launches": nsteps // 16, "kernel_launches": st["launches"] - l0}
+
+
 def run_colatus(args, ws, rank, local):
     import torch
     from paper_1208_3444_b300 import binding as B
@@ -342,6 +371,7 @@ def run_colatus(args, ws, rank, local):
     if not args.no_128:
         force128 = time_force_128(B, inputs, torch)
     adjoint = time_adjoint(B, inputs, torch, stream)
+    ensemble = time_ensemble(B, inputs, torch, stream)
     if rank == 0:
         peaks = {}
         try:
@@ -382,6 +412,7 @@ def run_colatus(args, ws, rank, local):
             "roofline": roof,
             "force_128cubed": force128,
             "adjoint": adjoint,
+            "ensemble": ensemble,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,

@@ -216,6 +216,59 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
 colatus_status colatus_forces_noalloc(const float *pos, int64_t N, double eps, double G, double a,
                                       float *acc_out, void *cuda_stream);
 
+/* ------------------------------------------------------------ ensembles
+ * Many independent realisations of the same system of equations (Eqs. 1-5,
+ * KDK, FP32 compensated-free plain accumulation, FP64 a(t) shared by all, one
+ * softening per realisation), stepped together: each step is one persistent
+ * force launch over every realisation's interactions plus one fused
+ * kick/drift launch, and colatus_ensemble_step replays a captured CUDA graph
+ * of 16 steps at a time.  Arrays are dense concatenations: realisation r's
+ * N_r bodies follow those of realisations 0..r-1 (N_tot = sum N_r rows). */
+typedef struct colatus_ensemble *colatus_ens_t;
+
+/* R realisations with N_r[r] bodies (host array), masses (host, N_tot
+ * doubles), softenings eps_r (host, R doubles, > 0), the Eq. 2 parameters,
+ * a_start, G and a cudaStream_t (NULL: a library-owned stream). */
+colatus_status colatus_ensemble_init(colatus_ens_t *out, int R, const int64_t *N_r,
+                                     const double *masses, const double *eps_r, double Omega_R,
+                                     double Omega_M, double Omega_K, double Omega_L, double H0,
+                                     double a_start, double G, void *cuda_stream);
+/* Positions and velocities, N_tot x 3 (dtype, host or device; v may be NULL). */
+colatus_status colatus_ensemble_set_state(colatus_ens_t e, const void *x, const void *v, int dtype,
+                                          int on_device);
+colatus_status colatus_ensemble_get_state(colatus_ens_t e, void *x, void *v, int dtype,
+                                          int on_device, double *t, double *a);
+/* Comoving accelerations G a^-3 F of every body (N_tot x 3). */
+colatus_status colatus_ensemble_forces(colatus_ens_t e, void *acc_out, int dtype, int on_device);
+/* nsteps KDK steps of size dt > 0 for every realisation (asynchronous). */
+colatus_status colatus_ensemble_step(colatus_ens_t e, double dt, int64_t nsteps);
+colatus_status colatus_ensemble_synchronize(colatus_ens_t e);
+/* Synchronises; out[0] kernel launches (a 16-step graph counts its 33),
+ * out[1] interactions enqueued, out[2] steps, out[3] interactions per step,
+ * out[4]/out[5] milliseconds/number of force launches timed outside graphs
+ * since the last call; profile_on switches that timing on or off. */
+colatus_status colatus_ensemble_stats(colatus_ens_t e, int profile_on, double out[6]);
+const char *colatus_ensemble_last_error(colatus_ens_t e);
+void colatus_ensemble_destroy(colatus_ens_t e);
+
+/* Tangent-linear model for finite-time Lyapunov growth of single tracers
+ * (FP32, KDK).  Tangent b starts as a unit position perturbation `dir` (host
+ * double[3]; NULL: x axis) on body seeds[b] only, with zero velocity
+ * perturbation; the whole system's linear response is then propagated:
+ *     dF_k = G sum_{j != k} m_j J(d_kj) (dx_j - dx_k),  J(d) = I/s^3 - 3 d d^T/s^5,
+ * through the same KDK steps as the state.  After every step the norm
+ * |(dx, dv)| of the seed body of each tangent is recorded (ring of
+ * capacity_steps records); ln(norm)/t is the finite-time Lyapunov exponent.
+ * Initialising replaces any previous tangents. */
+colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, const double *dir,
+                                    int64_t capacity_steps);
+/* Advance the state and its tangents by nsteps KDK steps of size dt (FP32
+ * precision only).  COLATUS_E_STATE if the state was stepped without them. */
+colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps);
+/* Recorded growth, oldest first, host [nrec][B] floats; growth may be NULL
+ * to query *nrec_out.  Synchronises. */
+colatus_status colatus_tangent_read(colatus_t ctx, float *growth, int64_t *nrec_out);
+
 /* Release every device and host resource of ctx (NULL is a no-op). */
 void colatus_destroy(colatus_t ctx);
 

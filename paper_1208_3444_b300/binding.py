@@ -31,7 +31,11 @@ EXPORTS = ("colatus_init", "colatus_set_config", "colatus_set_masses", "colatus_
            "colatus_record_tracers", "colatus_read_tracers", "colatus_diagnostics",
            "colatus_last_error", "colatus_stats", "colatus_profile_forces",
            "colatus_profile_read", "colatus_force_vjp", "colatus_adjoint_forward",
-           "colatus_adjoint_backward", "colatus_forces_noalloc", "colatus_destroy")
+           "colatus_adjoint_backward", "colatus_forces_noalloc", "colatus_destroy",
+           "colatus_ensemble_init", "colatus_ensemble_set_state", "colatus_ensemble_get_state",
+           "colatus_ensemble_forces", "colatus_ensemble_step", "colatus_ensemble_synchronize",
+           "colatus_ensemble_stats", "colatus_ensemble_last_error", "colatus_ensemble_destroy",
+           "colatus_tangent_init", "colatus_tangent_step", "colatus_tangent_read")
 
 
 class ColatusError(RuntimeError):
@@ -72,6 +76,17 @@ def lib():
         "colatus_force_vjp": [_vp, _vp, _vp, _vp, _int, _int],
         "colatus_adjoint_forward": [_vp, _dbl, _i64, _i64],
         "colatus_adjoint_backward": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _int, _int],
+        "colatus_ensemble_init": [ctypes.POINTER(_vp), _int, _vp, _vp, _vp, _dbl, _dbl, _dbl, _dbl,
+                                  _dbl, _dbl, _dbl, _vp],
+        "colatus_ensemble_set_state": [_vp, _vp, _vp, _int, _int],
+        "colatus_ensemble_get_state": [_vp, _vp, _vp, _int, _int, _vp, _vp],
+        "colatus_ensemble_forces": [_vp, _vp, _int, _int],
+        "colatus_ensemble_step": [_vp, _dbl, _i64],
+        "colatus_ensemble_synchronize": [_vp],
+        "colatus_ensemble_stats": [_vp, _int, _vp],
+        "colatus_tangent_init": [_vp, _vp, _int, _vp, _i64],
+        "colatus_tangent_step": [_vp, _dbl, _i64],
+        "colatus_tangent_read": [_vp, _vp, _vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -81,6 +96,10 @@ def lib():
     L.colatus_last_error.restype = ctypes.c_char_p
     L.colatus_destroy.argtypes = [_vp]
     L.colatus_destroy.restype = None
+    L.colatus_ensemble_last_error.argtypes = [_vp]
+    L.colatus_ensemble_last_error.restype = ctypes.c_char_p
+    L.colatus_ensemble_destroy.argtypes = [_vp]
+    L.colatus_ensemble_destroy.restype = None
     _lib = L
     return L
 
@@ -371,9 +390,100 @@ class Simulation:
         colatus_adjoint_backward(self.h, cast(gx_T), cast(gv_T), cast(gm_T), gx, gv, gm)
         return gx, gv, gm
 
+    def tangent_init(self, seeds, capacity_steps, direction=(1.0, 0.0, 0.0)):
+        sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.int64).reshape(-1))
+        d = np.ascontiguousarray(np.asarray(direction, dtype=np.float64))
+        self.ntan = sd.size
+        _check(lib().colatus_tangent_init(self.h, sd.ctypes.data, int(sd.size), d.ctypes.data,
+                                          int(capacity_steps)), self.h)
+
+    def tangent_step(self, dt, nsteps=1):
+        _check(lib().colatus_tangent_step(self.h, float(dt), int(nsteps)), self.h)
+
+    def tangent_growth(self):
+        """[nrec, B] norms |(dx, dv)| of each tangent's seed body after each step."""
+        n = ctypes.c_int64()
+        _check(lib().colatus_tangent_read(self.h, None, ctypes.byref(n)), self.h)
+        out = np.empty((n.value, self.ntan), dtype=np.float32)
+        if n.value:
+            _check(lib().colatus_tangent_read(self.h, out.ctypes.data, ctypes.byref(n)), self.h)
+        return out
+
     def close(self):
         if self.h:
             colatus_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ ensembles
+def _echeck(status, handle):
+    if status != OK:
+        msg = lib().colatus_ensemble_last_error(handle)
+        raise ColatusError(status, msg.decode() if msg else "")
+
+
+class Ensemble:
+    """R independent realisations stepped together (colatus_ensemble_*).
+    Arrays are dense concatenations of the realisations (N_tot rows)."""
+
+    def __init__(self, Ns, masses, eps_r, cosmo, a_start, G=1.0, stream=None):
+        Ns = np.ascontiguousarray(np.asarray(Ns, dtype=np.int64))
+        m = np.ascontiguousarray(np.asarray(masses, dtype=np.float64).reshape(-1))
+        e = np.ascontiguousarray(np.asarray(eps_r, dtype=np.float64).reshape(-1))
+        if m.size != Ns.sum() or e.size != Ns.size:
+            raise ValueError("masses must have sum(Ns) entries and eps_r len(Ns)")
+        self.Ns, self.Ntot = Ns, int(Ns.sum())
+        c = dict(cosmo)
+        h = _vp()
+        st = lib().colatus_ensemble_init(ctypes.byref(h), int(Ns.size), Ns.ctypes.data, m.ctypes.data,
+                                         e.ctypes.data, c["Omega_R"], c["Omega_M"], c["Omega_K"],
+                                         c["Omega_L"], c["H0"], float(a_start), float(G),
+                                         None if stream is None else int(stream))
+        _echeck(st, None)
+        self.h = h
+
+    def set_state(self, x, v=None):
+        dev, dt, bufs = _same(x, v)
+        _echeck(lib().colatus_ensemble_set_state(self.h, bufs[0][0],
+                                                 bufs[1][0] if v is not None else None, dt, dev), self.h)
+
+    def state(self, dtype=np.float64):
+        x = np.empty((self.Ntot, 3), dtype=dtype)
+        v = np.empty((self.Ntot, 3), dtype=dtype)
+        t, a = _dbl(), _dbl()
+        dt = F64 if dtype == np.float64 else F32
+        _echeck(lib().colatus_ensemble_get_state(self.h, x.ctypes.data, v.ctypes.data, dt, 0,
+                                                 ctypes.byref(t), ctypes.byref(a)), self.h)
+        return x, v, t.value, a.value
+
+    def forces(self, out=None):
+        if out is None:
+            out = np.empty((self.Ntot, 3), dtype=np.float64)
+        p, dev, dt, keep = _buf(out)
+        _echeck(lib().colatus_ensemble_forces(self.h, p, dt, dev), self.h)
+        return out
+
+    def step(self, dt, nsteps=1):
+        _echeck(lib().colatus_ensemble_step(self.h, float(dt), int(nsteps)), self.h)
+
+    def synchronize(self):
+        _echeck(lib().colatus_ensemble_synchronize(self.h), self.h)
+
+    def stats(self, profile_on=False):
+        out = np.zeros(6)
+        _echeck(lib().colatus_ensemble_stats(self.h, int(profile_on), out.ctypes.data), self.h)
+        return dict(launches=int(out[0]), interactions=float(out[1]), steps=int(out[2]),
+                    pairs_per_step=float(out[3]), force_ms=float(out[4]), force_launches=int(out[5]))
+
+    def close(self):
+        if self.h:
+            lib().colatus_ensemble_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -11,8 +11,10 @@
 #include "colatus.h"
 #include "common.cuh"
 #include "diagnostics.cuh"
+#include "ensemble.cuh"
 #include "force.cuh"
 #include "integrate.cuh"
+#include "tangent.cuh"
 
 using namespace colatus;
 
@@ -76,6 +78,10 @@ constexpr int kVjpNT = 256, kVjpIPT = 2, kVjpJT = 256, kVjpMINB = 2;
 using VjpK = VjpKernel<kVjpNT, kVjpIPT, kVjpJT, kStages>;
 constexpr int kV64NT = 128, kV64JT = 32;
 using Vjp64K = Vjp64Kernel<kV64NT, kV64JT, kStages>;
+
+// JVP (tangent) kernel: 128 threads x 2 i-bodies, 128-body j-tiles of 64 B
+constexpr int kJvpNT = 128, kJvpIPT = 2, kJvpJT = 128, kJvpMINB = 4;
+using JvpK = JvpKernel<kJvpNT, kJvpIPT, kJvpJT, kStages>;
 
 constexpr long long kPadAlloc = 1024;   // buffers hold N rounded up to this
 constexpr int kChunk = 1024;            // steps enqueued per chunk of colatus_step
@@ -183,6 +189,20 @@ struct colatus_ctx {
     ForcePlan plan32[NUM_F32_VARIANTS];
     ForcePlan plan64;
     ForcePlan plan_vjp32, plan_vjp64;
+
+    // tangent model (colatus_tangent_*)
+    struct Tangent {
+        bool ready = false, open = false;
+        int B = 0, nchunk = 0;
+        long long n_pad = 0, last_step = -1;
+        double tau = 0.0;
+        ForcePlan plan;
+        float4 *dx = nullptr, *dv = nullptr, *dvh = nullptr, *pkt = nullptr;
+        long long *seeds = nullptr;
+        float *growth = nullptr;
+        long long cap = 0, base = 0;
+        double dir[3] = {1.0, 0.0, 0.0};
+    } tan;
 
     // discrete adjoint (colatus_adjoint_forward / colatus_adjoint_backward)
     struct Adjoint {
@@ -486,6 +506,10 @@ void free_all(colatus_t ctx) {
                     ctx->rec};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    void *tptrs[] = {ctx->tan.dx, ctx->tan.dv, ctx->tan.dvh, ctx->tan.pkt, ctx->tan.seeds,
+                     ctx->tan.growth};
+    for (void *p : tptrs)
+        if (p) cudaFree(p);
     void *aptrs[] = {ctx->adj.ck_x, ctx->adj.ck_v, ctx->adj.seg_x, ctx->adj.table, ctx->adj.rclk,
                      ctx->adj.rvs, ctx->adj.rvh, ctx->adj.racc, ctx->adj.rpk[0], ctx->adj.rpk[1],
                      ctx->adj.lx, ctx->adj.lv, ctx->adj.lvh, ctx->adj.lm, ctx->adj.pkw};
@@ -788,6 +812,41 @@ __global__ void vec3_to4_kernel(const void *src, int f64, long long N, T4 *dst) 
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     dst[i] = load3<T4, T>(src, f64, i);
+}
+
+
+// ------------------------------------------------------------------ tangent
+TangentState tan_state(colatus_t ctx) {
+    auto &t = ctx->tan;
+    TangentState T;
+    T.dx = t.dx;
+    T.dv = t.dv;
+    T.dvh = t.dvh;
+    T.pkt = t.pkt;
+    T.seeds = t.seeds;
+    T.growth = t.growth;
+    T.cap = t.cap;
+    T.base = t.base;
+    T.B = t.B;
+    T.nchunk = t.nchunk;
+    return T;
+}
+
+// Pack positions (pair-interleaved pk) with the tangents and run the JVP.
+colatus_status run_jvp(colatus_t ctx, const float *pk) {
+    auto &t = ctx->tan;
+    const TangentState T = tan_state(ctx);
+    dim3 grid(blocks_for(t.n_pad, 256), t.nchunk);
+    tan_pack_kernel<<<grid, 256, 0, ctx->stream>>>(pk, T, ctx->N, t.n_pad);
+    TRY(launched(ctx));
+    TRY(ensure_part(ctx, t.plan.part_bytes));
+    jvp_f32_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kJvpMINB>
+        <<<t.plan.L.G, kJvpNT, JvpK::SMEM, ctx->stream>>>(t.pkt, static_cast<float4 *>(ctx->part),
+                                                          ctx->flags, t.plan.L, t.n_pad,
+                                                          (float)(ctx->eps * ctx->eps));
+    TRY(launched(ctx));
+    ctx->interactions += (double)ctx->N * (double)ctx->N * t.B;
+    return COLATUS_OK;
 }
 
 }  // namespace
@@ -1447,6 +1506,149 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
     return COLATUS_OK;
 }
 
+colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, const double *dir,
+                                    int64_t capacity_steps) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    auto &t = ctx->tan;
+    if (B < 1 || !seeds || capacity_steps < 1) return fail(ctx, COLATUS_E_ARG, "need B >= 1 seeds and capacity");
+    for (int b = 0; b < B; ++b)
+        if (seeds[b] < 0 || seeds[b] >= ctx->N) return fail(ctx, COLATUS_E_ARG, "seed out of range");
+    double d[3] = {1.0, 0.0, 0.0};
+    if (dir) {
+        const double nrm = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+        if (!(nrm > 0.0) || !std::isfinite(nrm)) return fail(ctx, COLATUS_E_ARG, "bad direction");
+        for (int c = 0; c < 3; ++c) d[c] = dir[c] / nrm;
+    }
+    if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
+    CU(cudaStreamSynchronize(ctx->stream));
+    void *old[] = {t.dx, t.dv, t.dvh, t.pkt, t.seeds, t.growth};
+    for (void *p : old)
+        if (p) cudaFree(p);
+    t = colatus_ctx::Tangent();
+    int occ = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, jvp_f32_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kJvpMINB>, kJvpNT, JvpK::SMEM));
+    if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "JVP kernel cannot be resident");
+    t.B = B;
+    t.nchunk = (B + kTB - 1) / kTB;
+    t.n_pad = round_up(ctx->N, std::max(JvpK::ITILE, kJvpJT));
+    ForceLaunch L{};
+    L.n_it = (int)(t.n_pad / JvpK::ITILE);
+    L.n_jt = (int)(t.n_pad / kJvpJT);
+    L.W = (long long)t.nchunk * L.n_it * L.n_jt;
+    L.G = (int)std::max(1LL, std::min<long long>((long long)occ * ctx->num_sms, L.W));
+    long long smax = 1;
+    for (long long ct = 0; ct < (long long)t.nchunk * L.n_it; ++ct)
+        smax = std::max(smax, sk_owner((ct + 1) * L.n_jt - 1, L.W, L.G) - sk_owner(ct * L.n_jt, L.W, L.G) + 1);
+    L.S_max = (int)smax;
+    t.plan.L = L;
+    t.plan.itile = JvpK::ITILE;
+    t.plan.jt = kJvpJT;
+    t.plan.n_pad = t.n_pad;
+    t.plan.part_bytes = (size_t)t.nchunk * L.n_it * smax * 3 * JvpK::ITILE * sizeof(float4);
+    const size_t tb = (size_t)B * t.n_pad * sizeof(float4);
+    CU(cudaMalloc(&t.dx, tb));
+    CU(cudaMalloc(&t.dv, tb));
+    CU(cudaMalloc(&t.dvh, tb));
+    CU(cudaMalloc(&t.pkt, (size_t)t.nchunk * t.n_pad * 4 * sizeof(float4)));
+    CU(cudaMalloc(&t.seeds, B * sizeof(long long)));
+    CU(cudaMalloc(&t.growth, (size_t)capacity_steps * B * sizeof(float)));
+    CU(cudaMemset(t.dx, 0, tb));
+    CU(cudaMemset(t.dv, 0, tb));
+    CU(cudaMemset(t.dvh, 0, tb));
+    std::vector<long long> sd(seeds, seeds + B);
+    CU(cudaMemcpy(t.seeds, sd.data(), B * sizeof(long long), cudaMemcpyHostToDevice));
+    const float4 unit = make_float4((float)d[0], (float)d[1], (float)d[2], 0.f);
+    for (int b = 0; b < B; ++b)
+        CU(cudaMemcpy(t.dx + (size_t)b * t.n_pad + seeds[b], &unit, sizeof(unit), cudaMemcpyHostToDevice));
+    for (int c = 0; c < 3; ++c) t.dir[c] = d[c];
+    t.cap = capacity_steps;
+    t.base = ctx->host_step;
+    t.last_step = ctx->host_step;
+    t.ready = true;
+    t.open = false;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    auto &t = ctx->tan;
+    if (!t.ready) return fail(ctx, COLATUS_E_STATE, "colatus_tangent_init first");
+    if (ctx->prec == COLATUS_FP64 || ctx->scheme != COLATUS_KDK)
+        return fail(ctx, COLATUS_E_ARG, "the tangent model runs with FP32 precision and KDK");
+    if (t.last_step != ctx->host_step)
+        return fail(ctx, COLATUS_E_STATE, "the state moved without its tangents; re-initialise");
+    if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(ctx, COLATUS_E_ARG, "bad dt/nsteps");
+    if (nsteps == 0) return COLATUS_OK;
+    if (t.open && t.tau != dt) t.open = false;
+    if (ctx->spec_valid && ctx->spec_tau != dt) ctx->spec_valid = false;
+    const TangentState T = tan_state(ctx);
+    dim3 grid(blocks_for(ctx->N, 256), t.nchunk);
+    for (int64_t done = 0; done < nsteps;) {
+        const int n = (int)std::min<int64_t>(kChunk, nsteps - done);
+        TRY(need_table(ctx, dt, n));
+        if (!t.open) {
+            // tangent opening at x^n: JVP on the packed state positions
+            const ForcePlan &p = plan_f32(ctx);
+            pack_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(ctx->xs, ctx->pk[2],
+                                                                               ctx->N, p.n_pad);
+            TRY(launched(ctx));
+            TRY(run_jvp(ctx, ctx->pk[2]));
+            tan_open_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part),
+                                                           t.plan.L, t.plan.itile, T, ctx->table,
+                                                           kTabCap, ctx->host_step, dt, ctx->N, t.n_pad);
+            TRY(launched(ctx));
+            t.open = true;
+            t.tau = dt;
+        }
+        if (!ctx->spec_valid) {
+            TRY(open_step(ctx, dt));
+            ctx->spec_valid = true;
+            ctx->spec_tau = dt;
+        }
+        for (int j = 0; j < n; ++j) {
+            const int c = ctx->cur;
+            TRY(one_step(ctx, j, dt));
+            TRY(run_jvp(ctx, ctx->pk[c]));
+            tan_step_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part),
+                                                           t.plan.L, t.plan.itile, T, ctx->table,
+                                                           kTabCap, ctx->host_step + j, dt, ctx->N,
+                                                           t.n_pad);
+            TRY(launched(ctx));
+        }
+        done += n;
+        ctx->host_step += n;
+        TRY(refill_table(ctx));
+    }
+    ctx->acc_valid = true;
+    t.last_step = ctx->host_step;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_tangent_read(colatus_t ctx, float *growth, int64_t *nrec_out) {
+    if (!ctx || !nrec_out) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    auto &t = ctx->tan;
+    TRY(sync_and_check(ctx));
+    if (!t.ready) {
+        *nrec_out = 0;
+        return COLATUS_OK;
+    }
+    const long long total = t.last_step - t.base;
+    const long long nrec = std::min(total, t.cap);
+    *nrec_out = nrec;
+    if (!growth || nrec == 0) return COLATUS_OK;
+    std::vector<float> ring((size_t)t.cap * t.B);
+    CU(cudaMemcpy(ring.data(), t.growth, ring.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    for (long long k = 0; k < nrec; ++k) {
+        const long long s = total - nrec + k;
+        std::memcpy(growth + k * t.B, ring.data() + (s % t.cap) * t.B, t.B * sizeof(float));
+    }
+    return COLATUS_OK;
+}
+
 const char *colatus_last_error(colatus_t ctx) { return ctx ? ctx->err : g_init_err; }
 
 void colatus_destroy(colatus_t ctx) {
@@ -1469,3 +1671,6 @@ colatus_status colatus_stats(colatus_t ctx, double out[4]) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- ensembles
+#include "ensemble_api.cuh"

@@ -1,0 +1,538 @@
+// ensemble_api.cuh -- host side of the batched ensemble (colatus_ensemble_*),
+// included by colatus.cu after its helpers.
+//
+// Layout: realisation r's bodies are stored contiguously from body_off[r],
+// padded with zero-mass bodies to a multiple of the 256-body tile; users pass
+// and receive dense concatenated arrays (realisation r from user_off[r]).
+// A step is one persistent force launch over all realisations plus one fused
+// kick/drift epilogue; colatus_ensemble_step replays a captured CUDA graph of
+// 16 such steps (with their FP64 schedule kernel) per launch.
+#pragma once
+
+namespace {
+
+constexpr int kEnsNT = 64, kEnsIPT = 4, kEnsJT = 256, kEnsFold = 128, kEnsMinB = 8;
+using EnsK = F32Kernel<kEnsNT, kEnsIPT, kEnsJT, kStages, kEnsFold, false, false>;
+constexpr int kEnsTile = EnsK::ITILE;   // 256 bodies: the per-realisation padding unit
+constexpr int kEnsChunk = 16;           // steps per captured graph (even: ping-pong parity)
+static_assert(kEnsTile == kEnsJT, "ensemble tiles pad realisations to one size");
+
+}  // namespace
+
+struct colatus_ensemble {
+    int device = 0, num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int R = 0;
+    long long Ntot = 0, Npad = 0;
+    double G = 1.0, pairs = 0.0;
+    Cosmo cosmo{};
+    std::vector<long long> nbody, body_off, user_off, unit_off, tile_u0;
+    std::vector<int> n_jt, tile_r;
+    EnsLaunch E{};
+    void *meta = nullptr;                  // device descriptor arrays
+    long long *d_user_off = nullptr;
+    float4 *xs = nullptr, *vs = nullptr, *vh = nullptr, *acc = nullptr;
+    float *pk[3] = {nullptr, nullptr, nullptr};
+    float4 *part = nullptr;
+    int *flags = nullptr;
+    DevClock *clk = nullptr;
+    StepCoef *table = nullptr;             // kEnsChunk entries
+    double *stage = nullptr, *stage2 = nullptr;
+    bool have_state = false, spec_valid = false;
+    double spec_tau = 0.0;
+    int cur = 0;
+    long long host_step = 0, launches = 0;
+    double interactions = 0.0;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // per ping-pong parity
+    double graph_tau[2] = {0.0, 0.0};
+    char err[512] = {0};
+};
+
+namespace {
+
+colatus_status efail(colatus_ens_t e, colatus_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(e ? e->err : g_init_err, 512, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define ECU(call)                                                                             \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return efail(e, e_ == cudaErrorMemoryAllocation ? COLATUS_E_OOM : COLATUS_E_CUDA, \
+                         "%s: %s", #call, cudaGetErrorString(e_));                            \
+    } while (0)
+
+colatus_status elaunched(colatus_ens_t e) {
+    ++e->launches;
+    cudaError_t r = cudaGetLastError();
+    if (r != cudaSuccess) return efail(e, COLATUS_E_CUDA, "kernel launch: %s", cudaGetErrorString(r));
+    return COLATUS_OK;
+}
+
+// ---- user (dense) <-> padded layout
+__global__ void ens_masses_kernel(const double *m, const long long *user_off, EnsLaunch E,
+                                  long long Npad, float4 *xs, int *bad) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= Npad) return;
+    const int r = E.tile_r[i / kEnsTile];
+    const long long k = i - E.body_off[r];
+    if (k >= E.nbody[r]) {
+        xs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const double mi = m[user_off[r] + k];
+    if (!isfinite(mi) || mi < 0.0) atomicOr(bad, 1);
+    xs[i] = make_float4(0.f, 0.f, 0.f, (float)mi);
+}
+
+__global__ void ens_load_kernel(const void *x, const void *v, int f64, const long long *user_off,
+                                EnsLaunch E, long long Npad, float4 *xs, float4 *vs, int *bad) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= Npad) return;
+    const int r = E.tile_r[i / kEnsTile];
+    const long long k = i - E.body_off[r];
+    if (k >= E.nbody[r]) {
+        vs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const long long u = user_off[r] + k;
+    double p[3], q[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < 3; ++c) {
+        p[c] = f64 ? static_cast<const double *>(x)[3 * u + c] : static_cast<const float *>(x)[3 * u + c];
+        if (v)
+            q[c] = f64 ? static_cast<const double *>(v)[3 * u + c]
+                       : static_cast<const float *>(v)[3 * u + c];
+        if (!isfinite(p[c]) || !isfinite(q[c])) atomicOr(bad, 1);
+    }
+    xs[i] = make_float4((float)p[0], (float)p[1], (float)p[2], xs[i].w);
+    vs[i] = make_float4((float)q[0], (float)q[1], (float)q[2], 0.f);
+}
+
+// Real bodies of a (and b) into user arrays; `scale` from the clock (G a^-3)
+// when use_clock, else 1.
+__global__ void ens_store_kernel(const float4 *a, const float4 *b, const long long *user_off,
+                                 EnsLaunch E, long long Npad, void *oa, void *ob, int f64,
+                                 const DevClock *clk, double G, int use_clock) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= Npad) return;
+    const int r = E.tile_r[i / kEnsTile];
+    const long long k = i - E.body_off[r];
+    if (k >= E.nbody[r]) return;
+    const long long u = user_off[r] + k;
+    double s = 1.0;
+    if (use_clock) {
+        const double aa = clk->a;
+        s = G / (aa * aa * aa);
+    }
+    const float4 pa = a[i];
+    const float ca[3] = {pa.x, pa.y, pa.z};
+    for (int c = 0; c < 3; ++c) {
+        if (f64)
+            static_cast<double *>(oa)[3 * u + c] = use_clock ? s * ca[c] : (double)ca[c];
+        else
+            static_cast<float *>(oa)[3 * u + c] = use_clock ? (float)(s * ca[c]) : ca[c];
+    }
+    if (b && ob) {
+        const float4 pb = b[i];
+        const float cb[3] = {pb.x, pb.y, pb.z};
+        for (int c = 0; c < 3; ++c) {
+            if (f64)
+                static_cast<double *>(ob)[3 * u + c] = cb[c];
+            else
+                static_cast<float *>(ob)[3 * u + c] = cb[c];
+        }
+    }
+}
+
+colatus_status ens_force(colatus_ens_t e, const float *pk) {
+    if (e->profiling) {
+        while (e->ev.size() < e->ev_used + 2) {
+            cudaEvent_t v;
+            ECU(cudaEventCreate(&v));
+            e->ev.push_back(v);
+        }
+        ECU(cudaEventRecord(e->ev[e->ev_used], e->stream));
+    }
+    ens_force_kernel<kEnsNT, kEnsIPT, kEnsJT, kStages, kEnsFold, kEnsMinB>
+        <<<e->E.G, kEnsNT, EnsK::SMEM, e->stream>>>(pk, e->part, e->flags, e->E);
+    colatus_status st = elaunched(e);
+    if (st != COLATUS_OK) return st;
+    e->interactions += e->pairs;
+    if (e->profiling) {
+        ECU(cudaEventRecord(e->ev[e->ev_used + 1], e->stream));
+        e->ev_used += 2;
+    }
+    return COLATUS_OK;
+}
+
+unsigned ens_blocks(colatus_ens_t e) { return (unsigned)((e->Npad + 255) / 256); }
+
+colatus_status ens_force_at_state(colatus_ens_t e) {
+    ens_pack_kernel<<<ens_blocks(e), 256, 0, e->stream>>>(e->xs, e->pk[2], e->E, kEnsTile, e->Npad);
+    colatus_status st = elaunched(e);
+    if (st != COLATUS_OK) return st;
+    if ((st = ens_force(e, e->pk[2])) != COLATUS_OK) return st;
+    ens_forces_out_kernel<<<ens_blocks(e), 256, 0, e->stream>>>(e->part, e->E, kEnsTile, e->Npad,
+                                                               e->acc);
+    return elaunched(e);
+}
+
+// n <= kEnsChunk steps: their schedule, then force + epilogue per step.
+colatus_status ens_steps(colatus_ens_t e, double tau, int n) {
+    ens_table_kernel<<<1, 1, 0, e->stream>>>(e->cosmo, e->clk, e->table, n, tau, e->G, kFriedmannSub);
+    colatus_status st = elaunched(e);
+    if (st != COLATUS_OK) return st;
+    for (int j = 0; j < n; ++j) {
+        const int c = e->cur, nx = c ^ 1;
+        if ((st = ens_force(e, e->pk[c])) != COLATUS_OK) return st;
+        ens_step_kernel<<<ens_blocks(e), 256, 0, e->stream>>>(e->part, e->E, kEnsTile, e->pk[c], e->xs,
+                                                             e->vs, e->vh, e->acc, e->pk[nx], e->table,
+                                                             j, tau, e->Npad, e->flags, e->clk);
+        if ((st = elaunched(e)) != COLATUS_OK) return st;
+        e->cur = nx;
+    }
+    return COLATUS_OK;
+}
+
+colatus_status ens_capture(colatus_ens_t e, double tau) {
+    const int p = e->cur;
+    if (e->graph[p]) {
+        cudaGraphExecDestroy(e->graph[p]);
+        e->graph[p] = nullptr;
+    }
+    const bool prof = e->profiling;
+    e->profiling = false;   // no event records inside the graph
+    const long long l0 = e->launches;
+    const double i0 = e->interactions;
+    ECU(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
+    colatus_status st = ens_steps(e, tau, kEnsChunk);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
+    e->profiling = prof;
+    e->launches = l0;
+    e->interactions = i0;
+    e->cur = p;             // 16 steps return the ping-pong to its parity
+    if (st != COLATUS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (ce != cudaSuccess) return efail(e, COLATUS_E_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&e->graph[p], g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return efail(e, COLATUS_E_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    e->graph_tau[p] = tau;
+    return COLATUS_OK;
+}
+
+void ens_free(colatus_ens_t e) {
+    for (cudaGraphExec_t &g : e->graph)
+        if (g) cudaGraphExecDestroy(g);
+    for (cudaEvent_t v : e->ev) cudaEventDestroy(v);
+    void *ptrs[] = {e->meta, e->xs, e->vs, e->vh, e->acc, e->pk[0], e->pk[1], e->pk[2],
+                    e->part, e->flags, e->clk, e->table, e->stage, e->stage2};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
+}
+
+colatus_status ens_check(colatus_ens_t e, bool clear) {
+    int f[NUM_FLAGS];
+    ECU(cudaStreamSynchronize(e->stream));
+    ECU(cudaMemcpy(f, e->flags, sizeof(f), cudaMemcpyDeviceToHost));
+    if (clear) ECU(cudaMemset(e->flags, 0, sizeof(f)));
+    if (f[FLAG_TIMEOUT]) return efail(e, COLATUS_E_TIMEOUT, "a bounded device wait gave up");
+    if (f[FLAG_FRIEDMANN]) return efail(e, COLATUS_E_FRIEDMANN, "H^2 < 0 while integrating Eq. 2");
+    if (f[FLAG_NONFINITE]) return efail(e, COLATUS_E_NONFINITE, "non-finite position or velocity");
+    return COLATUS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+colatus_status colatus_ensemble_init(colatus_ens_t *out, int R, const int64_t *N_r,
+                                     const double *masses, const double *eps_r, double Omega_R,
+                                     double Omega_M, double Omega_K, double Omega_L, double H0,
+                                     double a_start, double G, void *cuda_stream) {
+    colatus_ens_t e = nullptr;
+    if (!out) return efail(nullptr, COLATUS_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (R < 1 || !N_r || !masses || !eps_r) return efail(nullptr, COLATUS_E_ARG, "bad arguments");
+    if (!(a_start > 0.0) || !std::isfinite(G)) return efail(nullptr, COLATUS_E_ARG, "bad a_start or G");
+    const double e2 = Omega_R / std::pow(a_start, 4) + Omega_M / std::pow(a_start, 3) +
+                      Omega_K / (a_start * a_start) + Omega_L;
+    if (!(e2 >= 0.0)) return efail(nullptr, COLATUS_E_ARG, "H^2(a_start) < 0");
+    for (int r = 0; r < R; ++r)
+        if (N_r[r] < 1 || !(eps_r[r] > 0.0) || !std::isfinite(eps_r[r]))
+            return efail(nullptr, COLATUS_E_ARG, "realisation %d: N >= 1 and eps > 0 needed", r);
+    e = new (std::nothrow) colatus_ensemble();
+    if (!e) return efail(nullptr, COLATUS_E_OOM, "host allocation failed");
+    auto bail = [&](colatus_status st) {
+        snprintf(g_init_err, sizeof(g_init_err), "%s", e->err);
+        ens_free(e);
+        delete e;
+        return st;
+    };
+    if (cudaGetDevice(&e->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device) != cudaSuccess)
+        return bail(efail(e, COLATUS_E_CUDA, "no CUDA device"));
+    e->R = R;
+    e->G = G;
+    e->cosmo = Cosmo{Omega_R, Omega_M, Omega_K, Omega_L, H0};
+    // descriptors
+    e->nbody.assign(N_r, N_r + R);
+    e->body_off.assign(R + 1, 0);
+    e->user_off.assign(R + 1, 0);
+    e->unit_off.assign(R + 1, 0);
+    e->n_jt.assign(R, 0);
+    for (int r = 0; r < R; ++r) {
+        const long long np = round_up(N_r[r], kEnsTile);
+        const long long nt = np / kEnsTile;
+        e->n_jt[r] = (int)nt;
+        for (long long t = 0; t < nt; ++t) {
+            e->tile_r.push_back(r);
+            e->tile_u0.push_back(e->unit_off[r] + t * nt);
+        }
+        e->body_off[r + 1] = e->body_off[r] + np;
+        e->user_off[r + 1] = e->user_off[r] + N_r[r];
+        e->unit_off[r + 1] = e->unit_off[r] + nt * nt;
+        e->pairs += (double)N_r[r] * (double)N_r[r];
+    }
+    e->Ntot = e->user_off[R];
+    e->Npad = e->body_off[R];
+    const int T = (int)e->tile_r.size();
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, ens_force_kernel<kEnsNT, kEnsIPT, kEnsJT, kStages, kEnsFold, kEnsMinB>, kEnsNT,
+            EnsK::SMEM) != cudaSuccess || occ < 1)
+        return bail(efail(e, COLATUS_E_CUDA, "ensemble force kernel cannot be resident"));
+    EnsLaunch &E = e->E;
+    E.W = e->unit_off[R];
+    E.R = R;
+    E.G = (int)std::min<long long>((long long)occ * e->num_sms, E.W);
+    E.T = T;
+    long long smax = 1;
+    for (int t = 0; t < T; ++t) {
+        const long long g0 = sk_owner(e->tile_u0[t], E.W, E.G);
+        const long long g1 = sk_owner(e->tile_u0[t] + e->n_jt[e->tile_r[t]] - 1, E.W, E.G);
+        smax = std::max(smax, g1 - g0 + 1);
+    }
+    E.S_max = (int)smax;
+    // device memory
+    const size_t ll = sizeof(long long);
+    const size_t meta_bytes = ll * ((R + 1) * 3 + R + T) + sizeof(int) * (R + T) + sizeof(float) * R + 64;
+    auto A = [&](void **p, size_t b) -> bool { return cudaMalloc(p, b) == cudaSuccess; };
+    const size_t np = (size_t)e->Npad;
+    bool ok = A(&e->meta, meta_bytes) && A((void **)&e->xs, np * 16) && A((void **)&e->vs, np * 16) &&
+              A((void **)&e->vh, np * 16) && A((void **)&e->acc, np * 16) &&
+              A((void **)&e->pk[0], np * 16) && A((void **)&e->pk[1], np * 16) &&
+              A((void **)&e->pk[2], np * 16) &&
+              A((void **)&e->part, (size_t)T * smax * kEnsTile * sizeof(float4)) &&
+              A((void **)&e->flags, NUM_FLAGS * sizeof(int)) && A((void **)&e->clk, sizeof(DevClock)) &&
+              A((void **)&e->table, kEnsChunk * sizeof(StepCoef)) &&
+              A((void **)&e->stage, (size_t)e->Ntot * 3 * sizeof(double)) &&
+              A((void **)&e->stage2, (size_t)e->Ntot * 3 * sizeof(double));
+    if (!ok) return bail(efail(e, COLATUS_E_OOM, "device allocation failed"));
+    if (cuda_stream) {
+        e->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(efail(e, COLATUS_E_CUDA, "stream creation failed"));
+        e->own_stream = true;
+    }
+    // descriptor upload (one host block mirroring the device carve-up)
+    std::vector<char> hm(meta_bytes, 0);
+    char *base = static_cast<char *>(e->meta);
+    size_t off = 0;
+    auto put = [&](const void *src, size_t bytes) -> char * {
+        std::memcpy(hm.data() + off, src, bytes);
+        char *d = base + off;
+        off += (bytes + 7) & ~size_t(7);
+        return d;
+    };
+    std::vector<float> eps2(R);
+    for (int r = 0; r < R; ++r) eps2[r] = (float)(eps_r[r] * eps_r[r]);
+    E.unit_off = reinterpret_cast<const long long *>(put(e->unit_off.data(), ll * (R + 1)));
+    E.body_off = reinterpret_cast<const long long *>(put(e->body_off.data(), ll * (R + 1)));
+    e->d_user_off = reinterpret_cast<long long *>(put(e->user_off.data(), ll * (R + 1)));
+    E.nbody = reinterpret_cast<const long long *>(put(e->nbody.data(), ll * R));
+    E.tile_u0 = reinterpret_cast<const long long *>(put(e->tile_u0.data(), ll * T));
+    E.n_jt = reinterpret_cast<const int *>(put(e->n_jt.data(), sizeof(int) * R));
+    E.tile_r = reinterpret_cast<const int *>(put(e->tile_r.data(), sizeof(int) * T));
+    E.eps2 = reinterpret_cast<const float *>(put(eps2.data(), sizeof(float) * R));
+    colatus_status st = COLATUS_OK;
+    cudaError_t ce = cudaMemcpy(e->meta, hm.data(), meta_bytes, cudaMemcpyHostToDevice);
+    DevClock clk{0.0, a_start, 0, 0};
+    if (ce == cudaSuccess) ce = cudaMemcpy(e->clk, &clk, sizeof(clk), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemset(e->flags, 0, NUM_FLAGS * sizeof(int));
+    for (float *p : e->pk)
+        if (ce == cudaSuccess) ce = cudaMemset(p, 0, np * 16);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpy(e->stage, masses, (size_t)e->Ntot * sizeof(double), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) return bail(efail(e, COLATUS_E_CUDA, "upload: %s", cudaGetErrorString(ce)));
+    ens_masses_kernel<<<ens_blocks(e), 256, 0, e->stream>>>(e->stage, e->d_user_off, E, e->Npad,
+                                                           e->xs, e->flags);
+    if ((st = elaunched(e)) != COLATUS_OK) return bail(st);
+    if ((st = ens_check(e, true)) != COLATUS_OK) return bail(COLATUS_E_ARG);
+    *out = e;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_ensemble_set_state(colatus_ens_t e, const void *x, const void *v, int dtype,
+                                          int on_device) {
+    if (!e || !x) return COLATUS_E_ARG;
+    DeviceGuard dg(e->device);
+    if (dtype != COLATUS_F32 && dtype != COLATUS_F64) return efail(e, COLATUS_E_ARG, "bad dtype");
+    const size_t bytes = (size_t)e->Ntot * 3 * (dtype == COLATUS_F64 ? 8 : 4);
+    const void *px = x, *pv = v;
+    if (!on_device) {
+        ECU(cudaMemcpyAsync(e->stage, x, bytes, cudaMemcpyHostToDevice, e->stream));
+        px = e->stage;
+        if (v) {
+            ECU(cudaMemcpyAsync(e->stage2, v, bytes, cudaMemcpyHostToDevice, e->stream));
+            pv = e->stage2;
+        }
+    }
+    TRY(ens_check(e, true));
+    ens_load_kernel<<<ens_blocks(e), 256, 0, e->stream>>>(px, pv, dtype == COLATUS_F64, e->d_user_off,
+                                                         e->E, e->Npad, e->xs, e->vs, e->flags);
+    TRY(elaunched(e));
+    TRY(ens_check(e, true));
+    e->have_state = true;
+    e->spec_valid = false;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_ensemble_get_state(colatus_ens_t e, void *x, void *v, int dtype,
+                                          int on_device, double *t, double *a) {
+    if (!e) return COLATUS_E_ARG;
+    DeviceGuard dg(e->device);
+    if (dtype != COLATUS_F32 && dtype != COLATUS_F64) return efail(e, COLATUS_E_ARG, "bad dtype");
+    TRY(ens_check(e, true));
+    if (x || v) {
+        if (!e->have_state) return efail(e, COLATUS_E_STATE, "no state has been set");
+        const size_t bytes = (size_t)e->Ntot * 3 * (dtype == COLATUS_F64 ? 8 : 4);
+        void *dx = on_device ? x : (x ? (void *)e->stage : nullptr);
+        void *dv = on_device ? v : (v ? (void *)e->stage2 : nullptr);
+        if (dx)
+            ens_store_kernel<<<ens_blocks(e), 256, 0, e->stream>>>(
+                e->xs, nullptr, e->d_user_off, e->E, e->Npad, dx, nullptr, dtype == COLATUS_F64, e->clk,
+                e->G, 0);
+        if (dv)
+            ens_store_kernel<<<ens_blocks(e), 256, 0, e->stream>>>(
+                e->vs, nullptr, e->d_user_off, e->E, e->Npad, dv, nullptr, dtype == COLATUS_F64, e->clk,
+                e->G, 0);
+        TRY(elaunched(e));
+        if (!on_device) {
+            if (x) ECU(cudaMemcpyAsync(x, e->stage, bytes, cudaMemcpyDeviceToHost, e->stream));
+            if (v) ECU(cudaMemcpyAsync(v, e->stage2, bytes, cudaMemcpyDeviceToHost, e->stream));
+        }
+        ECU(cudaStreamSynchronize(e->stream));
+    }
+    if (t || a) {
+        DevClock c;
+        ECU(cudaMemcpy(&c, e->clk, sizeof(c), cudaMemcpyDeviceToHost));
+        if (t) *t = c.t;
+        if (a) *a = c.a;
+    }
+    return COLATUS_OK;
+}
+
+colatus_status colatus_ensemble_forces(colatus_ens_t e, void *acc_out, int dtype, int on_device) {
+    if (!e || !acc_out) return COLATUS_E_ARG;
+    DeviceGuard dg(e->device);
+    if (dtype != COLATUS_F32 && dtype != COLATUS_F64) return efail(e, COLATUS_E_ARG, "bad dtype");
+    if (!e->have_state) return efail(e, COLATUS_E_STATE, "no state has been set");
+    TRY(ens_force_at_state(e));
+    void *dst = on_device ? acc_out : (void *)e->stage;
+    ens_store_kernel<<<ens_blocks(e), 256, 0, e->stream>>>(e->acc, nullptr, e->d_user_off, e->E,
+                                                          e->Npad, dst, nullptr, dtype == COLATUS_F64,
+                                                          e->clk, e->G, 1);
+    TRY(elaunched(e));
+    if (!on_device) {
+        ECU(cudaMemcpyAsync(acc_out, e->stage, (size_t)e->Ntot * 3 * (dtype == COLATUS_F64 ? 8 : 4),
+                            cudaMemcpyDeviceToHost, e->stream));
+        TRY(ens_check(e, true));
+    }
+    e->spec_valid = false;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_ensemble_step(colatus_ens_t e, double dt, int64_t nsteps) {
+    if (!e) return COLATUS_E_ARG;
+    DeviceGuard dg(e->device);
+    if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0)
+        return efail(e, COLATUS_E_ARG, "dt must be > 0 and nsteps >= 0");
+    if (!e->have_state) return efail(e, COLATUS_E_STATE, "no state has been set");
+    if (nsteps == 0) return COLATUS_OK;
+    if (!e->spec_valid || e->spec_tau != dt) {
+        TRY(ens_force_at_state(e));
+        ens_table_kernel<<<1, 1, 0, e->stream>>>(e->cosmo, e->clk, e->table, 1, dt, e->G, kFriedmannSub);
+        TRY(elaunched(e));
+        ens_open_kernel<<<ens_blocks(e), 256, 0, e->stream>>>(e->xs, e->vs, e->acc, e->vh, e->pk[e->cur],
+                                                             e->table, dt, e->E, kEnsTile, e->Npad);
+        TRY(elaunched(e));
+        e->spec_valid = true;
+        e->spec_tau = dt;
+    }
+    const long long full = nsteps / kEnsChunk;
+    const int rem = (int)(nsteps % kEnsChunk);
+    for (long long f = 0; f < full; ++f) {
+        if (!e->graph[e->cur] || e->graph_tau[e->cur] != dt) TRY(ens_capture(e, dt));
+        ECU(cudaGraphLaunch(e->graph[e->cur], e->stream));
+        e->launches += 1 + 2 * kEnsChunk;
+        e->interactions += kEnsChunk * e->pairs;
+    }
+    if (rem) TRY(ens_steps(e, dt, rem));
+    e->host_step += nsteps;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_ensemble_synchronize(colatus_ens_t e) {
+    if (!e) return COLATUS_E_ARG;
+    DeviceGuard dg(e->device);
+    return ens_check(e, true);
+}
+
+colatus_status colatus_ensemble_stats(colatus_ens_t e, int profile_on, double out[6]) {
+    if (!e || !out) return COLATUS_E_ARG;
+    DeviceGuard dg(e->device);
+    ECU(cudaStreamSynchronize(e->stream));
+    double ms = 0.0;
+    for (size_t k = 0; k + 1 < e->ev_used; k += 2) {
+        float t = 0.f;
+        ECU(cudaEventElapsedTime(&t, e->ev[k], e->ev[k + 1]));
+        ms += t;
+    }
+    out[0] = (double)e->launches;
+    out[1] = e->interactions;
+    out[2] = (double)e->host_step;
+    out[3] = e->pairs;
+    out[4] = ms;
+    out[5] = (double)(e->ev_used / 2);
+    e->ev_used = 0;
+    e->profiling = profile_on != 0;
+    return COLATUS_OK;
+}
+
+const char *colatus_ensemble_last_error(colatus_ens_t e) { return e ? e->err : g_init_err; }
+
+void colatus_ensemble_destroy(colatus_ens_t e) {
+    if (!e) return;
+    {
+        DeviceGuard dg(e->device);
+        if (e->stream) cudaStreamSynchronize(e->stream);
+        ens_free(e);
+    }
+    delete e;
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+"""GPU parity of the batched ensemble (many uneven-N realisations stepped in
+one persistent launch per step, 16 steps per captured CUDA graph) against the
+FP64 oracle run realisation by realisation."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1208_3444_b300 import binding as B
+from paper_1208_3444_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+LCDM_D = dict(Omega_R=0.0, Omega_M=0.3, Omega_K=0.0, Omega_L=0.7, H0=1.0)
+LCDM = oracle.Cosmology(0.0, 0.3, 0.0, 0.7, 1.0)
+TAU = inputs.lcdm_tau(2000)
+
+
+def rel_rms(a, b):
+    return float(np.sqrt(np.mean(np.sum((a - b) ** 2, axis=1))) /
+                 np.mean(np.linalg.norm(b, axis=1)))
+
+
+def concat(ics):
+    return (np.concatenate([ic.x for ic in ics]), np.concatenate([ic.v for ic in ics]),
+            np.concatenate([ic.m for ic in ics]), np.array([ic.eps for ic in ics]),
+            np.array([ic.N for ic in ics]))
+
+
+def test_forces_of_uneven_realisations():
+    rng = np.random.default_rng(40)
+    ics = []
+    for N, eps in ((1, 0.02), (7, 0.01), (300, 0.005), (1025, 0.01), (2000, 0.003), (4096, 0.01)):
+        x = inputs.f32(rng.random((N, 3)))
+        m = inputs.f32(rng.lognormal(0.0, 0.5, N) / N)
+        ics.append(inputs.ICs(x=x, v=np.zeros_like(x), m=m, eps=eps, name=f"r{N}"))
+    x, v, m, eps, Ns = concat(ics)
+    ens = B.Ensemble(Ns, m, eps, LCDM_D, 0.8, G=1.1)
+    try:
+        ens.set_state(x, v)
+        acc = ens.forces()
+    finally:
+        ens.close()
+    off = np.concatenate([[0], np.cumsum(Ns)])
+    for r, ic in enumerate(ics):
+        got = acc[off[r]:off[r + 1]]
+        if ic.N == 1:
+            assert np.all(got == 0)
+            continue
+        ref = oracle.forces(ic.x, ic.m, ic.eps, 1.1) / 0.8 ** 3
+        assert rel_rms(got, ref) < 1e-5, ic.name
+
+
+def critical_ensemble(counts, seed=6):
+    out = []
+    for r, N in enumerate(counts):
+        n = int(np.ceil(round(N ** (1.0 / 3.0), 9)))
+        while n ** 3 < N:
+            n += 1
+        out.append(inputs.perturbed_grid(n, 0.1, 0.02, seed * 100 + r, zeldovich=True, count=N,
+                                         total_mass=inputs.CRITICAL_MATTER_DENSITY))
+    return out
+
+
+def test_steps_match_oracle_per_realisation():
+    ics = critical_ensemble([512, 1000, 1729, 3000])
+    x, v, m, eps, Ns = concat(ics)
+    n = 20   # one 16-step graph replay and 4 direct steps
+    ens = B.Ensemble(Ns, m, eps, LCDM_D, inputs.A_START)
+    try:
+        ens.set_state(x, v)
+        ens.step(TAU, n)
+        gx, gv, t, a = ens.state()
+    finally:
+        ens.close()
+    off = np.concatenate([[0], np.cumsum(Ns)])
+    rng = np.random.default_rng(0)
+    for r, ic in enumerate(ics):
+        ref = oracle.run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n, "kdk")
+        # the dynamics' own response to rounding-sized (6e-8) input changes,
+        # measured with the oracle: a close encounter can amplify it past 1e-5
+        xp = ic.x * (1.0 + 6e-8 * rng.standard_normal(ic.x.shape))
+        pert = oracle.run(xp, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n, "kdk")
+        chaos_x = np.abs(pert["x"] - ref["x"]).max()
+        assert np.abs(gx[off[r]:off[r + 1]] - ref["x"]).max() < max(1e-5, 10.0 * chaos_x), r
+        rms = lambda d: float(np.sqrt(np.mean(np.sum(d ** 2, axis=1))))
+        chaos_v = rms(pert["v"] - ref["v"])
+        tol_v = max(1e-5 * rms(ref["v"]), 10.0 * chaos_v)
+        assert rms(gv[off[r]:off[r + 1]] - ref["v"]) < tol_v, r
+        assert a == pytest.approx(ref["schedule"]["a"][-1], rel=1e-13)
+    assert t == pytest.approx(n * TAU, rel=1e-13)
+
+
+def test_graph_replays_are_deterministic_and_split_calls_agree():
+    ics = critical_ensemble([700, 1300])
+    x, v, m, eps, Ns = concat(ics)
+    res = []
+    for chunks in ([32], [16, 16], [5, 27]):
+        ens = B.Ensemble(Ns, m, eps, LCDM_D, inputs.A_START)
+        try:
+            ens.set_state(x, v)
+            for c in chunks:
+                ens.step(TAU, c)
+            res.append(ens.state()[:2])
+        finally:
+            ens.close()
+    for r in res[1:]:
+        assert np.array_equal(r[0], res[0][0]) and np.array_equal(r[1], res[0][1])
+
+
+def test_ensemble_workload_momentum_invariant():
+    # the 64-realisation workload (log-uniform N in [1024, 32768]), 3 steps:
+    # sum m v of each realisation scales by the product of its drag factors
+    ics = inputs.ensemble(64, seed=5)
+    x, v, m, eps, Ns = concat(ics)
+    ens = B.Ensemble(Ns, m, eps, LCDM_D, inputs.A_START)
+    try:
+        ens.set_state(x, v)
+        ens.step(TAU, 3)
+        gx, gv, t, a = ens.state()
+        st = ens.stats()
+    finally:
+        ens.close()
+    assert np.all(np.isfinite(gx)) and np.all(np.isfinite(gv))
+    sch = oracle.schedule(LCDM, inputs.A_START, TAU, 3, "kdk")
+    fac = float(np.prod(sch["c1"] * sch["c2"]))
+    off = np.concatenate([[0], np.cumsum(Ns)])
+    for r in range(len(ics)):
+        s = slice(off[r], off[r + 1])
+        P0 = np.sum(m[s, None] * v[s], axis=0)
+        P1 = np.sum(m[s, None] * gv[s], axis=0)
+        scale = np.sum(m[s, None] * np.abs(gv[s]), axis=0)
+        assert np.all(np.abs(P1 - fac * P0) < 1e-5 * scale), r
+    assert st["pairs_per_step"] == pytest.approx(float(np.sum(Ns.astype(float) ** 2)))
