@@ -161,6 +161,17 @@ colatus_status colatus_profile_forces(colatus_t ctx, int on);
  * launches.  Synchronises the stream and resets the totals. */
 colatus_status colatus_profile_read(colatus_t ctx, double out[4]);
 
+/* Force-kernel tuning.  The FP32 force kernel exists in three tile shapes
+ * (threads x i-bodies per thread, j-tile): 0 = 512 x 4, 512 bodies (one CTA
+ * per SM); 1 = 256 x 4, 512 (two CTAs per SM); 2 = 128 x 2, 64 (small N).
+ * colatus_autotune times reps launches of every shape that fits N on the
+ * current state (for the context's FP32 precision and mass type), keeps the
+ * fastest for this context and returns it in *chosen; out_ms[3] (may be NULL)
+ * receives the mean milliseconds per launch (0 for shapes that do not fit).
+ * colatus_set_tuning applies a known choice (-1: built-in choice). */
+colatus_status colatus_autotune(colatus_t ctx, int reps, double out_ms[3], int *chosen);
+colatus_status colatus_set_tuning(colatus_t ctx, int shape);
+
 /* Vector-Jacobian product of the Eq. 1 acceleration at the current state:
  * for a co-vector w (N x 3), gx = d(sum_k w_k . acc_k)/dx (N x 3) and
  * gm = d(sum_k w_k . acc_k)/dm (N), with acc = G a^-3 F as in colatus_forces:

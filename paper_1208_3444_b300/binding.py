@@ -35,7 +35,8 @@ EXPORTS = ("colatus_init", "colatus_set_config", "colatus_set_masses", "colatus_
            "colatus_ensemble_init", "colatus_ensemble_set_state", "colatus_ensemble_get_state",
            "colatus_ensemble_forces", "colatus_ensemble_step", "colatus_ensemble_synchronize",
            "colatus_ensemble_stats", "colatus_ensemble_last_error", "colatus_ensemble_destroy",
-           "colatus_tangent_init", "colatus_tangent_step", "colatus_tangent_read")
+           "colatus_tangent_init", "colatus_tangent_step", "colatus_tangent_read",
+           "colatus_autotune", "colatus_set_tuning")
 
 
 class ColatusError(RuntimeError):
@@ -85,6 +86,8 @@ def lib():
         "colatus_ensemble_synchronize": [_vp],
         "colatus_ensemble_stats": [_vp, _int, _vp],
         "colatus_tangent_init": [_vp, _vp, _int, _vp, _i64],
+        "colatus_autotune": [_vp, _int, _vp, _vp],
+        "colatus_set_tuning": [_vp, _int],
         "colatus_tangent_step": [_vp, _dbl, _i64],
         "colatus_tangent_read": [_vp, _vp, _vp],
     }
@@ -389,6 +392,17 @@ class Simulation:
         cast = (lambda a: None if a is None else np.ascontiguousarray(a, dtype=dtype))
         colatus_adjoint_backward(self.h, cast(gx_T), cast(gv_T), cast(gm_T), gx, gv, gm)
         return gx, gv, gm
+
+    def autotune(self, reps=3):
+        """Time the FP32 force shapes on the current state; keep the fastest.
+        Returns (chosen shape, [ms per launch of shapes 0, 1, 2])."""
+        ms = np.zeros(3)
+        ch = ctypes.c_int()
+        _check(lib().colatus_autotune(self.h, int(reps), ms.ctypes.data, ctypes.byref(ch)), self.h)
+        return int(ch.value), ms.tolist()
+
+    def set_tuning(self, shape):
+        _check(lib().colatus_set_tuning(self.h, int(shape)), self.h)
 
     def tangent_init(self, seeds, capacity_steps, direction=(1.0, 0.0, 0.0)):
         sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.int64).reshape(-1))

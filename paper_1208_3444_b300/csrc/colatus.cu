@@ -19,14 +19,17 @@
 using namespace colatus;
 
 // ------------------------------------------------------------------ kernels
-// FP32 force variants: "wide" tiles (1024 i-bodies x 512 j-bodies per unit:
-// 256 threads x 4 i-bodies, 2 CTAs per SM) for large N, "narrow" tiles
-// (256 x 64) for N where the wide tiles would leave SMs idle; each as plain
-// or compensated (TwoSum fold every 32 j-pairs), for general or equal masses.
-// The wide shape was chosen by a sweep over threads x i-bodies x j-tile.
+// FP32 force variants: three tile shapes, each plain or compensated (TwoSum
+// fold), for general or equal masses.  Shapes (threads x i-bodies per
+// thread, j-tile): 0 = 512 x 4, 512 (one CTA per SM, 2048-body i-tiles) for
+// large N; 1 = 256 x 4, 512 (two CTAs per SM) for medium N; 2 = 128 x 2, 64
+// for small N.  Unroll depth and fold length per variant come from sweeps
+// on B300 (interactions per SM per clock).  colatus_autotune times the
+// shapes that fit N and keeps the fastest.
 namespace {
 
 constexpr int kStages = 4;
+constexpr int kShapes = 3;
 
 struct F32Variant {
     int nt, ipt, jt;
@@ -37,35 +40,39 @@ struct F32Variant {
                    float);
 };
 
-template <int NT, int IPT, int JT, int FOLD, bool COMP, bool EQM, int MINB>
+template <int NT, int IPT, int JT, int FOLD, bool COMP, bool EQM, int MINB, int UNR>
 void launch_f32(int grid, cudaStream_t st, const float *pk, float4 *part, int *flags, ForceLaunch L,
                 float eps2, float mass_eq) {
     using K = F32Kernel<NT, IPT, JT, kStages, FOLD, COMP, EQM>;
-    force_f32_kernel<NT, IPT, JT, kStages, FOLD, COMP, EQM, MINB>
+    force_f32_kernel<NT, IPT, JT, kStages, FOLD, COMP, EQM, MINB, UNR>
         <<<grid, NT, K::SMEM, st>>>(pk, part, flags, L, eps2, mass_eq);
 }
 
-template <int NT, int IPT, int JT, int FOLD, bool COMP, bool EQM, int MINB>
+template <int NT, int IPT, int JT, int FOLD, bool COMP, bool EQM, int MINB, int UNR>
 F32Variant make_f32() {
     using K = F32Kernel<NT, IPT, JT, kStages, FOLD, COMP, EQM>;
     return F32Variant{NT, IPT, JT, COMP, EQM, K::SMEM,
-                      (const void *)force_f32_kernel<NT, IPT, JT, kStages, FOLD, COMP, EQM, MINB>,
-                      &launch_f32<NT, IPT, JT, FOLD, COMP, EQM, MINB>};
+                      (const void *)force_f32_kernel<NT, IPT, JT, kStages, FOLD, COMP, EQM, MINB, UNR>,
+                      &launch_f32<NT, IPT, JT, FOLD, COMP, EQM, MINB, UNR>};
 }
 
-// index = 4 * narrow + 2 * comp + eqm
-enum { V_WIDE = 0, V_NARROW = 4, V_COMP = 2, V_EQM = 1, NUM_F32_VARIANTS = 8 };
+// index = 4 * shape + 2 * comp + eqm
+enum { V_COMP = 2, V_EQM = 1, NUM_F32_VARIANTS = 4 * kShapes };
 
 const F32Variant &f32_variant(int v) {
     static const F32Variant table[NUM_F32_VARIANTS] = {
-        make_f32<256, 4, 512, 256, false, false, 2>(),
-        make_f32<256, 4, 512, 256, false, true, 2>(),
-        make_f32<256, 4, 512, 32, true, false, 2>(),
-        make_f32<256, 4, 512, 32, true, true, 2>(),
-        make_f32<128, 2, 64, 32, false, false, 4>(),
-        make_f32<128, 2, 64, 32, false, true, 4>(),
-        make_f32<128, 2, 64, 32, true, false, 4>(),
-        make_f32<128, 2, 64, 32, true, true, 4>(),
+        make_f32<512, 4, 512, 256, false, false, 1, 2>(),
+        make_f32<512, 4, 512, 256, false, true, 1, 4>(),
+        make_f32<512, 4, 512, 256, true, false, 1, 4>(),
+        make_f32<512, 4, 512, 128, true, true, 1, 2>(),
+        make_f32<256, 4, 512, 256, false, false, 2, 2>(),
+        make_f32<256, 4, 512, 256, false, true, 2, 2>(),
+        make_f32<256, 4, 512, 128, true, false, 2, 2>(),
+        make_f32<256, 4, 512, 128, true, true, 2, 2>(),
+        make_f32<128, 2, 64, 32, false, false, 4, 2>(),
+        make_f32<128, 2, 64, 32, false, true, 4, 2>(),
+        make_f32<128, 2, 64, 32, true, false, 4, 2>(),
+        make_f32<128, 2, 64, 32, true, true, 4, 2>(),
     };
     return table[v];
 }
@@ -139,6 +146,7 @@ struct colatus_ctx {
 
     // host-side bookkeeping (all deterministic, no device read needed)
     long long host_step = 0;
+    int tuned_shape = -1;      // FP32 force shape forced by tuning (-1: built-in choice)
     bool eq_mass = false;      // all masses equal (as floats): EQM force kernels
     float mass_eq = 0.f;
     // look-ahead Friedmann schedule: entries [tab_lo, tab_hi) for step size
@@ -283,6 +291,8 @@ colatus_status launched(colatus_t ctx) {
 colatus_status build_plans(colatus_t ctx) {
     for (int v = 0; v < NUM_F32_VARIANTS; ++v) {
         const F32Variant &fv = f32_variant(v);
+        if (fv.smem > 48 * 1024)
+            CU(cudaFuncSetAttribute(fv.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, fv.smem));
         int occ = 0;
         CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fv.fn, fv.nt, fv.smem));
         if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "force variant %d cannot be resident", v);
@@ -331,10 +341,20 @@ colatus_status build_plans(colatus_t ctx) {
 // CTA still gets at least four units, narrow tiles otherwise.
 // The equal-mass kernels ignore m_j, so they are used only when no zero-mass
 // padding body enters the sum (N_pad == N).
+// Built-in shape choice: the largest shape that still gives every CTA at
+// least four units; colatus_autotune / colatus_set_tuning override it.
+int default_shape(colatus_t ctx, int comp) {
+    for (int sh = 0; sh < kShapes - 1; ++sh) {
+        const ForcePlan &p = ctx->plan32[4 * sh + comp];
+        if (p.L.W >= 4LL * p.L.G) return sh;
+    }
+    return kShapes - 1;
+}
+
 const ForcePlan &plan_f32(colatus_t ctx) {
     const int comp = ctx->prec == COLATUS_FP32_COMP ? V_COMP : 0;
-    const ForcePlan *w = &ctx->plan32[V_WIDE + comp];
-    if (w->L.W < 4LL * w->L.G) w = &ctx->plan32[V_NARROW + comp];
+    const int sh = ctx->tuned_shape >= 0 ? ctx->tuned_shape : default_shape(ctx, comp);
+    const ForcePlan *w = &ctx->plan32[4 * sh + comp];
     if (ctx->eq_mass && w->n_pad == ctx->N) w += V_EQM;
     return *w;
 }
@@ -898,6 +918,12 @@ colatus_status colatus_init(colatus_t *out, int64_t N, const double *masses, dou
     ctx->num_sms = prop.multiProcessorCount;
     ctx->N = N;
     ctx->n_alloc = round_up(N, kPadAlloc);
+    colatus_status st = build_plans(ctx);
+    if (st != COLATUS_OK) return bail(st);
+    // every buffer holds the largest padded size any launch plan uses
+    for (const ForcePlan &p : ctx->plan32) ctx->n_alloc = std::max(ctx->n_alloc, p.n_pad);
+    for (const ForcePlan *p : {&ctx->plan64, &ctx->plan_vjp32, &ctx->plan_vjp64})
+        ctx->n_alloc = std::max(ctx->n_alloc, p->n_pad);
     ctx->eps = eps;
     ctx->cosmo = Cosmo{Omega_R, Omega_M, Omega_K, Omega_L, H0};
 
@@ -909,7 +935,6 @@ colatus_status colatus_init(colatus_t *out, int64_t N, const double *masses, dou
         return COLATUS_OK;
     };
     const size_t na = (size_t)ctx->n_alloc;
-    colatus_status st = COLATUS_OK;
     void **f4[] = {(void **)&ctx->xs, (void **)&ctx->vs, (void **)&ctx->vh, (void **)&ctx->acc};
     for (void **p : f4)
         if (st == COLATUS_OK) st = alloc(p, na * sizeof(float4));
@@ -947,7 +972,6 @@ colatus_status colatus_init(colatus_t *out, int64_t N, const double *masses, dou
         }
         ctx->tab_ev_covers[k] = -1;
     }
-    if ((st = build_plans(ctx)) != COLATUS_OK) return bail(st);
 
     DevClock clk{0.0, a_start, 0, 0};
     cudaMemsetAsync(ctx->flags, 0, NUM_FLAGS * sizeof(int), ctx->stream);
@@ -1647,6 +1671,61 @@ colatus_status colatus_tangent_read(colatus_t ctx, float *growth, int64_t *nrec_
         std::memcpy(growth + k * t.B, ring.data() + (s % t.cap) * t.B, t.B * sizeof(float));
     }
     return COLATUS_OK;
+}
+
+colatus_status colatus_set_tuning(colatus_t ctx, int shape) {
+    if (!ctx) return COLATUS_E_ARG;
+    if (shape < -1 || shape >= kShapes) return fail(ctx, COLATUS_E_ARG, "shape must be -1 .. %d", kShapes - 1);
+    if (shape >= 0) {
+        const ForcePlan &p = ctx->plan32[4 * shape];
+        if (p.L.W < p.L.G) return fail(ctx, COLATUS_E_ARG, "shape %d does not fit N", shape);
+    }
+    ctx->tuned_shape = shape;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_autotune(colatus_t ctx, int reps, double out_ms[3], int *chosen) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    if (reps < 1) return fail(ctx, COLATUS_E_ARG, "reps must be >= 1");
+    if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
+    if (ctx->prec == COLATUS_FP64) return fail(ctx, COLATUS_E_ARG, "the tuned kernels are FP32");
+    TRY(sync_and_check(ctx));
+    const int keep = ctx->tuned_shape;
+    const bool prof = ctx->profiling;
+    const size_t used = ctx->ev_used;
+    double best = 0.0;
+    int best_sh = -1;
+    for (int sh = 0; sh < kShapes; ++sh) {
+        if (out_ms) out_ms[sh] = 0.0;
+        if (ctx->plan32[4 * sh].L.W < ctx->plan32[4 * sh].L.G) continue;   // does not fit
+        ctx->tuned_shape = sh;
+        TRY(force_at_state(ctx));                   // warm-up launch
+        ctx->profiling = true;
+        ctx->ev_used = used;
+        for (int r = 0; r < reps; ++r) TRY(force_at_state(ctx));
+        CU(cudaStreamSynchronize(ctx->stream));
+        double ms = 0.0;
+        for (size_t k = used; k + 1 < ctx->ev_used; k += 2) {
+            float e = 0.f;
+            CU(cudaEventElapsedTime(&e, ctx->ev_pool[k], ctx->ev_pool[k + 1]));
+            ms += e;
+        }
+        ms /= reps;
+        ctx->profiling = prof;
+        ctx->ev_used = used;
+        if (out_ms) out_ms[sh] = ms;
+        if (best_sh < 0 || ms < best) {
+            best = ms;
+            best_sh = sh;
+        }
+    }
+    ctx->profiling = prof;
+    ctx->ev_used = used;
+    ctx->tuned_shape = best_sh >= 0 ? best_sh : keep;
+    ctx->spec_valid = false;   // the next step re-opens with the chosen kernel
+    if (chosen) *chosen = ctx->tuned_shape;
+    return sync_and_check(ctx);
 }
 
 const char *colatus_last_error(colatus_t ctx) { return ctx ? ctx->err : g_init_err; }

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(NT, MINB)
         for (; u < uend; ++u) {
             const bool ok = mbar_wait_bounded(&full[stage], parity);
             if (ok)
-                f32_tile<IPT, JT, FOLD, false, false>(tiles + stage * JT, nx, ny, nz, e2, hx, hy, hz,
+                f32_tile<IPT, JT, FOLD, false, false, 2>(tiles + stage * JT, nx, ny, nz, e2, hx, hy, hz,
                                                       lx, ly, lz);
             if (__syncthreads_or(!ok)) {
                 bad = true;

@@ -74,7 +74,7 @@ struct F32Kernel {
 
 // Sum one j-tile (JT bodies, pair-interleaved in shared memory) into the
 // totals of the IPT i-bodies of this thread.
-template <int IPT, int JT, int FOLD, bool COMP, bool EQM>
+template <int IPT, int JT, int FOLD, bool COMP, bool EQM, int UNR>
 __device__ __forceinline__ void f32_tile(const float4 *__restrict__ t, const float2 (&nx)[IPT],
                                          const float2 (&ny)[IPT], const float2 (&nz)[IPT],
                                          const float2 e2, float (&hx)[IPT], float (&hy)[IPT],
@@ -90,7 +90,7 @@ __device__ __forceinline__ void f32_tile(const float4 *__restrict__ t, const flo
             py[k] = make_float2(0.f, 0.f);
             pz[k] = make_float2(0.f, 0.f);
         }
-#pragma unroll 2
+#pragma unroll (UNR)
         for (int q = q0; q < q0 + FOLD; ++q) {
             const float4 A = t[2 * q];      // x0 x1 y0 y1
             const float4 B = t[2 * q + 1];  // z0 z1 m0 m1
@@ -133,7 +133,8 @@ __device__ __forceinline__ void f32_tile(const float4 *__restrict__ t, const flo
 // (N_pad bodies, N_pad a multiple of ITILE and JT).  part: segments laid out
 // [n_it][S_max][COMP ? 2 : 1][ITILE] float4 (x, y, z, 0); for COMP the
 // second plane holds the low words.  EQM: segments are scaled by mass_eq.
-template <int NT, int IPT, int JT, int STAGES, int FOLD, bool COMP, bool EQM, int MINB>
+// UNR: unroll depth of the j-pair loop (a tuning knob).
+template <int NT, int IPT, int JT, int STAGES, int FOLD, bool COMP, bool EQM, int MINB, int UNR>
 __global__ void __launch_bounds__(NT, MINB)
     force_f32_kernel(const float *__restrict__ pk, float4 *__restrict__ part, int *__restrict__ flags,
                      ForceLaunch L, float eps2, float mass_eq) {
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(NT, MINB)
         for (; u < uend; ++u) {
             const bool ok = mbar_wait_bounded(&full[stage], parity);
             if (ok)
-                f32_tile<IPT, JT, FOLD, COMP, EQM>(tiles + stage * JT, nx, ny, nz, e2, hx, hy, hz,
+                f32_tile<IPT, JT, FOLD, COMP, EQM, UNR>(tiles + stage * JT, nx, ny, nz, e2, hx, hy, hz,
                                                    lx, ly, lz);
             if (__syncthreads_or(!ok)) {
                 bad = true;

@@ -35,8 +35,8 @@ static __device__ __align__(256) float4 g_noalloc_scratch[kScratchFloat4];
 
 constexpr int kStagesNA = 4;
 // the same two FP32 shapes as colatus_forces uses for general masses
-#define NA_WIDE force_f32_kernel<256, 4, 512, kStagesNA, 256, false, false, 2>
-#define NA_NARROW force_f32_kernel<128, 2, 64, kStagesNA, 32, false, false, 4>
+#define NA_WIDE force_f32_kernel<256, 4, 512, kStagesNA, 256, false, false, 2, 2>
+#define NA_NARROW force_f32_kernel<128, 2, 64, kStagesNA, 32, false, false, 4, 2>
 using WideK = F32Kernel<256, 4, 512, kStagesNA, 256, false, false>;
 using NarrowK = F32Kernel<128, 2, 64, kStagesNA, 32, false, false>;
 

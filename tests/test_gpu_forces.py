@@ -118,3 +118,40 @@ def test_deterministic_repeat():
     a = gpu_forces(x, m, 0.01, B.FP32)
     b = gpu_forces(x, m, 0.01, B.FP32)
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2])
+@pytest.mark.parametrize("prec", [B.FP32, B.FP32_COMP])
+@pytest.mark.parametrize("workload", ["grid32", "plummer"])
+def test_every_tile_shape(shape, prec, workload):
+    ic = inputs.grid32() if workload == "grid32" else inputs.plummer_clusters(30000, 9)
+    sim = B.Simulation(ic.m, ic.eps, LCDM, 1.0, prec=prec)
+    try:
+        sim.set_state(ic.x)
+        sim.set_tuning(shape)
+        got = sim.forces()
+    finally:
+        sim.close()
+    ref = oracle.forces(ic.x, ic.m, ic.eps)
+    assert rel_rms(got, ref) < TOL[prec]
+
+
+def test_autotune_and_cache(tmp_path):
+    from paper_1208_3444_b300 import tuning
+    ic = inputs.grid32()
+    sim = B.Simulation(ic.m, ic.eps, LCDM, 1.0, prec=B.FP32_COMP)
+    try:
+        sim.set_state(ic.x)
+        shape, ms = sim.autotune(2)
+        assert shape in (0, 1, 2) and ms[shape] == min(m for m in ms if m > 0)
+        got = sim.forces()
+        path = str(tmp_path / "tune.json")
+        rec = tuning.tuned(sim, path, ic.m, "gpu")
+        again = tuning.tuned(sim, path, ic.m, "gpu")
+        assert rec == again and tuning.load(path)
+        with pytest.raises(B.ColatusError):
+            sim.set_tuning(7)
+        sim.set_tuning(-1)
+    finally:
+        sim.close()
+    assert rel_rms(got, oracle.forces(ic.x, ic.m, ic.eps)) < TOL[B.FP32_COMP]

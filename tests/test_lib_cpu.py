@@ -81,3 +81,13 @@ def test_input_recipes():
     assert len(np.unique(tr)) == 64
     tau = inputs.lcdm_tau(2000)
     assert 4.7e-4 < tau < 4.9e-4
+
+
+def test_tuning_cache_roundtrip(tmp_path):
+    from paper_1208_3444_b300 import tuning
+    p = str(tmp_path / "t.json")
+    assert tuning.load(p) == {}
+    k = tuning.key("B300", 32768, 1, True)
+    tuning.save(p, {k: {"shape": 0, "ms": [0.3, 0.4, 0.9]}})
+    assert tuning.load(p)[k]["shape"] == 0
+    assert k == "B300|N=32768|prec=1|eqmass=1"
