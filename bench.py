@@ -157,6 +157,12 @@ def barrier(ws):
         dist.barrier()
 
 
+def aggregate_throughput(ws, steps, pairs, ms_max):
+    """Whole-job interactions/s: every rank ran `steps` steps of `pairs`
+    interactions; the slowest rank's time (ms) bounds the job."""
+    return ws * steps * float(pairs) / (ms_max * 1e-3)
+
+
 def max_over_ranks(ws, x):
     if ws == 1:
         return x
@@ -259,7 +265,10 @@ def time_adjoint(B, inputs, torch, stream, nsteps=40, k=20):
             "adjoint_step_over_forward_step": (b - rec) / f,
             "backward_total_over_forward": b / f,
             "vjp_interactions_per_sm_per_clk": ic.N * ic.N / (vjp * 1e-3) /
-            (torch.cuda.get_device_properties(0).multi_processor_count * 2.032e9)}
+            (torch.cuda.get_device_properties(0).multi_processor_count * 2.032e9),
+            "vjp_frac_of_lane_op_floor": ic.N * ic.N / (vjp * 1e-3) /
+            (torch.cuda.get_device_properties(0).multi_processor_count * 2.032e9) / (128.0 / 26.0),
+            "vjp_floor_note": "26 FP32 lane-ops per interaction at 128 lane-ops/SM/clk"}
 
 
 def time_ensemble(B, inputs, torch, stream, nsteps=48):
@@ -288,7 +297,39 @@ def time_ensemble(B, inputs, torch, stream, nsteps=48):
     return {"realisations": len(ics), "N_total": int(Ns.sum()), "N_min": int(Ns.min()),
             "N_max": int(Ns.max()), "interactions_per_step": pairs, "steps": nsteps,
             "ms_per_step": ms / nsteps, "interactions_per_s": pairs * nsteps / (ms * 1e-3),
-            "graph_launches": nsteps // 16, "kernel_launches": st["launches"] - l0}
+            "graph_launches": nsteps // 16, "kernel_launches": st["launches"] - l0,
+            "interactions_per_sm_per_clk": pairs * nsteps / (ms * 1e-3) /
+            (torch.cuda.get_device_properties(0).multi_processor_count * 2.032e9),
+            "frac_of_fp32_roofline": pairs * nsteps / (ms * 1e-3) /
+            (torch.cuda.get_device_properties(0).multi_processor_count * 2.032e9) / 12.8}
+
+
+def time_tangent(B, inputs, torch, stream, ntr=64, nsteps=2):
+    """Tangent-linear propagation of 64 single-tracer perturbations through
+    the 32^3 KDK steps (FP32): one JVP launch per step for all 64 tangents."""
+    ic = inputs.grid32()
+    tau = inputs.lcdm_tau(2000)
+    sim = B.Simulation(ic.m, ic.eps, LCDM, inputs.A_START, prec=B.FP32, stream=stream.cuda_stream)
+    try:
+        sim.set_state(ic.x, ic.v)
+        sim.tangent_init(inputs.tracers(ic.N, ntr, 7), nsteps + 1)
+        sim.tangent_step(tau, 1)
+        sim.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.tangent_step(tau, nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        growth = sim.tangent_growth()
+    finally:
+        sim.close()
+    ms = e0.elapsed_time(e1) / nsteps
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    tint = float(ic.N) * ic.N * ntr
+    return {"N": ic.N, "tangents": ntr, "ms_per_step": ms,
+            "tangent_interactions_per_s": tint / (ms * 1e-3),
+            "tangent_interactions_per_sm_per_clk": tint / (ms * 1e-3) / (nsm * 2.032e9),
+            "finite": bool(np.all(np.isfinite(growth)))}
 
 
 def run_colatus(args, ws, rank, local):
@@ -340,7 +381,7 @@ def run_colatus(args, ws, rank, local):
     sim.synchronize()
 
     step_ms_max = max_over_ranks(ws, step_ms)
-    value = ws * K * float(N) * N / (step_ms_max * 1e-3)
+    value = aggregate_throughput(ws, K, float(N) * N, step_ms_max)
 
     # end to end through the C ABI with host buffers: the initial state from
     # pinned host memory, then per step the paper's host loop (Appendix A,
@@ -372,6 +413,8 @@ def run_colatus(args, ws, rank, local):
         force128 = time_force_128(B, inputs, torch)
     adjoint = time_adjoint(B, inputs, torch, stream)
     ensemble = time_ensemble(B, inputs, torch, stream)
+    tangent = time_tangent(B, inputs, torch, stream)
+    pipes = B.colatus_probe_pipes()
     if rank == 0:
         peaks = {}
         try:
@@ -413,6 +456,10 @@ def run_colatus(args, ws, rank, local):
             "force_128cubed": force128,
             "adjoint": adjoint,
             "ensemble": ensemble,
+            "tangent": tangent,
+            "pipe_rates": {**pipes, "unit": "lane-ops (MUFU: results) per SM per clock",
+                           "what": "colatus_probe_pipes: independent chains of FFMA, FFMA2 "
+                                   "(f32x2), MUFU.RSQ"},
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,

@@ -280,6 +280,12 @@ colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps);
  * to query *nrec_out.  Synchronises. */
 colatus_status colatus_tangent_read(colatus_t ctx, float *growth, int64_t *nrec_out);
 
+/* Microbenchmark of the pipes the force roofline assumes, on the current
+ * device: out[0] scalar FFMA lane-ops, out[1] packed FFMA2 (f32x2) lane-ops,
+ * out[2] MUFU.RSQ results, each per SM per SM clock (independent chains, so
+ * throughput-bound); out[3] SMs; out[4] blocks per SM used. */
+colatus_status colatus_probe_pipes(double out[6]);
+
 /* Release every device and host resource of ctx (NULL is a no-op). */
 void colatus_destroy(colatus_t ctx);
 

@@ -36,7 +36,7 @@ EXPORTS = ("colatus_init", "colatus_set_config", "colatus_set_masses", "colatus_
            "colatus_ensemble_forces", "colatus_ensemble_step", "colatus_ensemble_synchronize",
            "colatus_ensemble_stats", "colatus_ensemble_last_error", "colatus_ensemble_destroy",
            "colatus_tangent_init", "colatus_tangent_step", "colatus_tangent_read",
-           "colatus_autotune", "colatus_set_tuning")
+           "colatus_autotune", "colatus_set_tuning", "colatus_probe_pipes")
 
 
 class ColatusError(RuntimeError):
@@ -88,6 +88,7 @@ def lib():
         "colatus_tangent_init": [_vp, _vp, _int, _vp, _i64],
         "colatus_autotune": [_vp, _int, _vp, _vp],
         "colatus_set_tuning": [_vp, _int],
+        "colatus_probe_pipes": [_vp],
         "colatus_tangent_step": [_vp, _dbl, _i64],
         "colatus_tangent_read": [_vp, _vp, _vp],
     }
@@ -295,6 +296,14 @@ def colatus_forces_noalloc(pos, eps, G, a, acc_out, stream=None):
                                       None if stream is None else int(stream))
     if st != OK:
         raise ColatusError(st, "colatus_forces_noalloc")
+
+
+def colatus_probe_pipes():
+    """Measured lane-ops per SM per clock: {'ffma', 'ffma2', 'mufu_rsq', 'sms'}."""
+    out = np.zeros(6)
+    _check(lib().colatus_probe_pipes(out.ctypes.data), None)
+    return {"ffma": float(out[0]), "ffma2": float(out[1]), "mufu_rsq": float(out[2]),
+            "sms": int(out[3])}
 
 
 def colatus_last_error(h=None):

@@ -14,6 +14,7 @@
 #include "ensemble.cuh"
 #include "force.cuh"
 #include "integrate.cuh"
+#include "probe.cuh"
 #include "tangent.cuh"
 
 using namespace colatus;
@@ -1726,6 +1727,47 @@ colatus_status colatus_autotune(colatus_t ctx, int reps, double out_ms[3], int *
     ctx->spec_valid = false;   // the next step re-opens with the chosen kernel
     if (chosen) *chosen = ctx->tuned_shape;
     return sync_and_check(ctx);
+}
+
+colatus_status colatus_probe_pipes(double out[6]) {
+    colatus_t ctx = nullptr;
+    if (!out) return fail(nullptr, COLATUS_E_ARG, "out is NULL");
+    int dev = 0, nsm = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int threads = 256, per_sm = 4, iters = 4096;
+    const int blocks = nsm * per_sm;
+    float *sink = nullptr;
+    long long *cyc = nullptr;
+    CU(cudaMalloc(&sink, threads * sizeof(float)));
+    CU(cudaMalloc(&cyc, blocks * sizeof(long long)));
+    std::vector<long long> h(blocks);
+    colatus_status st = COLATUS_OK;
+    for (int kind = 0; kind < 3 && st == COLATUS_OK; ++kind) {
+        cudaMemset(cyc, 0, blocks * sizeof(long long));
+        for (int rep = 0; rep < 2; ++rep) {   // the second run is timed (warm)
+            cudaMemset(cyc, 0, blocks * sizeof(long long));
+            if (kind == 0) probe_pipe_kernel<0><<<blocks, threads>>>(iters, 0.5f, sink, cyc);
+            if (kind == 1) probe_pipe_kernel<1><<<blocks, threads>>>(iters, 0.5f, sink, cyc);
+            if (kind == 2) probe_pipe_kernel<2><<<blocks, threads>>>(iters, 0.5f, sink, cyc);
+        }
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemcpy(h.data(), cyc, blocks * sizeof(long long), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            st = fail(nullptr, COLATUS_E_CUDA, "probe: %s", cudaGetErrorString(e));
+            break;
+        }
+        long long mx = 1;
+        for (long long c : h) mx = std::max(mx, c);
+        const double lanes = (double)per_sm * threads * iters * kProbeChains * (kind == 1 ? 2.0 : 1.0);
+        out[kind] = lanes / (double)mx;
+    }
+    cudaFree(sink);
+    cudaFree(cyc);
+    out[3] = nsm;
+    out[4] = per_sm;
+    out[5] = 0.0;
+    return st;
 }
 
 const char *colatus_last_error(colatus_t ctx) { return ctx ? ctx->err : g_init_err; }
