@@ -28,6 +28,8 @@ __all__ = [
     "friedmann_advance", "forces", "forces_pairwise", "potential", "vjp", "jvp",
     "kick_coefficients", "schedule", "run", "diagnostics", "layzer_irvine",
     "adjoint_run", "tangent_run", "ftle", "num_threads", "PINS",
+    "deformation_force", "deformation_vjp", "deformation_jvp", "total_force",
+    "velocity_spectrum",
 ]
 
 # Parity pin of every oracle function: which non-oracle fact each one is
@@ -47,6 +49,12 @@ PINS = {
            "time reversibility, Layzer-Irvine tau^2 convergence",
     "adjoint_run": "central finite differences of a trajectory loss",
     "tangent_run": "finite differences of trajectories; adjoint duality",
+    "deformation_force": "equals the Eq. 1 pull of an extra body of mass C psi / G fixed at "
+                         "x_psi (the paper's own description); single-body closed form",
+    "deformation_vjp/jvp": "central finite differences of deformation_force",
+    "velocity_spectrum": "pure sinusoid closed form (peak height, Hann side lobes 1/4), "
+                         "Parseval identity with and without the window, numpy.fft.rfft, "
+                         "constant series",
 }
 
 
@@ -193,6 +201,47 @@ def jvp(x, m, dx, eps: float, G: float = 1.0, dm=None, rows=None) -> np.ndarray:
     return out
 
 
+# --------------------------------------------------- Eq. 6 deformation term
+def deformation_force(x, Cpsi: float, xpsi, eps: float) -> np.ndarray:
+    """The deformation term of Eq. 6 in the attractive reading of R1:
+    C psi (x_psi - x_k) / (|x_k - x_psi|^2 + eps^2)^{3/2} for every body k, the
+    pull of a fixed point "mass" C psi at x_psi (no G factor)."""
+    d = np.asarray(xpsi, dtype=np.float64)[None, :] - _d(x).reshape(-1, 3)
+    s2 = np.sum(d * d, axis=1) + eps * eps
+    return Cpsi * d / (s2 * np.sqrt(s2))[:, None]
+
+
+def _defo_J_apply(x, Cpsi, xpsi, eps, w):
+    """-C psi J(d_k) w_k with d_k = x_psi - x_k, J(d) = I/s^3 - 3 d d^T / s^5:
+    the derivative of deformation_force along w (J is symmetric)."""
+    d = np.asarray(xpsi, dtype=np.float64)[None, :] - _d(x).reshape(-1, 3)
+    w = _d(w).reshape(-1, 3)
+    s2 = np.sum(d * d, axis=1) + eps * eps
+    inv3 = 1.0 / (s2 * np.sqrt(s2))
+    inv5 = inv3 / s2
+    dw = np.sum(d * w, axis=1)
+    return -Cpsi * (w * inv3[:, None] - 3.0 * d * (dw * inv5)[:, None])
+
+
+def deformation_vjp(x, Cpsi: float, xpsi, eps: float, lam) -> np.ndarray:
+    """d(sum_k lam_k . deformation_force_k)/dx."""
+    return _defo_J_apply(x, Cpsi, xpsi, eps, lam)
+
+
+def deformation_jvp(x, Cpsi: float, xpsi, eps: float, dx) -> np.ndarray:
+    """Directional derivative of deformation_force along dx."""
+    return _defo_J_apply(x, Cpsi, xpsi, eps, dx)
+
+
+def total_force(x, m, eps: float, G: float, defo=None) -> np.ndarray:
+    """F of Eq. 1 (attractive), plus the Eq. 6 deformation term when
+    defo = (C psi, x_psi) is given."""
+    F = forces(x, m, eps, G)
+    if defo is not None:
+        F = F + deformation_force(x, defo[0], defo[1], eps)
+    return F
+
+
 # ------------------------------------------------- Eqs. 3-5 and KDK variant
 def kick_coefficients(a: float, H: float, h: float):
     """Trapezoidal Hubble-drag kick over a span h (Eq. 4 with tau -> h):
@@ -236,7 +285,7 @@ def schedule(cosmo: Cosmology, a_start: float, tau: float, nsteps: int,
 
 def run(x, v, m, eps: float, G: float, cosmo: Cosmology, a_start: float,
         tau: float, nsteps: int, scheme: str = "kdk", nsub: int = 8,
-        tracers=None, keep_states: bool = False, diag_every: int = 0):
+        tracers=None, keep_states: bool = False, diag_every: int = 0, defo=None):
     """Integrate Eq. 1 with the Hubble-drag leapfrog for nsteps.
 
     DKD follows Eqs. 3-5 literally:
@@ -250,6 +299,7 @@ def run(x, v, m, eps: float, G: float, cosmo: Cosmology, a_start: float,
     F is the raw Eq. 1 force; a^-3 sits in d.  Returns a dict with the final
     x, v, the schedule, tracer records [nsteps, ntr, 6] (x, v after each step),
     optional per-step states and diagnostics every diag_every steps.
+    defo = (C psi, x_psi) adds the Eq. 6 deformation term to F.
     """
     x = _d(x).reshape(-1, 3).copy()
     v = _d(v).reshape(-1, 3).copy()
@@ -261,18 +311,18 @@ def run(x, v, m, eps: float, G: float, cosmo: Cosmology, a_start: float,
     diags = []
     if diag_every:
         diags.append((0, diagnostics(x, v, m, sch["a"][0], eps, G, cosmo)))
-    F = forces(x, m, eps, G) if scheme == "kdk" else None
+    F = total_force(x, m, eps, G, defo) if scheme == "kdk" else None
     for n in range(nsteps):
         if keep_states:
             states.append((x.copy(), v.copy()))
         if scheme == "dkd":
             xh = x + 0.5 * tau * v
-            v = sch["c"][n] * v + sch["d"][n] * forces(xh, m, eps, G)
+            v = sch["c"][n] * v + sch["d"][n] * total_force(xh, m, eps, G, defo)
             x = xh + 0.5 * tau * v
         else:
             vh = sch["c1"][n] * v + sch["d1"][n] * F
             x = x + tau * vh
-            F = forces(x, m, eps, G)
+            F = total_force(x, m, eps, G, defo)
             v = sch["c2"][n] * vh + sch["d2"][n] * F
         if tr is not None:
             rec[n, :, :3] = x[tr]
@@ -330,7 +380,7 @@ def layzer_irvine(diags, t):
 # ---------------------------------------------------- discrete adjoint
 def adjoint_run(x0, v0, m, eps: float, G: float, cosmo: Cosmology, a_start: float,
                 tau: float, nsteps: int, gx_T, gv_T, gm_T=None,
-                scheme: str = "kdk", nsub: int = 8):
+                scheme: str = "kdk", nsub: int = 8, defo=None):
     """Exact transpose of the discrete leapfrog of ``run``.
 
     Given dLoss/dx^N, dLoss/dv^N (and an explicit dLoss/dm), returns
@@ -339,7 +389,15 @@ def adjoint_run(x0, v0, m, eps: float, G: float, cosmo: Cosmology, a_start: floa
     Every state of the forward pass is stored (no checkpointing).
     """
     m = _d(m).reshape(-1)
-    fw = run(x0, v0, m, eps, G, cosmo, a_start, tau, nsteps, scheme, nsub, keep_states=True)
+    fw = run(x0, v0, m, eps, G, cosmo, a_start, tau, nsteps, scheme, nsub, keep_states=True,
+             defo=defo)
+
+    def vjp_total(xx, w):
+        gx_, gm_ = vjp(xx, m, w, eps, G)
+        if defo is not None:
+            gx_ = gx_ + deformation_vjp(xx, defo[0], defo[1], eps, w)
+        return gx_, gm_
+
     sch, states = fw["schedule"], fw["states"]
     lx = _d(gx_T).reshape(-1, 3).copy()
     lv = _d(gv_T).reshape(-1, 3).copy()
@@ -353,7 +411,7 @@ def adjoint_run(x0, v0, m, eps: float, G: float, cosmo: Cosmology, a_start: floa
             lv = lv + 0.5 * tau * lx
             # v^{n+1} = c v^n + d F(xh)
             w = sch["d"][n] * lv
-            gx_, gm_ = vjp(xh, m, w, eps, G)
+            gx_, gm_ = vjp_total(xh, w)
             lxh = lxh + gx_
             gm = gm + gm_
             lv = sch["c"][n] * lv
@@ -361,12 +419,12 @@ def adjoint_run(x0, v0, m, eps: float, G: float, cosmo: Cosmology, a_start: floa
             lx = lxh
             lv = lv + 0.5 * tau * lxh
         else:
-            vh = sch["c1"][n] * v + sch["d1"][n] * forces(x, m, eps, G)
+            vh = sch["c1"][n] * v + sch["d1"][n] * total_force(x, m, eps, G, defo)
             x1 = x + tau * vh
             # v^{n+1} = c2 vh + d2 F(x^{n+1})
             lvh = sch["c2"][n] * lv
             w = sch["d2"][n] * lv
-            gx_, gm_ = vjp(x1, m, w, eps, G)
+            gx_, gm_ = vjp_total(x1, w)
             lx1 = lx + gx_
             gm = gm + gm_
             # x^{n+1} = x^n + tau vh
@@ -374,7 +432,7 @@ def adjoint_run(x0, v0, m, eps: float, G: float, cosmo: Cosmology, a_start: floa
             lx = lx1
             # vh = c1 v^n + d1 F(x^n)
             w = sch["d1"][n] * lvh
-            gx_, gm_ = vjp(x, m, w, eps, G)
+            gx_, gm_ = vjp_total(x, w)
             lx = lx + gx_
             gm = gm + gm_
             lv = sch["c1"][n] * lvh
@@ -384,7 +442,7 @@ def adjoint_run(x0, v0, m, eps: float, G: float, cosmo: Cosmology, a_start: floa
 # --------------------------------------------------------- tangent model
 def tangent_run(x0, v0, m, eps: float, G: float, cosmo: Cosmology, a_start: float,
                 tau: float, nsteps: int, dx0, dv0, scheme: str = "kdk", nsub: int = 8,
-                dm=None):
+                dm=None, defo=None):
     """Linearisation of ``run`` along (dx0, dv0[, dm]): returns the final
     tangent (dx, dv) and the per-step tangent states [nsteps+1] of (dx, dv)."""
     m = _d(m).reshape(-1)
@@ -394,25 +452,30 @@ def tangent_run(x0, v0, m, eps: float, G: float, cosmo: Cosmology, a_start: floa
     dv = _d(dv0).reshape(-1, 3).copy()
     sch = schedule(cosmo, a_start, tau, nsteps, scheme, nsub)
     hist = [(dx.copy(), dv.copy())]
+
+    def fj(xx, ddx):
+        F_ = total_force(xx, m, eps, G, defo)
+        dF_ = jvp(xx, m, ddx, eps, G, dm=dm)
+        if defo is not None:
+            dF_ = dF_ + deformation_jvp(xx, defo[0], defo[1], eps, ddx)
+        return F_, dF_
+
     for n in range(nsteps):
         if scheme == "dkd":
             xh = x + 0.5 * tau * v
             dxh = dx + 0.5 * tau * dv
-            F = forces(xh, m, eps, G)
-            dF = jvp(xh, m, dxh, eps, G, dm=dm)
+            F, dF = fj(xh, dxh)
             v = sch["c"][n] * v + sch["d"][n] * F
             dv = sch["c"][n] * dv + sch["d"][n] * dF
             x = xh + 0.5 * tau * v
             dx = dxh + 0.5 * tau * dv
         else:
-            F = forces(x, m, eps, G)
-            dF = jvp(x, m, dx, eps, G, dm=dm)
+            F, dF = fj(x, dx)
             vh = sch["c1"][n] * v + sch["d1"][n] * F
             dvh = sch["c1"][n] * dv + sch["d1"][n] * dF
             x = x + tau * vh
             dx = dx + tau * dvh
-            F = forces(x, m, eps, G)
-            dF = jvp(x, m, dx, eps, G, dm=dm)
+            F, dF = fj(x, dx)
             v = sch["c2"][n] * vh + sch["d2"][n] * F
             dv = sch["c2"][n] * dvh + sch["d2"][n] * dF
         hist.append((dx.copy(), dv.copy()))
@@ -440,3 +503,46 @@ def ftle(x0, v0, m, eps: float, G: float, cosmo: Cosmology, a_start: float,
         g = math.sqrt(float(np.sum(dxn[tracer] ** 2) + np.sum(dvn[tracer] ** 2)))
         out[n - 1] = math.log(g / g0) / (n * tau)
     return out
+
+
+# --------------------------------------- tracer velocity energy spectrum
+def velocity_spectrum(v, dt: float, window: str = "rect", detrend: bool = True) -> np.ndarray:
+    """One-sided energy spectrum of each tracer's velocity record (Sec. I and
+    Sec. IV: the velocity of single bodies at every step, and its energy power
+    spectrum, for chaotic-advection analysis).
+
+    v: [T, ntr, 3] velocities at uniform spacing dt.  With u = v - mean(v)
+    (detrend) or u = v, w the rectangular or periodic Hann window
+    w_n = (1 - cos(2 pi n / T)) / 2 and U = (1/T) sum_n w_n^2,
+
+        E_k(f_j) = c_j dt / (T U) * (1/2) sum_c |sum_n w_n u_{n,k,c} e^{-2 pi i j n / T}|^2
+
+    for j = 0 .. floor(T/2), f_j = j / (T dt), c_j = 2 except c_0 = 1 and
+    c_{T/2} = 1 (T even).  Then sum_j E_k(f_j) / (T dt) is the window-weighted
+    mean of (1/2)|u|^2, i.e. the specific kinetic energy of the fluctuation
+    (Parseval).  Returns E [ntr, floor(T/2)+1].  The DFT is the explicit sum
+    (a matrix product with the exponential table), in double precision.
+    """
+    v = np.asarray(v, dtype=np.float64)
+    T = v.shape[0]
+    u = v - v.mean(axis=0, keepdims=True) if detrend else v.copy()
+    n = np.arange(T)
+    if window == "hann":
+        w = 0.5 * (1.0 - np.cos(2.0 * np.pi * n / T))
+    elif window == "rect":
+        w = np.ones(T)
+    else:
+        raise ValueError(window)
+    U = float(np.sum(w * w)) / T
+    nf = T // 2 + 1
+    j = np.arange(nf)
+    # reduce j n mod T before forming the angle, so the table is exact to rounding
+    ang = 2.0 * np.pi * ((j[:, None] * n[None, :]) % T) / T
+    Ereal = np.cos(ang) @ (w[:, None, None] * u).reshape(T, -1)
+    Eimag = -np.sin(ang) @ (w[:, None, None] * u).reshape(T, -1)
+    power = (Ereal ** 2 + Eimag ** 2).reshape(nf, v.shape[1], 3).sum(axis=2)
+    c = np.full(nf, 2.0)
+    c[0] = 1.0
+    if T % 2 == 0:
+        c[-1] = 1.0
+    return (0.5 * c[:, None] * dt / (T * U) * power).T
