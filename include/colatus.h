@@ -88,6 +88,14 @@ colatus_status colatus_init(colatus_t *out, int64_t N, const double *masses, dou
 colatus_status colatus_set_config(colatus_t ctx, colatus_prec prec, colatus_scheme scheme,
                                   double G, void *cuda_stream);
 
+/* Deformation potential of Eq. 6: adds to every body's pull
+ *     C psi (x_psi - x_k) / (|x_k - x_psi|^2 + eps^2)^{3/2}
+ * inside the a^-3-scaled force (the pull of a point "mass" C psi / G fixed at
+ * x_psi, host double[3]).  C psi = 0 switches it off.  It enters the forces,
+ * the steps, the adjoint and the tangent model (not the ensemble).  Needs
+ * G != 0 (COLATUS_E_ARG otherwise). */
+colatus_status colatus_set_deformation(colatus_t ctx, double Cpsi, const double *x_psi);
+
 /* Replace the N masses (dtype elements, host or device). */
 colatus_status colatus_set_masses(colatus_t ctx, const void *m, int dtype, int on_device);
 
@@ -140,6 +148,36 @@ colatus_status colatus_read_tracers(colatus_t ctx, float *xv_out, int64_t *nrec_
  *   out[14] W_x = -(G/2) sum_{j != k} m_k m_j / s_kj   out[15] step count
  * (K + W obeys the Layzer-Irvine equation d(K+W)/dt = -H (2K + W)). */
 colatus_status colatus_diagnostics(colatus_t ctx, double out[COLATUS_NDIAG]);
+
+/* ---- Tracer velocity energy spectrum (Sec. I, Sec. IV: the velocity of
+ * single bodies at every step and its energy power spectrum).
+ *
+ * For T samples per tracer at uniform spacing dt, u = v - mean(v) when
+ * detrend != 0 (else u = v), w_n = 1 (window 0) or the periodic Hann window
+ * (1 - cos(2 pi n / T)) / 2 (window 1), U = (1/T) sum_n w_n^2:
+ *     E_k(f_j) = c_j dt / (T U) * 1/2 sum_c |sum_n w_n u_{n,k,c} e^{-2 pi i j n/T}|^2
+ * for j = 0 .. T/2 (integer division), f_j = j / (T dt); c_j = 2 except
+ * c_0 = 1 and c_{T/2} = 1 for even T.  Then sum_j E_k(f_j) / (T dt) is the
+ * window-weighted mean of |u|^2 / 2 (Parseval).  Computed on the GPU in FP64
+ * by a direct DFT with exactly reduced angles.  Output E is [ntr][T/2 + 1]
+ * doubles, row-major.  Needs 2 <= T <= 2^24. */
+
+/* Spectrum of a velocity series v laid out [T][ntr][stride] (dtype
+ * elements; the three velocity components are the first three of each
+ * stride).  on_device / out_on_device say where v and E_out live.  Runs on
+ * cuda_stream (NULL: the legacy default stream) and synchronises it unless both
+ * v and E_out are device memory.  Errors: colatus_last_error(NULL). */
+colatus_status colatus_velocity_spectrum(const void *v, int dtype, int on_device, int64_t T,
+                                         int64_t ntr, int64_t stride, double dt, int window,
+                                         int detrend, double *E_out, int out_on_device,
+                                         void *cuda_stream);
+
+/* Spectrum of the velocities recorded by colatus_record_tracers (the kept
+ * records, oldest first, read in place on the device); dt is the step size
+ * the records were taken with.  *nrec_out = T used; E_out (host) may be NULL
+ * to query it.  COLATUS_E_STATE if nothing is recorded.  Synchronises. */
+colatus_status colatus_tracer_spectrum(colatus_t ctx, double dt, int window, int detrend,
+                                       double *E_out, int64_t *nrec_out);
 
 /* Human-readable description of the last error on ctx ("" if none);
  * colatus_last_error(NULL) describes the last colatus_init failure. */

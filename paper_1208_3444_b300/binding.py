@@ -36,7 +36,8 @@ EXPORTS = ("colatus_init", "colatus_set_config", "colatus_set_masses", "colatus_
            "colatus_ensemble_forces", "colatus_ensemble_step", "colatus_ensemble_synchronize",
            "colatus_ensemble_stats", "colatus_ensemble_last_error", "colatus_ensemble_destroy",
            "colatus_tangent_init", "colatus_tangent_step", "colatus_tangent_read",
-           "colatus_autotune", "colatus_set_tuning", "colatus_probe_pipes")
+           "colatus_autotune", "colatus_set_tuning", "colatus_probe_pipes",
+           "colatus_set_deformation", "colatus_velocity_spectrum", "colatus_tracer_spectrum")
 
 
 class ColatusError(RuntimeError):
@@ -89,6 +90,10 @@ def lib():
         "colatus_autotune": [_vp, _int, _vp, _vp],
         "colatus_set_tuning": [_vp, _int],
         "colatus_probe_pipes": [_vp],
+        "colatus_set_deformation": [_vp, _dbl, _vp],
+        "colatus_velocity_spectrum": [_vp, _int, _int, _i64, _i64, _i64, _dbl, _int, _int, _vp,
+                                      _int, _vp],
+        "colatus_tracer_spectrum": [_vp, _dbl, _int, _int, _vp, _vp],
         "colatus_tangent_step": [_vp, _dbl, _i64],
         "colatus_tangent_read": [_vp, _vp, _vp],
     }
@@ -306,6 +311,44 @@ def colatus_probe_pipes():
             "sms": int(out[3])}
 
 
+WINDOWS = {"rect": 0, "hann": 1}
+
+
+def colatus_velocity_spectrum(v, dt, window="rect", detrend=True, out=None, stream=None,
+                              offset=0):
+    """Energy spectrum of a [T, ntr, stride] velocity series, host or CUDA,
+    whose components sit at [offset, offset + 3) of each stride (a tracer
+    record [T, ntr, 6] has offset 3); returns E [ntr, T//2 + 1] float64
+    (``out`` if given, which may be a CUDA float64 tensor)."""
+    ptr, on_dev, dtype, keep = _buf(v)
+    shape = tuple(v.shape)
+    if len(shape) != 3 or offset < 0 or shape[2] < offset + 3:
+        raise ValueError("v must be [T, ntr, stride >= offset + 3]")
+    T, ntr, stride = shape
+    ptr += offset * (8 if dtype == F64 else 4)
+    nf = T // 2 + 1
+    if out is None:
+        out = np.empty((ntr, nf), dtype=np.float64)
+    optr, out_dev, odt, okeep = _buf(out)
+    if odt != F64 or tuple(out.shape) != (ntr, nf):
+        raise ValueError("out must be float64 [ntr, T//2 + 1]")
+    sp = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(lib().colatus_velocity_spectrum(ptr, dtype, on_dev, T, ntr, stride, float(dt),
+                                           WINDOWS[window], int(bool(detrend)), optr, out_dev,
+                                           sp or None), None)
+    return out
+
+
+def colatus_tracer_spectrum(h, ntr, dt, window="rect", detrend=True):
+    n = ctypes.c_int64()
+    _check(lib().colatus_tracer_spectrum(h, float(dt), WINDOWS[window], int(bool(detrend)), None,
+                                         ctypes.byref(n)), h)
+    out = np.empty((ntr, n.value // 2 + 1), dtype=np.float64)
+    _check(lib().colatus_tracer_spectrum(h, float(dt), WINDOWS[window], int(bool(detrend)),
+                                         out.ctypes.data, ctypes.byref(n)), h)
+    return out
+
+
 def colatus_last_error(h=None):
     s = lib().colatus_last_error(h)
     return s.decode() if s else ""
@@ -345,6 +388,10 @@ class Simulation:
     def set_masses(self, m):
         colatus_set_masses(self.h, m)
 
+    def set_deformation(self, Cpsi, x_psi=(0.0, 0.0, 0.0)):
+        xp = np.ascontiguousarray(np.asarray(x_psi, dtype=np.float64))
+        _check(lib().colatus_set_deformation(self.h, float(Cpsi), xp.ctypes.data), self.h)
+
     def state(self, dtype=np.float64):
         x = np.empty((self.N, 3), dtype=dtype)
         v = np.empty((self.N, 3), dtype=dtype)
@@ -368,6 +415,10 @@ class Simulation:
 
     def read_tracers(self):
         return colatus_read_tracers(self.h, getattr(self, "ntr", 0))
+
+    def tracer_spectrum(self, dt, window="rect", detrend=True):
+        """Energy spectrum [ntr, nrec//2 + 1] of the recorded tracer velocities."""
+        return colatus_tracer_spectrum(self.h, getattr(self, "ntr", 0), dt, window, detrend)
 
     def diagnostics(self):
         return dict(zip(DIAG_NAMES, colatus_diagnostics(self.h)))

@@ -423,19 +423,42 @@ __device__ __forceinline__ void store_grad(void *gx, void *gm, int out_f64, long
     }
 }
 
+// Bodies and co-vector of entry i of the packed VJP input.
+__device__ __forceinline__ void pkw_load(const float *pkw, long long i, float &x, float &y, float &z,
+                                         float &wx, float &wy, float &wz) {
+    const float *p = pkw + (i >> 1) * 16 + (i & 1);
+    x = p[0];
+    y = p[2];
+    z = p[4];
+    wx = p[8];
+    wy = p[10];
+    wz = p[12];
+}
+
 __global__ void vjp_out_f32_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
-                                   long long N, void *gx, void *gm, int out_f64) {
+                                   long long N, void *gx, void *gm, int out_f64,
+                                   const float *__restrict__ pkw, Defo D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const float4 g = reduce_vjp_f32(part, L, itile, i);
+    float4 g = reduce_vjp_f32(part, L, itile, i);
+    if (D.on) {
+        float x, y, z, wx, wy, wz;
+        pkw_load(pkw, i, x, y, z, wx, wy, wz);
+        defo_jacobian<float>(D, x, y, z, wx, wy, wz, g.x, g.y, g.z);
+    }
     store_grad<float4, float>(gx, gm, out_f64, i, g.x, g.y, g.z, g.w);
 }
 
 __global__ void vjp_out_f64_kernel(const double4 *__restrict__ part, ForceLaunch L, int itile,
-                                   long long N, void *gx, void *gm, int out_f64) {
+                                   long long N, void *gx, void *gm, int out_f64,
+                                   const double4 *__restrict__ bw, Defo D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const double4 g = reduce_vjp_f64(part, L, itile, i);
+    double4 g = reduce_vjp_f64(part, L, itile, i);
+    if (D.on) {
+        const double4 p = bw[2 * i], w = bw[2 * i + 1];
+        defo_jacobian<double>(D, p.x, p.y, p.z, w.x, w.y, w.z, g.x, g.y, g.z);
+    }
     store_grad<double4, double>(gx, gm, out_f64, i, g.x, g.y, g.z, g.w);
 }
 
@@ -494,14 +517,19 @@ __global__ void adj_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
                                     const float4 *__restrict__ xn, float4 *lx, float4 *lv,
                                     float4 *lvh, float *lm, const StepCoef *__restrict__ table,
                                     long long n, double tau, float *pkw, long long N,
-                                    long long N_pad) {
+                                    long long N_pad, Defo D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N_pad) return;
     if (i >= N) {
         pkw_store(pkw, i, make_float4(0.f, 0.f, 0.f, 0.f), 0.f, 0.f, 0.f);
         return;
     }
-    const float4 g = reduce_vjp_f32(part, L, itile, i);
+    float4 g = reduce_vjp_f32(part, L, itile, i);
+    if (D.on) {   // deformation term at x_{n+1} with W_{n+1} (still in pkw)
+        float x, y, z, wx, wy, wz;
+        pkw_load(pkw, i, x, y, z, wx, wy, wz);
+        defo_jacobian<float>(D, x, y, z, wx, wy, wz, g.x, g.y, g.z);
+    }
     float4 ax = lx[i];
     ax.x += g.x;
     ax.y += g.y;
@@ -520,10 +548,16 @@ __global__ void adj_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
 }
 
 __global__ void adj_final_f32_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
-                                     float4 *lx, float *lm, long long N) {
+                                     float4 *lx, float *lm, long long N,
+                                     const float *__restrict__ pkw, Defo D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const float4 g = reduce_vjp_f32(part, L, itile, i);
+    float4 g = reduce_vjp_f32(part, L, itile, i);
+    if (D.on) {
+        float x, y, z, wx, wy, wz;
+        pkw_load(pkw, i, x, y, z, wx, wy, wz);
+        defo_jacobian<float>(D, x, y, z, wx, wy, wz, g.x, g.y, g.z);
+    }
     float4 ax = lx[i];
     ax.x += g.x;
     ax.y += g.y;
@@ -558,7 +592,7 @@ __global__ void adj_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
                                     const double4 *__restrict__ xn, double4 *lx, double4 *lv,
                                     double4 *lvh, double *lm, const StepCoef *__restrict__ table,
                                     long long n, double tau, double4 *bw, long long N,
-                                    long long N_pad) {
+                                    long long N_pad, Defo D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N_pad) return;
     if (i >= N) {
@@ -566,7 +600,11 @@ __global__ void adj_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
         bw[2 * i + 1] = make_double4(0.0, 0.0, 0.0, 0.0);
         return;
     }
-    const double4 g = reduce_vjp_f64(part, L, itile, i);
+    double4 g = reduce_vjp_f64(part, L, itile, i);
+    if (D.on) {
+        const double4 p = bw[2 * i], w = bw[2 * i + 1];
+        defo_jacobian<double>(D, p.x, p.y, p.z, w.x, w.y, w.z, g.x, g.y, g.z);
+    }
     double4 ax = lx[i];
     ax.x += g.x;
     ax.y += g.y;
@@ -586,10 +624,15 @@ __global__ void adj_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
 }
 
 __global__ void adj_final_f64_kernel(const double4 *__restrict__ part, ForceLaunch L, int itile,
-                                     double4 *lx, double *lm, long long N) {
+                                     double4 *lx, double *lm, long long N,
+                                     const double4 *__restrict__ bw, Defo D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const double4 g = reduce_vjp_f64(part, L, itile, i);
+    double4 g = reduce_vjp_f64(part, L, itile, i);
+    if (D.on) {
+        const double4 p = bw[2 * i], w = bw[2 * i + 1];
+        defo_jacobian<double>(D, p.x, p.y, p.z, w.x, w.y, w.z, g.x, g.y, g.z);
+    }
     double4 ax = lx[i];
     ax.x += g.x;
     ax.y += g.y;

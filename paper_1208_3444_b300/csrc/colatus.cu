@@ -15,6 +15,7 @@
 #include "force.cuh"
 #include "integrate.cuh"
 #include "probe.cuh"
+#include "spectrum.cuh"
 #include "tangent.cuh"
 
 using namespace colatus;
@@ -148,6 +149,8 @@ struct colatus_ctx {
     // host-side bookkeeping (all deterministic, no device read needed)
     long long host_step = 0;
     int tuned_shape = -1;      // FP32 force shape forced by tuning (-1: built-in choice)
+    double defo_C = 0.0;       // Eq. 6 deformation strength C psi (0: off)
+    double defo_x[3] = {0.0, 0.0, 0.0};
     bool eq_mass = false;      // all masses equal (as floats): EQM force kernels
     float mass_eq = 0.f;
     // look-ahead Friedmann schedule: entries [tab_lo, tab_hi) for step size
@@ -514,6 +517,18 @@ colatus_status sync_and_check(colatus_t ctx) {
 
 size_t elem_size(int dtype) { return dtype == COLATUS_F64 ? 8 : 4; }
 
+// Deformation term for the kernels: the G-less kappa = C psi / G.
+Defo defo_args(colatus_t ctx) {
+    Defo D{};
+    D.on = ctx->defo_C != 0.0 && ctx->G != 0.0;
+    D.kappa = D.on ? ctx->defo_C / ctx->G : 0.0;
+    D.x = ctx->defo_x[0];
+    D.y = ctx->defo_x[1];
+    D.z = ctx->defo_x[2];
+    D.eps2 = ctx->eps * ctx->eps;
+    return D;
+}
+
 colatus_status check_dtype(colatus_t ctx, int dtype) {
     if (dtype != COLATUS_F32 && dtype != COLATUS_F64) return fail(ctx, COLATUS_E_ARG, "bad dtype %d", dtype);
     return COLATUS_OK;
@@ -640,18 +655,18 @@ colatus_status force_output(colatus_t ctx, void *out, int out_f64, bool to_acc) 
         const ForcePlan &p = ctx->plan64;
         forces_out_f64_kernel<<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
             static_cast<const double4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk, ctx->G, out,
-            out_f64, to_acc ? ctx->acc64 : nullptr);
+            out_f64, to_acc ? ctx->acc64 : nullptr, ctx->pos64[2], defo_args(ctx));
         return launched(ctx);
     }
     const ForcePlan &p = plan_f32(ctx);
     if (ctx->prec == COLATUS_FP32_COMP)
         forces_out_f32_kernel<true><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
             static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk, ctx->G, out,
-            out_f64, to_acc ? ctx->acc : nullptr);
+            out_f64, to_acc ? ctx->acc : nullptr, ctx->pk[2], defo_args(ctx));
     else
         forces_out_f32_kernel<false><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
             static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk, ctx->G, out,
-            out_f64, to_acc ? ctx->acc : nullptr);
+            out_f64, to_acc ? ctx->acc : nullptr, ctx->pk[2], defo_args(ctx));
     return launched(ctx);
 }
 
@@ -710,6 +725,7 @@ colatus_status launch_kdk_open(colatus_t ctx, const StepBufs &b, int c, long lon
 colatus_status launch_step(colatus_t ctx, const StepBufs &b, int c, long long step, double tau) {
     const int n = c ^ 1;
     const Tracers &tr = b.tr;
+    const Defo D = defo_args(ctx);
     if (ctx->prec == COLATUS_FP64) {
         const ForcePlan &p = ctx->plan64;
         TRY(run_force_f64(ctx, b.pos64[c]));
@@ -717,11 +733,11 @@ colatus_status launch_step(colatus_t ctx, const StepBufs &b, int c, long long st
         if (ctx->scheme == COLATUS_KDK)
             kdk_step_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
                 part, p.L, p.itile, b.pos64[c], b.xs64, b.vs64, b.vh64, b.acc64, b.pos64[n], b.table,
-                b.tcap, step, tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk);
+                b.tcap, step, tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk, D);
         else
             dkd_step_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
                 part, p.L, p.itile, b.pos64[c], b.xs64, b.vs64, b.acc64, b.pos64[n], b.table, b.tcap,
-                step, tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk);
+                step, tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk, D);
     } else {
         const ForcePlan &p = plan_f32(ctx);
         TRY(run_force_f32(ctx, p, b.pk[c]));
@@ -732,20 +748,20 @@ colatus_status launch_step(colatus_t ctx, const StepBufs &b, int c, long long st
             if (comp)
                 kdk_step_f32_kernel<true><<<nb, 256, 0, ctx->stream>>>(
                     part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.vh, b.acc, b.pk[n], b.table, b.tcap,
-                    step, tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk);
+                    step, tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk, D);
             else
                 kdk_step_f32_kernel<false><<<nb, 256, 0, ctx->stream>>>(
                     part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.vh, b.acc, b.pk[n], b.table, b.tcap,
-                    step, tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk);
+                    step, tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk, D);
         } else {
             if (comp)
                 dkd_step_f32_kernel<true><<<nb, 256, 0, ctx->stream>>>(
                     part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.acc, b.pk[n], b.table, b.tcap, step,
-                    tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk);
+                    tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk, D);
             else
                 dkd_step_f32_kernel<false><<<nb, 256, 0, ctx->stream>>>(
                     part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.acc, b.pk[n], b.table, b.tcap, step,
-                    tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk);
+                    tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk, D);
         }
     }
     return launched(ctx);
@@ -1290,7 +1306,9 @@ colatus_status colatus_force_vjp(colatus_t ctx, const void *w, void *gx, void *g
         TRY(launched(ctx));
         TRY(run_vjp(ctx));
         vjp_out_f64_kernel<<<nb, 256, 0, ctx->stream>>>(static_cast<const double4 *>(ctx->part), p.L,
-                                                        p.itile, ctx->N, dgx, dgm, f64in);
+                                                        p.itile, ctx->N, dgx, dgm, f64in,
+                                                        static_cast<const double4 *>(ctx->adj.pkw),
+                                                        defo_args(ctx));
     } else {
         const ForcePlan &p = ctx->plan_vjp32;
         vec3_to4_kernel<float4, float><<<nb, 256, 0, ctx->stream>>>(
@@ -1302,7 +1320,9 @@ colatus_status colatus_force_vjp(colatus_t ctx, const void *w, void *gx, void *g
         TRY(launched(ctx));
         TRY(run_vjp(ctx));
         vjp_out_f32_kernel<<<nb, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part), p.L,
-                                                        p.itile, ctx->N, dgx, dgm, f64in);
+                                                        p.itile, ctx->N, dgx, dgm, f64in,
+                                                        static_cast<const float *>(ctx->adj.pkw),
+                                                        defo_args(ctx));
     }
     TRY(launched(ctx));
     if (!on_device) {
@@ -1452,7 +1472,7 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
                 TRY(run_force_f64(ctx, b.pos64[0]));
                 forces_out_f64_kernel<<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
                     static_cast<const double4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk, ctx->G,
-                    nullptr, 0, b.acc64);
+                    nullptr, 0, b.acc64, b.pos64[0], defo_args(ctx));
             } else {
                 const ForcePlan &p = plan_f32(ctx);
                 pack_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
@@ -1462,11 +1482,11 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
                 if (ctx->prec == COLATUS_FP32_COMP)
                     forces_out_f32_kernel<true><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
                         static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk,
-                        ctx->G, nullptr, 0, b.acc);
+                        ctx->G, nullptr, 0, b.acc, b.pk[0], defo_args(ctx));
                 else
                     forces_out_f32_kernel<false><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
                         static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk,
-                        ctx->G, nullptr, 0, b.acc);
+                        ctx->G, nullptr, 0, b.acc, b.pk[0], defo_args(ctx));
             }
             TRY(launched(ctx));
             TRY(launch_kdk_open(ctx, b, 1, s0, a.tau));
@@ -1488,14 +1508,14 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
                     static_cast<const double4 *>(pos(n)), static_cast<double4 *>(a.lx),
                     static_cast<double4 *>(a.lv), static_cast<double4 *>(a.lvh),
                     static_cast<double *>(a.lm), a.table, n, a.tau, static_cast<double4 *>(a.pkw),
-                    ctx->N, pv.n_pad);
+                    ctx->N, pv.n_pad, defo_args(ctx));
             else
                 adj_step_f32_kernel<<<nbv, 256, 0, ctx->stream>>>(
                     static_cast<const float4 *>(ctx->part), pv.L, pv.itile,
                     static_cast<const float4 *>(pos(n)), static_cast<float4 *>(a.lx),
                     static_cast<float4 *>(a.lv), static_cast<float4 *>(a.lvh),
                     static_cast<float *>(a.lm), a.table, n, a.tau, static_cast<float *>(a.pkw),
-                    ctx->N, pv.n_pad);
+                    ctx->N, pv.n_pad, defo_args(ctx));
             TRY(launched(ctx));
         }
     }
@@ -1507,7 +1527,9 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
     if (f64) {
         adj_final_f64_kernel<<<nb, 256, 0, ctx->stream>>>(static_cast<const double4 *>(ctx->part),
                                                           pv.L, pv.itile, static_cast<double4 *>(a.lx),
-                                                          static_cast<double *>(a.lm), ctx->N);
+                                                          static_cast<double *>(a.lm), ctx->N,
+                                                          static_cast<const double4 *>(a.pkw),
+                                                          defo_args(ctx));
         TRY(launched(ctx));
         adj_store_kernel<double4, double><<<nb, 256, 0, ctx->stream>>>(
             static_cast<const double4 *>(a.lx), static_cast<const double4 *>(a.lv),
@@ -1515,7 +1537,9 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
     } else {
         adj_final_f32_kernel<<<nb, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part),
                                                           pv.L, pv.itile, static_cast<float4 *>(a.lx),
-                                                          static_cast<float *>(a.lm), ctx->N);
+                                                          static_cast<float *>(a.lm), ctx->N,
+                                                          static_cast<const float *>(a.pkw),
+                                                          defo_args(ctx));
         TRY(launched(ctx));
         adj_store_kernel<float4, float><<<nb, 256, 0, ctx->stream>>>(
             static_cast<const float4 *>(a.lx), static_cast<const float4 *>(a.lv),
@@ -1623,7 +1647,8 @@ colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps) {
             TRY(run_jvp(ctx, ctx->pk[2]));
             tan_open_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part),
                                                            t.plan.L, t.plan.itile, T, ctx->table,
-                                                           kTabCap, ctx->host_step, dt, ctx->N, t.n_pad);
+                                                           kTabCap, ctx->host_step, dt, ctx->N, t.n_pad,
+                                                           defo_args(ctx));
             TRY(launched(ctx));
             t.open = true;
             t.tau = dt;
@@ -1640,7 +1665,7 @@ colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps) {
             tan_step_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part),
                                                            t.plan.L, t.plan.itile, T, ctx->table,
                                                            kTabCap, ctx->host_step + j, dt, ctx->N,
-                                                           t.n_pad);
+                                                           t.n_pad, defo_args(ctx));
             TRY(launched(ctx));
         }
         done += n;
@@ -1770,6 +1795,23 @@ colatus_status colatus_probe_pipes(double out[6]) {
     return st;
 }
 
+colatus_status colatus_set_deformation(colatus_t ctx, double Cpsi, const double *x_psi) {
+    if (!ctx) return COLATUS_E_ARG;
+    if (!std::isfinite(Cpsi)) return fail(ctx, COLATUS_E_ARG, "C psi must be finite");
+    if (Cpsi != 0.0) {
+        if (!x_psi) return fail(ctx, COLATUS_E_ARG, "x_psi is NULL");
+        for (int c = 0; c < 3; ++c)
+            if (!std::isfinite(x_psi[c])) return fail(ctx, COLATUS_E_ARG, "x_psi must be finite");
+        if (ctx->G == 0.0) return fail(ctx, COLATUS_E_ARG, "the deformation term needs G != 0");
+        for (int c = 0; c < 3; ++c) ctx->defo_x[c] = x_psi[c];
+    }
+    ctx->defo_C = Cpsi;
+    ctx->acc_valid = false;
+    ctx->spec_valid = false;
+    ctx->tan.open = false;
+    return COLATUS_OK;
+}
+
 const char *colatus_last_error(colatus_t ctx) { return ctx ? ctx->err : g_init_err; }
 
 void colatus_destroy(colatus_t ctx) {
@@ -1795,3 +1837,4 @@ colatus_status colatus_stats(colatus_t ctx, double out[4]) {
 
 // ---------------------------------------------------------------- ensembles
 #include "ensemble_api.cuh"
+#include "spectrum_api.cuh"

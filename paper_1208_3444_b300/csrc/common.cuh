@@ -122,4 +122,54 @@ struct Cosmo {
     double Omega_R, Omega_M, Omega_K, Omega_L, H0;
 };
 
+// Eq. 6 deformation term, as a G-less addition to the raw force:
+// kappa (x_psi - x) / (|x - x_psi|^2 + eps^2)^{3/2} with kappa = C psi / G
+// (the pull of a fixed point mass C psi / G at x_psi).
+struct Defo {
+    double kappa, x, y, z, eps2;
+    int on, pad;
+};
+
+__device__ __forceinline__ void defo_force(const Defo &D, double px, double py, double pz, double &fx,
+                                           double &fy, double &fz) {
+    if (!D.on) return;
+    const double dx = D.x - px, dy = D.y - py, dz = D.z - pz;
+    const double r2 = dx * dx + dy * dy + dz * dz + D.eps2;
+    const double inv = 1.0 / sqrt(r2);
+    const double s = D.kappa * inv * inv * inv;
+    fx += s * dx;
+    fy += s * dy;
+    fz += s * dz;
+}
+
+// FP32 paths evaluate the O(N) term in FP64 too: x_psi is not float-exact,
+// and near x_psi its rounding is amplified by 1/s.
+__device__ __forceinline__ void defo_force(const Defo &D, float px, float py, float pz, float &fx,
+                                           float &fy, float &fz) {
+    if (!D.on) return;
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    defo_force(D, (double)px, (double)py, (double)pz, gx, gy, gz);
+    fx += (float)gx;
+    fy += (float)gy;
+    fz += (float)gz;
+}
+
+// Derivative of the deformation term along w: -kappa J(d) w, d = x_psi - x,
+// J(d) = I/s^3 - 3 d d^T/s^5 (symmetric, so this is also its transpose).
+// Evaluated in FP64 for both element types.
+template <typename T>
+__device__ __forceinline__ void defo_jacobian(const Defo &D, T px, T py, T pz, T wx, T wy, T wz,
+                                              T &gx, T &gy, T &gz) {
+    if (!D.on) return;
+    const double dx = D.x - (double)px, dy = D.y - (double)py, dz = D.z - (double)pz;
+    const double r2 = dx * dx + dy * dy + dz * dz + D.eps2;
+    const double inv = 1.0 / sqrt(r2);
+    const double inv3 = inv * inv * inv, inv5 = inv3 / r2;
+    const double dw = dx * (double)wx + dy * (double)wy + dz * (double)wz;
+    const double k = D.kappa;
+    gx -= (T)(k * ((double)wx * inv3 - 3.0 * dx * dw * inv5));
+    gy -= (T)(k * ((double)wy * inv3 - 3.0 * dy * dw * inv5));
+    gz -= (T)(k * ((double)wz * inv3 - 3.0 * dz * dw * inv5));
+}
+
 }  // namespace colatus

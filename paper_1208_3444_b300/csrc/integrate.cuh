@@ -226,12 +226,17 @@ __device__ __forceinline__ double3 reduce_f64(const double4 *__restrict__ part, 
 template <bool COMP>
 __global__ void forces_out_f32_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
                                       long long N, const DevClock *__restrict__ clk, double G,
-                                      void *out, int out_f64, float4 *__restrict__ acc) {
+                                      void *out, int out_f64, float4 *__restrict__ acc,
+                                      const float *__restrict__ pk, Defo D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double a = clk->a;
     const float scale = (float)(G / (a * a * a));
-    const float3 f = reduce_f32<COMP>(part, L, itile, i);
+    float3 f = reduce_f32<COMP>(part, L, itile, i);
+    if (D.on) {
+        const float4 x = pk_load(pk, i);
+        defo_force(D, x.x, x.y, x.z, f.x, f.y, f.z);
+    }
     if (acc) acc[i] = make_float4(f.x, f.y, f.z, 0.f);
     if (out) {
         if (out_f64) {
@@ -250,12 +255,17 @@ __global__ void forces_out_f32_kernel(const float4 *__restrict__ part, ForceLaun
 
 __global__ void forces_out_f64_kernel(const double4 *__restrict__ part, ForceLaunch L, int itile,
                                       long long N, const DevClock *__restrict__ clk, double G,
-                                      void *out, int out_f64, double4 *__restrict__ acc) {
+                                      void *out, int out_f64, double4 *__restrict__ acc,
+                                      const double4 *__restrict__ pos, Defo D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double a = clk->a;
     const double scale = G / (a * a * a);
-    const double3 f = reduce_f64(part, L, itile, i);
+    double3 f = reduce_f64(part, L, itile, i);
+    if (D.on) {
+        const double4 x = pos[i];
+        defo_force(D, x.x, x.y, x.z, f.x, f.y, f.z);
+    }
     if (acc) acc[i] = make_double4(f.x, f.y, f.z, 0.0);
     if (out) {
         if (out_f64) {
@@ -333,7 +343,7 @@ __global__ void kdk_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
                                     float4 *__restrict__ vs, float4 *__restrict__ vh,
                                     float4 *__restrict__ acc, float *__restrict__ pk_out,
                                     const StepCoef *__restrict__ table, int tcap, long long step, double tau,
-                                    long long N, long long N_pad, Tracers tr, int *flags, DevClock *clk) {
+                                    long long N, long long N_pad, Tracers tr, int *flags, DevClock *clk, Defo D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N_pad) return;
     if (i >= N) {
@@ -343,8 +353,9 @@ __global__ void kdk_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
     const StepCoef &sc = table[step % tcap];
     if (i == 0) advance_clock(clk, sc, flags);
     const float c2 = (float)sc.c2, d2 = (float)sc.d2, t = (float)tau;
-    const float3 F = reduce_f32<COMP>(part, L, itile, i);
+    float3 F = reduce_f32<COMP>(part, L, itile, i);
     const float4 x = pk_load(pk_in, i);
+    defo_force(D, x.x, x.y, x.z, F.x, F.y, F.z);
     const float4 h = vh[i];
     const float vx = c2 * h.x + d2 * F.x, vy = c2 * h.y + d2 * F.y, vz = c2 * h.z + d2 * F.z;
     acc[i] = make_float4(F.x, F.y, F.z, 0.f);
@@ -381,7 +392,7 @@ __global__ void dkd_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
                                     float4 *__restrict__ vs, float4 *__restrict__ acc,
                                     float *__restrict__ pk_out, const StepCoef *__restrict__ table,
                                     int tcap, long long step, double tau, long long N, long long N_pad, Tracers tr,
-                                    int *flags, DevClock *clk) {
+                                    int *flags, DevClock *clk, Defo D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N_pad) return;
     if (i >= N) {
@@ -391,8 +402,9 @@ __global__ void dkd_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
     const StepCoef &sc = table[step % tcap];
     if (i == 0) advance_clock(clk, sc, flags);
     const float c = (float)sc.c, d = (float)sc.d, h = (float)(0.5 * tau);
-    const float3 F = reduce_f32<COMP>(part, L, itile, i);
+    float3 F = reduce_f32<COMP>(part, L, itile, i);
     const float4 xh = pk_load(pk_in, i);
+    defo_force(D, xh.x, xh.y, xh.z, F.x, F.y, F.z);
     const float4 v0 = vs[i];
     const float vx = c * v0.x + d * F.x, vy = c * v0.y + d * F.y, vz = c * v0.z + d * F.z;
     const float x1 = xh.x + h * vx, y1 = xh.y + h * vy, z1 = xh.z + h * vz;
@@ -428,7 +440,7 @@ __global__ void kdk_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
                                     double4 *__restrict__ vs, double4 *__restrict__ vh,
                                     double4 *__restrict__ acc, double4 *__restrict__ pos_out,
                                     const StepCoef *__restrict__ table, int tcap, long long step, double tau,
-                                    long long N, long long N_pad, Tracers tr, int *flags, DevClock *clk) {
+                                    long long N, long long N_pad, Tracers tr, int *flags, DevClock *clk, Defo D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N_pad) return;
     if (i >= N) {
@@ -438,8 +450,9 @@ __global__ void kdk_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
     const StepCoef &sc = table[step % tcap];
     if (i == 0) advance_clock(clk, sc, flags);
     const double c2 = sc.c2, d2 = sc.d2;
-    const double3 F = reduce_f64(part, L, itile, i);
+    double3 F = reduce_f64(part, L, itile, i);
     const double4 x = pos_in[i];
+    defo_force(D, x.x, x.y, x.z, F.x, F.y, F.z);
     const double4 h = vh[i];
     const double vx = c2 * h.x + d2 * F.x, vy = c2 * h.y + d2 * F.y, vz = c2 * h.z + d2 * F.z;
     acc[i] = make_double4(F.x, F.y, F.z, 0.0);
@@ -471,7 +484,7 @@ __global__ void dkd_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
                                     double4 *__restrict__ vs, double4 *__restrict__ acc,
                                     double4 *__restrict__ pos_out,
                                     const StepCoef *__restrict__ table, int tcap, long long step, double tau,
-                                    long long N, long long N_pad, Tracers tr, int *flags, DevClock *clk) {
+                                    long long N, long long N_pad, Tracers tr, int *flags, DevClock *clk, Defo D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N_pad) return;
     if (i >= N) {
@@ -481,8 +494,9 @@ __global__ void dkd_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
     const StepCoef &sc = table[step % tcap];
     if (i == 0) advance_clock(clk, sc, flags);
     const double c = sc.c, d = sc.d, h = 0.5 * tau;
-    const double3 F = reduce_f64(part, L, itile, i);
+    double3 F = reduce_f64(part, L, itile, i);
     const double4 xh = pos_in[i];
+    defo_force(D, xh.x, xh.y, xh.z, F.x, F.y, F.z);
     const double4 v0 = vs[i];
     const double vx = c * v0.x + d * F.x, vy = c * v0.y + d * F.y, vz = c * v0.z + d * F.z;
     const double x1 = xh.x + h * vx, y1 = xh.y + h * vy, z1 = xh.z + h * vz;

@@ -214,14 +214,29 @@ __global__ void tan_pack_kernel(const float *__restrict__ pk, TangentState T, lo
 }
 
 // Opening of the tangent: dvh = c1 dv + d1 dF(x^n);  dx' = dx + tau dvh.
+// Deformation term's tangent at the packed position of (chunk, i).
+__device__ __forceinline__ void tan_defo(const TangentState &T, const Defo &D, int chunk,
+                                         long long i, long long n_pad, float (&f)[12]) {
+    if (!D.on) return;
+    const float4 x = T.pkt[((long long)chunk * n_pad + i) * 4];
+#pragma unroll
+    for (int q = 0; q < kTB; ++q) {
+        const long long b = (long long)chunk * kTB + q;
+        if (b >= T.B) break;
+        const float4 d = T.dx[b * n_pad + i];
+        defo_jacobian<float>(D, x.x, x.y, x.z, d.x, d.y, d.z, f[3 * q], f[3 * q + 1], f[3 * q + 2]);
+    }
+}
+
 __global__ void tan_open_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
                                 TangentState T, const StepCoef *__restrict__ table, int tcap,
-                                long long step, double tau, long long N, long long n_pad) {
+                                long long step, double tau, long long N, long long n_pad, Defo D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int chunk = blockIdx.y;
     if (i >= N) return;
     float f[12];
     jvp_reduce(part, L, itile, chunk, i, f);
+    tan_defo(T, D, chunk, i, n_pad, f);
     const StepCoef &e = table[step % tcap];
     const float c1 = (float)e.c1, d1 = (float)e.d1, t = (float)tau;
 #pragma unroll
@@ -243,12 +258,13 @@ __global__ void tan_open_kernel(const float4 *__restrict__ part, ForceLaunch L, 
 // dx += tau dvh.
 __global__ void tan_step_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
                                 TangentState T, const StepCoef *__restrict__ table, int tcap,
-                                long long step, double tau, long long N, long long n_pad) {
+                                long long step, double tau, long long N, long long n_pad, Defo D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int chunk = blockIdx.y;
     if (i >= N) return;
     float f[12];
     jvp_reduce(part, L, itile, chunk, i, f);
+    tan_defo(T, D, chunk, i, n_pad, f);
     const StepCoef &e = table[step % tcap];
     const float c2 = (float)e.c2, d2 = (float)e.d2, t = (float)tau;
 #pragma unroll
