@@ -29,7 +29,7 @@ __all__ = [
     "kick_coefficients", "schedule", "run", "diagnostics", "layzer_irvine",
     "adjoint_run", "tangent_run", "ftle", "num_threads", "PINS",
     "deformation_force", "deformation_vjp", "deformation_jvp", "total_force",
-    "velocity_spectrum",
+    "velocity_spectrum", "friedmann_integrals", "canonical_coefficients",
 ]
 
 # Parity pin of every oracle function: which non-oracle fact each one is
@@ -52,6 +52,11 @@ PINS = {
     "deformation_force": "equals the Eq. 1 pull of an extra body of mass C psi / G fixed at "
                          "x_psi (the paper's own description); single-body closed form",
     "deformation_vjp/jvp": "central finite differences of deformation_force",
+    "friedmann_integrals": "closed-form int dt/a and int dt/a^2 for EdS, de Sitter and a static "
+                           "universe; fourth-order convergence; a(t) bitwise friedmann_advance's",
+    "run (canonical)": "H0 = 0 reduces to the drag KDK; drag-only canonical momentum a^2 v "
+                       "conserved exactly; the one-step map is symplectic in (x, a^2 v) while "
+                       "the drag KDK's is not; second-order convergence to the drag KDK's limit",
     "velocity_spectrum": "pure sinusoid closed form (peak height, Hann side lobes 1/4), "
                          "Parseval identity with and without the window, numpy.fft.rfft, "
                          "constant series",
@@ -243,6 +248,41 @@ def total_force(x, m, eps: float, G: float, defo=None) -> np.ndarray:
 
 
 # ------------------------------------------------- Eqs. 3-5 and KDK variant
+def friedmann_integrals(a: float, dt: float, c: Cosmology, nsub: int):
+    """Advance a(t) by dt as friedmann_advance does and integrate the drift and
+    kick factors of the canonical leapfrog (the symplectic reformulation of
+    Sec. II, after Quinn et al.): returns (a(t+dt), int dt/a, int dt/a^2).
+    RK4 on the system (a, I1, I2)' = (a H(a), 1/a, 1/a^2) with nsub sub-steps,
+    so a(t) is the same sequence as friedmann_advance's."""
+    h = dt / nsub
+    I1 = I2 = 0.0
+    for _ in range(nsub):
+        s1 = a
+        k1 = friedmann_rhs(s1, c)
+        s2 = a + 0.5 * h * k1
+        k2 = friedmann_rhs(s2, c)
+        s3 = a + 0.5 * h * k2
+        k3 = friedmann_rhs(s3, c)
+        s4 = a + h * k3
+        k4 = friedmann_rhs(s4, c)
+        I1 += (h / 6.0) * (1.0 / s1 + 2.0 / s2 + 2.0 / s3 + 1.0 / s4)
+        I2 += (h / 6.0) * (1.0 / s1 ** 2 + 2.0 / s2 ** 2 + 2.0 / s3 ** 2 + 1.0 / s4 ** 2)
+        a = a + (h / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+    return a, I1, I2
+
+
+def canonical_coefficients(a0: float, a1: float, K1: float, K2: float, D: float, tau: float):
+    """The canonical kick-drift-kick (p = a^2 v per unit mass, dp/dt = G F / a,
+    dx/dt = p / a^2; drift x += p int dt/a^2, kick p += G F int dt/a) written
+    in the velocity form of ``run``'s KDK, with vh the mean drift velocity
+    (x^{n+1} = x^n + tau vh):
+        vh      = (D/tau) a0^2 v^n + (D/tau) K1 G F(x^n)
+        v^{n+1} = tau/(D a1^2) vh  + K2/a1^2 G F(x^{n+1})
+    K1, K2 = int dt/a over the two half steps, D = int dt/a^2 over the step.
+    Returns (c1, d1, c2, d2) without G (G is applied like the drag kick's)."""
+    return D / tau * a0 * a0, D / tau * K1, tau / (D * a1 * a1), K2 / (a1 * a1)
+
+
 def kick_coefficients(a: float, H: float, h: float):
     """Trapezoidal Hubble-drag kick over a span h (Eq. 4 with tau -> h):
     v' = c v + d F with c = (1 - H h)/(1 + H h), d = h / (a^3 (1 + H h))."""
@@ -256,18 +296,33 @@ def schedule(cosmo: Cosmology, a_start: float, tau: float, nsteps: int,
     a is advanced from t^n to t^{n+1/2} and on to t^{n+1} with nsub RK4
     sub-steps per half step.  Returns a dict of arrays: a (nsteps+1 values at
     integer steps), a_half, and the coefficients: DKD -> c, d (at t^{n+1/2});
-    KDK -> c1, d1 (at t^n, span tau/2) and c2, d2 (at t^{n+1}, span tau/2).
+    KDK -> c1, d1 (at t^n, span tau/2) and c2, d2 (at t^{n+1}, span tau/2);
+    canonical -> c1, d1, c2, d2 of canonical_coefficients, plus K1, K2, D.
     """
     a_int = np.empty(nsteps + 1)
     a_half = np.empty(nsteps)
     a_int[0] = a_start
     a = a_start
+    K1 = np.empty(nsteps)
+    K2 = np.empty(nsteps)
+    D = np.empty(nsteps)
     for n in range(nsteps):
-        a_half[n] = friedmann_advance(a, 0.5 * tau, cosmo, nsub)
-        a = friedmann_advance(a_half[n], 0.5 * tau, cosmo, nsub)
+        if scheme == "canonical":
+            a_half[n], K1[n], Da = friedmann_integrals(a, 0.5 * tau, cosmo, nsub)
+            a, K2[n], Db = friedmann_integrals(a_half[n], 0.5 * tau, cosmo, nsub)
+            D[n] = Da + Db
+        else:
+            a_half[n] = friedmann_advance(a, 0.5 * tau, cosmo, nsub)
+            a = friedmann_advance(a_half[n], 0.5 * tau, cosmo, nsub)
         a_int[n + 1] = a
     out = {"a": a_int, "a_half": a_half, "t": tau * np.arange(nsteps + 1)}
-    if scheme == "dkd":
+    if scheme == "canonical":
+        cc = [canonical_coefficients(a_int[n], a_int[n + 1], K1[n], K2[n], D[n], tau)
+              for n in range(nsteps)]
+        for k, name in enumerate(("c1", "d1", "c2", "d2")):
+            out[name] = np.array([q[k] for q in cc])
+        out["K1"], out["K2"], out["D"] = K1, K2, D
+    elif scheme == "dkd":
         cd = [kick_coefficients(ah, hubble(ah, cosmo), tau) for ah in a_half]
         out["c"] = np.array([p[0] for p in cd])
         out["d"] = np.array([p[1] for p in cd])
@@ -279,7 +334,7 @@ def schedule(cosmo: Cosmology, a_start: float, tau: float, nsteps: int,
         out["c2"] = np.array([p[0] for p in k2])
         out["d2"] = np.array([p[1] for p in k2])
     else:
-        raise ValueError("scheme must be 'dkd' or 'kdk'")
+        raise ValueError("scheme must be 'dkd', 'kdk' or 'canonical'")
     return out
 
 
@@ -311,7 +366,7 @@ def run(x, v, m, eps: float, G: float, cosmo: Cosmology, a_start: float,
     diags = []
     if diag_every:
         diags.append((0, diagnostics(x, v, m, sch["a"][0], eps, G, cosmo)))
-    F = total_force(x, m, eps, G, defo) if scheme == "kdk" else None
+    F = total_force(x, m, eps, G, defo) if scheme != "dkd" else None
     for n in range(nsteps):
         if keep_states:
             states.append((x.copy(), v.copy()))
