@@ -61,7 +61,11 @@ typedef enum {
 
 typedef enum {
     COLATUS_DKD = 0,  /* Eqs. 3-5: half drift, kick at t^{n+1/2}, half drift             */
-    COLATUS_KDK = 1   /* half kick at t^n, drift, half kick at t^{n+1} (span tau/2 each) */
+    COLATUS_KDK = 1,  /* half kick at t^n, drift, half kick at t^{n+1} (span tau/2 each) */
+    COLATUS_KDK_CANONICAL = 2  /* the symplectic canonical leapfrog of Sec. II: p = a^2 v,
+                                  kick p += G F int dt/a over each half step, drift
+                                  x += p int dt/a^2 over the step (FP64 RK4 quadrature
+                                  along a(t)); takes KDK's place everywhere KDK is accepted */
 } colatus_scheme;
 
 typedef enum { COLATUS_F32 = 0, COLATUS_F64 = 1 } colatus_dtype;

@@ -18,7 +18,7 @@ LIB_PATH = os.environ.get("COLATUS_LIBRARY") or os.path.join(HERE, "libcolatus.s
 # enums of colatus.h
 OK, E_ARG, E_CUDA, E_NONFINITE, E_FRIEDMANN, E_STATE, E_OOM, E_TIMEOUT = range(8)
 FP32, FP32_COMP, FP64 = 0, 1, 2
-DKD, KDK = 0, 1
+DKD, KDK, KDK_CANONICAL = 0, 1, 2
 F32, F64 = 0, 1
 NDIAG = 16
 STATUS_NAMES = {0: "COLATUS_OK", 1: "COLATUS_E_ARG", 2: "COLATUS_E_CUDA",

@@ -517,6 +517,10 @@ colatus_status sync_and_check(colatus_t ctx) {
 
 size_t elem_size(int dtype) { return dtype == COLATUS_F64 ? 8 : 4; }
 
+// Both kick-drift-kick schemes share every kernel; only the schedule differs.
+bool is_kdk(colatus_t ctx) { return ctx->scheme != COLATUS_DKD; }
+int canonical(colatus_t ctx) { return ctx->scheme == COLATUS_KDK_CANONICAL ? 1 : 0; }
+
 // Deformation term for the kernels: the G-less kappa = C psi / G.
 Defo defo_args(colatus_t ctx) {
     Defo D{};
@@ -581,7 +585,8 @@ colatus_status load_masses(colatus_t ctx, const void *src, int f64) {
 colatus_status extend_table(colatus_t ctx, int n) {
     if (n <= 0) return COLATUS_OK;
     friedmann_table_kernel<<<1, 1, 0, ctx->tstream>>>(ctx->cosmo, ctx->tclk, ctx->table, kTabCap,
-                                                      n, ctx->tab_tau, ctx->tab_G, kFriedmannSub);
+                                                      n, ctx->tab_tau, ctx->tab_G, kFriedmannSub,
+                                                      canonical(ctx));
     TRY(launched(ctx));
     ctx->tab_hi += n;
     const int k = ctx->tab_ev_next;
@@ -591,7 +596,7 @@ colatus_status extend_table(colatus_t ctx, int n) {
     return COLATUS_OK;
 }
 
-// Make schedule entries [host_step, host_step + n) available to the main
+// Make schedule entries [host_step, host_step + n] available to the main
 // stream for step size tau.  The schedule stream first waits for all work
 // already enqueued on the main stream, so an extension never overwrites ring
 // entries that enqueued steps still read (the ring holds kTabCap entries and
@@ -608,7 +613,9 @@ colatus_status need_table(colatus_t ctx, double tau, int n) {
         ctx->tab_hi = ctx->host_step;
         for (long long &c : ctx->tab_ev_covers) c = -1;
     }
-    const long long need = ctx->host_step + n;
+    // steps [host_step, host_step + n) and the entry after them, whose
+    // opening coefficients the last step's epilogue applies
+    const long long need = ctx->host_step + n + 1;
     if (ctx->tab_hi < need) TRY(extend_table(ctx, (int)(need + kLookahead - ctx->tab_hi)));
     // wait only for the earliest extension that completes the needed entries
     int best = -1;
@@ -730,7 +737,7 @@ colatus_status launch_step(colatus_t ctx, const StepBufs &b, int c, long long st
         const ForcePlan &p = ctx->plan64;
         TRY(run_force_f64(ctx, b.pos64[c]));
         const double4 *part = static_cast<const double4 *>(ctx->part);
-        if (ctx->scheme == COLATUS_KDK)
+        if (is_kdk(ctx))
             kdk_step_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
                 part, p.L, p.itile, b.pos64[c], b.xs64, b.vs64, b.vh64, b.acc64, b.pos64[n], b.table,
                 b.tcap, step, tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk, D);
@@ -744,7 +751,7 @@ colatus_status launch_step(colatus_t ctx, const StepBufs &b, int c, long long st
         const float4 *part = static_cast<const float4 *>(ctx->part);
         const bool comp = ctx->prec == COLATUS_FP32_COMP;
         const unsigned nb = blocks_for(p.n_pad, 256);
-        if (ctx->scheme == COLATUS_KDK) {
+        if (is_kdk(ctx)) {
             if (comp)
                 kdk_step_f32_kernel<true><<<nb, 256, 0, ctx->stream>>>(
                     part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.vh, b.acc, b.pk[n], b.table, b.tcap,
@@ -771,7 +778,7 @@ colatus_status launch_step(colatus_t ctx, const StepBufs &b, int c, long long st
 // DKD half drift, from the state into the force input pk[cur].
 colatus_status open_step(colatus_t ctx, double tau) {
     const bool f64 = ctx->prec == COLATUS_FP64;
-    if (ctx->scheme == COLATUS_KDK) {
+    if (is_kdk(ctx)) {
         if (!ctx->acc_valid) {
             TRY(force_at_state(ctx));
             TRY(force_output(ctx, nullptr, 0, true));
@@ -1014,7 +1021,7 @@ colatus_status colatus_set_config(colatus_t ctx, colatus_prec prec, colatus_sche
     DeviceGuard dg(ctx->device);
     if (prec != COLATUS_FP32 && prec != COLATUS_FP32_COMP && prec != COLATUS_FP64)
         return fail(ctx, COLATUS_E_ARG, "bad precision %d", (int)prec);
-    if (scheme != COLATUS_DKD && scheme != COLATUS_KDK)
+    if (scheme != COLATUS_DKD && scheme != COLATUS_KDK && scheme != COLATUS_KDK_CANONICAL)
         return fail(ctx, COLATUS_E_ARG, "bad scheme %d", (int)scheme);
     if (!std::isfinite(G)) return fail(ctx, COLATUS_E_ARG, "G must be finite");
     if (cuda_stream && (cudaStream_t)cuda_stream != ctx->stream) {
@@ -1029,7 +1036,9 @@ colatus_status colatus_set_config(colatus_t ctx, colatus_prec prec, colatus_sche
             ctx->xs, ctx->vs, ctx->xs64, ctx->vs64, is64 ? 1 : 0, ctx->N);
         TRY(launched(ctx));
     }
-    if (prec != ctx->prec || scheme != ctx->scheme) ctx->acc_valid = false;
+    if (prec != ctx->prec || (scheme == COLATUS_DKD) != (ctx->scheme == COLATUS_DKD))
+        ctx->acc_valid = false;
+    if (scheme != ctx->scheme) ctx->tab_valid = false;   // the schedule's coefficients change
     ctx->spec_valid = false;
     ctx->prec = prec;
     ctx->scheme = scheme;
@@ -1157,7 +1166,7 @@ colatus_status colatus_step(colatus_t ctx, double dt, int64_t nsteps) {
         ctx->host_step += n;
         TRY(refill_table(ctx));
     }
-    ctx->acc_valid = ctx->scheme == COLATUS_KDK;
+    ctx->acc_valid = is_kdk(ctx);
     return COLATUS_OK;
 }
 
@@ -1343,7 +1352,7 @@ colatus_status colatus_adjoint_forward(colatus_t ctx, double dt, int64_t nsteps,
     if (nsteps < 1 || checkpoint_every < 1)
         return fail(ctx, COLATUS_E_ARG, "nsteps and checkpoint_every must be >= 1");
     if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
-    if (ctx->scheme != COLATUS_KDK)
+    if (!is_kdk(ctx))
         return fail(ctx, COLATUS_E_ARG, "the adjoint is built for the KDK scheme");
     auto &a = ctx->adj;
     a.ready = false;
@@ -1370,7 +1379,8 @@ colatus_status colatus_adjoint_forward(colatus_t ctx, double dt, int64_t nsteps,
     // index the forward's schedule by step within the pass (0 .. nsteps-1)
     CU(cudaMemsetAsync(&a.rclk->step, 0, sizeof(a.rclk->step), ctx->stream));
     friedmann_table_kernel<<<1, 1, 0, ctx->stream>>>(ctx->cosmo, a.rclk, a.table, (int)nsteps,
-                                                     (int)nsteps, dt, ctx->G, kFriedmannSub);
+                                                     (int)nsteps, dt, ctx->G, kFriedmannSub,
+                                                     canonical(ctx));
     TRY(launched(ctx));
     const long long step0 = ctx->host_step;
     const bool f64 = ctx->prec == COLATUS_FP64;
@@ -1625,7 +1635,7 @@ colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps) {
     DeviceGuard dg(ctx->device);
     auto &t = ctx->tan;
     if (!t.ready) return fail(ctx, COLATUS_E_STATE, "colatus_tangent_init first");
-    if (ctx->prec == COLATUS_FP64 || ctx->scheme != COLATUS_KDK)
+    if (ctx->prec == COLATUS_FP64 || !is_kdk(ctx))
         return fail(ctx, COLATUS_E_ARG, "the tangent model runs with FP32 precision and KDK");
     if (t.last_step != ctx->host_step)
         return fail(ctx, COLATUS_E_STATE, "the state moved without its tangents; re-initialise");

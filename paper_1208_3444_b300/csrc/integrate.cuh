@@ -28,16 +28,26 @@ __device__ inline double hubble_of(double a, const Cosmo &c, bool &bad) {
     return friedmann_rhs(a, c, bad) / a;
 }
 
-// Classical RK4 with nsub equal sub-steps over dt.
+// Classical RK4 with nsub equal sub-steps over dt, on the system
+// (a, I1, I2)' = (a H(a), 1/a, 1/a^2): I1 and I2 accumulate int dt/a and
+// int dt/a^2, the kick and drift factors of the canonical leapfrog.  Every
+// scheme goes through this one routine, so a(t) does not depend on it.
 __device__ inline double friedmann_advance(double a, double dt, const Cosmo &c, int nsub,
-                                           bool &bad) {
-    const double h = dt / nsub;
+                                           bool &bad, double &I1, double &I2) {
+    const double h = dt / nsub, h6 = h / 6.0;
     for (int s = 0; s < nsub; ++s) {
-        const double k1 = friedmann_rhs(a, c, bad);
-        const double k2 = friedmann_rhs(a + 0.5 * h * k1, c, bad);
-        const double k3 = friedmann_rhs(a + 0.5 * h * k2, c, bad);
-        const double k4 = friedmann_rhs(a + h * k3, c, bad);
-        a = a + (h / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
+        const double s2 = a;
+        const double k1 = friedmann_rhs(s2, c, bad);
+        const double s3 = a + 0.5 * h * k1;
+        const double k2 = friedmann_rhs(s3, c, bad);
+        const double s4 = a + 0.5 * h * k2;
+        const double k3 = friedmann_rhs(s4, c, bad);
+        const double s5 = a + h * k3;
+        const double k4 = friedmann_rhs(s5, c, bad);
+        const double r1 = 1.0 / s2, r2 = 1.0 / s3, r3 = 1.0 / s4, r4 = 1.0 / s5;
+        I1 += h6 * (r1 + 2.0 * r2 + 2.0 * r3 + r4);
+        I2 += h6 * (r1 * r1 + 2.0 * (r2 * r2) + 2.0 * (r3 * r3) + r4 * r4);
+        a = a + h6 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
     }
     return a;
 }
@@ -51,23 +61,38 @@ __device__ inline void kick_coef(double a, double H, double h, double G, double 
 // One thread: extend the look-ahead schedule by n steps of size tau from its
 // frontier `tclk` (a, t and the absolute index of the next step), writing
 // the entry of step s to table[s % tcap].  The per-step sequence (advance
-// tau/2 to t^{n+1/2}, then tau/2 to t^{n+1}) is the same for DKD and KDK, so
-// a(t) does not depend on the scheme.  A negative Eq. 2 radicand marks the
-// entry bad; the step that consumes it raises FLAG_FRIEDMANN.
+// tau/2 to t^{n+1/2}, then tau/2 to t^{n+1}) is the same for every scheme,
+// so a(t) does not depend on the scheme.  canonical != 0 replaces the KDK
+// coefficients by those of the canonical (symplectic) leapfrog of Sec. II:
+// p = a^2 v, kick p += G F int dt/a, drift x += p int dt/a^2, written in the
+// velocity form vh = c1 v + d1 F, x' = x + tau vh, v' = c2 vh + d2 F with
+// c1 = (D/tau) a0^2, d1 = G (D/tau) K1, c2 = tau / (D a1^2), d2 = G K2 / a1^2
+// (K1, K2: int dt/a over the half steps; D: int dt/a^2 over the step).  A
+// negative Eq. 2 radicand marks the entry bad; the step that consumes it
+// raises FLAG_FRIEDMANN.
 __global__ void friedmann_table_kernel(Cosmo cosmo, DevClock *tclk, StepCoef *table, int tcap,
-                                       int n, double tau, double G, int nsub) {
+                                       int n, double tau, double G, int nsub, int canonical) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     double a = tclk->a, t = tclk->t;
     const long long step0 = tclk->step;
     for (int j = 0; j < n; ++j) {
         bool bad = false;
         StepCoef s;
+        double K1 = 0.0, K2 = 0.0, D = 0.0;
         s.a0 = a;
-        s.ah = friedmann_advance(a, 0.5 * tau, cosmo, nsub, bad);
-        s.a1 = friedmann_advance(s.ah, 0.5 * tau, cosmo, nsub, bad);
+        s.ah = friedmann_advance(a, 0.5 * tau, cosmo, nsub, bad, K1, D);
+        s.a1 = friedmann_advance(s.ah, 0.5 * tau, cosmo, nsub, bad, K2, D);
         kick_coef(s.ah, hubble_of(s.ah, cosmo, bad), tau, G, s.c, s.d);
-        kick_coef(s.a0, hubble_of(s.a0, cosmo, bad), 0.5 * tau, G, s.c1, s.d1);
-        kick_coef(s.a1, hubble_of(s.a1, cosmo, bad), 0.5 * tau, G, s.c2, s.d2);
+        if (canonical) {
+            const double Dt = D / tau;
+            s.c1 = Dt * (s.a0 * s.a0);
+            s.d1 = G * Dt * K1;
+            s.c2 = tau / (D * (s.a1 * s.a1));
+            s.d2 = G * K2 / (s.a1 * s.a1);
+        } else {
+            kick_coef(s.a0, hubble_of(s.a0, cosmo, bad), 0.5 * tau, G, s.c1, s.d1);
+            kick_coef(s.a1, hubble_of(s.a1, cosmo, bad), 0.5 * tau, G, s.c2, s.d2);
+        }
         t = t + tau;
         s.t1 = t;
         s.step = step0 + j;
@@ -335,8 +360,10 @@ __global__ void kdk_open_f32_kernel(const float4 *__restrict__ xs, const float4 
 }
 
 // KDK step j, after the force at x^{n+1} (pk_in):
-//   v^{n+1} = c2 vh + d2 F;  record;  next step's opening (same coefficients,
-//   both at t^{n+1}): vh = c2 v^{n+1} + d2 F;  x^{n+2} = x^{n+1} + tau vh.
+//   v^{n+1} = c2 vh + d2 F;  record;  next step's opening with the next
+//   entry's coefficients: vh = c1' v^{n+1} + d1' F;  x^{n+2} = x^{n+1} + tau vh.
+// (For the drag scheme c1', d1' equal c2, d2 bit for bit: both are the half
+// kick at t^{n+1}.)
 template <bool COMP>
 __global__ void kdk_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
                                     const float *__restrict__ pk_in, float4 *__restrict__ xs,
@@ -351,8 +378,10 @@ __global__ void kdk_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
         return;
     }
     const StepCoef &sc = table[step % tcap];
+    const StepCoef &nc = table[(step + 1) % tcap];
     if (i == 0) advance_clock(clk, sc, flags);
     const float c2 = (float)sc.c2, d2 = (float)sc.d2, t = (float)tau;
+    const float c1n = (float)nc.c1, d1n = (float)nc.d1;
     float3 F = reduce_f32<COMP>(part, L, itile, i);
     const float4 x = pk_load(pk_in, i);
     defo_force(D, x.x, x.y, x.z, F.x, F.y, F.z);
@@ -362,7 +391,7 @@ __global__ void kdk_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
     xs[i] = x;
     vs[i] = make_float4(vx, vy, vz, 0.f);
     record(tr, i, sc.step, x.x, x.y, x.z, vx, vy, vz);
-    const float nx = c2 * vx + d2 * F.x, ny = c2 * vy + d2 * F.y, nz = c2 * vz + d2 * F.z;
+    const float nx = c1n * vx + d1n * F.x, ny = c1n * vy + d1n * F.y, nz = c1n * vz + d1n * F.z;
     vh[i] = make_float4(nx, ny, nz, 0.f);
     pk_store(pk_out, i, x.x + t * nx, x.y + t * ny, x.z + t * nz, x.w);
     if (!finite3(x.x, x.y, x.z) || !finite3(vx, vy, vz)) atomicOr(&flags[FLAG_NONFINITE], 1);
@@ -448,8 +477,9 @@ __global__ void kdk_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
         return;
     }
     const StepCoef &sc = table[step % tcap];
+    const StepCoef &nc = table[(step + 1) % tcap];
     if (i == 0) advance_clock(clk, sc, flags);
-    const double c2 = sc.c2, d2 = sc.d2;
+    const double c2 = sc.c2, d2 = sc.d2, c1n = nc.c1, d1n = nc.d1;
     double3 F = reduce_f64(part, L, itile, i);
     const double4 x = pos_in[i];
     defo_force(D, x.x, x.y, x.z, F.x, F.y, F.z);
@@ -459,7 +489,7 @@ __global__ void kdk_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
     xs[i] = x;
     vs[i] = make_double4(vx, vy, vz, 0.0);
     record(tr, i, sc.step, x.x, x.y, x.z, vx, vy, vz);
-    const double nx = c2 * vx + d2 * F.x, ny = c2 * vy + d2 * F.y, nz = c2 * vz + d2 * F.z;
+    const double nx = c1n * vx + d1n * F.x, ny = c1n * vy + d1n * F.y, nz = c1n * vz + d1n * F.z;
     vh[i] = make_double4(nx, ny, nz, 0.0);
     pos_out[i] = make_double4(x.x + tau * nx, x.y + tau * ny, x.z + tau * nz, x.w);
     if (!finite3(x.x, x.y, x.z) || !finite3(vx, vy, vz)) atomicOr(&flags[FLAG_NONFINITE], 1);

@@ -254,8 +254,8 @@ __global__ void tan_open_kernel(const float4 *__restrict__ part, ForceLaunch L, 
 }
 
 // Step of the tangent after the JVP at x^{n+1}: dv = c2 dvh + d2 dF; record
-// the seed body's |(dx, dv)|; open the next step: dvh = c2 dv + d2 dF,
-// dx += tau dvh.
+// the seed body's |(dx, dv)|; open the next step with the next entry's
+// coefficients: dvh = c1' dv + d1' dF, dx += tau dvh.
 __global__ void tan_step_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
                                 TangentState T, const StepCoef *__restrict__ table, int tcap,
                                 long long step, double tau, long long N, long long n_pad, Defo D) {
@@ -266,7 +266,9 @@ __global__ void tan_step_kernel(const float4 *__restrict__ part, ForceLaunch L, 
     jvp_reduce(part, L, itile, chunk, i, f);
     tan_defo(T, D, chunk, i, n_pad, f);
     const StepCoef &e = table[step % tcap];
+    const StepCoef &en = table[(step + 1) % tcap];
     const float c2 = (float)e.c2, d2 = (float)e.d2, t = (float)tau;
+    const float c1n = (float)en.c1, d1n = (float)en.d1;
 #pragma unroll
     for (int q = 0; q < kTB; ++q) {
         const long long b = (long long)chunk * kTB + q;
@@ -282,8 +284,8 @@ __global__ void tan_step_kernel(const float4 *__restrict__ part, ForceLaunch L, 
             T.growth[r * T.B + b] =
                 sqrtf(x.x * x.x + x.y * x.y + x.z * x.z + vx * vx + vy * vy + vz * vz);
         }
-        const float nx = c2 * vx + d2 * f[3 * q], ny = c2 * vy + d2 * f[3 * q + 1],
-                    nz = c2 * vz + d2 * f[3 * q + 2];
+        const float nx = c1n * vx + d1n * f[3 * q], ny = c1n * vy + d1n * f[3 * q + 1],
+                    nz = c1n * vz + d1n * f[3 * q + 2];
         T.dvh[k] = make_float4(nx, ny, nz, 0.f);
         T.dx[k] = make_float4(x.x + t * nx, x.y + t * ny, x.z + t * nz, 0.f);
     }
