@@ -190,6 +190,66 @@ void colatus_oracle_jvp_rows(int64_t n, const double *x, const double *m,
     }
 }
 
+/* Periodic boundaries (Sec. II: periodic, for a homogeneous distribution):
+ * the real-space part of the Ewald sum of the Newtonian pull over all images
+ * x_j + n L (n integer, |n_c| <= nreal around the minimum image), plus the
+ * softening correction of the nearest image, for target rows:
+ *
+ *   out_k = G sum_j m_j [ sum_n N_S(d_j + n L) + P(d_j) - N(d_j) ]
+ *
+ * d_j = minimum image of x_j - x_k, N(d) = d/|d|^3, P(d) = d/(|d|^2+eps^2)^1.5,
+ * N_S(r) = r [erfc(alpha |r|)/|r|^3 + 2 alpha/sqrt(pi) exp(-alpha^2 |r|^2)/|r|^2],
+ * and every |r| = 0 term (the self pair's own cell) left out.  The
+ * reciprocal-space part is added by the caller.  Brute force: one loop per
+ * image, in order. */
+void colatus_oracle_ewald_real_rows(int64_t n, const double *x, const double *m,
+                                    double eps, double G, double L, double alpha,
+                                    int64_t nreal, const int64_t *rows, int64_t nrows,
+                                    double *out)
+{
+    const double eps2 = eps * eps;
+    const double c_g = 2.0 * alpha / sqrt(acos(-1.0));   /* 2 alpha / sqrt(pi) */
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t r = 0; r < nrows; ++r) {
+        const int64_t k = rows[r];
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double d[3];
+            for (int c = 0; c < 3; ++c) {
+                d[c] = x[3 * j + c] - x[3 * k + c];
+                d[c] -= L * nearbyint(d[c] / L);
+            }
+            const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (d2 > 0.0) {
+                /* nearest image: Plummer instead of Newton */
+                const double s2 = d2 + eps2;
+                const double w = m[j] * (1.0 / (s2 * sqrt(s2)) - 1.0 / (d2 * sqrt(d2)));
+                ax += w * d[0];
+                ay += w * d[1];
+                az += w * d[2];
+            }
+            for (int64_t i0 = -nreal; i0 <= nreal; ++i0)
+                for (int64_t i1 = -nreal; i1 <= nreal; ++i1)
+                    for (int64_t i2 = -nreal; i2 <= nreal; ++i2) {
+                        const double e0 = d[0] + L * (double)i0;
+                        const double e1 = d[1] + L * (double)i1;
+                        const double e2 = d[2] + L * (double)i2;
+                        const double q2 = e0 * e0 + e1 * e1 + e2 * e2;
+                        if (q2 == 0.0) continue;
+                        const double q = sqrt(q2);
+                        const double w = m[j] * (erfc(alpha * q) / (q2 * q) +
+                                                 c_g * exp(-alpha * alpha * q2) / q2);
+                        ax += w * e0;
+                        ay += w * e1;
+                        az += w * e2;
+                    }
+        }
+        out[3 * r + 0] = G * ax;
+        out[3 * r + 1] = G * ay;
+        out[3 * r + 2] = G * az;
+    }
+}
+
 /* Number of OpenMP threads the parallel loops above use. */
 int colatus_oracle_threads(void)
 {

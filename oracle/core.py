@@ -30,6 +30,7 @@ __all__ = [
     "adjoint_run", "tangent_run", "ftle", "num_threads", "PINS",
     "deformation_force", "deformation_vjp", "deformation_jvp", "total_force",
     "velocity_spectrum", "friedmann_integrals", "canonical_coefficients",
+    "ewald_forces",
 ]
 
 # Parity pin of every oracle function: which non-oracle fact each one is
@@ -57,6 +58,10 @@ PINS = {
     "run (canonical)": "H0 = 0 reduces to the drag KDK; drag-only canonical momentum a^2 v "
                        "conserved exactly; the one-step map is symplectic in (x, a^2 v) while "
                        "the drag KDK's is not; second-order convergence to the drag KDK's limit",
+    "ewald_forces": "independent of the splitting parameter alpha; zero on a perfect lattice "
+                    "and between bodies half a box apart; periodic in every body's position "
+                    "and translation invariant; Newton's third law; at separations << L "
+                    "the isolated Plummer force plus the background term (4 pi/3V) m d",
     "velocity_spectrum": "pure sinusoid closed form (peak height, Hann side lobes 1/4), "
                          "Parseval identity with and without the window, numpy.fft.rfft, "
                          "constant series",
@@ -92,10 +97,12 @@ def _load():
         L.colatus_oracle_potential_rows.argtypes = [i64, _dp, _dp, dbl, dbl, _ip, i64, _dp]
         L.colatus_oracle_vjp_rows.argtypes = [i64, _dp, _dp, _dp, dbl, dbl, _ip, i64, _dp, _dp]
         L.colatus_oracle_jvp_rows.argtypes = [i64, _dp, _dp, _dp, _dp, dbl, dbl, _ip, i64, _dp]
+        L.colatus_oracle_ewald_real_rows.argtypes = [i64, _dp, _dp, dbl, dbl, dbl, dbl, i64, _ip,
+                                                     i64, _dp]
         L.colatus_oracle_threads.restype = ctypes.c_int
         for f in (L.colatus_oracle_forces_pairwise, L.colatus_oracle_forces_rows,
                   L.colatus_oracle_potential_rows, L.colatus_oracle_vjp_rows,
-                  L.colatus_oracle_jvp_rows):
+                  L.colatus_oracle_jvp_rows, L.colatus_oracle_ewald_real_rows):
             f.restype = None
         _lib = L
     return _lib
@@ -238,10 +245,11 @@ def deformation_jvp(x, Cpsi: float, xpsi, eps: float, dx) -> np.ndarray:
     return _defo_J_apply(x, Cpsi, xpsi, eps, dx)
 
 
-def total_force(x, m, eps: float, G: float, defo=None) -> np.ndarray:
+def total_force(x, m, eps: float, G: float, defo=None, box=None) -> np.ndarray:
     """F of Eq. 1 (attractive), plus the Eq. 6 deformation term when
-    defo = (C psi, x_psi) is given."""
-    F = forces(x, m, eps, G)
+    defo = (C psi, x_psi) is given; box = L makes the boundaries periodic
+    (``ewald_forces``)."""
+    F = forces(x, m, eps, G) if box is None else ewald_forces(x, m, eps, box, G)
     if defo is not None:
         F = F + deformation_force(x, defo[0], defo[1], eps)
     return F
@@ -340,7 +348,7 @@ def schedule(cosmo: Cosmology, a_start: float, tau: float, nsteps: int,
 
 def run(x, v, m, eps: float, G: float, cosmo: Cosmology, a_start: float,
         tau: float, nsteps: int, scheme: str = "kdk", nsub: int = 8,
-        tracers=None, keep_states: bool = False, diag_every: int = 0, defo=None):
+        tracers=None, keep_states: bool = False, diag_every: int = 0, defo=None, box=None):
     """Integrate Eq. 1 with the Hubble-drag leapfrog for nsteps.
 
     DKD follows Eqs. 3-5 literally:
@@ -354,7 +362,8 @@ def run(x, v, m, eps: float, G: float, cosmo: Cosmology, a_start: float,
     F is the raw Eq. 1 force; a^-3 sits in d.  Returns a dict with the final
     x, v, the schedule, tracer records [nsteps, ntr, 6] (x, v after each step),
     optional per-step states and diagnostics every diag_every steps.
-    defo = (C psi, x_psi) adds the Eq. 6 deformation term to F.
+    defo = (C psi, x_psi) adds the Eq. 6 deformation term to F; box = L
+    makes the boundaries periodic (positions are not wrapped).
     """
     x = _d(x).reshape(-1, 3).copy()
     v = _d(v).reshape(-1, 3).copy()
@@ -366,18 +375,18 @@ def run(x, v, m, eps: float, G: float, cosmo: Cosmology, a_start: float,
     diags = []
     if diag_every:
         diags.append((0, diagnostics(x, v, m, sch["a"][0], eps, G, cosmo)))
-    F = total_force(x, m, eps, G, defo) if scheme != "dkd" else None
+    F = total_force(x, m, eps, G, defo, box) if scheme != "dkd" else None
     for n in range(nsteps):
         if keep_states:
             states.append((x.copy(), v.copy()))
         if scheme == "dkd":
             xh = x + 0.5 * tau * v
-            v = sch["c"][n] * v + sch["d"][n] * total_force(xh, m, eps, G, defo)
+            v = sch["c"][n] * v + sch["d"][n] * total_force(xh, m, eps, G, defo, box)
             x = xh + 0.5 * tau * v
         else:
             vh = sch["c1"][n] * v + sch["d1"][n] * F
             x = x + tau * vh
-            F = total_force(x, m, eps, G, defo)
+            F = total_force(x, m, eps, G, defo, box)
             v = sch["c2"][n] * vh + sch["d2"][n] * F
         if tr is not None:
             rec[n, :, :3] = x[tr]
@@ -601,3 +610,43 @@ def velocity_spectrum(v, dt: float, window: str = "rect", detrend: bool = True) 
     if T % 2 == 0:
         c[-1] = 1.0
     return (0.5 * c[:, None] * dt / (T * U) * power).T
+
+
+# ------------------------------------------------- periodic boundaries (Ewald)
+def ewald_forces(x, m, eps: float, L: float, G: float = 1.0, alpha=None, nreal: int = 2,
+                 nk=None, rows=None) -> np.ndarray:
+    """Raw attractive force (Eq. 1 without a^-3) in a periodic box of side L
+    (Sec. II states periodic boundaries for a homogeneous distribution): the
+    pull of every image of every body, with the uniform mean density removed
+    (the k = 0 mode left out, so a homogeneous box feels no force), and the
+    nearest image Plummer-softened with eps instead of Newtonian.
+
+    Ewald's split with parameter alpha: the real-space sum over images within
+    nreal boxes of the nearest one (C loops) plus the reciprocal sum over
+    k = 2 pi n / L, 0 < |n_c| <= nk:
+        a_L(x_k) = -(4 pi G / L^3) sum_k exp(-k^2/(4 alpha^2)) / k^2
+                     * k * sum_j m_j sin(k . (x_k - x_j)).
+    Defaults (alpha L = 6, nreal = 2, nk = 12) converge both sums to double
+    rounding.  The result does not depend on alpha."""
+    x, m = _d(x).reshape(-1, 3), _d(m).reshape(-1)
+    rows = _rows(len(m), rows)
+    alpha = 6.0 / L if alpha is None else float(alpha)
+    if nk is None:
+        # exp(-pi^2 n^2 / (alpha L)^2) below 1e-18
+        nk = int(math.ceil(alpha * L / math.pi * math.sqrt(18.0 * math.log(10.0))))
+    out = np.empty((len(rows), 3))
+    _load().colatus_oracle_ewald_real_rows(len(m), _ptr(x), _ptr(m), float(eps), float(G), float(L),
+                                           alpha, int(nreal), _ptr(rows, _ip), len(rows), _ptr(out))
+    r = np.arange(-nk, nk + 1)
+    n = np.stack(np.meshgrid(r, r, r, indexing="ij"), axis=-1).reshape(-1, 3)
+    n = n[np.any(n != 0, axis=1)]
+    V = L ** 3
+    xt = x[rows]
+    for c0 in range(0, len(n), 2048):
+        k = 2.0 * np.pi / L * n[c0:c0 + 2048]                      # [K, 3]
+        k2 = np.sum(k * k, axis=1)
+        w = 4.0 * np.pi * G / V * np.exp(-k2 / (4.0 * alpha * alpha)) / k2
+        rho = np.exp(1j * (k @ x.T)) @ m                            # sum_j m_j e^{i k.x_j}
+        s = np.imag(np.exp(1j * (k @ xt.T)) * np.conj(rho)[:, None])  # sum_j m_j sin(k.(x_t - x_j))
+        out -= (w[:, None] * s).T @ k
+    return out
