@@ -332,6 +332,41 @@ def time_tangent(B, inputs, torch, stream, ntr=64, nsteps=2):
             "finite": bool(np.all(np.isfinite(growth)))}
 
 
+def time_periodic(B, inputs, torch, stream, nsteps=10):
+    """Periodic boundaries (Ewald summation) on the 32^3 workload, FP32
+    compensated KDK: per step the real-space all-pairs kernel (minimum images),
+    the k-space structure factors and long-range force, and the epilogue."""
+    ic = inputs.grid32()
+    tau = inputs.lcdm_tau(2000)
+    sim = B.Simulation(ic.m, ic.eps, LCDM, inputs.A_START, prec=B.FP32_COMP, scheme=B.KDK,
+                       stream=stream.cuda_stream)
+    try:
+        sim.set_state(ic.x, ic.v)
+        sim.set_periodic(1.0)
+        sim.step(tau, 2)
+        sim.synchronize()
+        sim.profile_forces(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(tau, nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fms, n = sim.profile_read()
+        sim.profile_forces(False)
+        par = sim.periodic_params()
+    finally:
+        sim.close()
+    ms = e0.elapsed_time(e1) / nsteps
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    pairs = float(ic.N) * ic.N
+    return {"N": ic.N, "box": 1.0, "alpha": par["alpha"], "nk": par["nk"], "k_vectors": par["nkv"],
+            "ms_per_step": ms, "interactions_per_s": pairs / (ms * 1e-3),
+            "real_space_ms_per_launch": fms / n,
+            "real_space_interactions_per_sm_per_clk": pairs / (fms / n * 1e-3) / (nsm * 2.032e9),
+            "what": "KDK step with periodic boundaries; real space = the minimum-image "
+                    "all-pairs kernel alone (events around it)"}
+
+
 def run_colatus(args, ws, rank, local):
     import torch
     from paper_1208_3444_b300 import binding as B
@@ -414,6 +449,7 @@ def run_colatus(args, ws, rank, local):
     adjoint = time_adjoint(B, inputs, torch, stream)
     ensemble = time_ensemble(B, inputs, torch, stream)
     tangent = time_tangent(B, inputs, torch, stream)
+    periodic = time_periodic(B, inputs, torch, stream)
     pipes = B.colatus_probe_pipes()
     if rank == 0:
         peaks = {}
@@ -457,6 +493,7 @@ def run_colatus(args, ws, rank, local):
             "adjoint": adjoint,
             "ensemble": ensemble,
             "tangent": tangent,
+            "periodic": periodic,
             "pipe_rates": {**pipes, "unit": "lane-ops (MUFU: results) per SM per clock",
                            "what": "colatus_probe_pipes: independent chains of FFMA, FFMA2 "
                                    "(f32x2), MUFU.RSQ"},

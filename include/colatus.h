@@ -100,6 +100,26 @@ colatus_status colatus_set_config(colatus_t ctx, colatus_prec prec, colatus_sche
  * G != 0 (COLATUS_E_ARG otherwise). */
 colatus_status colatus_set_deformation(colatus_t ctx, double Cpsi, const double *x_psi);
 
+/* Periodic boundaries (Sec. II) in a cube of side L: every body pulls with
+ * all its images, the uniform mean density is removed (a homogeneous box
+ * feels no force), and the nearest image is Plummer-softened with eps:
+ *   F_k = sum_j m_j [ sum_n N(d_j + n L) - N(d_j) + P(d_j) ],
+ *   d_j = minimum image of x_j - x_k, N(d) = d/|d|^3, P(d) = d/(|d|^2+eps^2)^1.5,
+ * evaluated by Ewald summation: a real-space all-pairs kernel over minimum
+ * images and a reciprocal-space sum over 0 < |n| <= nk, k = 2 pi n / L.
+ * alpha <= 0 and nk <= 0 choose them from the precision (truncation below
+ * 1e-8 of a pair term in the FP32 modes, 1e-15 in FP64); nk <= 64.  Positions
+ * are not wrapped: the minimum image is taken per pair.  L = 0 restores
+ * isolated boundaries.  Forces and both step schemes honour it; the force
+ * VJP, the adjoint, the tangent model and autotuning return COLATUS_E_STATE
+ * while it is on, and it does not combine with the deformation term
+ * (COLATUS_E_ARG).  colatus_diagnostics keeps the isolated potential. */
+colatus_status colatus_set_periodic(colatus_t ctx, double L, double alpha, int nk);
+
+/* The Ewald parameters in use: alpha, nk and the number of k-vectors of the
+ * half space (any pointer may be NULL).  COLATUS_E_STATE if not periodic. */
+colatus_status colatus_periodic_params(colatus_t ctx, double *alpha_out, int *nk_out, int *nkv_out);
+
 /* Replace the N masses (dtype elements, host or device). */
 colatus_status colatus_set_masses(colatus_t ctx, const void *m, int dtype, int on_device);
 

@@ -613,7 +613,7 @@ def velocity_spectrum(v, dt: float, window: str = "rect", detrend: bool = True) 
 
 
 # ------------------------------------------------- periodic boundaries (Ewald)
-def ewald_forces(x, m, eps: float, L: float, G: float = 1.0, alpha=None, nreal: int = 2,
+def ewald_forces(x, m, eps: float, L: float, G: float = 1.0, alpha=None, nreal: int = 1,
                  nk=None, rows=None) -> np.ndarray:
     """Raw attractive force (Eq. 1 without a^-3) in a periodic box of side L
     (Sec. II states periodic boundaries for a homogeneous distribution): the
@@ -626,8 +626,9 @@ def ewald_forces(x, m, eps: float, L: float, G: float = 1.0, alpha=None, nreal: 
     k = 2 pi n / L, 0 < |n_c| <= nk:
         a_L(x_k) = -(4 pi G / L^3) sum_k exp(-k^2/(4 alpha^2)) / k^2
                      * k * sum_j m_j sin(k . (x_k - x_j)).
-    Defaults (alpha L = 6, nreal = 2, nk = 12) converge both sums to double
-    rounding.  The result does not depend on alpha."""
+    Defaults (alpha L = 6, nreal = 1: the first image left out is 1.5 L away,
+    erfc(9) ~ 4e-37; nk from exp(-(pi nk/(alpha L))^2) < 1e-18) converge both
+    sums to double rounding.  The result does not depend on alpha."""
     x, m = _d(x).reshape(-1, 3), _d(m).reshape(-1)
     rows = _rows(len(m), rows)
     alpha = 6.0 / L if alpha is None else float(alpha)

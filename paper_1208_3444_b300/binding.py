@@ -37,7 +37,8 @@ EXPORTS = ("colatus_init", "colatus_set_config", "colatus_set_masses", "colatus_
            "colatus_ensemble_stats", "colatus_ensemble_last_error", "colatus_ensemble_destroy",
            "colatus_tangent_init", "colatus_tangent_step", "colatus_tangent_read",
            "colatus_autotune", "colatus_set_tuning", "colatus_probe_pipes",
-           "colatus_set_deformation", "colatus_velocity_spectrum", "colatus_tracer_spectrum")
+           "colatus_set_deformation", "colatus_velocity_spectrum", "colatus_tracer_spectrum",
+           "colatus_set_periodic", "colatus_periodic_params")
 
 
 class ColatusError(RuntimeError):
@@ -94,6 +95,8 @@ def lib():
         "colatus_velocity_spectrum": [_vp, _int, _int, _i64, _i64, _i64, _dbl, _int, _int, _vp,
                                       _int, _vp],
         "colatus_tracer_spectrum": [_vp, _dbl, _int, _int, _vp, _vp],
+        "colatus_set_periodic": [_vp, _dbl, _dbl, _int],
+        "colatus_periodic_params": [_vp, _vp, _vp, _vp],
         "colatus_tangent_step": [_vp, _dbl, _i64],
         "colatus_tangent_read": [_vp, _vp, _vp],
     }
@@ -387,6 +390,17 @@ class Simulation:
 
     def set_masses(self, m):
         colatus_set_masses(self.h, m)
+
+    def set_periodic(self, L, alpha=0.0, nk=0):
+        """Periodic boundaries in a cube of side L (0: isolated); alpha, nk <= 0
+        choose the Ewald parameters from the precision."""
+        _check(lib().colatus_set_periodic(self.h, float(L), float(alpha), int(nk)), self.h)
+
+    def periodic_params(self):
+        a, nk, nkv = ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().colatus_periodic_params(self.h, ctypes.byref(a), ctypes.byref(nk),
+                                             ctypes.byref(nkv)), self.h)
+        return dict(alpha=a.value, nk=nk.value, nkv=nkv.value)
 
     def set_deformation(self, Cpsi, x_psi=(0.0, 0.0, 0.0)):
         xp = np.ascontiguousarray(np.asarray(x_psi, dtype=np.float64))

@@ -437,7 +437,7 @@ __device__ __forceinline__ void pkw_load(const float *pkw, long long i, float &x
 
 __global__ void vjp_out_f32_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
                                    long long N, void *gx, void *gm, int out_f64,
-                                   const float *__restrict__ pkw, Defo D) {
+                                   const float *__restrict__ pkw, Extra D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     float4 g = reduce_vjp_f32(part, L, itile, i);
@@ -451,7 +451,7 @@ __global__ void vjp_out_f32_kernel(const float4 *__restrict__ part, ForceLaunch 
 
 __global__ void vjp_out_f64_kernel(const double4 *__restrict__ part, ForceLaunch L, int itile,
                                    long long N, void *gx, void *gm, int out_f64,
-                                   const double4 *__restrict__ bw, Defo D) {
+                                   const double4 *__restrict__ bw, Extra D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     double4 g = reduce_vjp_f64(part, L, itile, i);
@@ -517,7 +517,7 @@ __global__ void adj_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
                                     const float4 *__restrict__ xn, float4 *lx, float4 *lv,
                                     float4 *lvh, float *lm, const StepCoef *__restrict__ table,
                                     long long n, double tau, float *pkw, long long N,
-                                    long long N_pad, Defo D) {
+                                    long long N_pad, Extra D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N_pad) return;
     if (i >= N) {
@@ -549,7 +549,7 @@ __global__ void adj_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
 
 __global__ void adj_final_f32_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
                                      float4 *lx, float *lm, long long N,
-                                     const float *__restrict__ pkw, Defo D) {
+                                     const float *__restrict__ pkw, Extra D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     float4 g = reduce_vjp_f32(part, L, itile, i);
@@ -592,7 +592,7 @@ __global__ void adj_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
                                     const double4 *__restrict__ xn, double4 *lx, double4 *lv,
                                     double4 *lvh, double *lm, const StepCoef *__restrict__ table,
                                     long long n, double tau, double4 *bw, long long N,
-                                    long long N_pad, Defo D) {
+                                    long long N_pad, Extra D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N_pad) return;
     if (i >= N) {
@@ -625,7 +625,7 @@ __global__ void adj_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
 
 __global__ void adj_final_f64_kernel(const double4 *__restrict__ part, ForceLaunch L, int itile,
                                      double4 *lx, double *lm, long long N,
-                                     const double4 *__restrict__ bw, Defo D) {
+                                     const double4 *__restrict__ bw, Extra D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     double4 g = reduce_vjp_f64(part, L, itile, i);

@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "diagnostics.cuh"
 #include "ensemble.cuh"
+#include "ewald.cuh"
 #include "force.cuh"
 #include "integrate.cuh"
 #include "probe.cuh"
@@ -92,6 +93,15 @@ using Vjp64K = Vjp64Kernel<kV64NT, kV64JT, kStages>;
 constexpr int kJvpNT = 128, kJvpIPT = 2, kJvpJT = 128, kJvpMINB = 4;
 using JvpK = JvpKernel<kJvpNT, kJvpIPT, kJvpJT, kStages>;
 
+// Periodic (Ewald) real-space kernels: FP32 256 threads x 2 i-bodies,
+// 256-body j-tiles; FP64 128 x 1, 32-body tiles.
+constexpr int kEwNT = 256, kEwIPT = 2, kEwJT = 256, kEwFold = 32, kEwMinB = 2;
+using EwK = EwaldF32Kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, false>;
+using EwKC = EwaldF32Kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, true>;
+constexpr int kEw64NT = 128, kEw64JT = 32;
+using Ew64K = EwaldF64Kernel<kEw64NT, kEw64JT, kStages>;
+constexpr int kEwMaxNk = 64;
+
 constexpr long long kPadAlloc = 1024;   // buffers hold N rounded up to this
 constexpr int kChunk = 1024;            // steps enqueued per chunk of colatus_step
 constexpr int kTabCap = 4096;           // ring of look-ahead schedule entries
@@ -123,13 +133,29 @@ ForceLaunch make_launch(long long n_pad, int itile, int jt, long long g_target) 
     return L;
 }
 
+
+// A persistent kernel's launch geometry comes in two versions: the full
+// grid, and one that leaves one SM free for the Friedmann schedule kernel
+// while an extension of the look-ahead schedule runs on the side stream (see
+// choose_grid).  L is the one in use; segment buffers are sized for both.
 struct ForcePlan {
     int variant = -1;       // F32 variant, or -1 for FP64
     long long n_pad = 0;    // bodies incl. zero-mass padding
     int itile = 0, jt = 0;
-    ForceLaunch L{};
+    ForceLaunch L{}, L_full{}, L_red{};
     size_t part_bytes = 0;
 };
+
+// Both geometries of a plan (n_pad, itile, jt set); elem_bytes per segment
+// entry per body.
+void finish_plan(ForcePlan &p, int occ, int num_sms, size_t elem_bytes) {
+    p.L_full = make_launch(p.n_pad, p.itile, p.jt, (long long)occ * num_sms);
+    p.L_red = make_launch(p.n_pad, p.itile, p.jt, (long long)occ * std::max(1, num_sms - 1));
+    p.L = p.L_full;
+    const size_t segs = std::max((size_t)p.L_full.n_it * p.L_full.S_max,
+                                 (size_t)p.L_red.n_it * p.L_red.S_max);
+    p.part_bytes = segs * p.itile * elem_bytes;
+}
 
 }  // namespace
 
@@ -157,6 +183,7 @@ struct colatus_ctx {
     // tab_tau and G tab_G, computed on tstream ahead of the steps
     bool tab_valid = false;
     long long tab_hi = 0;
+    int tab_smem = 0;          // dynamic shared memory of the schedule kernel: a whole SM's
     double tab_tau = 0.0, tab_G = 0.0;
     bool have_state = false;
     bool acc_valid = false;    // acc holds F at the state position
@@ -201,6 +228,19 @@ struct colatus_ctx {
     ForcePlan plan32[NUM_F32_VARIANTS];
     ForcePlan plan64;
     ForcePlan plan_vjp32, plan_vjp64;
+
+    // periodic boundaries (colatus_set_periodic): Ewald parameters and buffers
+    bool periodic = false;
+    double box = 0.0, ew_alpha_req = 0.0;   // requested alpha (<= 0: from the precision)
+    int ew_nk_req = 0;                      // requested nk (<= 0: from the precision)
+    EwaldArgs ew{};
+    int nkv = 0;
+    KVec *kv = nullptr;
+    double *kw = nullptr;
+    double2 *rho = nullptr;
+    void *lr = nullptr;                     // n_alloc float4 / double4 long-range forces
+    size_t kv_cap = 0;
+    ForcePlan plan_ew32[2], plan_ew64;
 
     // tangent model (colatus_tangent_*)
     struct Tangent {
@@ -305,8 +345,7 @@ colatus_status build_plans(colatus_t ctx) {
         p.itile = fv.nt * fv.ipt;
         p.jt = fv.jt;
         p.n_pad = round_up(ctx->N, std::max(p.itile, p.jt));
-        p.L = make_launch(p.n_pad, p.itile, p.jt, (long long)occ * ctx->num_sms);
-        p.part_bytes = (size_t)p.L.n_it * p.L.S_max * p.itile * sizeof(float4) * (fv.comp ? 2 : 1);
+        finish_plan(p, occ, ctx->num_sms, sizeof(float4) * (fv.comp ? 2 : 1));
     }
     int occ = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -317,8 +356,7 @@ colatus_status build_plans(colatus_t ctx) {
     p.itile = F64K::ITILE;
     p.jt = kF64JT;
     p.n_pad = round_up(ctx->N, std::max(p.itile, p.jt));
-    p.L = make_launch(p.n_pad, p.itile, p.jt, (long long)occ * ctx->num_sms);
-    p.part_bytes = (size_t)p.L.n_it * p.L.S_max * p.itile * sizeof(double4);
+    finish_plan(p, occ, ctx->num_sms, sizeof(double4));
 
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &occ, vjp_f32_kernel<kVjpNT, kVjpIPT, kVjpJT, kStages, kVjpMINB>, kVjpNT, VjpK::SMEM));
@@ -327,8 +365,7 @@ colatus_status build_plans(colatus_t ctx) {
     v.itile = VjpK::ITILE;
     v.jt = kVjpJT;
     v.n_pad = round_up(ctx->N, std::max(v.itile, v.jt));
-    v.L = make_launch(v.n_pad, v.itile, v.jt, (long long)occ * ctx->num_sms);
-    v.part_bytes = (size_t)v.L.n_it * v.L.S_max * v.itile * sizeof(float4);
+    finish_plan(v, occ, ctx->num_sms, sizeof(float4));
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &occ, vjp_f64_kernel<kV64NT, kV64JT, kStages>, kV64NT, Vjp64K::SMEM));
     if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "FP64 VJP kernel cannot be resident");
@@ -336,8 +373,29 @@ colatus_status build_plans(colatus_t ctx) {
     w.itile = Vjp64K::ITILE;
     w.jt = kV64JT;
     w.n_pad = round_up(ctx->N, std::max(w.itile, w.jt));
-    w.L = make_launch(w.n_pad, w.itile, w.jt, (long long)occ * ctx->num_sms);
-    w.part_bytes = (size_t)w.L.n_it * w.L.S_max * w.itile * sizeof(double4);
+    finish_plan(w, occ, ctx->num_sms, sizeof(double4));
+
+    for (int comp = 0; comp < 2; ++comp) {
+        const void *fn = comp ? (const void *)ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold,
+                                                              true, kEwMinB>
+                              : (const void *)ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold,
+                                                              false, kEwMinB>;
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kEwNT, EwK::SMEM));
+        if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "Ewald kernel cannot be resident");
+        ForcePlan &e = ctx->plan_ew32[comp];
+        e.itile = EwK::ITILE;
+        e.jt = kEwJT;
+        e.n_pad = round_up(ctx->N, std::max(e.itile, e.jt));
+        finish_plan(e, occ, ctx->num_sms, sizeof(float4) * (comp ? 2 : 1));
+    }
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, ewald_f64_kernel<kEw64NT, kEw64JT, kStages>, kEw64NT, Ew64K::SMEM));
+    if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "FP64 Ewald kernel cannot be resident");
+    ForcePlan &e64 = ctx->plan_ew64;
+    e64.itile = Ew64K::ITILE;
+    e64.jt = kEw64JT;
+    e64.n_pad = round_up(ctx->N, std::max(e64.itile, e64.jt));
+    finish_plan(e64, occ, ctx->num_sms, sizeof(double4));
     return COLATUS_OK;
 }
 
@@ -350,18 +408,21 @@ colatus_status build_plans(colatus_t ctx) {
 int default_shape(colatus_t ctx, int comp) {
     for (int sh = 0; sh < kShapes - 1; ++sh) {
         const ForcePlan &p = ctx->plan32[4 * sh + comp];
-        if (p.L.W >= 4LL * p.L.G) return sh;
+        if (p.L_full.W >= 4LL * p.L_full.G) return sh;
     }
     return kShapes - 1;
 }
 
 const ForcePlan &plan_f32(colatus_t ctx) {
+    if (ctx->periodic) return ctx->plan_ew32[ctx->prec == COLATUS_FP32_COMP ? 1 : 0];
     const int comp = ctx->prec == COLATUS_FP32_COMP ? V_COMP : 0;
     const int sh = ctx->tuned_shape >= 0 ? ctx->tuned_shape : default_shape(ctx, comp);
     const ForcePlan *w = &ctx->plan32[4 * sh + comp];
     if (ctx->eq_mass && w->n_pad == ctx->N) w += V_EQM;
     return *w;
 }
+
+const ForcePlan &plan_f64(colatus_t ctx) { return ctx->periodic ? ctx->plan_ew64 : ctx->plan64; }
 
 colatus_status ensure_part(colatus_t ctx, size_t bytes) {
     if (bytes <= ctx->part_bytes) return COLATUS_OK;
@@ -395,8 +456,126 @@ colatus_status prof_end(colatus_t ctx, int cat = 0) {
     return COLATUS_OK;
 }
 
+// Ewald parameters for the current precision.  alpha (unless requested) from
+// the real-space truncation: the images beyond the nearest are at r >= L/2,
+// where the pair term is below erfc(x) + (2x/sqrt(pi)) exp(-x^2), x = alpha L/2;
+// nk (unless requested) from exp(-(pi nk / (alpha L))^2), the largest k-space
+// weight left out.  Both at tol = 1e-8 (FP32 modes) or 1e-15 (FP64).
+colatus_status ewald_setup(colatus_t ctx) {
+    const double L = ctx->box, pi = std::acos(-1.0);
+    const bool f64 = ctx->prec == COLATUS_FP64;
+    const double tol = f64 ? 1e-15 : 1e-8;
+    double alpha = ctx->ew_alpha_req;
+    if (!(alpha > 0.0)) {
+        double lo = 0.5, hi = 10.0;
+        for (int it = 0; it < 100; ++it) {
+            const double x = 0.5 * (lo + hi);
+            const double err = std::erfc(x) + 2.0 * x / std::sqrt(pi) * std::exp(-x * x);
+            (err > tol ? lo : hi) = x;
+        }
+        alpha = 2.0 * hi / L;
+    }
+    int nk = ctx->ew_nk_req;
+    if (nk <= 0) nk = (int)std::ceil(alpha * L / pi * std::sqrt(std::log(1.0 / tol)));
+    if (nk > kEwMaxNk) return fail(ctx, COLATUS_E_ARG, "Ewald needs nk = %d > %d", nk, kEwMaxNk);
+    std::vector<KVec> kv;
+    std::vector<double> w;
+    const double V = L * L * L, tk = 2.0 * pi / L;
+    for (int nx = 0; nx <= nk; ++nx)
+        for (int ny = -nk; ny <= nk; ++ny)
+            for (int nz = -nk; nz <= nk; ++nz) {
+                const int n2 = nx * nx + ny * ny + nz * nz;
+                if (n2 == 0 || n2 > nk * nk) continue;
+                if (!(nx > 0 || (nx == 0 && (ny > 0 || (ny == 0 && nz > 0))))) continue;
+                const double k2 = tk * tk * n2;
+                kv.push_back(KVec{nx, ny, nz, 0});
+                w.push_back(2.0 * 4.0 * pi / V * std::exp(-k2 / (4.0 * alpha * alpha)) / k2);
+            }
+    const size_t nkv = kv.size();
+    if (nkv > ctx->kv_cap) {
+        for (void *q : {(void *)ctx->kv, (void *)ctx->kw, (void *)ctx->rho})
+            if (q) cudaFree(q);
+        ctx->kv = nullptr;
+        ctx->kw = nullptr;
+        ctx->rho = nullptr;
+        ctx->kv_cap = 0;
+        CU(cudaMalloc(&ctx->kv, nkv * sizeof(KVec)));
+        CU(cudaMalloc(&ctx->kw, nkv * sizeof(double)));
+        CU(cudaMalloc(&ctx->rho, nkv * sizeof(double2)));
+        ctx->kv_cap = nkv;
+    }
+    if (!ctx->lr) CU(cudaMalloc(&ctx->lr, (size_t)ctx->n_alloc * sizeof(double4)));
+    CU(cudaMemcpyAsync(ctx->kv, kv.data(), nkv * sizeof(KVec), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->kw, w.data(), nkv * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));   // the host vectors go out of scope
+    ctx->nkv = (int)nkv;
+    EwaldArgs &A = ctx->ew;
+    A.L = L;
+    A.alpha = alpha;
+    A.Lf = (float)L;
+    A.invLf = (float)(1.0 / L);
+    A.alpha_f = (float)alpha;
+    A.alpha2_log2e = (float)(alpha * alpha / std::log(2.0));
+    A.cg = (float)(2.0 * alpha / std::sqrt(pi));
+    A.s0 = (float)(-4.0 / 3.0 * alpha * alpha * alpha / std::sqrt(pi));
+    A.s1 = (float)(0.8 * std::pow(alpha, 5) / std::sqrt(pi));
+    A.x2_series = (float)((0.05 / alpha) * (0.05 / alpha));
+    A.nk = nk;
+    // shared memory of the k-space kernels grows with nk
+    const int nt = nk + 1;
+    const size_t es = f64 ? sizeof(double) : sizeof(float);
+    const size_t smem_rho = (size_t)kEwBodies * (3 * nt * 2 + 1) * es;
+    const size_t smem_f = kEwKChunk * sizeof(KVec) + 2 * kEwKChunk * es + (size_t)kEwFThreads * 3 * nt * 2 * es;
+    const void *frho = f64 ? (const void *)ewald_rho_kernel<double> : (const void *)ewald_rho_kernel<float>;
+    const void *fk = f64 ? (const void *)ewald_kforce_kernel<double, double4>
+                         : (const void *)ewald_kforce_kernel<float, float4>;
+    CU(cudaFuncSetAttribute(frho, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rho));
+    CU(cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f));
+    return COLATUS_OK;
+}
+
+// Periodic boundaries: the k-space part, after the real-space kernel.
+// Structure factors into ctx->rho, then the long-range force at every body
+// into ctx->lr.  pk (FP32 packed) or pos (FP64) holds the positions.
+template <typename T, typename T4>
+colatus_status run_ewald_kspace(colatus_t ctx, const float *pk, const double4 *pos) {
+    const int nt = ctx->ew.nk + 1;
+    CU(cudaMemsetAsync(ctx->rho, 0, (size_t)ctx->nkv * sizeof(double2), ctx->stream));
+    const int kchunks = (ctx->nkv + kEwKThreads - 1) / kEwKThreads;
+    const long long max_split = std::max(1LL, ctx->N / kEwBodies);
+    const int splits = (int)std::min<long long>(std::max(1, 2 * ctx->num_sms / kchunks), max_split);
+    const size_t smem_rho = (size_t)kEwBodies * (3 * nt * 2 + 1) * sizeof(T);
+    ewald_rho_kernel<T><<<dim3(kchunks, splits), kEwKThreads, smem_rho, ctx->stream>>>(
+        pk, pos, ctx->N, ctx->kv, ctx->nkv, ctx->ew, ctx->rho);
+    TRY(launched(ctx));
+    const size_t smem_f = kEwKChunk * sizeof(KVec) + 2 * kEwKChunk * sizeof(T) +
+                          (size_t)kEwFThreads * 3 * nt * 2 * sizeof(T);
+    ewald_kforce_kernel<T, T4><<<blocks_for(ctx->N, kEwFThreads), kEwFThreads, smem_f, ctx->stream>>>(
+        pk, pos, ctx->N, ctx->kv, ctx->kw, ctx->rho, ctx->nkv, ctx->ew, static_cast<T4 *>(ctx->lr));
+    return launched(ctx);
+}
+
+colatus_status run_ewald_f32(colatus_t ctx, const ForcePlan &p, const float *pk) {
+    TRY(ensure_part(ctx, p.part_bytes));
+    const float eps2 = (float)(ctx->eps * ctx->eps);
+    TRY(prof_begin(ctx));
+    if (ctx->prec == COLATUS_FP32_COMP)
+        ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, true, kEwMinB>
+            <<<p.L.G, kEwNT, EwKC::SMEM, ctx->stream>>>(pk, static_cast<float4 *>(ctx->part), ctx->flags,
+                                                        p.L, eps2, ctx->ew);
+    else
+        ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, false, kEwMinB>
+            <<<p.L.G, kEwNT, EwK::SMEM, ctx->stream>>>(pk, static_cast<float4 *>(ctx->part), ctx->flags,
+                                                       p.L, eps2, ctx->ew);
+    TRY(launched(ctx));
+    ctx->interactions += (double)ctx->N * (double)ctx->N;
+    TRY(prof_end(ctx));
+    return run_ewald_kspace<float, float4>(ctx, pk, nullptr);
+}
+
 // Launch the force sum on packed FP32 bodies; segments land in ctx->part.
 colatus_status run_force_f32(colatus_t ctx, const ForcePlan &p, const float *pk) {
+    if (ctx->periodic) return run_ewald_f32(ctx, p, pk);
     TRY(ensure_part(ctx, p.part_bytes));
     const F32Variant &fv = f32_variant(p.variant);
     const float eps2 = (float)(ctx->eps * ctx->eps);
@@ -409,6 +588,17 @@ colatus_status run_force_f32(colatus_t ctx, const ForcePlan &p, const float *pk)
 }
 
 colatus_status run_force_f64(colatus_t ctx, const double4 *pos) {
+    if (ctx->periodic) {
+        const ForcePlan &p = ctx->plan_ew64;
+        TRY(ensure_part(ctx, p.part_bytes));
+        TRY(prof_begin(ctx));
+        ewald_f64_kernel<kEw64NT, kEw64JT, kStages><<<p.L.G, kEw64NT, Ew64K::SMEM, ctx->stream>>>(
+            pos, static_cast<double4 *>(ctx->part), ctx->flags, p.L, ctx->eps * ctx->eps, ctx->ew);
+        TRY(launched(ctx));
+        ctx->interactions += (double)ctx->N * (double)ctx->N;
+        TRY(prof_end(ctx));
+        return run_ewald_kspace<double, double4>(ctx, nullptr, pos);
+    }
     const ForcePlan &p = ctx->plan64;
     TRY(ensure_part(ctx, p.part_bytes));
     TRY(prof_begin(ctx));
@@ -522,14 +712,16 @@ bool is_kdk(colatus_t ctx) { return ctx->scheme != COLATUS_DKD; }
 int canonical(colatus_t ctx) { return ctx->scheme == COLATUS_KDK_CANONICAL ? 1 : 0; }
 
 // Deformation term for the kernels: the G-less kappa = C psi / G.
-Defo defo_args(colatus_t ctx) {
-    Defo D{};
+Extra extra_args(colatus_t ctx) {
+    Extra D{};
     D.on = ctx->defo_C != 0.0 && ctx->G != 0.0;
     D.kappa = D.on ? ctx->defo_C / ctx->G : 0.0;
     D.x = ctx->defo_x[0];
     D.y = ctx->defo_x[1];
     D.z = ctx->defo_x[2];
     D.eps2 = ctx->eps * ctx->eps;
+    D.lr32 = ctx->periodic && ctx->prec != COLATUS_FP64 ? static_cast<const float4 *>(ctx->lr) : nullptr;
+    D.lr64 = ctx->periodic && ctx->prec == COLATUS_FP64 ? static_cast<const double4 *>(ctx->lr) : nullptr;
     return D;
 }
 
@@ -543,7 +735,7 @@ void free_all(colatus_t ctx) {
                     ctx->xs64, ctx->vs64, ctx->vh64, ctx->acc64, ctx->pos64[0], ctx->pos64[1],
                     ctx->pos64[2], ctx->m64, ctx->part, ctx->flags, ctx->mstat, ctx->clk,
                     ctx->tclk, ctx->table, ctx->stage, ctx->stage2, ctx->diag, ctx->tslot,
-                    ctx->rec};
+                    ctx->rec, ctx->kv, ctx->kw, ctx->rho, ctx->lr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *tptrs[] = {ctx->tan.dx, ctx->tan.dv, ctx->tan.dvh, ctx->tan.pkt, ctx->tan.seeds,
@@ -584,7 +776,7 @@ colatus_status load_masses(colatus_t ctx, const void *src, int f64) {
 // Extend the look-ahead schedule by n entries on the schedule stream.
 colatus_status extend_table(colatus_t ctx, int n) {
     if (n <= 0) return COLATUS_OK;
-    friedmann_table_kernel<<<1, 1, 0, ctx->tstream>>>(ctx->cosmo, ctx->tclk, ctx->table, kTabCap,
+    friedmann_table_kernel<<<1, 1, ctx->tab_smem, ctx->tstream>>>(ctx->cosmo, ctx->tclk, ctx->table, kTabCap,
                                                       n, ctx->tab_tau, ctx->tab_G, kFriedmannSub,
                                                       canonical(ctx));
     TRY(launched(ctx));
@@ -594,6 +786,29 @@ colatus_status extend_table(colatus_t ctx, int n) {
     CU(cudaEventRecord(ctx->tab_ev[k], ctx->tstream));
     ctx->tab_ev_covers[k] = ctx->tab_hi;
     return COLATUS_OK;
+}
+
+// Persistent kernels enqueued while a schedule extension may still run on
+// the side stream use one SM fewer: the schedule kernel asks for a whole SM's
+// shared memory, so it runs alone on the SM left free.  (A lone FP64 thread
+// next to a force CTA slows that CTA, and so the whole stream-K grid, by
+// about 1.7x on this GPU, whose FP64 rate is a small fraction of FP32.)
+// Called once per API call, before its first launch: every force launch and
+// the epilogue that sums its segments then share one geometry.
+bool extension_in_flight(colatus_t ctx) {
+    for (int k = 0; k < kTabEvents; ++k)
+        if (ctx->tab_ev[k] && cudaEventQuery(ctx->tab_ev[k]) == cudaErrorNotReady) return true;
+    return false;
+}
+
+void choose_grid(colatus_t ctx) {
+    const bool red = extension_in_flight(ctx);
+    auto pick = [red](ForcePlan &p) { p.L = red ? p.L_red : p.L_full; };
+    for (ForcePlan &p : ctx->plan32) pick(p);
+    for (ForcePlan &p : ctx->plan_ew32) pick(p);
+    for (ForcePlan *p : {&ctx->plan64, &ctx->plan_vjp32, &ctx->plan_vjp64, &ctx->plan_ew64})
+        pick(*p);
+    if (ctx->tan.ready) pick(ctx->tan.plan);
 }
 
 // Make schedule entries [host_step, host_step + n] available to the main
@@ -643,7 +858,7 @@ colatus_status refill_table(colatus_t ctx) {
 // buffer and run the force sum (segments in ctx->part).
 colatus_status force_at_state(colatus_t ctx) {
     if (ctx->prec == COLATUS_FP64) {
-        const ForcePlan &p = ctx->plan64;
+        const ForcePlan &p = plan_f64(ctx);
         pack_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(ctx->xs64, ctx->pos64[2],
                                                                            ctx->N, p.n_pad);
         TRY(launched(ctx));
@@ -659,21 +874,21 @@ colatus_status force_at_state(colatus_t ctx) {
 // Reduce the segments of the last force sum into acc and/or out.
 colatus_status force_output(colatus_t ctx, void *out, int out_f64, bool to_acc) {
     if (ctx->prec == COLATUS_FP64) {
-        const ForcePlan &p = ctx->plan64;
+        const ForcePlan &p = plan_f64(ctx);
         forces_out_f64_kernel<<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
             static_cast<const double4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk, ctx->G, out,
-            out_f64, to_acc ? ctx->acc64 : nullptr, ctx->pos64[2], defo_args(ctx));
+            out_f64, to_acc ? ctx->acc64 : nullptr, ctx->pos64[2], extra_args(ctx));
         return launched(ctx);
     }
     const ForcePlan &p = plan_f32(ctx);
     if (ctx->prec == COLATUS_FP32_COMP)
         forces_out_f32_kernel<true><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
             static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk, ctx->G, out,
-            out_f64, to_acc ? ctx->acc : nullptr, ctx->pk[2], defo_args(ctx));
+            out_f64, to_acc ? ctx->acc : nullptr, ctx->pk[2], extra_args(ctx));
     else
         forces_out_f32_kernel<false><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
             static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk, ctx->G, out,
-            out_f64, to_acc ? ctx->acc : nullptr, ctx->pk[2], defo_args(ctx));
+            out_f64, to_acc ? ctx->acc : nullptr, ctx->pk[2], extra_args(ctx));
     return launched(ctx);
 }
 
@@ -716,7 +931,7 @@ StepBufs ctx_bufs(colatus_t ctx) {
 // KDK opening (half kick + drift) from (xs, vs) with F = acc into pk[c].
 colatus_status launch_kdk_open(colatus_t ctx, const StepBufs &b, int c, long long step, double tau) {
     if (ctx->prec == COLATUS_FP64) {
-        const ForcePlan &p = ctx->plan64;
+        const ForcePlan &p = plan_f64(ctx);
         kdk_open_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
             b.xs64, b.vs64, b.acc64, b.vh64, b.pos64[c], b.table, b.tcap, step, tau, ctx->N, p.n_pad);
     } else {
@@ -732,9 +947,9 @@ colatus_status launch_kdk_open(colatus_t ctx, const StepBufs &b, int c, long lon
 colatus_status launch_step(colatus_t ctx, const StepBufs &b, int c, long long step, double tau) {
     const int n = c ^ 1;
     const Tracers &tr = b.tr;
-    const Defo D = defo_args(ctx);
+    const Extra D = extra_args(ctx);
     if (ctx->prec == COLATUS_FP64) {
-        const ForcePlan &p = ctx->plan64;
+        const ForcePlan &p = plan_f64(ctx);
         TRY(run_force_f64(ctx, b.pos64[c]));
         const double4 *part = static_cast<const double4 *>(ctx->part);
         if (is_kdk(ctx))
@@ -787,7 +1002,7 @@ colatus_status open_step(colatus_t ctx, double tau) {
         return launch_kdk_open(ctx, ctx_bufs(ctx), ctx->cur, ctx->host_step, tau);
     }
     if (f64) {
-        const ForcePlan &p = ctx->plan64;
+        const ForcePlan &p = plan_f64(ctx);
         dkd_open_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
             ctx->xs64, ctx->vs64, ctx->pos64[ctx->cur], tau, ctx->N, p.n_pad);
     } else {
@@ -940,13 +1155,20 @@ colatus_status colatus_init(colatus_t *out, int64_t N, const double *masses, dou
         return bail(COLATUS_E_CUDA);
     }
     ctx->num_sms = prop.multiProcessorCount;
+    ctx->tab_smem = (int)prop.sharedMemPerBlockOptin;
+    if ((e = cudaFuncSetAttribute(friedmann_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  ctx->tab_smem)) != cudaSuccess) {
+        fail(ctx, COLATUS_E_CUDA, "schedule kernel attributes: %s", cudaGetErrorString(e));
+        return bail(COLATUS_E_CUDA);
+    }
     ctx->N = N;
     ctx->n_alloc = round_up(N, kPadAlloc);
     colatus_status st = build_plans(ctx);
     if (st != COLATUS_OK) return bail(st);
     // every buffer holds the largest padded size any launch plan uses
     for (const ForcePlan &p : ctx->plan32) ctx->n_alloc = std::max(ctx->n_alloc, p.n_pad);
-    for (const ForcePlan *p : {&ctx->plan64, &ctx->plan_vjp32, &ctx->plan_vjp64})
+    for (const ForcePlan *p : {&ctx->plan64, &ctx->plan_vjp32, &ctx->plan_vjp64, &ctx->plan_ew32[0],
+                               &ctx->plan_ew32[1], &ctx->plan_ew64})
         ctx->n_alloc = std::max(ctx->n_alloc, p->n_pad);
     ctx->eps = eps;
     ctx->cosmo = Cosmo{Omega_R, Omega_M, Omega_K, Omega_L, H0};
@@ -1043,6 +1265,7 @@ colatus_status colatus_set_config(colatus_t ctx, colatus_prec prec, colatus_sche
     ctx->prec = prec;
     ctx->scheme = scheme;
     ctx->G = G;
+    if (ctx->periodic && was64 != is64) TRY(ewald_setup(ctx));   // tolerance follows the precision
     return COLATUS_OK;
 }
 
@@ -1133,6 +1356,7 @@ colatus_status colatus_forces(colatus_t ctx, void *acc_out, int dtype, int on_de
     TRY(check_dtype(ctx, dtype));
     if (!acc_out) return fail(ctx, COLATUS_E_ARG, "acc_out is NULL");
     if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
+    choose_grid(ctx);
     TRY(force_at_state(ctx));
     void *dst = on_device ? acc_out : (void *)ctx->stage;
     TRY(force_output(ctx, dst, dtype == COLATUS_F64, true));
@@ -1156,6 +1380,7 @@ colatus_status colatus_step(colatus_t ctx, double dt, int64_t nsteps) {
     for (int64_t done = 0; done < nsteps;) {
         const int n = (int)std::min<int64_t>(kChunk, nsteps - done);
         TRY(need_table(ctx, dt, n));
+        choose_grid(ctx);
         if (!ctx->spec_valid) {
             TRY(open_step(ctx, dt));
             ctx->spec_valid = true;
@@ -1290,10 +1515,12 @@ colatus_status colatus_force_vjp(colatus_t ctx, const void *w, void *gx, void *g
                                  int on_device) {
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
+    if (ctx->periodic) return fail(ctx, COLATUS_E_STATE, "%s is not built for periodic boundaries", "the force VJP");
     TRY(check_dtype(ctx, dtype));
     if (!w || (!gx && !gm)) return fail(ctx, COLATUS_E_ARG, "need w and at least one output");
     if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
     TRY(adj_alloc(ctx));
+    choose_grid(ctx);
     const int f64in = dtype == COLATUS_F64;
     const size_t vbytes = (size_t)ctx->N * 3 * elem_size(dtype);
     const void *src = w;
@@ -1317,7 +1544,7 @@ colatus_status colatus_force_vjp(colatus_t ctx, const void *w, void *gx, void *g
         vjp_out_f64_kernel<<<nb, 256, 0, ctx->stream>>>(static_cast<const double4 *>(ctx->part), p.L,
                                                         p.itile, ctx->N, dgx, dgm, f64in,
                                                         static_cast<const double4 *>(ctx->adj.pkw),
-                                                        defo_args(ctx));
+                                                        extra_args(ctx));
     } else {
         const ForcePlan &p = ctx->plan_vjp32;
         vec3_to4_kernel<float4, float><<<nb, 256, 0, ctx->stream>>>(
@@ -1331,7 +1558,7 @@ colatus_status colatus_force_vjp(colatus_t ctx, const void *w, void *gx, void *g
         vjp_out_f32_kernel<<<nb, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part), p.L,
                                                         p.itile, ctx->N, dgx, dgm, f64in,
                                                         static_cast<const float *>(ctx->adj.pkw),
-                                                        defo_args(ctx));
+                                                        extra_args(ctx));
     }
     TRY(launched(ctx));
     if (!on_device) {
@@ -1348,6 +1575,7 @@ colatus_status colatus_adjoint_forward(colatus_t ctx, double dt, int64_t nsteps,
                                        int64_t checkpoint_every) {
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
+    if (ctx->periodic) return fail(ctx, COLATUS_E_STATE, "%s is not built for periodic boundaries", "the adjoint");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, COLATUS_E_ARG, "dt must be finite and > 0");
     if (nsteps < 1 || checkpoint_every < 1)
         return fail(ctx, COLATUS_E_ARG, "nsteps and checkpoint_every must be >= 1");
@@ -1413,6 +1641,7 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
     if (!a.ready) return fail(ctx, COLATUS_E_STATE, "no adjoint forward pass recorded");
     if (ctx->host_step != a.step0 + a.nsteps || ctx->prec != a.prec)
         return fail(ctx, COLATUS_E_STATE, "the state moved on since the adjoint forward pass");
+    choose_grid(ctx);
     const bool f64 = ctx->prec == COLATUS_FP64;
     const int in64 = dtype == COLATUS_F64;
     const size_t vbytes = (size_t)ctx->N * 3 * elem_size(dtype);
@@ -1475,14 +1704,14 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
             b.tr = Tracers{nullptr, nullptr, 1, 0, 0};
             // F at the checkpoint
             if (f64) {
-                const ForcePlan &p = ctx->plan64;
+                const ForcePlan &p = plan_f64(ctx);
                 pack_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
                     b.xs64, b.pos64[0], ctx->N, p.n_pad);
                 TRY(launched(ctx));
                 TRY(run_force_f64(ctx, b.pos64[0]));
                 forces_out_f64_kernel<<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
                     static_cast<const double4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk, ctx->G,
-                    nullptr, 0, b.acc64, b.pos64[0], defo_args(ctx));
+                    nullptr, 0, b.acc64, b.pos64[0], extra_args(ctx));
             } else {
                 const ForcePlan &p = plan_f32(ctx);
                 pack_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
@@ -1492,11 +1721,11 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
                 if (ctx->prec == COLATUS_FP32_COMP)
                     forces_out_f32_kernel<true><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
                         static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk,
-                        ctx->G, nullptr, 0, b.acc, b.pk[0], defo_args(ctx));
+                        ctx->G, nullptr, 0, b.acc, b.pk[0], extra_args(ctx));
                 else
                     forces_out_f32_kernel<false><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
                         static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk,
-                        ctx->G, nullptr, 0, b.acc, b.pk[0], defo_args(ctx));
+                        ctx->G, nullptr, 0, b.acc, b.pk[0], extra_args(ctx));
             }
             TRY(launched(ctx));
             TRY(launch_kdk_open(ctx, b, 1, s0, a.tau));
@@ -1518,14 +1747,14 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
                     static_cast<const double4 *>(pos(n)), static_cast<double4 *>(a.lx),
                     static_cast<double4 *>(a.lv), static_cast<double4 *>(a.lvh),
                     static_cast<double *>(a.lm), a.table, n, a.tau, static_cast<double4 *>(a.pkw),
-                    ctx->N, pv.n_pad, defo_args(ctx));
+                    ctx->N, pv.n_pad, extra_args(ctx));
             else
                 adj_step_f32_kernel<<<nbv, 256, 0, ctx->stream>>>(
                     static_cast<const float4 *>(ctx->part), pv.L, pv.itile,
                     static_cast<const float4 *>(pos(n)), static_cast<float4 *>(a.lx),
                     static_cast<float4 *>(a.lv), static_cast<float4 *>(a.lvh),
                     static_cast<float *>(a.lm), a.table, n, a.tau, static_cast<float *>(a.pkw),
-                    ctx->N, pv.n_pad, defo_args(ctx));
+                    ctx->N, pv.n_pad, extra_args(ctx));
             TRY(launched(ctx));
         }
     }
@@ -1539,7 +1768,7 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
                                                           pv.L, pv.itile, static_cast<double4 *>(a.lx),
                                                           static_cast<double *>(a.lm), ctx->N,
                                                           static_cast<const double4 *>(a.pkw),
-                                                          defo_args(ctx));
+                                                          extra_args(ctx));
         TRY(launched(ctx));
         adj_store_kernel<double4, double><<<nb, 256, 0, ctx->stream>>>(
             static_cast<const double4 *>(a.lx), static_cast<const double4 *>(a.lv),
@@ -1549,7 +1778,7 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
                                                           pv.L, pv.itile, static_cast<float4 *>(a.lx),
                                                           static_cast<float *>(a.lm), ctx->N,
                                                           static_cast<const float *>(a.pkw),
-                                                          defo_args(ctx));
+                                                          extra_args(ctx));
         TRY(launched(ctx));
         adj_store_kernel<float4, float><<<nb, 256, 0, ctx->stream>>>(
             static_cast<const float4 *>(a.lx), static_cast<const float4 *>(a.lv),
@@ -1569,6 +1798,7 @@ colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, 
                                     int64_t capacity_steps) {
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
+    if (ctx->periodic) return fail(ctx, COLATUS_E_STATE, "%s is not built for periodic boundaries", "the tangent model");
     auto &t = ctx->tan;
     if (B < 1 || !seeds || capacity_steps < 1) return fail(ctx, COLATUS_E_ARG, "need B >= 1 seeds and capacity");
     for (int b = 0; b < B; ++b)
@@ -1592,20 +1822,29 @@ colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, 
     t.B = B;
     t.nchunk = (B + kTB - 1) / kTB;
     t.n_pad = round_up(ctx->N, std::max(JvpK::ITILE, kJvpJT));
-    ForceLaunch L{};
-    L.n_it = (int)(t.n_pad / JvpK::ITILE);
-    L.n_jt = (int)(t.n_pad / kJvpJT);
-    L.W = (long long)t.nchunk * L.n_it * L.n_jt;
-    L.G = (int)std::max(1LL, std::min<long long>((long long)occ * ctx->num_sms, L.W));
-    long long smax = 1;
-    for (long long ct = 0; ct < (long long)t.nchunk * L.n_it; ++ct)
-        smax = std::max(smax, sk_owner((ct + 1) * L.n_jt - 1, L.W, L.G) - sk_owner(ct * L.n_jt, L.W, L.G) + 1);
-    L.S_max = (int)smax;
-    t.plan.L = L;
+    // units over all chunks' (i-tile x j-tile) pairs, full grid and one SM free
+    auto jvp_launch = [&](int sms) {
+        ForceLaunch L{};
+        L.n_it = (int)(t.n_pad / JvpK::ITILE);
+        L.n_jt = (int)(t.n_pad / kJvpJT);
+        L.W = (long long)t.nchunk * L.n_it * L.n_jt;
+        L.G = (int)std::max(1LL, std::min<long long>((long long)occ * sms, L.W));
+        long long smax = 1;
+        for (long long ct = 0; ct < (long long)t.nchunk * L.n_it; ++ct)
+            smax = std::max(smax, sk_owner((ct + 1) * L.n_jt - 1, L.W, L.G) -
+                                      sk_owner(ct * L.n_jt, L.W, L.G) + 1);
+        L.S_max = (int)smax;
+        return L;
+    };
+    t.plan.L_full = jvp_launch(ctx->num_sms);
+    t.plan.L_red = jvp_launch(std::max(1, ctx->num_sms - 1));
+    t.plan.L = t.plan.L_full;
     t.plan.itile = JvpK::ITILE;
     t.plan.jt = kJvpJT;
     t.plan.n_pad = t.n_pad;
-    t.plan.part_bytes = (size_t)t.nchunk * L.n_it * smax * 3 * JvpK::ITILE * sizeof(float4);
+    t.plan.part_bytes = (size_t)t.nchunk * t.plan.L_full.n_it *
+                        std::max(t.plan.L_full.S_max, t.plan.L_red.S_max) * 3 * JvpK::ITILE *
+                        sizeof(float4);
     const size_t tb = (size_t)B * t.n_pad * sizeof(float4);
     CU(cudaMalloc(&t.dx, tb));
     CU(cudaMalloc(&t.dv, tb));
@@ -1633,6 +1872,7 @@ colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, 
 colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps) {
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
+    if (ctx->periodic) return fail(ctx, COLATUS_E_STATE, "%s is not built for periodic boundaries", "the tangent model");
     auto &t = ctx->tan;
     if (!t.ready) return fail(ctx, COLATUS_E_STATE, "colatus_tangent_init first");
     if (ctx->prec == COLATUS_FP64 || !is_kdk(ctx))
@@ -1648,6 +1888,7 @@ colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps) {
     for (int64_t done = 0; done < nsteps;) {
         const int n = (int)std::min<int64_t>(kChunk, nsteps - done);
         TRY(need_table(ctx, dt, n));
+        choose_grid(ctx);
         if (!t.open) {
             // tangent opening at x^n: JVP on the packed state positions
             const ForcePlan &p = plan_f32(ctx);
@@ -1658,7 +1899,7 @@ colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps) {
             tan_open_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part),
                                                            t.plan.L, t.plan.itile, T, ctx->table,
                                                            kTabCap, ctx->host_step, dt, ctx->N, t.n_pad,
-                                                           defo_args(ctx));
+                                                           extra_args(ctx));
             TRY(launched(ctx));
             t.open = true;
             t.tau = dt;
@@ -1675,7 +1916,7 @@ colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps) {
             tan_step_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part),
                                                            t.plan.L, t.plan.itile, T, ctx->table,
                                                            kTabCap, ctx->host_step + j, dt, ctx->N,
-                                                           t.n_pad, defo_args(ctx));
+                                                           t.n_pad, extra_args(ctx));
             TRY(launched(ctx));
         }
         done += n;
@@ -1714,7 +1955,7 @@ colatus_status colatus_set_tuning(colatus_t ctx, int shape) {
     if (shape < -1 || shape >= kShapes) return fail(ctx, COLATUS_E_ARG, "shape must be -1 .. %d", kShapes - 1);
     if (shape >= 0) {
         const ForcePlan &p = ctx->plan32[4 * shape];
-        if (p.L.W < p.L.G) return fail(ctx, COLATUS_E_ARG, "shape %d does not fit N", shape);
+        if (p.L_full.W < p.L_full.G) return fail(ctx, COLATUS_E_ARG, "shape %d does not fit N", shape);
     }
     ctx->tuned_shape = shape;
     return COLATUS_OK;
@@ -1723,10 +1964,12 @@ colatus_status colatus_set_tuning(colatus_t ctx, int shape) {
 colatus_status colatus_autotune(colatus_t ctx, int reps, double out_ms[3], int *chosen) {
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
+    if (ctx->periodic) return fail(ctx, COLATUS_E_STATE, "%s is not built for periodic boundaries", "autotuning");
     if (reps < 1) return fail(ctx, COLATUS_E_ARG, "reps must be >= 1");
     if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
     if (ctx->prec == COLATUS_FP64) return fail(ctx, COLATUS_E_ARG, "the tuned kernels are FP32");
     TRY(sync_and_check(ctx));
+    choose_grid(ctx);
     const int keep = ctx->tuned_shape;
     const bool prof = ctx->profiling;
     const size_t used = ctx->ev_used;
@@ -1805,6 +2048,42 @@ colatus_status colatus_probe_pipes(double out[6]) {
     return st;
 }
 
+colatus_status colatus_set_periodic(colatus_t ctx, double L, double alpha, int nk) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    if (L == 0.0) {
+        if (ctx->periodic) {
+            ctx->periodic = false;
+            ctx->acc_valid = ctx->spec_valid = false;
+        }
+        return COLATUS_OK;
+    }
+    if (!(L > 0.0) || !std::isfinite(L)) return fail(ctx, COLATUS_E_ARG, "L must be finite and > 0");
+    if (!std::isfinite(alpha)) return fail(ctx, COLATUS_E_ARG, "alpha must be finite");
+    if (nk > kEwMaxNk) return fail(ctx, COLATUS_E_ARG, "nk must be <= %d", kEwMaxNk);
+    if (ctx->defo_C != 0.0)
+        return fail(ctx, COLATUS_E_ARG, "periodic boundaries do not combine with the deformation term");
+    ctx->box = L;
+    ctx->ew_alpha_req = alpha;
+    ctx->ew_nk_req = nk;
+    ctx->periodic = true;
+    colatus_status st = ewald_setup(ctx);
+    if (st != COLATUS_OK) ctx->periodic = false;
+    ctx->acc_valid = ctx->spec_valid = false;
+    ctx->tan.open = false;
+    ctx->adj.ready = false;
+    return st;
+}
+
+colatus_status colatus_periodic_params(colatus_t ctx, double *alpha_out, int *nk_out, int *nkv_out) {
+    if (!ctx) return COLATUS_E_ARG;
+    if (!ctx->periodic) return fail(ctx, COLATUS_E_STATE, "boundaries are not periodic");
+    if (alpha_out) *alpha_out = ctx->ew.alpha;
+    if (nk_out) *nk_out = ctx->ew.nk;
+    if (nkv_out) *nkv_out = ctx->nkv;
+    return COLATUS_OK;
+}
+
 colatus_status colatus_set_deformation(colatus_t ctx, double Cpsi, const double *x_psi) {
     if (!ctx) return COLATUS_E_ARG;
     if (!std::isfinite(Cpsi)) return fail(ctx, COLATUS_E_ARG, "C psi must be finite");
@@ -1813,6 +2092,8 @@ colatus_status colatus_set_deformation(colatus_t ctx, double Cpsi, const double 
         for (int c = 0; c < 3; ++c)
             if (!std::isfinite(x_psi[c])) return fail(ctx, COLATUS_E_ARG, "x_psi must be finite");
         if (ctx->G == 0.0) return fail(ctx, COLATUS_E_ARG, "the deformation term needs G != 0");
+        if (ctx->periodic)
+            return fail(ctx, COLATUS_E_ARG, "the deformation term does not combine with periodic boundaries");
         for (int c = 0; c < 3; ++c) ctx->defo_x[c] = x_psi[c];
     }
     ctx->defo_C = Cpsi;

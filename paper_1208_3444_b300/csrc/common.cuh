@@ -122,15 +122,20 @@ struct Cosmo {
     double Omega_R, Omega_M, Omega_K, Omega_L, H0;
 };
 
-// Eq. 6 deformation term, as a G-less addition to the raw force:
-// kappa (x_psi - x) / (|x - x_psi|^2 + eps^2)^{3/2} with kappa = C psi / G
-// (the pull of a fixed point mass C psi / G at x_psi).
-struct Defo {
+// O(N) per-body terms the epilogues add to the pair sum (both G-less, like
+// the raw force):
+//  * the Eq. 6 deformation pull kappa (x_psi - x) / (|x - x_psi|^2 + eps^2)^{3/2}
+//    with kappa = C psi / G (a fixed point mass C psi / G at x_psi), when on;
+//  * the reciprocal-space part of the periodic (Ewald) force, lr32 / lr64[i],
+//    when not null.
+struct Extra {
     double kappa, x, y, z, eps2;
     int on, pad;
+    const float4 *lr32;
+    const double4 *lr64;
 };
 
-__device__ __forceinline__ void defo_force(const Defo &D, double px, double py, double pz, double &fx,
+__device__ __forceinline__ void defo_force(const Extra &D, double px, double py, double pz, double &fx,
                                            double &fy, double &fz) {
     if (!D.on) return;
     const double dx = D.x - px, dy = D.y - py, dz = D.z - pz;
@@ -144,7 +149,7 @@ __device__ __forceinline__ void defo_force(const Defo &D, double px, double py, 
 
 // FP32 paths evaluate the O(N) term in FP64 too: x_psi is not float-exact,
 // and near x_psi its rounding is amplified by 1/s.
-__device__ __forceinline__ void defo_force(const Defo &D, float px, float py, float pz, float &fx,
+__device__ __forceinline__ void defo_force(const Extra &D, float px, float py, float pz, float &fx,
                                            float &fy, float &fz) {
     if (!D.on) return;
     double gx = 0.0, gy = 0.0, gz = 0.0;
@@ -154,11 +159,29 @@ __device__ __forceinline__ void defo_force(const Defo &D, float px, float py, fl
     fz += (float)gz;
 }
 
+__device__ __forceinline__ void add_long_range(const Extra &E, long long i, float &fx, float &fy,
+                                               float &fz) {
+    if (!E.lr32) return;
+    const float4 l = E.lr32[i];
+    fx += l.x;
+    fy += l.y;
+    fz += l.z;
+}
+
+__device__ __forceinline__ void add_long_range(const Extra &E, long long i, double &fx, double &fy,
+                                               double &fz) {
+    if (!E.lr64) return;
+    const double4 l = E.lr64[i];
+    fx += l.x;
+    fy += l.y;
+    fz += l.z;
+}
+
 // Derivative of the deformation term along w: -kappa J(d) w, d = x_psi - x,
 // J(d) = I/s^3 - 3 d d^T/s^5 (symmetric, so this is also its transpose).
 // Evaluated in FP64 for both element types.
 template <typename T>
-__device__ __forceinline__ void defo_jacobian(const Defo &D, T px, T py, T pz, T wx, T wy, T wz,
+__device__ __forceinline__ void defo_jacobian(const Extra &D, T px, T py, T pz, T wx, T wy, T wz,
                                               T &gx, T &gy, T &gz) {
     if (!D.on) return;
     const double dx = D.x - (double)px, dy = D.y - (double)py, dz = D.z - (double)pz;

@@ -252,7 +252,7 @@ template <bool COMP>
 __global__ void forces_out_f32_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
                                       long long N, const DevClock *__restrict__ clk, double G,
                                       void *out, int out_f64, float4 *__restrict__ acc,
-                                      const float *__restrict__ pk, Defo D) {
+                                      const float *__restrict__ pk, Extra D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double a = clk->a;
@@ -262,6 +262,7 @@ __global__ void forces_out_f32_kernel(const float4 *__restrict__ part, ForceLaun
         const float4 x = pk_load(pk, i);
         defo_force(D, x.x, x.y, x.z, f.x, f.y, f.z);
     }
+    add_long_range(D, i, f.x, f.y, f.z);
     if (acc) acc[i] = make_float4(f.x, f.y, f.z, 0.f);
     if (out) {
         if (out_f64) {
@@ -281,7 +282,7 @@ __global__ void forces_out_f32_kernel(const float4 *__restrict__ part, ForceLaun
 __global__ void forces_out_f64_kernel(const double4 *__restrict__ part, ForceLaunch L, int itile,
                                       long long N, const DevClock *__restrict__ clk, double G,
                                       void *out, int out_f64, double4 *__restrict__ acc,
-                                      const double4 *__restrict__ pos, Defo D) {
+                                      const double4 *__restrict__ pos, Extra D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double a = clk->a;
@@ -291,6 +292,7 @@ __global__ void forces_out_f64_kernel(const double4 *__restrict__ part, ForceLau
         const double4 x = pos[i];
         defo_force(D, x.x, x.y, x.z, f.x, f.y, f.z);
     }
+    add_long_range(D, i, f.x, f.y, f.z);
     if (acc) acc[i] = make_double4(f.x, f.y, f.z, 0.0);
     if (out) {
         if (out_f64) {
@@ -370,7 +372,7 @@ __global__ void kdk_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
                                     float4 *__restrict__ vs, float4 *__restrict__ vh,
                                     float4 *__restrict__ acc, float *__restrict__ pk_out,
                                     const StepCoef *__restrict__ table, int tcap, long long step, double tau,
-                                    long long N, long long N_pad, Tracers tr, int *flags, DevClock *clk, Defo D) {
+                                    long long N, long long N_pad, Tracers tr, int *flags, DevClock *clk, Extra D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N_pad) return;
     if (i >= N) {
@@ -385,6 +387,7 @@ __global__ void kdk_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
     float3 F = reduce_f32<COMP>(part, L, itile, i);
     const float4 x = pk_load(pk_in, i);
     defo_force(D, x.x, x.y, x.z, F.x, F.y, F.z);
+    add_long_range(D, i, F.x, F.y, F.z);
     const float4 h = vh[i];
     const float vx = c2 * h.x + d2 * F.x, vy = c2 * h.y + d2 * F.y, vz = c2 * h.z + d2 * F.z;
     acc[i] = make_float4(F.x, F.y, F.z, 0.f);
@@ -421,7 +424,7 @@ __global__ void dkd_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
                                     float4 *__restrict__ vs, float4 *__restrict__ acc,
                                     float *__restrict__ pk_out, const StepCoef *__restrict__ table,
                                     int tcap, long long step, double tau, long long N, long long N_pad, Tracers tr,
-                                    int *flags, DevClock *clk, Defo D) {
+                                    int *flags, DevClock *clk, Extra D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N_pad) return;
     if (i >= N) {
@@ -434,6 +437,7 @@ __global__ void dkd_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
     float3 F = reduce_f32<COMP>(part, L, itile, i);
     const float4 xh = pk_load(pk_in, i);
     defo_force(D, xh.x, xh.y, xh.z, F.x, F.y, F.z);
+    add_long_range(D, i, F.x, F.y, F.z);
     const float4 v0 = vs[i];
     const float vx = c * v0.x + d * F.x, vy = c * v0.y + d * F.y, vz = c * v0.z + d * F.z;
     const float x1 = xh.x + h * vx, y1 = xh.y + h * vy, z1 = xh.z + h * vz;
@@ -469,7 +473,7 @@ __global__ void kdk_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
                                     double4 *__restrict__ vs, double4 *__restrict__ vh,
                                     double4 *__restrict__ acc, double4 *__restrict__ pos_out,
                                     const StepCoef *__restrict__ table, int tcap, long long step, double tau,
-                                    long long N, long long N_pad, Tracers tr, int *flags, DevClock *clk, Defo D) {
+                                    long long N, long long N_pad, Tracers tr, int *flags, DevClock *clk, Extra D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N_pad) return;
     if (i >= N) {
@@ -483,6 +487,7 @@ __global__ void kdk_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
     double3 F = reduce_f64(part, L, itile, i);
     const double4 x = pos_in[i];
     defo_force(D, x.x, x.y, x.z, F.x, F.y, F.z);
+    add_long_range(D, i, F.x, F.y, F.z);
     const double4 h = vh[i];
     const double vx = c2 * h.x + d2 * F.x, vy = c2 * h.y + d2 * F.y, vz = c2 * h.z + d2 * F.z;
     acc[i] = make_double4(F.x, F.y, F.z, 0.0);
@@ -514,7 +519,7 @@ __global__ void dkd_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
                                     double4 *__restrict__ vs, double4 *__restrict__ acc,
                                     double4 *__restrict__ pos_out,
                                     const StepCoef *__restrict__ table, int tcap, long long step, double tau,
-                                    long long N, long long N_pad, Tracers tr, int *flags, DevClock *clk, Defo D) {
+                                    long long N, long long N_pad, Tracers tr, int *flags, DevClock *clk, Extra D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N_pad) return;
     if (i >= N) {
@@ -527,6 +532,7 @@ __global__ void dkd_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
     double3 F = reduce_f64(part, L, itile, i);
     const double4 xh = pos_in[i];
     defo_force(D, xh.x, xh.y, xh.z, F.x, F.y, F.z);
+    add_long_range(D, i, F.x, F.y, F.z);
     const double4 v0 = vs[i];
     const double vx = c * v0.x + d * F.x, vy = c * v0.y + d * F.y, vz = c * v0.z + d * F.z;
     const double x1 = xh.x + h * vx, y1 = xh.y + h * vy, z1 = xh.z + h * vz;

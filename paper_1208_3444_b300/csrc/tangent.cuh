@@ -215,7 +215,7 @@ __global__ void tan_pack_kernel(const float *__restrict__ pk, TangentState T, lo
 
 // Opening of the tangent: dvh = c1 dv + d1 dF(x^n);  dx' = dx + tau dvh.
 // Deformation term's tangent at the packed position of (chunk, i).
-__device__ __forceinline__ void tan_defo(const TangentState &T, const Defo &D, int chunk,
+__device__ __forceinline__ void tan_defo(const TangentState &T, const Extra &D, int chunk,
                                          long long i, long long n_pad, float (&f)[12]) {
     if (!D.on) return;
     const float4 x = T.pkt[((long long)chunk * n_pad + i) * 4];
@@ -230,7 +230,7 @@ __device__ __forceinline__ void tan_defo(const TangentState &T, const Defo &D, i
 
 __global__ void tan_open_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
                                 TangentState T, const StepCoef *__restrict__ table, int tcap,
-                                long long step, double tau, long long N, long long n_pad, Defo D) {
+                                long long step, double tau, long long N, long long n_pad, Extra D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int chunk = blockIdx.y;
     if (i >= N) return;
@@ -258,7 +258,7 @@ __global__ void tan_open_kernel(const float4 *__restrict__ part, ForceLaunch L, 
 // coefficients: dvh = c1' dv + d1' dF, dx += tau dvh.
 __global__ void tan_step_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
                                 TangentState T, const StepCoef *__restrict__ table, int tcap,
-                                long long step, double tau, long long N, long long n_pad, Defo D) {
+                                long long step, double tau, long long N, long long n_pad, Extra D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int chunk = blockIdx.y;
     if (i >= N) return;
