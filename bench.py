@@ -236,6 +236,13 @@ def time_adjoint(B, inputs, torch, stream, nsteps=40, k=20):
                        stream=stream.cuda_stream)
     try:
         sim.set_state(ic.x, ic.v)
+        gv = np.zeros((ic.N, 3))
+        gv[inputs.tracers(ic.N, 64, 7)] = 1.0
+        # warm-up pass of the same shape: loads the adjoint kernels (lazy
+        # module loading) and sizes the checkpoint buffers outside the timed region
+        sim.adjoint_forward(tau, nsteps, k)
+        sim.adjoint_backward(None, gv)
+        sim.set_state(ic.x, ic.v)
         sim.step(tau, 3)
         sim.synchronize()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -243,8 +250,6 @@ def time_adjoint(B, inputs, torch, stream, nsteps=40, k=20):
         ev[0].record(stream)
         sim.adjoint_forward(tau, nsteps, k)
         ev[1].record(stream)
-        gv = np.zeros((ic.N, 3))
-        gv[inputs.tracers(ic.N, 64, 7)] = 1.0
         fwd = sim.profile_read_all()
         ev[2].record(stream)
         sim.adjoint_backward(None, gv)

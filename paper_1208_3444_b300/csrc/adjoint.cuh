@@ -35,8 +35,9 @@ struct VjpKernel {
 };
 
 // One j-tile of the VJP for the IPT i-bodies of this thread.  ibase: index of
-// the tile's first j-body; MASK: the tile may contain i itself.
-template <int IPT, int JT, bool MASK>
+// the tile's first j-body; MASK: the tile may contain i itself; UNR: unroll
+// depth of the j-pair loop (a tuning knob).
+template <int IPT, int JT, bool MASK, int UNR>
 __device__ __forceinline__ void vjp_tile(const float4 *__restrict__ t, long long jbase,
                                          const long long (&ii)[IPT], const float2 (&nx)[IPT],
                                          const float2 (&ny)[IPT], const float2 (&nz)[IPT],
@@ -45,7 +46,7 @@ __device__ __forceinline__ void vjp_tile(const float4 *__restrict__ t, long long
                                          const float2 e2, float2 (&Ux)[IPT], float2 (&Uy)[IPT],
                                          float2 (&Uz)[IPT], float2 (&Bm)[IPT], float2 (&Vx)[IPT],
                                          float2 (&Vy)[IPT], float2 (&Vz)[IPT], float2 (&Gm)[IPT]) {
-#pragma unroll 1
+#pragma unroll (UNR)
     for (int q = 0; q < JT / 2; ++q) {
         const float4 A = t[4 * q];
         const float4 Bq = t[4 * q + 1];
@@ -93,7 +94,7 @@ __device__ __forceinline__ void vjp_tile(const float4 *__restrict__ t, long long
     }
 }
 
-template <int NT, int IPT, int JT, int STAGES, int MINB>
+template <int NT, int IPT, int JT, int STAGES, int MINB, int UNR = 1>
 __global__ void __launch_bounds__(NT, MINB)
     vjp_f32_kernel(const float *__restrict__ pkw, float4 *__restrict__ part, int *__restrict__ flags,
                    ForceLaunch L, float eps2) {
@@ -157,10 +158,10 @@ __global__ void __launch_bounds__(NT, MINB)
                 const long long jt = u % n_jt;
                 const long long jlo = jt * JT;
                 if (jlo < ihi && jlo + JT > ilo)
-                    vjp_tile<IPT, JT, true>(tiles + stage * TILE_F4, jlo, ii, nx, ny, nz, mi, wxi,
+                    vjp_tile<IPT, JT, true, UNR>(tiles + stage * TILE_F4, jlo, ii, nx, ny, nz, mi, wxi,
                                             wyi, wzi, e2, Ux, Uy, Uz, Bm, Vx, Vy, Vz, Gm);
                 else
-                    vjp_tile<IPT, JT, false>(tiles + stage * TILE_F4, jlo, ii, nx, ny, nz, mi, wxi,
+                    vjp_tile<IPT, JT, false, UNR>(tiles + stage * TILE_F4, jlo, ii, nx, ny, nz, mi, wxi,
                                              wyi, wzi, e2, Ux, Uy, Uz, Bm, Vx, Vy, Vz, Gm);
             }
             if (__syncthreads_or(!ok)) {
