@@ -84,9 +84,9 @@ constexpr int kF64NT = 128, kF64IPT = 2, kF64JT = 64;
 using F64K = F64Kernel<kF64NT, kF64IPT, kF64JT, kStages>;
 
 // VJP kernels: FP32 256 threads x 4 i-bodies, 256-body j-tiles, one CTA per
-// SM, j-loop unrolled by 2 (the fastest of a sweep of 20 shapes on B300 at
-// 32^3: 3.66 interactions/SM/clk); FP64 128 x 1, 32-body tiles
-constexpr int kVjpNT = 256, kVjpIPT = 4, kVjpJT = 256, kVjpMINB = 1, kVjpUnr = 2;
+// SM, j-loop unrolled by 4 (the fastest of a sweep of about 30 shapes and
+// unroll depths on B300 at 32^3); FP64 128 x 1, 32-body tiles
+constexpr int kVjpNT = 256, kVjpIPT = 4, kVjpJT = 256, kVjpMINB = 1, kVjpUnr = 4;
 using VjpK = VjpKernel<kVjpNT, kVjpIPT, kVjpJT, kStages>;
 constexpr int kV64NT = 128, kV64JT = 32;
 using Vjp64K = Vjp64Kernel<kV64NT, kV64JT, kStages>;
@@ -269,6 +269,7 @@ struct colatus_ctx {
         void *ck_x = nullptr, *ck_v = nullptr;   // [nck][n_alloc] checkpoints (float4 / double4)
         void *seg_x = nullptr;                   // [k][n_alloc] recomputed positions
         StepCoef *table = nullptr;               // [nsteps] schedule of the forward
+        cudaEvent_t tab_ev = nullptr;            // table computed (side stream)
         DevClock *rclk = nullptr;                // scratch clock
         void *rvs = nullptr, *rvh = nullptr, *racc = nullptr;   // recompute state
         void *rpk[2] = {nullptr, nullptr};       // recompute force inputs
@@ -751,6 +752,7 @@ void free_all(colatus_t ctx) {
         if (p) cudaFree(p);
     for (cudaEvent_t e : ctx->tab_ev)
         if (e) cudaEventDestroy(e);
+    if (ctx->adj.tab_ev) cudaEventDestroy(ctx->adj.tab_ev);
     if (ctx->main_ev) cudaEventDestroy(ctx->main_ev);
     if (ctx->tstream) cudaStreamDestroy(ctx->tstream);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -800,6 +802,7 @@ colatus_status extend_table(colatus_t ctx, int n) {
 bool extension_in_flight(colatus_t ctx) {
     for (int k = 0; k < kTabEvents; ++k)
         if (ctx->tab_ev[k] && cudaEventQuery(ctx->tab_ev[k]) == cudaErrorNotReady) return true;
+    if (ctx->adj.tab_ev && cudaEventQuery(ctx->adj.tab_ev) == cudaErrorNotReady) return true;
     return false;
 }
 
@@ -1034,6 +1037,7 @@ colatus_status adj_alloc(colatus_t ctx) {
     CU(cudaMalloc(&a.lm, na * 8));
     CU(cudaMalloc(&a.rclk, sizeof(DevClock)));
     CU(cudaMalloc(&a.pkw, na * 64));
+    CU(cudaEventCreateWithFlags(&a.tab_ev, cudaEventDisableTiming));
     return COLATUS_OK;
 }
 
@@ -1608,10 +1612,15 @@ colatus_status colatus_adjoint_forward(colatus_t ctx, double dt, int64_t nsteps,
     TRY(launched(ctx));
     // index the forward's schedule by step within the pass (0 .. nsteps-1)
     CU(cudaMemsetAsync(&a.rclk->step, 0, sizeof(a.rclk->step), ctx->stream));
-    friedmann_table_kernel<<<1, 1, 0, ctx->stream>>>(ctx->cosmo, a.rclk, a.table, (int)nsteps,
-                                                     (int)nsteps, dt, ctx->G, kFriedmannSub,
-                                                     canonical(ctx));
+    // only the backward pass reads it: computed on the side stream, off the
+    // forward steps' critical path (which then use the smaller grids)
+    CU(cudaEventRecord(ctx->main_ev, ctx->stream));
+    CU(cudaStreamWaitEvent(ctx->tstream, ctx->main_ev, 0));
+    friedmann_table_kernel<<<1, 1, ctx->tab_smem, ctx->tstream>>>(
+        ctx->cosmo, a.rclk, a.table, (int)nsteps, (int)nsteps, dt, ctx->G, kFriedmannSub,
+        canonical(ctx));
     TRY(launched(ctx));
+    CU(cudaEventRecord(a.tab_ev, ctx->tstream));
     const long long step0 = ctx->host_step;
     const bool f64 = ctx->prec == COLATUS_FP64;
     for (int c = 0; c < nck; ++c) {
@@ -1643,6 +1652,7 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
     if (!a.ready) return fail(ctx, COLATUS_E_STATE, "no adjoint forward pass recorded");
     if (ctx->host_step != a.step0 + a.nsteps || ctx->prec != a.prec)
         return fail(ctx, COLATUS_E_STATE, "the state moved on since the adjoint forward pass");
+    CU(cudaStreamWaitEvent(ctx->stream, a.tab_ev, 0));   // the forward's schedule
     choose_grid(ctx);
     const bool f64 = ctx->prec == COLATUS_FP64;
     const int in64 = dtype == COLATUS_F64;
