@@ -520,6 +520,7 @@ colatus_status ewald_setup(colatus_t ctx) {
     A.alpha_f = (float)alpha;
     A.alpha2_log2e = (float)(alpha * alpha / std::log(2.0));
     A.cg = (float)(2.0 * alpha / std::sqrt(pi));
+    A.p_alpha = (float)((double)kAsP * alpha);
     A.s0 = (float)(-4.0 / 3.0 * alpha * alpha * alpha / std::sqrt(pi));
     A.s1 = (float)(0.8 * std::pow(alpha, 5) / std::sqrt(pi));
     A.x2_series = (float)((0.05 / alpha) * (0.05 / alpha));

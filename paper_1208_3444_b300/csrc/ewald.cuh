@@ -47,6 +47,7 @@ struct EwaldArgs {
     float Lf, invLf;          // box and 1/box
     float alpha2_log2e;       // alpha^2 log2(e): exp(-alpha^2 r^2) = 2^(-this r^2)
     float alpha_f, cg;        // alpha; 2 alpha / sqrt(pi)
+    float p_alpha;            // A&S 7.1.26 p times alpha
     float s0, s1;             // series of the bracket: s0 + s1 r^2 for alpha r < 0.05
     float x2_series;          // (0.05 / alpha)^2: r^2 below which the series is used
     int nk;                   // |n| <= nk in each table
@@ -80,9 +81,22 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
-__device__ __forceinline__ float2 rint2(float2 v) { return make_float2(rintf(v.x), rintf(v.y)); }
+// Minimum image of a pair-packed separation on the FMA pipe: fma(d, 1/L, M)
+// with M = 1.5 * 2^23 rounds d/L to the nearest integer (ties to even) in
+// its single rounding, for |d/L| < 2^22; subtracting M leaves that integer n,
+// and d - L n is the minimum image.  (rintf runs on the XU pipe, which the
+// pair body already loads with four MUFU results.)
+__device__ __forceinline__ float2 min_image2(float2 d, float2 iL, float2 Lm) {
+    const float2 magic = make_float2(12582912.f, 12582912.f);
+    const float2 n = __fadd2_rn(__ffma2_rn(d, iL, magic), make_float2(-12582912.f, -12582912.f));
+    return __ffma2_rn(Lm, n, d);
+}
 
-// Real-space bracket times m_j for two j-bodies at once (packed f32x2).
+// Real-space bracket times m_j for two j-bodies at once (packed f32x2):
+//   m_j [ (r^2+eps^2)^{-3/2} + (1/r^2) (e (q_erfc / r + cg) - 1/r) ],
+// e = exp(-alpha^2 r^2), q_erfc = erfc(alpha r) / e from A&S 7.1.26 with
+// t = 1 / (1 + p alpha r); 36 FP32 lane-ops and 4 MUFU results per pair
+// including the minimum image and the accumulation.
 __device__ __forceinline__ float2 ewald_pair2(const float2 dx, const float2 dy, const float2 dz,
                                               const float2 mj, const EwaldArgs &A, const float2 e2) {
     float2 r2 = __fmul2_rn(dx, dx);
@@ -92,22 +106,19 @@ __device__ __forceinline__ float2 ewald_pair2(const float2 dx, const float2 dy, 
     const float2 ip = make_float2(rsqrt_approx(s2.x), rsqrt_approx(s2.y));
     const float2 ip3 = __fmul2_rn(__fmul2_rn(ip, ip), ip);
     const float2 ir = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-    const float2 al = make_float2(A.alpha_f, A.alpha_f);
-    const float2 x = __fmul2_rn(__fmul2_rn(al, r2), ir);                       // alpha r
+    const float2 pr2 = __fmul2_rn(make_float2(A.p_alpha, A.p_alpha), r2);
+    const float2 den = __ffma2_rn(pr2, ir, make_float2(1.f, 1.f));           // 1 + p alpha r
+    const float2 t = make_float2(rcp_approx(den.x), rcp_approx(den.y));
     const float2 ea = __fmul2_rn(make_float2(-A.alpha2_log2e, -A.alpha2_log2e), r2);
     const float2 ex = make_float2(ex2_approx(ea.x), ex2_approx(ea.y));       // exp(-alpha^2 r^2)
-    const float2 den = __ffma2_rn(make_float2(kAsP, kAsP), x, make_float2(1.f, 1.f));
-    const float2 t = make_float2(rcp_approx(den.x), rcp_approx(den.y));
     float2 poly = __ffma2_rn(make_float2(kAsA5, kAsA5), t, make_float2(kAsA4, kAsA4));
     poly = __ffma2_rn(poly, t, make_float2(kAsA3, kAsA3));
     poly = __ffma2_rn(poly, t, make_float2(kAsA2, kAsA2));
     poly = __ffma2_rn(poly, t, make_float2(kAsA1, kAsA1));
-    poly = __fmul2_rn(poly, t);                                              // erfc(x) / exp(-x^2)
-    const float2 ir2 = __fmul2_rn(ir, ir);
-    const float2 ir3 = __fmul2_rn(ir2, ir);
-    // -erf/r^3 + cg e/r^2 = e (erfc_poly / r^3 + cg / r^2) - 1/r^3
-    const float2 g = __ffma2_rn(poly, ir3, __fmul2_rn(make_float2(A.cg, A.cg), ir2));
-    float2 f = __ffma2_rn(ex, g, make_float2(-ir3.x, -ir3.y));
+    const float2 qe = __fmul2_rn(poly, t);                                   // erfc(x) / exp(-x^2)
+    const float2 q = __ffma2_rn(qe, ir, make_float2(A.cg, A.cg));
+    const float2 h = __ffma2_rn(ex, q, make_float2(-ir.x, -ir.y));
+    float2 f = __fmul2_rn(h, __fmul2_rn(ir, ir));         // -erf(x)/r^3 + cg e / r^2
     const float2 fs = __ffma2_rn(make_float2(A.s1, A.s1), r2, make_float2(A.s0, A.s0));
     f.x = r2.x < A.x2_series ? fs.x : f.x;
     f.y = r2.y < A.x2_series ? fs.y : f.y;
@@ -185,9 +196,9 @@ __global__ void __launch_bounds__(NT, MINB)
                             float2 dx = __fadd2_rn(xj, nx[k]);
                             float2 dy = __fadd2_rn(yj, ny[k]);
                             float2 dz = __fadd2_rn(zj, nz[k]);
-                            dx = __ffma2_rn(Lm, rint2(__fmul2_rn(dx, iL)), dx);
-                            dy = __ffma2_rn(Lm, rint2(__fmul2_rn(dy, iL)), dy);
-                            dz = __ffma2_rn(Lm, rint2(__fmul2_rn(dz, iL)), dz);
+                            dx = min_image2(dx, iL, Lm);
+                            dy = min_image2(dy, iL, Lm);
+                            dz = min_image2(dz, iL, Lm);
                             const float2 s = ewald_pair2(dx, dy, dz, mj, A, e2);
                             px[k] = __ffma2_rn(dx, s, px[k]);
                             py[k] = __ffma2_rn(dy, s, py[k]);

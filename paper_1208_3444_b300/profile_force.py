@@ -1,13 +1,20 @@
-"""Run a few force-kernel launches on one workload, for profiling with ncu.
+"""Run a few launches of one all-pairs kernel on one workload, for profiling
+with ncu.
 
     python -m paper_1208_3444_b300.profile_force --workload grid32 --prec comp --launches 1
+    python -m paper_1208_3444_b300.profile_force --op vjp --workload grid32 --launches 1
+    python -m paper_1208_3444_b300.profile_force --periodic 1.0 --workload grid32 --launches 1
 
-Prints the CUDA-event duration of each force-kernel launch (meaningless under
-a profiler, which serialises and replays kernels).
+--op force runs colatus_forces (the force kernel, or with --periodic L the
+Ewald real-space and k-space kernels); --op vjp runs colatus_force_vjp with a
+seeded co-vector.  Prints the CUDA-event duration of the all-pairs kernel
+(meaningless under a profiler, which serialises and replays kernels).
 """
 import argparse
 import os
 import sys
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
@@ -38,18 +45,27 @@ def main():
                    help="grid16 | grid32 | uniform<N> | plummer<N>")
     p.add_argument("--prec", default="comp", choices=sorted(PRECS))
     p.add_argument("--launches", type=int, default=1)
+    p.add_argument("--op", default="force", choices=["force", "vjp"])
+    p.add_argument("--periodic", type=float, default=0.0, help="box side L (0: isolated)")
     a = p.parse_args()
     ic = workload(a.workload)
     sim = B.Simulation(ic.m, ic.eps, LCDM, 1.0, prec=PRECS[a.prec])
     try:
         sim.set_state(ic.x)
+        if a.periodic:
+            sim.set_periodic(a.periodic)
+        w = np.random.default_rng(1).standard_normal((ic.N, 3))
         sim.profile_forces(True)
         for _ in range(a.launches):
-            sim.forces()
-        ms, n = sim.profile_read()
+            if a.op == "vjp":
+                sim.force_vjp(w)
+            else:
+                sim.forces()
+        ms, n = sim.profile_read(vjp=a.op == "vjp")
     finally:
         sim.close()
-    print(f"{a.workload} N={ic.N} prec={a.prec}: {n} launches, {ms / max(n, 1):.3f} ms each")
+    print(f"{a.op} {a.workload} N={ic.N} prec={a.prec} periodic={a.periodic}: {n} launches, "
+          f"{ms / max(n, 1):.3f} ms each")
 
 
 if __name__ == "__main__":
