@@ -241,6 +241,8 @@ struct colatus_ctx {
     double *kw = nullptr;
     double2 *rho = nullptr;
     void *lr = nullptr;                     // n_alloc float4 / double4 long-range forces
+    void *ph = nullptr;                     // [n_alloc][3][nk+1] phase tables (float2 / double2)
+    size_t ph_bytes = 0;
     size_t kv_cap = 0;
     ForcePlan plan_ew32[2], plan_ew64;
 
@@ -459,6 +461,8 @@ colatus_status prof_end(colatus_t ctx, int cat = 0) {
     return COLATUS_OK;
 }
 
+colatus_status grow(colatus_t ctx, void **p, size_t *have, size_t need);
+
 // Ewald parameters for the current precision.  alpha (unless requested) from
 // the real-space truncation: the images beyond the nearest are at r >= L/2,
 // where the pair term is below erfc(x) + (2x/sqrt(pi)) exp(-x^2), x = alpha L/2;
@@ -508,6 +512,8 @@ colatus_status ewald_setup(colatus_t ctx) {
         ctx->kv_cap = nkv;
     }
     if (!ctx->lr) CU(cudaMalloc(&ctx->lr, (size_t)ctx->n_alloc * sizeof(double4)));
+    TRY(grow(ctx, &ctx->ph, &ctx->ph_bytes,
+             (size_t)ctx->n_alloc * 3 * (nk + 1) * (f64 ? sizeof(double2) : sizeof(float2))));
     CU(cudaMemcpyAsync(ctx->kv, kv.data(), nkv * sizeof(KVec), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(ctx->kw, w.data(), nkv * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));   // the host vectors go out of scope
@@ -528,8 +534,9 @@ colatus_status ewald_setup(colatus_t ctx) {
     // shared memory of the k-space kernels grows with nk
     const int nt = nk + 1;
     const size_t es = f64 ? sizeof(double) : sizeof(float);
-    const size_t smem_rho = (size_t)kEwBodies * (3 * nt * 2 + 1) * es;
-    const size_t smem_f = kEwKChunk * sizeof(KVec) + 2 * kEwKChunk * es + (size_t)kEwFThreads * 3 * nt * 2 * es;
+    const size_t smem_rho = (size_t)kEwBodies * 3 * nt * 2 * es + kEwBodies * es;
+    const size_t smem_f = kEwKChunk * (f64 ? sizeof(KStage<double>) : sizeof(KStage<float>)) +
+                          (size_t)kEwFThreads * 3 * nt * 2 * es;
     const void *frho = f64 ? (const void *)ewald_rho_kernel<double> : (const void *)ewald_rho_kernel<float>;
     const void *fk = f64 ? (const void *)ewald_kforce_kernel<double, double4>
                          : (const void *)ewald_kforce_kernel<float, float4>;
@@ -543,19 +550,23 @@ colatus_status ewald_setup(colatus_t ctx) {
 // into ctx->lr.  pk (FP32 packed) or pos (FP64) holds the positions.
 template <typename T, typename T4>
 colatus_status run_ewald_kspace(colatus_t ctx, const float *pk, const double4 *pos) {
+    using T2 = typename Vec2<T>::type;
     const int nt = ctx->ew.nk + 1;
+    T2 *ph = static_cast<T2 *>(ctx->ph);
+    ewald_phase_kernel<T><<<blocks_for(3 * ctx->N, 128), 128, 0, ctx->stream>>>(pk, pos, ctx->N,
+                                                                                ctx->ew, ph);
+    TRY(launched(ctx));
     CU(cudaMemsetAsync(ctx->rho, 0, (size_t)ctx->nkv * sizeof(double2), ctx->stream));
     const int kchunks = (ctx->nkv + kEwKThreads - 1) / kEwKThreads;
     const long long max_split = std::max(1LL, ctx->N / kEwBodies);
-    const int splits = (int)std::min<long long>(std::max(1, 2 * ctx->num_sms / kchunks), max_split);
-    const size_t smem_rho = (size_t)kEwBodies * (3 * nt * 2 + 1) * sizeof(T);
+    const int splits = (int)std::min<long long>(std::max(1, 4 * ctx->num_sms / kchunks), max_split);
+    const size_t smem_rho = (size_t)kEwBodies * 3 * nt * sizeof(T2) + kEwBodies * sizeof(T);
     ewald_rho_kernel<T><<<dim3(kchunks, splits), kEwKThreads, smem_rho, ctx->stream>>>(
-        pk, pos, ctx->N, ctx->kv, ctx->nkv, ctx->ew, ctx->rho);
+        pk, pos, ctx->N, ph, ctx->kv, ctx->nkv, ctx->ew, ctx->rho);
     TRY(launched(ctx));
-    const size_t smem_f = kEwKChunk * sizeof(KVec) + 2 * kEwKChunk * sizeof(T) +
-                          (size_t)kEwFThreads * 3 * nt * 2 * sizeof(T);
+    const size_t smem_f = kEwKChunk * sizeof(KStage<T>) + (size_t)kEwFThreads * 3 * nt * sizeof(T2);
     ewald_kforce_kernel<T, T4><<<blocks_for(ctx->N, kEwFThreads), kEwFThreads, smem_f, ctx->stream>>>(
-        pk, pos, ctx->N, ctx->kv, ctx->kw, ctx->rho, ctx->nkv, ctx->ew, static_cast<T4 *>(ctx->lr));
+        ctx->N, ph, ctx->kv, ctx->kw, ctx->rho, ctx->nkv, ctx->ew, static_cast<T4 *>(ctx->lr));
     return launched(ctx);
 }
 
@@ -739,7 +750,7 @@ void free_all(colatus_t ctx) {
                     ctx->xs64, ctx->vs64, ctx->vh64, ctx->acc64, ctx->pos64[0], ctx->pos64[1],
                     ctx->pos64[2], ctx->m64, ctx->part, ctx->flags, ctx->mstat, ctx->clk,
                     ctx->tclk, ctx->table, ctx->stage, ctx->stage2, ctx->diag, ctx->tslot,
-                    ctx->rec, ctx->kv, ctx->kw, ctx->rho, ctx->lr};
+                    ctx->rec, ctx->kv, ctx->kw, ctx->rho, ctx->lr, ctx->ph};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *tptrs[] = {ctx->tan.dx, ctx->tan.dv, ctx->tan.dvh, ctx->tan.pkt, ctx->tan.seeds,

@@ -31,10 +31,11 @@
 // Abramowitz & Stegun 7.1.26 (|error| <= 1.5e-7, its exp shared with the
 // Gaussian term); FP64 uses the library erfc.
 //
-// k space: the structure factors are one pass over (k, body) pairs, each body's
-// exp(2 pi i n x/L) taken from a per-body table whose phases are reduced
-// exactly (n x/L in FP64, minus its nearest integer) before sincospi; the force
-// pass evaluates the k-sum at every body from the same kind of table.
+// k space: every body's tables exp(2 pi i n x_c/L), n = 0..nk, are computed
+// once per force evaluation (ewald_phase_kernel; n x_c/L reduced exactly in
+// FP64 before sincospi); the structure factors are one pass over (k, body)
+// pairs with those tables staged in shared memory, and the force pass
+// evaluates the k-sum at every body from its own tables.
 #pragma once
 
 #include "common.cuh"
@@ -371,20 +372,6 @@ struct KVec {
     int nx, ny, nz, pad;
 };
 
-// exp(2 pi i n u) for n = 0..nk into tab (stride 1), with n u reduced exactly
-// (u = x / L in FP64: n u is exact for |n| < 2^20, minus its nearest integer).
-template <typename T>
-__device__ __forceinline__ void phase_table(double u, int nk, T *re, T *im) {
-    for (int n = 0; n <= nk; ++n) {
-        double f = (double)n * u;
-        f -= rint(f);
-        T s, c;
-        sincospi((T)(2.0 * f), &s, &c);
-        re[n] = c;
-        im[n] = s;
-    }
-}
-
 // Body position component as FP64 from either layout.
 __device__ __forceinline__ double3 body_pos(const float *pk, const double4 *pos, long long i) {
     if (pos) {
@@ -400,49 +387,82 @@ __device__ __forceinline__ double body_mass(const float *pk, const double4 *pos,
     return (double)pk[(i >> 1) * 8 + (i & 1) + 6];
 }
 
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+// Phase tables of every body, once per force evaluation:
+//   ph[(3 i + c) (nk + 1) + n] = exp(2 pi i n x_c / L),  n = 0..nk,
+// with n x_c / L reduced exactly (FP64: exact for |n| < 2^20, minus its
+// nearest integer) before sincospi.  One thread per (body, axis).
+template <typename T>
+__global__ void ewald_phase_kernel(const float *__restrict__ pk, const double4 *__restrict__ pos,
+                                   long long N, EwaldArgs A, typename Vec2<T>::type *__restrict__ ph) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= 3 * N) return;
+    const long long i = q / 3;
+    const int c = (int)(q - 3 * i);
+    const double3 p = body_pos(pk, pos, i);
+    const double u = (c == 0 ? p.x : (c == 1 ? p.y : p.z)) / A.L;
+    typename Vec2<T>::type *o = ph + q * (A.nk + 1);
+    for (int n = 0; n <= A.nk; ++n) {
+        double f = (double)n * u;
+        f -= rint(f);
+        T sn, cs;
+        sincospi((T)(2.0 * f), &sn, &cs);
+        o[n].x = cs;
+        o[n].y = sn;
+    }
+}
+
 constexpr int kEwBodies = 32;     // bodies per shared-memory table batch
 constexpr int kEwKThreads = 128;  // k-vectors per block of the structure-factor kernel
 
+// exp(i k.x) of one body from its three axis tables (tab: [3][nt]); negative
+// ny, nz take the conjugate.
+template <typename T, typename T2>
+__device__ __forceinline__ void phase_of(const T2 *tab, int nt, const KVec &k, T &re, T &im) {
+    const T2 x = tab[k.nx];
+    T2 y = tab[nt + abs(k.ny)];
+    T2 z = tab[2 * nt + abs(k.nz)];
+    if (k.ny < 0) y.y = -y.y;
+    if (k.nz < 0) z.y = -z.y;
+    const T er = x.x * y.x - x.y * y.y, ei = x.x * y.y + x.y * y.x;
+    re = er * z.x - ei * z.y;
+    im = er * z.y + ei * z.x;
+}
+
 // rho[k] += sum over this block's bodies of m_j exp(i k.x_j); grid (k chunks,
-// body splits), block kEwKThreads.  Tables: [kEwBodies][3][nk+1] (re, im).
+// body splits), block kEwKThreads; the bodies' tables are staged through
+// shared memory kEwBodies at a time.
 template <typename T>
 __global__ void __launch_bounds__(kEwKThreads)
     ewald_rho_kernel(const float *__restrict__ pk, const double4 *__restrict__ pos, long long N,
-                     const KVec *__restrict__ kv, int nkv, EwaldArgs A, double2 *__restrict__ rho) {
+                     const typename Vec2<T>::type *__restrict__ ph, const KVec *__restrict__ kv,
+                     int nkv, EwaldArgs A, double2 *__restrict__ rho) {
+    using T2 = typename Vec2<T>::type;
     extern __shared__ __align__(16) unsigned char sm[];
     const int nt = A.nk + 1;
-    T *tre = reinterpret_cast<T *>(sm);
-    T *tim = tre + kEwBodies * 3 * nt;
-    T *tm = tim + kEwBodies * 3 * nt;
+    T2 *tab = reinterpret_cast<T2 *>(sm);                       // [kEwBodies][3][nt]
+    T *tm = reinterpret_cast<T *>(tab + kEwBodies * 3 * nt);    // [kEwBodies]
     const int kidx = blockIdx.x * kEwKThreads + threadIdx.x;
     KVec k = {0, 0, 0, 0};
     if (kidx < nkv) k = kv[kidx];
-    const int ay = abs(k.ny), az = abs(k.nz);
-    const T sy = k.ny < 0 ? (T)-1 : (T)1, sz = k.nz < 0 ? (T)-1 : (T)1;
     const long long per = (N + gridDim.y - 1) / gridDim.y;
     const long long b0 = (long long)blockIdx.y * per, b1 = min(N, b0 + per);
     double cr = 0.0, ci = 0.0;
-    const double invL = 1.0 / A.L;
     for (long long j0 = b0; j0 < b1; j0 += kEwBodies) {
         const int nb = (int)min((long long)kEwBodies, b1 - j0);
         __syncthreads();
-        for (int q = threadIdx.x; q < nb * 3; q += kEwKThreads) {
-            const int b = q / 3, c = q - 3 * b;
-            const double3 p = body_pos(pk, pos, j0 + b);
-            const double xc = c == 0 ? p.x : (c == 1 ? p.y : p.z);
-            phase_table<T>(xc * invL, A.nk, tre + (b * 3 + c) * nt, tim + (b * 3 + c) * nt);
-            if (c == 0) tm[b] = (T)body_mass(pk, pos, j0 + b);
-        }
+        const T2 *src = ph + j0 * 3 * nt;
+        for (int q = threadIdx.x; q < nb * 3 * nt; q += kEwKThreads) tab[q] = src[q];
+        for (int b = threadIdx.x; b < nb; b += kEwKThreads) tm[b] = (T)body_mass(pk, pos, j0 + b);
         __syncthreads();
         if (kidx < nkv) {
             T pr = 0, pi = 0;
             for (int b = 0; b < nb; ++b) {
-                const T *r = tre + b * 3 * nt, *i = tim + b * 3 * nt;
-                const T xr = r[k.nx], xi = i[k.nx];
-                const T yr = r[nt + ay], yi = sy * i[nt + ay];
-                const T zr = r[2 * nt + az], zi = sz * i[2 * nt + az];
-                const T er = xr * yr - xi * yi, ei = xr * yi + xi * yr;
-                const T fr = er * zr - ei * zi, fi = er * zi + ei * zr;
+                T fr, fi;
+                phase_of<T, T2>(tab + b * 3 * nt, nt, k, fr, fi);
                 pr += tm[b] * fr;
                 pi += tm[b] * fi;
             }
@@ -458,63 +478,84 @@ __global__ void __launch_bounds__(kEwKThreads)
 
 // Long-range acceleration (G-less) at every body:
 //   lr_i = -sum_k w_k k [sin(k.x_i) C(k) - cos(k.x_i) S(k)]
-// One thread per body; k-vectors with their weighted structure factors are
-// staged through shared memory kEwKChunk at a time; the body's phase tables
-// live in shared memory too ([3][nk+1] per thread).
+// One thread per body.  The k-vectors are staged through shared memory
+// kEwKChunk at a time, already in the form the loop uses (the three table
+// offsets, the conjugation signs, n as floating point, w C and w S), so the
+// loop body is table reads and FMAs only; two accumulator chains.  The
+// block's body tables sit in shared memory as [3 nt][kEwFThreads]: every
+// thread evaluates the same k at a time, so a warp reads consecutive entries.
 constexpr int kEwFThreads = 64;
 constexpr int kEwKChunk = 256;
 
+template <typename T>
+struct __align__(16) KStage {   // 48 B (float) / 80 B (double): whole 16-byte loads
+    int ox, oy, oz, pad;   // table rows of |nx|, |ny|, |nz| (x 64 threads)
+    T sy, sz;              // signs of ny, nz (conjugation)
+    T kx, ky, kz;          // n as floating point
+    T wc, ws;              // w_k C(k), w_k S(k)
+    T pad2;
+};
+
 template <typename T, typename T4>
 __global__ void __launch_bounds__(kEwFThreads)
-    ewald_kforce_kernel(const float *__restrict__ pk, const double4 *__restrict__ pos, long long N,
+    ewald_kforce_kernel(long long N, const typename Vec2<T>::type *__restrict__ ph,
                         const KVec *__restrict__ kv, const double *__restrict__ w,
                         const double2 *__restrict__ rho, int nkv, EwaldArgs A, T4 *__restrict__ lr) {
+    using T2 = typename Vec2<T>::type;
     extern __shared__ __align__(16) unsigned char sm[];
     const int nt = A.nk + 1;
-    KVec *skv = reinterpret_cast<KVec *>(sm);
-    T *sc = reinterpret_cast<T *>(skv + kEwKChunk);       // w C
-    T *ss = sc + kEwKChunk;                               // w S
-    T *tre = ss + kEwKChunk;
-    T *tim = tre + kEwFThreads * 3 * nt;
-    const long long i = (long long)blockIdx.x * kEwFThreads + threadIdx.x;
-    T *re = tre + threadIdx.x * 3 * nt, *im = tim + threadIdx.x * 3 * nt;
-    if (i < N) {
-        const double3 p = body_pos(pk, pos, i);
-        const double invL = 1.0 / A.L;
-        phase_table<T>(p.x * invL, A.nk, re, im);
-        phase_table<T>(p.y * invL, A.nk, re + nt, im + nt);
-        phase_table<T>(p.z * invL, A.nk, re + 2 * nt, im + 2 * nt);
+    KStage<T> *sk = reinterpret_cast<KStage<T> *>(sm);
+    T2 *tab = reinterpret_cast<T2 *>(sk + kEwKChunk);
+    const long long i0 = (long long)blockIdx.x * kEwFThreads;
+    const int nb = (int)min((long long)kEwFThreads, N - i0);
+    for (int q = threadIdx.x; q < nb * 3 * nt; q += kEwFThreads) {
+        const int b = q / (3 * nt), r = q - b * 3 * nt;
+        tab[r * kEwFThreads + b] = ph[i0 * 3 * nt + q];
     }
+    const long long i = i0 + threadIdx.x;
+    const T2 *mine = tab + threadIdx.x;
     const double tpl = 2.0 * acos(-1.0) / A.L;
     double ax = 0.0, ay = 0.0, az = 0.0;
     for (int k0 = 0; k0 < nkv; k0 += kEwKChunk) {
         const int nc = min(kEwKChunk, nkv - k0);
         __syncthreads();
         for (int q = threadIdx.x; q < nc; q += kEwFThreads) {
-            skv[q] = kv[k0 + q];
+            const KVec k = kv[k0 + q];
             const double2 r = rho[k0 + q];
-            sc[q] = (T)(w[k0 + q] * r.x);
-            ss[q] = (T)(w[k0 + q] * r.y);
+            KStage<T> e;
+            e.ox = k.nx * kEwFThreads;
+            e.oy = (nt + abs(k.ny)) * kEwFThreads;
+            e.oz = (2 * nt + abs(k.nz)) * kEwFThreads;
+            e.pad = 0;
+            e.sy = k.ny < 0 ? (T)-1 : (T)1;
+            e.sz = k.nz < 0 ? (T)-1 : (T)1;
+            e.kx = (T)k.nx;
+            e.ky = (T)k.ny;
+            e.kz = (T)k.nz;
+            e.wc = (T)(w[k0 + q] * r.x);
+            e.ws = (T)(w[k0 + q] * r.y);
+            e.pad2 = (T)0;
+            sk[q] = e;
         }
         __syncthreads();
         if (i < N) {
-            T px = 0, py = 0, pz = 0;
+            T px[2] = {0, 0}, py[2] = {0, 0}, pz[2] = {0, 0};
+#pragma unroll 2
             for (int q = 0; q < nc; ++q) {
-                const KVec k = skv[q];
-                const int ay_ = abs(k.ny), az_ = abs(k.nz);
-                const T xr = re[k.nx], xi = im[k.nx];
-                const T yr = re[nt + ay_], yi = (k.ny < 0 ? -im[nt + ay_] : im[nt + ay_]);
-                const T zr = re[2 * nt + az_], zi = (k.nz < 0 ? -im[2 * nt + az_] : im[2 * nt + az_]);
-                const T er = xr * yr - xi * yi, ei = xr * yi + xi * yr;
-                const T cr = er * zr - ei * zi, si = er * zi + ei * zr;   // cos, sin of k.x_i
-                const T b = si * sc[q] - cr * ss[q];
-                px += b * (T)k.nx;
-                py += b * (T)k.ny;
-                pz += b * (T)k.nz;
+                const KStage<T> &e = sk[q];
+                const T2 x = mine[e.ox], y = mine[e.oy], z = mine[e.oz];
+                const T yi = e.sy * y.y, zi = e.sz * z.y;
+                const T er = x.x * y.x - x.y * yi, ei = x.x * yi + x.y * y.x;
+                const T cr = er * z.x - ei * zi, si = er * zi + ei * z.x;   // cos, sin of k.x_i
+                const T b = si * e.wc - cr * e.ws;
+                const int c = q & 1;
+                px[c] += b * e.kx;
+                py[c] += b * e.ky;
+                pz[c] += b * e.kz;
             }
-            ax += (double)px;
-            ay += (double)py;
-            az += (double)pz;
+            ax += (double)px[0] + (double)px[1];
+            ay += (double)py[0] + (double)py[1];
+            az += (double)pz[0] + (double)pz[1];
         }
     }
     if (i < N) {
