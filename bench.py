@@ -226,8 +226,9 @@ def time_force_128(B, inputs, torch, launches=3):
             "interactions_per_s": ic.N * ic.N * n / (ms * 1e-3), "prec": "fp32"}
 
 
-def time_adjoint(B, inputs, torch, stream, nsteps=40, k=20):
-    """Adjoint vs forward step time on the 32^3 workload (FP32 compensated):
+def time_adjoint(B, inputs, torch, stream, nsteps=200, k=20):
+    """Adjoint vs forward step time on the 32^3 workload (FP32 compensated), in
+    the adjoint configuration: 200 KDK steps, checkpoints every 20.  Reports
     the backward per step without the checkpoint recomputation (one VJP + the
     transposed update) over the forward step, and the total including it."""
     ic = inputs.grid32()
