@@ -137,6 +137,21 @@ colatus_status colatus_set_state(colatus_t ctx, const void *x, const void *v, in
 colatus_status colatus_get_state(colatus_t ctx, void *x, void *v, int dtype, int on_device,
                                  double *t, double *a);
 
+/* Asynchronous read-back of positions and velocities (N x 3, dtype) into
+ * HOST memory: the state after the steps enqueued so far is snapshotted on
+ * the device (in order on the context's stream) and copied to x and v on a
+ * separate copy stream, so the copy overlaps the steps enqueued after it
+ * (pinned host memory is needed for the overlap).  Returns without waiting,
+ * except when two earlier read-backs are still copying (two slots).  x and v
+ * must stay valid and untouched until colatus_wait_state,
+ * colatus_synchronize or colatus_get_state returns.  Either may be NULL, not
+ * both.  Errors: COLATUS_E_ARG, COLATUS_E_STATE (no state). */
+colatus_status colatus_get_state_async(colatus_t ctx, void *x, void *v, int dtype);
+
+/* Wait for every read-back started by colatus_get_state_async and for the
+ * context's stream; reports device error flags as colatus_synchronize does. */
+colatus_status colatus_wait_state(colatus_t ctx);
+
 /* Comoving acceleration of Eq. 1 at the current state and scale factor:
  * acc_out (N x 3, dtype) = a^-3 G sum_{j != k} m_j (x_j - x_k) / s^3.
  * Device output is asynchronous on the context's stream; host output

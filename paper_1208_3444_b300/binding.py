@@ -38,7 +38,8 @@ EXPORTS = ("colatus_init", "colatus_set_config", "colatus_set_masses", "colatus_
            "colatus_tangent_init", "colatus_tangent_step", "colatus_tangent_read",
            "colatus_autotune", "colatus_set_tuning", "colatus_probe_pipes",
            "colatus_set_deformation", "colatus_velocity_spectrum", "colatus_tracer_spectrum",
-           "colatus_set_periodic", "colatus_periodic_params")
+           "colatus_set_periodic", "colatus_periodic_params", "colatus_get_state_async",
+           "colatus_wait_state")
 
 
 class ColatusError(RuntimeError):
@@ -96,6 +97,8 @@ def lib():
                                       _int, _vp],
         "colatus_tracer_spectrum": [_vp, _dbl, _int, _int, _vp, _vp],
         "colatus_set_periodic": [_vp, _dbl, _dbl, _int],
+        "colatus_get_state_async": [_vp, _vp, _vp, _int],
+        "colatus_wait_state": [_vp],
         "colatus_periodic_params": [_vp, _vp, _vp, _vp],
         "colatus_tangent_step": [_vp, _dbl, _i64],
         "colatus_tangent_read": [_vp, _vp, _vp],
@@ -350,6 +353,27 @@ def colatus_tracer_spectrum(h, ntr, dt, window="rect", detrend=True):
     _check(lib().colatus_tracer_spectrum(h, float(dt), WINDOWS[window], int(bool(detrend)),
                                          out.ctypes.data, ctypes.byref(n)), h)
     return out
+
+
+def colatus_get_state_async(h, x, v):
+    """Start a read-back of the state into host arrays/tensors x, v (N x 3,
+    float32 or float64, the same dtype; pinned tensors let it overlap later
+    steps).  They must stay alive until colatus_wait_state."""
+    px, dx, tx, kx = _buf(x) if x is not None else (None, 0, None, None)
+    pv, dv, tv, kv = _buf(v) if v is not None else (None, 0, None, None)
+    if dx or dv:
+        raise ValueError("colatus_get_state_async writes host memory")
+    # the copy lands after this call returns: the caller's own buffers only,
+    # never a converted temporary
+    if (x is not None and kx is not x) or (v is not None and kv is not v):
+        raise ValueError("x and v must be C-contiguous float32/float64 arrays or tensors")
+    if x is not None and v is not None and tx != tv:
+        raise ValueError("x and v must have the same dtype")
+    _check(lib().colatus_get_state_async(h, px, pv, tx if x is not None else tv), h)
+
+
+def colatus_wait_state(h):
+    _check(lib().colatus_wait_state(h), h)
 
 
 def colatus_last_error(h=None):

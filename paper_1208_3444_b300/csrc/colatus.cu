@@ -136,27 +136,26 @@ ForceLaunch make_launch(long long n_pad, int itile, int jt, long long g_target) 
 }
 
 
-// A persistent kernel's launch geometry comes in two versions: the full
-// grid, and one that leaves one SM free for the Friedmann schedule kernel
-// while an extension of the look-ahead schedule runs on the side stream (see
-// choose_grid).  L is the one in use; segment buffers are sized for both.
+// Launch geometry of a persistent kernel.  Its grid leaves one SM free: the
+// Friedmann schedule kernel extends the look-ahead schedule on a side stream
+// while steps run, and it claims a whole SM's shared memory so that no force
+// CTA shares its SM (a lone FP64 thread next to a force CTA slows that CTA,
+// and so the whole stream-K grid, by ~1.7x on this GPU).  The grid is the
+// same whether or not an extension is running, so the segment sums, and the
+// results, do not depend on timing.
 struct ForcePlan {
     int variant = -1;       // F32 variant, or -1 for FP64
     long long n_pad = 0;    // bodies incl. zero-mass padding
     int itile = 0, jt = 0;
-    ForceLaunch L{}, L_full{}, L_red{};
+    ForceLaunch L{};
     size_t part_bytes = 0;
 };
 
-// Both geometries of a plan (n_pad, itile, jt set); elem_bytes per segment
-// entry per body.
+// Launch geometry of a plan (n_pad, itile, jt set) on all SMs but one;
+// elem_bytes per segment entry per body.
 void finish_plan(ForcePlan &p, int occ, int num_sms, size_t elem_bytes) {
-    p.L_full = make_launch(p.n_pad, p.itile, p.jt, (long long)occ * num_sms);
-    p.L_red = make_launch(p.n_pad, p.itile, p.jt, (long long)occ * std::max(1, num_sms - 1));
-    p.L = p.L_full;
-    const size_t segs = std::max((size_t)p.L_full.n_it * p.L_full.S_max,
-                                 (size_t)p.L_red.n_it * p.L_red.S_max);
-    p.part_bytes = segs * p.itile * elem_bytes;
+    p.L = make_launch(p.n_pad, p.itile, p.jt, (long long)occ * std::max(1, num_sms - 1));
+    p.part_bytes = (size_t)p.L.n_it * p.L.S_max * p.itile * elem_bytes;
 }
 
 }  // namespace
@@ -216,6 +215,15 @@ struct colatus_ctx {
     cudaEvent_t tab_ev[kTabEvents] = {};
     long long tab_ev_covers[kTabEvents] = {};
     int tab_ev_next = 0;
+    // asynchronous state read-back (colatus_get_state_async): a copy stream
+    // and two staging slots, each with its snapshot / copy-done events
+    cudaStream_t cstream = nullptr;
+    struct ReadSlot {
+        void *x = nullptr, *v = nullptr;   // device staging, N x 3 doubles each
+        cudaEvent_t snap = nullptr, done = nullptr;
+        bool busy = false;
+    } rslot[2];
+    int rnext = 0;
     double *stage = nullptr;       // N x 3 doubles for host <-> device transfers
     double *stage2 = nullptr;
     double *diag = nullptr;        // diagnostic partial sums
@@ -413,7 +421,7 @@ colatus_status build_plans(colatus_t ctx) {
 int default_shape(colatus_t ctx, int comp) {
     for (int sh = 0; sh < kShapes - 1; ++sh) {
         const ForcePlan &p = ctx->plan32[4 * sh + comp];
-        if (p.L_full.W >= 4LL * p.L_full.G) return sh;
+        if (p.L.W >= 4LL * p.L.G) return sh;
     }
     return kShapes - 1;
 }
@@ -762,6 +770,14 @@ void free_all(colatus_t ctx) {
                      ctx->adj.lx, ctx->adj.lv, ctx->adj.lvh, ctx->adj.lm, ctx->adj.pkw};
     for (void *p : aptrs)
         if (p) cudaFree(p);
+    if (ctx->cstream) cudaStreamSynchronize(ctx->cstream);
+    for (auto &r : ctx->rslot) {
+        if (r.x) cudaFree(r.x);
+        if (r.v) cudaFree(r.v);
+        if (r.snap) cudaEventDestroy(r.snap);
+        if (r.done) cudaEventDestroy(r.done);
+    }
+    if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
     for (cudaEvent_t e : ctx->tab_ev)
         if (e) cudaEventDestroy(e);
     if (ctx->adj.tab_ev) cudaEventDestroy(ctx->adj.tab_ev);
@@ -802,30 +818,6 @@ colatus_status extend_table(colatus_t ctx, int n) {
     CU(cudaEventRecord(ctx->tab_ev[k], ctx->tstream));
     ctx->tab_ev_covers[k] = ctx->tab_hi;
     return COLATUS_OK;
-}
-
-// Persistent kernels enqueued while a schedule extension may still run on
-// the side stream use one SM fewer: the schedule kernel asks for a whole SM's
-// shared memory, so it runs alone on the SM left free.  (A lone FP64 thread
-// next to a force CTA slows that CTA, and so the whole stream-K grid, by
-// about 1.7x on this GPU, whose FP64 rate is a small fraction of FP32.)
-// Called once per API call, before its first launch: every force launch and
-// the epilogue that sums its segments then share one geometry.
-bool extension_in_flight(colatus_t ctx) {
-    for (int k = 0; k < kTabEvents; ++k)
-        if (ctx->tab_ev[k] && cudaEventQuery(ctx->tab_ev[k]) == cudaErrorNotReady) return true;
-    if (ctx->adj.tab_ev && cudaEventQuery(ctx->adj.tab_ev) == cudaErrorNotReady) return true;
-    return false;
-}
-
-void choose_grid(colatus_t ctx) {
-    const bool red = extension_in_flight(ctx);
-    auto pick = [red](ForcePlan &p) { p.L = red ? p.L_red : p.L_full; };
-    for (ForcePlan &p : ctx->plan32) pick(p);
-    for (ForcePlan &p : ctx->plan_ew32) pick(p);
-    for (ForcePlan *p : {&ctx->plan64, &ctx->plan_vjp32, &ctx->plan_vjp64, &ctx->plan_ew64})
-        pick(*p);
-    if (ctx->tan.ready) pick(ctx->tan.plan);
 }
 
 // Make schedule entries [host_step, host_step + n] available to the main
@@ -1338,11 +1330,21 @@ colatus_status colatus_set_state(colatus_t ctx, const void *x, const void *v, in
     return COLATUS_OK;
 }
 
+colatus_status wait_reads(colatus_t ctx) {
+    for (auto &r : ctx->rslot)
+        if (r.busy) {
+            CU(cudaEventSynchronize(r.done));
+            r.busy = false;
+        }
+    return COLATUS_OK;
+}
+
 colatus_status colatus_get_state(colatus_t ctx, void *x, void *v, int dtype, int on_device,
                                  double *t, double *a) {
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
     TRY(check_dtype(ctx, dtype));
+    TRY(wait_reads(ctx));
     TRY(sync_and_check(ctx));
     if (x || v) {
         if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
@@ -1368,13 +1370,53 @@ colatus_status colatus_get_state(colatus_t ctx, void *x, void *v, int dtype, int
     return COLATUS_OK;
 }
 
+colatus_status colatus_get_state_async(colatus_t ctx, void *x, void *v, int dtype) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    TRY(check_dtype(ctx, dtype));
+    if (!x && !v) return fail(ctx, COLATUS_E_ARG, "x and v are both NULL");
+    if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
+    if (!ctx->cstream) {
+        CU(cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking));
+        for (auto &r : ctx->rslot) {
+            CU(cudaMalloc(&r.x, (size_t)ctx->N * 3 * sizeof(double)));
+            CU(cudaMalloc(&r.v, (size_t)ctx->N * 3 * sizeof(double)));
+            CU(cudaEventCreateWithFlags(&r.snap, cudaEventDisableTiming));
+            CU(cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming));
+        }
+    }
+    auto &r = ctx->rslot[ctx->rnext];
+    ctx->rnext ^= 1;
+    if (r.busy) CU(cudaEventSynchronize(r.done));   // its previous copy still reads the slot
+    r.busy = false;
+    // snapshot, ordered after the steps enqueued so far
+    store_state_kernel<<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
+        ctx->xs, ctx->vs, ctx->xs64, ctx->vs64, ctx->prec == COLATUS_FP64, ctx->N, x ? r.x : nullptr,
+        v ? r.v : nullptr, dtype == COLATUS_F64);
+    TRY(launched(ctx));
+    CU(cudaEventRecord(r.snap, ctx->stream));
+    CU(cudaStreamWaitEvent(ctx->cstream, r.snap, 0));
+    const size_t bytes = (size_t)ctx->N * 3 * elem_size(dtype);
+    if (x) CU(cudaMemcpyAsync(x, r.x, bytes, cudaMemcpyDeviceToHost, ctx->cstream));
+    if (v) CU(cudaMemcpyAsync(v, r.v, bytes, cudaMemcpyDeviceToHost, ctx->cstream));
+    CU(cudaEventRecord(r.done, ctx->cstream));
+    r.busy = true;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_wait_state(colatus_t ctx) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    TRY(wait_reads(ctx));
+    return sync_and_check(ctx);
+}
+
 colatus_status colatus_forces(colatus_t ctx, void *acc_out, int dtype, int on_device) {
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
     TRY(check_dtype(ctx, dtype));
     if (!acc_out) return fail(ctx, COLATUS_E_ARG, "acc_out is NULL");
     if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
-    choose_grid(ctx);
     TRY(force_at_state(ctx));
     void *dst = on_device ? acc_out : (void *)ctx->stage;
     TRY(force_output(ctx, dst, dtype == COLATUS_F64, true));
@@ -1398,8 +1440,7 @@ colatus_status colatus_step(colatus_t ctx, double dt, int64_t nsteps) {
     for (int64_t done = 0; done < nsteps;) {
         const int n = (int)std::min<int64_t>(kChunk, nsteps - done);
         TRY(need_table(ctx, dt, n));
-        choose_grid(ctx);
-        if (!ctx->spec_valid) {
+            if (!ctx->spec_valid) {
             TRY(open_step(ctx, dt));
             ctx->spec_valid = true;
             ctx->spec_tau = dt;
@@ -1416,6 +1457,7 @@ colatus_status colatus_step(colatus_t ctx, double dt, int64_t nsteps) {
 colatus_status colatus_synchronize(colatus_t ctx) {
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
+    TRY(wait_reads(ctx));
     return sync_and_check(ctx);
 }
 
@@ -1538,7 +1580,6 @@ colatus_status colatus_force_vjp(colatus_t ctx, const void *w, void *gx, void *g
     if (!w || (!gx && !gm)) return fail(ctx, COLATUS_E_ARG, "need w and at least one output");
     if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
     TRY(adj_alloc(ctx));
-    choose_grid(ctx);
     const int f64in = dtype == COLATUS_F64;
     const size_t vbytes = (size_t)ctx->N * 3 * elem_size(dtype);
     const void *src = w;
@@ -1665,7 +1706,6 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
     if (ctx->host_step != a.step0 + a.nsteps || ctx->prec != a.prec)
         return fail(ctx, COLATUS_E_STATE, "the state moved on since the adjoint forward pass");
     CU(cudaStreamWaitEvent(ctx->stream, a.tab_ev, 0));   // the forward's schedule
-    choose_grid(ctx);
     const bool f64 = ctx->prec == COLATUS_FP64;
     const int in64 = dtype == COLATUS_F64;
     const size_t vbytes = (size_t)ctx->N * 3 * elem_size(dtype);
@@ -1846,7 +1886,7 @@ colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, 
     t.B = B;
     t.nchunk = (B + kTB - 1) / kTB;
     t.n_pad = round_up(ctx->N, std::max(JvpK::ITILE, kJvpJT));
-    // units over all chunks' (i-tile x j-tile) pairs, full grid and one SM free
+    // units over all chunks' (i-tile x j-tile) pairs
     auto jvp_launch = [&](int sms) {
         ForceLaunch L{};
         L.n_it = (int)(t.n_pad / JvpK::ITILE);
@@ -1860,14 +1900,11 @@ colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, 
         L.S_max = (int)smax;
         return L;
     };
-    t.plan.L_full = jvp_launch(ctx->num_sms);
-    t.plan.L_red = jvp_launch(std::max(1, ctx->num_sms - 1));
-    t.plan.L = t.plan.L_full;
+    t.plan.L = jvp_launch(std::max(1, ctx->num_sms - 1));   // one SM for the schedule kernel
     t.plan.itile = JvpK::ITILE;
     t.plan.jt = kJvpJT;
     t.plan.n_pad = t.n_pad;
-    t.plan.part_bytes = (size_t)t.nchunk * t.plan.L_full.n_it *
-                        std::max(t.plan.L_full.S_max, t.plan.L_red.S_max) * 3 * JvpK::ITILE *
+    t.plan.part_bytes = (size_t)t.nchunk * t.plan.L.n_it * t.plan.L.S_max * 3 * JvpK::ITILE *
                         sizeof(float4);
     const size_t tb = (size_t)B * t.n_pad * sizeof(float4);
     CU(cudaMalloc(&t.dx, tb));
@@ -1912,8 +1949,7 @@ colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps) {
     for (int64_t done = 0; done < nsteps;) {
         const int n = (int)std::min<int64_t>(kChunk, nsteps - done);
         TRY(need_table(ctx, dt, n));
-        choose_grid(ctx);
-        if (!t.open) {
+            if (!t.open) {
             // tangent opening at x^n: JVP on the packed state positions
             const ForcePlan &p = plan_f32(ctx);
             pack_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(ctx->xs, ctx->pk[2],
@@ -1979,7 +2015,7 @@ colatus_status colatus_set_tuning(colatus_t ctx, int shape) {
     if (shape < -1 || shape >= kShapes) return fail(ctx, COLATUS_E_ARG, "shape must be -1 .. %d", kShapes - 1);
     if (shape >= 0) {
         const ForcePlan &p = ctx->plan32[4 * shape];
-        if (p.L_full.W < p.L_full.G) return fail(ctx, COLATUS_E_ARG, "shape %d does not fit N", shape);
+        if (p.L.W < p.L.G) return fail(ctx, COLATUS_E_ARG, "shape %d does not fit N", shape);
     }
     ctx->tuned_shape = shape;
     return COLATUS_OK;
@@ -1993,7 +2029,6 @@ colatus_status colatus_autotune(colatus_t ctx, int reps, double out_ms[3], int *
     if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
     if (ctx->prec == COLATUS_FP64) return fail(ctx, COLATUS_E_ARG, "the tuned kernels are FP32");
     TRY(sync_and_check(ctx));
-    choose_grid(ctx);
     const int keep = ctx->tuned_shape;
     const bool prof = ctx->profiling;
     const size_t used = ctx->ev_used;
