@@ -181,13 +181,17 @@ def run_reference(args, ws, rank):
     import oracle
     from paper_1208_3444_b300 import inputs
     ic = inputs.grid32()
-    rows_per_step = 128
+    # 2048 target rows per step (the CPU baseline's call size): enough work
+    # per call to keep every host core busy; 200 steps take a few seconds
+    rows_per_step = 2048
     rng = np.random.default_rng(1)
     for _ in range(args.warmup):
-        oracle.forces(ic.x, ic.m, ic.eps, rows=rng.choice(ic.N, rows_per_step, replace=False))
+        oracle.forces(ic.x, ic.m, ic.eps,
+                      rows=np.sort(rng.choice(ic.N, rows_per_step, replace=False)))
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.forces(ic.x, ic.m, ic.eps, rows=rng.choice(ic.N, rows_per_step, replace=False))
+        oracle.forces(ic.x, ic.m, ic.eps,
+                      rows=np.sort(rng.choice(ic.N, rows_per_step, replace=False)))
     dt = time.perf_counter() - t0
     value = args.steps * rows_per_step * ic.N / dt
     sample = (f"each step: FP64 oracle forces on {rows_per_step} random target bodies x all "
