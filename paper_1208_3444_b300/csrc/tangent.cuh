@@ -32,7 +32,7 @@ struct JvpKernel {
 
 // units: chunk-major, then i-tile, then j-tile (W = nchunk * n_it * n_jt).
 // pkt: [nchunk][N_pad][4] float4; part: [nchunk * n_it][S_max][3][ITILE] float4
-template <int NT, int IPT, int JT, int STAGES, int MINB>
+template <int NT, int IPT, int JT, int STAGES, int MINB, int UNR = 1>
 __global__ void __launch_bounds__(NT, MINB)
     jvp_f32_kernel(const float4 *__restrict__ pkt, float4 *__restrict__ part, int *__restrict__ flags,
                    ForceLaunch L, long long n_pad, float eps2) {
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(NT, MINB)
             const bool ok = mbar_wait_bounded(&full[stage], parity);
             if (ok) {
                 const float4 *tl = tiles + stage * JT * 4;
-#pragma unroll 1
+#pragma unroll (UNR)
                 for (int j = 0; j < JT; ++j) {
                     const float4 P = tl[4 * j], A = tl[4 * j + 1], Bv = tl[4 * j + 2], C = tl[4 * j + 3];
                     const float t[12] = {A.x, A.y, A.z, A.w, Bv.x, Bv.y, Bv.z, Bv.w, C.x, C.y, C.z, C.w};
