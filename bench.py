@@ -37,9 +37,9 @@ FLOPS_PER_INTERACTION = 20          # Nyland et al. convention
 FP32_FLOP_PER_CLK_PER_SM = 256      # 128 FP32 lanes x FMA
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one launch of the 32^3 compensated force kernel,
-# force_f32_kernel<512, 4, 512, 4, 128, 1, 1, 1, 2>, from one ncu capture
+# force_f32_kernel<512, 4, 512, 4, 256, 1, 1, 1, 2>, from one ncu capture
 # (profiles/force_f32_comp_grid32.md); set to None when that kernel changes.
-FORCE_KERNEL_TRAFFIC = 540928
+FORCE_KERNEL_TRAFFIC = 540672
 
 
 def parse():

@@ -67,7 +67,7 @@ const F32Variant &f32_variant(int v) {
         make_f32<512, 4, 512, 256, false, false, 1, 2>(),
         make_f32<512, 4, 512, 256, false, true, 1, 4>(),
         make_f32<512, 4, 512, 256, true, false, 1, 4>(),
-        make_f32<512, 4, 512, 128, true, true, 1, 2>(),
+        make_f32<512, 4, 512, 256, true, true, 1, 2>(),
         make_f32<256, 4, 512, 256, false, false, 2, 2>(),
         make_f32<256, 4, 512, 256, false, true, 2, 2>(),
         make_f32<256, 4, 512, 128, true, false, 2, 2>(),
