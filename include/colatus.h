@@ -218,6 +218,14 @@ colatus_status colatus_velocity_spectrum(const void *v, int dtype, int on_device
 colatus_status colatus_tracer_spectrum(colatus_t ctx, double dt, int window, int detrend,
                                        double *E_out, int64_t *nrec_out);
 
+/* Self-test of the device-side failure path: one CTA waits on a barrier
+ * that nothing completes, gives up after limit_cycles SM cycles (1 ..
+ * 2e9; the pipelined kernels use 2e9, about a second) and raises the same
+ * timeout flag the force, VJP and JVP kernels raise when a bulk-copy wait
+ * gives up.  Returns COLATUS_E_TIMEOUT when the path works (the flag is
+ * cleared; the context stays usable), COLATUS_E_ARG for a bad limit. */
+colatus_status colatus_selftest_wait(colatus_t ctx, int64_t limit_cycles);
+
 /* Human-readable description of the last error on ctx ("" if none);
  * colatus_last_error(NULL) describes the last colatus_init failure. */
 const char *colatus_last_error(colatus_t ctx);

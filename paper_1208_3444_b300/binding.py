@@ -39,7 +39,7 @@ EXPORTS = ("colatus_init", "colatus_set_config", "colatus_set_masses", "colatus_
            "colatus_autotune", "colatus_set_tuning", "colatus_probe_pipes",
            "colatus_set_deformation", "colatus_velocity_spectrum", "colatus_tracer_spectrum",
            "colatus_set_periodic", "colatus_periodic_params", "colatus_get_state_async",
-           "colatus_wait_state")
+           "colatus_wait_state", "colatus_selftest_wait")
 
 
 class ColatusError(RuntimeError):
@@ -99,6 +99,7 @@ def lib():
         "colatus_set_periodic": [_vp, _dbl, _dbl, _int],
         "colatus_get_state_async": [_vp, _vp, _vp, _int],
         "colatus_wait_state": [_vp],
+        "colatus_selftest_wait": [_vp, _i64],
         "colatus_periodic_params": [_vp, _vp, _vp, _vp],
         "colatus_tangent_step": [_vp, _dbl, _i64],
         "colatus_tangent_read": [_vp, _vp, _vp],
@@ -374,6 +375,12 @@ def colatus_get_state_async(h, x, v):
 
 def colatus_wait_state(h):
     _check(lib().colatus_wait_state(h), h)
+
+
+def colatus_selftest_wait(h, limit_cycles):
+    """Run the bounded-wait self-test; raises ColatusError (COLATUS_E_TIMEOUT)
+    when the failure path works."""
+    _check(lib().colatus_selftest_wait(h, int(limit_cycles)), h)
 
 
 def colatus_last_error(h=None):

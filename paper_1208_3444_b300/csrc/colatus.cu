@@ -634,6 +634,20 @@ colatus_status run_force_f64(colatus_t ctx, const double4 *pos) {
     return prof_end(ctx);
 }
 
+// Self-test of the bounded waits: one CTA waits on an mbarrier that nothing
+// ever completes, with a short limit, and raises FLAG_TIMEOUT as the
+// pipelined kernels do when a wait gives up.  Nothing faults or hangs.
+__global__ void wait_selftest_kernel(int *flags, long long limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, limit);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(&flags[FLAG_TIMEOUT], 1);
+}
+
 // ---- state conversion kernels (I/O only)
 __global__ void load_state_kernel(const void *x, const void *v, int f64, const double *m64,
                                   long long N, float4 *xs, float4 *vs, double4 *xs64,
@@ -2107,6 +2121,17 @@ colatus_status colatus_probe_pipes(double out[6]) {
     out[4] = per_sm;
     out[5] = 0.0;
     return st;
+}
+
+colatus_status colatus_selftest_wait(colatus_t ctx, int64_t limit_cycles) {
+    if (!ctx) return COLATUS_E_ARG;
+    DeviceGuard dg(ctx->device);
+    if (limit_cycles < 1 || limit_cycles > kWaitCycles)
+        return fail(ctx, COLATUS_E_ARG, "limit_cycles must be in [1, %lld]", kWaitCycles);
+    TRY(sync_and_check(ctx));
+    wait_selftest_kernel<<<1, 32, 0, ctx->stream>>>(ctx->flags, limit_cycles);
+    TRY(launched(ctx));
+    return sync_and_check(ctx);
 }
 
 colatus_status colatus_set_periodic(colatus_t ctx, double L, double alpha, int nk) {
