@@ -200,3 +200,28 @@ def test_recollapse_reports_friedmann_error():
         assert e.value.status == B.E_FRIEDMANN
     finally:
         sim.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(B.FP64, 1e-9), (B.FP32_COMP, 1e-4)])
+def test_layzer_irvine_residual_follows_the_oracle(prec, tol):
+    # 50 KDK steps of the 16^3 box at the background density, diagnostics
+    # (FP64 reductions on the GPU) after every step: the residual of
+    # d(K+W)/dt = -H (2K+W) is the leapfrog's own O(tau^2) error (~2e-3 of
+    # |W0| here) and must follow the oracle's residual for the same run
+    ic = inputs.grid16(critical=True)
+    n = 50
+    sim = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START, prec=prec, scheme=B.KDK)
+    try:
+        sim.set_state(ic.x, ic.v)
+        diags = [sim.diagnostics()]
+        for _ in range(n):
+            sim.step(TAU, 1)
+            diags.append(sim.diagnostics())
+    finally:
+        sim.close()
+    t = np.array([d["t"] for d in diags])
+    res_gpu = oracle.layzer_irvine(diags, t)
+    r = oracle.run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n, "kdk", diag_every=1)
+    res_ref = oracle.layzer_irvine([d[1] for d in r["diagnostics"]], TAU * np.arange(n + 1))
+    assert 1e-3 < np.abs(res_ref).max() < 1e-2            # the discretisation error is resolved
+    np.testing.assert_allclose(res_gpu, res_ref, rtol=0, atol=tol)
