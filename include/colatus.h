@@ -236,8 +236,9 @@ const char *colatus_last_error(colatus_t ctx);
 colatus_status colatus_stats(colatus_t ctx, double out[4]);
 
 /* Kernel timing for measurement: with on != 0 every launch of the force
- * kernel is bracketed by a pair of CUDA events recorded on the context's
- * stream (on = 0 stops and discards them). */
+ * kernel, the VJP kernel and the adjoint's per-step update kernel is
+ * bracketed by a pair of CUDA events recorded on the context's stream
+ * (on = 0 stops and discards them). */
 colatus_status colatus_profile_forces(colatus_t ctx, int on);
 
 /* Durations since the last read, from the event pairs of
@@ -245,6 +246,13 @@ colatus_status colatus_profile_forces(colatus_t ctx, int on);
  * force-kernel launches, out[2] milliseconds and out[3] number of VJP-kernel
  * launches.  Synchronises the stream and resets the totals. */
 colatus_status colatus_profile_read(colatus_t ctx, double out[4]);
+
+/* The same with a third kind: out[0..3] as colatus_profile_read, out[4]
+ * milliseconds and out[5] number of launches of the discrete adjoint's
+ * per-step update kernel (the transposed kick-drift-kick update that follows
+ * each VJP in colatus_adjoint_backward).  Synchronises the stream and resets
+ * the totals. */
+colatus_status colatus_profile_read_kinds(colatus_t ctx, double out[6]);
 
 /* Force-kernel tuning.  The FP32 force kernel exists in three tile shapes
  * (threads x i-bodies per thread, j-tile): 0 = 512 x 4, 512 bodies (one CTA

@@ -39,7 +39,7 @@ EXPORTS = ("colatus_init", "colatus_set_config", "colatus_set_masses", "colatus_
            "colatus_autotune", "colatus_set_tuning", "colatus_probe_pipes",
            "colatus_set_deformation", "colatus_velocity_spectrum", "colatus_tracer_spectrum",
            "colatus_set_periodic", "colatus_periodic_params", "colatus_get_state_async",
-           "colatus_wait_state", "colatus_selftest_wait")
+           "colatus_wait_state", "colatus_selftest_wait", "colatus_profile_read_kinds")
 
 
 class ColatusError(RuntimeError):
@@ -76,6 +76,7 @@ def lib():
         "colatus_stats": [_vp, _vp],
         "colatus_profile_forces": [_vp, _int],
         "colatus_profile_read": [_vp, _vp],
+        "colatus_profile_read_kinds": [_vp, _vp],
         "colatus_forces_noalloc": [_vp, _i64, _dbl, _dbl, _dbl, _vp, _vp],
         "colatus_force_vjp": [_vp, _vp, _vp, _vp, _int, _int],
         "colatus_adjoint_forward": [_vp, _dbl, _i64, _i64],
@@ -254,10 +255,12 @@ def colatus_profile_read(h, vjp=False):
 
 
 def colatus_profile_read_all(h):
-    """{'force': (ms, launches), 'vjp': (ms, launches)} since the last read."""
-    out = np.zeros(4)
-    _check(lib().colatus_profile_read(h, out.ctypes.data), h)
-    return {"force": (float(out[0]), int(out[1])), "vjp": (float(out[2]), int(out[3]))}
+    """{'force': (ms, launches), 'vjp': (ms, launches), 'adjoint_update': (ms,
+    launches)} since the last read."""
+    out = np.zeros(6)
+    _check(lib().colatus_profile_read_kinds(h, out.ctypes.data), h)
+    return {"force": (float(out[0]), int(out[1])), "vjp": (float(out[2]), int(out[3])),
+            "adjoint_update": (float(out[4]), int(out[5]))}
 
 
 def _same(*arrs):

@@ -11,6 +11,13 @@
 //     U_i = sum inv3 w_j,  B_i = sum m_j inv3,  Gm_i = sum inv3 (w_j . d),
 //     V_i = sum inv5 (m_i (w_j . d) - m_j (w_i . d)) d.
 // That is 26 FP32 lane-ops and one MUFU.RSQ per interaction (the force: 12).
+// Scaled form: with w'_i = w_i / m_i the pair weight m_i l_j - m_j l_i is
+// m_i (l_j - m_j (w'_i . d)), so V_i = m_i sum inv5 (l_j - m_j (w'_i . d)) d
+// and the multiply by m_i leaves the pair loop: 25 lane-ops.  The scaled
+// quantities differ from the general form's by the factor 1/m_i, so an i-tile
+// takes this form when every body in it has a mass within 2^-40 .. 2^40 and a
+// finite scaled co-vector, or a zero co-vector (padding).  Any other tile (a
+// massless body with a co-vector, for one) takes the 26-op form.
 // The self pair must be masked here: its U and B terms are each ~1/eps^3 and
 // cancel only in exact arithmetic.  Masking is done only in the units whose
 // j-tile overlaps the i-tile.
@@ -27,6 +34,12 @@
 
 namespace colatus {
 
+// Range check of the scaled form for one i-body: mass m within 2^-40 .. 2^40
+// and finite scaled co-vector (sx, sy, sz).
+__device__ __forceinline__ bool scaled_fits(float m, float sx, float sy, float sz) {
+    return m >= 0x1p-40f && m <= 0x1p40f && isfinite(sx) && isfinite(sy) && isfinite(sz);
+}
+
 template <int NT, int IPT, int JT, int STAGES>
 struct VjpKernel {
     static constexpr int ITILE = NT * IPT;
@@ -35,9 +48,10 @@ struct VjpKernel {
 };
 
 // One j-tile of the VJP for the IPT i-bodies of this thread.  ibase: index of
-// the tile's first j-body; MASK: the tile may contain i itself; UNR: unroll
-// depth of the j-pair loop (a tuning knob).
-template <int IPT, int JT, bool MASK, int UNR>
+// the tile's first j-body; MASK: the tile may contain i itself; SCALED: the
+// 25-op form, with (wxi, wyi, wzi) holding w_i / m_i and mi unused (V then
+// accumulates V_i / m_i); UNR: unroll depth of the j-pair loop (a tuning knob).
+template <int IPT, int JT, bool MASK, bool SCALED, int UNR>
 __device__ __forceinline__ void vjp_tile(const float4 *__restrict__ t, long long jbase,
                                          const long long (&ii)[IPT], const float2 (&nx)[IPT],
                                          const float2 (&ny)[IPT], const float2 (&nz)[IPT],
@@ -84,7 +98,8 @@ __device__ __forceinline__ void vjp_tile(const float4 *__restrict__ t, long long
             float2 li = __fmul2_rn(wxi[k], dx);
             li = __ffma2_rn(wyi[k], dy, li);
             li = __ffma2_rn(wzi[k], dz, li);
-            const float2 dw = __ffma2_rn(mi[k], lj, __fmul2_rn(nmj, li));
+            const float2 dw = SCALED ? __ffma2_rn(nmj, li, lj)
+                                     : __ffma2_rn(mi[k], lj, __fmul2_rn(nmj, li));
             const float2 g = __fmul2_rn(inv5, dw);
             Vx[k] = __ffma2_rn(g, dx, Vx[k]);
             Vy[k] = __ffma2_rn(g, dy, Vy[k]);
@@ -151,18 +166,53 @@ __global__ void __launch_bounds__(NT, MINB)
             Ux[k] = Uy[k] = Uz[k] = Bm[k] = make_float2(0.f, 0.f);
             Vx[k] = Vy[k] = Vz[k] = Gm[k] = make_float2(0.f, 0.f);
         }
+        // the scaled form for this i-tile?  (block-uniform: every thread
+        // reaches this point once per i-tile)
+        bool fits = true;
+        float sxi[IPT], syi[IPT], szi[IPT];
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            const float m = mi[k].x, r = 1.f / m;
+            sxi[k] = wxi[k].x * r;
+            syi[k] = wyi[k].x * r;
+            szi[k] = wzi[k].x * r;
+            if (wxi[k].x == 0.f && wyi[k].x == 0.f && wzi[k].x == 0.f)
+                sxi[k] = syi[k] = szi[k] = 0.f;
+            else
+                fits = fits && scaled_fits(m, sxi[k], syi[k], szi[k]);
+        }
+        const bool scaled = __syncthreads_and(fits);
+        if (scaled) {
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) {
+                wxi[k] = make_float2(sxi[k], sxi[k]);
+                wyi[k] = make_float2(syi[k], syi[k]);
+                wzi[k] = make_float2(szi[k], szi[k]);
+            }
+        }
         const long long ilo = it * K::ITILE, ihi = ilo + K::ITILE;
         for (; u < uend; ++u) {
             const bool ok = mbar_wait_bounded(&full[stage], parity);
             if (ok) {
                 const long long jt = u % n_jt;
                 const long long jlo = jt * JT;
-                if (jlo < ihi && jlo + JT > ilo)
-                    vjp_tile<IPT, JT, true, UNR>(tiles + stage * TILE_F4, jlo, ii, nx, ny, nz, mi, wxi,
-                                            wyi, wzi, e2, Ux, Uy, Uz, Bm, Vx, Vy, Vz, Gm);
-                else
-                    vjp_tile<IPT, JT, false, UNR>(tiles + stage * TILE_F4, jlo, ii, nx, ny, nz, mi, wxi,
-                                             wyi, wzi, e2, Ux, Uy, Uz, Bm, Vx, Vy, Vz, Gm);
+                const float4 *t = tiles + stage * TILE_F4;
+                const bool diag = jlo < ihi && jlo + JT > ilo;
+                if (scaled) {
+                    if (diag)
+                        vjp_tile<IPT, JT, true, true, UNR>(t, jlo, ii, nx, ny, nz, mi, wxi, wyi, wzi, e2,
+                                                          Ux, Uy, Uz, Bm, Vx, Vy, Vz, Gm);
+                    else
+                        vjp_tile<IPT, JT, false, true, UNR>(t, jlo, ii, nx, ny, nz, mi, wxi, wyi, wzi,
+                                                           e2, Ux, Uy, Uz, Bm, Vx, Vy, Vz, Gm);
+                } else {
+                    if (diag)
+                        vjp_tile<IPT, JT, true, false, UNR>(t, jlo, ii, nx, ny, nz, mi, wxi, wyi, wzi,
+                                                           e2, Ux, Uy, Uz, Bm, Vx, Vy, Vz, Gm);
+                    else
+                        vjp_tile<IPT, JT, false, false, UNR>(t, jlo, ii, nx, ny, nz, mi, wxi, wyi,
+                                                            wzi, e2, Ux, Uy, Uz, Bm, Vx, Vy, Vz, Gm);
+                }
             }
             if (__syncthreads_or(!ok)) {
                 bad = true;
@@ -184,11 +234,14 @@ __global__ void __launch_bounds__(NT, MINB)
         float4 *dst = part + (it * L.S_max + sidx) * (long long)K::ITILE;
 #pragma unroll
         for (int k = 0; k < IPT; ++k) {
+            const float *p = pkw + (ii[k] >> 1) * 16 + (ii[k] & 1);
             const float m = mi[k].x;
+            const float wx = __ldg(p + 8), wy = __ldg(p + 10), wz = __ldg(p + 12);
             const float bm = Bm[k].x + Bm[k].y;
-            const float gx = m * (Ux[k].x + Ux[k].y) - bm * wxi[k].x - 3.f * (Vx[k].x + Vx[k].y);
-            const float gy = m * (Uy[k].x + Uy[k].y) - bm * wyi[k].x - 3.f * (Vy[k].x + Vy[k].y);
-            const float gz = m * (Uz[k].x + Uz[k].y) - bm * wzi[k].x - 3.f * (Vz[k].x + Vz[k].y);
+            const float v3 = scaled ? 3.f * m : 3.f;
+            const float gx = m * (Ux[k].x + Ux[k].y) - bm * wx - v3 * (Vx[k].x + Vx[k].y);
+            const float gy = m * (Uy[k].x + Uy[k].y) - bm * wy - v3 * (Vy[k].x + Vy[k].y);
+            const float gz = m * (Uz[k].x + Uz[k].y) - bm * wz - v3 * (Vz[k].x + Vz[k].y);
             dst[tid + k * NT] = make_float4(gx, gy, gz, -(Gm[k].x + Gm[k].y));
         }
     }

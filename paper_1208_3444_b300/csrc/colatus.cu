@@ -94,7 +94,7 @@ using Vjp64K = Vjp64Kernel<kV64NT, kV64JT, kStages>;
 // JVP (tangent) kernel: 128 threads x 2 i-bodies, 128-body j-tiles of 64 B,
 // j-loop unrolled by 4 (fastest of eight shapes timed on B300 at 32^3 with
 // 64 tangents: 38.6 ms per step, 13 % less than without unrolling)
-constexpr int kJvpNT = 128, kJvpIPT = 2, kJvpJT = 128, kJvpMINB = 4, kJvpUnr = 4;
+constexpr int kJvpNT = 256, kJvpIPT = 2, kJvpJT = 128, kJvpMINB = 1, kJvpUnr = 4;
 using JvpK = JvpKernel<kJvpNT, kJvpIPT, kJvpJT, kStages>;
 
 // Periodic (Ewald) real-space kernels: FP32 256 threads x 2 i-bodies,
@@ -263,7 +263,8 @@ struct colatus_ctx {
         long long n_pad = 0, last_step = -1;
         double tau = 0.0;
         ForcePlan plan;
-        float4 *dx = nullptr, *dv = nullptr, *dvh = nullptr, *pkt = nullptr;
+        float4 *dx = nullptr, *dv = nullptr, *dvh = nullptr;
+        float *pkt = nullptr;                    // packed JVP input, pair-interleaved
         long long *seeds = nullptr;
         float *growth = nullptr;
         long long cap = 0, base = 0;
@@ -292,7 +293,7 @@ struct colatus_ctx {
     // force-kernel timing (colatus_profile_forces)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
-    std::vector<int> ev_cat;      // category of each event pair: 0 force, 1 VJP
+    std::vector<int> ev_cat;      // category of each event pair: 0 force, 1 VJP, 2 adjoint update
     size_t ev_used = 0;
 
     char err[512] = {0};
@@ -1125,7 +1126,7 @@ colatus_status run_jvp(colatus_t ctx, const float *pk) {
     tan_pack_kernel<<<grid, 256, 0, ctx->stream>>>(pk, T, ctx->N, t.n_pad);
     TRY(launched(ctx));
     TRY(ensure_part(ctx, t.plan.part_bytes));
-    jvp_f32_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kJvpMINB, kJvpUnr>
+    jvp_f32x2_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kJvpMINB, kJvpUnr>
         <<<t.plan.L.G, kJvpNT, JvpK::SMEM, ctx->stream>>>(t.pkt, static_cast<float4 *>(ctx->part),
                                                           ctx->flags, t.plan.L, t.n_pad,
                                                           (float)(ctx->eps * ctx->eps));
@@ -1570,19 +1571,27 @@ colatus_status colatus_profile_forces(colatus_t ctx, int on) {
     return COLATUS_OK;
 }
 
-colatus_status colatus_profile_read(colatus_t ctx, double out[4]) {
+colatus_status colatus_profile_read_kinds(colatus_t ctx, double out[6]) {
     if (!ctx || !out) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
     CU(cudaStreamSynchronize(ctx->stream));
-    for (int k = 0; k < 4; ++k) out[k] = 0.0;
+    for (int k = 0; k < 6; ++k) out[k] = 0.0;
     for (size_t k = 0; k + 1 < ctx->ev_used; k += 2) {
         float e = 0.f;
         CU(cudaEventElapsedTime(&e, ctx->ev_pool[k], ctx->ev_pool[k + 1]));
-        const int c = ctx->ev_cat[k] ? 2 : 0;
+        const int c = 2 * std::min(ctx->ev_cat[k], 2);
         out[c] += e;
         out[c + 1] += 1.0;
     }
     ctx->ev_used = 0;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_profile_read(colatus_t ctx, double out[4]) {
+    if (!ctx || !out) return COLATUS_E_ARG;
+    double all[6];
+    TRY(colatus_profile_read_kinds(ctx, all));
+    for (int k = 0; k < 4; ++k) out[k] = all[k];
     return COLATUS_OK;
 }
 
@@ -1821,6 +1830,7 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
         }
         for (long long n = s1 - 1; n >= s0; --n) {
             TRY(run_vjp(ctx));
+            TRY(prof_begin(ctx));
             if (f64)
                 adj_step_f64_kernel<<<nbv, 256, 0, ctx->stream>>>(
                     static_cast<const double4 *>(ctx->part), pv.L, pv.itile,
@@ -1836,6 +1846,7 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
                     static_cast<float *>(a.lm), a.table, n, a.tau, static_cast<float *>(a.pkw),
                     ctx->N, pv.n_pad, extra_args(ctx));
             TRY(launched(ctx));
+            TRY(prof_end(ctx, 2));
         }
     }
     TRY(run_vjp(ctx));
@@ -1897,7 +1908,7 @@ colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, 
     t = colatus_ctx::Tangent();
     int occ = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, jvp_f32_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kJvpMINB, kJvpUnr>, kJvpNT, JvpK::SMEM));
+        &occ, jvp_f32x2_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kJvpMINB, kJvpUnr>, kJvpNT, JvpK::SMEM));
     if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "JVP kernel cannot be resident");
     t.B = B;
     t.nchunk = (B + kTB - 1) / kTB;
@@ -1926,7 +1937,7 @@ colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, 
     CU(cudaMalloc(&t.dx, tb));
     CU(cudaMalloc(&t.dv, tb));
     CU(cudaMalloc(&t.dvh, tb));
-    CU(cudaMalloc(&t.pkt, (size_t)t.nchunk * t.n_pad * 4 * sizeof(float4)));
+    CU(cudaMalloc(&t.pkt, (size_t)t.nchunk * t.n_pad * kPktSlots * sizeof(float)));
     CU(cudaMalloc(&t.seeds, B * sizeof(long long)));
     CU(cudaMalloc(&t.growth, (size_t)capacity_steps * B * sizeof(float)));
     CU(cudaMemset(t.dx, 0, tb));

@@ -12,7 +12,7 @@
 //
 // Same stream-K decomposition and bulk-copy pipeline as force.cuh, over
 // (tangent chunk, i-tile, j-tile) units.  Per body and chunk the packed tile
-// holds (x, y, z, m) and TB tangent positions: 4 float4 = 64 B for TB = 4.
+// holds (x, y, z, m) and TB tangent positions: 64 B for TB = 4.
 #pragma once
 
 #include "common.cuh"
@@ -30,13 +30,32 @@ struct JvpKernel {
     static constexpr int SMEM = STAGES * TILE_BYTES + STAGES * 8;
 };
 
-// units: chunk-major, then i-tile, then j-tile (W = nchunk * n_it * n_jt).
-// pkt: [nchunk][N_pad][4] float4; part: [nchunk * n_it][S_max][3][ITILE] float4
+// Two j-bodies per f32x2 lane pair: every FP32 operation of the pair term is
+// one f32x2 instruction for two interactions (half the issue slots of scalar
+// code at the same FMA-pipe work).  Bodies are pair-interleaved: per pair of
+// bodies (2p, 2p + 1) and chunk, 32 floats
+//     [x0 x1 y0 y1 | z0 z1 m0 m1 | t0x0 t0x1 t0y0 t0y1 | t0z0 t0z1 t1x0 t1x1 | ...]
+// i.e. slot s of body i at float 2 s + (i & 1), slots x, y, z, m, then the TB
+// tangent positions (x, y, z) in order; a j-tile of JT bodies is JT * 64 B.
+// Units: chunk-major, then i-tile, then j-tile (W = nchunk * n_it * n_jt);
+// part: [nchunk * n_it][S_max][3][ITILE] float4.
+constexpr int kPktSlots = 4 + 3 * kTB;   // 16
+
+__device__ __forceinline__ float *pkt_body(float *pkt, long long chunk, long long n_pad, long long i) {
+    return pkt + (chunk * n_pad + (i & ~1LL)) * kPktSlots + (i & 1);
+}
+__device__ __forceinline__ const float *pkt_body(const float *pkt, long long chunk, long long n_pad,
+                                                 long long i) {
+    return pkt + (chunk * n_pad + (i & ~1LL)) * kPktSlots + (i & 1);
+}
+
 template <int NT, int IPT, int JT, int STAGES, int MINB, int UNR = 1>
 __global__ void __launch_bounds__(NT, MINB)
-    jvp_f32_kernel(const float4 *__restrict__ pkt, float4 *__restrict__ part, int *__restrict__ flags,
-                   ForceLaunch L, long long n_pad, float eps2) {
+    jvp_f32x2_kernel(const float *__restrict__ pkt, float4 *__restrict__ part, int *__restrict__ flags,
+                     ForceLaunch L, long long n_pad, float eps2) {
     using K = JvpKernel<NT, IPT, JT, STAGES>;
+    static_assert(JT % 2 == 0, "pairs of j-bodies");
+    constexpr int TILE_F4 = JT * 4;   // float4 per tile
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *tiles = reinterpret_cast<float4 *>(smem);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * K::TILE_BYTES);
@@ -45,12 +64,12 @@ __global__ void __launch_bounds__(NT, MINB)
     const long long W = L.W;
     const long long u0 = sk_begin(g, W, G), u1 = sk_begin(g + 1, W, G);
     const int n_jt = L.n_jt;
-    const long long per_it = n_jt;                           // units per (chunk, i-tile)
-    auto tile_src = [&](long long u) -> const float4 * {
-        const long long ct = u / per_it;                     // (chunk, i-tile) index
+    const long long per_it = n_jt;
+    auto tile_src = [&](long long u) -> const float * {
+        const long long ct = u / per_it;
         const long long chunk = ct / L.n_it;
         const long long jt = u % per_it;
-        return pkt + (chunk * n_pad + jt * JT) * 4;
+        return pkt + (chunk * n_pad + jt * JT) * kPktSlots;
     };
     if (tid == 0) {
 #pragma unroll
@@ -61,10 +80,10 @@ __global__ void __launch_bounds__(NT, MINB)
     if (tid == 0) {
         for (int s = 0; s < STAGES && u0 + s < u1; ++s) {
             mbar_arrive_expect_tx(&full[s], K::TILE_BYTES);
-            bulk_load(tiles + s * JT * 4, tile_src(u0 + s), K::TILE_BYTES, &full[s]);
+            bulk_load(tiles + s * TILE_F4, tile_src(u0 + s), K::TILE_BYTES, &full[s]);
         }
     }
-    const float e2 = eps2;
+    const float2 e2 = make_float2(eps2, eps2);
     long long u = u0;
     bool bad = false;
     int stage = 0;
@@ -73,52 +92,61 @@ __global__ void __launch_bounds__(NT, MINB)
         const long long ct = u / per_it;
         const long long chunk = ct / L.n_it, it = ct % L.n_it;
         const long long uend = min(u1, (ct + 1) * per_it);
-        float xi[IPT], yi[IPT], zi[IPT], tx[IPT][kTB], ty[IPT][kTB], tz[IPT][kTB];
-        float ax[IPT][kTB], ay[IPT][kTB], az[IPT][kTB];
+        // i-side values broadcast to both lanes, negated
+        float2 nx[IPT], ny[IPT], nz[IPT], ti[IPT][3 * kTB], ac[IPT][3 * kTB];
 #pragma unroll
         for (int k = 0; k < IPT; ++k) {
             const long long i = it * K::ITILE + tid + k * NT;
-            const float4 *p = pkt + (chunk * n_pad + i) * 4;
-            const float4 P = p[0], A = p[1], Bv = p[2], C = p[3];
-            xi[k] = P.x;
-            yi[k] = P.y;
-            zi[k] = P.z;
-            const float t[12] = {A.x, A.y, A.z, A.w, Bv.x, Bv.y, Bv.z, Bv.w, C.x, C.y, C.z, C.w};
+            const float *p = pkt_body(pkt, chunk, n_pad, i);
+            const float x = __ldg(p), y = __ldg(p + 2), z = __ldg(p + 4);
+            nx[k] = make_float2(-x, -x);
+            ny[k] = make_float2(-y, -y);
+            nz[k] = make_float2(-z, -z);
 #pragma unroll
-            for (int b = 0; b < kTB; ++b) {
-                tx[k][b] = t[3 * b];
-                ty[k][b] = t[3 * b + 1];
-                tz[k][b] = t[3 * b + 2];
-                ax[k][b] = ay[k][b] = az[k][b] = 0.f;
+            for (int c = 0; c < 3 * kTB; ++c) {
+                const float t = -__ldg(p + 2 * (4 + c));
+                ti[k][c] = make_float2(t, t);
+                ac[k][c] = make_float2(0.f, 0.f);
             }
         }
         for (; u < uend; ++u) {
             const bool ok = mbar_wait_bounded(&full[stage], parity);
             if (ok) {
-                const float4 *tl = tiles + stage * JT * 4;
+                const float4 *tl = tiles + stage * TILE_F4;
 #pragma unroll (UNR)
-                for (int j = 0; j < JT; ++j) {
-                    const float4 P = tl[4 * j], A = tl[4 * j + 1], Bv = tl[4 * j + 2], C = tl[4 * j + 3];
-                    const float t[12] = {A.x, A.y, A.z, A.w, Bv.x, Bv.y, Bv.z, Bv.w, C.x, C.y, C.z, C.w};
-                    const float m3 = -3.f * P.w;
+                for (int q = 0; q < JT / 2; ++q) {
+                    float2 v[kPktSlots];
+#pragma unroll
+                    for (int f = 0; f < kPktSlots / 2; ++f) {
+                        const float4 F = tl[8 * q + f];
+                        v[2 * f] = make_float2(F.x, F.y);
+                        v[2 * f + 1] = make_float2(F.z, F.w);
+                    }
+                    const float2 mj = v[3];
+                    const float2 m3 = __fmul2_rn(make_float2(-3.f, -3.f), mj);
 #pragma unroll
                     for (int k = 0; k < IPT; ++k) {
-                        const float dx = P.x - xi[k], dy = P.y - yi[k], dz = P.z - zi[k];
-                        const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, e2)));
-                        const float inv = rsqrt_approx(r2);
-                        const float inv2 = inv * inv;
-                        const float inv3 = inv * inv2;
-                        const float al = P.w * inv3;
-                        const float be = m3 * (inv3 * inv2);
+                        const float2 dx = __fadd2_rn(v[0], nx[k]);
+                        const float2 dy = __fadd2_rn(v[1], ny[k]);
+                        const float2 dz = __fadd2_rn(v[2], nz[k]);
+                        float2 r2 = __ffma2_rn(dx, dx, e2);
+                        r2 = __ffma2_rn(dy, dy, r2);
+                        r2 = __ffma2_rn(dz, dz, r2);
+                        const float2 inv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                        const float2 inv2 = __fmul2_rn(inv, inv);
+                        const float2 inv3 = __fmul2_rn(inv, inv2);
+                        const float2 al = __fmul2_rn(mj, inv3);
+                        const float2 be = __fmul2_rn(m3, __fmul2_rn(inv3, inv2));
 #pragma unroll
                         for (int b = 0; b < kTB; ++b) {
-                            const float ux = t[3 * b] - tx[k][b];
-                            const float uy = t[3 * b + 1] - ty[k][b];
-                            const float uz = t[3 * b + 2] - tz[k][b];
-                            const float s = be * fmaf(dz, uz, fmaf(dy, uy, dx * ux));
-                            ax[k][b] = fmaf(s, dx, fmaf(al, ux, ax[k][b]));
-                            ay[k][b] = fmaf(s, dy, fmaf(al, uy, ay[k][b]));
-                            az[k][b] = fmaf(s, dz, fmaf(al, uz, az[k][b]));
+                            const float2 ux = __fadd2_rn(v[4 + 3 * b], ti[k][3 * b]);
+                            const float2 uy = __fadd2_rn(v[5 + 3 * b], ti[k][3 * b + 1]);
+                            const float2 uz = __fadd2_rn(v[6 + 3 * b], ti[k][3 * b + 2]);
+                            const float2 s =
+                                __fmul2_rn(be, __ffma2_rn(dz, uz, __ffma2_rn(dy, uy, __fmul2_rn(dx, ux))));
+                            ac[k][3 * b] = __ffma2_rn(s, dx, __ffma2_rn(al, ux, ac[k][3 * b]));
+                            ac[k][3 * b + 1] = __ffma2_rn(s, dy, __ffma2_rn(al, uy, ac[k][3 * b + 1]));
+                            ac[k][3 * b + 2] = __ffma2_rn(s, dz, __ffma2_rn(al, uz, ac[k][3 * b + 2]));
                         }
                     }
                 }
@@ -129,7 +157,7 @@ __global__ void __launch_bounds__(NT, MINB)
             }
             if (tid == 0 && u + STAGES < u1) {
                 mbar_arrive_expect_tx(&full[stage], K::TILE_BYTES);
-                bulk_load(tiles + stage * JT * 4, tile_src(u + STAGES), K::TILE_BYTES, &full[stage]);
+                bulk_load(tiles + stage * TILE_F4, tile_src(u + STAGES), K::TILE_BYTES, &full[stage]);
             }
             if (++stage == STAGES) {
                 stage = 0;
@@ -142,9 +170,12 @@ __global__ void __launch_bounds__(NT, MINB)
 #pragma unroll
         for (int k = 0; k < IPT; ++k) {
             const int il = tid + k * NT;
-            dst[il] = make_float4(ax[k][0], ay[k][0], az[k][0], ax[k][1]);
-            dst[K::ITILE + il] = make_float4(ay[k][1], az[k][1], ax[k][2], ay[k][2]);
-            dst[2 * K::ITILE + il] = make_float4(az[k][2], ax[k][3], ay[k][3], az[k][3]);
+            float a[3 * kTB];
+#pragma unroll
+            for (int c = 0; c < 3 * kTB; ++c) a[c] = ac[k][c].x + ac[k][c].y;
+            dst[il] = make_float4(a[0], a[1], a[2], a[3]);
+            dst[K::ITILE + il] = make_float4(a[4], a[5], a[6], a[7]);
+            dst[2 * K::ITILE + il] = make_float4(a[8], a[9], a[10], a[11]);
         }
     }
     if (bad && tid == 0) {
@@ -182,7 +213,7 @@ __device__ __forceinline__ void jvp_reduce(const float4 *__restrict__ part, cons
 // [B][N_pad] arrays; seeds[b] is the body whose own growth is recorded.
 struct TangentState {
     float4 *dx, *dv, *dvh;
-    float4 *pkt;              // [nchunk][N_pad][4]
+    float *pkt;               // [nchunk][N_pad / 2][32], pair-interleaved (jvp_f32x2_kernel)
     const long long *seeds;   // [B]
     float *growth;            // [cap][B]
     long long cap, base;      // records kept, absolute step at which recording started
@@ -206,11 +237,13 @@ __global__ void tan_pack_kernel(const float *__restrict__ pk, TangentState T, lo
         t[3 * q + 1] = d.y;
         t[3 * q + 2] = d.z;
     }
-    float4 *o = T.pkt + ((long long)chunk * n_pad + i) * 4;
-    o[0] = x;
-    o[1] = make_float4(t[0], t[1], t[2], t[3]);
-    o[2] = make_float4(t[4], t[5], t[6], t[7]);
-    o[3] = make_float4(t[8], t[9], t[10], t[11]);
+    float *o = pkt_body(T.pkt, chunk, n_pad, i);
+    o[0] = x.x;
+    o[2] = x.y;
+    o[4] = x.z;
+    o[6] = x.w;
+#pragma unroll
+    for (int c = 0; c < 3 * kTB; ++c) o[2 * (4 + c)] = t[c];
 }
 
 // Opening of the tangent: dvh = c1 dv + d1 dF(x^n);  dx' = dx + tau dvh.
@@ -218,13 +251,13 @@ __global__ void tan_pack_kernel(const float *__restrict__ pk, TangentState T, lo
 __device__ __forceinline__ void tan_defo(const TangentState &T, const Extra &D, int chunk,
                                          long long i, long long n_pad, float (&f)[12]) {
     if (!D.on) return;
-    const float4 x = T.pkt[((long long)chunk * n_pad + i) * 4];
+    const float *x = pkt_body(T.pkt, chunk, n_pad, i);
 #pragma unroll
     for (int q = 0; q < kTB; ++q) {
         const long long b = (long long)chunk * kTB + q;
         if (b >= T.B) break;
         const float4 d = T.dx[b * n_pad + i];
-        defo_jacobian<float>(D, x.x, x.y, x.z, d.x, d.y, d.z, f[3 * q], f[3 * q + 1], f[3 * q + 2]);
+        defo_jacobian<float>(D, x[0], x[2], x[4], d.x, d.y, d.z, f[3 * q], f[3 * q + 1], f[3 * q + 2]);
     }
 }
 

@@ -65,6 +65,41 @@ def test_force_vjp_matches_oracle(N, prec, tol):
     assert rel(gm, scale * rm) < tol
 
 
+@pytest.mark.parametrize("case", ["massless", "tiny", "huge", "zero_covector"])
+def test_force_vjp_mass_edge_cases(case):
+    # The FP32 VJP takes a shorter form (co-vector divided by the mass) in
+    # blocks of bodies whose masses and scaled co-vectors are of moderate
+    # size, and the general form elsewhere.  These inputs mix both within one
+    # call: a massless body with a co-vector, masses of 1e-25 or 1e25, and
+    # bodies whose co-vector is zero.
+    N = 3000
+    x, m, w = random_system(N, 320)
+    m = m.astype(np.float64)
+    G = 1.3
+    if case == "massless":
+        m[[1500, 2500, 2999]] = 0.0
+    elif case == "tiny":
+        m[[1200, 2600]] = 1e-25
+    elif case == "huge":            # ~3e11: the short form; ~3e21: the general one
+        m *= 1e15
+        m[2048:] *= 1e10
+        G = 1.3e-20
+    else:
+        w[1000:2100] = 0.0
+        m[2000:2050] = 0.0
+    m = inputs.f32(m)
+    a, eps = 0.5, 0.01
+    sim = B.Simulation(m, eps, LCDM_D, a, prec=B.FP32, G=G)
+    try:
+        sim.set_state(x)
+        gx, gm = sim.force_vjp(w)
+    finally:
+        sim.close()
+    rx, rm = oracle.vjp(x, m, w, eps, G)
+    assert rel(gx, rx / a ** 3) < 1e-5
+    assert rel(gm, rm / a ** 3) < 1e-5
+
+
 def tracer_loss_grads(xT, vT, m, aT, tr):
     """L = 1/2 sum_tracers m a^2 |v|^2 and its gradients at the final state."""
     gv = np.zeros_like(vT)
