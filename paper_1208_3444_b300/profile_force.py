@@ -4,11 +4,13 @@ with ncu.
     python -m paper_1208_3444_b300.profile_force --workload grid32 --prec comp --launches 1
     python -m paper_1208_3444_b300.profile_force --op vjp --workload grid32 --launches 1
     python -m paper_1208_3444_b300.profile_force --periodic 1.0 --workload grid32 --launches 1
+    python -m paper_1208_3444_b300.profile_force --op jvp --workload grid32 --launches 1
 
 --op force runs colatus_forces (the force kernel, or with --periodic L the
 Ewald real-space and k-space kernels); --op vjp runs colatus_force_vjp with a
-seeded co-vector.  Prints the CUDA-event duration of the all-pairs kernel
-(meaningless under a profiler, which serialises and replays kernels).
+seeded co-vector; --op jvp runs tangent steps of 64 single-tracer tangents
+(one JVP launch each).  Prints the CUDA-event duration of the force or VJP
+kernel (meaningless under a profiler, which serialises and replays kernels).
 """
 import argparse
 import os
@@ -45,13 +47,19 @@ def main():
                    help="grid16 | grid32 | uniform<N> | plummer<N>")
     p.add_argument("--prec", default="comp", choices=sorted(PRECS))
     p.add_argument("--launches", type=int, default=1)
-    p.add_argument("--op", default="force", choices=["force", "vjp"])
+    p.add_argument("--op", default="force", choices=["force", "vjp", "jvp"])
     p.add_argument("--periodic", type=float, default=0.0, help="box side L (0: isolated)")
     a = p.parse_args()
     ic = workload(a.workload)
     sim = B.Simulation(ic.m, ic.eps, LCDM, 1.0, prec=PRECS[a.prec])
     try:
-        sim.set_state(ic.x)
+        sim.set_state(ic.x, ic.v)
+        if a.op == "jvp":
+            sim.tangent_init(inputs.tracers(ic.N, 64, 7), a.launches)
+            sim.tangent_step(inputs.lcdm_tau(2000), a.launches)
+            sim.synchronize()
+            print(f"jvp {a.workload} N={ic.N}: {a.launches} tangent steps of 64 tangents")
+            return
         if a.periodic:
             sim.set_periodic(a.periodic)
         w = np.random.default_rng(1).standard_normal((ic.N, 3))
