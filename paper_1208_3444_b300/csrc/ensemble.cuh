@@ -9,6 +9,13 @@
 // is balanced whatever the mix of N_r.  Softening is per realisation.  The
 // j-tiles of a unit never cross a realisation boundary, so realisations never
 // interact.
+//
+// Padding bodies have zero mass and sit at (2^100, 2^100, 2^100): the squared
+// distance from any body at moderate coordinates overflows to +inf, rsqrt
+// gives 0 and the pair term is exactly 0 in either form of the pair sum,
+// including the equal-mass form that never reads the mass.  When every
+// realisation has equal masses, the kernel takes that form (one FP32 lane-op
+// fewer per interaction) and the epilogues multiply the sums by m_r.
 #pragma once
 
 #include "common.cuh"
@@ -30,7 +37,10 @@ struct EnsLaunch {
     const float *eps2;              // [R]   softening^2
     const int *tile_r;              // [T]   realisation of global i-tile t
     const long long *tile_u0;       // [T]   first unit of global i-tile t
+    const float *meq;               // [R]   equal mass of realisation r (equal-mass kernel), or null
 };
+
+constexpr float kEnsFar = 0x1p100f;   // coordinate of the padding bodies
 
 // Realisation containing unit u (binary search over unit_off).
 __device__ __forceinline__ int ens_find(const long long *off, int R, long long u) {
@@ -51,11 +61,11 @@ __device__ __forceinline__ long long ens_jbody(const EnsLaunch &E, int r, long l
     return E.body_off[r] + (local % E.n_jt[r]) * JT;
 }
 
-template <int NT, int IPT, int JT, int STAGES, int FOLD, int MINB>
+template <int NT, int IPT, int JT, int STAGES, int FOLD, int MINB, bool EQM>
 __global__ void __launch_bounds__(NT, MINB)
     ens_force_kernel(const float *__restrict__ pk, float4 *__restrict__ part, int *__restrict__ flags,
                      EnsLaunch E) {
-    using K = F32Kernel<NT, IPT, JT, STAGES, FOLD, false, false>;
+    using K = F32Kernel<NT, IPT, JT, STAGES, FOLD, false, EQM>;
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *tiles = reinterpret_cast<float4 *>(smem);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * K::TILE_BYTES);
@@ -110,8 +120,8 @@ __global__ void __launch_bounds__(NT, MINB)
         for (; u < uend; ++u) {
             const bool ok = mbar_wait_bounded(&full[stage], parity);
             if (ok)
-                f32_tile<IPT, JT, FOLD, false, false, 2>(tiles + stage * JT, nx, ny, nz, e2, hx, hy, hz,
-                                                      lx, ly, lz);
+                f32_tile<IPT, JT, FOLD, false, EQM, 2>(tiles + stage * JT, nx, ny, nz, e2, hx, hy, hz,
+                                                    lx, ly, lz);
             if (__syncthreads_or(!ok)) {
                 bad = true;
                 break;
@@ -162,6 +172,12 @@ __device__ __forceinline__ float3 ens_reduce(const float4 *__restrict__ part, co
         fy += v.y;
         fz += v.z;
     }
+    if (E.meq) {
+        const float m = E.meq[r];
+        fx *= m;
+        fy *= m;
+        fz *= m;
+    }
     return make_float3(fx, fy, fz);
 }
 
@@ -202,7 +218,7 @@ __global__ void ens_table_kernel(Cosmo cosmo, const DevClock *clk, StepCoef *tab
     }
 }
 
-// Packing of the (real) state into the force input; padding is zero-mass.
+// Packing of the (real) state into the force input; padding is zero-mass and far away.
 __global__ void ens_pack_kernel(const float4 *__restrict__ xs, float *__restrict__ pk, EnsLaunch E,
                                 int itile, long long Npad) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -211,7 +227,7 @@ __global__ void ens_pack_kernel(const float4 *__restrict__ xs, float *__restrict
         const float4 b = xs[i];
         pk_store(pk, i, b.x, b.y, b.z, b.w);
     } else {
-        pk_store(pk, i, 0.f, 0.f, 0.f, 0.f);
+        pk_store(pk, i, kEnsFar, kEnsFar, kEnsFar, 0.f);
     }
 }
 
@@ -233,7 +249,7 @@ __global__ void ens_open_kernel(const float4 *__restrict__ xs, const float4 *__r
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= Npad) return;
     if (!ens_real(E, itile, i)) {
-        pk_store(pk_out, i, 0.f, 0.f, 0.f, 0.f);
+        pk_store(pk_out, i, kEnsFar, kEnsFar, kEnsFar, 0.f);
         return;
     }
     const float c1 = (float)table[0].c1, d1 = (float)table[0].d1, t = (float)tau;
@@ -256,7 +272,7 @@ __global__ void ens_step_kernel(const float4 *__restrict__ part, EnsLaunch E, in
     const StepCoef &sc = table[j];
     if (i == 0) advance_clock(clk, sc, flags);
     if (!ens_real(E, itile, i)) {
-        pk_store(pk_out, i, 0.f, 0.f, 0.f, 0.f);
+        pk_store(pk_out, i, kEnsFar, kEnsFar, kEnsFar, 0.f);
         return;
     }
     const float c2 = (float)sc.c2, d2 = (float)sc.d2, t = (float)tau;

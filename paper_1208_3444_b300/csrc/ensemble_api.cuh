@@ -15,7 +15,7 @@ namespace {
 // 256-body tiles timed on the 64-realisation ensemble (3.95 ms/step against
 // 4.10 for 64 x 4 at 8 CTAs per SM)
 constexpr int kEnsNT = 128, kEnsIPT = 2, kEnsJT = 256, kEnsFold = 128, kEnsMinB = 4;
-using EnsK = F32Kernel<kEnsNT, kEnsIPT, kEnsJT, kStages, kEnsFold, false, false>;
+using EnsK = F32Kernel<kEnsNT, kEnsIPT, kEnsJT, kStages, kEnsFold, false, false>;   // SMEM, ITILE: the same for EQM
 constexpr int kEnsTile = EnsK::ITILE;   // 256 bodies: the per-realisation padding unit
 constexpr int kEnsChunk = 16;           // steps per captured graph (even: ping-pong parity)
 static_assert(kEnsTile == kEnsJT, "ensemble tiles pad realisations to one size");
@@ -164,8 +164,12 @@ colatus_status ens_force(colatus_ens_t e, const float *pk) {
         }
         ECU(cudaEventRecord(e->ev[e->ev_used], e->stream));
     }
-    ens_force_kernel<kEnsNT, kEnsIPT, kEnsJT, kStages, kEnsFold, kEnsMinB>
-        <<<e->E.G, kEnsNT, EnsK::SMEM, e->stream>>>(pk, e->part, e->flags, e->E);
+    if (e->E.meq)
+        ens_force_kernel<kEnsNT, kEnsIPT, kEnsJT, kStages, kEnsFold, kEnsMinB, true>
+            <<<e->E.G, kEnsNT, EnsK::SMEM, e->stream>>>(pk, e->part, e->flags, e->E);
+    else
+        ens_force_kernel<kEnsNT, kEnsIPT, kEnsJT, kStages, kEnsFold, kEnsMinB, false>
+            <<<e->E.G, kEnsNT, EnsK::SMEM, e->stream>>>(pk, e->part, e->flags, e->E);
     colatus_status st = elaunched(e);
     if (st != COLATUS_OK) return st;
     e->interactions += e->pairs;
@@ -312,11 +316,23 @@ colatus_status colatus_ensemble_init(colatus_ens_t *out, int R, const int64_t *N
     e->Ntot = e->user_off[R];
     e->Npad = e->body_off[R];
     const int T = (int)e->tile_r.size();
-    int occ = 0;
+    // equal masses within every realisation (as floats): the equal-mass kernel
+    std::vector<float> meq(R, 0.f);
+    bool eqm = true;
+    for (int r = 0; r < R && eqm; ++r) {
+        meq[r] = (float)masses[e->user_off[r]];
+        for (long long k = 1; k < N_r[r] && eqm; ++k) eqm = (float)masses[e->user_off[r] + k] == meq[r];
+    }
+    int occ = 0, occ2 = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, ens_force_kernel<kEnsNT, kEnsIPT, kEnsJT, kStages, kEnsFold, kEnsMinB>, kEnsNT,
-            EnsK::SMEM) != cudaSuccess || occ < 1)
+            &occ, ens_force_kernel<kEnsNT, kEnsIPT, kEnsJT, kStages, kEnsFold, kEnsMinB, false>, kEnsNT,
+            EnsK::SMEM) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ2, ens_force_kernel<kEnsNT, kEnsIPT, kEnsJT, kStages, kEnsFold, kEnsMinB, true>, kEnsNT,
+            EnsK::SMEM) != cudaSuccess ||
+        std::min(occ, occ2) < 1)
         return bail(efail(e, COLATUS_E_CUDA, "ensemble force kernel cannot be resident"));
+    occ = std::min(occ, occ2);
     EnsLaunch &E = e->E;
     E.W = e->unit_off[R];
     E.R = R;
@@ -331,7 +347,7 @@ colatus_status colatus_ensemble_init(colatus_ens_t *out, int R, const int64_t *N
     E.S_max = (int)smax;
     // device memory
     const size_t ll = sizeof(long long);
-    const size_t meta_bytes = ll * ((R + 1) * 3 + R + T) + sizeof(int) * (R + T) + sizeof(float) * R + 64;
+    const size_t meta_bytes = ll * ((R + 1) * 3 + R + T) + sizeof(int) * (R + T) + sizeof(float) * 2 * R + 72;
     auto A = [&](void **p, size_t b) -> bool { return cudaMalloc(p, b) == cudaSuccess; };
     const size_t np = (size_t)e->Npad;
     bool ok = A(&e->meta, meta_bytes) && A((void **)&e->xs, np * 16) && A((void **)&e->vs, np * 16) &&
@@ -371,6 +387,7 @@ colatus_status colatus_ensemble_init(colatus_ens_t *out, int R, const int64_t *N
     E.n_jt = reinterpret_cast<const int *>(put(e->n_jt.data(), sizeof(int) * R));
     E.tile_r = reinterpret_cast<const int *>(put(e->tile_r.data(), sizeof(int) * T));
     E.eps2 = reinterpret_cast<const float *>(put(eps2.data(), sizeof(float) * R));
+    E.meq = eqm ? reinterpret_cast<const float *>(put(meq.data(), sizeof(float) * R)) : nullptr;
     colatus_status st = COLATUS_OK;
     cudaError_t ce = cudaMemcpy(e->meta, hm.data(), meta_bytes, cudaMemcpyHostToDevice);
     DevClock clk{0.0, a_start, 0, 0};

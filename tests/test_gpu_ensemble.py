@@ -26,12 +26,18 @@ def concat(ics):
             np.array([ic.N for ic in ics]))
 
 
-def test_forces_of_uneven_realisations():
+@pytest.mark.parametrize("masses", ["lognormal", "equal"])
+def test_forces_of_uneven_realisations(masses):
+    # "equal": every realisation has its own equal masses, so the ensemble
+    # takes the equal-mass kernel, whose padding bodies must contribute nothing
     rng = np.random.default_rng(40)
     ics = []
     for N, eps in ((1, 0.02), (7, 0.01), (300, 0.005), (1025, 0.01), (2000, 0.003), (4096, 0.01)):
         x = inputs.f32(rng.random((N, 3)))
-        m = inputs.f32(rng.lognormal(0.0, 0.5, N) / N)
+        if masses == "equal":
+            m = inputs.f32(np.full(N, rng.lognormal(0.0, 0.5) / N))
+        else:
+            m = inputs.f32(rng.lognormal(0.0, 0.5, N) / N)
         ics.append(inputs.ICs(x=x, v=np.zeros_like(x), m=m, eps=eps, name=f"r{N}"))
     x, v, m, eps, Ns = concat(ics)
     ens = B.Ensemble(Ns, m, eps, LCDM_D, 0.8, G=1.1)
