@@ -290,14 +290,16 @@ def time_adjoint(B, inputs, torch, stream, nsteps=200, k=20):
 
 
 def time_ensemble(B, inputs, torch, stream, nsteps=48):
-    """The 64-realisation ensemble (N_r log-uniform in [1024, 32768]): KDK
-    steps under the library's captured 16-step graphs, aggregate throughput."""
+    """The 64-realisation ensemble (N_r log-uniform in [1024, 32768]): the
+    autotuner picks the force kernel's CTA shape, then KDK steps under the
+    library's captured 16-step graphs, aggregate throughput."""
     ics = inputs.ensemble(64, seed=5)
     Ns = np.array([ic.N for ic in ics])
     ens = B.Ensemble(Ns, np.concatenate([ic.m for ic in ics]), [ic.eps for ic in ics], LCDM,
                      inputs.A_START, stream=stream.cuda_stream)
     try:
         ens.set_state(np.concatenate([ic.x for ic in ics]), np.concatenate([ic.v for ic in ics]))
+        tune_ms, shape = ens.autotune(3)      # the project's autotuner picks the CTA shape
         tau = inputs.lcdm_tau(2000)
         ens.step(tau, 16)
         ens.synchronize()
@@ -316,6 +318,8 @@ def time_ensemble(B, inputs, torch, stream, nsteps=48):
             "N_max": int(Ns.max()), "interactions_per_step": pairs, "steps": nsteps,
             "ms_per_step": ms / nsteps, "interactions_per_s": pairs * nsteps / (ms * 1e-3),
             "graph_launches": nsteps // 16, "kernel_launches": st["launches"] - l0,
+            "autotune": {"shape": shape, "ms_per_force": [round(float(t), 4) for t in tune_ms],
+                         "shapes": ["128x2, 4 CTAs/SM", "256x1, 4 CTAs/SM", "64x4, 8 CTAs/SM"]},
             "interactions_per_sm_per_clk": pairs * nsteps / (ms * 1e-3) /
             (torch.cuda.get_device_properties(0).multi_processor_count * 2.032e9),
             "frac_of_fp32_roofline": pairs * nsteps / (ms * 1e-3) /

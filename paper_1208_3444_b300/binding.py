@@ -39,7 +39,8 @@ EXPORTS = ("colatus_init", "colatus_set_config", "colatus_set_masses", "colatus_
            "colatus_autotune", "colatus_set_tuning", "colatus_probe_pipes",
            "colatus_set_deformation", "colatus_velocity_spectrum", "colatus_tracer_spectrum",
            "colatus_set_periodic", "colatus_periodic_params", "colatus_get_state_async",
-           "colatus_wait_state", "colatus_selftest_wait", "colatus_profile_read_kinds")
+           "colatus_wait_state", "colatus_selftest_wait", "colatus_profile_read_kinds",
+           "colatus_ensemble_autotune", "colatus_ensemble_set_tuning")
 
 
 class ColatusError(RuntimeError):
@@ -77,6 +78,8 @@ def lib():
         "colatus_profile_forces": [_vp, _int],
         "colatus_profile_read": [_vp, _vp],
         "colatus_profile_read_kinds": [_vp, _vp],
+        "colatus_ensemble_autotune": [_vp, _int, _vp, _vp],
+        "colatus_ensemble_set_tuning": [_vp, _int],
         "colatus_forces_noalloc": [_vp, _i64, _dbl, _dbl, _dbl, _vp, _vp],
         "colatus_force_vjp": [_vp, _vp, _vp, _vp, _int, _int],
         "colatus_adjoint_forward": [_vp, _dbl, _i64, _i64],
@@ -596,6 +599,18 @@ class Ensemble:
 
     def synchronize(self):
         _echeck(lib().colatus_ensemble_synchronize(self.h), self.h)
+
+    def autotune(self, reps=3):
+        """Time the force kernel's CTA shapes at the current state and keep
+        the fastest: (milliseconds per evaluation of each shape, chosen)."""
+        ms = np.zeros(3)
+        ch = ctypes.c_int(-1)
+        _echeck(lib().colatus_ensemble_autotune(self.h, int(reps), ms.ctypes.data, ctypes.byref(ch)),
+                self.h)
+        return ms, ch.value
+
+    def set_tuning(self, shape):
+        _echeck(lib().colatus_ensemble_set_tuning(self.h, int(shape)), self.h)
 
     def stats(self, profile_on=False):
         out = np.zeros(6)

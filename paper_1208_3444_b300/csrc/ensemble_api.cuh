@@ -14,11 +14,43 @@ namespace {
 // 128 threads x 2 i-bodies, 4 CTAs per SM: the fastest of six shapes with
 // 256-body tiles timed on the 64-realisation ensemble (3.95 ms/step against
 // 4.10 for 64 x 4 at 8 CTAs per SM)
-constexpr int kEnsNT = 128, kEnsIPT = 2, kEnsJT = 256, kEnsFold = 128, kEnsMinB = 4;
-using EnsK = F32Kernel<kEnsNT, kEnsIPT, kEnsJT, kStages, kEnsFold, false, false>;   // SMEM, ITILE: the same for EQM
+constexpr int kEnsJT = 256, kEnsFold = 128;
+using EnsK = F32Kernel<128, 2, kEnsJT, kStages, kEnsFold, false, false>;   // SMEM: every shape's
 constexpr int kEnsTile = EnsK::ITILE;   // 256 bodies: the per-realisation padding unit
 constexpr int kEnsChunk = 16;           // steps per captured graph (even: ping-pong parity)
 static_assert(kEnsTile == kEnsJT, "ensemble tiles pad realisations to one size");
+
+// CTA shapes of the ensemble force kernel (threads x i-bodies per thread,
+// CTAs per SM), all with 256-body i- and j-tiles, so that the padding and the
+// unit list do not depend on the shape.  Shape 0 is the built-in choice;
+// colatus_ensemble_autotune times all of them on the ensemble at hand.
+constexpr int kEnsShapes = 3;
+struct EnsVariant {
+    int nt;
+    const void *fn[2];   // general masses, equal masses
+    void (*launch[2])(int grid, cudaStream_t, const float *, float4 *, int *, EnsLaunch);
+};
+
+template <int NT, int IPT, int MINB, bool EQM>
+void ens_launch(int grid, cudaStream_t st, const float *pk, float4 *part, int *flags, EnsLaunch E) {
+    static_assert(NT * IPT == kEnsTile, "one i-tile per CTA pass");
+    ens_force_kernel<NT, IPT, kEnsJT, kStages, kEnsFold, MINB, EQM><<<grid, NT, EnsK::SMEM, st>>>(
+        pk, part, flags, E);
+}
+
+template <int NT, int IPT, int MINB>
+EnsVariant make_ens() {
+    return EnsVariant{NT,
+                      {(const void *)ens_force_kernel<NT, IPT, kEnsJT, kStages, kEnsFold, MINB, false>,
+                       (const void *)ens_force_kernel<NT, IPT, kEnsJT, kStages, kEnsFold, MINB, true>},
+                      {&ens_launch<NT, IPT, MINB, false>, &ens_launch<NT, IPT, MINB, true>}};
+}
+
+const EnsVariant &ens_variant(int s) {
+    static const EnsVariant table[kEnsShapes] = {make_ens<128, 2, 4>(), make_ens<256, 1, 4>(),
+                                                 make_ens<64, 4, 8>()};
+    return table[s];
+}
 
 }  // namespace
 
@@ -33,6 +65,8 @@ struct colatus_ensemble {
     std::vector<long long> nbody, body_off, user_off, unit_off, tile_u0;
     std::vector<int> n_jt, tile_r;
     EnsLaunch E{};
+    int shape = 0;                         // CTA shape of the force kernel (ens_variant)
+    int shape_G[kEnsShapes] = {0}, shape_S[kEnsShapes] = {0};   // grid and S_max per shape
     void *meta = nullptr;                  // device descriptor arrays
     long long *d_user_off = nullptr;
     float4 *xs = nullptr, *vs = nullptr, *vh = nullptr, *acc = nullptr;
@@ -164,12 +198,7 @@ colatus_status ens_force(colatus_ens_t e, const float *pk) {
         }
         ECU(cudaEventRecord(e->ev[e->ev_used], e->stream));
     }
-    if (e->E.meq)
-        ens_force_kernel<kEnsNT, kEnsIPT, kEnsJT, kStages, kEnsFold, kEnsMinB, true>
-            <<<e->E.G, kEnsNT, EnsK::SMEM, e->stream>>>(pk, e->part, e->flags, e->E);
-    else
-        ens_force_kernel<kEnsNT, kEnsIPT, kEnsJT, kStages, kEnsFold, kEnsMinB, false>
-            <<<e->E.G, kEnsNT, EnsK::SMEM, e->stream>>>(pk, e->part, e->flags, e->E);
+    ens_variant(e->shape).launch[e->E.meq ? 1 : 0](e->E.G, e->stream, pk, e->part, e->flags, e->E);
     colatus_status st = elaunched(e);
     if (st != COLATUS_OK) return st;
     e->interactions += e->pairs;
@@ -250,6 +279,20 @@ void ens_free(colatus_ens_t e) {
     if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
 }
 
+// Use CTA shape sh from now on: its grid and segment layout, new graphs, and
+// a new opening force (the old one was summed in the other shape's order).
+void ens_set_shape(colatus_ens_t e, int sh) {
+    e->shape = sh;
+    e->E.G = e->shape_G[sh];
+    e->E.S_max = e->shape_S[sh];
+    for (cudaGraphExec_t &g : e->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    e->spec_valid = false;
+}
+
 colatus_status ens_check(colatus_ens_t e, bool clear) {
     int f[NUM_FLAGS];
     ECU(cudaStreamSynchronize(e->stream));
@@ -323,28 +366,32 @@ colatus_status colatus_ensemble_init(colatus_ens_t *out, int R, const int64_t *N
         meq[r] = (float)masses[e->user_off[r]];
         for (long long k = 1; k < N_r[r] && eqm; ++k) eqm = (float)masses[e->user_off[r] + k] == meq[r];
     }
-    int occ = 0, occ2 = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, ens_force_kernel<kEnsNT, kEnsIPT, kEnsJT, kStages, kEnsFold, kEnsMinB, false>, kEnsNT,
-            EnsK::SMEM) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ2, ens_force_kernel<kEnsNT, kEnsIPT, kEnsJT, kStages, kEnsFold, kEnsMinB, true>, kEnsNT,
-            EnsK::SMEM) != cudaSuccess ||
-        std::min(occ, occ2) < 1)
-        return bail(efail(e, COLATUS_E_CUDA, "ensemble force kernel cannot be resident"));
-    occ = std::min(occ, occ2);
     EnsLaunch &E = e->E;
     E.W = e->unit_off[R];
     E.R = R;
-    E.G = (int)std::min<long long>((long long)occ * e->num_sms, E.W);
     E.T = T;
+    // grid and segment count of every shape; part is sized for the largest
     long long smax = 1;
-    for (int t = 0; t < T; ++t) {
-        const long long g0 = sk_owner(e->tile_u0[t], E.W, E.G);
-        const long long g1 = sk_owner(e->tile_u0[t] + e->n_jt[e->tile_r[t]] - 1, E.W, E.G);
-        smax = std::max(smax, g1 - g0 + 1);
+    for (int sh = 0; sh < kEnsShapes; ++sh) {
+        const EnsVariant &v = ens_variant(sh);
+        int occ = 0, occ2 = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn[0], v.nt, EnsK::SMEM) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, v.fn[1], v.nt, EnsK::SMEM) != cudaSuccess ||
+            std::min(occ, occ2) < 1)
+            return bail(efail(e, COLATUS_E_CUDA, "ensemble force kernel (shape %d) cannot be resident", sh));
+        const long long G = std::min<long long>((long long)std::min(occ, occ2) * e->num_sms, E.W);
+        long long sm = 1;
+        for (int t = 0; t < T; ++t) {
+            const long long g0 = sk_owner(e->tile_u0[t], E.W, G);
+            const long long g1 = sk_owner(e->tile_u0[t] + e->n_jt[e->tile_r[t]] - 1, E.W, G);
+            sm = std::max(sm, g1 - g0 + 1);
+        }
+        e->shape_G[sh] = (int)G;
+        e->shape_S[sh] = (int)sm;
+        smax = std::max(smax, sm);
     }
-    E.S_max = (int)smax;
+    E.G = e->shape_G[0];
+    E.S_max = e->shape_S[0];
     // device memory
     const size_t ll = sizeof(long long);
     const size_t meta_bytes = ll * ((R + 1) * 3 + R + T) + sizeof(int) * (R + T) + sizeof(float) * 2 * R + 72;
@@ -540,6 +587,61 @@ colatus_status colatus_ensemble_stats(colatus_ens_t e, int profile_on, double ou
     out[5] = (double)(e->ev_used / 2);
     e->ev_used = 0;
     e->profiling = profile_on != 0;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_ensemble_set_tuning(colatus_ens_t e, int shape) {
+    if (!e) return COLATUS_E_ARG;
+    DeviceGuard dg(e->device);
+    if (shape < -1 || shape >= kEnsShapes) return efail(e, COLATUS_E_ARG, "shape must be -1 .. %d", kEnsShapes - 1);
+    TRY(ens_check(e, true));
+    ens_set_shape(e, shape < 0 ? 0 : shape);
+    return COLATUS_OK;
+}
+
+colatus_status colatus_ensemble_autotune(colatus_ens_t e, int reps, double out_ms[3], int *chosen) {
+    if (!e) return COLATUS_E_ARG;
+    DeviceGuard dg(e->device);
+    if (reps < 1) return efail(e, COLATUS_E_ARG, "reps must be >= 1");
+    if (!e->have_state) return efail(e, COLATUS_E_STATE, "no state has been set");
+    TRY(ens_check(e, true));
+    ens_pack_kernel<<<ens_blocks(e), 256, 0, e->stream>>>(e->xs, e->pk[2], e->E, kEnsTile, e->Npad);
+    TRY(elaunched(e));
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    colatus_status st = COLATUS_OK;
+    double ms[kEnsShapes];
+    if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess)
+        st = efail(e, COLATUS_E_CUDA, "event creation failed");
+    const bool prof = e->profiling;
+    e->profiling = false;
+    for (int sh = 0; sh < kEnsShapes && st == COLATUS_OK; ++sh) {
+        e->E.G = e->shape_G[sh];
+        e->E.S_max = e->shape_S[sh];
+        e->shape = sh;
+        st = ens_force(e, e->pk[2]);   // warm-up (lazy module loading)
+        if (st == COLATUS_OK && cudaEventRecord(ev[0], e->stream) != cudaSuccess)
+            st = efail(e, COLATUS_E_CUDA, "event record failed");
+        for (int r = 0; r < reps && st == COLATUS_OK; ++r) st = ens_force(e, e->pk[2]);
+        float t = 0.f;
+        if (st == COLATUS_OK && (cudaEventRecord(ev[1], e->stream) != cudaSuccess ||
+                                 cudaEventSynchronize(ev[1]) != cudaSuccess ||
+                                 cudaEventElapsedTime(&t, ev[0], ev[1]) != cudaSuccess))
+            st = efail(e, COLATUS_E_CUDA, "event timing failed");
+        ms[sh] = (double)t / reps;
+    }
+    e->profiling = prof;
+    for (cudaEvent_t v : ev)
+        if (v) cudaEventDestroy(v);
+    if (st == COLATUS_OK) st = ens_check(e, true);
+    int best = 0;
+    if (st == COLATUS_OK)
+        for (int sh = 1; sh < kEnsShapes; ++sh)
+            if (ms[sh] < ms[best]) best = sh;
+    ens_set_shape(e, st == COLATUS_OK ? best : 0);
+    if (st != COLATUS_OK) return st;
+    for (int sh = 0; sh < kEnsShapes; ++sh)
+        if (out_ms) out_ms[sh] = ms[sh];
+    if (chosen) *chosen = best;
     return COLATUS_OK;
 }
 

@@ -137,3 +137,37 @@ def test_ensemble_workload_momentum_invariant():
         scale = np.sum(m[s, None] * np.abs(gv[s]), axis=0)
         assert np.all(np.abs(P1 - fac * P0) < 1e-5 * scale), r
     assert st["pairs_per_step"] == pytest.approx(float(np.sum(Ns.astype(float) ** 2)))
+
+
+@pytest.mark.parametrize("masses", ["lognormal", "equal"])
+def test_autotune_and_every_shape(masses):
+    rng = np.random.default_rng(41)
+    ics = []
+    for N, eps in ((5, 0.02), (700, 0.01), (1300, 0.005), (2500, 0.01)):
+        x = inputs.f32(rng.random((N, 3)))
+        m = (np.full(N, rng.lognormal(0.0, 0.5) / N) if masses == "equal"
+             else rng.lognormal(0.0, 0.5, N) / N)
+        ics.append(inputs.ICs(x=x, v=inputs.f32(0.1 * rng.standard_normal((N, 3))), m=inputs.f32(m),
+                              eps=eps, name=f"r{N}"))
+    x, v, m, eps, Ns = concat(ics)
+    off = np.concatenate([[0], np.cumsum(Ns)])
+    refs = [oracle.forces(ic.x, ic.m, ic.eps) for ic in ics]
+    ens = B.Ensemble(Ns, m, eps, LCDM_D, 1.0)
+    try:
+        ens.set_state(x, v)
+        ms, chosen = ens.autotune(2)
+        assert np.all(ms > 0) and chosen == int(np.argmin(ms))
+        for shape in range(3):
+            ens.set_tuning(shape)
+            ens.set_state(x, v)                              # back to the initial positions
+            a = ens.state()[3]                               # the clock has moved on
+            acc = ens.forces()
+            assert np.array_equal(acc, ens.forces())          # deterministic per shape
+            for r, ref in enumerate(refs):
+                assert rel_rms(acc[off[r]:off[r + 1]], ref / a ** 3) < 1e-5, (shape, r)
+            ens.step(TAU, 17)                                # a fresh graph per shape
+            assert np.all(np.isfinite(ens.state()[1]))
+        with pytest.raises(B.ColatusError):
+            ens.set_tuning(3)
+    finally:
+        ens.close()
