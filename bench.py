@@ -124,18 +124,33 @@ def cpu_baseline(seconds, rows_per_call=2048):
     ic = inputs.grid32()
     rng = np.random.default_rng(0)
     oracle.forces(ic.x, ic.m, ic.eps, rows=np.arange(64))        # start the thread pool
-    done, calls = 0, 0
-    t0 = time.perf_counter()
-    while time.perf_counter() - t0 < seconds:
-        oracle.forces(ic.x, ic.m, ic.eps,
-                      rows=np.sort(rng.choice(ic.N, rows_per_call, replace=False)))
-        done += rows_per_call
-        calls += 1
-    dt = time.perf_counter() - t0
-    return {"value": done * ic.N / dt, "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle",
+    cores = oracle.num_threads()
+
+    def rate(budget, rows):
+        done, calls = 0, 0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < budget:
+            oracle.forces(ic.x, ic.m, ic.eps, rows=np.sort(rng.choice(ic.N, rows, replace=False)))
+            done += rows
+            calls += 1
+        dt = time.perf_counter() - t0
+        return done * ic.N / dt, done, calls, dt
+
+    value, done, calls, dt = rate(seconds, rows_per_call)
+    oracle.set_threads(1)
+    one, done1, _, dt1 = rate(max(1.0, seconds / 5), 128)
+    oracle.set_threads(cores)
+    cpu = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            cpu = next(l.split(":", 1)[1].strip() for l in f if l.startswith("model name"))
+    except (OSError, StopIteration):
+        pass
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "value_1_thread": one, "cpu": cpu,
             "sample": f"FP64 oracle forces on {done} random target rows ({calls} calls of "
-                      f"{rows_per_call}) x all {ic.N} sources of the 32^3 workload ({dt:.1f} s)"}
+                      f"{rows_per_call}) x all {ic.N} sources of the 32^3 workload ({dt:.1f} s) on "
+                      f"{cores} threads; {done1} rows on 1 thread ({dt1:.1f} s)"}
 
 
 # --------------------------------------------------------------- distributed

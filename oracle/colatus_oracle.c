@@ -266,3 +266,15 @@ int colatus_oracle_threads(void)
     }
     return t;
 }
+
+/* Run the parallel loops above on n threads from now on (n >= 1; the
+ * OpenMP default otherwise).  Used to time the oracle on one core. */
+void colatus_oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

@@ -27,7 +27,7 @@ __all__ = [
     "Cosmology", "FriedmannError", "E2", "hubble", "friedmann_rhs",
     "friedmann_advance", "forces", "forces_pairwise", "potential", "vjp", "jvp",
     "kick_coefficients", "schedule", "run", "diagnostics", "layzer_irvine",
-    "adjoint_run", "tangent_run", "ftle", "num_threads", "PINS",
+    "adjoint_run", "tangent_run", "ftle", "num_threads", "set_threads", "PINS",
     "deformation_force", "deformation_vjp", "deformation_jvp", "total_force",
     "velocity_spectrum", "friedmann_integrals", "canonical_coefficients",
     "ewald_forces",
@@ -100,6 +100,8 @@ def _load():
         L.colatus_oracle_ewald_real_rows.argtypes = [i64, _dp, _dp, dbl, dbl, dbl, dbl, i64, _ip,
                                                      i64, _dp]
         L.colatus_oracle_threads.restype = ctypes.c_int
+        L.colatus_oracle_set_threads.argtypes = [ctypes.c_int]
+        L.colatus_oracle_set_threads.restype = None
         for f in (L.colatus_oracle_forces_pairwise, L.colatus_oracle_forces_rows,
                   L.colatus_oracle_potential_rows, L.colatus_oracle_vjp_rows,
                   L.colatus_oracle_jvp_rows, L.colatus_oracle_ewald_real_rows):
@@ -111,6 +113,11 @@ def _load():
 def num_threads() -> int:
     """OpenMP threads the row-parallel pair loops use."""
     return int(_load().colatus_oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """Run the row-parallel pair loops on n threads from now on."""
+    _load().colatus_oracle_set_threads(int(n))
 
 
 def _d(a):
