@@ -108,7 +108,7 @@ colatus_status colatus_set_deformation(colatus_t ctx, double Cpsi, const double 
  * evaluated by Ewald summation: a real-space all-pairs kernel over minimum
  * images and a reciprocal-space sum over 0 < |n| <= nk, k = 2 pi n / L.
  * alpha <= 0 and nk <= 0 choose them from the precision (truncation below
- * 1e-8 of a pair term in the FP32 modes, 1e-15 in FP64); nk <= 64.  Positions
+ * 1e-8 of a pair term in the FP32 modes, 1e-15 in FP64); nk <= 63.  Positions
  * are not wrapped: the minimum image is taken per pair.  L = 0 restores
  * isolated boundaries.  Forces and both step schemes honour it; the force
  * VJP, the adjoint, the tangent model and autotuning return COLATUS_E_STATE

@@ -104,7 +104,8 @@ using EwK = EwaldF32Kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, false>;
 using EwKC = EwaldF32Kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, true>;
 constexpr int kEw64NT = 128, kEw64JT = 32;
 using Ew64K = EwaldF64Kernel<kEw64NT, kEw64JT, kStages>;
-constexpr int kEwMaxNk = 64;
+constexpr int kEwMaxNk = 63;   // shared memory of the k-space kernels in FP64; a pencil fits one block
+constexpr int kEwRhoBlocksPerSM = 8;   // structure-factor blocks per SM (k chunks x body splits)
 
 constexpr long long kPadAlloc = 1024;   // buffers hold N rounded up to this
 constexpr int kChunk = 1024;            // steps enqueued per chunk of colatus_step
@@ -247,9 +248,14 @@ struct colatus_ctx {
     int ew_nk_req = 0;                      // requested nk (<= 0: from the precision)
     EwaldArgs ew{};
     int nkv = 0;
-    KVec *kv = nullptr;
     double *kw = nullptr;
     double2 *rho = nullptr;
+    void *rho_part = nullptr;               // [splits][nkv] partial structure factors
+    size_t rho_part_bytes = 0;
+    double2 *wcs = nullptr;                 // [nkv] (w C, w S) as float2 or double2
+    KPencil *pen = nullptr;                 // k-vector pencils (runs of nz at fixed nx, ny)
+    int *rchunk = nullptr, *fchunk = nullptr;   // first pencil of each k-space chunk (+ end)
+    int npen = 0, nrchunk = 0, nfchunk = 0, rchunk_np = 0;   // rchunk_np: most pencils in one chunk
     void *lr = nullptr;                     // n_alloc float4 / double4 long-range forces
     void *ph = nullptr;                     // [n_alloc][3][nk+1] phase tables (float2 / double2)
     size_t ph_bytes = 0;
@@ -510,22 +516,63 @@ colatus_status ewald_setup(colatus_t ctx) {
                 w.push_back(2.0 * 4.0 * pi / V * std::exp(-k2 / (4.0 * alpha * alpha)) / k2);
             }
     const size_t nkv = kv.size();
+    // pencils: runs of consecutive nz at fixed (nx, ny), in k order
+    std::vector<KPencil> pen;
+    for (size_t k = 0; k < nkv; ++k) {
+        if (pen.empty() || pen.back().nx != kv[k].nx || pen.back().ny != kv[k].ny ||
+            pen.back().nz0 + pen.back().len != kv[k].nz)
+            pen.push_back(KPencil{kv[k].nx, kv[k].ny, kv[k].nz, 0, (int)k, 0, 0, 0});
+        ++pen.back().len;
+    }
+    // chunks of whole pencils holding at most `cap` k-vectors: first pencil of each, then the end
+    auto chunks = [&](int cap) {
+        std::vector<int> c{0};
+        int have = 0;
+        for (int p = 0; p < (int)pen.size(); ++p) {
+            if (have + pen[p].len > cap) {
+                c.push_back(p);
+                have = 0;
+            }
+            have += pen[p].len;
+        }
+        c.push_back((int)pen.size());
+        return c;
+    };
+    const std::vector<int> rch = chunks(kEwKThreads);
+    const std::vector<int> fch = chunks(f64 ? ew_fk<double>() : ew_fk<float>());
     if (nkv > ctx->kv_cap) {
-        for (void *q : {(void *)ctx->kv, (void *)ctx->kw, (void *)ctx->rho})
+        for (void *q : {(void *)ctx->kw, (void *)ctx->rho, (void *)ctx->wcs, (void *)ctx->pen,
+                        (void *)ctx->rchunk, (void *)ctx->fchunk})
             if (q) cudaFree(q);
-        ctx->kv = nullptr;
         ctx->kw = nullptr;
         ctx->rho = nullptr;
+        ctx->wcs = nullptr;
+        ctx->pen = nullptr;
+        ctx->rchunk = ctx->fchunk = nullptr;
         ctx->kv_cap = 0;
-        CU(cudaMalloc(&ctx->kv, nkv * sizeof(KVec)));
         CU(cudaMalloc(&ctx->kw, nkv * sizeof(double)));
         CU(cudaMalloc(&ctx->rho, nkv * sizeof(double2)));
+        CU(cudaMalloc(&ctx->wcs, nkv * sizeof(double2)));
+        // at most one pencil (and chunk) per k-vector
+        CU(cudaMalloc(&ctx->pen, nkv * sizeof(KPencil)));
+        CU(cudaMalloc(&ctx->rchunk, (nkv + 1) * sizeof(int)));
+        CU(cudaMalloc(&ctx->fchunk, (nkv + 1) * sizeof(int)));
         ctx->kv_cap = nkv;
     }
+    CU(cudaMemcpyAsync(ctx->pen, pen.data(), pen.size() * sizeof(KPencil), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CU(cudaMemcpyAsync(ctx->rchunk, rch.data(), rch.size() * sizeof(int), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CU(cudaMemcpyAsync(ctx->fchunk, fch.data(), fch.size() * sizeof(int), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    ctx->npen = (int)pen.size();
+    ctx->nrchunk = (int)rch.size() - 1;
+    ctx->rchunk_np = 1;
+    for (int c = 0; c < ctx->nrchunk; ++c) ctx->rchunk_np = std::max(ctx->rchunk_np, rch[c + 1] - rch[c]);
+    ctx->nfchunk = (int)fch.size() - 1;
     if (!ctx->lr) CU(cudaMalloc(&ctx->lr, (size_t)ctx->n_alloc * sizeof(double4)));
     TRY(grow(ctx, &ctx->ph, &ctx->ph_bytes,
              (size_t)ctx->n_alloc * 3 * (nk + 1) * (f64 ? sizeof(double2) : sizeof(float2))));
-    CU(cudaMemcpyAsync(ctx->kv, kv.data(), nkv * sizeof(KVec), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(ctx->kw, w.data(), nkv * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));   // the host vectors go out of scope
     ctx->nkv = (int)nkv;
@@ -545,9 +592,8 @@ colatus_status ewald_setup(colatus_t ctx) {
     // shared memory of the k-space kernels grows with nk
     const int nt = nk + 1;
     const size_t es = f64 ? sizeof(double) : sizeof(float);
-    const size_t smem_rho = (size_t)kEwBodies * 3 * nt * 2 * es + kEwBodies * es;
-    const size_t smem_f = kEwKChunk * (f64 ? sizeof(KStage<double>) : sizeof(KStage<float>)) +
-                          (size_t)kEwFThreads * 3 * nt * 2 * es;
+    const size_t smem_rho = f64 ? ew_rho_smem<double>(nk, ctx->rchunk_np) : ew_rho_smem<float>(nk, ctx->rchunk_np);
+    const size_t smem_f = kEwFKBytes + (size_t)kEwFThreads * 3 * nt * 2 * es;
     const void *frho = f64 ? (const void *)ewald_rho_kernel<double> : (const void *)ewald_rho_kernel<float>;
     const void *fk = f64 ? (const void *)ewald_kforce_kernel<double, double4>
                          : (const void *)ewald_kforce_kernel<float, float4>;
@@ -567,17 +613,24 @@ colatus_status run_ewald_kspace(colatus_t ctx, const float *pk, const double4 *p
     ewald_phase_kernel<T><<<blocks_for(3 * ctx->N, 128), 128, 0, ctx->stream>>>(pk, pos, ctx->N,
                                                                                 ctx->ew, ph);
     TRY(launched(ctx));
-    CU(cudaMemsetAsync(ctx->rho, 0, (size_t)ctx->nkv * sizeof(double2), ctx->stream));
-    const int kchunks = (ctx->nkv + kEwKThreads - 1) / kEwKThreads;
-    const long long max_split = std::max(1LL, ctx->N / kEwBodies);
-    const int splits = (int)std::min<long long>(std::max(1, 4 * ctx->num_sms / kchunks), max_split);
-    const size_t smem_rho = (size_t)kEwBodies * 3 * nt * sizeof(T2) + kEwBodies * sizeof(T);
+    const int kchunks = ctx->nrchunk;
+    const long long max_split = std::max(1LL, ctx->N / ew_bodies<T>());
+    const int splits = (int)std::min<long long>(std::max(1, kEwRhoBlocksPerSM * ctx->num_sms / kchunks),
+                                                max_split);
+    TRY(grow(ctx, &ctx->rho_part, &ctx->rho_part_bytes, (size_t)splits * ctx->nkv * sizeof(double2)));
+    const size_t smem_rho = ew_rho_smem<T>(ctx->ew.nk, ctx->rchunk_np);
     ewald_rho_kernel<T><<<dim3(kchunks, splits), kEwKThreads, smem_rho, ctx->stream>>>(
-        pk, pos, ctx->N, ph, ctx->kv, ctx->nkv, ctx->ew, ctx->rho);
+        pk, pos, ctx->N, ph, ctx->pen, ctx->rchunk, ctx->rchunk_np, ctx->nkv, ctx->ew,
+        static_cast<double2 *>(ctx->rho_part));
     TRY(launched(ctx));
-    const size_t smem_f = kEwKChunk * sizeof(KStage<T>) + (size_t)kEwFThreads * 3 * nt * sizeof(T2);
-    ewald_kforce_kernel<T, T4><<<blocks_for(ctx->N, kEwFThreads), kEwFThreads, smem_f, ctx->stream>>>(
-        ctx->N, ph, ctx->kv, ctx->kw, ctx->rho, ctx->nkv, ctx->ew, static_cast<T4 *>(ctx->lr));
+    T2 *wcs = reinterpret_cast<T2 *>(ctx->wcs);
+    ewald_rho_sum_kernel<T><<<blocks_for(ctx->nkv, 256), 256, 0, ctx->stream>>>(
+        static_cast<const double2 *>(ctx->rho_part), splits, ctx->nkv, ctx->kw, ctx->rho, wcs);
+    TRY(launched(ctx));
+    const size_t smem_f = kEwFKBytes + (size_t)kEwFThreads * 3 * nt * sizeof(T2);
+    ewald_kforce_kernel<T, T4><<<blocks_for(ctx->N, kEwFThreads), kEwFThreads * kEwFSlices, smem_f,
+                                 ctx->stream>>>(ctx->N, ph, ctx->pen, ctx->fchunk, ctx->nfchunk, wcs,
+                                                ctx->ew, static_cast<T4 *>(ctx->lr));
     return launched(ctx);
 }
 
@@ -775,7 +828,8 @@ void free_all(colatus_t ctx) {
                     ctx->xs64, ctx->vs64, ctx->vh64, ctx->acc64, ctx->pos64[0], ctx->pos64[1],
                     ctx->pos64[2], ctx->m64, ctx->part, ctx->flags, ctx->mstat, ctx->clk,
                     ctx->tclk, ctx->table, ctx->stage, ctx->stage2, ctx->diag, ctx->tslot,
-                    ctx->rec, ctx->kv, ctx->kw, ctx->rho, ctx->lr, ctx->ph};
+                    ctx->rec, ctx->kw, ctx->rho, ctx->rho_part, ctx->wcs, ctx->pen,
+                    ctx->rchunk, ctx->fchunk, ctx->lr, ctx->ph};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *tptrs[] = {ctx->tan.dx, ctx->tan.dv, ctx->tan.dvh, ctx->tan.pkt, ctx->tan.seeds,

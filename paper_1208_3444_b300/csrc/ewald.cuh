@@ -33,9 +33,11 @@
 //
 // k space: every body's tables exp(2 pi i n x_c/L), n = 0..nk, are computed
 // once per force evaluation (ewald_phase_kernel; n x_c/L reduced exactly in
-// FP64 before sincospi); the structure factors are one pass over (k, body)
-// pairs with those tables staged in shared memory, and the force pass
-// evaluates the k-sum at every body from its own tables.
+// FP64 before sincospi).  The k-vectors come in pencils of consecutive nz at
+// fixed (nx, ny); the x-y phase product is formed once per pencil and body.
+// The structure factors are one pass over (k, body) pairs (partial sums per
+// body split, added in order), and the force pass evaluates the k-sum at every
+// body from its own tables.
 #pragma once
 
 #include "common.cuh"
@@ -415,39 +417,62 @@ __global__ void ewald_phase_kernel(const float *__restrict__ pk, const double4 *
     }
 }
 
-constexpr int kEwBodies = 32;     // bodies per shared-memory table batch
-constexpr int kEwKThreads = 128;  // k-vectors per block of the structure-factor kernel
+// The k-vectors of the half space are ordered (nx, ny, nz) with nz fastest, so
+// those sharing (nx, ny) form a "pencil" of consecutive nz.  exp(i k.x) is the
+// product of the x and y phases, once per pencil and body, with the z phase.
+struct KPencil {
+    int nx, ny, nz0, len;         // k = (nx, ny, nz0 .. nz0 + len - 1)
+    int koff, pad0, pad1, pad2;   // index of the pencil's first k-vector
+};
 
-// exp(i k.x) of one body from its three axis tables (tab: [3][nt]); negative
-// ny, nz take the conjugate.
+// exp(i n 2 pi x_c / L) of one body for -nk <= n <= nk from its table of
+// n = 0 .. nk (entries `stride` apart): negative n take the conjugate.
 template <typename T, typename T2>
-__device__ __forceinline__ void phase_of(const T2 *tab, int nt, const KVec &k, T &re, T &im) {
-    const T2 x = tab[k.nx];
-    T2 y = tab[nt + abs(k.ny)];
-    T2 z = tab[2 * nt + abs(k.nz)];
-    if (k.ny < 0) y.y = -y.y;
-    if (k.nz < 0) z.y = -z.y;
-    const T er = x.x * y.x - x.y * y.y, ei = x.x * y.y + x.y * y.x;
-    re = er * z.x - ei * z.y;
-    im = er * z.y + ei * z.x;
+__device__ __forceinline__ T2 axis_phase(const T2 *row, int n, int stride) {
+    T2 v = row[(n < 0 ? -n : n) * stride];
+    if (n < 0) v.y = -v.y;
+    return v;
 }
 
-// rho[k] += sum over this block's bodies of m_j exp(i k.x_j); grid (k chunks,
-// body splits), block kEwKThreads; the bodies' tables are staged through
-// shared memory kEwBodies at a time.
+constexpr int kEwKThreads = 256;  // k-vectors per block of the structure-factor kernel
+
+// bodies per shared-memory batch of the structure-factor kernel
+template <typename T>
+__host__ __device__ constexpr int ew_bodies() { return sizeof(T) == 4 ? 64 : 32; }
+
+// Partial structure factors: rho_part[split][k] = sum over the split's bodies
+// of m_j exp(i k.x_j).  Grid (k chunks, body splits); a chunk is a run of whole
+// pencils with at most kEwKThreads k-vectors (rchunk: first pencil of chunk c;
+// np_max pencils at most), one k per thread.  Per batch of kEwBodies bodies the
+// block stages their tables, then the per-(body, pencil) base
+// m_j exp(i (kx x_j + ky y_j)), so a k costs one z-table read and one complex
+// multiply-add per body.  ewald_rho_sum_kernel adds the splits in order
+// (deterministic).
 template <typename T>
 __global__ void __launch_bounds__(kEwKThreads)
     ewald_rho_kernel(const float *__restrict__ pk, const double4 *__restrict__ pos, long long N,
-                     const typename Vec2<T>::type *__restrict__ ph, const KVec *__restrict__ kv,
-                     int nkv, EwaldArgs A, double2 *__restrict__ rho) {
+                     const typename Vec2<T>::type *__restrict__ ph, const KPencil *__restrict__ pen,
+                     const int *__restrict__ rchunk, int np_max, int nkv, EwaldArgs A,
+                     double2 *__restrict__ rho_part) {
     using T2 = typename Vec2<T>::type;
+    constexpr int kEwBodies = ew_bodies<T>();
     extern __shared__ __align__(16) unsigned char sm[];
     const int nt = A.nk + 1;
     T2 *tab = reinterpret_cast<T2 *>(sm);                       // [kEwBodies][3][nt]
-    T *tm = reinterpret_cast<T *>(tab + kEwBodies * 3 * nt);    // [kEwBodies]
-    const int kidx = blockIdx.x * kEwKThreads + threadIdx.x;
-    KVec k = {0, 0, 0, 0};
-    if (kidx < nkv) k = kv[kidx];
+    T2 *base = tab + kEwBodies * 3 * nt;                        // [kEwBodies][np_max]
+    T *tm = reinterpret_cast<T *>(base + kEwBodies * np_max);   // [kEwBodies]
+    int2 *sp = reinterpret_cast<int2 *>(tm + kEwBodies);        // [np_max] (nx, ny) of the chunk
+    const int p0 = rchunk[blockIdx.x], np = rchunk[blockIdx.x + 1] - p0;
+    const int k0 = pen[p0].koff;
+    const int nkc = pen[p0 + np - 1].koff + pen[p0 + np - 1].len - k0;
+    const int t = threadIdx.x;
+    for (int l = t; l < np; l += kEwKThreads) sp[l] = make_int2(pen[p0 + l].nx, pen[p0 + l].ny);
+    // this thread's k: its pencil (lp) and nz
+    int lp = 0;
+    while (lp + 1 < np && pen[p0 + lp + 1].koff <= k0 + t) ++lp;
+    const int nz = pen[p0 + lp].nz0 + (k0 + t - pen[p0 + lp].koff);
+    const int zrow = 2 * nt + (nz < 0 ? -nz : nz);
+    const T zs = nz < 0 ? (T)-1 : (T)1;
     const long long per = (N + gridDim.y - 1) / gridDim.y;
     const long long b0 = (long long)blockIdx.y * per, b1 = min(N, b0 + per);
     double cr = 0.0, ci = 0.0;
@@ -455,113 +480,170 @@ __global__ void __launch_bounds__(kEwKThreads)
         const int nb = (int)min((long long)kEwBodies, b1 - j0);
         __syncthreads();
         const T2 *src = ph + j0 * 3 * nt;
-        for (int q = threadIdx.x; q < nb * 3 * nt; q += kEwKThreads) tab[q] = src[q];
-        for (int b = threadIdx.x; b < nb; b += kEwKThreads) tm[b] = (T)body_mass(pk, pos, j0 + b);
+        for (int q = t; q < nb * 3 * nt; q += kEwKThreads) tab[q] = src[q];
+        for (int b = t; b < nb; b += kEwKThreads) tm[b] = (T)body_mass(pk, pos, j0 + b);
         __syncthreads();
-        if (kidx < nkv) {
+        for (int q = t; q < nb * np; q += kEwKThreads) {
+            const int b = q / np, l = q - b * np;
+            const int2 P = sp[l];
+            const T2 *tb = tab + b * 3 * nt;
+            const T2 x = tb[P.x];
+            const T2 y = axis_phase<T, T2>(tb + nt, P.y, 1);
+            const T m = tm[b];
+            T2 v;
+            v.x = m * (x.x * y.x - x.y * y.y);
+            v.y = m * (x.x * y.y + x.y * y.x);
+            base[q] = v;
+        }
+        __syncthreads();
+        if (t < nkc) {
             T pr = 0, pi = 0;
+#pragma unroll 4
             for (int b = 0; b < nb; ++b) {
-                T fr, fi;
-                phase_of<T, T2>(tab + b * 3 * nt, nt, k, fr, fi);
-                pr += tm[b] * fr;
-                pi += tm[b] * fi;
+                const T2 z = tab[b * 3 * nt + zrow];
+                const T2 w = base[b * np + lp];
+                const T zi = zs * z.y;
+                pr += w.x * z.x - w.y * zi;
+                pi += w.x * zi + w.y * z.x;
             }
             cr += (double)pr;
             ci += (double)pi;
         }
     }
-    if (kidx < nkv) {
-        atomicAdd(&rho[kidx].x, cr);
-        atomicAdd(&rho[kidx].y, ci);
+    if (t < nkc) rho_part[(long long)blockIdx.y * nkv + k0 + t] = make_double2(cr, ci);
+}
+
+// Shared memory of ewald_rho_kernel.
+template <typename T>
+__host__ inline size_t ew_rho_smem(int nk, int np_max) {
+    using T2 = typename Vec2<T>::type;
+    constexpr int nb = ew_bodies<T>();
+    return ((size_t)nb * 3 * (nk + 1) + (size_t)nb * np_max) * sizeof(T2) + nb * sizeof(T) +
+           (size_t)np_max * sizeof(int2);
+}
+
+// rho[k] = sum of the splits in order; wcs[k] = (w_k C(k), w_k S(k)) for the
+// long-range force (C, S the real and imaginary parts of rho).
+template <typename T>
+__global__ void ewald_rho_sum_kernel(const double2 *__restrict__ rho_part, int splits, int nkv,
+                                     const double *__restrict__ w, double2 *__restrict__ rho,
+                                     typename Vec2<T>::type *__restrict__ wcs) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nkv) return;
+    double r = 0.0, i = 0.0;
+    for (int s = 0; s < splits; ++s) {
+        const double2 v = rho_part[(long long)s * nkv + k];
+        r += v.x;
+        i += v.y;
     }
+    rho[k] = make_double2(r, i);
+    wcs[k].x = (T)(w[k] * r);
+    wcs[k].y = (T)(w[k] * i);
 }
 
 // Long-range acceleration (G-less) at every body:
-//   lr_i = -sum_k w_k k [sin(k.x_i) C(k) - cos(k.x_i) S(k)]
-// One thread per body.  The k-vectors are staged through shared memory
-// kEwKChunk at a time, already in the form the loop uses (the three table
-// offsets, the conjugation signs, n as floating point, w C and w S), so the
-// loop body is table reads and FMAs only; two accumulator chains.  The
-// block's body tables sit in shared memory as [3 nt][kEwFThreads]: every
-// thread evaluates the same k at a time, so a warp reads consecutive entries.
-constexpr int kEwFThreads = 64;
-constexpr int kEwKChunk = 256;
+//   lr_i = -sum_k w_k k [sin(k.x_i) C(k) - cos(k.x_i) S(k)].
+// A block holds kEwFThreads bodies' tables in shared memory as
+// [3 nt][kEwFThreads] (a warp reads consecutive entries) and runs
+// kEwFSlices threads per body, each taking every kEwFSlices-th pencil.  Per
+// pencil a thread forms the x-y phase once, then walks nz: one z-table read,
+// one complex multiply and the weights (w C, w S) read as a broadcast per k.
+// The sum over a pencil is scaled by (nx, ny) once.  Pencils arrive in chunks
+// of at most ew_fk<T>() k-vectors (fchunk), whose weights are staged first.
+// The slices' sums are added in slice order at the end (deterministic).
+constexpr int kEwFThreads = 64;    // bodies per block
+constexpr int kEwFSlices = 4;      // threads per body
+constexpr int kEwFKBytes = 16384;  // staged weights per chunk
 
 template <typename T>
-struct __align__(16) KStage {   // 48 B (float) / 80 B (double): whole 16-byte loads
-    int ox, oy, oz, pad;   // table rows of |nx|, |ny|, |nz| (x 64 threads)
-    T sy, sz;              // signs of ny, nz (conjugation)
-    T kx, ky, kz;          // n as floating point
-    T wc, ws;              // w_k C(k), w_k S(k)
-    T pad2;
-};
+__host__ __device__ constexpr int ew_fk() { return kEwFKBytes / (2 * (int)sizeof(T)); }
 
 template <typename T, typename T4>
-__global__ void __launch_bounds__(kEwFThreads)
+__global__ void __launch_bounds__(kEwFThreads * kEwFSlices)
     ewald_kforce_kernel(long long N, const typename Vec2<T>::type *__restrict__ ph,
-                        const KVec *__restrict__ kv, const double *__restrict__ w,
-                        const double2 *__restrict__ rho, int nkv, EwaldArgs A, T4 *__restrict__ lr) {
+                        const KPencil *__restrict__ pen, const int *__restrict__ fchunk, int nfchunk,
+                        const typename Vec2<T>::type *__restrict__ wcs, EwaldArgs A,
+                        T4 *__restrict__ lr) {
     using T2 = typename Vec2<T>::type;
+    constexpr int NT = kEwFThreads * kEwFSlices;
+    constexpr int FK = ew_fk<T>();
     extern __shared__ __align__(16) unsigned char sm[];
     const int nt = A.nk + 1;
-    KStage<T> *sk = reinterpret_cast<KStage<T> *>(sm);
-    T2 *tab = reinterpret_cast<T2 *>(sk + kEwKChunk);
+    T2 *sw = reinterpret_cast<T2 *>(sm);   // [FK] weights of the chunk
+    T2 *tab = sw + FK;                     // [3 nt][kEwFThreads]
     const long long i0 = (long long)blockIdx.x * kEwFThreads;
     const int nb = (int)min((long long)kEwFThreads, N - i0);
-    for (int q = threadIdx.x; q < nb * 3 * nt; q += kEwFThreads) {
+    for (int q = threadIdx.x; q < nb * 3 * nt; q += NT) {
         const int b = q / (3 * nt), r = q - b * 3 * nt;
         tab[r * kEwFThreads + b] = ph[i0 * 3 * nt + q];
     }
-    const long long i = i0 + threadIdx.x;
-    const T2 *mine = tab + threadIdx.x;
+    const int bi = threadIdx.x % kEwFThreads, sl = threadIdx.x / kEwFThreads;
+    const long long i = i0 + bi;
+    const T2 *mine = tab + bi;
+    const T2 *zt = mine + 2 * nt * kEwFThreads;
     const double tpl = 2.0 * acos(-1.0) / A.L;
     double ax = 0.0, ay = 0.0, az = 0.0;
-    for (int k0 = 0; k0 < nkv; k0 += kEwKChunk) {
-        const int nc = min(kEwKChunk, nkv - k0);
+    for (int c = 0; c < nfchunk; ++c) {
+        const int p0 = fchunk[c], p1 = fchunk[c + 1];
+        const int k0 = pen[p0].koff, nkc = pen[p1 - 1].koff + pen[p1 - 1].len - k0;
         __syncthreads();
-        for (int q = threadIdx.x; q < nc; q += kEwFThreads) {
-            const KVec k = kv[k0 + q];
-            const double2 r = rho[k0 + q];
-            KStage<T> e;
-            e.ox = k.nx * kEwFThreads;
-            e.oy = (nt + abs(k.ny)) * kEwFThreads;
-            e.oz = (2 * nt + abs(k.nz)) * kEwFThreads;
-            e.pad = 0;
-            e.sy = k.ny < 0 ? (T)-1 : (T)1;
-            e.sz = k.nz < 0 ? (T)-1 : (T)1;
-            e.kx = (T)k.nx;
-            e.ky = (T)k.ny;
-            e.kz = (T)k.nz;
-            e.wc = (T)(w[k0 + q] * r.x);
-            e.ws = (T)(w[k0 + q] * r.y);
-            e.pad2 = (T)0;
-            sk[q] = e;
-        }
+        for (int q = threadIdx.x; q < nkc; q += NT) sw[q] = wcs[k0 + q];
         __syncthreads();
         if (i < N) {
-            T px[2] = {0, 0}, py[2] = {0, 0}, pz[2] = {0, 0};
-#pragma unroll 2
-            for (int q = 0; q < nc; ++q) {
-                const KStage<T> &e = sk[q];
-                const T2 x = mine[e.ox], y = mine[e.oy], z = mine[e.oz];
-                const T yi = e.sy * y.y, zi = e.sz * z.y;
-                const T er = x.x * y.x - x.y * yi, ei = x.x * yi + x.y * y.x;
-                const T cr = er * z.x - ei * zi, si = er * zi + ei * z.x;   // cos, sin of k.x_i
-                const T b = si * e.wc - cr * e.ws;
-                const int c = q & 1;
-                px[c] += b * e.kx;
-                py[c] += b * e.ky;
-                pz[c] += b * e.kz;
+            T px = 0, py = 0, pz = 0;
+            for (int p = p0 + sl; p < p1; p += kEwFSlices) {
+                const KPencil P = pen[p];
+                const T2 x = mine[P.nx * kEwFThreads];
+                const T2 y = axis_phase<T, T2>(mine + nt * kEwFThreads, P.ny, kEwFThreads);
+                const T er = x.x * y.x - x.y * y.y, ei = x.x * y.y + x.y * y.x;
+                const T2 *wk = sw + (P.koff - k0 - P.nz0);   // weights indexed by nz
+                T B = 0, Bz = 0;
+                const int nz1 = P.nz0 + P.len;
+                int nz = P.nz0;
+                for (; nz < 0 && nz < nz1; ++nz) {           // negative nz: conjugate z phase
+                    const T2 z = zt[-nz * kEwFThreads];
+                    const T cr = er * z.x + ei * z.y, si = ei * z.x - er * z.y;
+                    const T2 w = wk[nz];
+                    const T b = si * w.x - cr * w.y;
+                    B += b;
+                    Bz += b * (T)nz;
+                }
+                for (; nz < nz1; ++nz) {
+                    const T2 z = zt[nz * kEwFThreads];
+                    const T cr = er * z.x - ei * z.y, si = er * z.y + ei * z.x;
+                    const T2 w = wk[nz];
+                    const T b = si * w.x - cr * w.y;
+                    B += b;
+                    Bz += b * (T)nz;
+                }
+                px += (T)P.nx * B;
+                py += (T)P.ny * B;
+                pz += Bz;
             }
-            ax += (double)px[0] + (double)px[1];
-            ay += (double)py[0] + (double)py[1];
-            az += (double)pz[0] + (double)pz[1];
+            ax += (double)px;
+            ay += (double)py;
+            az += (double)pz;
         }
     }
-    if (i < N) {
-        lr[i].x = (T)(-tpl * ax);
-        lr[i].y = (T)(-tpl * ay);
-        lr[i].z = (T)(-tpl * az);
+    // add the slices in order; the weight staging area holds the partial sums
+    __syncthreads();
+    double *red = reinterpret_cast<double *>(sm);   // [3][kEwFSlices][kEwFThreads]
+    static_assert(3 * NT * sizeof(double) <= kEwFKBytes, "reduction fits");
+    red[(0 * kEwFSlices + sl) * kEwFThreads + bi] = ax;
+    red[(1 * kEwFSlices + sl) * kEwFThreads + bi] = ay;
+    red[(2 * kEwFSlices + sl) * kEwFThreads + bi] = az;
+    __syncthreads();
+    if (sl == 0 && i < N) {
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+#pragma unroll
+        for (int t = 0; t < kEwFSlices; ++t) {
+            sx += red[(0 * kEwFSlices + t) * kEwFThreads + bi];
+            sy += red[(1 * kEwFSlices + t) * kEwFThreads + bi];
+            sz += red[(2 * kEwFSlices + t) * kEwFThreads + bi];
+        }
+        lr[i].x = (T)(-tpl * sx);
+        lr[i].y = (T)(-tpl * sy);
+        lr[i].z = (T)(-tpl * sz);
         lr[i].w = (T)0;
     }
 }

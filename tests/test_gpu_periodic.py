@@ -166,3 +166,18 @@ def test_paths_not_built_for_periodic_boundaries_refuse():
             sim.periodic_params()
     finally:
         sim.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_periodic_forces_are_deterministic(prec):
+    # the structure factors are summed over body splits in a fixed order
+    rng = np.random.default_rng(814)
+    x, m = inputs.f32(rng.random((5000, 3))), inputs.f32(rng.random(5000) / 5000)
+    sim = B.Simulation(m, 0.01, LCDM_D, 1.0, prec=prec)
+    try:
+        sim.set_state(x)
+        sim.set_periodic(1.0)
+        first = sim.forces()
+        assert all(np.array_equal(first, sim.forces()) for _ in range(3))
+    finally:
+        sim.close()
