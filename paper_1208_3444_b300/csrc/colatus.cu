@@ -112,7 +112,8 @@ constexpr int kChunk = 1024;            // steps enqueued per chunk of colatus_s
 constexpr int kTabCap = 4096;           // ring of look-ahead schedule entries
 constexpr int kLookahead = 256;         // schedule entries kept ahead of the state
 constexpr int kFriedmannSub = 8;        // RK4 sub-steps per half step
-constexpr int kTabEvents = 8;           // extension events kept in flight
+constexpr int kTabEvents = 64;          // extension events kept in flight (one per piece)
+constexpr int kTabPiece = 64;           // schedule entries per extension launch
 static_assert(kChunk + 4 * kLookahead <= kTabCap, "schedule ring too small");
 
 long long round_up(long long n, long long m) { return (n + m - 1) / m * m; }
@@ -876,27 +877,47 @@ colatus_status load_masses(colatus_t ctx, const void *src, int f64) {
     return COLATUS_OK;
 }
 
-// Extend the look-ahead schedule by n entries on the schedule stream.
+// Extend the look-ahead schedule by n entries on the schedule stream, in
+// launches of kTabPiece entries, each followed by an event that records how
+// far the schedule then reaches; steps wait only for the piece they need.
 colatus_status extend_table(colatus_t ctx, int n) {
-    if (n <= 0) return COLATUS_OK;
-    friedmann_table_kernel<<<1, 1, ctx->tab_smem, ctx->tstream>>>(ctx->cosmo, ctx->tclk, ctx->table, kTabCap,
-                                                      n, ctx->tab_tau, ctx->tab_G, kFriedmannSub,
-                                                      canonical(ctx));
-    TRY(launched(ctx));
-    ctx->tab_hi += n;
-    const int k = ctx->tab_ev_next;
-    ctx->tab_ev_next = (k + 1) % kTabEvents;
-    CU(cudaEventRecord(ctx->tab_ev[k], ctx->tstream));
-    ctx->tab_ev_covers[k] = ctx->tab_hi;
+    for (int done = 0; done < n; done += kTabPiece) {
+        const int m = std::min(kTabPiece, n - done);
+        friedmann_table_kernel<<<1, 1, ctx->tab_smem, ctx->tstream>>>(
+            ctx->cosmo, ctx->tclk, ctx->table, kTabCap, m, ctx->tab_tau, ctx->tab_G, kFriedmannSub,
+            canonical(ctx));
+        TRY(launched(ctx));
+        ctx->tab_hi += m;
+        const int k = ctx->tab_ev_next;
+        ctx->tab_ev_next = (k + 1) % kTabEvents;
+        CU(cudaEventRecord(ctx->tab_ev[k], ctx->tstream));
+        ctx->tab_ev_covers[k] = ctx->tab_hi;
+    }
     return COLATUS_OK;
 }
 
-// Make schedule entries [host_step, host_step + n] available to the main
-// stream for step size tau.  The schedule stream first waits for all work
-// already enqueued on the main stream, so an extension never overwrites ring
-// entries that enqueued steps still read (the ring holds kTabCap entries and
-// at most kChunk + 4 kLookahead are live).
-colatus_status need_table(colatus_t ctx, double tau, int n) {
+// Make the main stream wait until the schedule holds the entries below
+// `need` (the earliest extension piece that reaches it).
+colatus_status wait_table(colatus_t ctx, long long need) {
+    int best = -1;
+    for (int k = 0; k < kTabEvents; ++k)
+        if (ctx->tab_ev_covers[k] >= need &&
+            (best < 0 || ctx->tab_ev_covers[k] < ctx->tab_ev_covers[best]))
+            best = k;
+    if (best < 0) return fail(ctx, COLATUS_E_STATE, "schedule bookkeeping lost its extension");
+    CU(cudaStreamWaitEvent(ctx->stream, ctx->tab_ev[best], 0));
+    return COLATUS_OK;
+}
+
+// Make schedule entries [host_step, host_step + n] available for step size
+// tau: extend the schedule to cover them (plus the look-ahead), and make the
+// main stream wait for the first `first` steps' entries only; a caller that
+// passes first < n waits for the rest with wait_table as it goes.  The
+// schedule stream first waits for all work already enqueued on the main
+// stream, so an extension never overwrites ring entries that enqueued steps
+// still read (the ring holds kTabCap entries and at most kChunk +
+// 4 kLookahead are live).
+colatus_status need_table(colatus_t ctx, double tau, int n, int first) {
     CU(cudaEventRecord(ctx->main_ev, ctx->stream));
     CU(cudaStreamWaitEvent(ctx->tstream, ctx->main_ev, 0));
     if (!ctx->tab_valid || ctx->tab_tau != tau || ctx->tab_G != ctx->G) {
@@ -912,15 +933,14 @@ colatus_status need_table(colatus_t ctx, double tau, int n) {
     // opening coefficients the last step's epilogue applies
     const long long need = ctx->host_step + n + 1;
     if (ctx->tab_hi < need) TRY(extend_table(ctx, (int)(need + kLookahead - ctx->tab_hi)));
-    // wait only for the earliest extension that completes the needed entries
-    int best = -1;
-    for (int k = 0; k < kTabEvents; ++k)
-        if (ctx->tab_ev_covers[k] >= need &&
-            (best < 0 || ctx->tab_ev_covers[k] < ctx->tab_ev_covers[best]))
-            best = k;
-    if (best < 0) return fail(ctx, COLATUS_E_STATE, "schedule bookkeeping lost its extension");
-    CU(cudaStreamWaitEvent(ctx->stream, ctx->tab_ev[best], 0));
-    return COLATUS_OK;
+    return wait_table(ctx, ctx->host_step + std::min(first, n) + 1);
+}
+
+// Before step j of a chunk of n steps enqueued after need_table(.., n,
+// kTabPiece): every kTabPiece steps, wait for the next piece's entries.
+colatus_status wait_table_at(colatus_t ctx, int j, int n) {
+    if (j == 0 || j % kTabPiece != 0) return COLATUS_OK;
+    return wait_table(ctx, ctx->host_step + std::min(j + kTabPiece, n) + 1);
 }
 
 // After enqueuing steps: keep kLookahead entries ahead, computed on the
@@ -1510,13 +1530,16 @@ colatus_status colatus_step(colatus_t ctx, double dt, int64_t nsteps) {
     if (ctx->spec_valid && ctx->spec_tau != dt) ctx->spec_valid = false;
     for (int64_t done = 0; done < nsteps;) {
         const int n = (int)std::min<int64_t>(kChunk, nsteps - done);
-        TRY(need_table(ctx, dt, n));
-            if (!ctx->spec_valid) {
+        TRY(need_table(ctx, dt, n, kTabPiece));
+        if (!ctx->spec_valid) {
             TRY(open_step(ctx, dt));
             ctx->spec_valid = true;
             ctx->spec_tau = dt;
         }
-        for (int j = 0; j < n; ++j) TRY(one_step(ctx, j, dt));
+        for (int j = 0; j < n; ++j) {
+            TRY(wait_table_at(ctx, j, n));
+            TRY(one_step(ctx, j, dt));
+        }
         done += n;
         ctx->host_step += n;
         TRY(refill_table(ctx));
@@ -2029,8 +2052,8 @@ colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps) {
     dim3 grid(blocks_for(ctx->N, 256), t.nchunk);
     for (int64_t done = 0; done < nsteps;) {
         const int n = (int)std::min<int64_t>(kChunk, nsteps - done);
-        TRY(need_table(ctx, dt, n));
-            if (!t.open) {
+        TRY(need_table(ctx, dt, n, kTabPiece));
+        if (!t.open) {
             // tangent opening at x^n: JVP on the packed state positions
             const ForcePlan &p = plan_f32(ctx);
             pack_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(ctx->xs, ctx->pk[2],
@@ -2052,6 +2075,7 @@ colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps) {
         }
         for (int j = 0; j < n; ++j) {
             const int c = ctx->cur;
+            TRY(wait_table_at(ctx, j, n));
             TRY(one_step(ctx, j, dt));
             TRY(run_jvp(ctx, ctx->pk[c]));
             tan_step_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part),

@@ -197,10 +197,10 @@ __global__ void ens_table_kernel(Cosmo cosmo, const DevClock *clk, StepCoef *tab
     for (int j = 0; j < n; ++j) {
         bool bad = false;
         StepCoef s;
-        double K = 0.0, Dr = 0.0;   // canonical factors: unused by the drag scheme
+        double K = 0.0, Dr = 0.0;   // canonical integrals: not computed for the drag scheme
         s.a0 = a;
-        s.ah = friedmann_advance(a, 0.5 * tau, cosmo, nsub, bad, K, Dr);
-        s.a1 = friedmann_advance(s.ah, 0.5 * tau, cosmo, nsub, bad, K, Dr);
+        s.ah = friedmann_advance<false>(a, 0.5 * tau, cosmo, nsub, bad, K, Dr);
+        s.a1 = friedmann_advance<false>(s.ah, 0.5 * tau, cosmo, nsub, bad, K, Dr);
         kick_coef(s.ah, hubble_of(s.ah, cosmo, bad), tau, G, s.c, s.d);
         kick_coef(s.a0, hubble_of(s.a0, cosmo, bad), 0.5 * tau, G, s.c1, s.d1);
         kick_coef(s.a1, hubble_of(s.a1, cosmo, bad), 0.5 * tau, G, s.c2, s.d2);

@@ -30,8 +30,12 @@ __device__ inline double hubble_of(double a, const Cosmo &c, bool &bad) {
 
 // Classical RK4 with nsub equal sub-steps over dt, on the system
 // (a, I1, I2)' = (a H(a), 1/a, 1/a^2): I1 and I2 accumulate int dt/a and
-// int dt/a^2, the kick and drift factors of the canonical leapfrog.  Every
-// scheme goes through this one routine, so a(t) does not depend on it.
+// int dt/a^2, the kick and drift factors of the canonical leapfrog.  The
+// a-chain is the same instruction sequence with or without the integrals
+// (INTEG), so a(t) is bitwise the same for every scheme; the drag schemes
+// skip the integrals and their four FP64 divisions per sub-step (this GPU's
+// FP64 pipe takes about 16 cycles per warp instruction, even for one thread).
+template <bool INTEG>
 __device__ inline double friedmann_advance(double a, double dt, const Cosmo &c, int nsub,
                                            bool &bad, double &I1, double &I2) {
     const double h = dt / nsub, h6 = h / 6.0;
@@ -44,9 +48,11 @@ __device__ inline double friedmann_advance(double a, double dt, const Cosmo &c, 
         const double k3 = friedmann_rhs(s4, c, bad);
         const double s5 = a + h * k3;
         const double k4 = friedmann_rhs(s5, c, bad);
-        const double r1 = 1.0 / s2, r2 = 1.0 / s3, r3 = 1.0 / s4, r4 = 1.0 / s5;
-        I1 += h6 * (r1 + 2.0 * r2 + 2.0 * r3 + r4);
-        I2 += h6 * (r1 * r1 + 2.0 * (r2 * r2) + 2.0 * (r3 * r3) + r4 * r4);
+        if (INTEG) {
+            const double r1 = 1.0 / s2, r2 = 1.0 / s3, r3 = 1.0 / s4, r4 = 1.0 / s5;
+            I1 += h6 * (r1 + 2.0 * r2 + 2.0 * r3 + r4);
+            I2 += h6 * (r1 * r1 + 2.0 * (r2 * r2) + 2.0 * (r3 * r3) + r4 * r4);
+        }
         a = a + h6 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
     }
     return a;
@@ -80,8 +86,13 @@ __global__ void friedmann_table_kernel(Cosmo cosmo, DevClock *tclk, StepCoef *ta
         StepCoef s;
         double K1 = 0.0, K2 = 0.0, D = 0.0;
         s.a0 = a;
-        s.ah = friedmann_advance(a, 0.5 * tau, cosmo, nsub, bad, K1, D);
-        s.a1 = friedmann_advance(s.ah, 0.5 * tau, cosmo, nsub, bad, K2, D);
+        if (canonical) {
+            s.ah = friedmann_advance<true>(a, 0.5 * tau, cosmo, nsub, bad, K1, D);
+            s.a1 = friedmann_advance<true>(s.ah, 0.5 * tau, cosmo, nsub, bad, K2, D);
+        } else {
+            s.ah = friedmann_advance<false>(a, 0.5 * tau, cosmo, nsub, bad, K1, D);
+            s.a1 = friedmann_advance<false>(s.ah, 0.5 * tau, cosmo, nsub, bad, K2, D);
+        }
         kick_coef(s.ah, hubble_of(s.ah, cosmo, bad), tau, G, s.c, s.d);
         if (canonical) {
             const double Dt = D / tau;

@@ -225,3 +225,28 @@ def test_layzer_irvine_residual_follows_the_oracle(prec, tol):
     res_ref = oracle.layzer_irvine([d[1] for d in r["diagnostics"]], TAU * np.arange(n + 1))
     assert 1e-3 < np.abs(res_ref).max() < 1e-2            # the discretisation error is resolved
     np.testing.assert_allclose(res_gpu, res_ref, rtol=0, atol=tol)
+
+
+@pytest.mark.parametrize("scheme", [B.KDK, B.KDK_CANONICAL])
+def test_long_calls_match_single_steps_and_the_schedule(scheme):
+    # One call of 300 steps runs while the FP64 schedule is still being
+    # extended (in pieces of tens of entries on a side stream); it must give
+    # the same states, bit for bit, as 300 calls of one step, and the
+    # oracle's a(t).
+    ic = inputs.grid8()
+    n = 300
+    out = []
+    for calls in ([n], [1] * n):
+        sim = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START, prec=B.FP32, scheme=scheme)
+        try:
+            sim.set_state(ic.x, ic.v)
+            for c in calls:
+                sim.step(TAU, c)
+            out.append(sim.state())
+        finally:
+            sim.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    kind = "canonical" if scheme == B.KDK_CANONICAL else "kdk"
+    sch = oracle.schedule(LCDM, inputs.A_START, TAU, n, kind)
+    assert out[0][3] == pytest.approx(sch["a"][-1], rel=1e-13)
+    assert out[0][2] == pytest.approx(n * TAU, rel=1e-13)
