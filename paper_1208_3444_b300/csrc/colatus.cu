@@ -2284,7 +2284,10 @@ void colatus_destroy(colatus_t ctx) {
     if (!ctx) return;
     {
         DeviceGuard dg(ctx->device);
+        // the schedule and read-back streams may still run work that uses the buffers
         if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+        if (ctx->tstream) cudaStreamSynchronize(ctx->tstream);
+        if (ctx->cstream) cudaStreamSynchronize(ctx->cstream);
         free_all(ctx);
     }
     delete ctx;
