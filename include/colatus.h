@@ -81,7 +81,12 @@ typedef enum { COLATUS_F32 = 0, COLATUS_F64 = 1 } colatus_dtype;
  * Defaults: COLATUS_FP32, COLATUS_KDK, G = 1, a library-owned stream.
  * Errors: COLATUS_E_ARG (N < 1, eps <= 0 or not finite, a_start <= 0, NULL
  * pointers, H^2(a_start) < 0), COLATUS_E_OOM, COLATUS_E_CUDA.  On error *out
- * is set to NULL and nothing is leaked. */
+ * is set to NULL and nothing is leaked.
+ * Checkpoint and resume: after any colatus_step, colatus_get_state gives
+ * (x, v, t, a).  A new context created with a_start = a and the same masses,
+ * eps, Omega_*, H0, precision, scheme and G, given x and v with
+ * colatus_set_state, continues the run bit for bit with the same step size
+ * (its time restarts at 0, so add t). */
 colatus_status colatus_init(colatus_t *out, int64_t N, const double *masses, double eps,
                             double Omega_R, double Omega_M, double Omega_K, double Omega_L,
                             double H0, double a_start);

@@ -81,6 +81,19 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     return y;
 }
 
+// The kick a x + b y and the drift x + t v with one fixed rounding sequence.
+// The _rn intrinsics are never contracted or reordered by the compiler, so
+// every kernel that applies the same kick or drift (a step's epilogue and a
+// later call's opening, for one) produces the same bits.
+__device__ __forceinline__ float kick2(float a, float x, float b, float y) {
+    return __fmaf_rn(b, y, __fmul_rn(a, x));
+}
+__device__ __forceinline__ double kick2(double a, double x, double b, double y) {
+    return __fma_rn(b, y, __dmul_rn(a, x));
+}
+__device__ __forceinline__ float drift1(float x, float t, float v) { return __fmaf_rn(t, v, x); }
+__device__ __forceinline__ double drift1(double x, double t, double v) { return __fma_rn(t, v, x); }
+
 // Knuth's TwoSum: s + e == a + b exactly (round-to-nearest).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = a + b;

@@ -254,9 +254,9 @@ __global__ void ens_open_kernel(const float4 *__restrict__ xs, const float4 *__r
     }
     const float c1 = (float)table[0].c1, d1 = (float)table[0].d1, t = (float)tau;
     const float4 x = xs[i], v = vs[i], F = acc[i];
-    const float hx = c1 * v.x + d1 * F.x, hy = c1 * v.y + d1 * F.y, hz = c1 * v.z + d1 * F.z;
+    const float hx = kick2(c1, v.x, d1, F.x), hy = kick2(c1, v.y, d1, F.y), hz = kick2(c1, v.z, d1, F.z);
     vh[i] = make_float4(hx, hy, hz, 0.f);
-    pk_store(pk_out, i, x.x + t * hx, x.y + t * hy, x.z + t * hz, x.w);
+    pk_store(pk_out, i, drift1(x.x, t, hx), drift1(x.y, t, hy), drift1(x.z, t, hz), x.w);
 }
 
 // KDK step j of a chunk after the force at x^{n+1} (pk_in): close the step,
@@ -279,13 +279,13 @@ __global__ void ens_step_kernel(const float4 *__restrict__ part, EnsLaunch E, in
     const float3 F = ens_reduce(part, E, itile, i);
     const float4 x = pk_load(pk_in, i);
     const float4 h = vh[i];
-    const float vx = c2 * h.x + d2 * F.x, vy = c2 * h.y + d2 * F.y, vz = c2 * h.z + d2 * F.z;
+    const float vx = kick2(c2, h.x, d2, F.x), vy = kick2(c2, h.y, d2, F.y), vz = kick2(c2, h.z, d2, F.z);
     acc[i] = make_float4(F.x, F.y, F.z, 0.f);
     xs[i] = x;
     vs[i] = make_float4(vx, vy, vz, 0.f);
-    const float nx = c2 * vx + d2 * F.x, ny = c2 * vy + d2 * F.y, nz = c2 * vz + d2 * F.z;
+    const float nx = kick2(c2, vx, d2, F.x), ny = kick2(c2, vy, d2, F.y), nz = kick2(c2, vz, d2, F.z);
     vh[i] = make_float4(nx, ny, nz, 0.f);
-    pk_store(pk_out, i, x.x + t * nx, x.y + t * ny, x.z + t * nz, x.w);
+    pk_store(pk_out, i, drift1(x.x, t, nx), drift1(x.y, t, ny), drift1(x.z, t, nz), x.w);
     if (!finite3(x.x, x.y, x.z) || !finite3(vx, vy, vz)) atomicOr(&flags[FLAG_NONFINITE], 1);
 }
 

@@ -367,9 +367,9 @@ __global__ void kdk_open_f32_kernel(const float4 *__restrict__ xs, const float4 
     }
     const float c1 = (float)table[step % tcap].c1, d1 = (float)table[step % tcap].d1, t = (float)tau;
     const float4 x = xs[i], v = vs[i], F = acc[i];
-    const float hx = c1 * v.x + d1 * F.x, hy = c1 * v.y + d1 * F.y, hz = c1 * v.z + d1 * F.z;
+    const float hx = kick2(c1, v.x, d1, F.x), hy = kick2(c1, v.y, d1, F.y), hz = kick2(c1, v.z, d1, F.z);
     vh[i] = make_float4(hx, hy, hz, 0.f);
-    pk_store(pk_out, i, x.x + t * hx, x.y + t * hy, x.z + t * hz, x.w);
+    pk_store(pk_out, i, drift1(x.x, t, hx), drift1(x.y, t, hy), drift1(x.z, t, hz), x.w);
 }
 
 // KDK step j, after the force at x^{n+1} (pk_in):
@@ -400,14 +400,14 @@ __global__ void kdk_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
     defo_force(D, x.x, x.y, x.z, F.x, F.y, F.z);
     add_long_range(D, i, F.x, F.y, F.z);
     const float4 h = vh[i];
-    const float vx = c2 * h.x + d2 * F.x, vy = c2 * h.y + d2 * F.y, vz = c2 * h.z + d2 * F.z;
+    const float vx = kick2(c2, h.x, d2, F.x), vy = kick2(c2, h.y, d2, F.y), vz = kick2(c2, h.z, d2, F.z);
     acc[i] = make_float4(F.x, F.y, F.z, 0.f);
     xs[i] = x;
     vs[i] = make_float4(vx, vy, vz, 0.f);
     record(tr, i, sc.step, x.x, x.y, x.z, vx, vy, vz);
-    const float nx = c1n * vx + d1n * F.x, ny = c1n * vy + d1n * F.y, nz = c1n * vz + d1n * F.z;
+    const float nx = kick2(c1n, vx, d1n, F.x), ny = kick2(c1n, vy, d1n, F.y), nz = kick2(c1n, vz, d1n, F.z);
     vh[i] = make_float4(nx, ny, nz, 0.f);
-    pk_store(pk_out, i, x.x + t * nx, x.y + t * ny, x.z + t * nz, x.w);
+    pk_store(pk_out, i, drift1(x.x, t, nx), drift1(x.y, t, ny), drift1(x.z, t, nz), x.w);
     if (!finite3(x.x, x.y, x.z) || !finite3(vx, vy, vz)) atomicOr(&flags[FLAG_NONFINITE], 1);
 }
 
@@ -423,7 +423,7 @@ __global__ void dkd_open_f32_kernel(const float4 *__restrict__ xs, const float4 
     }
     const float h = (float)(0.5 * tau);
     const float4 x = xs[i], v = vs[i];
-    pk_store(pk_out, i, x.x + h * v.x, x.y + h * v.y, x.z + h * v.z, x.w);
+    pk_store(pk_out, i, drift1(x.x, h, v.x), drift1(x.y, h, v.y), drift1(x.z, h, v.z), x.w);
 }
 
 // DKD step j (Eqs. 3-5), after the force at x^{n+1/2} (pk_in):
@@ -450,13 +450,13 @@ __global__ void dkd_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
     defo_force(D, xh.x, xh.y, xh.z, F.x, F.y, F.z);
     add_long_range(D, i, F.x, F.y, F.z);
     const float4 v0 = vs[i];
-    const float vx = c * v0.x + d * F.x, vy = c * v0.y + d * F.y, vz = c * v0.z + d * F.z;
-    const float x1 = xh.x + h * vx, y1 = xh.y + h * vy, z1 = xh.z + h * vz;
+    const float vx = kick2(c, v0.x, d, F.x), vy = kick2(c, v0.y, d, F.y), vz = kick2(c, v0.z, d, F.z);
+    const float x1 = drift1(xh.x, h, vx), y1 = drift1(xh.y, h, vy), z1 = drift1(xh.z, h, vz);
     acc[i] = make_float4(F.x, F.y, F.z, 0.f);
     xs[i] = make_float4(x1, y1, z1, xh.w);
     vs[i] = make_float4(vx, vy, vz, 0.f);
     record(tr, i, sc.step, x1, y1, z1, vx, vy, vz);
-    pk_store(pk_out, i, x1 + h * vx, y1 + h * vy, z1 + h * vz, xh.w);
+    pk_store(pk_out, i, drift1(x1, h, vx), drift1(y1, h, vy), drift1(z1, h, vz), xh.w);
     if (!finite3(x1, y1, z1) || !finite3(vx, vy, vz)) atomicOr(&flags[FLAG_NONFINITE], 1);
 }
 
@@ -474,9 +474,9 @@ __global__ void kdk_open_f64_kernel(const double4 *__restrict__ xs, const double
     }
     const double c1 = table[step % tcap].c1, d1 = table[step % tcap].d1;
     const double4 x = xs[i], v = vs[i], F = acc[i];
-    const double hx = c1 * v.x + d1 * F.x, hy = c1 * v.y + d1 * F.y, hz = c1 * v.z + d1 * F.z;
+    const double hx = kick2(c1, v.x, d1, F.x), hy = kick2(c1, v.y, d1, F.y), hz = kick2(c1, v.z, d1, F.z);
     vh[i] = make_double4(hx, hy, hz, 0.0);
-    pos_out[i] = make_double4(x.x + tau * hx, x.y + tau * hy, x.z + tau * hz, x.w);
+    pos_out[i] = make_double4(drift1(x.x, tau, hx), drift1(x.y, tau, hy), drift1(x.z, tau, hz), x.w);
 }
 
 __global__ void kdk_step_f64_kernel(const double4 *__restrict__ part, ForceLaunch L, int itile,
@@ -500,14 +500,14 @@ __global__ void kdk_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
     defo_force(D, x.x, x.y, x.z, F.x, F.y, F.z);
     add_long_range(D, i, F.x, F.y, F.z);
     const double4 h = vh[i];
-    const double vx = c2 * h.x + d2 * F.x, vy = c2 * h.y + d2 * F.y, vz = c2 * h.z + d2 * F.z;
+    const double vx = kick2(c2, h.x, d2, F.x), vy = kick2(c2, h.y, d2, F.y), vz = kick2(c2, h.z, d2, F.z);
     acc[i] = make_double4(F.x, F.y, F.z, 0.0);
     xs[i] = x;
     vs[i] = make_double4(vx, vy, vz, 0.0);
     record(tr, i, sc.step, x.x, x.y, x.z, vx, vy, vz);
-    const double nx = c1n * vx + d1n * F.x, ny = c1n * vy + d1n * F.y, nz = c1n * vz + d1n * F.z;
+    const double nx = kick2(c1n, vx, d1n, F.x), ny = kick2(c1n, vy, d1n, F.y), nz = kick2(c1n, vz, d1n, F.z);
     vh[i] = make_double4(nx, ny, nz, 0.0);
-    pos_out[i] = make_double4(x.x + tau * nx, x.y + tau * ny, x.z + tau * nz, x.w);
+    pos_out[i] = make_double4(drift1(x.x, tau, nx), drift1(x.y, tau, ny), drift1(x.z, tau, nz), x.w);
     if (!finite3(x.x, x.y, x.z) || !finite3(vx, vy, vz)) atomicOr(&flags[FLAG_NONFINITE], 1);
 }
 
@@ -522,7 +522,7 @@ __global__ void dkd_open_f64_kernel(const double4 *__restrict__ xs, const double
     }
     const double h = 0.5 * tau;
     const double4 x = xs[i], v = vs[i];
-    pos_out[i] = make_double4(x.x + h * v.x, x.y + h * v.y, x.z + h * v.z, x.w);
+    pos_out[i] = make_double4(drift1(x.x, h, v.x), drift1(x.y, h, v.y), drift1(x.z, h, v.z), x.w);
 }
 
 __global__ void dkd_step_f64_kernel(const double4 *__restrict__ part, ForceLaunch L, int itile,
@@ -545,13 +545,13 @@ __global__ void dkd_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
     defo_force(D, xh.x, xh.y, xh.z, F.x, F.y, F.z);
     add_long_range(D, i, F.x, F.y, F.z);
     const double4 v0 = vs[i];
-    const double vx = c * v0.x + d * F.x, vy = c * v0.y + d * F.y, vz = c * v0.z + d * F.z;
-    const double x1 = xh.x + h * vx, y1 = xh.y + h * vy, z1 = xh.z + h * vz;
+    const double vx = kick2(c, v0.x, d, F.x), vy = kick2(c, v0.y, d, F.y), vz = kick2(c, v0.z, d, F.z);
+    const double x1 = drift1(xh.x, h, vx), y1 = drift1(xh.y, h, vy), z1 = drift1(xh.z, h, vz);
     acc[i] = make_double4(F.x, F.y, F.z, 0.0);
     xs[i] = make_double4(x1, y1, z1, xh.w);
     vs[i] = make_double4(vx, vy, vz, 0.0);
     record(tr, i, sc.step, x1, y1, z1, vx, vy, vz);
-    pos_out[i] = make_double4(x1 + h * vx, y1 + h * vy, z1 + h * vz, xh.w);
+    pos_out[i] = make_double4(drift1(x1, h, vx), drift1(y1, h, vy), drift1(z1, h, vz), xh.w);
     if (!finite3(x1, y1, z1) || !finite3(vx, vy, vz)) atomicOr(&flags[FLAG_NONFINITE], 1);
 }
 

@@ -278,11 +278,11 @@ __global__ void tan_open_kernel(const float4 *__restrict__ part, ForceLaunch L, 
         if (b >= T.B) break;
         const long long k = b * n_pad + i;
         const float4 v = T.dv[k];
-        const float hx = c1 * v.x + d1 * f[3 * q], hy = c1 * v.y + d1 * f[3 * q + 1],
-                    hz = c1 * v.z + d1 * f[3 * q + 2];
+        const float hx = kick2(c1, v.x, d1, f[3 * q]), hy = kick2(c1, v.y, d1, f[3 * q + 1]),
+                    hz = kick2(c1, v.z, d1, f[3 * q + 2]);
         T.dvh[k] = make_float4(hx, hy, hz, 0.f);
         const float4 x = T.dx[k];
-        T.dx[k] = make_float4(x.x + t * hx, x.y + t * hy, x.z + t * hz, 0.f);
+        T.dx[k] = make_float4(drift1(x.x, t, hx), drift1(x.y, t, hy), drift1(x.z, t, hz), 0.f);
     }
 }
 
@@ -308,8 +308,8 @@ __global__ void tan_step_kernel(const float4 *__restrict__ part, ForceLaunch L, 
         if (b >= T.B) break;
         const long long k = b * n_pad + i;
         const float4 h = T.dvh[k];
-        const float vx = c2 * h.x + d2 * f[3 * q], vy = c2 * h.y + d2 * f[3 * q + 1],
-                    vz = c2 * h.z + d2 * f[3 * q + 2];
+        const float vx = kick2(c2, h.x, d2, f[3 * q]), vy = kick2(c2, h.y, d2, f[3 * q + 1]),
+                    vz = kick2(c2, h.z, d2, f[3 * q + 2]);
         const float4 x = T.dx[k];
         T.dv[k] = make_float4(vx, vy, vz, 0.f);
         if (T.seeds[b] == i && T.cap > 0) {
@@ -317,10 +317,10 @@ __global__ void tan_step_kernel(const float4 *__restrict__ part, ForceLaunch L, 
             T.growth[r * T.B + b] =
                 sqrtf(x.x * x.x + x.y * x.y + x.z * x.z + vx * vx + vy * vy + vz * vz);
         }
-        const float nx = c1n * vx + d1n * f[3 * q], ny = c1n * vy + d1n * f[3 * q + 1],
-                    nz = c1n * vz + d1n * f[3 * q + 2];
+        const float nx = kick2(c1n, vx, d1n, f[3 * q]), ny = kick2(c1n, vy, d1n, f[3 * q + 1]),
+                    nz = kick2(c1n, vz, d1n, f[3 * q + 2]);
         T.dvh[k] = make_float4(nx, ny, nz, 0.f);
-        T.dx[k] = make_float4(x.x + t * nx, x.y + t * ny, x.z + t * nz, 0.f);
+        T.dx[k] = make_float4(drift1(x.x, t, nx), drift1(x.y, t, ny), drift1(x.z, t, nz), 0.f);
     }
 }
 
