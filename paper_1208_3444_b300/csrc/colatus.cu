@@ -1503,6 +1503,7 @@ colatus_status colatus_wait_state(colatus_t ctx) {
 }
 
 colatus_status colatus_forces(colatus_t ctx, void *acc_out, int dtype, int on_device) {
+    NvtxRange nvtx_("colatus_forces");
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
     TRY(check_dtype(ctx, dtype));
@@ -1521,6 +1522,7 @@ colatus_status colatus_forces(colatus_t ctx, void *acc_out, int dtype, int on_de
 }
 
 colatus_status colatus_step(colatus_t ctx, double dt, int64_t nsteps) {
+    NvtxRange nvtx_("colatus_step");
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, COLATUS_E_ARG, "dt must be finite and > 0");
@@ -1616,6 +1618,7 @@ colatus_status colatus_read_tracers(colatus_t ctx, float *xv_out, int64_t *nrec_
 }
 
 colatus_status colatus_diagnostics(colatus_t ctx, double out[COLATUS_NDIAG]) {
+    NvtxRange nvtx_("colatus_diagnostics");
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
     if (!out) return fail(ctx, COLATUS_E_ARG, "out is NULL");
@@ -1675,6 +1678,7 @@ colatus_status colatus_profile_read(colatus_t ctx, double out[4]) {
 
 colatus_status colatus_force_vjp(colatus_t ctx, const void *w, void *gx, void *gm, int dtype,
                                  int on_device) {
+    NvtxRange nvtx_("colatus_force_vjp");
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
     if (ctx->periodic) return fail(ctx, COLATUS_E_STATE, "%s is not built for periodic boundaries", "the force VJP");
@@ -1734,6 +1738,7 @@ colatus_status colatus_force_vjp(colatus_t ctx, const void *w, void *gx, void *g
 
 colatus_status colatus_adjoint_forward(colatus_t ctx, double dt, int64_t nsteps,
                                        int64_t checkpoint_every) {
+    NvtxRange nvtx_("colatus_adjoint_forward");
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
     if (ctx->periodic) return fail(ctx, COLATUS_E_STATE, "%s is not built for periodic boundaries", "the adjoint");
@@ -1800,6 +1805,7 @@ colatus_status colatus_adjoint_forward(colatus_t ctx, double dt, int64_t nsteps,
 colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const void *gv_T,
                                         const void *gm_T, void *gx_0, void *gv_0, void *gm,
                                         int dtype, int on_device) {
+    NvtxRange nvtx_("colatus_adjoint_backward");
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
     TRY(check_dtype(ctx, dtype));
@@ -2035,6 +2041,7 @@ colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, 
 }
 
 colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps) {
+    NvtxRange nvtx_("colatus_tangent_step");
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
     if (ctx->periodic) return fail(ctx, COLATUS_E_STATE, "%s is not built for periodic boundaries", "the tangent model");

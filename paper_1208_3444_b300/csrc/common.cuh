@@ -5,8 +5,19 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace colatus {
+
+// Host-side NVTX range over one library call, for profiler timelines and for
+// ncu's --nvtx filters (header-only NVTX: a no-op without a tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 
 // Device error flags (one int each, OR-ed by kernels, read by the host).
 enum DevFlag : int { FLAG_NONFINITE = 0, FLAG_FRIEDMANN = 1, FLAG_TIMEOUT = 2, NUM_FLAGS = 4 };

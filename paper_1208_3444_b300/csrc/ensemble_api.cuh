@@ -534,6 +534,7 @@ colatus_status colatus_ensemble_forces(colatus_ens_t e, void *acc_out, int dtype
 }
 
 colatus_status colatus_ensemble_step(colatus_ens_t e, double dt, int64_t nsteps) {
+    NvtxRange nvtx_("colatus_ensemble_step");
     if (!e) return COLATUS_E_ARG;
     DeviceGuard dg(e->device);
     if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0)

@@ -75,6 +75,7 @@ colatus_status colatus_velocity_spectrum(const void *v, int dtype, int on_device
 
 colatus_status colatus_tracer_spectrum(colatus_t ctx, double dt, int window, int detrend,
                                        double *E_out, int64_t *nrec_out) {
+    NvtxRange nvtx_("colatus_tracer_spectrum");
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
     if (!nrec_out) return fail(ctx, COLATUS_E_ARG, "nrec_out is NULL");
