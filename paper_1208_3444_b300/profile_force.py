@@ -5,11 +5,13 @@ with ncu.
     python -m paper_1208_3444_b300.profile_force --op vjp --workload grid32 --launches 1
     python -m paper_1208_3444_b300.profile_force --periodic 1.0 --workload grid32 --launches 1
     python -m paper_1208_3444_b300.profile_force --op jvp --workload grid32 --launches 1
+    python -m paper_1208_3444_b300.profile_force --op ensemble --launches 1
 
 --op force runs colatus_forces (the force kernel, or with --periodic L the
 Ewald real-space and k-space kernels); --op vjp runs colatus_force_vjp with a
 seeded co-vector; --op jvp runs tangent steps of 64 single-tracer tangents
-(one JVP launch each).  Prints the CUDA-event duration of the force or VJP
+(one JVP launch each); --op ensemble runs force evaluations of the
+64-realisation ensemble (--workload is ignored).  Prints the CUDA-event duration of the force or VJP
 kernel (meaningless under a profiler, which serialises and replays kernels).
 """
 import argparse
@@ -47,9 +49,22 @@ def main():
                    help="grid16 | grid32 | uniform<N> | plummer<N>")
     p.add_argument("--prec", default="comp", choices=sorted(PRECS))
     p.add_argument("--launches", type=int, default=1)
-    p.add_argument("--op", default="force", choices=["force", "vjp", "jvp"])
+    p.add_argument("--op", default="force", choices=["force", "vjp", "jvp", "ensemble"])
     p.add_argument("--periodic", type=float, default=0.0, help="box side L (0: isolated)")
     a = p.parse_args()
+    if a.op == "ensemble":
+        ics = inputs.ensemble(64, seed=5)
+        ens = B.Ensemble(np.array([c.N for c in ics]), np.concatenate([c.m for c in ics]),
+                         [c.eps for c in ics], LCDM, 1.0)
+        try:
+            ens.set_state(np.concatenate([c.x for c in ics]), np.concatenate([c.v for c in ics]))
+            for _ in range(a.launches):
+                ens.forces()
+            ens.synchronize()
+        finally:
+            ens.close()
+        print(f"ensemble: 64 realisations, {a.launches} force evaluations")
+        return
     ic = workload(a.workload)
     sim = B.Simulation(ic.m, ic.eps, LCDM, 1.0, prec=PRECS[a.prec])
     try:
