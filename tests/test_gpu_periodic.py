@@ -181,3 +181,20 @@ def test_periodic_forces_are_deterministic(prec):
         assert all(np.array_equal(first, sim.forces()) for _ in range(3))
     finally:
         sim.close()
+
+
+def test_extreme_k_space_sizes():
+    # nk = 63 is the largest the k-space kernels' shared memory allows (a
+    # superset of the converged sum, so the result matches the oracle); nk = 1
+    # leaves a single shell of k-vectors (a truncated sum: finite, and different).
+    rng = np.random.default_rng(815)
+    x, m = inputs.f32(rng.random((3000, 3))), inputs.f32(rng.random(3000) / 3000)
+    ref = oracle.ewald_forces(x, m, 0.01, 1.0)
+    big, p = periodic_forces(x, m, 0.01, 1.0, B.FP32, alpha=9.0, nk=63)
+    assert p["nk"] == 63 and p["nkv"] > 500000
+    assert rel_rms(big, ref) < 1e-5
+    small, p = periodic_forces(x, m, 0.01, 1.0, B.FP32, alpha=9.0, nk=1)
+    assert p["nkv"] == 3 and np.all(np.isfinite(small))
+    assert rel_rms(small, ref) > 1e-3
+    with pytest.raises(B.ColatusError):
+        periodic_forces(x, m, 0.01, 1.0, B.FP32, alpha=9.0, nk=64)
