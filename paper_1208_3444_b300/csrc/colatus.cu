@@ -2014,7 +2014,7 @@ colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, 
     t.plan.itile = JvpK::ITILE;
     t.plan.jt = kJvpJT;
     t.plan.n_pad = t.n_pad;
-    t.plan.part_bytes = (size_t)t.nchunk * t.plan.L.n_it * t.plan.L.S_max * 3 * JvpK::ITILE *
+    t.plan.part_bytes = (size_t)t.nchunk * t.plan.L.n_it * t.plan.L.S_max * kTPlanes * JvpK::ITILE *
                         sizeof(float4);
     const size_t tb = (size_t)B * t.n_pad * sizeof(float4);
     CU(cudaMalloc(&t.dx, tb));

@@ -21,12 +21,15 @@
 
 namespace colatus {
 
-constexpr int kTB = 4;   // tangents per chunk
+constexpr int kTB = 4;              // tangents per chunk
+constexpr int kTC = 3 * kTB;        // tangent components per body and chunk
+constexpr int kTPlanes = kTC / 4;   // float4 planes per body in the segments
+static_assert(kTC % 4 == 0, "segments hold whole float4 planes");
 
 template <int NT, int IPT, int JT, int STAGES>
 struct JvpKernel {
     static constexpr int ITILE = NT * IPT;
-    static constexpr uint32_t TILE_BYTES = JT * 64;
+    static constexpr uint32_t TILE_BYTES = JT * (4 + kTC) * 4;   // (x, y, z, m) + tangents
     static constexpr int SMEM = STAGES * TILE_BYTES + STAGES * 8;
 };
 
@@ -118,7 +121,7 @@ __global__ void __launch_bounds__(NT, MINB)
                     float2 v[kPktSlots];
 #pragma unroll
                     for (int f = 0; f < kPktSlots / 2; ++f) {
-                        const float4 F = tl[8 * q + f];
+                        const float4 F = tl[(kPktSlots / 2) * q + f];
                         v[2 * f] = make_float2(F.x, F.y);
                         v[2 * f + 1] = make_float2(F.z, F.w);
                     }
@@ -166,16 +169,16 @@ __global__ void __launch_bounds__(NT, MINB)
         }
         if (bad) break;
         const long long sidx = g - sk_owner(ct * per_it, W, G);
-        float4 *dst = part + (ct * L.S_max + sidx) * 3LL * K::ITILE;
+        float4 *dst = part + (ct * L.S_max + sidx) * (long long)kTPlanes * K::ITILE;
 #pragma unroll
         for (int k = 0; k < IPT; ++k) {
             const int il = tid + k * NT;
-            float a[3 * kTB];
+            float a[kTC];
 #pragma unroll
-            for (int c = 0; c < 3 * kTB; ++c) a[c] = ac[k][c].x + ac[k][c].y;
-            dst[il] = make_float4(a[0], a[1], a[2], a[3]);
-            dst[K::ITILE + il] = make_float4(a[4], a[5], a[6], a[7]);
-            dst[2 * K::ITILE + il] = make_float4(a[8], a[9], a[10], a[11]);
+            for (int c = 0; c < kTC; ++c) a[c] = ac[k][c].x + ac[k][c].y;
+#pragma unroll
+            for (int pl = 0; pl < kTPlanes; ++pl)
+                dst[pl * K::ITILE + il] = make_float4(a[4 * pl], a[4 * pl + 1], a[4 * pl + 2], a[4 * pl + 3]);
         }
     }
     if (bad && tid == 0) {
@@ -192,20 +195,23 @@ __global__ void __launch_bounds__(NT, MINB)
 
 // Sum the segments of (chunk, body i): the TB force perturbations.
 __device__ __forceinline__ void jvp_reduce(const float4 *__restrict__ part, const ForceLaunch &L,
-                                           int itile, long long chunk, long long i, float (&f)[12]) {
+                                           int itile, long long chunk, long long i, float (&f)[kTC]) {
     const long long it = i / itile, il = i - it * itile;
     const long long ct = chunk * L.n_it + it;
     const long long g0 = sk_owner(ct * L.n_jt, L.W, L.G);
     const long long g1 = sk_owner((ct + 1) * L.n_jt - 1, L.W, L.G);
-    const float4 *p = part + ct * L.S_max * 3LL * itile + il;
+    const float4 *p = part + ct * L.S_max * (long long)kTPlanes * itile + il;
 #pragma unroll
-    for (int c = 0; c < 12; ++c) f[c] = 0.f;
+    for (int c = 0; c < kTC; ++c) f[c] = 0.f;
     for (long long s = 0; s <= g1 - g0; ++s) {
-        const float4 a = __ldg(p + (3 * s) * itile), b = __ldg(p + (3 * s + 1) * itile),
-                     c = __ldg(p + (3 * s + 2) * itile);
-        const float v[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
 #pragma unroll
-        for (int q = 0; q < 12; ++q) f[q] += v[q];
+        for (int pl = 0; pl < kTPlanes; ++pl) {
+            const float4 a = __ldg(p + (kTPlanes * s + pl) * itile);
+            f[4 * pl] += a.x;
+            f[4 * pl + 1] += a.y;
+            f[4 * pl + 2] += a.z;
+            f[4 * pl + 3] += a.w;
+        }
     }
 }
 
@@ -227,7 +233,7 @@ __global__ void tan_pack_kernel(const float *__restrict__ pk, TangentState T, lo
     const int chunk = blockIdx.y;
     if (i >= n_pad) return;
     const float4 x = pk_load(pk, i);
-    float t[12];
+    float t[kTC];
 #pragma unroll
     for (int q = 0; q < kTB; ++q) {
         const long long b = (long long)chunk * kTB + q;
@@ -249,7 +255,7 @@ __global__ void tan_pack_kernel(const float *__restrict__ pk, TangentState T, lo
 // Opening of the tangent: dvh = c1 dv + d1 dF(x^n);  dx' = dx + tau dvh.
 // Deformation term's tangent at the packed position of (chunk, i).
 __device__ __forceinline__ void tan_defo(const TangentState &T, const Extra &D, int chunk,
-                                         long long i, long long n_pad, float (&f)[12]) {
+                                         long long i, long long n_pad, float (&f)[kTC]) {
     if (!D.on) return;
     const float *x = pkt_body(T.pkt, chunk, n_pad, i);
 #pragma unroll
@@ -267,7 +273,7 @@ __global__ void tan_open_kernel(const float4 *__restrict__ part, ForceLaunch L, 
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int chunk = blockIdx.y;
     if (i >= N) return;
-    float f[12];
+    float f[kTC];
     jvp_reduce(part, L, itile, chunk, i, f);
     tan_defo(T, D, chunk, i, n_pad, f);
     const StepCoef &e = table[step % tcap];
@@ -295,7 +301,7 @@ __global__ void tan_step_kernel(const float4 *__restrict__ part, ForceLaunch L, 
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int chunk = blockIdx.y;
     if (i >= N) return;
-    float f[12];
+    float f[kTC];
     jvp_reduce(part, L, itile, chunk, i, f);
     tan_defo(T, D, chunk, i, n_pad, f);
     const StepCoef &e = table[step % tcap];
