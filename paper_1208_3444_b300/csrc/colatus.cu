@@ -94,7 +94,7 @@ using Vjp64K = Vjp64Kernel<kV64NT, kV64JT, kStages>;
 // JVP (tangent) kernel: 128 threads x 2 i-bodies, 128-body j-tiles of 64 B,
 // j-loop unrolled by 4 (fastest of eight shapes timed on B300 at 32^3 with
 // 64 tangents: 38.6 ms per step, 13 % less than without unrolling)
-constexpr int kJvpNT = 256, kJvpIPT = 2, kJvpJT = 128, kJvpMINB = 1, kJvpUnr = 4;
+constexpr int kJvpNT = 256, kJvpIPT = 1, kJvpJT = 128, kJvpMINB = 1, kJvpUnr = 4;
 using JvpK = JvpKernel<kJvpNT, kJvpIPT, kJvpJT, kStages>;
 
 // Periodic (Ewald) real-space kernels: FP32 256 threads x 2 i-bodies,
@@ -1990,6 +1990,9 @@ colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, 
         if (p) cudaFree(p);
     t = colatus_ctx::Tangent();
     int occ = 0;
+    if (JvpK::SMEM > 48 * 1024)
+        CU(cudaFuncSetAttribute(jvp_f32x2_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kJvpMINB, kJvpUnr>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, JvpK::SMEM));
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &occ, jvp_f32x2_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kJvpMINB, kJvpUnr>, kJvpNT, JvpK::SMEM));
     if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "JVP kernel cannot be resident");

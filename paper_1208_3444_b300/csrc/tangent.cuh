@@ -21,7 +21,7 @@
 
 namespace colatus {
 
-constexpr int kTB = 4;              // tangents per chunk
+constexpr int kTB = 8;              // tangents per chunk
 constexpr int kTC = 3 * kTB;        // tangent components per body and chunk
 constexpr int kTPlanes = kTC / 4;   // float4 planes per body in the segments
 static_assert(kTC % 4 == 0, "segments hold whole float4 planes");
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(NT, MINB)
                      ForceLaunch L, long long n_pad, float eps2) {
     using K = JvpKernel<NT, IPT, JT, STAGES>;
     static_assert(JT % 2 == 0, "pairs of j-bodies");
-    constexpr int TILE_F4 = JT * 4;   // float4 per tile
+    constexpr int TILE_F4 = K::TILE_BYTES / 16;   // float4 per tile
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *tiles = reinterpret_cast<float4 *>(smem);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * K::TILE_BYTES);
