@@ -12,7 +12,7 @@
 //
 // Same stream-K decomposition and bulk-copy pipeline as force.cuh, over
 // (tangent chunk, i-tile, j-tile) units.  Per body and chunk the packed tile
-// holds (x, y, z, m) and TB tangent positions: 64 B for TB = 4.
+// holds (x, y, z, m) and TB tangent positions: 16 + 12 TB bytes (112 B for TB = 8).
 #pragma once
 
 #include "common.cuh"
@@ -39,10 +39,10 @@ struct JvpKernel {
 // bodies (2p, 2p + 1) and chunk, 32 floats
 //     [x0 x1 y0 y1 | z0 z1 m0 m1 | t0x0 t0x1 t0y0 t0y1 | t0z0 t0z1 t1x0 t1x1 | ...]
 // i.e. slot s of body i at float 2 s + (i & 1), slots x, y, z, m, then the TB
-// tangent positions (x, y, z) in order; a j-tile of JT bodies is JT * 64 B.
+// tangent positions (x, y, z) in order; a j-tile of JT bodies is JT * (16 + 12 TB) B.
 // Units: chunk-major, then i-tile, then j-tile (W = nchunk * n_it * n_jt);
 // part: [nchunk * n_it][S_max][3][ITILE] float4.
-constexpr int kPktSlots = 4 + 3 * kTB;   // 16
+constexpr int kPktSlots = 4 + 3 * kTB;   // 28 for TB = 8
 
 __device__ __forceinline__ float *pkt_body(float *pkt, long long chunk, long long n_pad, long long i) {
     return pkt + (chunk * n_pad + (i & ~1LL)) * kPktSlots + (i & 1);
