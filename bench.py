@@ -369,6 +369,40 @@ def time_tangent(B, inputs, torch, stream, ntr=64, nsteps=2):
             "finite": bool(np.all(np.isfinite(growth)))}
 
 
+def time_paper_run(B, inputs, torch, stream, nsteps=2000):
+    """The whole paper-scale run as one call: 32^3 from a = 1/51 to a = 1 in
+    2000 KDK steps (FP32 compensated forces, FP64 a(t)), 64 tracers recorded
+    every step, then their velocity energy spectra and the diagnostics."""
+    ic = inputs.grid32()
+    tau = inputs.lcdm_tau(nsteps)
+    sim = B.Simulation(ic.m, ic.eps, LCDM, inputs.A_START, prec=B.FP32_COMP, scheme=B.KDK,
+                       stream=stream.cuda_stream)
+    try:
+        sim.set_state(ic.x, ic.v)
+        sim.record_tracers(inputs.tracers(ic.N, 64, 7), nsteps)
+        sim.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        t0 = time.perf_counter()
+        ev[0].record(stream)
+        sim.step(tau, nsteps)
+        ev[1].record(stream)
+        spec = sim.tracer_spectrum(tau, "hann")
+        ev[2].record(stream)
+        diag = sim.diagnostics()
+        wall = time.perf_counter() - t0
+        _, _, t, a = sim.state()
+    finally:
+        sim.close()
+    steps_ms = ev[0].elapsed_time(ev[1])
+    return {"N": ic.N, "steps": nsteps, "a_final": a, "t_final": t,
+            "steps_ms": steps_ms, "steps_per_s": nsteps / (steps_ms * 1e-3),
+            "spectrum_ms": ev[1].elapsed_time(ev[2]), "spectrum_shape": list(spec.shape),
+            "wall_s_with_readback": wall, "finite": bool(np.isfinite(diag["K"])),
+            "what": "one colatus_step call of 2000 steps, then colatus_tracer_spectrum and "
+                    "colatus_diagnostics; the paper's only run was this size on a GTX680, "
+                    "with no time reported"}
+
+
 def time_periodic(B, inputs, torch, stream, nsteps=10):
     """Periodic boundaries (Ewald summation) on the 32^3 workload, FP32
     compensated KDK: per step the real-space all-pairs kernel (minimum images),
@@ -491,6 +525,7 @@ def run_colatus(args, ws, rank, local):
     ensemble = time_ensemble(B, inputs, torch, stream)
     tangent = time_tangent(B, inputs, torch, stream)
     periodic = time_periodic(B, inputs, torch, stream)
+    paper_run = time_paper_run(B, inputs, torch, stream)
     pipes = B.colatus_probe_pipes()
     if rank == 0:
         peaks = {}
@@ -535,6 +570,7 @@ def run_colatus(args, ws, rank, local):
             "ensemble": ensemble,
             "tangent": tangent,
             "periodic": periodic,
+            "paper_run": paper_run,
             "pipe_rates": {**pipes, "unit": "lane-ops (MUFU: results) per SM per clock",
                            "what": "colatus_probe_pipes: independent chains of FFMA, FFMA2 "
                                    "(f32x2), MUFU.RSQ"},
