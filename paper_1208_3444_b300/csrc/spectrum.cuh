@@ -10,11 +10,21 @@
 //     E_k(f_j) = c_j dt / (T U) * 1/2 sum_c |sum_n w_n u_{n,k,c} exp(-2 pi i j n / T)|^2,
 // j = 0 .. T/2, c_j = 2 except for j = 0 and j = T/2 (T even).
 //
-// One block per (tracer, chunk of 256 frequencies); the block stages the
-// windowed series in shared memory, 512 samples at a time, and every thread
-// accumulates one frequency in FP64.  The twiddle of (j, n) is the table entry
-// (j n mod T), so the angle is reduced exactly before any rounding.
+// Two kernels compute the same sums, both in FP64 with every twiddle angle
+// reduced exactly (table entry (e mod T) of exp(2 pi i e / T)):
+//
+// * spectrum_fft_kernel, for T <= kSpecFftMaxT whose prime factors are all
+//   <= kSpecFftMaxP: a mixed-radix Stockham FFT in shared memory, O(T sum p)
+//   multiply-adds.  A cluster of two CTAs per tracer: CTA 0 transforms the
+//   complex series u_x + i u_y, CTA 1 the series u_z; the sum over components
+//   of the real series' power is (|Z_j|^2 + |Z_{T-j}|^2) / 2 for either, and
+//   CTA 0 reads CTA 1's transform through distributed shared memory.
+// * spectrum_kernel otherwise: the direct sum, one block per (tracer, chunk
+//   of 256 frequencies); the block stages the windowed series in shared
+//   memory, 512 samples at a time, and every thread accumulates one frequency.
 #pragma once
+
+#include <cooperative_groups.h>
 
 #include "common.cuh"
 
@@ -22,6 +32,15 @@ namespace colatus {
 
 constexpr int kSpecThreads = 256;
 constexpr int kSpecChunk = 512;
+constexpr int kSpecFftMaxT = 6144;       // two complex FP64 buffers of T: 192 KB of shared memory
+constexpr int kSpecFftMaxP = 64;         // largest radix taken as one stage
+constexpr int kSpecFftMaxStages = 16;    // 4^6 > kSpecFftMaxT, so at most 13 factors
+
+// Radices of the FFT stages, in order (T = p[0] p[1] ... p[nst-1]).
+struct SpecPlan {
+    int nst;
+    int p[kSpecFftMaxStages];
+};
 
 struct SpecSeries {
     const void *base;          // first velocity component of row 0, tracer 0
@@ -41,8 +60,10 @@ __global__ void spectrum_twiddle_kernel(double2 *tw, long long T) {
     tw[m] = make_double2(c, s);
 }
 
+// Requires 0 <= first < cap and n < T <= cap, so first + n < 2 cap.
 __device__ __forceinline__ double spec_load(const SpecSeries &S, long long n, long long k, int c) {
-    const long long r = (S.first + n) % S.cap;
+    long long r = S.first + n;
+    if (r >= S.cap) r -= S.cap;
     const long long off = r * S.row_stride + k * S.tr_stride + c;
     return S.f64 ? static_cast<const double *>(S.base)[off]
                  : (double)static_cast<const float *>(S.base)[off];
@@ -131,6 +152,101 @@ spectrum_kernel(SpecSeries S, const double2 *__restrict__ tw, double dt, int win
                          re[2] * re[2] + im[2] * im[2];
         E[k * nf + j] = cj * dt / ((double)T * U) * 0.5 * p;
     }
+}
+
+// Stockham stage of radix p over N = T points: with L the length of the
+// transforms done so far and m = N / (p L), the input holds the L-point
+// transforms Y_r (r < p m) at [r L, r L + L), and output o = k p L + j'
+// (k < m, j' < p L) is the p L-point transform
+//     Z_k[j'] = sum_q exp(-2 pi i q m j' / N) Y_{k + m q}[j' mod L].
+// The exponent q m j' is advanced by m j' < N and reduced by one subtraction.
+__device__ __forceinline__ void spec_fft_stage(const double2 *__restrict__ src,
+                                               double2 *__restrict__ dst,
+                                               const double2 *__restrict__ tw, int N, int p, int L) {
+    const int pL = p * L, m = N / pL;
+    for (int o = threadIdx.x; o < N; o += kSpecThreads) {
+        const int kk = o / pL, jp = o - kk * pL, j = jp % L;
+        const int de = m * jp;
+        const double2 *y = src + kk * L + j;
+        double re = 0.0, im = 0.0;
+        int e = 0;
+        for (int q = 0; q < p; ++q) {
+            const double2 c = __ldg(&tw[e]);
+            const double2 v = y[q * m * L];
+            // v (cos - i sin)
+            re = fma(v.x, c.x, re);
+            re = fma(v.y, c.y, re);
+            im = fma(v.y, c.x, im);
+            im = fma(-v.x, c.y, im);
+            e += de;
+            if (e >= N) e -= N;
+        }
+        dst[o] = make_double2(re, im);
+    }
+}
+
+// Grid (ntr, 2), clusters of (1, 2): block rank 0 transforms u_x + i u_y and
+// writes E, block rank 1 transforms u_z.  Dynamic shared memory: 2 T double2.
+__global__ void __cluster_dims__(1, 2, 1) __launch_bounds__(kSpecThreads)
+spectrum_fft_kernel(SpecSeries S, const double2 *__restrict__ tw, SpecPlan plan, double dt,
+                    int window, int detrend, double *__restrict__ E) {
+    extern __shared__ double2 spec_buf[];
+    __shared__ double red[(kSpecThreads / 32) * 4];
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int s = (int)cluster.block_rank();
+    const long long k = blockIdx.x;
+    const int N = (int)S.T;
+    const long long nf = N / 2 + 1;
+    const int c0 = s == 0 ? 0 : 2;
+
+    // means of this block's components and the window's mean square U
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int n = threadIdx.x; n < N; n += kSpecThreads) {
+        const double w = spec_window(tw, n, window);
+        if (detrend) {
+            acc[0] += spec_load(S, n, k, c0);
+            if (s == 0) acc[1] += spec_load(S, n, k, 1);
+        }
+        acc[3] += w * w;
+    }
+    spec_block_sum4(acc, red);
+    const double inv_T = 1.0 / (double)N;
+    const double m0 = acc[0] * inv_T, m1 = acc[1] * inv_T, U = acc[3] * inv_T;
+
+    double2 *src = spec_buf, *dst = spec_buf + N;
+    for (int n = threadIdx.x; n < N; n += kSpecThreads) {
+        const double w = spec_window(tw, n, window);
+        src[n] = make_double2(w * (spec_load(S, n, k, c0) - m0),
+                              s == 0 ? w * (spec_load(S, n, k, 1) - m1) : 0.0);
+    }
+    __syncthreads();
+    int L = 1;
+    for (int st = 0; st < plan.nst; ++st) {
+        spec_fft_stage(src, dst, tw, N, plan.p[st], L);
+        __syncthreads();
+        double2 *t = src;
+        src = dst;
+        dst = t;
+        L *= plan.p[st];
+    }
+
+    // both transforms complete; block 0 reads block 1's through DSMEM
+    cluster.sync();
+    if (s == 0) {
+        const double2 *z = cluster.map_shared_rank(src, 1);
+        const double scale = dt / ((double)N * U) * 0.5 * 0.5;
+        for (int j = threadIdx.x; j < nf; j += kSpecThreads) {
+            const int jm = j == 0 ? 0 : N - j;
+            const double2 a = src[j], b = src[jm], c = z[j], d = z[jm];
+            const double pxy = a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y;
+            const double pz = c.x * c.x + c.y * c.y + d.x * d.x + d.y * d.y;
+            const double cj = (j == 0 || 2 * j == N) ? 1.0 : 2.0;
+            E[k * nf + j] = cj * scale * (pxy + pz);
+        }
+    }
+    // block 1's shared memory stays alive until block 0 has read it
+    cluster.sync();
 }
 
 }  // namespace colatus

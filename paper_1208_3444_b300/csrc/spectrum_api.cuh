@@ -15,14 +15,43 @@ colatus_status spec_check(colatus_t ctx, long long T, long long ntr, double dt, 
     return COLATUS_OK;
 }
 
+// FFT stages for T: radix 4 while it divides, then 2, then the odd primes in
+// increasing order.  False if T is too long for shared memory or has a prime
+// factor above kSpecFftMaxP (the direct sum is taken then).
+bool spec_plan(long long T, SpecPlan &plan) {
+    plan.nst = 0;
+    if (T > kSpecFftMaxT) return false;
+    long long n = T;
+    auto take = [&](int p) {
+        while (n % p == 0 && plan.nst < kSpecFftMaxStages) {
+            plan.p[plan.nst++] = p;
+            n /= p;
+        }
+    };
+    take(4);
+    take(2);
+    for (int p = 3; p <= kSpecFftMaxP && n > 1; p += 2) take(p);
+    return n == 1;
+}
+
 // Twiddles into tw (T double2), then E (device, ntr x (T/2+1) doubles).
 colatus_status spec_launch(colatus_t ctx, const SpecSeries &S, double2 *tw, double dt, int window,
                            int detrend, double *E, cudaStream_t stream) {
     spectrum_twiddle_kernel<<<blocks_for(S.T, 256), 256, 0, stream>>>(tw, S.T);
     CU(cudaGetLastError());
-    const long long nf = S.T / 2 + 1;
-    const dim3 grid((unsigned)S.ntr, blocks_for(nf, kSpecThreads));
-    spectrum_kernel<<<grid, kSpecThreads, 0, stream>>>(S, tw, dt, window, detrend ? 1 : 0, E);
+    SpecPlan plan;
+    if (spec_plan(S.T, plan)) {
+        const size_t smem = 2 * (size_t)S.T * sizeof(double2);
+        CU(cudaFuncSetAttribute(spectrum_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+        const dim3 grid((unsigned)S.ntr, 2);
+        spectrum_fft_kernel<<<grid, kSpecThreads, smem, stream>>>(S, tw, plan, dt, window,
+                                                                  detrend ? 1 : 0, E);
+    } else {
+        const long long nf = S.T / 2 + 1;
+        const dim3 grid((unsigned)S.ntr, blocks_for(nf, kSpecThreads));
+        spectrum_kernel<<<grid, kSpecThreads, 0, stream>>>(S, tw, dt, window, detrend ? 1 : 0, E);
+    }
     CU(cudaGetLastError());
     if (ctx) ctx->launches += 2;
     return COLATUS_OK;

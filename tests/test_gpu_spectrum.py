@@ -1,5 +1,10 @@
 """GPU parity of the tracer velocity energy spectrum against the oracle's
-direct DFT (both in FP64; the GPU sums in another order)."""
+direct DFT (both in FP64; the GPU sums in another order).
+
+The library takes a mixed-radix FFT for T <= 6144 whose prime factors are
+all <= 64 and the direct sum otherwise; the lengths below cover both, the
+boundaries between them (6144, 6145, 6400; a radix-61 stage, a prime 67)
+and the paper's record length of 2000 steps for 64 tracers."""
 import numpy as np
 import pytest
 
@@ -28,7 +33,9 @@ def series(T, ntr, seed, dtype):
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 @pytest.mark.parametrize("window", ["rect", "hann"])
-@pytest.mark.parametrize("T,ntr", [(2, 1), (3, 5), (257, 64), (500, 7), (1041, 3), (4113, 2)])
+@pytest.mark.parametrize("T,ntr", [(2, 1), (3, 5), (257, 64), (500, 7), (1041, 3), (4113, 2),
+                                   (2000, 64), (4096, 3), (6144, 2), (6145, 1), (6400, 1),
+                                   (122, 4), (134, 3)])
 def test_random_series(T, ntr, window, dtype):
     v = series(T, ntr, T + ntr, dtype)
     for detrend in (True, False):
@@ -55,13 +62,15 @@ def test_device_tensors_and_record_layout():
     assert close(r6, ref)
 
 
-def test_recorded_tracers_in_the_ring():
+@pytest.mark.parametrize("cap", [24, 23])
+def test_recorded_tracers_in_the_ring(cap):
+    # 24 records take the FFT, 23 (prime) the direct sum
     ic = inputs.grid16(critical=True)
     tr = inputs.tracers(ic.N, 64, 3)
     sim = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START, prec=B.FP32)
     try:
         sim.set_state(ic.x, ic.v)
-        sim.record_tracers(tr, 24)          # 40 steps: the ring wraps, the last 24 are kept
+        sim.record_tracers(tr, cap)         # 40 steps: the ring wraps, the last cap are kept
         sim.step(TAU, 15)
         sim.step(TAU, 25)
         rec = sim.read_tracers()
@@ -69,7 +78,7 @@ def test_recorded_tracers_in_the_ring():
         E_rect = sim.tracer_spectrum(TAU, "rect", detrend=False)
     finally:
         sim.close()
-    assert rec.shape == (24, 64, 6)
+    assert rec.shape == (cap, 64, 6)
     v = rec[:, :, 3:].astype(np.float64)
     assert close(E, oracle.velocity_spectrum(v, TAU, "hann"))
     assert close(E_rect, oracle.velocity_spectrum(v, TAU, "rect", detrend=False))
