@@ -410,6 +410,41 @@ def time_paper_run(B, inputs, torch, stream, nsteps=2000):
                     "with no time reported"}
 
 
+def time_schemes(B, inputs, torch, stream, nsteps=50):
+    """The step variants on the 32^3 workload, FP32 compensated force, one
+    colatus_step call of nsteps after two warm-up steps (L2 not flushed; the
+    state is 1 MB): the paper's DKD (Eqs. 3-5), the drag KDK, the canonical
+    (symplectic) KDK of Sec. II, and the drag KDK with the Eq. 6 deformation
+    term.  All run the same force kernel; the variants differ in O(N) epilogue
+    work and in the FP64 schedule."""
+    ic = inputs.grid32()
+    tau = inputs.lcdm_tau(2000)
+    out = {}
+    for name, scheme, defo in (("dkd", B.DKD, False), ("kdk", B.KDK, False),
+                               ("kdk_canonical", B.KDK_CANONICAL, False),
+                               ("kdk_deformation", B.KDK, True)):
+        sim = B.Simulation(ic.m, ic.eps, LCDM, inputs.A_START, prec=B.FP32_COMP, scheme=scheme,
+                           stream=stream.cuda_stream)
+        try:
+            sim.set_state(ic.x, ic.v)
+            if defo:
+                sim.set_deformation(0.01 * float(np.sum(ic.m)), np.array([0.5, 0.5, 0.5]))
+            sim.step(tau, 2)
+            sim.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(tau, nsteps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        finally:
+            sim.close()
+        ms = e0.elapsed_time(e1) / nsteps
+        out[name] = {"ms_per_step": ms, "interactions_per_s": float(ic.N) * ic.N / (ms * 1e-3)}
+    out["what"] = (f"{nsteps} steps of 32^3 per variant in one colatus_step call, FP32 compensated, "
+                   "L2 not flushed")
+    return out
+
+
 def time_periodic(B, inputs, torch, stream, nsteps=10):
     """Periodic boundaries (Ewald summation) on the 32^3 workload, FP32
     compensated KDK: per step the real-space all-pairs kernel (minimum images),
@@ -532,6 +567,7 @@ def run_colatus(args, ws, rank, local):
     ensemble = time_ensemble(B, inputs, torch, stream)
     tangent = time_tangent(B, inputs, torch, stream)
     periodic = time_periodic(B, inputs, torch, stream)
+    schemes = time_schemes(B, inputs, torch, stream)
     paper_run = time_paper_run(B, inputs, torch, stream)
     pipes = B.colatus_probe_pipes()
     if rank == 0:
@@ -576,7 +612,7 @@ def run_colatus(args, ws, rank, local):
             "adjoint": adjoint,
             "ensemble": ensemble,
             "tangent": tangent,
-            "periodic": periodic,
+            "periodic": periodic, "schemes": schemes,
             "paper_run": paper_run,
             "pipe_rates": {**pipes, "unit": "lane-ops (MUFU: results) per SM per clock",
                            "what": "colatus_probe_pipes: independent chains of FFMA, FFMA2 "
