@@ -39,7 +39,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one launch of the 32^3 compensated force kernel,
 # force_f32_kernel<512, 4, 512, 4, 256, 1, 1, 1, 2>, from one ncu capture
 # (profiles/force_f32_comp_grid32.md); set to None when that kernel changes.
-FORCE_KERNEL_TRAFFIC = 540672
+FORCE_KERNEL_TRAFFIC = 540928
 
 
 def parse():

@@ -6,12 +6,15 @@ with ncu.
     python -m paper_1208_3444_b300.profile_force --periodic 1.0 --workload grid32 --launches 1
     python -m paper_1208_3444_b300.profile_force --op jvp --workload grid32 --launches 1
     python -m paper_1208_3444_b300.profile_force --op ensemble --launches 1
+    python -m paper_1208_3444_b300.profile_force --op spectrum --launches 1
 
 --op force runs colatus_forces (the force kernel, or with --periodic L the
 Ewald real-space and k-space kernels); --op vjp runs colatus_force_vjp with a
 seeded co-vector; --op jvp runs tangent steps of 64 single-tracer tangents
 (one JVP launch each); --op ensemble runs force evaluations of the
-64-realisation ensemble (--workload is ignored).  Prints the CUDA-event duration of the force or VJP
+64-realisation ensemble (--workload is ignored); --op spectrum runs
+colatus_velocity_spectrum on a seeded device series of 2000 records of 64
+tracers (Hann window, detrended; --workload is ignored).  Prints the CUDA-event duration of the force or VJP
 kernel (meaningless under a profiler, which serialises and replays kernels).
 """
 import argparse
@@ -49,7 +52,7 @@ def main():
                    help="grid16 | grid32 | uniform<N> | plummer<N>")
     p.add_argument("--prec", default="comp", choices=sorted(PRECS))
     p.add_argument("--launches", type=int, default=1)
-    p.add_argument("--op", default="force", choices=["force", "vjp", "jvp", "ensemble"])
+    p.add_argument("--op", default="force", choices=["force", "vjp", "jvp", "ensemble", "spectrum"])
     p.add_argument("--periodic", type=float, default=0.0, help="box side L (0: isolated)")
     a = p.parse_args()
     if a.op == "ensemble":
@@ -64,6 +67,16 @@ def main():
         finally:
             ens.close()
         print(f"ensemble: 64 realisations, {a.launches} force evaluations")
+        return
+    if a.op == "spectrum":
+        import torch
+        g = torch.Generator(device="cuda").manual_seed(11)
+        v = torch.randn((2000, 64, 3), device="cuda", dtype=torch.float32, generator=g)
+        out = torch.empty((64, 1001), device="cuda", dtype=torch.float64)
+        for _ in range(a.launches):
+            B.colatus_velocity_spectrum(v, inputs.lcdm_tau(2000), "hann", True, out=out)
+        torch.cuda.synchronize()
+        print(f"spectrum: T=2000, 64 tracers, {a.launches} calls")
         return
     ic = workload(a.workload)
     sim = B.Simulation(ic.m, ic.eps, LCDM, 1.0, prec=PRECS[a.prec])
