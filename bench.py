@@ -267,7 +267,7 @@ def time_adjoint(B, inputs, torch, stream, nsteps=200, k=20):
         sim.set_state(ic.x, ic.v)
         sim.step(tau, 3)
         sim.synchronize()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
         sim.profile_forces(True)
         ev[0].record(stream)
         sim.adjoint_forward(tau, nsteps, k)
@@ -381,7 +381,7 @@ def time_paper_run(B, inputs, torch, stream, nsteps=2000):
         sim.set_state(ic.x, ic.v)
         sim.record_tracers(inputs.tracers(ic.N, 64, 7), nsteps)
         sim.synchronize()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
         t0 = time.perf_counter()
         ev[0].record(stream)
         sim.step(tau, nsteps)
@@ -396,6 +396,11 @@ def time_paper_run(B, inputs, torch, stream, nsteps=2000):
         sim.tracer_spectrum(tau, "hann")
         ev[4].record(stream)
         stream.synchronize()
+        # a repeat of the diagnostics (O(N^2) potential energy, moments)
+        ev[5].record(stream)
+        sim.diagnostics()
+        ev[6].record(stream)
+        stream.synchronize()
         _, _, t, a = sim.state()
     finally:
         sim.close()
@@ -403,7 +408,7 @@ def time_paper_run(B, inputs, torch, stream, nsteps=2000):
     return {"N": ic.N, "steps": nsteps, "a_final": a, "t_final": t,
             "steps_ms": steps_ms, "steps_per_s": nsteps / (steps_ms * 1e-3),
             "spectrum_ms": ev[3].elapsed_time(ev[4]), "spectrum_first_call_ms": ev[1].elapsed_time(ev[2]),
-            "spectrum_shape": list(spec.shape),
+            "spectrum_shape": list(spec.shape), "diagnostics_ms": ev[5].elapsed_time(ev[6]),
             "wall_s_with_readback": wall, "finite": bool(np.isfinite(diag["K"])),
             "what": "one colatus_step call of 2000 steps, then colatus_tracer_spectrum and "
                     "colatus_diagnostics; the paper's only run was this size on a GTX680, "

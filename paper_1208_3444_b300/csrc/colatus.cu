@@ -253,6 +253,8 @@ struct colatus_ctx {
     double2 *rho = nullptr;
     void *rho_part = nullptr;               // [splits][nkv] partial structure factors
     size_t rho_part_bytes = 0;
+    void *pot_part = nullptr;               // [splits][N] potential pair sums (diagnostics)
+    size_t pot_part_bytes = 0;
     double2 *wcs = nullptr;                 // [nkv] (w C, w S) as float2 or double2
     KPencil *pen = nullptr;                 // k-vector pencils (runs of nz at fixed nx, ny)
     int *rchunk = nullptr, *fchunk = nullptr;   // first pencil of each k-space chunk (+ end)
@@ -830,7 +832,7 @@ void free_all(colatus_t ctx) {
                     ctx->pos64[2], ctx->m64, ctx->part, ctx->flags, ctx->mstat, ctx->clk,
                     ctx->tclk, ctx->table, ctx->stage, ctx->stage2, ctx->diag, ctx->tslot,
                     ctx->rec, ctx->kw, ctx->rho, ctx->rho_part, ctx->wcs, ctx->pen,
-                    ctx->rchunk, ctx->fchunk, ctx->lr, ctx->ph};
+                    ctx->rchunk, ctx->fchunk, ctx->lr, ctx->ph, ctx->pot_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *tptrs[] = {ctx->tan.dx, ctx->tan.dv, ctx->tan.dvh, ctx->tan.pkt, ctx->tan.seeds,
@@ -1627,8 +1629,35 @@ colatus_status colatus_diagnostics(colatus_t ctx, double out[COLATUS_NDIAG]) {
     const bool f64 = ctx->prec == COLATUS_FP64;
     CU(cudaMemsetAsync(ctx->diag, 0, kDiagSlots * sizeof(double), ctx->stream));
     const unsigned nb = (unsigned)std::min<long long>(blocks_for(ctx->N, kDiagThreads), 4L * ctx->num_sms);
-    potential_energy_kernel<<<nb, kDiagThreads, 0, ctx->stream>>>(
-        ctx->xs, ctx->xs64, f64 ? 1 : 0, ctx->N, ctx->eps * ctx->eps, ctx->diag);
+    // potential pair sums: i-tiles x source splits.  Blocks are equal work
+    // (tps source tiles), so the time goes as ceil(blocks / SMs) x tps; take
+    // the split with the least (fewer blocks on ties), at most 64 splits and
+    // at most 64 MB of per-split sums.
+    const long long n_ib = (ctx->N + kPotITILE - 1) / kPotITILE;
+    const long long n_jt = (ctx->N + kPotJT - 1) / kPotJT;
+    const long long max_sp = std::max(1LL, std::min({n_jt, 64LL, (8LL << 20) / ctx->N}));
+    long long tps = n_jt, best = -1;
+    for (long long sp = 1; sp <= max_sp; ++sp) {
+        const long long t = (n_jt + sp - 1) / sp, blocks = n_ib * ((n_jt + t - 1) / t);
+        const long long cost = (blocks + ctx->num_sms - 1) / ctx->num_sms * t;
+        if (best < 0 || cost < best) {
+            best = cost;
+            tps = t;
+        }
+    }
+    const int splits = (int)((n_jt + tps - 1) / tps);
+    TRY(grow(ctx, &ctx->pot_part, &ctx->pot_part_bytes, (size_t)splits * ctx->N * sizeof(double)));
+    double *pot_part = static_cast<double *>(ctx->pot_part);
+    const dim3 pgrid((unsigned)n_ib, (unsigned)splits);
+    if (f64)
+        potential_f64_kernel<<<pgrid, kDiagThreads, 0, ctx->stream>>>(
+            ctx->xs64, ctx->N, ctx->eps * ctx->eps, (int)tps, pot_part);
+    else
+        potential_f32_kernel<<<pgrid, kDiagThreads, 0, ctx->stream>>>(
+            ctx->xs, ctx->N, (float)(ctx->eps * ctx->eps), (int)tps, pot_part);
+    TRY(launched(ctx));
+    potential_sum_kernel<<<nb, kDiagThreads, 0, ctx->stream>>>(pot_part, splits, ctx->xs, ctx->xs64,
+                                                               f64 ? 1 : 0, ctx->N, ctx->diag);
     TRY(launched(ctx));
     moments_kernel<<<nb, kDiagThreads, 0, ctx->stream>>>(ctx->xs, ctx->vs, ctx->xs64, ctx->vs64,
                                                         f64 ? 1 : 0, ctx->N, ctx->diag);

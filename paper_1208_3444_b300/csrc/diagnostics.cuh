@@ -35,43 +35,134 @@ __device__ __forceinline__ void block_sum_to(double v, double *slot) {
     }
 }
 
-// sum_k m_k sum_{j != k} m_j / s_kj (the self pair is masked).  FP32 modes use
-// FP32 pair terms (refined rsqrt) summed in FP64 every 64 sources.
+// ------------------------------------------------------------- potential
+// W_x needs sum_k m_k sum_{j != k} m_j / s_kj.  The pair sums are tiled like
+// the force: a block takes kPotITILE target bodies (kPotIPT per thread) and
+// one split of the source tiles, staged kPotJT at a time in shared memory, and
+// writes its per-body sums to part[split][k]; potential_sum_kernel then adds
+// the splits in order and forms sum_k m_k (...).  The self pair is masked in
+// the tiles that contain it.  FP32 modes use FP32 pair terms (rsqrt refined by
+// one Newton step) summed 64 sources at a time, each partial added in FP64.
+constexpr int kPotIPT = 4;
+constexpr int kPotJT = 256;
+constexpr int kPotITILE = kDiagThreads * kPotIPT;
+constexpr int kPotChunk = 64;
+
+template <bool MASK>
+__device__ __forceinline__ void pot_f32_tile(const float4 *tile, long long j0, long long i0,
+                                             const float (&bx)[kPotIPT], const float (&by)[kPotIPT],
+                                             const float (&bz)[kPotIPT], float e2,
+                                             double (&s)[kPotIPT]) {
+    for (int q = 0; q < kPotJT; q += kPotChunk) {
+        float p[kPotIPT];
+#pragma unroll
+        for (int k = 0; k < kPotIPT; ++k) p[k] = 0.f;
+#pragma unroll 4
+        for (int jj = q; jj < q + kPotChunk; ++jj) {
+            const float4 c = tile[jj];
+#pragma unroll
+            for (int k = 0; k < kPotIPT; ++k) {
+                const float dx = c.x - bx[k], dy = c.y - by[k], dz = c.z - bz[k];
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2)));
+                float y = rsqrt_approx(r2);
+                y = y * fmaf(-0.5f * r2 * y, y, 1.5f);
+                const float w = MASK && j0 + jj == i0 + threadIdx.x + k * kDiagThreads ? 0.f : c.w;
+                p[k] = fmaf(w, y, p[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kPotIPT; ++k) s[k] += (double)p[k];
+    }
+}
+
+// Grid (ceil(N / kPotITILE), splits); split y covers source tiles
+// [y tps, (y + 1) tps).  Bodies past N (in the last tiles) have zero mass.
 __global__ void __launch_bounds__(kDiagThreads)
-    potential_energy_kernel(const float4 *__restrict__ xs, const double4 *__restrict__ xs64,
-                            int f64, long long N, double eps2, double *diag) {
+    potential_f32_kernel(const float4 *__restrict__ xs, long long N, float e2, int tps,
+                         double *__restrict__ part) {
+    __shared__ float4 tile[kPotJT];
+    const long long i0 = (long long)blockIdx.x * kPotITILE;
+    const long long n_jt = (N + kPotJT - 1) / kPotJT;
+    const long long jt0 = (long long)blockIdx.y * tps, jt1 = min(jt0 + tps, n_jt);
+    float bx[kPotIPT], by[kPotIPT], bz[kPotIPT];
+    double s[kPotIPT];
+#pragma unroll
+    for (int k = 0; k < kPotIPT; ++k) {
+        const long long i = i0 + threadIdx.x + k * kDiagThreads;
+        const float4 b = i < N ? xs[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        bx[k] = b.x;
+        by[k] = b.y;
+        bz[k] = b.z;
+        s[k] = 0.0;
+    }
+    for (long long jt = jt0; jt < jt1; ++jt) {
+        const long long j0 = jt * kPotJT, j = j0 + threadIdx.x;
+        __syncthreads();
+        tile[threadIdx.x] = j < N ? xs[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        if (j0 < i0 + kPotITILE && j0 + kPotJT > i0)
+            pot_f32_tile<true>(tile, j0, i0, bx, by, bz, e2, s);
+        else
+            pot_f32_tile<false>(tile, j0, i0, bx, by, bz, e2, s);
+    }
+#pragma unroll
+    for (int k = 0; k < kPotIPT; ++k) {
+        const long long i = i0 + threadIdx.x + k * kDiagThreads;
+        if (i < N) part[(long long)blockIdx.y * N + i] = s[k];
+    }
+}
+
+// The same in FP64 (library rsqrt, FP64 sums).
+__global__ void __launch_bounds__(kDiagThreads)
+    potential_f64_kernel(const double4 *__restrict__ xs, long long N, double e2, int tps,
+                         double *__restrict__ part) {
+    __shared__ double4 tile[kPotJT];
+    const long long i0 = (long long)blockIdx.x * kPotITILE;
+    const long long n_jt = (N + kPotJT - 1) / kPotJT;
+    const long long jt0 = (long long)blockIdx.y * tps, jt1 = min(jt0 + tps, n_jt);
+    double bx[kPotIPT], by[kPotIPT], bz[kPotIPT], s[kPotIPT];
+#pragma unroll
+    for (int k = 0; k < kPotIPT; ++k) {
+        const long long i = i0 + threadIdx.x + k * kDiagThreads;
+        const double4 b = i < N ? xs[i] : make_double4(0.0, 0.0, 0.0, 0.0);
+        bx[k] = b.x;
+        by[k] = b.y;
+        bz[k] = b.z;
+        s[k] = 0.0;
+    }
+    for (long long jt = jt0; jt < jt1; ++jt) {
+        const long long j0 = jt * kPotJT, j = j0 + threadIdx.x;
+        __syncthreads();
+        tile[threadIdx.x] = j < N ? xs[j] : make_double4(0.0, 0.0, 0.0, 0.0);
+        __syncthreads();
+        const bool diag = j0 < i0 + kPotITILE && j0 + kPotJT > i0;
+        for (int jj = 0; jj < kPotJT; ++jj) {
+            const double4 c = tile[jj];
+#pragma unroll
+            for (int k = 0; k < kPotIPT; ++k) {
+                const double dx = c.x - bx[k], dy = c.y - by[k], dz = c.z - bz[k];
+                const double w = diag && j0 + jj == i0 + threadIdx.x + k * kDiagThreads ? 0.0 : c.w;
+                s[k] = fma(w, rsqrt(fma(dx, dx, fma(dy, dy, fma(dz, dz, e2)))), s[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kPotIPT; ++k) {
+        const long long i = i0 + threadIdx.x + k * kDiagThreads;
+        if (i < N) part[(long long)blockIdx.y * N + i] = s[k];
+    }
+}
+
+// sum_k m_k sum_split part[split][k], the splits in order, into the block's slot.
+__global__ void __launch_bounds__(kDiagThreads)
+    potential_sum_kernel(const double *__restrict__ part, int splits, const float4 *__restrict__ xs,
+                         const double4 *__restrict__ xs64, int f64, long long N, double *diag) {
     double acc = 0.0;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < N;
          k += (long long)gridDim.x * blockDim.x) {
         double s = 0.0;
-        if (f64) {
-            const double4 b = xs64[k];
-            for (long long j = 0; j < N; ++j) {
-                if (j == k) continue;
-                const double4 c = xs64[j];
-                const double dx = c.x - b.x, dy = c.y - b.y, dz = c.z - b.z;
-                s += c.w * rsqrt(dx * dx + dy * dy + dz * dz + eps2);
-            }
-            acc += b.w * s;
-        } else {
-            const float4 b = xs[k];
-            const float e2 = (float)eps2;
-            for (long long j0 = 0; j0 < N; j0 += 64) {
-                float p = 0.f;
-                const long long j1 = j0 + 64 < N ? j0 + 64 : N;
-                for (long long j = j0; j < j1; ++j) {
-                    if (j == k) continue;
-                    const float4 c = xs[j];
-                    const float dx = c.x - b.x, dy = c.y - b.y, dz = c.z - b.z;
-                    const float r2 = dx * dx + dy * dy + dz * dz + e2;
-                    float y = rsqrt_approx(r2);
-                    y = y * (1.5f - 0.5f * r2 * y * y);
-                    p += c.w * y;
-                }
-                s += (double)p;
-            }
-            acc += (double)b.w * s;
-        }
+        for (int q = 0; q < splits; ++q) s += part[(long long)q * N + k];
+        acc += (f64 ? xs64[k].w : (double)xs[k].w) * s;
     }
     block_sum_to(acc, diag + blockIdx.x * kDiagQ + 0);
 }

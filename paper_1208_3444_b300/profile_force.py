@@ -7,6 +7,7 @@ with ncu.
     python -m paper_1208_3444_b300.profile_force --op jvp --workload grid32 --launches 1
     python -m paper_1208_3444_b300.profile_force --op ensemble --launches 1
     python -m paper_1208_3444_b300.profile_force --op spectrum --launches 1
+    python -m paper_1208_3444_b300.profile_force --op diagnostics --workload grid32 --launches 1
 
 --op force runs colatus_forces (the force kernel, or with --periodic L the
 Ewald real-space and k-space kernels); --op vjp runs colatus_force_vjp with a
@@ -14,7 +15,8 @@ seeded co-vector; --op jvp runs tangent steps of 64 single-tracer tangents
 (one JVP launch each); --op ensemble runs force evaluations of the
 64-realisation ensemble (--workload is ignored); --op spectrum runs
 colatus_velocity_spectrum on a seeded device series of 2000 records of 64
-tracers (Hann window, detrended; --workload is ignored).  Prints the CUDA-event duration of the force or VJP
+tracers (Hann window, detrended; --workload is ignored); --op diagnostics
+runs colatus_diagnostics (the O(N^2) potential energy and the moments).  Prints the CUDA-event duration of the force or VJP
 kernel (meaningless under a profiler, which serialises and replays kernels).
 """
 import argparse
@@ -52,7 +54,7 @@ def main():
                    help="grid16 | grid32 | uniform<N> | plummer<N>")
     p.add_argument("--prec", default="comp", choices=sorted(PRECS))
     p.add_argument("--launches", type=int, default=1)
-    p.add_argument("--op", default="force", choices=["force", "vjp", "jvp", "ensemble", "spectrum"])
+    p.add_argument("--op", default="force", choices=["force", "vjp", "jvp", "ensemble", "spectrum", "diagnostics"])
     p.add_argument("--periodic", type=float, default=0.0, help="box side L (0: isolated)")
     a = p.parse_args()
     if a.op == "ensemble":
@@ -87,6 +89,11 @@ def main():
             sim.tangent_step(inputs.lcdm_tau(2000), a.launches)
             sim.synchronize()
             print(f"jvp {a.workload} N={ic.N}: {a.launches} tangent steps of 64 tangents")
+            return
+        if a.op == "diagnostics":
+            for _ in range(a.launches):
+                d = sim.diagnostics()
+            print(f"diagnostics {a.workload} N={ic.N} prec={a.prec}: {a.launches} calls, W={d['W']:.9e}")
             return
         if a.periodic:
             sim.set_periodic(a.periodic)

@@ -9,7 +9,8 @@ evaluates 512 seeded rows against every source.
 
 Tolerances as in test_gpu_forces.py and test_gpu_adjoint.py: force RMS over
 bodies relative to the mean abs(F), 1e-5 FP32, 1e-6 FP32 compensated, 1e-11
-FP64; VJP normwise 1e-5 (FP32) and 1e-10 (FP64); tangent growth 1e-4.
+FP64; VJP normwise 1e-5 (FP32) and 1e-10 (FP64); tangent growth 1e-4; the
+potential energy W of the diagnostics 1e-6 (FP32 modes) and 1e-11 (FP64).
 """
 import numpy as np
 import pytest
@@ -117,3 +118,23 @@ def test_tangent_chunks_and_ragged_size(B_):
                                         dx0, np.zeros_like(v), "kdk")
         ref = np.array([np.sqrt(np.sum(h[0][s] ** 2) + np.sum(h[1][s] ** 2)) for h in hist[1:]])
         np.testing.assert_allclose(growth[:, b], ref, rtol=1e-4)
+
+
+@pytest.mark.parametrize("prec", [B.FP32, B.FP32_COMP, B.FP64])
+@pytest.mark.parametrize("N", [1, 2, 255, 1023, 1025, 4097, 10007])
+def test_potential_energy_at_tile_boundaries(N, prec):
+    # W of the diagnostics: the tiled pair sums with the self pair masked in
+    # the tiles that hold it, against the oracle's potential
+    x, m, _ = system(N, False, 7500 + N)
+    eps = 0.003
+    sim = B.Simulation(m, eps, LCDM_D, 1.0, prec=prec)
+    try:
+        sim.set_state(x)
+        W = sim.diagnostics()["W"]
+    finally:
+        sim.close()
+    ref = oracle.diagnostics(x, np.zeros_like(x), m, 1.0, eps, 1.0)["W"]
+    if N == 1:
+        assert W == 0.0 and ref == 0.0
+        return
+    assert W == pytest.approx(ref, rel=1e-11 if prec == B.FP64 else 1e-6)
