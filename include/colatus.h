@@ -190,7 +190,10 @@ colatus_status colatus_read_tracers(colatus_t ctx, float *xv_out, int64_t *nrec_
  *   out[2..4] P = sum m a^2 v             out[5..7] L = sum m a^2 x cross v
  *   out[8..10] centre of mass             out[11] a   out[12] t   out[13] H(a)
  *   out[14] W_x = -(G/2) sum_{j != k} m_k m_j / s_kj   out[15] step count
- * (K + W obeys the Layzer-Irvine equation d(K+W)/dt = -H (2K + W)). */
+ * (K + W obeys the Layzer-Irvine equation d(K+W)/dt = -H (2K + W)).
+ * The first call (and a call after N grows) allocates the context's scratch
+ * for the per-split potential sums, at most 64 MB.  Errors: COLATUS_E_STATE
+ * (no state set), COLATUS_E_CUDA (the allocation or a launch failed). */
 colatus_status colatus_diagnostics(colatus_t ctx, double out[COLATUS_NDIAG]);
 
 /* ---- Tracer velocity energy spectrum (Sec. I, Sec. IV: the velocity of
