@@ -191,7 +191,7 @@ colatus_status colatus_read_tracers(colatus_t ctx, float *xv_out, int64_t *nrec_
  *   out[8..10] centre of mass             out[11] a   out[12] t   out[13] H(a)
  *   out[14] W_x = -(G/2) sum_{j != k} m_k m_j / s_kj   out[15] step count
  * (K + W obeys the Layzer-Irvine equation d(K+W)/dt = -H (2K + W)).
- * The first call (and a call after N grows) allocates the context's scratch
+ * The first call allocates the context's scratch
  * for the per-split potential sums, at most 64 MB.  Errors: COLATUS_E_STATE
  * (no state set), COLATUS_E_CUDA (the allocation or a launch failed). */
 colatus_status colatus_diagnostics(colatus_t ctx, double out[COLATUS_NDIAG]);
