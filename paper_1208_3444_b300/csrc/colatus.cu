@@ -1628,7 +1628,8 @@ colatus_status colatus_diagnostics(colatus_t ctx, double out[COLATUS_NDIAG]) {
     TRY(sync_and_check(ctx));
     const bool f64 = ctx->prec == COLATUS_FP64;
     CU(cudaMemsetAsync(ctx->diag, 0, kDiagSlots * sizeof(double), ctx->stream));
-    const unsigned nb = (unsigned)std::min<long long>(blocks_for(ctx->N, kDiagThreads), 4L * ctx->num_sms);
+    const unsigned nb = (unsigned)std::min<long long>(
+        {(long long)blocks_for(ctx->N, kDiagThreads), 4LL * ctx->num_sms, (long long)kDiagMaxBlocks});
     // potential pair sums: i-tiles x source splits.  Blocks are equal work
     // (tps source tiles), so the time goes as ceil(blocks / SMs) x tps; take
     // the split with the least (fewer blocks on ties), at most 64 splits and
@@ -1662,7 +1663,8 @@ colatus_status colatus_diagnostics(colatus_t ctx, double out[COLATUS_NDIAG]) {
     moments_kernel<<<nb, kDiagThreads, 0, ctx->stream>>>(ctx->xs, ctx->vs, ctx->xs64, ctx->vs64,
                                                         f64 ? 1 : 0, ctx->N, ctx->diag);
     TRY(launched(ctx));
-    finish_diagnostics_kernel<<<1, 1, 0, ctx->stream>>>(ctx->diag, ctx->clk, ctx->cosmo, ctx->G);
+    finish_diagnostics_kernel<<<1, kDiagQ * 32, 0, ctx->stream>>>(ctx->diag, (int)nb, ctx->clk, ctx->cosmo,
+                                                                ctx->G);
     TRY(launched(ctx));
     CU(cudaMemcpyAsync(out, ctx->diag + kDiagOut, COLATUS_NDIAG * sizeof(double),
                        cudaMemcpyDeviceToHost, ctx->stream));

@@ -198,13 +198,20 @@ __global__ void __launch_bounds__(kDiagThreads)
     for (int c = 0; c < 11; ++c) block_sum_to(q[c], diag + blockIdx.x * kDiagQ + 1 + c);
 }
 
-// Combine the block slots (in block order) into the output record.
-__global__ void finish_diagnostics_kernel(double *diag, const DevClock *clk, Cosmo cosmo, double G) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double s[kDiagQ];
-    for (int c = 0; c < kDiagQ; ++c) s[c] = 0.0;
-    for (int b = 0; b < kDiagMaxBlocks; ++b)
-        for (int c = 0; c < kDiagQ; ++c) s[c] += diag[b * kDiagQ + c];
+// Combine the slots of the nb blocks used into the output record.  Warp c
+// sums quantity c: lane l adds blocks l, l + 32, ... in order, then a fixed
+// shuffle tree adds the lanes, so the result does not depend on timing.
+// Launch with kDiagQ warps.
+__global__ void __launch_bounds__(kDiagQ * 32)
+    finish_diagnostics_kernel(double *diag, int nb, const DevClock *clk, Cosmo cosmo, double G) {
+    __shared__ double s[kDiagQ];
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double v = 0.0;
+    for (int b = lane; b < nb; b += 32) v += diag[b * kDiagQ + c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s[c] = v;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     const double a = clk->a, a2 = a * a;
     bool bad = false;
     const double H = hubble_of(a, cosmo, bad);
@@ -212,9 +219,9 @@ __global__ void finish_diagnostics_kernel(double *diag, const DevClock *clk, Cos
     const double Wx = -0.5 * G * s[0];
     o[0] = 0.5 * a2 * s[1];
     o[1] = Wx / a;
-    for (int c = 0; c < 3; ++c) o[2 + c] = a2 * s[2 + c];
-    for (int c = 0; c < 3; ++c) o[5 + c] = a2 * s[5 + c];
-    for (int c = 0; c < 3; ++c) o[8 + c] = s[8 + c] / s[11];
+    for (int q = 0; q < 3; ++q) o[2 + q] = a2 * s[2 + q];
+    for (int q = 0; q < 3; ++q) o[5 + q] = a2 * s[5 + q];
+    for (int q = 0; q < 3; ++q) o[8 + q] = s[8 + q] / s[11];
     o[11] = a;
     o[12] = clk->t;
     o[13] = bad ? __longlong_as_double(0x7ff8000000000000LL) : H;
