@@ -48,30 +48,46 @@ constexpr int kPotJT = 256;
 constexpr int kPotITILE = kDiagThreads * kPotIPT;
 constexpr int kPotChunk = 64;
 
+// One source tile, pair-interleaved in shared memory (per source pair: x0 x1
+// y0 y1 | z0 z1 m0 m1), two sources per f32x2 lane pair; the 64 sources of
+// each chunk are summed in FP32 and added to s in FP64.
 template <bool MASK>
-__device__ __forceinline__ void pot_f32_tile(const float4 *tile, long long j0, long long i0,
-                                             const float (&bx)[kPotIPT], const float (&by)[kPotIPT],
-                                             const float (&bz)[kPotIPT], float e2,
+__device__ __forceinline__ void pot_f32_tile(const float4 *__restrict__ t, long long j0, long long i0,
+                                             const float2 (&nx)[kPotIPT], const float2 (&ny)[kPotIPT],
+                                             const float2 (&nz)[kPotIPT], float2 e2,
                                              double (&s)[kPotIPT]) {
-    for (int q = 0; q < kPotJT; q += kPotChunk) {
-        float p[kPotIPT];
+    const float2 mhalf = make_float2(-0.5f, -0.5f), three_halves = make_float2(1.5f, 1.5f);
+    for (int q0 = 0; q0 < kPotJT / 2; q0 += kPotChunk / 2) {
+        float2 p[kPotIPT];
 #pragma unroll
-        for (int k = 0; k < kPotIPT; ++k) p[k] = 0.f;
-#pragma unroll 4
-        for (int jj = q; jj < q + kPotChunk; ++jj) {
-            const float4 c = tile[jj];
+        for (int k = 0; k < kPotIPT; ++k) p[k] = make_float2(0.f, 0.f);
+#pragma unroll 2
+        for (int q = q0; q < q0 + kPotChunk / 2; ++q) {
+            const float4 A = t[2 * q];      // x0 x1 y0 y1
+            const float4 B = t[2 * q + 1];  // z0 z1 m0 m1
+            const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
+            const float2 zj = make_float2(B.x, B.y);
 #pragma unroll
             for (int k = 0; k < kPotIPT; ++k) {
-                const float dx = c.x - bx[k], dy = c.y - by[k], dz = c.z - bz[k];
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2)));
-                float y = rsqrt_approx(r2);
-                y = y * fmaf(-0.5f * r2 * y, y, 1.5f);
-                const float w = MASK && j0 + jj == i0 + threadIdx.x + k * kDiagThreads ? 0.f : c.w;
-                p[k] = fmaf(w, y, p[k]);
+                const float2 dx = __fadd2_rn(xj, nx[k]), dy = __fadd2_rn(yj, ny[k]),
+                             dz = __fadd2_rn(zj, nz[k]);
+                float2 r2 = __ffma2_rn(dz, dz, e2);
+                r2 = __ffma2_rn(dy, dy, r2);
+                r2 = __ffma2_rn(dx, dx, r2);
+                float2 y = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                // one Newton step: y (3/2 - r2 y^2 / 2)
+                y = __fmul2_rn(y, __ffma2_rn(__fmul2_rn(__fmul2_rn(mhalf, r2), y), y, three_halves));
+                float2 w = make_float2(B.z, B.w);
+                if (MASK) {
+                    const long long i = i0 + threadIdx.x + k * kDiagThreads, j = j0 + 2 * q;
+                    if (j == i) w.x = 0.f;
+                    if (j + 1 == i) w.y = 0.f;
+                }
+                p[k] = __ffma2_rn(w, y, p[k]);
             }
         }
 #pragma unroll
-        for (int k = 0; k < kPotIPT; ++k) s[k] += (double)p[k];
+        for (int k = 0; k < kPotIPT; ++k) s[k] += (double)p[k].x + (double)p[k].y;
     }
 }
 
@@ -80,30 +96,37 @@ __device__ __forceinline__ void pot_f32_tile(const float4 *tile, long long j0, l
 __global__ void __launch_bounds__(kDiagThreads)
     potential_f32_kernel(const float4 *__restrict__ xs, long long N, float e2, int tps,
                          double *__restrict__ part) {
-    __shared__ float4 tile[kPotJT];
+    __shared__ __align__(16) float tile[kPotJT * 4];
     const long long i0 = (long long)blockIdx.x * kPotITILE;
     const long long n_jt = (N + kPotJT - 1) / kPotJT;
     const long long jt0 = (long long)blockIdx.y * tps, jt1 = min(jt0 + tps, n_jt);
-    float bx[kPotIPT], by[kPotIPT], bz[kPotIPT];
+    float2 nx[kPotIPT], ny[kPotIPT], nz[kPotIPT];
     double s[kPotIPT];
 #pragma unroll
     for (int k = 0; k < kPotIPT; ++k) {
         const long long i = i0 + threadIdx.x + k * kDiagThreads;
         const float4 b = i < N ? xs[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        bx[k] = b.x;
-        by[k] = b.y;
-        bz[k] = b.z;
+        nx[k] = make_float2(-b.x, -b.x);
+        ny[k] = make_float2(-b.y, -b.y);
+        nz[k] = make_float2(-b.z, -b.z);
         s[k] = 0.0;
     }
+    const float2 e22 = make_float2(e2, e2);
+    float *slot = tile + (threadIdx.x >> 1) * 8 + (threadIdx.x & 1);
     for (long long jt = jt0; jt < jt1; ++jt) {
         const long long j0 = jt * kPotJT, j = j0 + threadIdx.x;
+        const float4 c = j < N ? xs[j] : make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
-        tile[threadIdx.x] = j < N ? xs[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        slot[0] = c.x;
+        slot[2] = c.y;
+        slot[4] = c.z;
+        slot[6] = c.w;
         __syncthreads();
+        const float4 *t4 = reinterpret_cast<const float4 *>(tile);
         if (j0 < i0 + kPotITILE && j0 + kPotJT > i0)
-            pot_f32_tile<true>(tile, j0, i0, bx, by, bz, e2, s);
+            pot_f32_tile<true>(t4, j0, i0, nx, ny, nz, e22, s);
         else
-            pot_f32_tile<false>(tile, j0, i0, bx, by, bz, e2, s);
+            pot_f32_tile<false>(t4, j0, i0, nx, ny, nz, e22, s);
     }
 #pragma unroll
     for (int k = 0; k < kPotIPT; ++k) {
