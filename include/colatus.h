@@ -150,7 +150,10 @@ colatus_status colatus_get_state(colatus_t ctx, void *x, void *v, int dtype, int
  * except when two earlier read-backs are still copying (two slots).  x and v
  * must stay valid and untouched until colatus_wait_state,
  * colatus_synchronize or colatus_get_state returns.  Either may be NULL, not
- * both.  Errors: COLATUS_E_ARG, COLATUS_E_STATE (no state). */
+ * both.  The first call on a context creates the copy stream and the two
+ * device slots (N x 3 doubles each for x and v); its cudaMalloc calls
+ * synchronise the device once.  Errors: COLATUS_E_ARG, COLATUS_E_STATE (no
+ * state), COLATUS_E_CUDA. */
 colatus_status colatus_get_state_async(colatus_t ctx, void *x, void *v, int dtype);
 
 /* Wait for every read-back started by colatus_get_state_async and for the
