@@ -147,10 +147,10 @@ colatus_status colatus_get_state(colatus_t ctx, void *x, void *v, int dtype, int
  * the device (in order on the context's stream) and copied to x and v on a
  * separate copy stream, so the copy overlaps the steps enqueued after it
  * (pinned host memory is needed for the overlap).  Returns without waiting,
- * except when two earlier read-backs are still copying (two slots).  x and v
+ * except when four earlier read-backs are still copying (four slots).  x and v
  * must stay valid and untouched until colatus_wait_state,
  * colatus_synchronize or colatus_get_state returns.  Either may be NULL, not
- * both.  The first call on a context creates the copy stream and the two
+ * both.  The first call on a context creates the copy stream and the four
  * device slots (N x 3 doubles each for x and v); its cudaMalloc calls
  * synchronise the device once.  Errors: COLATUS_E_ARG, COLATUS_E_STATE (no
  * state), COLATUS_E_CUDA. */

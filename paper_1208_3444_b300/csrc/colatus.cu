@@ -113,6 +113,7 @@ constexpr int kTabCap = 4096;           // ring of look-ahead schedule entries
 constexpr int kLookahead = 256;         // schedule entries kept ahead of the state
 constexpr int kFriedmannSub = 8;        // RK4 sub-steps per half step
 constexpr int kTabEvents = 64;          // extension events kept in flight (one per piece)
+constexpr int kReadSlots = 4;      // asynchronous read-backs in flight per context
 constexpr int kTabPiece = 64;           // schedule entries per extension launch
 static_assert(kChunk + 4 * kLookahead <= kTabCap, "schedule ring too small");
 
@@ -220,13 +221,14 @@ struct colatus_ctx {
     long long tab_ev_covers[kTabEvents] = {};
     int tab_ev_next = 0;
     // asynchronous state read-back (colatus_get_state_async): a copy stream
-    // and two staging slots, each with its snapshot / copy-done events
+    // and kReadSlots staging slots, each with its snapshot / copy-done
+    // events; the host may run that many read-backs ahead of the copies
     cudaStream_t cstream = nullptr;
     struct ReadSlot {
         void *x = nullptr, *v = nullptr;   // device staging, N x 3 doubles each
         cudaEvent_t snap = nullptr, done = nullptr;
         bool busy = false;
-    } rslot[2];
+    } rslot[kReadSlots];
     int rnext = 0;
     double *stage = nullptr;       // N x 3 doubles for host <-> device transfers
     double *stage2 = nullptr;
@@ -1479,7 +1481,7 @@ colatus_status colatus_get_state_async(colatus_t ctx, void *x, void *v, int dtyp
         }
     }
     auto &r = ctx->rslot[ctx->rnext];
-    ctx->rnext ^= 1;
+    ctx->rnext = (ctx->rnext + 1) % kReadSlots;
     if (r.busy) CU(cudaEventSynchronize(r.done));   // its previous copy still reads the slot
     r.busy = false;
     // snapshot, ordered after the steps enqueued so far

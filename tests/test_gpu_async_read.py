@@ -16,7 +16,7 @@ TAU = inputs.lcdm_tau(2000)
 def test_async_reads_match_synchronous_reads(dtype):
     import torch
     ic = inputs.grid16(critical=True)
-    n = 6
+    n = 10
     sim = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START, prec=B.FP32_COMP)
     try:
         sim.set_state(ic.x, ic.v)
