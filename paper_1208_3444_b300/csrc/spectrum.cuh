@@ -14,8 +14,8 @@
 // reduced exactly (table entry (e mod T) of exp(2 pi i e / T)):
 //
 // * spectrum_fft_kernel, for T <= kSpecFftMaxT whose prime factors are all
-//   <= kSpecFftMaxP: a mixed-radix Stockham FFT in shared memory, O(T sum p)
-//   multiply-adds.  A cluster of two CTAs per tracer: CTA 0 transforms the
+//   <= kSpecFftMaxP: a mixed-radix Stockham FFT in shared memory (radix-4 and
+//   radix-5 butterflies written out, other radices as direct p-point sums).  A cluster of two CTAs per tracer: CTA 0 transforms the
 //   complex series u_x + i u_y, CTA 1 the series u_z; the sum over components
 //   of the real series' power is (|Z_j|^2 + |Z_{T-j}|^2) / 2 for either, and
 //   CTA 0 reads CTA 1's transform through distributed shared memory.
@@ -159,11 +159,69 @@ spectrum_kernel(SpecSeries S, const double2 *__restrict__ tw, double dt, int win
 // transforms Y_r (r < p m) at [r L, r L + L), and output o = k p L + j'
 // (k < m, j' < p L) is the p L-point transform
 //     Z_k[j'] = sum_q exp(-2 pi i q m j' / N) Y_{k + m q}[j' mod L].
-// The exponent q m j' is advanced by m j' < N and reduced by one subtraction.
+// Radix 4 and 5 take one butterfly per thread: the inputs a_q =
+// Y_{k + m q}[j] exp(-2 pi i q m j / N) (q m j < N) and their p-point DFT
+// written out; other radices take one output per thread, the exponent
+// q m j' advanced by m j' < N and reduced by one subtraction.
+
+// v exp(-i theta) for the table entry c = (cos theta, sin theta)
+__device__ __forceinline__ double2 spec_rot(double2 v, double2 c) {
+    return make_double2(fma(v.x, c.x, v.y * c.y), fma(v.y, c.x, -(v.x * c.y)));
+}
+
 __device__ __forceinline__ void spec_fft_stage(const double2 *__restrict__ src,
                                                double2 *__restrict__ dst,
                                                const double2 *__restrict__ tw, int N, int p, int L) {
-    const int pL = p * L, m = N / pL;
+    const int pL = p * L, m = N / pL, step = m * L;
+    if (p == 4) {
+        for (int b = threadIdx.x; b < N / 4; b += kSpecThreads) {
+            const int k = b / L, j = b - k * L, e = m * j;
+            const double2 *y = src + k * L + j;
+            const double2 a0 = y[0], a1 = spec_rot(y[step], __ldg(&tw[e])),
+                          a2 = spec_rot(y[2 * step], __ldg(&tw[2 * e])),
+                          a3 = spec_rot(y[3 * step], __ldg(&tw[3 * e]));
+            const double2 t0 = make_double2(a0.x + a2.x, a0.y + a2.y);
+            const double2 t1 = make_double2(a0.x - a2.x, a0.y - a2.y);
+            const double2 t2 = make_double2(a1.x + a3.x, a1.y + a3.y);
+            const double2 t3 = make_double2(a1.y - a3.y, a3.x - a1.x);   // -i (a1 - a3)
+            double2 *z = dst + k * pL + j;
+            z[0] = make_double2(t0.x + t2.x, t0.y + t2.y);
+            z[L] = make_double2(t1.x + t3.x, t1.y + t3.y);
+            z[2 * L] = make_double2(t0.x - t2.x, t0.y - t2.y);
+            z[3 * L] = make_double2(t1.x - t3.x, t1.y - t3.y);
+        }
+        return;
+    }
+    if (p == 5) {
+        // cos and sin of 2 pi / 5 and 4 pi / 5 from the table (N is a multiple of 5)
+        const double2 w1 = __ldg(&tw[N / 5]), w2 = __ldg(&tw[2 * (N / 5)]);
+        for (int b = threadIdx.x; b < N / 5; b += kSpecThreads) {
+            const int k = b / L, j = b - k * L, e = m * j;
+            const double2 *y = src + k * L + j;
+            const double2 a0 = y[0], a1 = spec_rot(y[step], __ldg(&tw[e])),
+                          a2 = spec_rot(y[2 * step], __ldg(&tw[2 * e])),
+                          a3 = spec_rot(y[3 * step], __ldg(&tw[3 * e])),
+                          a4 = spec_rot(y[4 * step], __ldg(&tw[4 * e]));
+            const double2 b1 = make_double2(a1.x + a4.x, a1.y + a4.y);
+            const double2 b2 = make_double2(a2.x + a3.x, a2.y + a3.y);
+            const double2 d1 = make_double2(a1.x - a4.x, a1.y - a4.y);
+            const double2 d2 = make_double2(a2.x - a3.x, a2.y - a3.y);
+            const double2 r1 = make_double2(fma(w2.x, b2.x, fma(w1.x, b1.x, a0.x)),
+                                            fma(w2.x, b2.y, fma(w1.x, b1.y, a0.y)));
+            const double2 r2 = make_double2(fma(w1.x, b2.x, fma(w2.x, b1.x, a0.x)),
+                                            fma(w1.x, b2.y, fma(w2.x, b1.y, a0.y)));
+            const double2 i1 = make_double2(fma(w2.y, d2.x, w1.y * d1.x), fma(w2.y, d2.y, w1.y * d1.y));
+            const double2 i2 = make_double2(fma(-w1.y, d2.x, w2.y * d1.x), fma(-w1.y, d2.y, w2.y * d1.y));
+            // Z_1 = r1 - i i1, Z_4 = r1 + i i1, Z_2 = r2 - i i2, Z_3 = r2 + i i2
+            double2 *z = dst + k * pL + j;
+            z[0] = make_double2(a0.x + b1.x + b2.x, a0.y + b1.y + b2.y);
+            z[L] = make_double2(r1.x + i1.y, r1.y - i1.x);
+            z[4 * L] = make_double2(r1.x - i1.y, r1.y + i1.x);
+            z[2 * L] = make_double2(r2.x + i2.y, r2.y - i2.x);
+            z[3 * L] = make_double2(r2.x - i2.y, r2.y + i2.x);
+        }
+        return;
+    }
     for (int o = threadIdx.x; o < N; o += kSpecThreads) {
         const int kk = o / pL, jp = o - kk * pL, j = jp % L;
         const int de = m * jp;
@@ -172,7 +230,7 @@ __device__ __forceinline__ void spec_fft_stage(const double2 *__restrict__ src,
         int e = 0;
         for (int q = 0; q < p; ++q) {
             const double2 c = __ldg(&tw[e]);
-            const double2 v = y[q * m * L];
+            const double2 v = y[q * step];
             // v (cos - i sin)
             re = fma(v.x, c.x, re);
             re = fma(v.y, c.y, re);
