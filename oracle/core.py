@@ -50,6 +50,11 @@ PINS = {
            "time reversibility, Layzer-Irvine tau^2 convergence",
     "adjoint_run": "central finite differences of a trajectory loss",
     "tangent_run": "finite differences of trajectories; adjoint duality",
+    "ftle": "central differences of two oracle trajectories; the exact discrete solution "
+            "of the KDK leapfrog for a coincident pair (a harmonic relative coordinate)",
+    "diagnostics": "rigid rotation L = a^2 I omega and K = omega.L/2 (inertia tensor by hand); "
+                   "boosts (P += a^2 M u, L about the centre of mass unchanged); translations "
+                   "(COM += s, L += s x P); mirror symmetry; two-body Plummer energy; powers of a",
     "deformation_force": "equals the Eq. 1 pull of an extra body of mass C psi / G fixed at "
                          "x_psi (the paper's own description); single-body closed form",
     "deformation_vjp/jvp": "central finite differences of deformation_force",
