@@ -140,7 +140,39 @@ def test_diagnostics_match_oracle():
     np.testing.assert_allclose([gd["Cx"], gd["Cy"], gd["Cz"]], d["COM"], rtol=1e-12)
     pscale = abs(d["K"]) ** 0.5
     np.testing.assert_allclose([gd["Px"], gd["Py"], gd["Pz"]], d["P"], atol=1e-12 * pscale + 1e-15)
+    # |x| <= ~1, so |L| is bounded by the same scale as |P|
+    np.testing.assert_allclose([gd["Lx"], gd["Ly"], gd["Lz"]], d["L"], atol=1e-12 * pscale + 1e-15)
     assert gd["step"] == 5
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.FP32_COMP])
+def test_diagnostics_of_a_rotating_boosted_box_match_oracle(prec):
+    # a box with a rigid rotation, a bulk velocity and random motions, so that
+    # every moment (P, L, COM) is far from zero; compared element by element
+    ic = inputs.grid16(critical=True)
+    rng = np.random.default_rng(8)
+    c = ic.x.mean(0)
+    w = np.array([0.4, -0.9, 1.3])
+    ic.v = inputs.f32(np.cross(w, ic.x - c) + np.array([0.3, 0.1, -0.2])
+                      + 0.05 * rng.standard_normal(ic.x.shape))
+    n = 3
+    g = run_gpu(ic, prec, "kdk", n)
+    r = oracle.run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n, "kdk")
+    d = oracle.diagnostics(g["x"], g["v"], ic.m, g["a"], ic.eps, 1.0, LCDM)
+    gd = g["diag"]
+    tol = 1e-12 if prec == B.FP64 else 1e-6
+    # same state on both sides: the GPU's moments of its own state
+    for key, names in (("P", ("Px", "Py", "Pz")), ("L", ("Lx", "Ly", "Lz")),
+                       ("COM", ("Cx", "Cy", "Cz"))):
+        got = np.array([gd[k] for k in names])
+        np.testing.assert_allclose(got, d[key], atol=tol * np.abs(d[key]).max())
+        assert np.abs(d[key]).max() > 1e-3 * (1.0 if key == "COM" else ic.m.sum() * g["a"] ** 2)
+    assert gd["K"] == pytest.approx(d["K"], rel=tol)
+    assert gd["W"] == pytest.approx(d["W"], rel=tol)
+    # and the oracle's own trajectory gives the same moments (before collapse)
+    dr = oracle.diagnostics(r["x"], r["v"], ic.m, r["schedule"]["a"][-1], ic.eps, 1.0, LCDM)
+    np.testing.assert_allclose([gd["Lx"], gd["Ly"], gd["Lz"]], dr["L"],
+                               atol=1e-5 * np.abs(dr["L"]).max())
 
 
 def test_fp32_diagnostics_close_to_oracle():
