@@ -40,7 +40,7 @@ EXPORTS = ("colatus_init", "colatus_set_config", "colatus_set_masses", "colatus_
            "colatus_set_deformation", "colatus_velocity_spectrum", "colatus_tracer_spectrum",
            "colatus_set_periodic", "colatus_periodic_params", "colatus_get_state_async",
            "colatus_wait_state", "colatus_selftest_wait", "colatus_profile_read_kinds",
-           "colatus_ensemble_autotune", "colatus_ensemble_set_tuning")
+           "colatus_ensemble_autotune", "colatus_ensemble_set_tuning", "colatus_force_plan")
 
 
 class ColatusError(RuntimeError):
@@ -81,6 +81,7 @@ def lib():
         "colatus_ensemble_autotune": [_vp, _int, _vp, _vp],
         "colatus_ensemble_set_tuning": [_vp, _int],
         "colatus_forces_noalloc": [_vp, _i64, _dbl, _dbl, _dbl, _vp, _vp],
+        "colatus_force_plan": [_vp, _vp],
         "colatus_force_vjp": [_vp, _vp, _vp, _vp, _int, _int],
         "colatus_adjoint_forward": [_vp, _dbl, _i64, _i64],
         "colatus_adjoint_backward": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _int, _int],
@@ -305,13 +306,20 @@ def colatus_adjoint_backward(h, gx_T=None, gv_T=None, gm_T=None, gx_0=None, gv_0
 def colatus_forces_noalloc(pos, eps, G, a, acc_out, stream=None):
     """Allocation-free force (see colatus.h): pos is a CUDA float32 tensor of
     N x 4 (x, y, z, m), acc_out a CUDA float32 tensor of N x 3."""
+    import torch
     for t, cols in ((pos, 4), (acc_out, 3)):
         p, dev, dt, keep = _buf(t)
         if not dev or dt != F32 or tuple(t.shape[1:]) != (cols,):
             raise ValueError(f"expected a contiguous CUDA float32 tensor of N x {cols}")
-    st = lib().colatus_forces_noalloc(pos.data_ptr(), int(pos.shape[0]), float(eps), float(G),
-                                      float(a), acc_out.data_ptr(),
-                                      None if stream is None else int(stream))
+    if pos.device != acc_out.device:
+        raise ValueError("pos and acc_out must be on the same GPU")
+    if acc_out.shape[0] != pos.shape[0]:
+        raise ValueError("pos and acc_out must have the same number of rows")
+    # the C call runs on the current device; make it the tensors' device
+    with torch.cuda.device(pos.device):
+        st = lib().colatus_forces_noalloc(pos.data_ptr(), int(pos.shape[0]), float(eps), float(G),
+                                          float(a), acc_out.data_ptr(),
+                                          None if stream is None else int(stream))
     if st != OK:
         raise ColatusError(st, "colatus_forces_noalloc")
 
@@ -477,6 +485,14 @@ class Simulation:
     def stats(self):
         s = colatus_stats(self.h)
         return dict(launches=int(s[0]), interactions=float(s[1]), steps=int(s[2]), N=int(s[3]))
+
+    def force_plan(self):
+        """The force kernel launched for the current configuration (colatus_force_plan)."""
+        out = np.zeros(8, dtype=np.int64)
+        _check(lib().colatus_force_plan(self.h, out.ctypes.data), self.h)
+        kinds = ("force_f32", "force_f64", "ewald_f32", "ewald_f64")
+        return dict(kind=kinds[int(out[0])], threads=int(out[1]), ipt=int(out[2]), jt=int(out[3]),
+                    comp=bool(out[4]), eqm=bool(out[5]), grid=int(out[6]), units=int(out[7]))
 
     def profile_forces(self, on=True):
         colatus_profile_forces(self.h, on)

@@ -8,9 +8,12 @@
 // entry point runs the same persistent force kernel as colatus_forces but
 // keeps every scratch byte it needs (the packed bodies, the force segments and
 // the error flags) in one file-scope static device array of fixed size, so it
-// allocates nothing.  Every GPU that loads the library holds that array
-// (about 8.6 MiB) until the process exits.
+// allocates nothing.  A GPU holds that array (about 8.6 MiB) from the first
+// use of the library's kernels on it until the process exits (with lazy
+// module loading, the CUDA default, it is placed on a device when the module
+// is first used there).
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 
@@ -28,6 +31,13 @@ constexpr long long kSegFloat4 = 524288;            // 8 MiB of force segments
 constexpr long long kFlagFloat4 = 1;                // NUM_FLAGS ints
 constexpr long long kScratchFloat4 = kPkFloat4 + kSegFloat4 + kFlagFloat4;
 constexpr int kMaxDevices = 64;
+// Persistent-grid caps.  A tile is touched by at most ceil(G / n_it) + 1 CTAs,
+// so the segments need n_it * S_max <= G + 2 n_it slots of ITILE bodies.  At
+// N <= 32768, n_it <= 32 (wide, 1024-body i-tiles) or 128 (narrow, 256), and
+// kSegFloat4 holds 512 or 2048 such slots: G <= 448 and G <= 1792 fit on any
+// device, whatever its SM count and occupancy.
+constexpr long long kWideMaxGrid = 448;
+constexpr long long kNarrowMaxGrid = 1792;
 
 // The scratch.  Host code must not use this name as an address: on the host
 // it is only a stand-in; the device address comes from cudaGetSymbolAddress.
@@ -127,6 +137,19 @@ __global__ void na_out_kernel(const float4 *__restrict__ seg, ForceLaunch L, int
     acc_out[3 * i + 2] = scale * fz;
 }
 
+// A device pointer that the current device can use: device or managed
+// memory allocated on that device.
+bool on_device(const void *p, int dev) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
+
+long long min_ll(long long a, long long b) { return a < b ? a : b; }
+
 }  // namespace
 
 extern "C" colatus_status colatus_forces_noalloc(const float *pos, int64_t N, double eps, double G,
@@ -135,23 +158,48 @@ extern "C" colatus_status colatus_forces_noalloc(const float *pos, int64_t N, do
     if (N < 1 || N > kNoAllocMaxBodies) return COLATUS_E_ARG;
     if (!(eps > 0.0) || !std::isfinite(eps) || !(a > 0.0) || !std::isfinite(a) || !std::isfinite(G))
         return COLATUS_E_ARG;
+    // the pack kernel reads pos as float4
+    if ((reinterpret_cast<uintptr_t>(pos) & 15) || (reinterpret_cast<uintptr_t>(acc_out) & 3))
+        return COLATUS_E_ARG;
+    // a non-sticky error left by an earlier, unrelated call would otherwise be
+    // reported as this call's launch failure
+    cudaGetLastError();
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return COLATUS_E_CUDA;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    // the call synchronises and reads flags back: not allowed inside a capture
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return COLATUS_E_STATE;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return COLATUS_E_STATE;
+    // every buffer and the stream must belong to the current device
+    if (stream) {
+        int sdev = -1;
+        if (cudaStreamGetDevice(stream, &sdev) != cudaSuccess) {
+            cudaGetLastError();
+            return COLATUS_E_ARG;
+        }
+        if (sdev != dev) return COLATUS_E_ARG;
+    }
+    if (!on_device(pos, dev) || !on_device(acc_out, dev)) return COLATUS_E_ARG;
     DeviceSetup *ds = nullptr;
     colatus_status st = setup_device(dev, &ds);
     if (st != COLATUS_OK) return st;
-    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
 
     // wide tiles when every CTA gets at least four units, narrow otherwise
     int s_max = 0;
     long long n_pad = round_up_na(N, 1024);
     int itile = WideK::ITILE;
-    ForceLaunch L = plan_na(n_pad, itile, 512, (long long)ds->occ_wide * ds->num_sms, &s_max);
+    ForceLaunch L = plan_na(n_pad, itile, 512,
+                            min_ll((long long)ds->occ_wide * ds->num_sms, kWideMaxGrid), &s_max);
     bool wide = L.W >= 4LL * L.G;
     if (!wide) {
         n_pad = round_up_na(N, 256);
         itile = NarrowK::ITILE;
-        L = plan_na(n_pad, itile, 64, (long long)ds->occ_narrow * ds->num_sms, &s_max);
+        L = plan_na(n_pad, itile, 64,
+                    min_ll((long long)ds->occ_narrow * ds->num_sms, kNarrowMaxGrid), &s_max);
     }
     if ((long long)L.n_it * s_max * itile > kSegFloat4) return COLATUS_E_ARG;
     if (n_pad > kPkFloat4) return COLATUS_E_ARG;
@@ -162,11 +210,13 @@ extern "C" colatus_status colatus_forces_noalloc(const float *pos, int64_t N, do
     if (cudaMemsetAsync(flags, 0, NUM_FLAGS * sizeof(int), stream) != cudaSuccess) return COLATUS_E_CUDA;
     na_pack_kernel<<<(unsigned)((n_pad + 255) / 256), 256, 0, stream>>>(
         reinterpret_cast<const float4 *>(pos), pk, N, n_pad);
+    if (cudaGetLastError() != cudaSuccess) return COLATUS_E_CUDA;
     const float eps2 = (float)(eps * eps);
     if (wide)
         NA_WIDE<<<L.G, 256, WideK::SMEM, stream>>>(pk, seg, flags, L, eps2, 1.f);
     else
         NA_NARROW<<<L.G, 128, NarrowK::SMEM, stream>>>(pk, seg, flags, L, eps2, 1.f);
+    if (cudaGetLastError() != cudaSuccess) return COLATUS_E_CUDA;
     const float scale = (float)(G / (a * a * a));
     na_out_kernel<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(seg, L, itile, N, scale, acc_out);
     if (cudaGetLastError() != cudaSuccess) return COLATUS_E_CUDA;
