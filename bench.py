@@ -36,10 +36,35 @@ LCDM = dict(Omega_R=0.0, Omega_M=0.3, Omega_K=0.0, Omega_L=0.7, H0=1.0)
 FLOPS_PER_INTERACTION = 20          # Nyland et al. convention
 FP32_FLOP_PER_CLK_PER_SM = 256      # 128 FP32 lanes x FMA
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) of one launch of the 32^3 compensated force kernel,
-# force_f32_kernel<512, 4, 512, 4, 256, 1, 1, 1, 2>, from one ncu capture
-# (profiles/force_f32_comp_grid32.md); set to None when that kernel changes.
-FORCE_KERNEL_TRAFFIC = 540928
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the 32^3 compensated equal-mass force kernel, from one ncu capture.  The
+# figure is reported only while the launched kernel has the captured shape and
+# its source files hash to the captured sources; otherwise traffic is null.
+FORCE_KERNEL_TRAFFIC = {
+    "bytes": 540928,
+    "plan": dict(kind="force_f32", threads=512, ipt=4, jt=512, comp=True, eqm=True),
+    "template": "force_f32_kernel<512, 4, 512, 4, 256, true, true, 1, 2>",
+    "sources": ("paper_1208_3444_b300/csrc/force.cuh", "paper_1208_3444_b300/csrc/common.cuh"),
+    "sha256": "579503cbf47a53d099b67805f5c51d20b571a8d933235e5a03b557ae8542ee1f",
+}
+
+
+def source_hash(paths):
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def force_traffic(plan):
+    """The captured DRAM bytes per launch if `plan` (Simulation.force_plan())
+    is the captured kernel built from the captured sources, else None."""
+    t = FORCE_KERNEL_TRAFFIC
+    same_shape = all(plan.get(k) == v for k, v in t["plan"].items())
+    same_source = source_hash(t["sources"]) == t["sha256"]
+    return (t["bytes"] if same_shape and same_source else None), same_shape, same_source
 
 
 def parse():
@@ -512,6 +537,7 @@ def run_colatus(args, ws, rank, local):
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     launches0 = sim.stats()["launches"]
+    plan = sim.force_plan()
     sim.profile_forces(True)
     clocks = ClockSampler(local)
     barrier(ws)
@@ -592,11 +618,16 @@ def run_colatus(args, ws, rank, local):
         achieved_int = float(N) * N * nforce / (force_ms * 1e-3)
         achieved = achieved_int * FLOPS_PER_INTERACTION / 1e12
         peak = nsm * FP32_FLOP_PER_CLK_PER_SM * f_mhz * 1e6 / 1e12
+        traffic, same_shape, same_source = force_traffic(plan)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": FORCE_KERNEL_TRAFFIC,
-                "traffic_note": "dram bytes per launch from ncu (profiles/force_f32_comp_grid32.md); "
-                                "algorithmic HBM bytes: 524288 (positions read once)",
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum per launch of "
+                                 f"{FORCE_KERNEL_TRAFFIC['template']} from one ncu capture; "
+                                 f"launched kernel has the captured shape: {same_shape}; sources "
+                                 f"unchanged since the capture: {same_source}; algorithmic HBM "
+                                 "bytes: 524288 (positions read once)"),
                 "kernel": "force_f32_kernel (FP32 compensated, stream-K)",
+                "launched_plan": plan,
                 "interactions_per_s": achieved_int,
                 "int_per_sm_per_clk": achieved_int / (nsm * f_mhz * 1e6),
                 "peak_basis": f"{nsm} SMs x {FP32_FLOP_PER_CLK_PER_SM} FP32 flop/clk x "
@@ -634,6 +665,18 @@ def run_colatus(args, ws, rank, local):
         }
         if not args.no_cpu:
             result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        # the headline figures again, last, so that a cut-off copy of the line keeps them
+        result["headline"] = {
+            "force_32cubed_frac": roof["frac"],
+            "force_128cubed_frac": force128["frac"] if force128 else None,
+            "force_128cubed_ms": force128["ms_per_launch"] if force128 else None,
+            "force_128cubed_interactions_per_s": force128["interactions_per_s"] if force128 else None,
+            "adjoint_step_over_forward_step": adjoint["adjoint_step_over_forward_step"],
+            "vjp_frac_of_lane_op_floor": adjoint["vjp_frac_of_lane_op_floor"],
+            "ensemble_frac_of_fp32_roofline": ensemble["frac_of_fp32_roofline"],
+            "periodic_real_space_int_per_sm_per_clk": periodic["real_space_interactions_per_sm_per_clk"],
+            "e2e_over_value": e2e["value"] / value,
+        }
     return result
 
 

@@ -54,8 +54,11 @@ typedef enum {
 
 typedef enum {
     COLATUS_FP32 = 0,       /* FP32 pair arithmetic, blocked FP32 accumulation         */
-    COLATUS_FP32_COMP = 1,  /* FP32 pair arithmetic with a refined rsqrt and two-float
-                               (TwoSum) accumulation of the j-sum                      */
+    COLATUS_FP32_COMP = 1,  /* FP32 pair arithmetic (the same bare SFU rsqrt.approx as
+                               COLATUS_FP32); the j-sum is accumulated in FP32 blocks of
+                               32 to 256 j-bodies (by tile shape), each block folded into
+                               a two-float (TwoSum) hi/lo total; only
+                               colatus_diagnostics refines its rsqrt                   */
     COLATUS_FP64 = 2        /* FP64 everywhere (state, pair arithmetic, sums)          */
 } colatus_prec;
 
@@ -129,14 +132,18 @@ colatus_status colatus_periodic_params(colatus_t ctx, double *alpha_out, int *nk
 colatus_status colatus_set_masses(colatus_t ctx, const void *m, int dtype, int on_device);
 
 /* Set positions x and velocities v (N x 3 each, dtype elements, host or
- * device) at the current (t, a).  v may be NULL for bodies at rest.  The
+ * device) at the current (t, a).  This is the host-to-device copy of the
+ * initial conditions in the paper's Appendix A host program (read the data
+ * file, copy the bodies to the GPU); here it may also restore a saved state.  v may be NULL for bodies at rest.  The
  * FP32 modes store float state: double input is rounded to float.
  * Errors: COLATUS_E_ARG, COLATUS_E_NONFINITE (a non-finite input value). */
 colatus_status colatus_set_state(colatus_t ctx, const void *x, const void *v, int dtype,
                                  int on_device);
 
 /* Read positions and velocities (N x 3, dtype) and the current t and a
- * (either may be NULL).  Synchronises the stream and reports any device
+ * (either may be NULL).  This is the paper's Appendix A device-to-host copy
+ * of every position and velocity, which the paper makes after every step and
+ * which here is made on request.  Synchronises the stream and reports any device
  * error flag raised since the last check (COLATUS_E_NONFINITE,
  * COLATUS_E_FRIEDMANN, COLATUS_E_TIMEOUT). */
 colatus_status colatus_get_state(colatus_t ctx, void *x, void *v, int dtype, int on_device,
@@ -176,19 +183,24 @@ colatus_status colatus_step(colatus_t ctx, double dt, int64_t nsteps);
 /* Wait for all enqueued work and report device error flags. */
 colatus_status colatus_synchronize(colatus_t ctx);
 
-/* Record (x, v) of ntr bodies idx[0..ntr) (host int64 indices, distinct,
+/* Tracers: the paper follows the velocity of single bodies at every step
+ * (Sec. I; Appendix A copies every body's state back after each step).
+ * Record (x, v) of ntr bodies idx[0..ntr) (host int64 indices, distinct,
  * in [0, N)) after every subsequent step, into a device ring buffer of
  * capacity_steps records (the oldest are overwritten).  ntr = 0 stops
  * recording.  Replaces any earlier recording. */
 colatus_status colatus_record_tracers(colatus_t ctx, const int64_t *idx, int ntr,
                                       int64_t capacity_steps);
 
-/* Copy the recorded tracers, oldest first, to host memory xv_out laid out
+/* The single-body records of Sec. I, read back (the part of Appendix A's
+ * per-step device-to-host copy that the tracer study needs).
+ * Copy the recorded tracers, oldest first, to host memory xv_out laid out
  * [nrec][ntr][6] floats (x, y, z, vx, vy, vz); *nrec_out = records copied
  * (<= capacity).  xv_out may be NULL to query *nrec_out.  Synchronises. */
 colatus_status colatus_read_tracers(colatus_t ctx, float *xv_out, int64_t *nrec_out);
 
-/* FP64 diagnostics at the current state (synchronises):
+/* FP64 diagnostics at the current state (synchronises).  Their definitions
+ * come from the Hamiltonian of Sec. II (canonical momentum p = m a^2 v):
  *   out[0] K = (1/2) sum m a^2 |v|^2      out[1] W = W_x / a
  *   out[2..4] P = sum m a^2 v             out[5..7] L = sum m a^2 x cross v
  *   out[8..10] centre of mass             out[11] a   out[12] t   out[13] H(a)
@@ -245,6 +257,16 @@ const char *colatus_last_error(colatus_t ctx);
  * interactions enqueued (N^2 per force evaluation), out[2] steps taken,
  * out[3] N. */
 colatus_status colatus_stats(colatus_t ctx, double out[4]);
+
+/* The force kernel that colatus_forces and colatus_step launch for the
+ * current precision, masses, boundaries and tuning, for measurement (the
+ * Eq. 1 sum of the paper's Appendix A kernel; this names its launch shape):
+ * out[0] kind (0 FP32 all-pairs, 1 FP64 all-pairs, 2 FP32 periodic real
+ * space, 3 FP64 periodic real space), out[1] threads per CTA, out[2]
+ * i-bodies per thread, out[3] j-tile bodies, out[4] compensated accumulation
+ * (0/1), out[5] equal-mass form (0/1), out[6] persistent grid (CTAs),
+ * out[7] work units (i-tile x j-tile).  Errors: COLATUS_E_ARG. */
+colatus_status colatus_force_plan(colatus_t ctx, int64_t out[8]);
 
 /* Kernel timing for measurement: with on != 0 every launch of the force
  * kernel, the VJP kernel and the adjoint's per-step update kernel is
@@ -318,16 +340,21 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
  *   acc_out[3k..3k+2] = G a^-3 sum_{j != k} m_j (x_j - x_k) / (|x_j - x_k|^2 + eps^2)^{3/2}
  *   pos:     device array of N float4 (x, y, z, m), 16-byte aligned.
  *   acc_out: device array of N x 3 floats.
- *   N:       1 <= N <= 32768; eps > 0, a > 0, G finite (else COLATUS_E_ARG).
+ *   N:       1 <= N <= 32768 on any device; eps > 0, a > 0, G finite.
  *   cuda_stream: the cudaStream_t to run on (NULL: the legacy default stream).
+ * pos, acc_out and the stream must belong to the current device, and pos must
+ * be 16-byte aligned; otherwise, and for sizes or parameters out of range, the
+ * call returns COLATUS_E_ARG before it launches anything.
  * It allocates nothing: its scratch (packed bodies, force segments, error
- * flags) is one fixed static device array of about 8.6 MiB that every GPU
- * loading the library holds until the process exits.  The first call on a
- * device also resolves that array's device address (cudaGetSymbolAddress);
- * make this first call before any stream capture.  Every call shares the
- * scratch, so calls whose GPU work overlaps (different streams or threads)
- * race: serialise them.  The call synchronises `cuda_stream` before it
- * returns and reports a device-side wait that gave up as COLATUS_E_TIMEOUT. */
+ * flags) is one fixed static device array of about 8.6 MiB, which a GPU holds
+ * from the first use of the library's kernels on it until the process exits.
+ * The first call on a device also resolves that array's device address
+ * (cudaGetSymbolAddress).  The call copies the error flags to the host and
+ * synchronises `cuda_stream` before it returns, so it cannot be called while
+ * that stream is being captured into a CUDA graph (COLATUS_E_STATE).  Every
+ * call shares the scratch, so calls whose GPU work overlaps (different streams
+ * or threads) race: serialise them.  A device-side wait that gave up is
+ * reported as COLATUS_E_TIMEOUT. */
 colatus_status colatus_forces_noalloc(const float *pos, int64_t N, double eps, double G, double a,
                                       float *acc_out, void *cuda_stream);
 

@@ -2336,6 +2336,34 @@ void colatus_destroy(colatus_t ctx) {
     delete ctx;
 }
 
+colatus_status colatus_force_plan(colatus_t ctx, int64_t out[8]) {
+    if (!ctx || !out) return COLATUS_E_ARG;
+    const bool f64 = ctx->prec == COLATUS_FP64;
+    const ForcePlan &p = f64 ? plan_f64(ctx) : plan_f32(ctx);
+    out[0] = (ctx->periodic ? 2 : 0) + (f64 ? 1 : 0);
+    if (f64) {
+        out[1] = ctx->periodic ? kEw64NT : kF64NT;
+        out[2] = ctx->periodic ? 1 : kF64IPT;
+        out[4] = 0;
+        out[5] = 0;
+    } else if (ctx->periodic) {
+        out[1] = kEwNT;
+        out[2] = kEwIPT;
+        out[4] = ctx->prec == COLATUS_FP32_COMP ? 1 : 0;
+        out[5] = 0;
+    } else {
+        const F32Variant &fv = f32_variant(p.variant);
+        out[1] = fv.nt;
+        out[2] = fv.ipt;
+        out[4] = fv.comp ? 1 : 0;
+        out[5] = fv.eqm ? 1 : 0;
+    }
+    out[3] = p.jt;
+    out[6] = p.L.G;
+    out[7] = p.L.W;
+    return COLATUS_OK;
+}
+
 colatus_status colatus_stats(colatus_t ctx, double out[4]) {
     if (!ctx || !out) return COLATUS_E_ARG;
     out[0] = (double)ctx->launches;
