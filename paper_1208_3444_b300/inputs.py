@@ -166,11 +166,14 @@ def grid8(seed: int = 4) -> ICs:
     return perturbed_grid(8, 0.1, 0.02, seed, zeldovich=True, name="grid8")
 
 
-def ensemble(R: int = 64, seed: int = 5, nmin: int = 1024, nmax: int = 32768):
+def ensemble(R: int = 64, seed: int = 5, nmin: int = 1024, nmax: int = 32768,
+             critical: bool = False):
     """R realisations with N_r = round(nmin (nmax/nmin)^U), U uniform (log-
     uniform N), each a perturbed grid of side ceil(N_r^{1/3}) keeping N_r
     lattice points, sigma = 0.1 and eps = 0.02 local spacing, growing-mode
-    velocities; seeds derived from ``seed``."""
+    velocities; seeds derived from ``seed``.  critical=True gives each
+    realisation the background matter density as its total mass (the same
+    positions and velocities)."""
     rng = np.random.default_rng(seed)
     Ns = np.rint(nmin * (nmax / nmin) ** rng.random(R)).astype(np.int64)
     out = []
@@ -179,5 +182,6 @@ def ensemble(R: int = 64, seed: int = 5, nmin: int = 1024, nmax: int = 32768):
         while n ** 3 < Nr:
             n += 1
         out.append(perturbed_grid(n, 0.1, 0.02, seed * 1000 + r, zeldovich=True,
-                                  count=int(Nr), name=f"ensemble[{r}]"))
+                                  count=int(Nr), name=f"ensemble[{r}]",
+                                  total_mass=CRITICAL_MATTER_DENSITY if critical else 1.0))
     return out
