@@ -250,6 +250,128 @@ void colatus_oracle_ewald_real_rows(int64_t n, const double *x, const double *m,
     }
 }
 
+/* Jacobian of the real-space periodic pair term of
+ * colatus_oracle_ewald_real_rows with respect to the separation d (the
+ * minimum image of x_j - x_k): the pair term is R(d) = sum_n N_S(d + n L)
+ * + P(d) - N(d), so, differentiating each term (Sec. II periodic boundaries,
+ * Ewald split; J is symmetric and even in d):
+ *   N_S(e) = e h(q):       J = h I + (h'(q)/q) e e^T,
+ *       h = erfc(alpha q)/q^3 + c_g exp(-alpha^2 q^2)/q^2,
+ *       h'(q)/q = -3 h/q^2 - 2 alpha^2 c_g exp(-alpha^2 q^2)/q^2;
+ *   P(d) = d/s^3:          J = I/s^3 - 3 d d^T/s^5,  s^2 = |d|^2 + eps^2;
+ *   N(d) = d/|d|^3:        J = I/r^3 - 3 d d^T/r^5.
+ * Every q = 0 image is left out, as in the force.  At d = 0 exactly (two
+ * distinct bodies at one point) the nearest image's P - N + N_S is taken at
+ * its limit, (1/eps^3 - (4/3) alpha^3/sqrt(pi)) I.  Also returns R(d) in Rv. */
+static void ewald_real_pair_jacobian(const double d[3], double eps2, double L, double alpha,
+                                     int64_t nreal, double J[3][3], double Rv[3])
+{
+    const double pi = acos(-1.0);
+    const double c_g = 2.0 * alpha / sqrt(pi);
+    for (int a = 0; a < 3; ++a) {
+        Rv[a] = 0.0;
+        for (int b = 0; b < 3; ++b) J[a][b] = 0.0;
+    }
+    const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (d2 > 0.0) {
+        const double s2 = d2 + eps2, s = sqrt(s2), r = sqrt(d2);
+        const double is3 = 1.0 / (s2 * s), is5 = is3 / s2;
+        const double ir3 = 1.0 / (d2 * r), ir5 = ir3 / d2;
+        for (int a = 0; a < 3; ++a) {
+            Rv[a] += (is3 - ir3) * d[a];
+            J[a][a] += is3 - ir3;
+            for (int b = 0; b < 3; ++b) J[a][b] += -3.0 * (is5 - ir5) * d[a] * d[b];
+        }
+    } else {
+        const double lim = 1.0 / (eps2 * sqrt(eps2)) - 4.0 / 3.0 * alpha * alpha * alpha / sqrt(pi);
+        for (int a = 0; a < 3; ++a) J[a][a] += lim;
+    }
+    for (int64_t i0 = -nreal; i0 <= nreal; ++i0)
+        for (int64_t i1 = -nreal; i1 <= nreal; ++i1)
+            for (int64_t i2 = -nreal; i2 <= nreal; ++i2) {
+                const double e[3] = {d[0] + L * (double)i0, d[1] + L * (double)i1,
+                                     d[2] + L * (double)i2};
+                const double q2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+                if (q2 == 0.0) continue;
+                const double q = sqrt(q2);
+                const double g = exp(-alpha * alpha * q2);
+                const double h = erfc(alpha * q) / (q2 * q) + c_g * g / q2;
+                const double hq = -3.0 * h / q2 - 2.0 * alpha * alpha * c_g * g / q2;
+                for (int a = 0; a < 3; ++a) {
+                    Rv[a] += h * e[a];
+                    J[a][a] += h;
+                    for (int b = 0; b < 3; ++b) J[a][b] += hq * e[a] * e[b];
+                }
+            }
+}
+
+static void min_image(const double *x, int64_t j, int64_t k, double L, double d[3])
+{
+    for (int c = 0; c < 3; ++c) {
+        d[c] = x[3 * j + c] - x[3 * k + c];
+        d[c] -= L * nearbyint(d[c] / L);
+    }
+}
+
+/* Real-space part of the periodic force's directional derivative along
+ * (dx, dm) (dm may be NULL), for target rows k:
+ *   out_k = G sum_{j != k} [ m_j J_R(d_kj) (dx_j - dx_k) + dm_j R(d_kj) ]. */
+void colatus_oracle_ewald_real_jvp_rows(int64_t n, const double *x, const double *m,
+                                        const double *dx, const double *dm, double eps, double G,
+                                        double L, double alpha, int64_t nreal,
+                                        const int64_t *rows, int64_t nrows, double *out)
+{
+    const double eps2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t r = 0; r < nrows; ++r) {
+        const int64_t k = rows[r];
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == k) continue;
+            double d[3], J[3][3], Rv[3];
+            min_image(x, j, k, L, d);
+            ewald_real_pair_jacobian(d, eps2, L, alpha, nreal, J, Rv);
+            const double u[3] = {dx[3 * j] - dx[3 * k], dx[3 * j + 1] - dx[3 * k + 1],
+                                 dx[3 * j + 2] - dx[3 * k + 2]};
+            for (int a = 0; a < 3; ++a) {
+                acc[a] += m[j] * (J[a][0] * u[0] + J[a][1] * u[1] + J[a][2] * u[2]);
+                if (dm) acc[a] += dm[j] * Rv[a];
+            }
+        }
+        for (int a = 0; a < 3; ++a) out[3 * r + a] = G * acc[a];
+    }
+}
+
+/* Real-space part of the periodic force's vector-Jacobian product: for
+ * L = sum_k lam_k . F_k and target rows i,
+ *   gx_i = G sum_{j != i} J_R(d_ij) (m_i lam_j - m_j lam_i),
+ *   gm_i = -G sum_{j != i} lam_j . R(d_ij). */
+void colatus_oracle_ewald_real_vjp_rows(int64_t n, const double *x, const double *m,
+                                        const double *lam, double eps, double G, double L,
+                                        double alpha, int64_t nreal, const int64_t *rows,
+                                        int64_t nrows, double *gx, double *gm)
+{
+    const double eps2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t r = 0; r < nrows; ++r) {
+        const int64_t i = rows[r];
+        double acc[3] = {0.0, 0.0, 0.0}, am = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3], J[3][3], Rv[3];
+            min_image(x, j, i, L, d);
+            ewald_real_pair_jacobian(d, eps2, L, alpha, nreal, J, Rv);
+            double u[3];
+            for (int a = 0; a < 3; ++a) u[a] = m[i] * lam[3 * j + a] - m[j] * lam[3 * i + a];
+            for (int a = 0; a < 3; ++a)
+                acc[a] += J[a][0] * u[0] + J[a][1] * u[1] + J[a][2] * u[2];
+            am += lam[3 * j] * Rv[0] + lam[3 * j + 1] * Rv[1] + lam[3 * j + 2] * Rv[2];
+        }
+        for (int a = 0; a < 3; ++a) gx[3 * r + a] = G * acc[a];
+        gm[r] = -G * am;
+    }
+}
+
 /* Number of OpenMP threads the parallel loops above use. */
 int colatus_oracle_threads(void)
 {

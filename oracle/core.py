@@ -30,7 +30,7 @@ __all__ = [
     "adjoint_run", "tangent_run", "ftle", "num_threads", "set_threads", "PINS",
     "deformation_force", "deformation_vjp", "deformation_jvp", "total_force",
     "velocity_spectrum", "friedmann_integrals", "canonical_coefficients",
-    "ewald_forces",
+    "ewald_forces", "ewald_jvp", "ewald_vjp",
 ]
 
 # Parity pin of every oracle function: which non-oracle fact each one is
@@ -67,6 +67,14 @@ PINS = {
                     "and between bodies half a box apart; periodic in every body's position "
                     "and translation invariant; Newton's third law; at separations << L "
                     "the isolated Plummer force plus the background term (4 pi/3V) m d",
+    "ewald_jvp": "central finite differences of ewald_forces in x and m; independent of "
+                 "the splitting parameter alpha; zero row sum of the mass-weighted Jacobian "
+                 "(translation); the isolated Jacobian plus (4 pi/3V) m I at separations << L",
+    "ewald_vjp": "duality <lam, J u> = <J^T lam, u> with ewald_jvp in x and m; central "
+                 "finite differences of lam . ewald_forces; alpha independence; sum of "
+                 "dL/dx is zero (translation invariance)",
+    "adjoint_run / tangent_run (box)": "central finite differences of a periodic trajectory "
+                                       "loss; adjoint-tangent duality",
     "velocity_spectrum": "pure sinusoid closed form (peak height, Hann side lobes 1/4), "
                          "Parseval identity with and without the window, numpy.fft.rfft, "
                          "constant series",
@@ -104,12 +112,17 @@ def _load():
         L.colatus_oracle_jvp_rows.argtypes = [i64, _dp, _dp, _dp, _dp, dbl, dbl, _ip, i64, _dp]
         L.colatus_oracle_ewald_real_rows.argtypes = [i64, _dp, _dp, dbl, dbl, dbl, dbl, i64, _ip,
                                                      i64, _dp]
+        L.colatus_oracle_ewald_real_jvp_rows.argtypes = [i64, _dp, _dp, _dp, _dp, dbl, dbl, dbl, dbl,
+                                                         i64, _ip, i64, _dp]
+        L.colatus_oracle_ewald_real_vjp_rows.argtypes = [i64, _dp, _dp, _dp, dbl, dbl, dbl, dbl, i64,
+                                                         _ip, i64, _dp, _dp]
         L.colatus_oracle_threads.restype = ctypes.c_int
         L.colatus_oracle_set_threads.argtypes = [ctypes.c_int]
         L.colatus_oracle_set_threads.restype = None
         for f in (L.colatus_oracle_forces_pairwise, L.colatus_oracle_forces_rows,
                   L.colatus_oracle_potential_rows, L.colatus_oracle_vjp_rows,
-                  L.colatus_oracle_jvp_rows, L.colatus_oracle_ewald_real_rows):
+                  L.colatus_oracle_jvp_rows, L.colatus_oracle_ewald_real_rows,
+                  L.colatus_oracle_ewald_real_jvp_rows, L.colatus_oracle_ewald_real_vjp_rows):
             f.restype = None
         _lib = L
     return _lib
@@ -456,19 +469,22 @@ def layzer_irvine(diags, t):
 # ---------------------------------------------------- discrete adjoint
 def adjoint_run(x0, v0, m, eps: float, G: float, cosmo: Cosmology, a_start: float,
                 tau: float, nsteps: int, gx_T, gv_T, gm_T=None,
-                scheme: str = "kdk", nsub: int = 8, defo=None):
+                scheme: str = "kdk", nsub: int = 8, defo=None, box=None):
     """Exact transpose of the discrete leapfrog of ``run``.
 
     Given dLoss/dx^N, dLoss/dv^N (and an explicit dLoss/dm), returns
     (dLoss/dx^0, dLoss/dv^0, dLoss/dm) of the same FP64 trajectory.  The
     scale factor does not depend on the particles, so c, d carry no gradient.
-    Every state of the forward pass is stored (no checkpointing).
+    Every state of the forward pass is stored (no checkpointing).  box = L:
+    periodic boundaries (``ewald_forces`` and ``ewald_vjp``).
     """
     m = _d(m).reshape(-1)
     fw = run(x0, v0, m, eps, G, cosmo, a_start, tau, nsteps, scheme, nsub, keep_states=True,
-             defo=defo)
+             defo=defo, box=box)
 
     def vjp_total(xx, w):
+        if box is not None:
+            return ewald_vjp(xx, m, w, eps, box, G)
         gx_, gm_ = vjp(xx, m, w, eps, G)
         if defo is not None:
             gx_ = gx_ + deformation_vjp(xx, defo[0], defo[1], eps, w)
@@ -495,7 +511,7 @@ def adjoint_run(x0, v0, m, eps: float, G: float, cosmo: Cosmology, a_start: floa
             lx = lxh
             lv = lv + 0.5 * tau * lxh
         else:
-            vh = sch["c1"][n] * v + sch["d1"][n] * total_force(x, m, eps, G, defo)
+            vh = sch["c1"][n] * v + sch["d1"][n] * total_force(x, m, eps, G, defo, box)
             x1 = x + tau * vh
             # v^{n+1} = c2 vh + d2 F(x^{n+1})
             lvh = sch["c2"][n] * lv
@@ -518,9 +534,10 @@ def adjoint_run(x0, v0, m, eps: float, G: float, cosmo: Cosmology, a_start: floa
 # --------------------------------------------------------- tangent model
 def tangent_run(x0, v0, m, eps: float, G: float, cosmo: Cosmology, a_start: float,
                 tau: float, nsteps: int, dx0, dv0, scheme: str = "kdk", nsub: int = 8,
-                dm=None, defo=None):
+                dm=None, defo=None, box=None):
     """Linearisation of ``run`` along (dx0, dv0[, dm]): returns the final
-    tangent (dx, dv) and the per-step tangent states [nsteps+1] of (dx, dv)."""
+    tangent (dx, dv) and the per-step tangent states [nsteps+1] of (dx, dv).
+    box = L: periodic boundaries (``ewald_forces`` and ``ewald_jvp``)."""
     m = _d(m).reshape(-1)
     x = _d(x0).reshape(-1, 3).copy()
     v = _d(v0).reshape(-1, 3).copy()
@@ -530,7 +547,9 @@ def tangent_run(x0, v0, m, eps: float, G: float, cosmo: Cosmology, a_start: floa
     hist = [(dx.copy(), dv.copy())]
 
     def fj(xx, ddx):
-        F_ = total_force(xx, m, eps, G, defo)
+        F_ = total_force(xx, m, eps, G, defo, box)
+        if box is not None:
+            return F_, ewald_jvp(xx, m, ddx, eps, box, G, dm=dm)
         dF_ = jvp(xx, m, ddx, eps, G, dm=dm)
         if defo is not None:
             dF_ = dF_ + deformation_jvp(xx, defo[0], defo[1], eps, ddx)
@@ -560,7 +579,7 @@ def tangent_run(x0, v0, m, eps: float, G: float, cosmo: Cosmology, a_start: floa
 
 def ftle(x0, v0, m, eps: float, G: float, cosmo: Cosmology, a_start: float,
          tau: float, nsteps: int, tracer: int, direction=(1.0, 0.0, 0.0),
-         scheme: str = "kdk", nsub: int = 8) -> np.ndarray:
+         scheme: str = "kdk", nsub: int = 8, box=None) -> np.ndarray:
     """Finite-time Lyapunov growth of one tracer's own phase-space perturbation.
 
     The tangent is seeded with a unit position perturbation on the tracer only
@@ -571,7 +590,7 @@ def ftle(x0, v0, m, eps: float, G: float, cosmo: Cosmology, a_start: float,
     dx0 = np.zeros((n_, 3))
     dx0[tracer] = np.asarray(direction, dtype=np.float64) / np.linalg.norm(direction)
     _, _, hist = tangent_run(x0, v0, m, eps, G, cosmo, a_start, tau, nsteps,
-                             dx0, np.zeros((n_, 3)), scheme, nsub)
+                             dx0, np.zeros((n_, 3)), scheme, nsub, box=box)
     g0 = math.sqrt(float(np.sum(hist[0][0][tracer] ** 2) + np.sum(hist[0][1][tracer] ** 2)))
     out = np.empty(nsteps)
     for n in range(1, nsteps + 1):
@@ -663,3 +682,98 @@ def ewald_forces(x, m, eps: float, L: float, G: float = 1.0, alpha=None, nreal: 
         s = np.imag(np.exp(1j * (k @ xt.T)) * np.conj(rho)[:, None])  # sum_j m_j sin(k.(x_t - x_j))
         out -= (w[:, None] * s).T @ k
     return out
+
+
+def _ewald_defaults(L, alpha, nk):
+    alpha = 6.0 / L if alpha is None else float(alpha)
+    if nk is None:
+        nk = int(math.ceil(alpha * L / math.pi * math.sqrt(18.0 * math.log(10.0))))
+    return alpha, nk
+
+
+def _kvectors(L, nk):
+    r = np.arange(-nk, nk + 1)
+    n = np.stack(np.meshgrid(r, r, r, indexing="ij"), axis=-1).reshape(-1, 3)
+    return n[np.any(n != 0, axis=1)]
+
+
+def ewald_jvp(x, m, dx, eps: float, L: float, G: float = 1.0, alpha=None, nreal: int = 1,
+              nk=None, rows=None, dm=None) -> np.ndarray:
+    """Directional derivative of ``ewald_forces`` along (dx, dm).
+
+    The periodic force is F_k = G sum_j m_j Phi(x_j - x_k) with Phi odd; its
+    derivative is G sum_j [m_j J(d_kj) (dx_j - dx_k) + dm_j Phi(d_kj)], J the
+    Jacobian of Phi.  Real space: C loops over the same images as the force
+    (colatus_oracle_ewald_real_jvp_rows).  Reciprocal space, differentiating
+    the k-sum of ``ewald_forces`` term by term:
+        (4 pi G / L^3) sum_k A(k) k sum_j [ m_j cos(k.(x_j - x_k)) k.(dx_j - dx_k)
+                                            + dm_j sin(k.(x_j - x_k)) ],
+    A(k) = exp(-k^2/(4 alpha^2)) / k^2."""
+    x, m, dx = _d(x).reshape(-1, 3), _d(m).reshape(-1), _d(dx).reshape(-1, 3)
+    rows = _rows(len(m), rows)
+    alpha, nk = _ewald_defaults(L, alpha, nk)
+    keep = None if dm is None else _d(dm).reshape(-1)
+    out = np.empty((len(rows), 3))
+    _load().colatus_oracle_ewald_real_jvp_rows(len(m), _ptr(x), _ptr(m), _ptr(dx),
+                                               None if keep is None else _ptr(keep), float(eps),
+                                               float(G), float(L), alpha, int(nreal),
+                                               _ptr(rows, _ip), len(rows), _ptr(out))
+    n = _kvectors(L, nk)
+    V = L ** 3
+    xt, dxt = x[rows], dx[rows]
+    for c0 in range(0, len(n), 2048):
+        k = 2.0 * np.pi / L * n[c0:c0 + 2048]                       # [K, 3]
+        k2 = np.sum(k * k, axis=1)
+        A = 4.0 * np.pi * G / V * np.exp(-k2 / (4.0 * alpha * alpha)) / k2
+        cj, sj = np.cos(k @ x.T), np.sin(k @ x.T)                    # [K, N]
+        ct, st = np.cos(k @ xt.T), np.sin(k @ xt.T)                  # [K, R]
+        kdx = k @ dx.T                                               # k . dx_j
+        P = (cj * kdx) @ m                                           # sum_j m_j (k.dx_j) cos
+        Q = (sj * kdx) @ m                                           # sum_j m_j (k.dx_j) sin
+        C, S = cj @ m, sj @ m
+        # sum_j m_j cos(k.(x_j - x_t)) k.dx_j = cos_t P + sin_t Q
+        # sum_j m_j cos(k.(x_j - x_t)) k.dx_t = (k.dx_t) (cos_t C + sin_t S)
+        term = ct * P[:, None] + st * Q[:, None] - (k @ dxt.T) * (ct * C[:, None] + st * S[:, None])
+        if keep is not None:
+            Cd, Sd = cj @ keep, sj @ keep
+            # sum_j dm_j sin(k.(x_j - x_t)) = cos_t Sd - sin_t Cd
+            term = term + ct * Sd[:, None] - st * Cd[:, None]
+        out += (A[:, None] * term).T @ k
+    return out
+
+
+def ewald_vjp(x, m, lam, eps: float, L: float, G: float = 1.0, alpha=None, nreal: int = 1,
+              nk=None, rows=None):
+    """(dL/dx, dL/dm) of L = sum_k lam_k . F_k for the periodic force of
+    ``ewald_forces``: with F_k = G sum_j m_j Phi(x_j - x_k),
+        dL/dx_i = G sum_j J(d_ij) (m_i lam_j - m_j lam_i),
+        dL/dm_i = -G sum_j lam_j . Phi(d_ij).
+    Real space by C loops (colatus_oracle_ewald_real_vjp_rows); reciprocal
+    space from the k-sum, with cos/sin(k.(x_j - x_i)) expanded per k."""
+    x, m, lam = _d(x).reshape(-1, 3), _d(m).reshape(-1), _d(lam).reshape(-1, 3)
+    rows = _rows(len(m), rows)
+    alpha, nk = _ewald_defaults(L, alpha, nk)
+    gx, gm = np.empty((len(rows), 3)), np.empty(len(rows))
+    _load().colatus_oracle_ewald_real_vjp_rows(len(m), _ptr(x), _ptr(m), _ptr(lam), float(eps),
+                                               float(G), float(L), alpha, int(nreal),
+                                               _ptr(rows, _ip), len(rows), _ptr(gx), _ptr(gm))
+    n = _kvectors(L, nk)
+    V = L ** 3
+    xt, lt, mt = x[rows], lam[rows], m[rows]
+    for c0 in range(0, len(n), 2048):
+        k = 2.0 * np.pi / L * n[c0:c0 + 2048]
+        k2 = np.sum(k * k, axis=1)
+        A = 4.0 * np.pi * G / V * np.exp(-k2 / (4.0 * alpha * alpha)) / k2
+        cj, sj = np.cos(k @ x.T), np.sin(k @ x.T)
+        ct, st = np.cos(k @ xt.T), np.sin(k @ xt.T)
+        kl = k @ lam.T                                               # k . lam_j
+        Pw, Qw = np.sum(cj * kl, axis=1), np.sum(sj * kl, axis=1)
+        C, S = cj @ m, sj @ m
+        # sum_j cos(k.(x_j - x_i)) [m_i k.lam_j - m_j k.lam_i]
+        term = (mt[None, :] * (ct * Pw[:, None] + st * Qw[:, None])
+                - (k @ lt.T) * (ct * C[:, None] + st * S[:, None]))
+        gx += (A[:, None] * term).T @ k
+        # -sum_j k.lam_j sin(k.(x_j - x_i)) = -(cos_i Qw - sin_i Pw)
+        gm -= A @ (ct * Qw[:, None] - st * Pw[:, None])
+    return gx, gm
+
