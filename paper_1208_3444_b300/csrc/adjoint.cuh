@@ -495,6 +495,7 @@ __global__ void vjp_out_f32_kernel(const float4 *__restrict__ part, ForceLaunch 
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     float4 g = reduce_vjp_f32(part, L, itile, i);
+    add_kspace_vjp(D, i, g);
     if (D.on) {
         float x, y, z, wx, wy, wz;
         pkw_load(pkw, i, x, y, z, wx, wy, wz);
@@ -509,6 +510,7 @@ __global__ void vjp_out_f64_kernel(const double4 *__restrict__ part, ForceLaunch
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     double4 g = reduce_vjp_f64(part, L, itile, i);
+    add_kspace_vjp(D, i, g);
     if (D.on) {
         const double4 p = bw[2 * i], w = bw[2 * i + 1];
         defo_jacobian<double>(D, p.x, p.y, p.z, w.x, w.y, w.z, g.x, g.y, g.z);
@@ -579,6 +581,7 @@ __global__ void adj_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
         return;
     }
     float4 g = reduce_vjp_f32(part, L, itile, i);
+    add_kspace_vjp(D, i, g);
     if (D.on) {   // deformation term at x_{n+1} with W_{n+1} (still in pkw)
         float x, y, z, wx, wy, wz;
         pkw_load(pkw, i, x, y, z, wx, wy, wz);
@@ -607,6 +610,7 @@ __global__ void adj_final_f32_kernel(const float4 *__restrict__ part, ForceLaunc
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     float4 g = reduce_vjp_f32(part, L, itile, i);
+    add_kspace_vjp(D, i, g);
     if (D.on) {
         float x, y, z, wx, wy, wz;
         pkw_load(pkw, i, x, y, z, wx, wy, wz);
@@ -655,6 +659,7 @@ __global__ void adj_step_f64_kernel(const double4 *__restrict__ part, ForceLaunc
         return;
     }
     double4 g = reduce_vjp_f64(part, L, itile, i);
+    add_kspace_vjp(D, i, g);
     if (D.on) {
         const double4 p = bw[2 * i], w = bw[2 * i + 1];
         defo_jacobian<double>(D, p.x, p.y, p.z, w.x, w.y, w.z, g.x, g.y, g.z);
@@ -683,6 +688,7 @@ __global__ void adj_final_f64_kernel(const double4 *__restrict__ part, ForceLaun
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     double4 g = reduce_vjp_f64(part, L, itile, i);
+    add_kspace_vjp(D, i, g);
     if (D.on) {
         const double4 p = bw[2 * i], w = bw[2 * i + 1];
         defo_jacobian<double>(D, p.x, p.y, p.z, w.x, w.y, w.z, g.x, g.y, g.z);

@@ -13,6 +13,7 @@
 #include "diagnostics.cuh"
 #include "ensemble.cuh"
 #include "ewald.cuh"
+#include "ewald_adjoint.cuh"
 #include "force.cuh"
 #include "integrate.cuh"
 #include "probe.cuh"
@@ -104,6 +105,12 @@ using EwK = EwaldF32Kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, false>;
 using EwKC = EwaldF32Kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, true>;
 constexpr int kEw64NT = 128, kEw64JT = 32;
 using Ew64K = EwaldF64Kernel<kEw64NT, kEw64JT, kStages>;
+// Periodic VJP (real space): FP32 256 threads x 2 i-bodies, 256-body tiles of
+// the VJP layout; FP64 128 x 1, 32-body tiles.
+constexpr int kEwVjpNT = 256, kEwVjpIPT = 2, kEwVjpJT = 256, kEwVjpMinB = 1;
+using EwVjpK = EwaldVjpKernel<kEwVjpNT, kEwVjpIPT, kEwVjpJT, kStages>;
+constexpr int kEwV64NT = 128, kEwV64JT = 32;
+using EwVjp64K = EwaldVjp64Kernel<kEwV64NT, kEwV64JT, kStages>;
 constexpr int kEwMaxNk = 63;   // shared memory of the k-space kernels in FP64; a pencil fits one block
 constexpr int kEwRhoBlocksPerSM = 8;   // structure-factor blocks per SM (k chunks x body splits)
 
@@ -244,6 +251,7 @@ struct colatus_ctx {
     ForcePlan plan32[NUM_F32_VARIANTS];
     ForcePlan plan64;
     ForcePlan plan_vjp32, plan_vjp64;
+    ForcePlan plan_ewvjp32, plan_ewvjp64;   // periodic VJP (real space)
 
     // periodic boundaries (colatus_set_periodic): Ewald parameters and buffers
     bool periodic = false;
@@ -262,6 +270,9 @@ struct colatus_ctx {
     int *rchunk = nullptr, *fchunk = nullptr;   // first pencil of each k-space chunk (+ end)
     int npen = 0, nrchunk = 0, nfchunk = 0, rchunk_np = 0;   // rchunk_np: most pencils in one chunk
     void *lr = nullptr;                     // n_alloc float4 / double4 long-range forces
+    void *lrv = nullptr;                    // n_alloc float4 / double4 reciprocal VJP (dL/dx, dL/dm)
+    void *kwr = nullptr, *kwl = nullptr;    // [nkv] w_k rho(k), w_k Lambda(k) of the VJP
+    size_t kwrl_cap = 0;
     void *ph = nullptr;                     // [n_alloc][3][nk+1] phase tables (float2 / double2)
     size_t ph_bytes = 0;
     size_t kv_cap = 0;
@@ -401,6 +412,23 @@ colatus_status build_plans(colatus_t ctx) {
     w.jt = kV64JT;
     w.n_pad = round_up(ctx->N, std::max(w.itile, w.jt));
     finish_plan(w, occ, ctx->num_sms, sizeof(double4));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, ewald_vjp_f32_kernel<kEwVjpNT, kEwVjpIPT, kEwVjpJT, kStages, kEwVjpMinB>, kEwVjpNT,
+        EwVjpK::SMEM));
+    if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "periodic VJP kernel cannot be resident");
+    ForcePlan &ev = ctx->plan_ewvjp32;
+    ev.itile = EwVjpK::ITILE;
+    ev.jt = kEwVjpJT;
+    ev.n_pad = round_up(ctx->N, std::max(ev.itile, ev.jt));
+    finish_plan(ev, occ, ctx->num_sms, sizeof(float4));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, ewald_vjp_f64_kernel<kEwV64NT, kEwV64JT, kStages>, kEwV64NT, EwVjp64K::SMEM));
+    if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "FP64 periodic VJP kernel cannot be resident");
+    ForcePlan &ew = ctx->plan_ewvjp64;
+    ew.itile = EwVjp64K::ITILE;
+    ew.jt = kEwV64JT;
+    ew.n_pad = round_up(ctx->N, std::max(ew.itile, ew.jt));
+    finish_plan(ew, occ, ctx->num_sms, sizeof(double4));
 
     for (int comp = 0; comp < 2; ++comp) {
         const void *fn = comp ? (const void *)ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold,
@@ -594,6 +622,9 @@ colatus_status ewald_setup(colatus_t ctx) {
     A.s1 = (float)(0.8 * std::pow(alpha, 5) / std::sqrt(pi));
     A.x2_series = (float)((0.05 / alpha) * (0.05 / alpha));
     A.nk = nk;
+    A.c2ag = (float)(2.0 * alpha * alpha * 2.0 * alpha / std::sqrt(pi));
+    A.ncs0 = (float)(-1.6 * std::pow(alpha, 5) / std::sqrt(pi));
+    A.ncs1 = (float)(8.0 / 7.0 * std::pow(alpha, 7) / std::sqrt(pi));
     // shared memory of the k-space kernels grows with nk
     const int nt = nk + 1;
     const size_t es = f64 ? sizeof(double) : sizeof(float);
@@ -604,6 +635,10 @@ colatus_status ewald_setup(colatus_t ctx) {
                          : (const void *)ewald_kforce_kernel<float, float4>;
     CU(cudaFuncSetAttribute(frho, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rho));
     CU(cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f));
+    const void *fkv = f64 ? (const void *)ewald_kvjp_kernel<double, double4>
+                          : (const void *)ewald_kvjp_kernel<float, float4>;
+    const size_t smem_kv = f64 ? ew_kvjp_smem<double>(nk) : ew_kvjp_smem<float>(nk);
+    CU(cudaFuncSetAttribute(fkv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_kv));
     return COLATUS_OK;
 }
 
@@ -615,8 +650,8 @@ colatus_status run_ewald_kspace(colatus_t ctx, const float *pk, const double4 *p
     using T2 = typename Vec2<T>::type;
     const int nt = ctx->ew.nk + 1;
     T2 *ph = static_cast<T2 *>(ctx->ph);
-    ewald_phase_kernel<T><<<blocks_for(3 * ctx->N, 128), 128, 0, ctx->stream>>>(pk, pos, ctx->N,
-                                                                                ctx->ew, ph);
+    ewald_phase_kernel<T><<<blocks_for(3 * ctx->N, 128), 128, 0, ctx->stream>>>(
+        masses_of(pk, pos), ctx->N, ctx->ew, ph);
     TRY(launched(ctx));
     const int kchunks = ctx->nrchunk;
     const long long max_split = std::max(1LL, ctx->N / ew_bodies<T>());
@@ -625,7 +660,7 @@ colatus_status run_ewald_kspace(colatus_t ctx, const float *pk, const double4 *p
     TRY(grow(ctx, &ctx->rho_part, &ctx->rho_part_bytes, (size_t)splits * ctx->nkv * sizeof(double2)));
     const size_t smem_rho = ew_rho_smem<T>(ctx->ew.nk, ctx->rchunk_np);
     ewald_rho_kernel<T><<<dim3(kchunks, splits), kEwKThreads, smem_rho, ctx->stream>>>(
-        pk, pos, ctx->N, ph, ctx->pen, ctx->rchunk, ctx->rchunk_np, ctx->nkv, ctx->ew,
+        masses_of(pk, pos), ctx->N, ph, ctx->pen, ctx->rchunk, ctx->rchunk_np, ctx->nkv, ctx->ew,
         static_cast<double2 *>(ctx->rho_part));
     TRY(launched(ctx));
     T2 *wcs = reinterpret_cast<T2 *>(ctx->wcs);
@@ -834,7 +869,8 @@ void free_all(colatus_t ctx) {
                     ctx->pos64[2], ctx->m64, ctx->part, ctx->flags, ctx->mstat, ctx->clk,
                     ctx->tclk, ctx->table, ctx->stage, ctx->stage2, ctx->diag, ctx->tslot,
                     ctx->rec, ctx->kw, ctx->rho, ctx->rho_part, ctx->wcs, ctx->pen,
-                    ctx->rchunk, ctx->fchunk, ctx->lr, ctx->ph, ctx->pot_part};
+                    ctx->rchunk, ctx->fchunk, ctx->lr, ctx->ph, ctx->pot_part, ctx->lrv,
+                    ctx->kwr, ctx->kwl};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *tptrs[] = {ctx->tan.dx, ctx->tan.dv, ctx->tan.dvh, ctx->tan.pkt, ctx->tan.seeds,
@@ -1150,13 +1186,88 @@ colatus_status grow(colatus_t ctx, void **p, size_t *have, size_t need) {
     return COLATUS_OK;
 }
 
-// One VJP launch on the packed bodies + co-vectors in adj.pkw.
+// The VJP's launch plan: the periodic kernel's when the boundaries are periodic.
+const ForcePlan &vjp_plan(colatus_t ctx) {
+    const bool f64 = ctx->prec == COLATUS_FP64;
+    if (ctx->periodic) return f64 ? ctx->plan_ewvjp64 : ctx->plan_ewvjp32;
+    return f64 ? ctx->plan_vjp64 : ctx->plan_vjp32;
+}
+
+// Per-body terms of the VJP consumers: the deformation term and, with
+// periodic boundaries, the reciprocal-space VJP (lrv).
+Extra vjp_extra(colatus_t ctx) {
+    Extra D = extra_args(ctx);
+    D.lr32 = ctx->periodic && ctx->prec != COLATUS_FP64 ? static_cast<const float4 *>(ctx->lrv) : nullptr;
+    D.lr64 = ctx->periodic && ctx->prec == COLATUS_FP64 ? static_cast<const double4 *>(ctx->lrv) : nullptr;
+    return D;
+}
+
+// Reciprocal-space VJP of the bodies and co-vectors packed in adj.pkw, into
+// lrv: phase tables of the packed positions, four structure-factor passes
+// (weights m, w_x, w_y, w_z), their weights per k, then one pass per body.
+template <typename T, typename T4>
+colatus_status run_ewald_kspace_vjp(colatus_t ctx) {
+    using T2 = typename Vec2<T>::type;
+    const bool f64 = sizeof(T) == 8;
+    if (!ctx->lrv) CU(cudaMalloc(&ctx->lrv, (size_t)ctx->n_alloc * sizeof(double4)));
+    if (ctx->kwrl_cap < (size_t)ctx->nkv) {
+        if (ctx->kwr) cudaFree(ctx->kwr);
+        if (ctx->kwl) cudaFree(ctx->kwl);
+        ctx->kwr = ctx->kwl = nullptr;
+        ctx->kwrl_cap = 0;
+        CU(cudaMalloc(&ctx->kwr, ctx->nkv * sizeof(double2)));
+        CU(cudaMalloc(&ctx->kwl, ctx->nkv * sizeof(double2)));
+        ctx->kwrl_cap = ctx->nkv;
+    }
+    BodySrc src{f64 ? nullptr : static_cast<const float *>(ctx->adj.pkw),
+                f64 ? static_cast<const double4 *>(ctx->adj.pkw) : nullptr, f64 ? 2 : 16, f64 ? 3 : 6};
+    T2 *ph = static_cast<T2 *>(ctx->ph);
+    ewald_phase_kernel<T><<<blocks_for(3 * ctx->N, 128), 128, 0, ctx->stream>>>(src, ctx->N, ctx->ew, ph);
+    TRY(launched(ctx));
+    const int kchunks = ctx->nrchunk;
+    const long long max_split = std::max(1LL, ctx->N / ew_bodies<T>());
+    const int splits = (int)std::min<long long>(std::max(1, kEwRhoBlocksPerSM * ctx->num_sms / kchunks),
+                                                max_split);
+    const size_t plane = (size_t)splits * ctx->nkv;
+    TRY(grow(ctx, &ctx->rho_part, &ctx->rho_part_bytes, 4 * plane * sizeof(double2)));
+    const size_t smem_rho = ew_rho_smem<T>(ctx->ew.nk, ctx->rchunk_np);
+    const int widx[4] = {f64 ? 3 : 6, f64 ? 4 : 8, f64 ? 5 : 10, f64 ? 6 : 12};
+    for (int c = 0; c < 4; ++c) {
+        src.widx = widx[c];
+        ewald_rho_kernel<T><<<dim3(kchunks, splits), kEwKThreads, smem_rho, ctx->stream>>>(
+            src, ctx->N, ph, ctx->pen, ctx->rchunk, ctx->rchunk_np, ctx->nkv, ctx->ew,
+            static_cast<double2 *>(ctx->rho_part) + c * plane);
+        TRY(launched(ctx));
+    }
+    ewald_vjp_weights_kernel<T><<<blocks_for(ctx->npen, 128), 128, 0, ctx->stream>>>(
+        static_cast<const double2 *>(ctx->rho_part), splits, ctx->nkv, ctx->kw, ctx->pen, ctx->npen,
+        2.0 * std::acos(-1.0) / ctx->ew.L, static_cast<T2 *>(ctx->kwr), static_cast<T2 *>(ctx->kwl));
+    TRY(launched(ctx));
+    src.widx = widx[0];
+    ewald_kvjp_kernel<T, T4><<<blocks_for(ctx->N, kEwFThreads), kEwFThreads * kEwFSlices,
+                               ew_kvjp_smem<T>(ctx->ew.nk), ctx->stream>>>(
+        ctx->N, ph, ctx->pen, ctx->npen, static_cast<const T2 *>(ctx->kwr),
+        static_cast<const T2 *>(ctx->kwl), src, ctx->ew, static_cast<T4 *>(ctx->lrv));
+    return launched(ctx);
+}
+
+// One VJP launch on the packed bodies + co-vectors in adj.pkw (with periodic
+// boundaries: the real-space kernel, then the reciprocal-space VJP).
 colatus_status run_vjp(colatus_t ctx) {
     const bool f64 = ctx->prec == COLATUS_FP64;
-    const ForcePlan &p = f64 ? ctx->plan_vjp64 : ctx->plan_vjp32;
+    const ForcePlan &p = vjp_plan(ctx);
     TRY(ensure_part(ctx, p.part_bytes));
     TRY(prof_begin(ctx));
-    if (f64)
+    if (ctx->periodic && f64)
+        ewald_vjp_f64_kernel<kEwV64NT, kEwV64JT, kStages><<<p.L.G, kEwV64NT, EwVjp64K::SMEM, ctx->stream>>>(
+            static_cast<const double4 *>(ctx->adj.pkw), static_cast<double4 *>(ctx->part), ctx->flags,
+            p.L, ctx->eps * ctx->eps, ctx->ew);
+    else if (ctx->periodic)
+        ewald_vjp_f32_kernel<kEwVjpNT, kEwVjpIPT, kEwVjpJT, kStages, kEwVjpMinB>
+            <<<p.L.G, kEwVjpNT, EwVjpK::SMEM, ctx->stream>>>(
+                static_cast<const float *>(ctx->adj.pkw), static_cast<float4 *>(ctx->part), ctx->flags,
+                p.L, (float)(ctx->eps * ctx->eps), ctx->ew);
+    else if (f64)
         vjp_f64_kernel<kV64NT, kV64JT, kStages><<<p.L.G, kV64NT, Vjp64K::SMEM, ctx->stream>>>(
             static_cast<const double4 *>(ctx->adj.pkw), static_cast<double4 *>(ctx->part),
             ctx->flags, p.L, ctx->eps * ctx->eps);
@@ -1167,7 +1278,9 @@ colatus_status run_vjp(colatus_t ctx) {
                 ctx->flags, p.L, (float)(ctx->eps * ctx->eps));
     TRY(launched(ctx));
     ctx->interactions += (double)ctx->N * (double)ctx->N;
-    return prof_end(ctx, 1);
+    TRY(prof_end(ctx, 1));
+    if (!ctx->periodic) return COLATUS_OK;
+    return f64 ? run_ewald_kspace_vjp<double, double4>(ctx) : run_ewald_kspace_vjp<float, float4>(ctx);
 }
 
 // N x 3 vectors (dtype, device) -> float4 / double4 per body.
@@ -1272,7 +1385,8 @@ colatus_status colatus_init(colatus_t *out, int64_t N, const double *masses, dou
     if (st != COLATUS_OK) return bail(st);
     // every buffer holds the largest padded size any launch plan uses
     for (const ForcePlan &p : ctx->plan32) ctx->n_alloc = std::max(ctx->n_alloc, p.n_pad);
-    for (const ForcePlan *p : {&ctx->plan64, &ctx->plan_vjp32, &ctx->plan_vjp64, &ctx->plan_ew32[0],
+    for (const ForcePlan *p : {&ctx->plan64, &ctx->plan_vjp32, &ctx->plan_vjp64, &ctx->plan_ewvjp32,
+                               &ctx->plan_ewvjp64, &ctx->plan_ew32[0],
                                &ctx->plan_ew32[1], &ctx->plan_ew64})
         ctx->n_alloc = std::max(ctx->n_alloc, p->n_pad);
     ctx->eps = eps;
@@ -1714,7 +1828,6 @@ colatus_status colatus_force_vjp(colatus_t ctx, const void *w, void *gx, void *g
     NvtxRange nvtx_("colatus_force_vjp");
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
-    if (ctx->periodic) return fail(ctx, COLATUS_E_STATE, "%s is not built for periodic boundaries", "the force VJP");
     TRY(check_dtype(ctx, dtype));
     if (!w || (!gx && !gm)) return fail(ctx, COLATUS_E_ARG, "need w and at least one output");
     if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
@@ -1730,7 +1843,7 @@ colatus_status colatus_force_vjp(colatus_t ctx, const void *w, void *gx, void *g
     void *dgx = on_device ? gx : (gx ? (void *)ctx->stage : nullptr);
     void *dgm = on_device ? gm : (gm ? (void *)ctx->stage2 : nullptr);
     if (ctx->prec == COLATUS_FP64) {
-        const ForcePlan &p = ctx->plan_vjp64;
+        const ForcePlan &p = vjp_plan(ctx);
         vec3_to4_kernel<double4, double><<<nb, 256, 0, ctx->stream>>>(
             src, f64in, ctx->N, static_cast<double4 *>(ctx->adj.lx));
         TRY(launched(ctx));
@@ -1742,9 +1855,9 @@ colatus_status colatus_force_vjp(colatus_t ctx, const void *w, void *gx, void *g
         vjp_out_f64_kernel<<<nb, 256, 0, ctx->stream>>>(static_cast<const double4 *>(ctx->part), p.L,
                                                         p.itile, ctx->N, dgx, dgm, f64in,
                                                         static_cast<const double4 *>(ctx->adj.pkw),
-                                                        extra_args(ctx));
+                                                        vjp_extra(ctx));
     } else {
-        const ForcePlan &p = ctx->plan_vjp32;
+        const ForcePlan &p = vjp_plan(ctx);
         vec3_to4_kernel<float4, float><<<nb, 256, 0, ctx->stream>>>(
             src, f64in, ctx->N, static_cast<float4 *>(ctx->adj.lx));
         TRY(launched(ctx));
@@ -1756,7 +1869,7 @@ colatus_status colatus_force_vjp(colatus_t ctx, const void *w, void *gx, void *g
         vjp_out_f32_kernel<<<nb, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part), p.L,
                                                         p.itile, ctx->N, dgx, dgm, f64in,
                                                         static_cast<const float *>(ctx->adj.pkw),
-                                                        extra_args(ctx));
+                                                        vjp_extra(ctx));
     }
     TRY(launched(ctx));
     if (!on_device) {
@@ -1774,7 +1887,6 @@ colatus_status colatus_adjoint_forward(colatus_t ctx, double dt, int64_t nsteps,
     NvtxRange nvtx_("colatus_adjoint_forward");
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
-    if (ctx->periodic) return fail(ctx, COLATUS_E_STATE, "%s is not built for periodic boundaries", "the adjoint");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, COLATUS_E_ARG, "dt must be finite and > 0");
     if (nsteps < 1 || checkpoint_every < 1)
         return fail(ctx, COLATUS_E_ARG, "nsteps and checkpoint_every must be >= 1");
@@ -1868,7 +1980,7 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
     }
     const size_t body = f64 ? sizeof(double4) : sizeof(float4);
     const size_t plane = (size_t)ctx->n_alloc * body;
-    const ForcePlan &pv = f64 ? ctx->plan_vjp64 : ctx->plan_vjp32;
+    const ForcePlan &pv = vjp_plan(ctx);
     const long long NS = a.nsteps;
     const unsigned nbv = blocks_for(pv.n_pad, 256);
     if (f64)
@@ -1953,14 +2065,14 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
                     static_cast<const double4 *>(pos(n)), static_cast<double4 *>(a.lx),
                     static_cast<double4 *>(a.lv), static_cast<double4 *>(a.lvh),
                     static_cast<double *>(a.lm), a.table, n, a.tau, static_cast<double4 *>(a.pkw),
-                    ctx->N, pv.n_pad, extra_args(ctx));
+                    ctx->N, pv.n_pad, vjp_extra(ctx));
             else
                 adj_step_f32_kernel<<<nbv, 256, 0, ctx->stream>>>(
                     static_cast<const float4 *>(ctx->part), pv.L, pv.itile,
                     static_cast<const float4 *>(pos(n)), static_cast<float4 *>(a.lx),
                     static_cast<float4 *>(a.lv), static_cast<float4 *>(a.lvh),
                     static_cast<float *>(a.lm), a.table, n, a.tau, static_cast<float *>(a.pkw),
-                    ctx->N, pv.n_pad, extra_args(ctx));
+                    ctx->N, pv.n_pad, vjp_extra(ctx));
             TRY(launched(ctx));
             TRY(prof_end(ctx, 2));
         }
@@ -1975,7 +2087,7 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
                                                           pv.L, pv.itile, static_cast<double4 *>(a.lx),
                                                           static_cast<double *>(a.lm), ctx->N,
                                                           static_cast<const double4 *>(a.pkw),
-                                                          extra_args(ctx));
+                                                          vjp_extra(ctx));
         TRY(launched(ctx));
         adj_store_kernel<double4, double><<<nb, 256, 0, ctx->stream>>>(
             static_cast<const double4 *>(a.lx), static_cast<const double4 *>(a.lv),
@@ -1985,7 +2097,7 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
                                                           pv.L, pv.itile, static_cast<float4 *>(a.lx),
                                                           static_cast<float *>(a.lm), ctx->N,
                                                           static_cast<const float *>(a.pkw),
-                                                          extra_args(ctx));
+                                                          vjp_extra(ctx));
         TRY(launched(ctx));
         adj_store_kernel<float4, float><<<nb, 256, 0, ctx->stream>>>(
             static_cast<const float4 *>(a.lx), static_cast<const float4 *>(a.lv),

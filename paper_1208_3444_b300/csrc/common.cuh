@@ -203,6 +203,26 @@ __device__ __forceinline__ void add_long_range(const Extra &E, long long i, doub
     fz += l.z;
 }
 
+// Add the reciprocal-space part of a periodic VJP (x, y, z: dL/dx; w:
+// dL/dm) of body i, when the VJP consumers are given one in lr32 / lr64.
+__device__ __forceinline__ void add_kspace_vjp(const Extra &E, long long i, float4 &g) {
+    if (!E.lr32) return;
+    const float4 l = E.lr32[i];
+    g.x += l.x;
+    g.y += l.y;
+    g.z += l.z;
+    g.w += l.w;
+}
+
+__device__ __forceinline__ void add_kspace_vjp(const Extra &E, long long i, double4 &g) {
+    if (!E.lr64) return;
+    const double4 l = E.lr64[i];
+    g.x += l.x;
+    g.y += l.y;
+    g.z += l.z;
+    g.w += l.w;
+}
+
 // Derivative of the deformation term along w: -kappa J(d) w, d = x_psi - x,
 // J(d) = I/s^3 - 3 d d^T/s^5 (symmetric, so this is also its transpose).
 // Evaluated in FP64 for both element types.

@@ -54,6 +54,9 @@ struct EwaldArgs {
     float s0, s1;             // series of the bracket: s0 + s1 r^2 for alpha r < 0.05
     float x2_series;          // (0.05 / alpha)^2: r^2 below which the series is used
     int nk;                   // |n| <= nk in each table
+    // derivatives (adjoint and tangent): 2 alpha^2 cg, and the series of minus
+    // the bracket's f'(r)/r, -(cs0 + cs1 r^2), for alpha r < 0.05
+    float c2ag, ncs0, ncs1;
 };
 
 // ---------------------------------------------------------------- FP32 real space
@@ -374,19 +377,45 @@ struct KVec {
     int nx, ny, nz, pad;
 };
 
-// Body position component as FP64 from either layout.
-__device__ __forceinline__ double3 body_pos(const float *pk, const double4 *pos, long long i) {
-    if (pos) {
-        const double4 p = pos[i];
+// Where the k-space kernels read bodies.  FP32: pair-interleaved records of
+// `rec` floats per pair of bodies (8: [x0 x1 y0 y1 z0 z1 m0 m1], the force
+// input; 16: the VJP input, whose co-vector follows at 8, 10, 12).  FP64:
+// `rec` double4 per body (1: (x, y, z, m); 2: then (wx, wy, wz, 0)).  The
+// structure factors weigh each body by entry `widx` of its record: the mass
+// (6 in FP32, 3 in FP64) or a co-vector component (8/10/12; 4/5/6).
+struct BodySrc {
+    const float *pk;
+    const double4 *pos;
+    int rec, widx;
+};
+
+__host__ __device__ inline BodySrc masses_of(const float *pk, const double4 *pos) {
+    return BodySrc{pk, pos, pos ? 1 : 8, pos ? 3 : 6};
+}
+
+// Body position as FP64 from either layout.
+__device__ __forceinline__ double3 body_pos(const BodySrc &b, long long i) {
+    if (b.pos) {
+        const double4 p = b.pos[i * b.rec];
         return make_double3(p.x, p.y, p.z);
     }
-    const float *p = pk + (i >> 1) * 8 + (i & 1);
+    const float *p = b.pk + (i >> 1) * b.rec + (i & 1);
     return make_double3((double)p[0], (double)p[2], (double)p[4]);
 }
 
-__device__ __forceinline__ double body_mass(const float *pk, const double4 *pos, long long i) {
-    if (pos) return pos[i].w;
-    return (double)pk[(i >> 1) * 8 + (i & 1) + 6];
+// Record entry k of body i (FP32: float k of the pair record's lane; FP64:
+// component k of the double4 record, 0..7).
+__device__ __forceinline__ double body_entry(const BodySrc &b, long long i, int k) {
+    if (b.pos) {
+        const double4 p = b.pos[i * b.rec + (k >> 2)];
+        const int c = k & 3;
+        return c == 0 ? p.x : (c == 1 ? p.y : (c == 2 ? p.z : p.w));
+    }
+    return (double)b.pk[(i >> 1) * b.rec + (i & 1) + k];
+}
+
+__device__ __forceinline__ double body_weight(const BodySrc &b, long long i) {
+    return body_entry(b, i, b.widx);
 }
 
 template <typename T> struct Vec2;
@@ -398,13 +427,13 @@ template <> struct Vec2<double> { using type = double2; };
 // with n x_c / L reduced exactly (FP64: exact for |n| < 2^20, minus its
 // nearest integer) before sincospi.  One thread per (body, axis).
 template <typename T>
-__global__ void ewald_phase_kernel(const float *__restrict__ pk, const double4 *__restrict__ pos,
-                                   long long N, EwaldArgs A, typename Vec2<T>::type *__restrict__ ph) {
+__global__ void ewald_phase_kernel(BodySrc src, long long N, EwaldArgs A,
+                                   typename Vec2<T>::type *__restrict__ ph) {
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= 3 * N) return;
     const long long i = q / 3;
     const int c = (int)(q - 3 * i);
-    const double3 p = body_pos(pk, pos, i);
+    const double3 p = body_pos(src, i);
     const double u = (c == 0 ? p.x : (c == 1 ? p.y : p.z)) / A.L;
     typename Vec2<T>::type *o = ph + q * (A.nk + 1);
     for (int n = 0; n <= A.nk; ++n) {
@@ -441,7 +470,8 @@ template <typename T>
 __host__ __device__ constexpr int ew_bodies() { return sizeof(T) == 4 ? 64 : 32; }
 
 // Partial structure factors: rho_part[split][k] = sum over the split's bodies
-// of m_j exp(i k.x_j).  Grid (k chunks, body splits); a chunk is a run of whole
+// of m_j exp(i k.x_j) (m_j: the weight src names, the mass by default).  Grid
+// (k chunks, body splits); a chunk is a run of whole
 // pencils with at most kEwKThreads k-vectors (rchunk: first pencil of chunk c;
 // np_max pencils at most), one k per thread.  Per batch of kEwBodies bodies the
 // block stages their tables, then the per-(body, pencil) base
@@ -450,7 +480,7 @@ __host__ __device__ constexpr int ew_bodies() { return sizeof(T) == 4 ? 64 : 32;
 // (deterministic).
 template <typename T>
 __global__ void __launch_bounds__(kEwKThreads)
-    ewald_rho_kernel(const float *__restrict__ pk, const double4 *__restrict__ pos, long long N,
+    ewald_rho_kernel(BodySrc src, long long N,
                      const typename Vec2<T>::type *__restrict__ ph, const KPencil *__restrict__ pen,
                      const int *__restrict__ rchunk, int np_max, int nkv, EwaldArgs A,
                      double2 *__restrict__ rho_part) {
@@ -479,9 +509,9 @@ __global__ void __launch_bounds__(kEwKThreads)
     for (long long j0 = b0; j0 < b1; j0 += kEwBodies) {
         const int nb = (int)min((long long)kEwBodies, b1 - j0);
         __syncthreads();
-        const T2 *src = ph + j0 * 3 * nt;
-        for (int q = t; q < nb * 3 * nt; q += kEwKThreads) tab[q] = src[q];
-        for (int b = t; b < nb; b += kEwKThreads) tm[b] = (T)body_mass(pk, pos, j0 + b);
+        const T2 *tsrc = ph + j0 * 3 * nt;
+        for (int q = t; q < nb * 3 * nt; q += kEwKThreads) tab[q] = tsrc[q];
+        for (int b = t; b < nb; b += kEwKThreads) tm[b] = (T)body_weight(src, j0 + b);
         __syncthreads();
         for (int q = t; q < nb * np; q += kEwKThreads) {
             const int b = q / np, l = q - b * np;
