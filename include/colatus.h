@@ -118,10 +118,12 @@ colatus_status colatus_set_deformation(colatus_t ctx, double Cpsi, const double 
  * alpha <= 0 and nk <= 0 choose them from the precision (truncation below
  * 1e-8 of a pair term in the FP32 modes, 1e-15 in FP64); nk <= 63.  Positions
  * are not wrapped: the minimum image is taken per pair.  L = 0 restores
- * isolated boundaries.  Forces and both step schemes honour it; the force
- * VJP, the adjoint, the tangent model and autotuning return COLATUS_E_STATE
- * while it is on, and it does not combine with the deformation term
- * (COLATUS_E_ARG).  colatus_diagnostics keeps the isolated potential. */
+ * isolated boundaries.  Forces, both step schemes, the force VJP, the
+ * adjoint and the tangent model honour it (their derivatives differentiate
+ * the Ewald sum: the real-space pair Jacobian over minimum images plus the
+ * reciprocal sum's); autotuning returns COLATUS_E_STATE while it is on, and
+ * it does not combine with the deformation term (COLATUS_E_ARG).
+ * colatus_diagnostics keeps the isolated potential. */
 colatus_status colatus_set_periodic(colatus_t ctx, double L, double alpha, int nk);
 
 /* The Ewald parameters in use: alpha, nk and the number of k-vectors of the

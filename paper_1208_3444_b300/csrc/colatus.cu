@@ -97,6 +97,8 @@ using Vjp64K = Vjp64Kernel<kV64NT, kV64JT, kStages>;
 // 64 tangents: 38.6 ms per step, 13 % less than without unrolling)
 constexpr int kJvpNT = 256, kJvpIPT = 1, kJvpJT = 128, kJvpMINB = 1, kJvpUnr = 4;
 using JvpK = JvpKernel<kJvpNT, kJvpIPT, kJvpJT, kStages>;
+// the periodic JVP runs the same shape and plan (tiles, units, segments)
+constexpr int kEwJvpMinB = 1;
 
 // Periodic (Ewald) real-space kernels: FP32 256 threads x 2 i-bodies,
 // 256-body j-tiles; FP64 128 x 1, 32-body tiles.
@@ -289,6 +291,7 @@ struct colatus_ctx {
         float *pkt = nullptr;                    // packed JVP input, pair-interleaved
         long long *seeds = nullptr;
         float *growth = nullptr;
+        float4 *lrt = nullptr;                   // [B][n_pad] reciprocal-space JVP (periodic)
         long long cap = 0, base = 0;
         double dir[3] = {1.0, 0.0, 0.0};
     } tan;
@@ -874,7 +877,7 @@ void free_all(colatus_t ctx) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *tptrs[] = {ctx->tan.dx, ctx->tan.dv, ctx->tan.dvh, ctx->tan.pkt, ctx->tan.seeds,
-                     ctx->tan.growth};
+                     ctx->tan.growth, ctx->tan.lrt};
     for (void *p : tptrs)
         if (p) cudaFree(p);
     void *aptrs[] = {ctx->adj.ck_x, ctx->adj.ck_v, ctx->adj.seg_x, ctx->adj.table, ctx->adj.rclk,
@@ -1202,6 +1205,19 @@ Extra vjp_extra(colatus_t ctx) {
     return D;
 }
 
+// The per-k weights of the reciprocal-space VJP and JVP (kwr, kwl).
+colatus_status kweight_bufs(colatus_t ctx) {
+    if (ctx->kwrl_cap >= (size_t)ctx->nkv) return COLATUS_OK;
+    if (ctx->kwr) cudaFree(ctx->kwr);
+    if (ctx->kwl) cudaFree(ctx->kwl);
+    ctx->kwr = ctx->kwl = nullptr;
+    ctx->kwrl_cap = 0;
+    CU(cudaMalloc(&ctx->kwr, ctx->nkv * sizeof(double2)));
+    CU(cudaMalloc(&ctx->kwl, ctx->nkv * sizeof(double2)));
+    ctx->kwrl_cap = ctx->nkv;
+    return COLATUS_OK;
+}
+
 // Reciprocal-space VJP of the bodies and co-vectors packed in adj.pkw, into
 // lrv: phase tables of the packed positions, four structure-factor passes
 // (weights m, w_x, w_y, w_z), their weights per k, then one pass per body.
@@ -1210,15 +1226,7 @@ colatus_status run_ewald_kspace_vjp(colatus_t ctx) {
     using T2 = typename Vec2<T>::type;
     const bool f64 = sizeof(T) == 8;
     if (!ctx->lrv) CU(cudaMalloc(&ctx->lrv, (size_t)ctx->n_alloc * sizeof(double4)));
-    if (ctx->kwrl_cap < (size_t)ctx->nkv) {
-        if (ctx->kwr) cudaFree(ctx->kwr);
-        if (ctx->kwl) cudaFree(ctx->kwl);
-        ctx->kwr = ctx->kwl = nullptr;
-        ctx->kwrl_cap = 0;
-        CU(cudaMalloc(&ctx->kwr, ctx->nkv * sizeof(double2)));
-        CU(cudaMalloc(&ctx->kwl, ctx->nkv * sizeof(double2)));
-        ctx->kwrl_cap = ctx->nkv;
-    }
+    TRY(kweight_bufs(ctx));
     BodySrc src{f64 ? nullptr : static_cast<const float *>(ctx->adj.pkw),
                 f64 ? static_cast<const double4 *>(ctx->adj.pkw) : nullptr, f64 ? 2 : 16, f64 ? 3 : 6};
     T2 *ph = static_cast<T2 *>(ctx->ph);
@@ -1247,7 +1255,7 @@ colatus_status run_ewald_kspace_vjp(colatus_t ctx) {
     ewald_kvjp_kernel<T, T4><<<blocks_for(ctx->N, kEwFThreads), kEwFThreads * kEwFSlices,
                                ew_kvjp_smem<T>(ctx->ew.nk), ctx->stream>>>(
         ctx->N, ph, ctx->pen, ctx->npen, static_cast<const T2 *>(ctx->kwr),
-        static_cast<const T2 *>(ctx->kwl), src, ctx->ew, static_cast<T4 *>(ctx->lrv));
+        static_cast<const T2 *>(ctx->kwl), src, nullptr, ctx->ew, static_cast<T4 *>(ctx->lrv));
     return launched(ctx);
 }
 
@@ -1309,6 +1317,55 @@ TangentState tan_state(colatus_t ctx) {
     return T;
 }
 
+// Reciprocal-space JVP of every tangent at the positions in pk, into
+// tan.lrt[b]: phase tables and the mass structure factors once, then per
+// tangent three structure-factor passes weighted by m_j dx_j, their per-k
+// weights, and one pass per body (m_i -> 1, w_i -> dx_i).
+colatus_status run_ewald_kspace_jvp(colatus_t ctx, const float *pk) {
+    auto &t = ctx->tan;
+    if (!t.lrt) CU(cudaMalloc(&t.lrt, (size_t)t.B * t.n_pad * sizeof(float4)));
+    TRY(kweight_bufs(ctx));
+    BodySrc src = masses_of(pk, nullptr);
+    float2 *ph = static_cast<float2 *>(ctx->ph);
+    ewald_phase_kernel<float><<<blocks_for(3 * ctx->N, 128), 128, 0, ctx->stream>>>(src, ctx->N, ctx->ew,
+                                                                                   ph);
+    TRY(launched(ctx));
+    const int kchunks = ctx->nrchunk;
+    const long long max_split = std::max(1LL, ctx->N / ew_bodies<float>());
+    const int splits = (int)std::min<long long>(std::max(1, kEwRhoBlocksPerSM * ctx->num_sms / kchunks),
+                                                max_split);
+    const size_t plane = (size_t)splits * ctx->nkv;
+    TRY(grow(ctx, &ctx->rho_part, &ctx->rho_part_bytes, 4 * plane * sizeof(double2)));
+    const size_t smem_rho = ew_rho_smem<float>(ctx->ew.nk, ctx->rchunk_np);
+    double2 *rp = static_cast<double2 *>(ctx->rho_part);
+    auto rho_pass = [&](const BodySrc &b, double2 *dst) {
+        ewald_rho_kernel<float><<<dim3(kchunks, splits), kEwKThreads, smem_rho, ctx->stream>>>(
+            b, ctx->N, ph, ctx->pen, ctx->rchunk, ctx->rchunk_np, ctx->nkv, ctx->ew, dst);
+        return launched(ctx);
+    };
+    TRY(rho_pass(src, rp));
+    const double tpl = 2.0 * std::acos(-1.0) / ctx->ew.L;
+    for (int b = 0; b < t.B; ++b) {
+        BodySrc sb = src;
+        sb.tv = t.dx + (size_t)b * t.n_pad;
+        for (int c = 0; c < 3; ++c) {
+            sb.tc = c;
+            TRY(rho_pass(sb, rp + (c + 1) * plane));
+        }
+        ewald_vjp_weights_kernel<float><<<blocks_for(ctx->npen, 128), 128, 0, ctx->stream>>>(
+            rp, splits, ctx->nkv, ctx->kw, ctx->pen, ctx->npen, tpl, static_cast<float2 *>(ctx->kwr),
+            static_cast<float2 *>(ctx->kwl));
+        TRY(launched(ctx));
+        ewald_kvjp_kernel<float, float4><<<blocks_for(ctx->N, kEwFThreads), kEwFThreads * kEwFSlices,
+                                           ew_kvjp_smem<float>(ctx->ew.nk), ctx->stream>>>(
+            ctx->N, ph, ctx->pen, ctx->npen, static_cast<const float2 *>(ctx->kwr),
+            static_cast<const float2 *>(ctx->kwl), src, t.dx + (size_t)b * t.n_pad, ctx->ew,
+            t.lrt + (size_t)b * t.n_pad);
+        TRY(launched(ctx));
+    }
+    return COLATUS_OK;
+}
+
 // Pack positions (pair-interleaved pk) with the tangents and run the JVP.
 colatus_status run_jvp(colatus_t ctx, const float *pk) {
     auto &t = ctx->tan;
@@ -1317,13 +1374,28 @@ colatus_status run_jvp(colatus_t ctx, const float *pk) {
     tan_pack_kernel<<<grid, 256, 0, ctx->stream>>>(pk, T, ctx->N, t.n_pad);
     TRY(launched(ctx));
     TRY(ensure_part(ctx, t.plan.part_bytes));
-    jvp_f32x2_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kJvpMINB, kJvpUnr>
-        <<<t.plan.L.G, kJvpNT, JvpK::SMEM, ctx->stream>>>(t.pkt, static_cast<float4 *>(ctx->part),
-                                                          ctx->flags, t.plan.L, t.n_pad,
-                                                          (float)(ctx->eps * ctx->eps));
+    if (ctx->periodic)
+        ewald_jvp_f32x2_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kEwJvpMinB>
+            <<<t.plan.L.G, kJvpNT, JvpK::SMEM, ctx->stream>>>(t.pkt, static_cast<float4 *>(ctx->part),
+                                                              ctx->flags, t.plan.L, t.n_pad,
+                                                              (float)(ctx->eps * ctx->eps), ctx->ew);
+    else
+        jvp_f32x2_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kJvpMINB, kJvpUnr>
+            <<<t.plan.L.G, kJvpNT, JvpK::SMEM, ctx->stream>>>(t.pkt, static_cast<float4 *>(ctx->part),
+                                                              ctx->flags, t.plan.L, t.n_pad,
+                                                              (float)(ctx->eps * ctx->eps));
     TRY(launched(ctx));
     ctx->interactions += (double)ctx->N * (double)ctx->N * t.B;
-    return COLATUS_OK;
+    return ctx->periodic ? run_ewald_kspace_jvp(ctx, pk) : COLATUS_OK;
+}
+
+// Per-body terms of the tangent epilogues: the deformation term and, with
+// periodic boundaries, the reciprocal-space JVP of every tangent (lrt).
+Extra tan_extra(colatus_t ctx) {
+    Extra D = extra_args(ctx);
+    D.lr32 = ctx->periodic ? ctx->tan.lrt : nullptr;
+    D.lr64 = nullptr;
+    return D;
 }
 
 }  // namespace
@@ -2117,7 +2189,6 @@ colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, 
                                     int64_t capacity_steps) {
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
-    if (ctx->periodic) return fail(ctx, COLATUS_E_STATE, "%s is not built for periodic boundaries", "the tangent model");
     auto &t = ctx->tan;
     if (B < 1 || !seeds || capacity_steps < 1) return fail(ctx, COLATUS_E_ARG, "need B >= 1 seeds and capacity");
     for (int b = 0; b < B; ++b)
@@ -2130,7 +2201,7 @@ colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, 
     }
     if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
     CU(cudaStreamSynchronize(ctx->stream));
-    void *old[] = {t.dx, t.dv, t.dvh, t.pkt, t.seeds, t.growth};
+    void *old[] = {t.dx, t.dv, t.dvh, t.pkt, t.seeds, t.growth, t.lrt};
     for (void *p : old)
         if (p) cudaFree(p);
     t = colatus_ctx::Tangent();
@@ -2140,6 +2211,13 @@ colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, 
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, JvpK::SMEM));
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &occ, jvp_f32x2_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kJvpMINB, kJvpUnr>, kJvpNT, JvpK::SMEM));
+    if (JvpK::SMEM > 48 * 1024)
+        CU(cudaFuncSetAttribute(ewald_jvp_f32x2_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kEwJvpMinB>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, JvpK::SMEM));
+    int occ_e = 0;   // the periodic JVP shares the plan: the smaller residency of the two
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ_e, ewald_jvp_f32x2_kernel<kJvpNT, kJvpIPT, kJvpJT, kStages, kEwJvpMinB>, kJvpNT, JvpK::SMEM));
+    occ = std::min(occ, occ_e);
     if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "JVP kernel cannot be resident");
     t.B = B;
     t.nchunk = (B + kTB - 1) / kTB;
@@ -2192,7 +2270,6 @@ colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps) {
     NvtxRange nvtx_("colatus_tangent_step");
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
-    if (ctx->periodic) return fail(ctx, COLATUS_E_STATE, "%s is not built for periodic boundaries", "the tangent model");
     auto &t = ctx->tan;
     if (!t.ready) return fail(ctx, COLATUS_E_STATE, "colatus_tangent_init first");
     if (ctx->prec == COLATUS_FP64 || !is_kdk(ctx))
@@ -2218,7 +2295,7 @@ colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps) {
             tan_open_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part),
                                                            t.plan.L, t.plan.itile, T, ctx->table,
                                                            kTabCap, ctx->host_step, dt, ctx->N, t.n_pad,
-                                                           extra_args(ctx));
+                                                           tan_extra(ctx));
             TRY(launched(ctx));
             t.open = true;
             t.tau = dt;
@@ -2236,7 +2313,7 @@ colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps) {
             tan_step_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part),
                                                            t.plan.L, t.plan.itile, T, ctx->table,
                                                            kTabCap, ctx->host_step + j, dt, ctx->N,
-                                                           t.n_pad, extra_args(ctx));
+                                                           t.n_pad, tan_extra(ctx));
             TRY(launched(ctx));
         }
         done += n;

@@ -1,5 +1,6 @@
 // ewald_adjoint.cuh -- derivatives of the periodic (Ewald-summed) force of
-// ewald.cuh: its vector-Jacobian product for the adjoint.
+// ewald.cuh: its vector-Jacobian product for the adjoint and its
+// Jacobian-vector product for the tangent model.
 //
 // The periodic force is F_k = sum_j m_j Phi(x_j - x_k) with Phi odd (the
 // real-space pair term over minimum images plus the reciprocal sum), so, for
@@ -27,12 +28,20 @@
 //     dL/dm_i += -sum_k w_k Im[e^{-i k.x_i} Lambda],
 // from four structure-factor passes (weights m, w_x, w_y, w_z) of
 // ewald_rho_kernel and one pass over (body, k) pairs.
+//
+// Tangent (JVP) along dx: dF_k = sum_j m_j J(d_kj) (dx_j - dx_k).  Real space
+// as the isolated JVP with a = m_j b and beta = m_j c; reciprocal space
+//     dF_k += sum_k w_k k Re[e^{-i k.x_k} (D(k) - (k.dx_k) rho(k))],
+//     D(k) = sum_j m_j (k.dx_j) e^{i k.x_j},
+// the VJP's reciprocal pass with m_i -> 1, w_i -> dx_k and Lambda -> D, one
+// tangent at a time (structure factors weighted by m_j dx_j).
 #pragma once
 
 #include "adjoint.cuh"
 #include "common.cuh"
 #include "ewald.cuh"
 #include "force.cuh"
+#include "tangent.cuh"
 
 namespace colatus {
 
@@ -419,7 +428,8 @@ __global__ void ewald_vjp_weights_kernel(const double2 *__restrict__ rho_part, i
     }
 }
 
-// Reciprocal-space VJP at every body (blocks of kEwFThreads bodies with
+// Reciprocal-space VJP at every body (with wv set: the JVP of one tangent,
+// m_i -> 1 and w_i -> wv[i]; out.w is then unused) (blocks of kEwFThreads bodies with
 // kEwFSlices threads per body, each taking every kEwFSlices-th pencil, the
 // bodies' phase tables staged in shared memory as in ewald_kforce_kernel):
 //   out_i = ( (2 pi/L) sum_k n Re[e^{-ik.x_i} (m_i wl - (k.w_i) wr)],
@@ -430,8 +440,8 @@ __global__ void __launch_bounds__(kEwFThreads * kEwFSlices)
     ewald_kvjp_kernel(long long N, const typename Vec2<T>::type *__restrict__ ph,
                       const KPencil *__restrict__ pen, int npen,
                       const typename Vec2<T>::type *__restrict__ wr,
-                      const typename Vec2<T>::type *__restrict__ wl, BodySrc src, EwaldArgs A,
-                      T4 *__restrict__ out) {
+                      const typename Vec2<T>::type *__restrict__ wl, BodySrc src,
+                      const float4 *__restrict__ wv, EwaldArgs A, T4 *__restrict__ out) {
     using T2 = typename Vec2<T>::type;
     constexpr int NT = kEwFThreads * kEwFSlices;
     extern __shared__ __align__(16) unsigned char sm[];
@@ -451,10 +461,11 @@ __global__ void __launch_bounds__(kEwFThreads * kEwFSlices)
     const double tpl = 2.0 * acos(-1.0) / A.L;
     double ax = 0.0, ay = 0.0, az = 0.0, am = 0.0;
     if (i < N) {
-        const T m = (T)body_entry(src, i, src.pos ? 3 : 6);
-        const T wx = (T)body_entry(src, i, src.pos ? 4 : 8);
-        const T wy = (T)body_entry(src, i, src.pos ? 5 : 10);
-        const T wz = (T)body_entry(src, i, src.pos ? 6 : 12);
+        // the VJP: m_i and w_i from the packed record; the JVP: 1 and dx_i
+        const T m = wv ? (T)1 : (T)body_entry(src, i, src.pos ? 3 : 6);
+        const T wx = wv ? (T)wv[i].x : (T)body_entry(src, i, src.pos ? 4 : 8);
+        const T wy = wv ? (T)wv[i].y : (T)body_entry(src, i, src.pos ? 5 : 10);
+        const T wz = wv ? (T)wv[i].z : (T)body_entry(src, i, src.pos ? 6 : 12);
         const T c1 = (T)tpl * wz;
         for (int p = sl; p < npen; p += kEwFSlices) {
             const KPencil P = pen[p];
@@ -508,6 +519,152 @@ __host__ inline size_t ew_kvjp_smem(int nk) {
     const size_t tabs = (size_t)kEwFThreads * 3 * (nk + 1) * 2 * sizeof(T);
     const size_t red = (size_t)4 * kEwFSlices * kEwFThreads * sizeof(double);
     return tabs > red ? tabs : red;
+}
+
+// Real-space periodic JVP for kTB tangents per chunk: jvp_f32x2_kernel's
+// pipeline, layout and segments with the periodic pair geometry (minimum
+// image, b and c of the Ewald real-space term shared by the tangents):
+//     dF_k += a u + (beta (d . u)) d,  a = m_j b,  beta = m_j c,  u = dx_j - dx_k.
+// The self pair contributes 0 (u = 0 exactly).
+template <int NT, int IPT, int JT, int STAGES, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    ewald_jvp_f32x2_kernel(const float *__restrict__ pkt, float4 *__restrict__ part,
+                           int *__restrict__ flags, ForceLaunch L, long long n_pad, float eps2,
+                           EwaldArgs A) {
+    using K = JvpKernel<NT, IPT, JT, STAGES>;
+    static_assert(JT % 2 == 0, "pairs of j-bodies");
+    constexpr int TILE_F4 = K::TILE_BYTES / 16;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float4 *tiles = reinterpret_cast<float4 *>(smem);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * K::TILE_BYTES);
+    const int tid = threadIdx.x;
+    const long long G = gridDim.x, g = blockIdx.x;
+    const long long W = L.W;
+    const long long u0 = sk_begin(g, W, G), u1 = sk_begin(g + 1, W, G);
+    const int n_jt = L.n_jt;
+    const long long per_it = n_jt;
+    auto tile_src = [&](long long u) -> const float * {
+        const long long ct = u / per_it;
+        const long long chunk = ct / L.n_it;
+        const long long jt = u % per_it;
+        return pkt + (chunk * n_pad + jt * JT) * kPktSlots;
+    };
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int s = 0; s < STAGES && u0 + s < u1; ++s) {
+            mbar_arrive_expect_tx(&full[s], K::TILE_BYTES);
+            bulk_load(tiles + s * TILE_F4, tile_src(u0 + s), K::TILE_BYTES, &full[s]);
+        }
+    }
+    const float2 e2 = make_float2(eps2, eps2);
+    const float2 Lm = make_float2(-A.Lf, -A.Lf), iL = make_float2(A.invLf, A.invLf);
+    long long u = u0;
+    bool bad = false;
+    int stage = 0;
+    uint32_t parity = 0;
+    while (u < u1) {
+        const long long ct = u / per_it;
+        const long long chunk = ct / L.n_it, it = ct % L.n_it;
+        const long long uend = min(u1, (ct + 1) * per_it);
+        float2 nx[IPT], ny[IPT], nz[IPT], ti[IPT][3 * kTB], ac[IPT][3 * kTB];
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            const long long i = it * K::ITILE + tid + k * NT;
+            const float *p = pkt_body(pkt, chunk, n_pad, i);
+            const float x = __ldg(p), y = __ldg(p + 2), z = __ldg(p + 4);
+            nx[k] = make_float2(-x, -x);
+            ny[k] = make_float2(-y, -y);
+            nz[k] = make_float2(-z, -z);
+#pragma unroll
+            for (int c = 0; c < 3 * kTB; ++c) {
+                const float t = -__ldg(p + 2 * (4 + c));
+                ti[k][c] = make_float2(t, t);
+                ac[k][c] = make_float2(0.f, 0.f);
+            }
+        }
+        for (; u < uend; ++u) {
+            const bool ok = mbar_wait_bounded(&full[stage], parity);
+            if (ok) {
+                const float4 *tl = tiles + stage * TILE_F4;
+#pragma unroll 1
+                for (int q = 0; q < JT / 2; ++q) {
+                    float2 v[kPktSlots];
+#pragma unroll
+                    for (int f = 0; f < kPktSlots / 2; ++f) {
+                        const float4 F = tl[(kPktSlots / 2) * q + f];
+                        v[2 * f] = make_float2(F.x, F.y);
+                        v[2 * f + 1] = make_float2(F.z, F.w);
+                    }
+                    const float2 mj = v[3];
+                    const float2 nmj = make_float2(-mj.x, -mj.y);
+#pragma unroll
+                    for (int k = 0; k < IPT; ++k) {
+                        float2 dx = __fadd2_rn(v[0], nx[k]);
+                        float2 dy = __fadd2_rn(v[1], ny[k]);
+                        float2 dz = __fadd2_rn(v[2], nz[k]);
+                        dx = min_image2(dx, iL, Lm);
+                        dy = min_image2(dy, iL, Lm);
+                        dz = min_image2(dz, iL, Lm);
+                        float2 b, nc;
+                        ewald_pair_bc2(dx, dy, dz, A, e2, b, nc);
+                        const float2 al = __fmul2_rn(mj, b);
+                        const float2 be = __fmul2_rn(nmj, nc);
+#pragma unroll
+                        for (int t = 0; t < kTB; ++t) {
+                            const float2 ux = __fadd2_rn(v[4 + 3 * t], ti[k][3 * t]);
+                            const float2 uy = __fadd2_rn(v[5 + 3 * t], ti[k][3 * t + 1]);
+                            const float2 uz = __fadd2_rn(v[6 + 3 * t], ti[k][3 * t + 2]);
+                            const float2 s =
+                                __fmul2_rn(be, __ffma2_rn(dz, uz, __ffma2_rn(dy, uy, __fmul2_rn(dx, ux))));
+                            ac[k][3 * t] = __ffma2_rn(s, dx, __ffma2_rn(al, ux, ac[k][3 * t]));
+                            ac[k][3 * t + 1] = __ffma2_rn(s, dy, __ffma2_rn(al, uy, ac[k][3 * t + 1]));
+                            ac[k][3 * t + 2] = __ffma2_rn(s, dz, __ffma2_rn(al, uz, ac[k][3 * t + 2]));
+                        }
+                    }
+                }
+            }
+            if (__syncthreads_or(!ok)) {
+                bad = true;
+                break;
+            }
+            if (tid == 0 && u + STAGES < u1) {
+                mbar_arrive_expect_tx(&full[stage], K::TILE_BYTES);
+                bulk_load(tiles + stage * TILE_F4, tile_src(u + STAGES), K::TILE_BYTES, &full[stage]);
+            }
+            if (++stage == STAGES) {
+                stage = 0;
+                parity ^= 1u;
+            }
+        }
+        if (bad) break;
+        const long long sidx = g - sk_owner(ct * per_it, W, G);
+        float4 *dst = part + (ct * L.S_max + sidx) * (long long)kTPlanes * K::ITILE;
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            const int il = tid + k * NT;
+            float a[kTC];
+#pragma unroll
+            for (int c = 0; c < kTC; ++c) a[c] = ac[k][c].x + ac[k][c].y;
+#pragma unroll
+            for (int pl = 0; pl < kTPlanes; ++pl)
+                dst[pl * K::ITILE + il] = make_float4(a[4 * pl], a[4 * pl + 1], a[4 * pl + 2], a[4 * pl + 3]);
+        }
+    }
+    if (bad && tid == 0) {
+        atomicOr(&flags[FLAG_TIMEOUT], 1);
+        for (long long v = u; v < u1 && v < u + STAGES; ++v) {
+            mbar_wait_bounded(&full[stage], parity);
+            if (++stage == STAGES) {
+                stage = 0;
+                parity ^= 1u;
+            }
+        }
+    }
 }
 
 }  // namespace colatus

@@ -267,6 +267,22 @@ __device__ __forceinline__ void tan_defo(const TangentState &T, const Extra &D, 
     }
 }
 
+// Reciprocal-space JVP of every tangent of the chunk at body i (periodic
+// boundaries: lr32 holds [B][n_pad] float4, one plane per tangent).
+__device__ __forceinline__ void tan_kspace(const TangentState &T, const Extra &D, int chunk,
+                                           long long i, long long n_pad, float (&f)[kTC]) {
+    if (!D.lr32) return;
+#pragma unroll
+    for (int q = 0; q < kTB; ++q) {
+        const long long b = (long long)chunk * kTB + q;
+        if (b >= T.B) break;
+        const float4 l = D.lr32[b * n_pad + i];
+        f[3 * q] += l.x;
+        f[3 * q + 1] += l.y;
+        f[3 * q + 2] += l.z;
+    }
+}
+
 __global__ void tan_open_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
                                 TangentState T, const StepCoef *__restrict__ table, int tcap,
                                 long long step, double tau, long long N, long long n_pad, Extra D) {
@@ -275,6 +291,7 @@ __global__ void tan_open_kernel(const float4 *__restrict__ part, ForceLaunch L, 
     if (i >= N) return;
     float f[kTC];
     jvp_reduce(part, L, itile, chunk, i, f);
+    tan_kspace(T, D, chunk, i, n_pad, f);
     tan_defo(T, D, chunk, i, n_pad, f);
     const StepCoef &e = table[step % tcap];
     const float c1 = (float)e.c1, d1 = (float)e.d1, t = (float)tau;
@@ -303,6 +320,7 @@ __global__ void tan_step_kernel(const float4 *__restrict__ part, ForceLaunch L, 
     if (i >= N) return;
     float f[kTC];
     jvp_reduce(part, L, itile, chunk, i, f);
+    tan_kspace(T, D, chunk, i, n_pad, f);
     tan_defo(T, D, chunk, i, n_pad, f);
     const StepCoef &e = table[step % tcap];
     const StepCoef &en = table[(step + 1) % tcap];

@@ -149,8 +149,7 @@ def test_paths_not_built_for_periodic_boundaries_refuse():
     try:
         sim.set_state(ic.x, ic.v)
         sim.set_periodic(1.0)
-        for call in (lambda: sim.tangent_init([0], 2),
-                     lambda: sim.autotune(1),
+        for call in (lambda: sim.autotune(1),
                      lambda: sim.set_deformation(0.1, (0.5, 0.5, 0.5))):
             with pytest.raises(B.ColatusError):
                 call()
