@@ -497,6 +497,20 @@ def time_periodic(B, inputs, torch, stream, nsteps=10):
         fms, n = sim.profile_read()
         sim.profile_forces(False)
         par = sim.periodic_params()
+        # the force VJP under periodic boundaries (device buffers): the whole
+        # call, and its real-space kernel alone
+        w = torch.randn((ic.N, 3), device="cuda", dtype=torch.float32)
+        gx, gm = torch.empty_like(w), torch.empty(ic.N, device="cuda", dtype=torch.float32)
+        B.colatus_force_vjp(sim.h, w, gx, gm)          # loads the kernels (lazy loading)
+        sim.synchronize()
+        sim.profile_forces(True)
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        B.colatus_force_vjp(sim.h, w, gx, gm)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        vms, vn = sim.profile_read(vjp=True)
+        sim.profile_forces(False)
     finally:
         sim.close()
     ms = e0.elapsed_time(e1) / nsteps
@@ -506,8 +520,13 @@ def time_periodic(B, inputs, torch, stream, nsteps=10):
             "ms_per_step": ms, "interactions_per_s": pairs / (ms * 1e-3),
             "real_space_ms_per_launch": fms / n,
             "real_space_interactions_per_sm_per_clk": pairs / (fms / n * 1e-3) / (nsm * 2.032e9),
+            "vjp_call_ms": e2.elapsed_time(e3),
+            "vjp_real_space_ms": vms / max(1, vn),
+            "vjp_real_space_interactions_per_sm_per_clk": pairs / (vms / max(1, vn) * 1e-3) /
+            (nsm * 2.032e9),
             "what": "KDK step with periodic boundaries; real space = the minimum-image "
-                    "all-pairs kernel alone (events around it)"}
+                    "all-pairs kernel alone (events around it); vjp = colatus_force_vjp on device "
+                    "buffers (real space plus the reciprocal-space VJP)"}
 
 
 def run_colatus(args, ws, rank, local):

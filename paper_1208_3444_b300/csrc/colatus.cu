@@ -102,7 +102,9 @@ constexpr int kEwJvpMinB = 1;
 
 // Periodic (Ewald) real-space kernels: FP32 256 threads x 2 i-bodies,
 // 256-body j-tiles; FP64 128 x 1, 32-body tiles.
-constexpr int kEwNT = 256, kEwIPT = 2, kEwJT = 256, kEwFold = 32, kEwMinB = 2;
+// 512 x 2 at one CTA per SM: 6 % faster than 256 x 2 at two, among eight
+// shapes timed on B300 at 32^3 (equal masses, compensated)
+constexpr int kEwNT = 512, kEwIPT = 2, kEwJT = 256, kEwFold = 32, kEwMinB = 1;
 using EwK = EwaldF32Kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, false>;
 using EwKC = EwaldF32Kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, true>;
 constexpr int kEw64NT = 128, kEw64JT = 32;
@@ -435,9 +437,9 @@ colatus_status build_plans(colatus_t ctx) {
 
     for (int comp = 0; comp < 2; ++comp) {
         const void *fn = comp ? (const void *)ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold,
-                                                              true, kEwMinB>
+                                                              true, kEwMinB, false>
                               : (const void *)ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold,
-                                                              false, kEwMinB>;
+                                                              false, kEwMinB, false>;
         CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kEwNT, EwK::SMEM));
         if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "Ewald kernel cannot be resident");
         ForcePlan &e = ctx->plan_ew32[comp];
@@ -681,14 +683,22 @@ colatus_status run_ewald_f32(colatus_t ctx, const ForcePlan &p, const float *pk)
     TRY(ensure_part(ctx, p.part_bytes));
     const float eps2 = (float)(ctx->eps * ctx->eps);
     TRY(prof_begin(ctx));
-    if (ctx->prec == COLATUS_FP32_COMP)
-        ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, true, kEwMinB>
-            <<<p.L.G, kEwNT, EwKC::SMEM, ctx->stream>>>(pk, static_cast<float4 *>(ctx->part), ctx->flags,
-                                                        p.L, eps2, ctx->ew);
+    // equal masses and no zero-mass padding: the equal-mass form
+    const bool eqm = ctx->eq_mass && p.n_pad == ctx->N;
+    float4 *part = static_cast<float4 *>(ctx->part);
+    const float me = ctx->mass_eq;
+    if (ctx->prec == COLATUS_FP32_COMP && eqm)
+        ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, true, kEwMinB, true>
+            <<<p.L.G, kEwNT, EwKC::SMEM, ctx->stream>>>(pk, part, ctx->flags, p.L, eps2, ctx->ew, me);
+    else if (ctx->prec == COLATUS_FP32_COMP)
+        ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, true, kEwMinB, false>
+            <<<p.L.G, kEwNT, EwKC::SMEM, ctx->stream>>>(pk, part, ctx->flags, p.L, eps2, ctx->ew, me);
+    else if (eqm)
+        ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, false, kEwMinB, true>
+            <<<p.L.G, kEwNT, EwK::SMEM, ctx->stream>>>(pk, part, ctx->flags, p.L, eps2, ctx->ew, me);
     else
-        ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, false, kEwMinB>
-            <<<p.L.G, kEwNT, EwK::SMEM, ctx->stream>>>(pk, static_cast<float4 *>(ctx->part), ctx->flags,
-                                                       p.L, eps2, ctx->ew);
+        ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, false, kEwMinB, false>
+            <<<p.L.G, kEwNT, EwK::SMEM, ctx->stream>>>(pk, part, ctx->flags, p.L, eps2, ctx->ew, me);
     TRY(launched(ctx));
     ctx->interactions += (double)ctx->N * (double)ctx->N;
     TRY(prof_end(ctx));
@@ -1247,7 +1257,7 @@ colatus_status run_ewald_kspace_vjp(colatus_t ctx) {
             static_cast<double2 *>(ctx->rho_part) + c * plane);
         TRY(launched(ctx));
     }
-    ewald_vjp_weights_kernel<T><<<blocks_for(ctx->npen, 128), 128, 0, ctx->stream>>>(
+    ewald_vjp_weights_kernel<T><<<blocks_for(ctx->nkv, 128), 128, 0, ctx->stream>>>(
         static_cast<const double2 *>(ctx->rho_part), splits, ctx->nkv, ctx->kw, ctx->pen, ctx->npen,
         2.0 * std::acos(-1.0) / ctx->ew.L, static_cast<T2 *>(ctx->kwr), static_cast<T2 *>(ctx->kwl));
     TRY(launched(ctx));
@@ -1352,7 +1362,7 @@ colatus_status run_ewald_kspace_jvp(colatus_t ctx, const float *pk) {
             sb.tc = c;
             TRY(rho_pass(sb, rp + (c + 1) * plane));
         }
-        ewald_vjp_weights_kernel<float><<<blocks_for(ctx->npen, 128), 128, 0, ctx->stream>>>(
+        ewald_vjp_weights_kernel<float><<<blocks_for(ctx->nkv, 128), 128, 0, ctx->stream>>>(
             rp, splits, ctx->nkv, ctx->kw, ctx->pen, ctx->npen, tpl, static_cast<float2 *>(ctx->kwr),
             static_cast<float2 *>(ctx->kwl));
         TRY(launched(ctx));
@@ -2539,7 +2549,7 @@ colatus_status colatus_force_plan(colatus_t ctx, int64_t out[8]) {
         out[1] = kEwNT;
         out[2] = kEwIPT;
         out[4] = ctx->prec == COLATUS_FP32_COMP ? 1 : 0;
-        out[5] = 0;
+        out[5] = ctx->eq_mass && p.n_pad == ctx->N ? 1 : 0;
     } else {
         const F32Variant &fv = f32_variant(p.variant);
         out[1] = fv.nt;

@@ -102,7 +102,9 @@ __device__ __forceinline__ float2 min_image2(float2 d, float2 iL, float2 Lm) {
 //   m_j [ (r^2+eps^2)^{-3/2} + (1/r^2) (e (q_erfc / r + cg) - 1/r) ],
 // e = exp(-alpha^2 r^2), q_erfc = erfc(alpha r) / e from A&S 7.1.26 with
 // t = 1 / (1 + p alpha r); 36 FP32 lane-ops and 4 MUFU results per pair
-// including the minimum image and the accumulation.
+// including the minimum image and the accumulation.  EQM (every body has
+// the same mass): the bracket alone, m folded into the segments (35 ops).
+template <bool EQM>
 __device__ __forceinline__ float2 ewald_pair2(const float2 dx, const float2 dy, const float2 dz,
                                               const float2 mj, const EwaldArgs &A, const float2 e2) {
     float2 r2 = __fmul2_rn(dx, dx);
@@ -128,13 +130,16 @@ __device__ __forceinline__ float2 ewald_pair2(const float2 dx, const float2 dy, 
     const float2 fs = __ffma2_rn(make_float2(A.s1, A.s1), r2, make_float2(A.s0, A.s0));
     f.x = r2.x < A.x2_series ? fs.x : f.x;
     f.y = r2.y < A.x2_series ? fs.y : f.y;
-    return __fmul2_rn(mj, __fadd2_rn(ip3, f));
+    const float2 br = __fadd2_rn(ip3, f);
+    return EQM ? br : __fmul2_rn(mj, br);
 }
 
-template <int NT, int IPT, int JT, int STAGES, int FOLD, bool COMP, int MINB>
+// EQM: every body has mass mass_eq (and no zero-mass padding enters): the
+// pair term drops m_j and the segments are scaled by mass_eq.
+template <int NT, int IPT, int JT, int STAGES, int FOLD, bool COMP, int MINB, bool EQM>
 __global__ void __launch_bounds__(NT, MINB)
     ewald_f32_kernel(const float *__restrict__ pk, float4 *__restrict__ part, int *__restrict__ flags,
-                     ForceLaunch L, float eps2, EwaldArgs A) {
+                     ForceLaunch L, float eps2, EwaldArgs A, float mass_eq) {
     using K = EwaldF32Kernel<NT, IPT, JT, STAGES, FOLD, COMP>;
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *tiles = reinterpret_cast<float4 *>(smem);
@@ -205,7 +210,7 @@ __global__ void __launch_bounds__(NT, MINB)
                             dx = min_image2(dx, iL, Lm);
                             dy = min_image2(dy, iL, Lm);
                             dz = min_image2(dz, iL, Lm);
-                            const float2 s = ewald_pair2(dx, dy, dz, mj, A, e2);
+                            const float2 s = ewald_pair2<EQM>(dx, dy, dz, mj, A, e2);
                             px[k] = __ffma2_rn(dx, s, px[k]);
                             py[k] = __ffma2_rn(dy, s, py[k]);
                             pz[k] = __ffma2_rn(dz, s, pz[k]);
@@ -243,10 +248,11 @@ __global__ void __launch_bounds__(NT, MINB)
         if (bad) break;
         const long long sidx = g - sk_owner(it * n_jt, W, G);
         float4 *dst = part + (it * L.S_max + sidx) * (COMP ? 2 : 1) * (long long)K::ITILE;
+        const float ms = EQM ? mass_eq : 1.f;
 #pragma unroll
         for (int k = 0; k < IPT; ++k) {
-            dst[tid + k * NT] = make_float4(hx[k], hy[k], hz[k], 0.f);
-            if (COMP) dst[K::ITILE + tid + k * NT] = make_float4(lx[k], ly[k], lz[k], 0.f);
+            dst[tid + k * NT] = make_float4(ms * hx[k], ms * hy[k], ms * hz[k], 0.f);
+            if (COMP) dst[K::ITILE + tid + k * NT] = make_float4(ms * lx[k], ms * ly[k], ms * lz[k], 0.f);
         }
     }
     if (bad && tid == 0) {

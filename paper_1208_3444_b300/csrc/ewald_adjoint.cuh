@@ -395,7 +395,8 @@ __global__ void __launch_bounds__(NT)
 
 // ------------------------------------------------------------------ k space
 // Weights of the reciprocal VJP from four channels of partial structure
-// factors rho_part[c][split][k] (c: m, w_x, w_y, w_z), one thread per pencil:
+// factors rho_part[c][split][k] (c: m, w_x, w_y, w_z), one thread per k (its
+// pencil found by bisection on the pencils' first k):
 //   wr[k] = w_k rho(k),  wl[k] = w_k Lambda(k),  Lambda = (2 pi/L) n . W(k).
 template <typename T>
 __global__ void ewald_vjp_weights_kernel(const double2 *__restrict__ rho_part, int splits, int nkv,
@@ -403,29 +404,33 @@ __global__ void ewald_vjp_weights_kernel(const double2 *__restrict__ rho_part, i
                                          const KPencil *__restrict__ pen, int npen, double tpl,
                                          typename Vec2<T>::type *__restrict__ wr,
                                          typename Vec2<T>::type *__restrict__ wl) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= npen) return;
-    const KPencil P = pen[p];
-    for (int q = 0; q < P.len; ++q) {
-        const int k = P.koff + q, nz = P.nz0 + q;
-        double s[4][2];
-        for (int c = 0; c < 4; ++c) {
-            double r = 0.0, i = 0.0;
-            for (int sp = 0; sp < splits; ++sp) {
-                const double2 v = rho_part[((long long)c * splits + sp) * nkv + k];
-                r += v.x;
-                i += v.y;
-            }
-            s[c][0] = r;
-            s[c][1] = i;
-        }
-        const double lr = tpl * (P.nx * s[1][0] + P.ny * s[2][0] + nz * s[3][0]);
-        const double li = tpl * (P.nx * s[1][1] + P.ny * s[2][1] + nz * s[3][1]);
-        wr[k].x = (T)(kw[k] * s[0][0]);
-        wr[k].y = (T)(kw[k] * s[0][1]);
-        wl[k].x = (T)(kw[k] * lr);
-        wl[k].y = (T)(kw[k] * li);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nkv) return;
+    int lo = 0, hi = npen - 1;   // the last pencil with koff <= k
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pen[mid].koff <= k) lo = mid;
+        else hi = mid - 1;
     }
+    const KPencil P = pen[lo];
+    const int nz = P.nz0 + (k - P.koff);
+    double s[4][2];
+    for (int c = 0; c < 4; ++c) {
+        double r = 0.0, i = 0.0;
+        for (int sp = 0; sp < splits; ++sp) {
+            const double2 v = rho_part[((long long)c * splits + sp) * nkv + k];
+            r += v.x;
+            i += v.y;
+        }
+        s[c][0] = r;
+        s[c][1] = i;
+    }
+    const double lr = tpl * (P.nx * s[1][0] + P.ny * s[2][0] + nz * s[3][0]);
+    const double li = tpl * (P.nx * s[1][1] + P.ny * s[2][1] + nz * s[3][1]);
+    wr[k].x = (T)(kw[k] * s[0][0]);
+    wr[k].y = (T)(kw[k] * s[0][1]);
+    wl[k].x = (T)(kw[k] * lr);
+    wl[k].y = (T)(kw[k] * li);
 }
 
 // Reciprocal-space VJP at every body (with wv set: the JVP of one tangent,

@@ -5,6 +5,7 @@ with ncu.
     python -m paper_1208_3444_b300.profile_force --op vjp --workload grid32 --launches 1
     python -m paper_1208_3444_b300.profile_force --periodic 1.0 --workload grid32 --launches 1
     python -m paper_1208_3444_b300.profile_force --op jvp --workload grid32 --launches 1
+    python -m paper_1208_3444_b300.profile_force --op vjp --periodic 1.0 --workload grid32 --launches 1
     python -m paper_1208_3444_b300.profile_force --op ensemble --launches 1
     python -m paper_1208_3444_b300.profile_force --op spectrum --launches 1
     python -m paper_1208_3444_b300.profile_force --op diagnostics --workload grid32 --launches 1
@@ -84,6 +85,8 @@ def main():
     sim = B.Simulation(ic.m, ic.eps, LCDM, 1.0, prec=PRECS[a.prec])
     try:
         sim.set_state(ic.x, ic.v)
+        if a.periodic:
+            sim.set_periodic(a.periodic)
         if a.op == "jvp":
             sim.tangent_init(inputs.tracers(ic.N, 64, 7), a.launches)
             sim.tangent_step(inputs.lcdm_tau(2000), a.launches)
@@ -95,8 +98,6 @@ def main():
                 d = sim.diagnostics()
             print(f"diagnostics {a.workload} N={ic.N} prec={a.prec}: {a.launches} calls, W={d['W']:.9e}")
             return
-        if a.periodic:
-            sim.set_periodic(a.periodic)
         w = np.random.default_rng(1).standard_normal((ic.N, 3))
         sim.profile_forces(True)
         for _ in range(a.launches):
