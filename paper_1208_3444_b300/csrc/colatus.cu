@@ -640,10 +640,27 @@ colatus_status ewald_setup(colatus_t ctx) {
                          : (const void *)ewald_kforce_kernel<float, float4>;
     CU(cudaFuncSetAttribute(frho, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rho));
     CU(cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f));
-    const void *fkv = f64 ? (const void *)ewald_kvjp_kernel<double, double4>
-                          : (const void *)ewald_kvjp_kernel<float, float4>;
-    const size_t smem_kv = f64 ? ew_kvjp_smem<double>(nk) : ew_kvjp_smem<float>(nk);
+    // the derivatives' reciprocal passes (VJP in this precision; the tangent
+    // model's multi-tangent passes in FP32)
+    const void *fkv = f64 ? (const void *)ewald_kvjp_kernel<double, double4, 1>
+                          : (const void *)ewald_kvjp_kernel<float, float4, 1>;
+    const size_t smem_kv = f64 ? ew_kvjp_smem<double, 1>(nk) : ew_kvjp_smem<float, 1>(nk);
     CU(cudaFuncSetAttribute(fkv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_kv));
+    const void *fm4 = f64 ? (const void *)ewald_rho_multi_kernel<double, 4>
+                          : (const void *)ewald_rho_multi_kernel<float, 4>;
+    const size_t smem_m4 = f64 ? ew_rho_multi_smem<double, 4>(nk, ctx->rchunk_np)
+                               : ew_rho_multi_smem<float, 4>(nk, ctx->rchunk_np);
+    CU(cudaFuncSetAttribute(fm4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m4));
+    if (!f64) {
+        CU(cudaFuncSetAttribute(ewald_rho_multi_kernel<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ew_rho_multi_smem<float, 1>(nk, ctx->rchunk_np)));
+        CU(cudaFuncSetAttribute(ewald_rho_multi_kernel<float, 3 * kTB>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ew_rho_multi_smem<float, 3 * kTB>(nk, ctx->rchunk_np)));
+        CU(cudaFuncSetAttribute(ewald_kvjp_kernel<float, float4, kTB>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ew_kvjp_smem<float, kTB>(nk)));
+    }
     return COLATUS_OK;
 }
 
@@ -1223,49 +1240,55 @@ colatus_status kweight_bufs(colatus_t ctx) {
     ctx->kwr = ctx->kwl = nullptr;
     ctx->kwrl_cap = 0;
     CU(cudaMalloc(&ctx->kwr, ctx->nkv * sizeof(double2)));
-    CU(cudaMalloc(&ctx->kwl, ctx->nkv * sizeof(double2)));
+    CU(cudaMalloc(&ctx->kwl, (size_t)kTB * ctx->nkv * sizeof(double2)));   // a plane per tangent
     ctx->kwrl_cap = ctx->nkv;
     return COLATUS_OK;
 }
 
+// Splits of the bodies in the structure-factor passes: enough blocks to
+// fill the GPU, at least ew_bodies<T>() bodies per split.
+template <typename T>
+int ew_splits(colatus_t ctx) {
+    const long long max_split = std::max(1LL, ctx->N / ew_bodies<T>());
+    return (int)std::min<long long>(std::max(1, kEwRhoBlocksPerSM * ctx->num_sms / ctx->nrchunk), max_split);
+}
+
 // Reciprocal-space VJP of the bodies and co-vectors packed in adj.pkw, into
-// lrv: phase tables of the packed positions, four structure-factor passes
-// (weights m, w_x, w_y, w_z), their weights per k, then one pass per body.
+// lrv: phase tables of the packed positions, one pass for the structure
+// factors weighted by m, w_x, w_y, w_z, their weights per k, then one pass
+// per body.
 template <typename T, typename T4>
 colatus_status run_ewald_kspace_vjp(colatus_t ctx) {
     using T2 = typename Vec2<T>::type;
     const bool f64 = sizeof(T) == 8;
     if (!ctx->lrv) CU(cudaMalloc(&ctx->lrv, (size_t)ctx->n_alloc * sizeof(double4)));
     TRY(kweight_bufs(ctx));
-    BodySrc src{f64 ? nullptr : static_cast<const float *>(ctx->adj.pkw),
-                f64 ? static_cast<const double4 *>(ctx->adj.pkw) : nullptr, f64 ? 2 : 16, f64 ? 3 : 6};
+    ChanSrc C{};
+    C.src = BodySrc{f64 ? nullptr : static_cast<const float *>(ctx->adj.pkw),
+                    f64 ? static_cast<const double4 *>(ctx->adj.pkw) : nullptr, f64 ? 2 : 16, f64 ? 3 : 6};
+    C.mode = 0;
+    const int widx[4] = {f64 ? 3 : 6, f64 ? 4 : 8, f64 ? 5 : 10, f64 ? 6 : 12};
+    for (int c = 0; c < 4; ++c) C.widx[c] = widx[c];
     T2 *ph = static_cast<T2 *>(ctx->ph);
-    ewald_phase_kernel<T><<<blocks_for(3 * ctx->N, 128), 128, 0, ctx->stream>>>(src, ctx->N, ctx->ew, ph);
+    ewald_phase_kernel<T><<<blocks_for(3 * ctx->N, 128), 128, 0, ctx->stream>>>(C.src, ctx->N, ctx->ew,
+                                                                                ph);
     TRY(launched(ctx));
-    const int kchunks = ctx->nrchunk;
-    const long long max_split = std::max(1LL, ctx->N / ew_bodies<T>());
-    const int splits = (int)std::min<long long>(std::max(1, kEwRhoBlocksPerSM * ctx->num_sms / kchunks),
-                                                max_split);
+    const int splits = ew_splits<T>(ctx);
     const size_t plane = (size_t)splits * ctx->nkv;
     TRY(grow(ctx, &ctx->rho_part, &ctx->rho_part_bytes, 4 * plane * sizeof(double2)));
-    const size_t smem_rho = ew_rho_smem<T>(ctx->ew.nk, ctx->rchunk_np);
-    const int widx[4] = {f64 ? 3 : 6, f64 ? 4 : 8, f64 ? 5 : 10, f64 ? 6 : 12};
-    for (int c = 0; c < 4; ++c) {
-        src.widx = widx[c];
-        ewald_rho_kernel<T><<<dim3(kchunks, splits), kEwKThreads, smem_rho, ctx->stream>>>(
-            src, ctx->N, ph, ctx->pen, ctx->rchunk, ctx->rchunk_np, ctx->nkv, ctx->ew,
-            static_cast<double2 *>(ctx->rho_part) + c * plane);
-        TRY(launched(ctx));
-    }
-    ewald_vjp_weights_kernel<T><<<blocks_for(ctx->nkv, 128), 128, 0, ctx->stream>>>(
-        static_cast<const double2 *>(ctx->rho_part), splits, ctx->nkv, ctx->kw, ctx->pen, ctx->npen,
-        2.0 * std::acos(-1.0) / ctx->ew.L, static_cast<T2 *>(ctx->kwr), static_cast<T2 *>(ctx->kwl));
+    double2 *rp = static_cast<double2 *>(ctx->rho_part);
+    ewald_rho_multi_kernel<T, 4><<<dim3(ctx->nrchunk, splits), kEwKThreads,
+                                   ew_rho_multi_smem<T, 4>(ctx->ew.nk, ctx->rchunk_np), ctx->stream>>>(
+        C, ctx->N, ph, ctx->pen, ctx->rchunk, ctx->rchunk_np, ctx->nkv, ctx->ew, rp);
     TRY(launched(ctx));
-    src.widx = widx[0];
-    ewald_kvjp_kernel<T, T4><<<blocks_for(ctx->N, kEwFThreads), kEwFThreads * kEwFSlices,
-                               ew_kvjp_smem<T>(ctx->ew.nk), ctx->stream>>>(
-        ctx->N, ph, ctx->pen, ctx->npen, static_cast<const T2 *>(ctx->kwr),
-        static_cast<const T2 *>(ctx->kwl), src, nullptr, ctx->ew, static_cast<T4 *>(ctx->lrv));
+    ewald_vjp_weights_kernel<T><<<blocks_for(ctx->nkv, 128), 128, 0, ctx->stream>>>(
+        rp, rp + plane, splits, ctx->nkv, ctx->kw, ctx->pen, ctx->npen, 2.0 * std::acos(-1.0) / ctx->ew.L,
+        static_cast<T2 *>(ctx->kwr), static_cast<T2 *>(ctx->kwl));
+    TRY(launched(ctx));
+    ewald_kvjp_kernel<T, T4, 1><<<blocks_for(ctx->N, kEwFThreads), kEwFThreads * kEwFSlices,
+                                  ew_kvjp_smem<T, 1>(ctx->ew.nk), ctx->stream>>>(
+        ctx->N, ph, ctx->pen, ctx->npen, ctx->nkv, static_cast<const T2 *>(ctx->kwr),
+        static_cast<const T2 *>(ctx->kwl), C.src, nullptr, 0, 1, ctx->ew, static_cast<T4 *>(ctx->lrv), 0);
     return launched(ctx);
 }
 
@@ -1329,48 +1352,53 @@ TangentState tan_state(colatus_t ctx) {
 
 // Reciprocal-space JVP of every tangent at the positions in pk, into
 // tan.lrt[b]: phase tables and the mass structure factors once, then per
-// tangent three structure-factor passes weighted by m_j dx_j, their per-k
-// weights, and one pass per body (m_i -> 1, w_i -> dx_i).
+// chunk of kTB tangents one pass for the structure factors weighted by
+// m_j dx_j (3 kTB channels), their per-k weights (a plane per tangent), and
+// one pass per body for the chunk (m_i -> 1, w_i -> dx_i).
 colatus_status run_ewald_kspace_jvp(colatus_t ctx, const float *pk) {
     auto &t = ctx->tan;
     if (!t.lrt) CU(cudaMalloc(&t.lrt, (size_t)t.B * t.n_pad * sizeof(float4)));
     TRY(kweight_bufs(ctx));
-    BodySrc src = masses_of(pk, nullptr);
+    ChanSrc C{};
+    C.src = masses_of(pk, nullptr);
+    C.mode = 0;
+    C.widx[0] = 6;
+    C.tdx = t.dx;
+    C.n_pad = t.n_pad;
+    C.B = t.B;
     float2 *ph = static_cast<float2 *>(ctx->ph);
-    ewald_phase_kernel<float><<<blocks_for(3 * ctx->N, 128), 128, 0, ctx->stream>>>(src, ctx->N, ctx->ew,
+    ewald_phase_kernel<float><<<blocks_for(3 * ctx->N, 128), 128, 0, ctx->stream>>>(C.src, ctx->N, ctx->ew,
                                                                                    ph);
     TRY(launched(ctx));
-    const int kchunks = ctx->nrchunk;
-    const long long max_split = std::max(1LL, ctx->N / ew_bodies<float>());
-    const int splits = (int)std::min<long long>(std::max(1, kEwRhoBlocksPerSM * ctx->num_sms / kchunks),
-                                                max_split);
+    const int splits = ew_splits<float>(ctx);
     const size_t plane = (size_t)splits * ctx->nkv;
-    TRY(grow(ctx, &ctx->rho_part, &ctx->rho_part_bytes, 4 * plane * sizeof(double2)));
-    const size_t smem_rho = ew_rho_smem<float>(ctx->ew.nk, ctx->rchunk_np);
+    TRY(grow(ctx, &ctx->rho_part, &ctx->rho_part_bytes, (1 + 3 * kTB) * plane * sizeof(double2)));
     double2 *rp = static_cast<double2 *>(ctx->rho_part);
-    auto rho_pass = [&](const BodySrc &b, double2 *dst) {
-        ewald_rho_kernel<float><<<dim3(kchunks, splits), kEwKThreads, smem_rho, ctx->stream>>>(
-            b, ctx->N, ph, ctx->pen, ctx->rchunk, ctx->rchunk_np, ctx->nkv, ctx->ew, dst);
-        return launched(ctx);
-    };
-    TRY(rho_pass(src, rp));
+    const dim3 grid(ctx->nrchunk, splits);
+    ewald_rho_multi_kernel<float, 1><<<grid, kEwKThreads, ew_rho_multi_smem<float, 1>(ctx->ew.nk, ctx->rchunk_np),
+                                       ctx->stream>>>(C, ctx->N, ph, ctx->pen, ctx->rchunk, ctx->rchunk_np,
+                                                      ctx->nkv, ctx->ew, rp);
+    TRY(launched(ctx));
     const double tpl = 2.0 * std::acos(-1.0) / ctx->ew.L;
-    for (int b = 0; b < t.B; ++b) {
-        BodySrc sb = src;
-        sb.tv = t.dx + (size_t)b * t.n_pad;
-        for (int c = 0; c < 3; ++c) {
-            sb.tc = c;
-            TRY(rho_pass(sb, rp + (c + 1) * plane));
-        }
-        ewald_vjp_weights_kernel<float><<<blocks_for(ctx->nkv, 128), 128, 0, ctx->stream>>>(
-            rp, splits, ctx->nkv, ctx->kw, ctx->pen, ctx->npen, tpl, static_cast<float2 *>(ctx->kwr),
-            static_cast<float2 *>(ctx->kwl));
+    float2 *wr = static_cast<float2 *>(ctx->kwr), *wl = static_cast<float2 *>(ctx->kwl);
+    C.mode = 1;
+    for (int b0 = 0; b0 < t.B; b0 += kTB) {
+        C.b0 = b0;
+        ewald_rho_multi_kernel<float, 3 * kTB>
+            <<<grid, kEwKThreads, ew_rho_multi_smem<float, 3 * kTB>(ctx->ew.nk, ctx->rchunk_np), ctx->stream>>>(
+                C, ctx->N, ph, ctx->pen, ctx->rchunk, ctx->rchunk_np, ctx->nkv, ctx->ew, rp + plane);
         TRY(launched(ctx));
-        ewald_kvjp_kernel<float, float4><<<blocks_for(ctx->N, kEwFThreads), kEwFThreads * kEwFSlices,
-                                           ew_kvjp_smem<float>(ctx->ew.nk), ctx->stream>>>(
-            ctx->N, ph, ctx->pen, ctx->npen, static_cast<const float2 *>(ctx->kwr),
-            static_cast<const float2 *>(ctx->kwl), src, t.dx + (size_t)b * t.n_pad, ctx->ew,
-            t.lrt + (size_t)b * t.n_pad);
+        const int ntan = std::min(kTB, t.B - b0);
+        for (int q = 0; q < ntan; ++q) {
+            ewald_vjp_weights_kernel<float><<<blocks_for(ctx->nkv, 128), 128, 0, ctx->stream>>>(
+                rp, rp + (1 + 3 * q) * plane, splits, ctx->nkv, ctx->kw, ctx->pen, ctx->npen, tpl, wr,
+                wl + (size_t)q * ctx->nkv);
+            TRY(launched(ctx));
+        }
+        ewald_kvjp_kernel<float, float4, kTB><<<blocks_for(ctx->N, kEwFThreads), kEwFThreads * kEwFSlices,
+                                                ew_kvjp_smem<float, kTB>(ctx->ew.nk), ctx->stream>>>(
+            ctx->N, ph, ctx->pen, ctx->npen, ctx->nkv, wr, wl, C.src, t.dx + (size_t)b0 * t.n_pad, t.n_pad,
+            ntan, ctx->ew, t.lrt + (size_t)b0 * t.n_pad, t.n_pad);
         TRY(launched(ctx));
     }
     return COLATUS_OK;

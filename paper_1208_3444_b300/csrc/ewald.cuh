@@ -389,18 +389,14 @@ struct KVec {
 // `rec` double4 per body (1: (x, y, z, m); 2: then (wx, wy, wz, 0)).  The
 // structure factors weigh each body by entry `widx` of its record: the mass
 // (6 in FP32, 3 in FP64) or a co-vector component (8/10/12; 4/5/6).
-// With tv set (FP32 only), the weight is instead the body's mass times
-// component tc (0, 1, 2) of tv[i]: the tangent model's m_j dx_j.
 struct BodySrc {
     const float *pk;
     const double4 *pos;
     int rec, widx;
-    const float4 *tv;
-    int tc;
 };
 
 __host__ __device__ inline BodySrc masses_of(const float *pk, const double4 *pos) {
-    return BodySrc{pk, pos, pos ? 1 : 8, pos ? 3 : 6, nullptr, 0};
+    return BodySrc{pk, pos, pos ? 1 : 8, pos ? 3 : 6};
 }
 
 // Body position as FP64 from either layout.
@@ -425,10 +421,6 @@ __device__ __forceinline__ double body_entry(const BodySrc &b, long long i, int 
 }
 
 __device__ __forceinline__ double body_weight(const BodySrc &b, long long i) {
-    if (b.tv) {
-        const float4 t = b.tv[i];
-        return body_entry(b, i, 6) * (double)(b.tc == 0 ? t.x : (b.tc == 1 ? t.y : t.z));
-    }
     return body_entry(b, i, b.widx);
 }
 

@@ -394,12 +394,14 @@ __global__ void __launch_bounds__(NT)
 }
 
 // ------------------------------------------------------------------ k space
-// Weights of the reciprocal VJP from four channels of partial structure
-// factors rho_part[c][split][k] (c: m, w_x, w_y, w_z), one thread per k (its
+// Weights of the reciprocal VJP (or of one tangent's JVP) from partial
+// structure factors: rho_m[split][k] weighted by m, and three planes
+// rho_w[c][split][k] weighted by w_c (or m dx_c), one thread per k (its
 // pencil found by bisection on the pencils' first k):
 //   wr[k] = w_k rho(k),  wl[k] = w_k Lambda(k),  Lambda = (2 pi/L) n . W(k).
 template <typename T>
-__global__ void ewald_vjp_weights_kernel(const double2 *__restrict__ rho_part, int splits, int nkv,
+__global__ void ewald_vjp_weights_kernel(const double2 *__restrict__ rho_m,
+                                         const double2 *__restrict__ rho_w, int splits, int nkv,
                                          const double *__restrict__ kw,
                                          const KPencil *__restrict__ pen, int npen, double tpl,
                                          typename Vec2<T>::type *__restrict__ wr,
@@ -416,9 +418,10 @@ __global__ void ewald_vjp_weights_kernel(const double2 *__restrict__ rho_part, i
     const int nz = P.nz0 + (k - P.koff);
     double s[4][2];
     for (int c = 0; c < 4; ++c) {
+        const double2 *src = c == 0 ? rho_m : rho_w + (long long)(c - 1) * splits * nkv;
         double r = 0.0, i = 0.0;
         for (int sp = 0; sp < splits; ++sp) {
-            const double2 v = rho_part[((long long)c * splits + sp) * nkv + k];
+            const double2 v = src[(long long)sp * nkv + k];
             r += v.x;
             i += v.y;
         }
@@ -433,22 +436,146 @@ __global__ void ewald_vjp_weights_kernel(const double2 *__restrict__ rho_part, i
     wl[k].y = (T)(kw[k] * li);
 }
 
-// Reciprocal-space VJP at every body (with wv set: the JVP of one tangent,
-// m_i -> 1 and w_i -> wv[i]; out.w is then unused) (blocks of kEwFThreads bodies with
-// kEwFSlices threads per body, each taking every kEwFSlices-th pencil, the
-// bodies' phase tables staged in shared memory as in ewald_kforce_kernel):
+// Channel weights of a multi-channel structure-factor pass: mode 0, entries
+// widx[c] of each body's packed record (the VJP's m, w_x, w_y, w_z); mode 1,
+// m_j dx_b[j] of the tangents b = b0 + c / 3 (component c % 3; 0 past B).
+struct ChanSrc {
+    BodySrc src;
+    int mode;
+    int widx[4];
+    const float4 *tdx;   // [B][n_pad] tangent positions (mode 1)
+    long long n_pad;
+    int b0, B;
+};
+
+__device__ __forceinline__ double chan_weight(const ChanSrc &C, long long j, int c) {
+    if (C.mode == 0) {
+        const int w = c == 0 ? C.widx[0] : (c == 1 ? C.widx[1] : (c == 2 ? C.widx[2] : C.widx[3]));
+        return body_entry(C.src, j, w);
+    }
+    const int b = C.b0 + c / 3;
+    if (b >= C.B) return 0.0;
+    const float4 d = C.tdx[(long long)b * C.n_pad + j];
+    const int q = c % 3;
+    return body_entry(C.src, j, 6) * (double)(q == 0 ? d.x : (q == 1 ? d.y : d.z));
+}
+
+// NCH structure factors in one pass: rho_part[c][split][k] = sum over the
+// split's bodies of w_c(j) exp(i k.x_j).  ewald_rho_kernel's decomposition
+// (k chunks x body splits, one k per thread, batches of bodies staged with
+// their tables); the per-(body, pencil) base holds the bare x-y phase, so a
+// (k, body) pair costs one complex product and two FMAs per channel.
+template <typename T, int NCH>
+__global__ void __launch_bounds__(kEwKThreads)
+    ewald_rho_multi_kernel(ChanSrc C, long long N, const typename Vec2<T>::type *__restrict__ ph,
+                           const KPencil *__restrict__ pen, const int *__restrict__ rchunk,
+                           int np_max, int nkv, EwaldArgs A, double2 *__restrict__ rho_part) {
+    using T2 = typename Vec2<T>::type;
+    constexpr int NB = ew_bodies<T>();
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int nt = A.nk + 1;
+    T2 *tab = reinterpret_cast<T2 *>(sm);                  // [NB][3][nt]
+    T2 *base = tab + NB * 3 * nt;                          // [NB][np_max]
+    T *tw = reinterpret_cast<T *>(base + NB * np_max);     // [NB][NCH]
+    int2 *sp = reinterpret_cast<int2 *>(tw + NB * NCH);    // [np_max]
+    const int p0 = rchunk[blockIdx.x], np = rchunk[blockIdx.x + 1] - p0;
+    const int k0 = pen[p0].koff;
+    const int nkc = pen[p0 + np - 1].koff + pen[p0 + np - 1].len - k0;
+    const int t = threadIdx.x;
+    for (int l = t; l < np; l += kEwKThreads) sp[l] = make_int2(pen[p0 + l].nx, pen[p0 + l].ny);
+    int lp = 0;
+    while (lp + 1 < np && pen[p0 + lp + 1].koff <= k0 + t) ++lp;
+    const int nz = pen[p0 + lp].nz0 + (k0 + t - pen[p0 + lp].koff);
+    const int zrow = 2 * nt + (nz < 0 ? -nz : nz);
+    const T zs = nz < 0 ? (T)-1 : (T)1;
+    const long long per = (N + gridDim.y - 1) / gridDim.y;
+    const long long b0 = (long long)blockIdx.y * per, b1 = min(N, b0 + per);
+    double cr[NCH], ci[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) cr[c] = ci[c] = 0.0;
+    for (long long j0 = b0; j0 < b1; j0 += NB) {
+        const int nb = (int)min((long long)NB, b1 - j0);
+        __syncthreads();
+        const T2 *tsrc = ph + j0 * 3 * nt;
+        for (int q = t; q < nb * 3 * nt; q += kEwKThreads) tab[q] = tsrc[q];
+        for (int q = t; q < nb * NCH; q += kEwKThreads)
+            tw[q] = (T)chan_weight(C, j0 + q / NCH, q % NCH);
+        __syncthreads();
+        for (int q = t; q < nb * np; q += kEwKThreads) {
+            const int b = q / np, l = q - b * np;
+            const int2 P = sp[l];
+            const T2 *tb = tab + b * 3 * nt;
+            const T2 x = tb[P.x];
+            const T2 y = axis_phase<T, T2>(tb + nt, P.y, 1);
+            T2 v;
+            v.x = x.x * y.x - x.y * y.y;
+            v.y = x.x * y.y + x.y * y.x;
+            base[q] = v;
+        }
+        __syncthreads();
+        if (t < nkc) {
+            T pr[NCH], pi[NCH];
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) pr[c] = pi[c] = 0;
+#pragma unroll 2
+            for (int b = 0; b < nb; ++b) {
+                const T2 z = tab[b * 3 * nt + zrow];
+                const T2 w = base[b * np + lp];
+                const T zi = zs * z.y;
+                const T er = w.x * z.x - w.y * zi, ei = w.x * zi + w.y * z.x;
+                const T *wb = tw + b * NCH;
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    pr[c] += wb[c] * er;
+                    pi[c] += wb[c] * ei;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                cr[c] += (double)pr[c];
+                ci[c] += (double)pi[c];
+            }
+        }
+    }
+    if (t < nkc) {
+        const long long plane = (long long)gridDim.y * nkv;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c)
+            rho_part[c * plane + (long long)blockIdx.y * nkv + k0 + t] = make_double2(cr[c], ci[c]);
+    }
+}
+
+// Shared memory of ewald_rho_multi_kernel.
+template <typename T, int NCH>
+__host__ inline size_t ew_rho_multi_smem(int nk, int np_max) {
+    using T2 = typename Vec2<T>::type;
+    constexpr int nb = ew_bodies<T>();
+    return ((size_t)nb * 3 * (nk + 1) + (size_t)nb * np_max) * sizeof(T2) + (size_t)nb * NCH * sizeof(T) +
+           (size_t)np_max * sizeof(int2);
+}
+
+// Reciprocal-space VJP at every body, or (NTAN tangents) the JVP of up to
+// NTAN tangents at once.  VJP (wv null, NTAN = 1): m_i and w_i from the
+// packed record,
 //   out_i = ( (2 pi/L) sum_k n Re[e^{-ik.x_i} (m_i wl - (k.w_i) wr)],
 //             -sum_k Im[e^{-ik.x_i} wl] ).
-// Slices are added in order (deterministic).
-template <typename T, typename T4>
+// JVP: m_i -> 1, w_i -> dx_t[i] = wv[t wstride + i], wl -> the tangent's own
+// plane wl + t nkv, out[t ostride + i] (x, y, z; w unused); the phase and
+// the wr part are shared by the tangents.  Blocks of kEwFThreads bodies with
+// kEwFSlices threads per body, each taking every kEwFSlices-th pencil, the
+// bodies' phase tables staged in shared memory as in ewald_kforce_kernel;
+// the slices are added in order (deterministic).
+template <typename T, typename T4, int NTAN>
 __global__ void __launch_bounds__(kEwFThreads * kEwFSlices)
     ewald_kvjp_kernel(long long N, const typename Vec2<T>::type *__restrict__ ph,
-                      const KPencil *__restrict__ pen, int npen,
+                      const KPencil *__restrict__ pen, int npen, int nkv,
                       const typename Vec2<T>::type *__restrict__ wr,
                       const typename Vec2<T>::type *__restrict__ wl, BodySrc src,
-                      const float4 *__restrict__ wv, EwaldArgs A, T4 *__restrict__ out) {
+                      const float4 *__restrict__ wv, long long wstride, int ntan, EwaldArgs A,
+                      T4 *__restrict__ out, long long ostride) {
     using T2 = typename Vec2<T>::type;
     constexpr int NT = kEwFThreads * kEwFSlices;
+    constexpr int NQ = NTAN == 1 ? 4 : 3 * NTAN;   // reduced quantities per body
     extern __shared__ __align__(16) unsigned char sm[];
     const int nt = A.nk + 1;
     T2 *tab = reinterpret_cast<T2 *>(sm);   // [3 nt][kEwFThreads]
@@ -464,65 +591,101 @@ __global__ void __launch_bounds__(kEwFThreads * kEwFSlices)
     const T2 *mine = tab + bi;
     const T2 *zt = mine + 2 * nt * kEwFThreads;
     const double tpl = 2.0 * acos(-1.0) / A.L;
-    double ax = 0.0, ay = 0.0, az = 0.0, am = 0.0;
+    double acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
     if (i < N) {
-        // the VJP: m_i and w_i from the packed record; the JVP: 1 and dx_i
-        const T m = wv ? (T)1 : (T)body_entry(src, i, src.pos ? 3 : 6);
-        const T wx = wv ? (T)wv[i].x : (T)body_entry(src, i, src.pos ? 4 : 8);
-        const T wy = wv ? (T)wv[i].y : (T)body_entry(src, i, src.pos ? 5 : 10);
-        const T wz = wv ? (T)wv[i].z : (T)body_entry(src, i, src.pos ? 6 : 12);
-        const T c1 = (T)tpl * wz;
+        T m = (T)1, wx[NTAN], wy[NTAN], wz[NTAN];
+        if (!wv) {
+            m = (T)body_entry(src, i, src.pos ? 3 : 6);
+            wx[0] = (T)body_entry(src, i, src.pos ? 4 : 8);
+            wy[0] = (T)body_entry(src, i, src.pos ? 5 : 10);
+            wz[0] = (T)body_entry(src, i, src.pos ? 6 : 12);
+        } else {
+#pragma unroll
+            for (int t = 0; t < NTAN; ++t) {
+                const float4 d = t < ntan ? wv[t * wstride + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+                wx[t] = (T)d.x;
+                wy[t] = (T)d.y;
+                wz[t] = (T)d.z;
+            }
+        }
         for (int p = sl; p < npen; p += kEwFSlices) {
             const KPencil P = pen[p];
             const T2 x = mine[P.nx * kEwFThreads];
             const T2 y = axis_phase<T, T2>(mine + nt * kEwFThreads, P.ny, kEwFThreads);
             const T er = x.x * y.x - x.y * y.y, ei = x.x * y.y + x.y * y.x;
-            const T c0 = (T)tpl * ((T)P.nx * wx + (T)P.ny * wy);
-            const T2 *r0 = wr + (P.koff - P.nz0), *l0 = wl + (P.koff - P.nz0);
-            T B = 0, Bz = 0, M = 0;
+            T c0[NTAN], c1[NTAN], B[NTAN], Bz[NTAN];
+#pragma unroll
+            for (int t = 0; t < NTAN; ++t) {
+                c0[t] = (T)tpl * ((T)P.nx * wx[t] + (T)P.ny * wy[t]);
+                c1[t] = (T)tpl * wz[t];
+                B[t] = Bz[t] = 0;
+            }
+            T M = 0;
+            const long long koff = P.koff - P.nz0;   // wr[koff + nz] is this pencil's k
             for (int nz = P.nz0; nz < P.nz0 + P.len; ++nz) {
                 T2 z = zt[(nz < 0 ? -nz : nz) * kEwFThreads];
                 if (nz < 0) z.y = -z.y;
                 const T Er = er * z.x - ei * z.y, Ei = er * z.y + ei * z.x;   // e^{i k.x_i}
-                const T2 R = r0[nz], W = l0[nz];
+                const T2 R = wr[koff + nz];
                 const T rr = Er * R.x + Ei * R.y;                             // Re[conj(E) wr]
-                const T lr = Er * W.x + Ei * W.y;                             // Re[conj(E) wl]
-                const T li = Er * W.y - Ei * W.x;                             // Im[conj(E) wl]
-                const T tt = m * lr - (c0 + (T)nz * c1) * rr;
-                B += tt;
-                Bz += tt * (T)nz;
-                M += li;
+#pragma unroll
+                for (int t = 0; t < NTAN; ++t) {
+                    const T2 W = wl[t * (long long)nkv + koff + nz];
+                    const T lr = Er * W.x + Ei * W.y;                         // Re[conj(E) wl]
+                    const T tt = m * lr - (c0[t] + (T)nz * c1[t]) * rr;
+                    B[t] += tt;
+                    Bz[t] += tt * (T)nz;
+                    if (NTAN == 1) M += Er * W.y - Ei * W.x;                  // Im[conj(E) wl]
+                }
             }
-            ax += (double)((T)P.nx * B);
-            ay += (double)((T)P.ny * B);
-            az += (double)Bz;
-            am += (double)M;
+#pragma unroll
+            for (int t = 0; t < NTAN; ++t) {
+                acc[3 * t] += (double)((T)P.nx * B[t]);
+                acc[3 * t + 1] += (double)((T)P.ny * B[t]);
+                acc[3 * t + 2] += (double)Bz[t];
+            }
+            if (NTAN == 1) acc[3] += (double)M;
         }
     }
     __syncthreads();
-    double *red = reinterpret_cast<double *>(sm);   // [4][kEwFSlices][kEwFThreads]
-    red[(0 * kEwFSlices + sl) * kEwFThreads + bi] = ax;
-    red[(1 * kEwFSlices + sl) * kEwFThreads + bi] = ay;
-    red[(2 * kEwFSlices + sl) * kEwFThreads + bi] = az;
-    red[(3 * kEwFSlices + sl) * kEwFThreads + bi] = am;
+    double *red = reinterpret_cast<double *>(sm);   // [NQ][kEwFSlices][kEwFThreads]
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) red[(q * kEwFSlices + sl) * kEwFThreads + bi] = acc[q];
     __syncthreads();
     if (sl == 0 && i < N) {
-        double s[4] = {0.0, 0.0, 0.0, 0.0};
+        double sum[NQ];
 #pragma unroll
-        for (int t = 0; t < kEwFSlices; ++t)
-            for (int c = 0; c < 4; ++c) s[c] += red[(c * kEwFSlices + t) * kEwFThreads + bi];
-        out[i].x = (T)(tpl * s[0]);
-        out[i].y = (T)(tpl * s[1]);
-        out[i].z = (T)(tpl * s[2]);
-        out[i].w = (T)(-s[3]);
+        for (int q = 0; q < NQ; ++q) {
+            sum[q] = 0.0;
+            for (int u = 0; u < kEwFSlices; ++u) sum[q] += red[(q * kEwFSlices + u) * kEwFThreads + bi];
+        }
+        if (NTAN == 1) {
+            out[i].x = (T)(tpl * sum[0]);
+            out[i].y = (T)(tpl * sum[1]);
+            out[i].z = (T)(tpl * sum[2]);
+            out[i].w = (T)(-sum[3]);
+        } else {
+#pragma unroll
+            for (int t = 0; t < NTAN; ++t) {
+                if (t >= ntan) break;
+                T4 &o = out[t * ostride + i];
+                o.x = (T)(tpl * sum[3 * t]);
+                o.y = (T)(tpl * sum[3 * t + 1]);
+                o.z = (T)(tpl * sum[3 * t + 2]);
+                o.w = (T)0;
+            }
+        }
     }
 }
 
 // Shared memory of ewald_kvjp_kernel: the tables, or the slice reduction.
-template <typename T>
+template <typename T, int NTAN>
 __host__ inline size_t ew_kvjp_smem(int nk) {
+    constexpr int NQ = NTAN == 1 ? 4 : 3 * NTAN;
     const size_t tabs = (size_t)kEwFThreads * 3 * (nk + 1) * 2 * sizeof(T);
-    const size_t red = (size_t)4 * kEwFSlices * kEwFThreads * sizeof(double);
+    const size_t red = (size_t)NQ * kEwFSlices * kEwFThreads * sizeof(double);
     return tabs > red ? tabs : red;
 }
 

@@ -101,3 +101,24 @@ def test_tracer_spectrum_of_the_paper_scale_run():
     ref = oracle.velocity_spectrum(rec[:, :, 3:].astype(np.float64), TAU, "hann")
     scale = np.abs(ref).max(axis=1, keepdims=True)
     assert np.all(np.abs(E - ref) <= 1e-9 * np.abs(ref) + 1e-10 * scale)
+
+
+def test_periodic_force_vjp_grid32_sampled_rows():
+    # the periodic force VJP the benchmark times (32^3, FP32 compensated
+    # context, unit box), on 192 sampled rows against the oracle's FP64
+    # ewald_vjp (alpha L = 4 for a small oracle k-sum; alpha does not matter,
+    # pinned in test_oracle_ewald_derivatives.py)
+    ic = inputs.grid32()
+    w = inputs.f32(np.random.default_rng(901).standard_normal(ic.x.shape))
+    sim = B.Simulation(ic.m, ic.eps, LCDM_D, 1.0, prec=B.FP32_COMP)
+    try:
+        sim.set_state(ic.x)
+        sim.set_periodic(1.0)
+        gx, gm = sim.force_vjp(w)
+    finally:
+        sim.close()
+    rows = rows32(192, 902)
+    rx, rm = oracle.ewald_vjp(ic.x, ic.m, w, ic.eps, 1.0, alpha=4.0, rows=rows)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    assert rel(gx[rows], rx) < 1e-5
+    assert rel(gm[rows], rm) < 1e-5
