@@ -136,3 +136,25 @@ def test_periodic_adjoint_matches_oracle_transpose(prec, tol):
     assert rel(gm, rm) < tol
     # translation invariance holds in a periodic box too
     assert np.all(np.abs(gx.sum(axis=0)) < 10 * tol * np.abs(gx).sum(axis=0))
+
+
+@pytest.mark.parametrize("prec", [B.FP32, B.FP64])
+def test_periodic_force_vjp_degenerate_cases(prec):
+    # one body: every pair is the self pair (masked in real space, exactly
+    # cancelling in the reciprocal sum); two distinct bodies at one point take
+    # the finite d -> 0 limit of the pair Jacobian; a third body elsewhere
+    rng = np.random.default_rng(940)
+    one_x = inputs.f32(rng.random((1, 3)))
+    gx, gm = periodic_vjp(one_x, np.array([0.7]), inputs.f32(rng.standard_normal((1, 3))), 0.02, 1.0,
+                          prec, 1.0, 1.0)
+    # the reciprocal terms are O(100) each here; they cancel to FP32 / FP64 rounding
+    small = 1e-3 if prec == B.FP32 else 1e-9
+    assert np.abs(gx).max() < small and np.abs(gm).max() < small
+    x = inputs.f32(np.array([[0.3, 0.4, 0.5], [0.3, 0.4, 0.5], [0.8, 0.1, 0.6]]))
+    m = inputs.f32(np.array([0.5, 0.25, 1.0]))
+    w = inputs.f32(rng.standard_normal((3, 3)))
+    gx, gm = periodic_vjp(x, m, w, 0.02, 1.0, prec, 1.0, 1.0)
+    rx, rm = oracle.ewald_vjp(x, m, w, 0.02, 1.0)
+    tol = 1e-5 if prec == B.FP32 else 1e-10
+    assert rel(gx, rx) < tol
+    assert rel(gm, rm) < tol
