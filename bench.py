@@ -325,8 +325,9 @@ def time_adjoint(B, inputs, torch, stream, nsteps=200, k=20):
             "vjp_interactions_per_sm_per_clk": ic.N * ic.N / (vjp * 1e-3) /
             (torch.cuda.get_device_properties(0).multi_processor_count * 2.032e9),
             "vjp_frac_of_lane_op_floor": ic.N * ic.N / (vjp * 1e-3) /
-            (torch.cuda.get_device_properties(0).multi_processor_count * 2.032e9) / (128.0 / 25.0),
-            "vjp_floor_note": "25 FP32 lane-ops per interaction (the scaled form every 32^3 i-tile takes) at 128 lane-ops/SM/clk"}
+            (torch.cuda.get_device_properties(0).multi_processor_count * 2.032e9) / (128.0 / 23.0),
+            "vjp_floor_note": "23 FP32 lane-ops per interaction (the equal-mass form the 32^3 adjoint "
+                              "takes; the general scaled form is 25) at 128 lane-ops/SM/clk"}
 
 
 def time_ensemble(B, inputs, torch, stream, nsteps=48):

@@ -257,6 +257,164 @@ __global__ void __launch_bounds__(NT, MINB)
     }
 }
 
+// Equal-mass VJP (every body has mass m, no zero-mass padding enters).  With
+// u = w_j - w_i the pair weight m_i w_j - m_j w_i is m u, so
+//     dL/dx_i = m sum_j J(d) u = m (U' - 3 V'),
+//     U' = sum inv3 u,  V' = sum inv5 (u . d) d,
+// and, with w_j . d = u . d + w_i . d,
+//     dL/dm_i = -sum inv3 (w_j . d) = -(Gm' + w_i . P_i),  Gm' = sum inv3 (u . d),
+// P_i = sum_j d inv3 = F_i / m the (G-less) force the forward pass already
+// computed at the same positions.  The kernel writes (m (U' - 3 V'), -Gm')
+// per segment and the consumers add -w_i . F_i / m (add_eqm_vjp): 23 FP32
+// lane-ops per interaction instead of 25, and no self-pair mask (u = 0).
+template <int JT, int UNR>
+__device__ __forceinline__ void vjp_eqm_tile(const float4 *__restrict__ t, const float2 (&nx)[4],
+                                             const float2 (&ny)[4], const float2 (&nz)[4],
+                                             const float2 (&nwx)[4], const float2 (&nwy)[4],
+                                             const float2 (&nwz)[4], const float2 e2,
+                                             float2 (&Ux)[4], float2 (&Uy)[4], float2 (&Uz)[4],
+                                             float2 (&Vx)[4], float2 (&Vy)[4], float2 (&Vz)[4],
+                                             float2 (&Gm)[4]) {
+#pragma unroll (UNR)
+    for (int q = 0; q < JT / 2; ++q) {
+        const float4 A = t[4 * q];
+        const float4 Bq = t[4 * q + 1];
+        const float4 C = t[4 * q + 2];
+        const float4 D = t[4 * q + 3];
+        const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
+        const float2 zj = make_float2(Bq.x, Bq.y);
+        const float2 wxj = make_float2(C.x, C.y), wyj = make_float2(C.z, C.w);
+        const float2 wzj = make_float2(D.x, D.y);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 dx = __fadd2_rn(xj, nx[k]);
+            const float2 dy = __fadd2_rn(yj, ny[k]);
+            const float2 dz = __fadd2_rn(zj, nz[k]);
+            float2 r2 = __ffma2_rn(dx, dx, e2);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            const float2 inv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+            const float2 inv2 = __fmul2_rn(inv, inv);
+            const float2 inv3 = __fmul2_rn(inv, inv2);
+            const float2 inv5 = __fmul2_rn(inv3, inv2);
+            const float2 ux = __fadd2_rn(wxj, nwx[k]);
+            const float2 uy = __fadd2_rn(wyj, nwy[k]);
+            const float2 uz = __fadd2_rn(wzj, nwz[k]);
+            Ux[k] = __ffma2_rn(inv3, ux, Ux[k]);
+            Uy[k] = __ffma2_rn(inv3, uy, Uy[k]);
+            Uz[k] = __ffma2_rn(inv3, uz, Uz[k]);
+            float2 du = __fmul2_rn(ux, dx);
+            du = __ffma2_rn(uy, dy, du);
+            du = __ffma2_rn(uz, dz, du);
+            const float2 g = __fmul2_rn(inv5, du);
+            Vx[k] = __ffma2_rn(g, dx, Vx[k]);
+            Vy[k] = __ffma2_rn(g, dy, Vy[k]);
+            Vz[k] = __ffma2_rn(g, dz, Vz[k]);
+            Gm[k] = __ffma2_rn(inv3, du, Gm[k]);
+        }
+    }
+}
+
+// Same launch shape, pipeline and segment layout as vjp_f32_kernel with
+// IPT = 4 (so the VJP's launch plan and consumers apply unchanged).
+template <int NT, int JT, int STAGES, int MINB, int UNR>
+__global__ void __launch_bounds__(NT, MINB)
+    vjp_eqm_f32_kernel(const float *__restrict__ pkw, float4 *__restrict__ part, int *__restrict__ flags,
+                       ForceLaunch L, float eps2) {
+    constexpr int IPT = 4;
+    using K = VjpKernel<NT, IPT, JT, STAGES>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float4 *tiles = reinterpret_cast<float4 *>(smem);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * K::TILE_BYTES);
+    constexpr int TILE_F4 = JT * 2;
+    const int tid = threadIdx.x;
+    const long long G = gridDim.x, g = blockIdx.x;
+    const long long W = L.W;
+    const long long u0 = sk_begin(g, W, G), u1 = sk_begin(g + 1, W, G);
+    const int n_jt = L.n_jt;
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int s = 0; s < STAGES && u0 + s < u1; ++s) {
+            const long long jt = (u0 + s) % n_jt;
+            mbar_arrive_expect_tx(&full[s], K::TILE_BYTES);
+            bulk_load(tiles + s * TILE_F4, pkw + jt * (long long)JT * 8, K::TILE_BYTES, &full[s]);
+        }
+    }
+    const float2 e2 = make_float2(eps2, eps2);
+    long long u = u0;
+    bool bad = false;
+    int stage = 0;
+    uint32_t parity = 0;
+    while (u < u1) {
+        const long long it = u / n_jt;
+        const long long uend = min(u1, (it + 1) * (long long)n_jt);
+        float2 nx[IPT], ny[IPT], nz[IPT], nwx[IPT], nwy[IPT], nwz[IPT];
+        float2 Ux[IPT], Uy[IPT], Uz[IPT], Vx[IPT], Vy[IPT], Vz[IPT], Gm[IPT];
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            const long long i = it * K::ITILE + tid + k * NT;
+            const float *p = pkw + (i >> 1) * 16 + (i & 1);
+            const float x = __ldg(p), y = __ldg(p + 2), z = __ldg(p + 4);
+            const float wx = __ldg(p + 8), wy = __ldg(p + 10), wz = __ldg(p + 12);
+            nx[k] = make_float2(-x, -x);
+            ny[k] = make_float2(-y, -y);
+            nz[k] = make_float2(-z, -z);
+            nwx[k] = make_float2(-wx, -wx);
+            nwy[k] = make_float2(-wy, -wy);
+            nwz[k] = make_float2(-wz, -wz);
+            Ux[k] = Uy[k] = Uz[k] = make_float2(0.f, 0.f);
+            Vx[k] = Vy[k] = Vz[k] = Gm[k] = make_float2(0.f, 0.f);
+        }
+        for (; u < uend; ++u) {
+            const bool ok = mbar_wait_bounded(&full[stage], parity);
+            if (ok)
+                vjp_eqm_tile<JT, UNR>(tiles + stage * TILE_F4, nx, ny, nz, nwx, nwy, nwz, e2, Ux, Uy, Uz,
+                                      Vx, Vy, Vz, Gm);
+            if (__syncthreads_or(!ok)) {
+                bad = true;
+                break;
+            }
+            if (tid == 0 && u + STAGES < u1) {
+                const long long jt = (u + STAGES) % n_jt;
+                mbar_arrive_expect_tx(&full[stage], K::TILE_BYTES);
+                bulk_load(tiles + stage * TILE_F4, pkw + jt * (long long)JT * 8, K::TILE_BYTES,
+                          &full[stage]);
+            }
+            if (++stage == STAGES) {
+                stage = 0;
+                parity ^= 1u;
+            }
+        }
+        if (bad) break;
+        const long long sidx = g - sk_owner(it * n_jt, W, G);
+        float4 *dst = part + (it * L.S_max + sidx) * (long long)K::ITILE;
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            const long long i = it * K::ITILE + tid + k * NT;
+            const float m = __ldg(pkw + (i >> 1) * 16 + (i & 1) + 6);
+            const float gx = m * ((Ux[k].x + Ux[k].y) - 3.f * (Vx[k].x + Vx[k].y));
+            const float gy = m * ((Uy[k].x + Uy[k].y) - 3.f * (Vy[k].x + Vy[k].y));
+            const float gz = m * ((Uz[k].x + Uz[k].y) - 3.f * (Vz[k].x + Vz[k].y));
+            dst[tid + k * NT] = make_float4(gx, gy, gz, -(Gm[k].x + Gm[k].y));
+        }
+    }
+    if (bad && tid == 0) {
+        atomicOr(&flags[FLAG_TIMEOUT], 1);
+        for (long long v = u; v < u1 && v < u + STAGES; ++v) {
+            mbar_wait_bounded(&full[stage], parity);
+            if (++stage == STAGES) {
+                stage = 0;
+                parity ^= 1u;
+            }
+        }
+    }
+}
+
 // FP64 VJP: bodies as two double4 per body, (x, y, z, m) and (wx, wy, wz, 0).
 template <int NT, int JT, int STAGES>
 struct Vjp64Kernel {
@@ -582,6 +740,11 @@ __global__ void adj_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
     }
     float4 g = reduce_vjp_f32(part, L, itile, i);
     add_kspace_vjp(D, i, g);
+    if (D.eqf) {   // the equal-mass VJP's -W_{n+1} . F(x_{n+1}) / m (W still in pkw)
+        float x, y, z, wx, wy, wz;
+        pkw_load(pkw, i, x, y, z, wx, wy, wz);
+        add_eqm_vjp(D, i, wx, wy, wz, g);
+    }
     if (D.on) {   // deformation term at x_{n+1} with W_{n+1} (still in pkw)
         float x, y, z, wx, wy, wz;
         pkw_load(pkw, i, x, y, z, wx, wy, wz);
@@ -611,6 +774,11 @@ __global__ void adj_final_f32_kernel(const float4 *__restrict__ part, ForceLaunc
     if (i >= N) return;
     float4 g = reduce_vjp_f32(part, L, itile, i);
     add_kspace_vjp(D, i, g);
+    if (D.eqf) {
+        float x, y, z, wx, wy, wz;
+        pkw_load(pkw, i, x, y, z, wx, wy, wz);
+        add_eqm_vjp(D, i, wx, wy, wz, g);
+    }
     if (D.on) {
         float x, y, z, wx, wy, wz;
         pkw_load(pkw, i, x, y, z, wx, wy, wz);

@@ -89,6 +89,7 @@ using F64K = F64Kernel<kF64NT, kF64IPT, kF64JT, kStages>;
 // unroll depths on B300 at 32^3); FP64 128 x 1, 32-body tiles
 constexpr int kVjpNT = 256, kVjpIPT = 4, kVjpJT = 256, kVjpMINB = 1, kVjpUnr = 4;
 using VjpK = VjpKernel<kVjpNT, kVjpIPT, kVjpJT, kStages>;
+static_assert(kVjpIPT == 4, "the equal-mass VJP kernel shares the VJP's launch plan (4 i-bodies per thread)");
 constexpr int kV64NT = 128, kV64JT = 32;
 using Vjp64K = Vjp64Kernel<kV64NT, kV64JT, kStages>;
 
@@ -315,6 +316,8 @@ struct colatus_ctx {
         void *rpk[2] = {nullptr, nullptr};       // recompute force inputs
         void *lx = nullptr, *lv = nullptr, *lvh = nullptr, *lm = nullptr;   // adjoint variables
         void *pkw = nullptr;                     // bodies + co-vector for the VJP
+        void *seg_f = nullptr;                   // [k+1][n_alloc] forces of a segment (equal-mass VJP)
+        size_t segf_bytes = 0;
     } adj;
 
     // force-kernel timing (colatus_profile_forces)
@@ -909,7 +912,8 @@ void free_all(colatus_t ctx) {
         if (p) cudaFree(p);
     void *aptrs[] = {ctx->adj.ck_x, ctx->adj.ck_v, ctx->adj.seg_x, ctx->adj.table, ctx->adj.rclk,
                      ctx->adj.rvs, ctx->adj.rvh, ctx->adj.racc, ctx->adj.rpk[0], ctx->adj.rpk[1],
-                     ctx->adj.lx, ctx->adj.lv, ctx->adj.lvh, ctx->adj.lm, ctx->adj.pkw};
+                     ctx->adj.lx, ctx->adj.lv, ctx->adj.lvh, ctx->adj.lm, ctx->adj.pkw,
+                     ctx->adj.seg_f};
     for (void *p : aptrs)
         if (p) cudaFree(p);
     if (ctx->cstream) cudaStreamSynchronize(ctx->cstream);
@@ -1293,8 +1297,9 @@ colatus_status run_ewald_kspace_vjp(colatus_t ctx) {
 }
 
 // One VJP launch on the packed bodies + co-vectors in adj.pkw (with periodic
-// boundaries: the real-space kernel, then the reciprocal-space VJP).
-colatus_status run_vjp(colatus_t ctx) {
+// boundaries: the real-space kernel, then the reciprocal-space VJP; eqm: the
+// equal-mass FP32 kernel, whose consumers need the forces at the positions).
+colatus_status run_vjp(colatus_t ctx, bool eqm = false) {
     const bool f64 = ctx->prec == COLATUS_FP64;
     const ForcePlan &p = vjp_plan(ctx);
     TRY(ensure_part(ctx, p.part_bytes));
@@ -1308,6 +1313,11 @@ colatus_status run_vjp(colatus_t ctx) {
             <<<p.L.G, kEwVjpNT, EwVjpK::SMEM, ctx->stream>>>(
                 static_cast<const float *>(ctx->adj.pkw), static_cast<float4 *>(ctx->part), ctx->flags,
                 p.L, (float)(ctx->eps * ctx->eps), ctx->ew);
+    else if (eqm)
+        vjp_eqm_f32_kernel<kVjpNT, kVjpJT, kStages, kVjpMINB, kVjpUnr>
+            <<<p.L.G, kVjpNT, VjpK::SMEM, ctx->stream>>>(
+                static_cast<const float *>(ctx->adj.pkw), static_cast<float4 *>(ctx->part),
+                ctx->flags, p.L, (float)(ctx->eps * ctx->eps));
     else if (f64)
         vjp_f64_kernel<kV64NT, kV64JT, kStages><<<p.L.G, kV64NT, Vjp64K::SMEM, ctx->stream>>>(
             static_cast<const double4 *>(ctx->adj.pkw), static_cast<double4 *>(ctx->part),
@@ -2093,6 +2103,22 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
     const ForcePlan &pv = vjp_plan(ctx);
     const long long NS = a.nsteps;
     const unsigned nbv = blocks_for(pv.n_pad, 256);
+    // Equal masses, isolated boundaries, no deformation term and no padding in
+    // the VJP's tiles: the equal-mass VJP, whose mass gradient takes the force
+    // at each position; the recompute keeps them (seg_f, slot n - s0 for x_n).
+    const bool eqm = !f64 && ctx->eq_mass && !ctx->periodic && ctx->defo_C == 0.0 && pv.n_pad == ctx->N;
+    if (eqm) TRY(grow(ctx, &a.seg_f, &a.segf_bytes, (size_t)(a.k + 1) * plane));
+    auto fslot = [&](long long j) {
+        return static_cast<float4 *>(a.seg_f) + (size_t)j * ctx->n_alloc;
+    };
+    auto vjp_args = [&](const float4 *f) {
+        Extra D = vjp_extra(ctx);
+        if (eqm) {
+            D.eqf = f;
+            D.eqminv = 1.f / ctx->mass_eq;
+        }
+        return D;
+    };
     if (f64)
         adj_init_f64_kernel<<<nbv, 256, 0, ctx->stream>>>(
             sx, sv, sm, in64, ctx->xs64, static_cast<double4 *>(a.lx), static_cast<double4 *>(a.lv),
@@ -2110,13 +2136,20 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
         auto pos = [&](long long n) -> void * {
             return n == s0 ? (void *)ckx : (void *)(static_cast<char *>(a.seg_x) + (n - s0) * plane);
         };
-        if (s1 - s0 > 1) {
+        if (eqm) {
+            // F(x_{s1}): the forward's last force, or the checkpoint force of
+            // the segment swept before this one (its slot 0)
+            const void *src = c == a.nck - 1 ? (const void *)ctx->acc : (const void *)fslot(0);
+            CU(cudaMemcpyAsync(fslot(s1 - s0), src, (size_t)ctx->N * sizeof(float4),
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+        if (s1 - s0 > 1 || eqm) {
             // recompute x_{s0+1} .. x_{s1-1} with the forward's own kernels
             StepBufs b;
             b.xs = reinterpret_cast<float4 *>(ckx);
             b.vs = reinterpret_cast<float4 *>(ckv);
             b.vh = static_cast<float4 *>(a.rvh);
-            b.acc = static_cast<float4 *>(a.racc);
+            b.acc = eqm ? fslot(0) : static_cast<float4 *>(a.racc);
             b.pk[0] = static_cast<float *>(a.rpk[0]);
             b.pk[1] = static_cast<float *>(a.rpk[1]);
             b.xs64 = reinterpret_cast<double4 *>(ckx);
@@ -2162,12 +2195,13 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
             for (long long n = s0; n < s1 - 1; ++n) {
                 b.xs = static_cast<float4 *>(pos(n + 1));
                 b.xs64 = static_cast<double4 *>(pos(n + 1));
+                if (eqm) b.acc = fslot(n + 1 - s0);
                 TRY(launch_step(ctx, b, cur, n, a.tau));
                 cur ^= 1;
             }
         }
         for (long long n = s1 - 1; n >= s0; --n) {
-            TRY(run_vjp(ctx));
+            TRY(run_vjp(ctx, eqm));
             TRY(prof_begin(ctx));
             if (f64)
                 adj_step_f64_kernel<<<nbv, 256, 0, ctx->stream>>>(
@@ -2182,12 +2216,12 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
                     static_cast<const float4 *>(pos(n)), static_cast<float4 *>(a.lx),
                     static_cast<float4 *>(a.lv), static_cast<float4 *>(a.lvh),
                     static_cast<float *>(a.lm), a.table, n, a.tau, static_cast<float *>(a.pkw),
-                    ctx->N, pv.n_pad, vjp_extra(ctx));
+                    ctx->N, pv.n_pad, vjp_args(eqm ? fslot(n + 1 - s0) : nullptr));
             TRY(launched(ctx));
             TRY(prof_end(ctx, 2));
         }
     }
-    TRY(run_vjp(ctx));
+    TRY(run_vjp(ctx, eqm));   // at x_0 (F(x_0): slot 0 of the first segment)
     const unsigned nb = blocks_for(ctx->N, 256);
     void *dgx = on_device ? gx_0 : (gx_0 ? (void *)ctx->stage : nullptr);
     void *dgv = on_device ? gv_0 : (gv_0 ? (void *)ctx->stage2 : nullptr);
@@ -2207,7 +2241,7 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
                                                           pv.L, pv.itile, static_cast<float4 *>(a.lx),
                                                           static_cast<float *>(a.lm), ctx->N,
                                                           static_cast<const float *>(a.pkw),
-                                                          vjp_extra(ctx));
+                                                          vjp_args(eqm ? fslot(0) : nullptr));
         TRY(launched(ctx));
         adj_store_kernel<float4, float><<<nb, 256, 0, ctx->stream>>>(
             static_cast<const float4 *>(a.lx), static_cast<const float4 *>(a.lv),

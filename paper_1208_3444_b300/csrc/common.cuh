@@ -148,17 +148,23 @@ struct Cosmo {
     double Omega_R, Omega_M, Omega_K, Omega_L, H0;
 };
 
-// O(N) per-body terms the epilogues add to the pair sum (both G-less, like
+// O(N) per-body terms the epilogues add to the pair sum (all G-less, like
 // the raw force):
 //  * the Eq. 6 deformation pull kappa (x_psi - x) / (|x - x_psi|^2 + eps^2)^{3/2}
 //    with kappa = C psi / G (a fixed point mass C psi / G at x_psi), when on;
 //  * the reciprocal-space part of the periodic (Ewald) force, lr32 / lr64[i],
-//    when not null.
+//    when not null (in the VJP and tangent consumers: that part of the VJP or
+//    JVP);
+//  * for the equal-mass FP32 VJP (vjp_eqm_f32_kernel): the forces at the VJP's
+//    positions, eqf, and 1 / m, whose term -w_i . F_i / m the VJP consumers
+//    add to dL/dm_i, when eqf is not null.
 struct Extra {
     double kappa, x, y, z, eps2;
     int on, pad;
     const float4 *lr32;
     const double4 *lr64;
+    const float4 *eqf;
+    float eqminv;
 };
 
 __device__ __forceinline__ void defo_force(const Extra &D, double px, double py, double pz, double &fx,
@@ -201,6 +207,14 @@ __device__ __forceinline__ void add_long_range(const Extra &E, long long i, doub
     fx += l.x;
     fy += l.y;
     fz += l.z;
+}
+
+// The equal-mass VJP's per-body term of dL/dm_i: -w_i . F_i / m.
+__device__ __forceinline__ void add_eqm_vjp(const Extra &E, long long i, float wx, float wy, float wz,
+                                            float4 &g) {
+    if (!E.eqf) return;
+    const float4 f = E.eqf[i];
+    g.w -= E.eqminv * (wx * f.x + wy * f.y + wz * f.z);
 }
 
 // Add the reciprocal-space part of a periodic VJP (x, y, z: dL/dx; w:
