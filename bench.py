@@ -45,7 +45,7 @@ FORCE_KERNEL_TRAFFIC = {
     "plan": dict(kind="force_f32", threads=512, ipt=4, jt=512, comp=True, eqm=True),
     "template": "force_f32_kernel<512, 4, 512, 4, 256, true, true, 1, 2>",
     "sources": ("paper_1208_3444_b300/csrc/force.cuh", "paper_1208_3444_b300/csrc/common.cuh"),
-    "sha256": "579503cbf47a53d099b67805f5c51d20b571a8d933235e5a03b557ae8542ee1f",
+    "sha256": "b5483b303868655cc85ddffdc25f92dca08c68853a68b8e7584418c7ba70a439",
 }
 
 

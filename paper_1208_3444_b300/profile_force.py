@@ -5,12 +5,15 @@ with ncu.
     python -m paper_1208_3444_b300.profile_force --op vjp --workload grid32 --launches 1
     python -m paper_1208_3444_b300.profile_force --periodic 1.0 --workload grid32 --launches 1
     python -m paper_1208_3444_b300.profile_force --op jvp --workload grid32 --launches 1
+    python -m paper_1208_3444_b300.profile_force --op adjoint --workload grid32 --launches 2
     python -m paper_1208_3444_b300.profile_force --op vjp --periodic 1.0 --workload grid32 --launches 1
     python -m paper_1208_3444_b300.profile_force --op ensemble --launches 1
     python -m paper_1208_3444_b300.profile_force --op spectrum --launches 1
     python -m paper_1208_3444_b300.profile_force --op diagnostics --workload grid32 --launches 1
 
---op force runs colatus_forces (the force kernel, or with --periodic L the
+--op adjoint runs colatus_adjoint_forward over --launches steps (checkpoints
+every step) and colatus_adjoint_backward (the equal-mass VJP for equal-mass
+workloads); --op force runs colatus_forces (the force kernel, or with --periodic L the
 Ewald real-space and k-space kernels); --op vjp runs colatus_force_vjp with a
 seeded co-vector; --op jvp runs tangent steps of 64 single-tracer tangents
 (one JVP launch each); --op ensemble runs force evaluations of the
@@ -55,7 +58,8 @@ def main():
                    help="grid16 | grid32 | uniform<N> | plummer<N>")
     p.add_argument("--prec", default="comp", choices=sorted(PRECS))
     p.add_argument("--launches", type=int, default=1)
-    p.add_argument("--op", default="force", choices=["force", "vjp", "jvp", "ensemble", "spectrum", "diagnostics"])
+    p.add_argument("--op", default="force", choices=["force", "vjp", "jvp", "adjoint", "ensemble", "spectrum",
+                            "diagnostics"])
     p.add_argument("--periodic", type=float, default=0.0, help="box side L (0: isolated)")
     a = p.parse_args()
     if a.op == "ensemble":
@@ -92,6 +96,14 @@ def main():
             sim.tangent_step(inputs.lcdm_tau(2000), a.launches)
             sim.synchronize()
             print(f"jvp {a.workload} N={ic.N}: {a.launches} tangent steps of 64 tangents")
+            return
+        if a.op == "adjoint":
+            sim.adjoint_forward(inputs.lcdm_tau(2000), a.launches, 1)
+            gv = np.zeros((ic.N, 3))
+            gv[inputs.tracers(ic.N, 64, 7)] = 1.0
+            sim.adjoint_backward(None, gv)
+            sim.synchronize()
+            print(f"adjoint {a.workload} N={ic.N} prec={a.prec}: {a.launches} steps forward and back")
             return
         if a.op == "diagnostics":
             for _ in range(a.launches):
