@@ -311,12 +311,12 @@ colatus_status colatus_set_tuning(colatus_t ctx, int shape);
 colatus_status colatus_force_vjp(colatus_t ctx, const void *w, void *gx, void *gm, int dtype,
                                  int on_device);
 
-/* Forward pass of the discrete adjoint (KDK only): advances the state by
- * nsteps steps of size dt exactly as colatus_step does, keeping a checkpoint
- * of (x, v) every checkpoint_every steps (device memory: nsteps /
- * checkpoint_every checkpoints of N bodies, plus checkpoint_every positions
- * for recomputation).  Errors: COLATUS_E_ARG (DKD scheme, sizes),
- * COLATUS_E_STATE (no state). */
+/* Forward pass of the discrete adjoint, for any of the three schemes:
+ * advances the state by nsteps steps of size dt exactly as colatus_step
+ * does, keeping a checkpoint of (x, v) every checkpoint_every steps (device
+ * memory: nsteps / checkpoint_every checkpoints of N bodies, plus
+ * checkpoint_every positions for recomputation, and as many velocities for
+ * DKD).  Errors: COLATUS_E_ARG (sizes), COLATUS_E_STATE (no state). */
 colatus_status colatus_adjoint_forward(colatus_t ctx, double dt, int64_t nsteps,
                                        int64_t checkpoint_every);
 
@@ -327,9 +327,11 @@ colatus_status colatus_adjoint_forward(colatus_t ctx, double dt, int64_t nsteps,
  * N x 3, gm: N; any may be NULL).  It is the exact transpose of the FP32 (or
  * FP64) leapfrog that was run: each segment between checkpoints is
  * recomputed with the forward's own kernels, then swept backwards with one
- * VJP (colatus_force_vjp's kernel) per step.  The state (the forward's end)
- * is left as it was.  Errors: COLATUS_E_STATE (no forward pass, or the state
- * was stepped or reconfigured since). */
+ * VJP (colatus_force_vjp's kernel) per step, at x_{n+1} for KDK and at the
+ * half-drift position x_n + (dt/2) v_n for DKD (Eqs. 3-5), plus one at x_0
+ * for KDK.  The state (the forward's end) is left as it was.  Errors:
+ * COLATUS_E_STATE (no forward pass, or the state was stepped, or the
+ * precision, scheme or G changed since). */
 colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const void *gv_T,
                                         const void *gm_T, void *gx_0, void *gv_0, void *gm,
                                         int dtype, int on_device);

@@ -869,6 +869,93 @@ __global__ void adj_final_f64_kernel(const double4 *__restrict__ part, ForceLaun
     lm[i] += g.w;
 }
 
+// ------------------------------------------------ adjoint of the DKD leapfrog
+// Forward step n (Eqs. 3-5; c_n, d_n at t^{n+1/2}):
+//   xh_n = x_n + (tau/2) v_n;  v_{n+1} = c_n v_n + d_n F(xh_n);
+//   x_{n+1} = xh_n + (tau/2) v_{n+1}.
+// Its transpose, from the adjoints (lx, lv) of step n+1:
+//   lvt = lv + (tau/2) lx;  W_n = d_n lvt;  (g_x, g_m) = VJP at xh_n with W_n;
+//   lx_n = lx + g_x;  lm += g_m;  lv_n = c_n lvt + (tau/2) lx_n.
+// Two element-wise kernels per step bracket the VJP: the pack of (xh_n, W_n),
+// with xh_n formed by the forward's own half drift (bitwise the position the
+// forward evaluated F at), and the update.
+__global__ void dkd_adj_pack_f32_kernel(const float4 *__restrict__ xn, const float4 *__restrict__ vn,
+                                        const float4 *__restrict__ lx, const float4 *__restrict__ lv,
+                                        const StepCoef *__restrict__ table, long long n, double tau,
+                                        float *pkw, long long N, long long N_pad) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N_pad) return;
+    if (i >= N) {
+        pkw_store(pkw, i, make_float4(0.f, 0.f, 0.f, 0.f), 0.f, 0.f, 0.f);
+        return;
+    }
+    const float h = (float)(0.5 * tau), d = (float)table[n].d;
+    const float4 x = xn[i], v = vn[i], ax = lx[i], av = lv[i];
+    const float4 xh = make_float4(drift1(x.x, h, v.x), drift1(x.y, h, v.y), drift1(x.z, h, v.z), x.w);
+    pkw_store(pkw, i, xh, d * drift1(av.x, h, ax.x), d * drift1(av.y, h, ax.y), d * drift1(av.z, h, ax.z));
+}
+
+__global__ void dkd_adj_update_f32_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
+                                          float4 *lx, float4 *lv, float *lm,
+                                          const StepCoef *__restrict__ table, long long n, double tau,
+                                          const float *__restrict__ pkw, long long N, Extra D) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float4 g = reduce_vjp_f32(part, L, itile, i);
+    add_kspace_vjp(D, i, g);
+    if (D.on) {   // deformation term at xh_n with W_n (in pkw)
+        float x, y, z, wx, wy, wz;
+        pkw_load(pkw, i, x, y, z, wx, wy, wz);
+        defo_jacobian<float>(D, x, y, z, wx, wy, wz, g.x, g.y, g.z);
+    }
+    const float h = (float)(0.5 * tau), c = (float)table[n].c;
+    const float4 ax = lx[i], av = lv[i];
+    const float tx = drift1(av.x, h, ax.x), ty = drift1(av.y, h, ax.y), tz = drift1(av.z, h, ax.z);
+    const float nx = ax.x + g.x, ny = ax.y + g.y, nz = ax.z + g.z;
+    lx[i] = make_float4(nx, ny, nz, 0.f);
+    lv[i] = make_float4(kick2(c, tx, h, nx), kick2(c, ty, h, ny), kick2(c, tz, h, nz), 0.f);
+    lm[i] += g.w;
+}
+
+__global__ void dkd_adj_pack_f64_kernel(const double4 *__restrict__ xn, const double4 *__restrict__ vn,
+                                        const double4 *__restrict__ lx, const double4 *__restrict__ lv,
+                                        const StepCoef *__restrict__ table, long long n, double tau,
+                                        double4 *bw, long long N, long long N_pad) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N_pad) return;
+    if (i >= N) {
+        bw[2 * i] = make_double4(0.0, 0.0, 0.0, 0.0);
+        bw[2 * i + 1] = make_double4(0.0, 0.0, 0.0, 0.0);
+        return;
+    }
+    const double h = 0.5 * tau, d = table[n].d;
+    const double4 x = xn[i], v = vn[i], ax = lx[i], av = lv[i];
+    bw[2 * i] = make_double4(drift1(x.x, h, v.x), drift1(x.y, h, v.y), drift1(x.z, h, v.z), x.w);
+    bw[2 * i + 1] = make_double4(d * drift1(av.x, h, ax.x), d * drift1(av.y, h, ax.y),
+                                 d * drift1(av.z, h, ax.z), 0.0);
+}
+
+__global__ void dkd_adj_update_f64_kernel(const double4 *__restrict__ part, ForceLaunch L, int itile,
+                                          double4 *lx, double4 *lv, double *lm,
+                                          const StepCoef *__restrict__ table, long long n, double tau,
+                                          const double4 *__restrict__ bw, long long N, Extra D) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double4 g = reduce_vjp_f64(part, L, itile, i);
+    add_kspace_vjp(D, i, g);
+    if (D.on) {
+        const double4 p = bw[2 * i], w = bw[2 * i + 1];
+        defo_jacobian<double>(D, p.x, p.y, p.z, w.x, w.y, w.z, g.x, g.y, g.z);
+    }
+    const double h = 0.5 * tau, c = table[n].c;
+    const double4 ax = lx[i], av = lv[i];
+    const double tx = drift1(av.x, h, ax.x), ty = drift1(av.y, h, ax.y), tz = drift1(av.z, h, ax.z);
+    const double nx = ax.x + g.x, ny = ax.y + g.y, nz = ax.z + g.z;
+    lx[i] = make_double4(nx, ny, nz, 0.0);
+    lv[i] = make_double4(kick2(c, tx, h, nx), kick2(c, ty, h, ny), kick2(c, tz, h, nz), 0.0);
+    lm[i] += g.w;
+}
+
 // Adjoint results in the caller's dtype: gx (N x 3), gv (N x 3), gm (N).
 template <typename T4, typename T>
 __global__ void adj_store_kernel(const T4 *__restrict__ lx, const T4 *__restrict__ lv,

@@ -306,6 +306,8 @@ struct colatus_ctx {
         int k = 0, nck = 0;
         double tau = 0.0;
         colatus_prec prec = COLATUS_FP32;
+        colatus_scheme scheme = COLATUS_KDK;      // of the recorded pass
+        double G = 1.0;
         size_t ck_bytes = 0, seg_bytes = 0, tab_bytes = 0;
         void *ck_x = nullptr, *ck_v = nullptr;   // [nck][n_alloc] checkpoints (float4 / double4)
         void *seg_x = nullptr;                   // [k][n_alloc] recomputed positions
@@ -318,6 +320,8 @@ struct colatus_ctx {
         void *pkw = nullptr;                     // bodies + co-vector for the VJP
         void *seg_f = nullptr;                   // [k+1][n_alloc] forces of a segment (equal-mass VJP)
         size_t segf_bytes = 0;
+        void *seg_v = nullptr;                   // [k][n_alloc] recomputed velocities (DKD)
+        size_t segv_bytes = 0;
     } adj;
 
     // force-kernel timing (colatus_profile_forces)
@@ -913,7 +917,7 @@ void free_all(colatus_t ctx) {
     void *aptrs[] = {ctx->adj.ck_x, ctx->adj.ck_v, ctx->adj.seg_x, ctx->adj.table, ctx->adj.rclk,
                      ctx->adj.rvs, ctx->adj.rvh, ctx->adj.racc, ctx->adj.rpk[0], ctx->adj.rpk[1],
                      ctx->adj.lx, ctx->adj.lv, ctx->adj.lvh, ctx->adj.lm, ctx->adj.pkw,
-                     ctx->adj.seg_f};
+                     ctx->adj.seg_f, ctx->adj.seg_v};
     for (void *p : aptrs)
         if (p) cudaFree(p);
     if (ctx->cstream) cudaStreamSynchronize(ctx->cstream);
@@ -2011,8 +2015,6 @@ colatus_status colatus_adjoint_forward(colatus_t ctx, double dt, int64_t nsteps,
     if (nsteps < 1 || checkpoint_every < 1)
         return fail(ctx, COLATUS_E_ARG, "nsteps and checkpoint_every must be >= 1");
     if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
-    if (!is_kdk(ctx))
-        return fail(ctx, COLATUS_E_ARG, "the adjoint is built for the KDK scheme");
     auto &a = ctx->adj;
     a.ready = false;
     TRY(adj_alloc(ctx));
@@ -2064,6 +2066,8 @@ colatus_status colatus_adjoint_forward(colatus_t ctx, double dt, int64_t nsteps,
     a.nck = nck;
     a.tau = dt;
     a.prec = ctx->prec;
+    a.scheme = ctx->scheme;
+    a.G = ctx->G;
     return COLATUS_OK;
 }
 
@@ -2076,8 +2080,9 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
     TRY(check_dtype(ctx, dtype));
     auto &a = ctx->adj;
     if (!a.ready) return fail(ctx, COLATUS_E_STATE, "no adjoint forward pass recorded");
-    if (ctx->host_step != a.step0 + a.nsteps || ctx->prec != a.prec)
-        return fail(ctx, COLATUS_E_STATE, "the state moved on since the adjoint forward pass");
+    if (ctx->host_step != a.step0 + a.nsteps || ctx->prec != a.prec || ctx->scheme != a.scheme ||
+        ctx->G != a.G)
+        return fail(ctx, COLATUS_E_STATE, "the state or the configuration changed since the adjoint forward pass");
     CU(cudaStreamWaitEvent(ctx->stream, a.tab_ev, 0));   // the forward's schedule
     const bool f64 = ctx->prec == COLATUS_FP64;
     const int in64 = dtype == COLATUS_F64;
@@ -2106,8 +2111,13 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
     // Equal masses, isolated boundaries, no deformation term and no padding in
     // the VJP's tiles: the equal-mass VJP, whose mass gradient takes the force
     // at each position; the recompute keeps them (seg_f, slot n - s0 for x_n).
-    const bool eqm = !f64 && ctx->eq_mass && !ctx->periodic && ctx->defo_C == 0.0 && pv.n_pad == ctx->N;
+    // DKD (Eqs. 3-5): one VJP per step at the half-drift position xh_n, formed
+    // from the segment's positions and velocities (seg_v keeps the latter).
+    const bool dkd = a.scheme == COLATUS_DKD;
+    const bool eqm = !dkd && !f64 && ctx->eq_mass && !ctx->periodic && ctx->defo_C == 0.0 &&
+                     pv.n_pad == ctx->N;
     if (eqm) TRY(grow(ctx, &a.seg_f, &a.segf_bytes, (size_t)(a.k + 1) * plane));
+    if (dkd) TRY(grow(ctx, &a.seg_v, &a.segv_bytes, (size_t)a.k * plane));
     auto fslot = [&](long long j) {
         return static_cast<float4 *>(a.seg_f) + (size_t)j * ctx->n_alloc;
     };
@@ -2136,6 +2146,9 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
         auto pos = [&](long long n) -> void * {
             return n == s0 ? (void *)ckx : (void *)(static_cast<char *>(a.seg_x) + (n - s0) * plane);
         };
+        auto vel = [&](long long n) -> void * {
+            return n == s0 ? (void *)ckv : (void *)(static_cast<char *>(a.seg_v) + (n - s0) * plane);
+        };
         if (eqm) {
             // F(x_{s1}): the forward's last force, or the checkpoint force of
             // the segment swept before this one (its slot 0)
@@ -2162,45 +2175,96 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
             b.tcap = (int)NS;
             b.clk = a.rclk;
             b.tr = Tracers{nullptr, nullptr, 1, 0, 0};
-            // F at the checkpoint
-            if (f64) {
-                const ForcePlan &p = plan_f64(ctx);
-                pack_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
-                    b.xs64, b.pos64[0], ctx->N, p.n_pad);
+            if (dkd) {
+                // the DKD steps update the velocity in place: start from a copy
+                // of the checkpoint's, then the half drift into the force input
+                CU(cudaMemcpyAsync(a.rvs, ckv, (size_t)ctx->N * body, cudaMemcpyDeviceToDevice,
+                                   ctx->stream));
+                b.vs = static_cast<float4 *>(a.rvs);
+                b.vs64 = static_cast<double4 *>(a.rvs);
+                if (f64) {
+                    const ForcePlan &p = plan_f64(ctx);
+                    dkd_open_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+                        b.xs64, b.vs64, b.pos64[1], a.tau, ctx->N, p.n_pad);
+                } else {
+                    const ForcePlan &p = plan_f32(ctx);
+                    dkd_open_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+                        b.xs, b.vs, b.pk[1], a.tau, ctx->N, p.n_pad);
+                }
                 TRY(launched(ctx));
-                TRY(run_force_f64(ctx, b.pos64[0]));
-                forces_out_f64_kernel<<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
-                    static_cast<const double4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk, ctx->G,
-                    nullptr, 0, b.acc64, b.pos64[0], extra_args(ctx));
             } else {
-                const ForcePlan &p = plan_f32(ctx);
-                pack_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
-                    b.xs, b.pk[0], ctx->N, p.n_pad);
+                // F at the checkpoint
+                if (f64) {
+                    const ForcePlan &p = plan_f64(ctx);
+                    pack_f64_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+                        b.xs64, b.pos64[0], ctx->N, p.n_pad);
+                    TRY(launched(ctx));
+                    TRY(run_force_f64(ctx, b.pos64[0]));
+                    forces_out_f64_kernel<<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
+                        static_cast<const double4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk, ctx->G,
+                        nullptr, 0, b.acc64, b.pos64[0], extra_args(ctx));
+                } else {
+                    const ForcePlan &p = plan_f32(ctx);
+                    pack_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(
+                        b.xs, b.pk[0], ctx->N, p.n_pad);
+                    TRY(launched(ctx));
+                    TRY(run_force_f32(ctx, p, b.pk[0]));
+                    if (ctx->prec == COLATUS_FP32_COMP)
+                        forces_out_f32_kernel<true><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
+                            static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk,
+                            ctx->G, nullptr, 0, b.acc, b.pk[0], extra_args(ctx));
+                    else
+                        forces_out_f32_kernel<false><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
+                            static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk,
+                            ctx->G, nullptr, 0, b.acc, b.pk[0], extra_args(ctx));
+                }
                 TRY(launched(ctx));
-                TRY(run_force_f32(ctx, p, b.pk[0]));
-                if (ctx->prec == COLATUS_FP32_COMP)
-                    forces_out_f32_kernel<true><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
-                        static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk,
-                        ctx->G, nullptr, 0, b.acc, b.pk[0], extra_args(ctx));
-                else
-                    forces_out_f32_kernel<false><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
-                        static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk,
-                        ctx->G, nullptr, 0, b.acc, b.pk[0], extra_args(ctx));
+                TRY(launch_kdk_open(ctx, b, 1, s0, a.tau));
+                b.vs = static_cast<float4 *>(a.rvs);
+                b.vs64 = static_cast<double4 *>(a.rvs);
             }
-            TRY(launched(ctx));
-            TRY(launch_kdk_open(ctx, b, 1, s0, a.tau));
             int cur = 1;
-            b.vs = static_cast<float4 *>(a.rvs);
-            b.vs64 = static_cast<double4 *>(a.rvs);
             for (long long n = s0; n < s1 - 1; ++n) {
                 b.xs = static_cast<float4 *>(pos(n + 1));
                 b.xs64 = static_cast<double4 *>(pos(n + 1));
                 if (eqm) b.acc = fslot(n + 1 - s0);
                 TRY(launch_step(ctx, b, cur, n, a.tau));
+                if (dkd)
+                    CU(cudaMemcpyAsync(vel(n + 1), a.rvs, (size_t)ctx->N * body, cudaMemcpyDeviceToDevice,
+                                       ctx->stream));
                 cur ^= 1;
             }
         }
-        for (long long n = s1 - 1; n >= s0; --n) {
+        for (long long n = s1 - 1; n >= s0 && dkd; --n) {
+            // DKD step n: pack (xh_n, W_n), the VJP at xh_n, the update
+            if (f64)
+                dkd_adj_pack_f64_kernel<<<nbv, 256, 0, ctx->stream>>>(
+                    static_cast<const double4 *>(pos(n)), static_cast<const double4 *>(vel(n)),
+                    static_cast<const double4 *>(a.lx), static_cast<const double4 *>(a.lv), a.table, n,
+                    a.tau, static_cast<double4 *>(a.pkw), ctx->N, pv.n_pad);
+            else
+                dkd_adj_pack_f32_kernel<<<nbv, 256, 0, ctx->stream>>>(
+                    static_cast<const float4 *>(pos(n)), static_cast<const float4 *>(vel(n)),
+                    static_cast<const float4 *>(a.lx), static_cast<const float4 *>(a.lv), a.table, n,
+                    a.tau, static_cast<float *>(a.pkw), ctx->N, pv.n_pad);
+            TRY(launched(ctx));
+            TRY(run_vjp(ctx));
+            TRY(prof_begin(ctx));
+            const unsigned nbn = blocks_for(ctx->N, 256);
+            if (f64)
+                dkd_adj_update_f64_kernel<<<nbn, 256, 0, ctx->stream>>>(
+                    static_cast<const double4 *>(ctx->part), pv.L, pv.itile, static_cast<double4 *>(a.lx),
+                    static_cast<double4 *>(a.lv), static_cast<double *>(a.lm), a.table, n, a.tau,
+                    static_cast<const double4 *>(a.pkw), ctx->N, vjp_extra(ctx));
+            else
+                dkd_adj_update_f32_kernel<<<nbn, 256, 0, ctx->stream>>>(
+                    static_cast<const float4 *>(ctx->part), pv.L, pv.itile, static_cast<float4 *>(a.lx),
+                    static_cast<float4 *>(a.lv), static_cast<float *>(a.lm), a.table, n, a.tau,
+                    static_cast<const float *>(a.pkw), ctx->N, vjp_extra(ctx));
+            TRY(launched(ctx));
+            TRY(prof_end(ctx, 2));
+        }
+        for (long long n = s1 - 1; n >= s0 && !dkd; --n) {
             TRY(run_vjp(ctx, eqm));
             TRY(prof_begin(ctx));
             if (f64)
@@ -2221,28 +2285,32 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
             TRY(prof_end(ctx, 2));
         }
     }
-    TRY(run_vjp(ctx, eqm));   // at x_0 (F(x_0): slot 0 of the first segment)
+    // KDK: F(x_0) enters the first half kick, so one more VJP at x_0 (F(x_0):
+    // slot 0 of the first segment for the equal-mass form).  DKD: the sweep
+    // already ended at step 0.
+    if (!dkd) TRY(run_vjp(ctx, eqm));
     const unsigned nb = blocks_for(ctx->N, 256);
     void *dgx = on_device ? gx_0 : (gx_0 ? (void *)ctx->stage : nullptr);
     void *dgv = on_device ? gv_0 : (gv_0 ? (void *)ctx->stage2 : nullptr);
     void *dgm = on_device ? gm : (gm ? a.rvh : nullptr);
     if (f64) {
-        adj_final_f64_kernel<<<nb, 256, 0, ctx->stream>>>(static_cast<const double4 *>(ctx->part),
-                                                          pv.L, pv.itile, static_cast<double4 *>(a.lx),
-                                                          static_cast<double *>(a.lm), ctx->N,
-                                                          static_cast<const double4 *>(a.pkw),
-                                                          vjp_extra(ctx));
-        TRY(launched(ctx));
+        if (!dkd) {
+            adj_final_f64_kernel<<<nb, 256, 0, ctx->stream>>>(
+                static_cast<const double4 *>(ctx->part), pv.L, pv.itile, static_cast<double4 *>(a.lx),
+                static_cast<double *>(a.lm), ctx->N, static_cast<const double4 *>(a.pkw), vjp_extra(ctx));
+            TRY(launched(ctx));
+        }
         adj_store_kernel<double4, double><<<nb, 256, 0, ctx->stream>>>(
             static_cast<const double4 *>(a.lx), static_cast<const double4 *>(a.lv),
             static_cast<const double *>(a.lm), ctx->N, dgx, dgv, dgm, in64);
     } else {
-        adj_final_f32_kernel<<<nb, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part),
-                                                          pv.L, pv.itile, static_cast<float4 *>(a.lx),
-                                                          static_cast<float *>(a.lm), ctx->N,
-                                                          static_cast<const float *>(a.pkw),
-                                                          vjp_args(eqm ? fslot(0) : nullptr));
-        TRY(launched(ctx));
+        if (!dkd) {
+            adj_final_f32_kernel<<<nb, 256, 0, ctx->stream>>>(
+                static_cast<const float4 *>(ctx->part), pv.L, pv.itile, static_cast<float4 *>(a.lx),
+                static_cast<float *>(a.lm), ctx->N, static_cast<const float *>(a.pkw),
+                vjp_args(eqm ? fslot(0) : nullptr));
+            TRY(launched(ctx));
+        }
         adj_store_kernel<float4, float><<<nb, 256, 0, ctx->stream>>>(
             static_cast<const float4 *>(a.lx), static_cast<const float4 *>(a.lv),
             static_cast<const float *>(a.lm), ctx->N, dgx, dgv, dgm, in64);

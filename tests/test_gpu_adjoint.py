@@ -2,7 +2,7 @@
 
 * the force VJP (gradient of sum w . acc with respect to positions and
   masses) against the oracle's FP64 VJP;
-* the checkpointed discrete adjoint of the KDK leapfrog against the oracle's
+* the checkpointed discrete adjoint of the KDK and DKD leapfrogs against the oracle's
   exact FP64 transpose and against central finite differences;
 * the torch.autograd wrappers.
 
@@ -217,10 +217,20 @@ def test_adjoint_state_checks():
         with pytest.raises(B.ColatusError) as e:
             sim.adjoint_backward(None, np.ones_like(ic.v))
         assert e.value.status == B.E_STATE
+        # the recorded pass is replayed with its own scheme and G: a change of
+        # either is refused
+        sim.adjoint_forward(TAU, 4, 2)
         sim.configure(scheme=B.DKD)
         with pytest.raises(B.ColatusError) as e:
-            sim.adjoint_forward(TAU, 4, 2)
-        assert e.value.status == B.E_ARG
+            sim.adjoint_backward(None, np.ones_like(ic.v))
+        assert e.value.status == B.E_STATE
+        sim.configure(scheme=B.KDK, G=2.0)
+        with pytest.raises(B.ColatusError) as e:
+            sim.adjoint_backward(None, np.ones_like(ic.v))
+        assert e.value.status == B.E_STATE
+        sim.configure(G=1.0)
+        gx, gv, gm = sim.adjoint_backward(None, np.ones_like(ic.v))
+        assert np.all(np.isfinite(gx)) and np.all(np.isfinite(gv))
     finally:
         sim.close()
 
@@ -282,3 +292,65 @@ def test_equal_mass_adjoint_matches_oracle_transpose(prec, k):
     r = oracle_adjoint(ic, n, tr)
     for key, g in (("gx", gx), ("gv", gv), ("gm", gm)):
         assert rel(g, r[key]) < 1e-4, key
+
+
+def _dkd_case():
+    ic = inputs.perturbed_grid(8, 0.1, 0.02, 4, zeldovich=True, total_mass=inputs.CRITICAL_MATTER_DENSITY)
+    return ic, inputs.tracers(ic.N, 64, 7)
+
+
+@pytest.mark.parametrize("prec,tol", [(B.FP64, 1e-9), (B.FP32, 1e-4), (B.FP32_COMP, 1e-4)])
+@pytest.mark.parametrize("k,n", [(5, 12), (1, 6)])
+def test_dkd_adjoint_matches_oracle_transpose(prec, tol, k, n):
+    # the paper's own drift-kick-drift leapfrog (Eqs. 3-5): one VJP per step
+    # at the half-drift position; checkpoints every 5 (5 + 5 + 2) or every step
+    ic, tr = _dkd_case()
+    sim = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START, prec=prec, scheme=B.DKD)
+    try:
+        sim.set_state(ic.x, ic.v)
+        sim.adjoint_forward(TAU, n, k)
+        xT, vT, t, aT = sim.state()
+        L, gvT, gmT = tracer_loss_grads(xT, vT, ic.m, aT, tr)
+        gx, gv, gm = sim.adjoint_backward(None, gvT, gmT)
+    finally:
+        sim.close()
+    r = oracle.run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n, "dkd")
+    _, rgvT, rgmT = tracer_loss_grads(r["x"], r["v"], ic.m, r["schedule"]["a"][-1], tr)
+    rx, rv, rm = oracle.adjoint_run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n,
+                                    np.zeros_like(ic.x), rgvT, rgmT, scheme="dkd")
+    assert rel(gx, rx) < tol
+    assert rel(gv, rv) < tol
+    assert rel(gm, rm) < tol
+
+
+def test_dkd_adjoint_directional_derivative_matches_finite_differences():
+    # FP64, 8 DKD steps: <dL/dx0, dx> + <dL/dv0, dv> against central
+    # differences of the GPU's own forward runs
+    ic, tr = _dkd_case()
+    n = 8
+    sim = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START, prec=B.FP64, scheme=B.DKD)
+    try:
+        sim.set_state(ic.x, ic.v)
+        sim.adjoint_forward(TAU, n, 3)
+        xT, vT, t, aT = sim.state()
+        L, gvT, gmT = tracer_loss_grads(xT, vT, ic.m, aT, tr)
+        gx, gv, gm = sim.adjoint_backward(None, gvT, gmT)
+    finally:
+        sim.close()
+    rng = np.random.default_rng(19)
+    dx, dv = rng.standard_normal(ic.x.shape), rng.standard_normal(ic.v.shape)
+    h = 1e-7
+
+    def loss(x, v):
+        s = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START, prec=B.FP64, scheme=B.DKD)
+        try:
+            s.set_state(x, v)
+            s.step(TAU, n)
+            x1, v1, _, a1 = s.state()
+        finally:
+            s.close()
+        return tracer_loss_grads(x1, v1, ic.m, a1, tr)[0]
+
+    fd = (loss(ic.x + h * dx, ic.v + h * dv) - loss(ic.x - h * dx, ic.v - h * dv)) / (2 * h)
+    ad = float(np.sum(gx * dx) + np.sum(gv * dv))
+    assert ad == pytest.approx(fd, rel=1e-6)

@@ -156,15 +156,18 @@ def test_force_vjp_with_deformation(prec, tol):
     assert rel(gm, rm / a ** 3) < tol
 
 
+@pytest.mark.parametrize("scheme", ["kdk", "dkd"])
 @pytest.mark.parametrize("prec,tol", [(B.FP64, 1e-9), (B.FP32_COMP, 1e-4)])
-def test_trajectory_adjoint_with_deformation(prec, tol):
+def test_trajectory_adjoint_with_deformation(prec, tol, scheme):
+    # DKD: the term's Jacobian at the half-drift positions
     ic = inputs.perturbed_grid(8, 0.1, 0.02, 4, zeldovich=True, total_mass=inputs.CRITICAL_MATTER_DENSITY)
     defo = (0.3 * inputs.CRITICAL_MATTER_DENSITY, XPSI)
     n = 20
     rng = np.random.default_rng(740)
     gxT = rng.standard_normal(ic.x.shape)
     gvT = rng.standard_normal(ic.v.shape)
-    sim = B.Simulation(ic.m, ic.eps, LCDM_D, A_LATE, prec=prec)
+    sim = B.Simulation(ic.m, ic.eps, LCDM_D, A_LATE, prec=prec,
+                       scheme=B.KDK if scheme == "kdk" else B.DKD)
     try:
         sim.set_state(ic.x, ic.v)
         sim.set_deformation(*defo)
@@ -173,7 +176,7 @@ def test_trajectory_adjoint_with_deformation(prec, tol):
     finally:
         sim.close()
     rx, rv, rm = oracle.adjoint_run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, A_LATE, TAU, n,
-                                    gxT, gvT, scheme="kdk", defo=defo)
+                                    gxT, gvT, scheme=scheme, defo=defo)
     for got, ref, k in ((gx, rx, "gx"), (gv, rv, "gv"), (gm, rm, "gm")):
         assert rel(got, ref) < tol, k
 

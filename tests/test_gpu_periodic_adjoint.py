@@ -1,7 +1,7 @@
 """GPU parity of the derivatives under periodic boundaries (Sec. II; Ewald
 summation): the force VJP against the oracle's converged FP64 ewald_vjp, and
-the checkpointed discrete adjoint of the KDK leapfrog against the oracle's
-exact transpose (adjoint_run with box = L).
+the checkpointed discrete adjoint of the KDK and DKD leapfrogs against the
+oracle's exact transpose (adjoint_run with box = L).
 
 Tolerances as for isolated boundaries: normwise relative error of the
 gradient vector, FP32 VJP 1e-5, FP64 1e-10; FP32 trajectory adjoint 1e-4,
@@ -107,20 +107,22 @@ def adjoint_case():
 
 
 @functools.lru_cache(maxsize=None)
-def adjoint_reference(n):
+def adjoint_reference(n, scheme="kdk"):
     ic, tr = adjoint_case()
-    r = oracle.run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n, "kdk", box=1.0)
+    r = oracle.run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n, scheme, box=1.0)
     rgvT, rgmT = tracer_loss_grads(r["x"], r["v"], ic.m, r["schedule"]["a"][-1], tr)
     return oracle.adjoint_run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n,
-                              np.zeros_like(ic.x), rgvT, rgmT, box=1.0)
+                              np.zeros_like(ic.x), rgvT, rgmT, scheme=scheme, box=1.0)
 
 
+@pytest.mark.parametrize("scheme", ["kdk", "dkd"])
 @pytest.mark.parametrize("prec,tol", [(B.FP64, 1e-9), (B.FP32, 1e-4), (B.FP32_COMP, 1e-4)])
-def test_periodic_adjoint_matches_oracle_transpose(prec, tol):
-    # 12 KDK steps with checkpoints every 5 (uneven segments 5 + 5 + 2)
+def test_periodic_adjoint_matches_oracle_transpose(prec, tol, scheme):
+    # 12 steps with checkpoints every 5 (uneven segments 5 + 5 + 2)
     ic, tr = adjoint_case()
     n = 12
-    sim = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START, prec=prec)
+    sim = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START, prec=prec,
+                       scheme=B.KDK if scheme == "kdk" else B.DKD)
     try:
         sim.set_state(ic.x, ic.v)
         sim.set_periodic(1.0)
@@ -130,7 +132,7 @@ def test_periodic_adjoint_matches_oracle_transpose(prec, tol):
         gx, gv, gm = sim.adjoint_backward(None, gvT, gmT)
     finally:
         sim.close()
-    rx, rv, rm = adjoint_reference(n)
+    rx, rv, rm = adjoint_reference(n, scheme)
     assert rel(gx, rx) < tol
     assert rel(gv, rv) < tol
     assert rel(gm, rm) < tol
