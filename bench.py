@@ -42,10 +42,10 @@ L2_FLUSH_BYTES = 256 << 20
 # its source files hash to the captured sources; otherwise traffic is null.
 FORCE_KERNEL_TRAFFIC = {
     "bytes": 540928,
-    "plan": dict(kind="force_f32", threads=512, ipt=4, jt=512, comp=True, eqm=True),
-    "template": "force_f32_kernel<512, 4, 512, 4, 256, true, true, 1, 2>",
+    "plan": dict(kind="force_f32", threads=512, ipt=4, jt=512, comp=True, eqm=True, nrcp=0),
+    "template": "force_f32_kernel<512, 4, 512, 4, 256, true, true, 1, 2, 0>",
     "sources": ("paper_1208_3444_b300/csrc/force.cuh", "paper_1208_3444_b300/csrc/common.cuh"),
-    "sha256": "b5483b303868655cc85ddffdc25f92dca08c68853a68b8e7584418c7ba70a439",
+    "sha256": "2a110c0e30d0ac10ca7214f3d281a896d648893e1486b1e3e8fae41e00051357",
 }
 
 

@@ -267,8 +267,10 @@ colatus_status colatus_stats(colatus_t ctx, double out[4]);
  * space, 3 FP64 periodic real space), out[1] threads per CTA, out[2]
  * i-bodies per thread, out[3] j-tile bodies, out[4] compensated accumulation
  * (0/1), out[5] equal-mass form (0/1), out[6] persistent grid (CTAs),
- * out[7] work units (i-tile x j-tile).  Errors: COLATUS_E_ARG. */
-colatus_status colatus_force_plan(colatus_t ctx, int64_t out[8]);
+ * out[7] work units (i-tile x j-tile), out[8] i-bodies per thread whose
+ * 1/s^2 is an rcp on the MUFU pipe rather than a square of the rsqrt on the
+ * FMA pipe.  Errors: COLATUS_E_ARG. */
+colatus_status colatus_force_plan(colatus_t ctx, int64_t out[9]);
 
 /* Kernel timing for measurement: with on != 0 every launch of the force
  * kernel, the VJP kernel and the adjoint's per-step update kernel is
@@ -396,11 +398,11 @@ colatus_status colatus_ensemble_synchronize(colatus_ens_t e);
 colatus_status colatus_ensemble_stats(colatus_ens_t e, int profile_on, double out[6]);
 /* Ensemble force-kernel tuning.  The kernel exists in three CTA shapes with
  * the same 256-body tiles (0: 128 threads x 2 bodies, 4 CTAs per SM; 1: 256 x 1,
- * 4 per SM; 2: 64 x 4, 8 per SM).  colatus_ensemble_autotune times reps force
+ * 4 per SM; 2: 64 x 4, 8 per SM, the built-in choice).  colatus_ensemble_autotune times reps force
  * evaluations of every shape at the current state (state required; one
  * untimed launch first), writes the milliseconds per evaluation to out_ms[k]
  * (may be NULL), keeps the fastest and returns its index in *chosen (may be
- * NULL).  colatus_ensemble_set_tuning applies a known choice (-1: shape 0).
+ * NULL).  colatus_ensemble_set_tuning applies a known choice (-1: shape 2).
  * Either call synchronises the stream, drops the captured step graphs and
  * recomputes the step opening at the next colatus_ensemble_step; results
  * then follow the new shape's summation order (deterministic per shape). */

@@ -38,29 +38,35 @@ constexpr int kShapes = 3;
 struct F32Variant {
     int nt, ipt, jt;
     bool comp, eqm;
+    int nrcp;
     int smem;
     const void *fn;
     void (*launch)(int grid, cudaStream_t, const float *, float4 *, int *, ForceLaunch, float,
                    float);
 };
 
-template <int NT, int IPT, int JT, int FOLD, bool COMP, bool EQM, int MINB, int UNR>
+template <int NT, int IPT, int JT, int FOLD, bool COMP, bool EQM, int MINB, int UNR, int NRCP>
 void launch_f32(int grid, cudaStream_t st, const float *pk, float4 *part, int *flags, ForceLaunch L,
                 float eps2, float mass_eq) {
     using K = F32Kernel<NT, IPT, JT, kStages, FOLD, COMP, EQM>;
-    force_f32_kernel<NT, IPT, JT, kStages, FOLD, COMP, EQM, MINB, UNR>
+    force_f32_kernel<NT, IPT, JT, kStages, FOLD, COMP, EQM, MINB, UNR, NRCP>
         <<<grid, NT, K::SMEM, st>>>(pk, part, flags, L, eps2, mass_eq);
 }
 
-template <int NT, int IPT, int JT, int FOLD, bool COMP, bool EQM, int MINB, int UNR>
+template <int NT, int IPT, int JT, int FOLD, bool COMP, bool EQM, int MINB, int UNR, int NRCP = 0>
 F32Variant make_f32() {
     using K = F32Kernel<NT, IPT, JT, kStages, FOLD, COMP, EQM>;
-    return F32Variant{NT, IPT, JT, COMP, EQM, K::SMEM,
-                      (const void *)force_f32_kernel<NT, IPT, JT, kStages, FOLD, COMP, EQM, MINB, UNR>,
-                      &launch_f32<NT, IPT, JT, FOLD, COMP, EQM, MINB, UNR>};
+    return F32Variant{NT, IPT, JT, COMP, EQM, NRCP, K::SMEM,
+                      (const void *)force_f32_kernel<NT, IPT, JT, kStages, FOLD, COMP, EQM, MINB, UNR, NRCP>,
+                      &launch_f32<NT, IPT, JT, FOLD, COMP, EQM, MINB, UNR, NRCP>};
 }
 
-// index = 4 * shape + 2 * comp + eqm
+// index = 4 * shape + 2 * comp + eqm.  An optional last argument (NRCP)
+// would move 1/s^2 of the first NRCP i-bodies of each thread from the FMA
+// pipe (a square of the rsqrt) to the MUFU pipe (an rcp).  On B300 at
+// N = 32^3 one i-body in four was 1 % faster for the compensated kernel
+// called alone but 1 % slower inside the step loop, and slower for the plain
+// kernel, so no single-system variant takes it (the ensemble's 64 x 4 does).
 enum { V_COMP = 2, V_EQM = 1, NUM_F32_VARIANTS = 4 * kShapes };
 
 const F32Variant &f32_variant(int v) {
@@ -214,6 +220,7 @@ struct colatus_ctx {
     // FP32 state: xs (x,y,z,m), vs, vh (KDK half-step velocity), acc (G-less F)
     float4 *xs = nullptr, *vs = nullptr, *vh = nullptr, *acc = nullptr;
     float *pk[3] = {nullptr, nullptr, nullptr};   // [0],[1] ping-pong, [2] aux
+    float *pk_ew = nullptr;                       // periodic: the force input wrapped into the box
     // FP64 state
     double4 *xs64 = nullptr, *vs64 = nullptr, *vh64 = nullptr, *acc64 = nullptr;
     double4 *pos64[3] = {nullptr, nullptr, nullptr};
@@ -616,6 +623,11 @@ colatus_status ewald_setup(colatus_t ctx) {
     for (int c = 0; c < ctx->nrchunk; ++c) ctx->rchunk_np = std::max(ctx->rchunk_np, rch[c + 1] - rch[c]);
     ctx->nfchunk = (int)fch.size() - 1;
     if (!ctx->lr) CU(cudaMalloc(&ctx->lr, (size_t)ctx->n_alloc * sizeof(double4)));
+    if (!f64 && !ctx->pk_ew) {
+        // the padding bodies stay zero: the phase kernel writes bodies 0 .. N-1
+        CU(cudaMalloc(&ctx->pk_ew, (size_t)ctx->n_alloc * 4 * sizeof(float)));
+        CU(cudaMemsetAsync(ctx->pk_ew, 0, (size_t)ctx->n_alloc * 4 * sizeof(float), ctx->stream));
+    }
     TRY(grow(ctx, &ctx->ph, &ctx->ph_bytes,
              (size_t)ctx->n_alloc * 3 * (nk + 1) * (f64 ? sizeof(double2) : sizeof(float2))));
     CU(cudaMemcpyAsync(ctx->kw, w.data(), nkv * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
@@ -671,17 +683,24 @@ colatus_status ewald_setup(colatus_t ctx) {
     return COLATUS_OK;
 }
 
-// Periodic boundaries: the k-space part, after the real-space kernel.
-// Structure factors into ctx->rho, then the long-range force at every body
-// into ctx->lr.  pk (FP32 packed) or pos (FP64) holds the positions.
+// Periodic boundaries: the phase tables of every body (FP32: also the
+// wrapped force input pk_ew), before the real-space kernel.
+template <typename T>
+colatus_status run_ewald_phases(colatus_t ctx, const float *pk, const double4 *pos) {
+    using T2 = typename Vec2<T>::type;
+    ewald_phase_kernel<T><<<blocks_for(3 * ctx->N, 128), 128, 0, ctx->stream>>>(
+        masses_of(pk, pos), ctx->N, ctx->ew, static_cast<T2 *>(ctx->ph), pos ? nullptr : ctx->pk_ew);
+    return launched(ctx);
+}
+
+// The k-space part, after the real-space kernel: structure factors into
+// ctx->rho, then the long-range force at every body into ctx->lr.  pk (FP32
+// packed) or pos (FP64) holds the positions; the phase tables are current.
 template <typename T, typename T4>
 colatus_status run_ewald_kspace(colatus_t ctx, const float *pk, const double4 *pos) {
     using T2 = typename Vec2<T>::type;
     const int nt = ctx->ew.nk + 1;
     T2 *ph = static_cast<T2 *>(ctx->ph);
-    ewald_phase_kernel<T><<<blocks_for(3 * ctx->N, 128), 128, 0, ctx->stream>>>(
-        masses_of(pk, pos), ctx->N, ctx->ew, ph);
-    TRY(launched(ctx));
     const int kchunks = ctx->nrchunk;
     const long long max_split = std::max(1LL, ctx->N / ew_bodies<T>());
     const int splits = (int)std::min<long long>(std::max(1, kEwRhoBlocksPerSM * ctx->num_sms / kchunks),
@@ -706,6 +725,8 @@ colatus_status run_ewald_kspace(colatus_t ctx, const float *pk, const double4 *p
 colatus_status run_ewald_f32(colatus_t ctx, const ForcePlan &p, const float *pk) {
     TRY(ensure_part(ctx, p.part_bytes));
     const float eps2 = (float)(ctx->eps * ctx->eps);
+    TRY(run_ewald_phases<float>(ctx, pk, nullptr));
+    const float *pkw = ctx->pk_ew;
     TRY(prof_begin(ctx));
     // equal masses and no zero-mass padding: the equal-mass form
     const bool eqm = ctx->eq_mass && p.n_pad == ctx->N;
@@ -713,16 +734,16 @@ colatus_status run_ewald_f32(colatus_t ctx, const ForcePlan &p, const float *pk)
     const float me = ctx->mass_eq;
     if (ctx->prec == COLATUS_FP32_COMP && eqm)
         ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, true, kEwMinB, true>
-            <<<p.L.G, kEwNT, EwKC::SMEM, ctx->stream>>>(pk, part, ctx->flags, p.L, eps2, ctx->ew, me);
+            <<<p.L.G, kEwNT, EwKC::SMEM, ctx->stream>>>(pkw, part, ctx->flags, p.L, eps2, ctx->ew, me);
     else if (ctx->prec == COLATUS_FP32_COMP)
         ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, true, kEwMinB, false>
-            <<<p.L.G, kEwNT, EwKC::SMEM, ctx->stream>>>(pk, part, ctx->flags, p.L, eps2, ctx->ew, me);
+            <<<p.L.G, kEwNT, EwKC::SMEM, ctx->stream>>>(pkw, part, ctx->flags, p.L, eps2, ctx->ew, me);
     else if (eqm)
         ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, false, kEwMinB, true>
-            <<<p.L.G, kEwNT, EwK::SMEM, ctx->stream>>>(pk, part, ctx->flags, p.L, eps2, ctx->ew, me);
+            <<<p.L.G, kEwNT, EwK::SMEM, ctx->stream>>>(pkw, part, ctx->flags, p.L, eps2, ctx->ew, me);
     else
         ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, false, kEwMinB, false>
-            <<<p.L.G, kEwNT, EwK::SMEM, ctx->stream>>>(pk, part, ctx->flags, p.L, eps2, ctx->ew, me);
+            <<<p.L.G, kEwNT, EwK::SMEM, ctx->stream>>>(pkw, part, ctx->flags, p.L, eps2, ctx->ew, me);
     TRY(launched(ctx));
     ctx->interactions += (double)ctx->N * (double)ctx->N;
     TRY(prof_end(ctx));
@@ -747,6 +768,7 @@ colatus_status run_force_f64(colatus_t ctx, const double4 *pos) {
     if (ctx->periodic) {
         const ForcePlan &p = ctx->plan_ew64;
         TRY(ensure_part(ctx, p.part_bytes));
+        TRY(run_ewald_phases<double>(ctx, nullptr, pos));
         TRY(prof_begin(ctx));
         ewald_f64_kernel<kEw64NT, kEw64JT, kStages><<<p.L.G, kEw64NT, Ew64K::SMEM, ctx->stream>>>(
             pos, static_cast<double4 *>(ctx->part), ctx->flags, p.L, ctx->eps * ctx->eps, ctx->ew);
@@ -907,7 +929,7 @@ void free_all(colatus_t ctx) {
                     ctx->tclk, ctx->table, ctx->stage, ctx->stage2, ctx->diag, ctx->tslot,
                     ctx->rec, ctx->kw, ctx->rho, ctx->rho_part, ctx->wcs, ctx->pen,
                     ctx->rchunk, ctx->fchunk, ctx->lr, ctx->ph, ctx->pot_part, ctx->lrv,
-                    ctx->kwr, ctx->kwl};
+                    ctx->kwr, ctx->kwl, ctx->pk_ew};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *tptrs[] = {ctx->tan.dx, ctx->tan.dv, ctx->tan.dvh, ctx->tan.pkt, ctx->tan.seeds,
@@ -1279,7 +1301,7 @@ colatus_status run_ewald_kspace_vjp(colatus_t ctx) {
     for (int c = 0; c < 4; ++c) C.widx[c] = widx[c];
     T2 *ph = static_cast<T2 *>(ctx->ph);
     ewald_phase_kernel<T><<<blocks_for(3 * ctx->N, 128), 128, 0, ctx->stream>>>(C.src, ctx->N, ctx->ew,
-                                                                                ph);
+                                                                                ph, nullptr);
     TRY(launched(ctx));
     const int splits = ew_splits<T>(ctx);
     const size_t plane = (size_t)splits * ctx->nkv;
@@ -1382,7 +1404,7 @@ colatus_status run_ewald_kspace_jvp(colatus_t ctx, const float *pk) {
     C.B = t.B;
     float2 *ph = static_cast<float2 *>(ctx->ph);
     ewald_phase_kernel<float><<<blocks_for(3 * ctx->N, 128), 128, 0, ctx->stream>>>(C.src, ctx->N, ctx->ew,
-                                                                                   ph);
+                                                                                   ph, nullptr);
     TRY(launched(ctx));
     const int splits = ew_splits<float>(ctx);
     const size_t plane = (size_t)splits * ctx->nkv;
@@ -2665,7 +2687,7 @@ void colatus_destroy(colatus_t ctx) {
     delete ctx;
 }
 
-colatus_status colatus_force_plan(colatus_t ctx, int64_t out[8]) {
+colatus_status colatus_force_plan(colatus_t ctx, int64_t out[9]) {
     if (!ctx || !out) return COLATUS_E_ARG;
     const bool f64 = ctx->prec == COLATUS_FP64;
     const ForcePlan &p = f64 ? plan_f64(ctx) : plan_f32(ctx);
@@ -2690,6 +2712,7 @@ colatus_status colatus_force_plan(colatus_t ctx, int64_t out[8]) {
     out[3] = p.jt;
     out[6] = p.L.G;
     out[7] = p.L.W;
+    out[8] = f64 || ctx->periodic ? 0 : f32_variant(p.variant).nrcp;
     return COLATUS_OK;
 }
 

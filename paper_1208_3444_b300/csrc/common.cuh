@@ -92,6 +92,12 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     return y;
 }
 
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // The kick a x + b y and the drift x + t v with one fixed rounding sequence.
 // The _rn intrinsics are never contracted or reordered by the compiler, so
 // every kernel that applies the same kick or drift (a step's epilogue and a

@@ -61,7 +61,7 @@ __device__ __forceinline__ long long ens_jbody(const EnsLaunch &E, int r, long l
     return E.body_off[r] + (local % E.n_jt[r]) * JT;
 }
 
-template <int NT, int IPT, int JT, int STAGES, int FOLD, int MINB, bool EQM>
+template <int NT, int IPT, int JT, int STAGES, int FOLD, int MINB, bool EQM, int NRCP = 0>
 __global__ void __launch_bounds__(NT, MINB)
     ens_force_kernel(const float *__restrict__ pk, float4 *__restrict__ part, int *__restrict__ flags,
                      EnsLaunch E) {
@@ -120,8 +120,8 @@ __global__ void __launch_bounds__(NT, MINB)
         for (; u < uend; ++u) {
             const bool ok = mbar_wait_bounded(&full[stage], parity);
             if (ok)
-                f32_tile<IPT, JT, FOLD, false, EQM, 2>(tiles + stage * JT, nx, ny, nz, e2, hx, hy, hz,
-                                                    lx, ly, lz);
+                f32_tile<IPT, JT, FOLD, false, EQM, 2, NRCP>(tiles + stage * JT, nx, ny, nz, e2, hx, hy,
+                                                          hz, lx, ly, lz);
             if (__syncthreads_or(!ok)) {
                 bad = true;
                 break;

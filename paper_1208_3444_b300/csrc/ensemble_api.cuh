@@ -11,9 +11,11 @@
 
 namespace {
 
-// 128 threads x 2 i-bodies, 4 CTAs per SM: the fastest of six shapes with
-// 256-body tiles timed on the 64-realisation ensemble (3.95 ms/step against
-// 4.10 for 64 x 4 at 8 CTAs per SM)
+// 256-body i- and j-tiles.  Of six CTA shapes timed on the 64-realisation
+// ensemble, 128 threads x 2 i-bodies (4 CTAs per SM) was the fastest with
+// every 1/s^2 from the FMA pipe (3.75 ms per force); 64 x 4 (8 CTAs per SM)
+// with one of its four i-bodies taking 1/s^2 from the MUFU pipe is faster
+// still (3.69 ms) and is the built-in shape.
 constexpr int kEnsJT = 256, kEnsFold = 128;
 using EnsK = F32Kernel<128, 2, kEnsJT, kStages, kEnsFold, false, false>;   // SMEM: every shape's
 constexpr int kEnsTile = EnsK::ITILE;   // 256 bodies: the per-realisation padding unit
@@ -22,33 +24,37 @@ static_assert(kEnsTile == kEnsJT, "ensemble tiles pad realisations to one size")
 
 // CTA shapes of the ensemble force kernel (threads x i-bodies per thread,
 // CTAs per SM), all with 256-body i- and j-tiles, so that the padding and the
-// unit list do not depend on the shape.  Shape 0 is the built-in choice;
+// unit list do not depend on the shape.  Shape kEnsDefault is the built-in choice;
 // colatus_ensemble_autotune times all of them on the ensemble at hand.
-constexpr int kEnsShapes = 3;
+constexpr int kEnsShapes = 3, kEnsDefault = 2;
 struct EnsVariant {
     int nt;
     const void *fn[2];   // general masses, equal masses
     void (*launch[2])(int grid, cudaStream_t, const float *, float4 *, int *, EnsLaunch);
 };
 
-template <int NT, int IPT, int MINB, bool EQM>
+template <int NT, int IPT, int MINB, int NRCP, bool EQM>
 void ens_launch(int grid, cudaStream_t st, const float *pk, float4 *part, int *flags, EnsLaunch E) {
     static_assert(NT * IPT == kEnsTile, "one i-tile per CTA pass");
-    ens_force_kernel<NT, IPT, kEnsJT, kStages, kEnsFold, MINB, EQM><<<grid, NT, EnsK::SMEM, st>>>(
+    ens_force_kernel<NT, IPT, kEnsJT, kStages, kEnsFold, MINB, EQM, NRCP><<<grid, NT, EnsK::SMEM, st>>>(
         pk, part, flags, E);
 }
 
-template <int NT, int IPT, int MINB>
+// NRCP: as for the single-system kernels, 1/s^2 of the first NRCP i-bodies of
+// a thread from an rcp on the MUFU pipe instead of a square on the FMA pipe
+template <int NT, int IPT, int MINB, int NRCP = 0>
 EnsVariant make_ens() {
     return EnsVariant{NT,
-                      {(const void *)ens_force_kernel<NT, IPT, kEnsJT, kStages, kEnsFold, MINB, false>,
-                       (const void *)ens_force_kernel<NT, IPT, kEnsJT, kStages, kEnsFold, MINB, true>},
-                      {&ens_launch<NT, IPT, MINB, false>, &ens_launch<NT, IPT, MINB, true>}};
+                      {(const void *)ens_force_kernel<NT, IPT, kEnsJT, kStages, kEnsFold, MINB, false, NRCP>,
+                       (const void *)ens_force_kernel<NT, IPT, kEnsJT, kStages, kEnsFold, MINB, true, NRCP>},
+                      {&ens_launch<NT, IPT, MINB, NRCP, false>, &ens_launch<NT, IPT, MINB, NRCP, true>}};
 }
 
+// 64 x 4 takes one rcp per four i-bodies: 3.69 ms per force on the
+// 64-realisation ensemble against 3.80 without it (and 3.75 for 128 x 2)
 const EnsVariant &ens_variant(int s) {
     static const EnsVariant table[kEnsShapes] = {make_ens<128, 2, 4>(), make_ens<256, 1, 4>(),
-                                                 make_ens<64, 4, 8>()};
+                                                 make_ens<64, 4, 8, 1>()};
     return table[s];
 }
 
@@ -65,7 +71,7 @@ struct colatus_ensemble {
     std::vector<long long> nbody, body_off, user_off, unit_off, tile_u0;
     std::vector<int> n_jt, tile_r;
     EnsLaunch E{};
-    int shape = 0;                         // CTA shape of the force kernel (ens_variant)
+    int shape = kEnsDefault;               // CTA shape of the force kernel (ens_variant)
     int shape_G[kEnsShapes] = {0}, shape_S[kEnsShapes] = {0};   // grid and S_max per shape
     void *meta = nullptr;                  // device descriptor arrays
     long long *d_user_off = nullptr;
@@ -390,8 +396,8 @@ colatus_status colatus_ensemble_init(colatus_ens_t *out, int R, const int64_t *N
         e->shape_S[sh] = (int)sm;
         smax = std::max(smax, sm);
     }
-    E.G = e->shape_G[0];
-    E.S_max = e->shape_S[0];
+    E.G = e->shape_G[kEnsDefault];
+    E.S_max = e->shape_S[kEnsDefault];
     // device memory
     const size_t ll = sizeof(long long);
     const size_t meta_bytes = ll * ((R + 1) * 3 + R + T) + sizeof(int) * (R + T) + sizeof(float) * 2 * R + 72;
@@ -596,7 +602,7 @@ colatus_status colatus_ensemble_set_tuning(colatus_ens_t e, int shape) {
     DeviceGuard dg(e->device);
     if (shape < -1 || shape >= kEnsShapes) return efail(e, COLATUS_E_ARG, "shape must be -1 .. %d", kEnsShapes - 1);
     TRY(ens_check(e, true));
-    ens_set_shape(e, shape < 0 ? 0 : shape);
+    ens_set_shape(e, shape < 0 ? kEnsDefault : shape);
     return COLATUS_OK;
 }
 
@@ -638,7 +644,7 @@ colatus_status colatus_ensemble_autotune(colatus_ens_t e, int reps, double out_m
     if (st == COLATUS_OK)
         for (int sh = 1; sh < kEnsShapes; ++sh)
             if (ms[sh] < ms[best]) best = sh;
-    ens_set_shape(e, st == COLATUS_OK ? best : 0);
+    ens_set_shape(e, st == COLATUS_OK ? best : kEnsDefault);
     if (st != COLATUS_OK) return st;
     for (int sh = 0; sh < kEnsShapes; ++sh)
         if (out_ms) out_ms[sh] = ms[sh];

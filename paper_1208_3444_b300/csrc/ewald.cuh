@@ -81,12 +81,6 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-__device__ __forceinline__ float rcp_approx(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 // Minimum image of a pair-packed separation on the FMA pipe: fma(d, 1/L, M)
 // with M = 1.5 * 2^23 rounds d/L to the nearest integer (ties to even) in
 // its single rounding, for |d/L| < 2^22; subtracting M leaves that integer n,
@@ -134,8 +128,11 @@ __device__ __forceinline__ float2 ewald_pair2(const float2 dx, const float2 dy, 
     return EQM ? br : __fmul2_rn(mj, br);
 }
 
-// EQM: every body has mass mass_eq (and no zero-mass padding enters): the
-// pair term drops m_j and the segments are scaled by mass_eq.
+// pk: the bodies with positions wrapped into [0, L] (ewald_phase_kernel
+// writes them), so every separation rounds once from coordinates of the
+// box's own size, whatever box the bodies have drifted to.  EQM: every body
+// has mass mass_eq (and no zero-mass padding enters): the pair term drops m_j
+// and the segments are scaled by mass_eq.
 template <int NT, int IPT, int JT, int STAGES, int FOLD, bool COMP, int MINB, bool EQM>
 __global__ void __launch_bounds__(NT, MINB)
     ewald_f32_kernel(const float *__restrict__ pk, float4 *__restrict__ part, int *__restrict__ flags,
@@ -432,15 +429,25 @@ template <> struct Vec2<double> { using type = double2; };
 //   ph[(3 i + c) (nk + 1) + n] = exp(2 pi i n x_c / L),  n = 0..nk,
 // with n x_c / L reduced exactly (FP64: exact for |n| < 2^20, minus its
 // nearest integer) before sincospi.  One thread per (body, axis).
+//
+// wrap (FP32 pair-packed bodies only, else null): the same bodies with each
+// coordinate wrapped into [0, L] as x - L floor(x / L) in FP64, rounded once
+// (exact for a coordinate already in [0, L)), the input of ewald_f32_kernel.
 template <typename T>
 __global__ void ewald_phase_kernel(BodySrc src, long long N, EwaldArgs A,
-                                   typename Vec2<T>::type *__restrict__ ph) {
+                                   typename Vec2<T>::type *__restrict__ ph, float *__restrict__ wrap) {
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= 3 * N) return;
     const long long i = q / 3;
     const int c = (int)(q - 3 * i);
     const double3 p = body_pos(src, i);
-    const double u = (c == 0 ? p.x : (c == 1 ? p.y : p.z)) / A.L;
+    const double xc = c == 0 ? p.x : (c == 1 ? p.y : p.z);
+    const double u = xc / A.L;
+    if (wrap) {
+        const long long o = (i >> 1) * 8 + (i & 1);
+        wrap[o + 2 * c] = (float)(xc - A.L * floor(u));
+        if (c == 0) wrap[o + 6] = src.pk[o + 6];
+    }
     typename Vec2<T>::type *o = ph + q * (A.nk + 1);
     for (int n = 0; n <= A.nk; ++n) {
         double f = (double)n * u;

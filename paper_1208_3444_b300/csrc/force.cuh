@@ -74,7 +74,7 @@ struct F32Kernel {
 
 // Sum one j-tile (JT bodies, pair-interleaved in shared memory) into the
 // totals of the IPT i-bodies of this thread.
-template <int IPT, int JT, int FOLD, bool COMP, bool EQM, int UNR>
+template <int IPT, int JT, int FOLD, bool COMP, bool EQM, int UNR, int NRCP = 0>
 __device__ __forceinline__ void f32_tile(const float4 *__restrict__ t, const float2 (&nx)[IPT],
                                          const float2 (&ny)[IPT], const float2 (&nz)[IPT],
                                          const float2 e2, float (&hx)[IPT], float (&hy)[IPT],
@@ -107,7 +107,8 @@ __device__ __forceinline__ void f32_tile(const float4 *__restrict__ t, const flo
                 r2 = __ffma2_rn(dy, dy, r2);
                 r2 = __ffma2_rn(dz, dz, r2);
                 const float2 inv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-                const float2 inv2 = __fmul2_rn(inv, inv);
+                const float2 inv2 = k < NRCP ? make_float2(rcp_approx(r2.x), rcp_approx(r2.y))
+                                             : __fmul2_rn(inv, inv);
                 const float2 s = EQM ? __fmul2_rn(inv, inv2) : __fmul2_rn(__fmul2_rn(mj, inv), inv2);
                 px[k] = __ffma2_rn(dx, s, px[k]);
                 py[k] = __ffma2_rn(dy, s, py[k]);
@@ -134,7 +135,8 @@ __device__ __forceinline__ void f32_tile(const float4 *__restrict__ t, const flo
 // [n_it][S_max][COMP ? 2 : 1][ITILE] float4 (x, y, z, 0); for COMP the
 // second plane holds the low words.  EQM: segments are scaled by mass_eq.
 // UNR: unroll depth of the j-pair loop (a tuning knob).
-template <int NT, int IPT, int JT, int STAGES, int FOLD, bool COMP, bool EQM, int MINB, int UNR>
+template <int NT, int IPT, int JT, int STAGES, int FOLD, bool COMP, bool EQM, int MINB, int UNR,
+          int NRCP = 0>
 __global__ void __launch_bounds__(NT, MINB)
     force_f32_kernel(const float *__restrict__ pk, float4 *__restrict__ part, int *__restrict__ flags,
                      ForceLaunch L, float eps2, float mass_eq) {
@@ -187,8 +189,8 @@ __global__ void __launch_bounds__(NT, MINB)
         for (; u < uend; ++u) {
             const bool ok = mbar_wait_bounded(&full[stage], parity);
             if (ok)
-                f32_tile<IPT, JT, FOLD, COMP, EQM, UNR>(tiles + stage * JT, nx, ny, nz, e2, hx, hy, hz,
-                                                   lx, ly, lz);
+                f32_tile<IPT, JT, FOLD, COMP, EQM, UNR, NRCP>(tiles + stage * JT, nx, ny, nz, e2, hx, hy,
+                                                         hz, lx, ly, lz);
             if (__syncthreads_or(!ok)) {
                 bad = true;
                 break;

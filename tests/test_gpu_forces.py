@@ -155,3 +155,19 @@ def test_autotune_and_cache(tmp_path):
     finally:
         sim.close()
     assert rel_rms(got, oracle.forces(ic.x, ic.m, ic.eps)) < TOL[B.FP32_COMP]
+
+
+def test_force_plan_names_the_launched_kernel():
+    # the 32^3 equal-mass bodies take shape 0 (512 x 4, 512-body j-tiles) with
+    # the equal-mass form, every 1/s^2 from the rsqrt
+    ic = inputs.grid32()
+    for prec, comp, nrcp in ((B.FP32, False, 0), (B.FP32_COMP, True, 0)):
+        sim = B.Simulation(ic.m, ic.eps, LCDM, 1.0, prec=prec)
+        try:
+            sim.set_state(ic.x)
+            p = sim.force_plan()
+        finally:
+            sim.close()
+        assert p["kind"] == "force_f32" and p["comp"] == comp and p["eqm"]
+        assert (p["threads"], p["ipt"], p["jt"], p["nrcp"]) == (512, 4, 512, nrcp)
+        assert p["units"] == (ic.N // 2048) * (ic.N // 512)
