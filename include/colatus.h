@@ -412,18 +412,22 @@ const char *colatus_ensemble_last_error(colatus_ens_t e);
 void colatus_ensemble_destroy(colatus_ens_t e);
 
 /* Tangent-linear model for finite-time Lyapunov growth of single tracers
- * (FP32, KDK).  Tangent b starts as a unit position perturbation `dir` (host
- * double[3]; NULL: x axis) on body seeds[b] only, with zero velocity
- * perturbation; the whole system's linear response is then propagated:
+ * (FP32; any of the three schemes).  Tangent b starts as a unit position
+ * perturbation `dir` (host double[3]; NULL: x axis) on body seeds[b] only,
+ * with zero velocity perturbation; the whole system's linear response is
+ * then propagated:
  *     dF_k = G sum_{j != k} m_j J(d_kj) (dx_j - dx_k),  J(d) = I/s^3 - 3 d d^T/s^5,
- * through the same KDK steps as the state.  After every step the norm
+ * through the same steps as the state (the linearisation of Eqs. 3-5 for
+ * DKD, with the JVP at the half-drift positions).  After every step the norm
  * |(dx, dv)| of the seed body of each tangent is recorded (ring of
  * capacity_steps records); ln(norm)/t is the finite-time Lyapunov exponent.
  * Initialising replaces any previous tangents. */
 colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, const double *dir,
                                     int64_t capacity_steps);
-/* Advance the state and its tangents by nsteps KDK steps of size dt (FP32
- * precision only).  COLATUS_E_STATE if the state was stepped without them. */
+/* Advance the state and its tangents by nsteps steps of size dt of the
+ * configured scheme (FP32 precision only; the step size and the scheme may
+ * change between calls).  COLATUS_E_STATE if the state was stepped without
+ * them. */
 colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps);
 /* Recorded growth, oldest first, host [nrec][B] floats; growth may be NULL
  * to query *nrec_out.  Synchronises. */

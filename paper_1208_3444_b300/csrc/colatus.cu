@@ -298,6 +298,7 @@ struct colatus_ctx {
         double tau = 0.0;
         ForcePlan plan;
         float4 *dx = nullptr, *dv = nullptr, *dvh = nullptr;
+        float4 *dxp = nullptr;                   // [B][n_pad] packed tangent positions (periodic)
         float *pkt = nullptr;                    // packed JVP input, pair-interleaved
         long long *seeds = nullptr;
         float *growth = nullptr;
@@ -932,8 +933,8 @@ void free_all(colatus_t ctx) {
                     ctx->kwr, ctx->kwl, ctx->pk_ew};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    void *tptrs[] = {ctx->tan.dx, ctx->tan.dv, ctx->tan.dvh, ctx->tan.pkt, ctx->tan.seeds,
-                     ctx->tan.growth, ctx->tan.lrt};
+    void *tptrs[] = {ctx->tan.dx, ctx->tan.dv, ctx->tan.dvh, ctx->tan.dxp, ctx->tan.pkt,
+                     ctx->tan.seeds, ctx->tan.growth, ctx->tan.lrt};
     for (void *p : tptrs)
         if (p) cudaFree(p);
     void *aptrs[] = {ctx->adj.ck_x, ctx->adj.ck_v, ctx->adj.seg_x, ctx->adj.table, ctx->adj.rclk,
@@ -1376,6 +1377,7 @@ TangentState tan_state(colatus_t ctx) {
     T.dx = t.dx;
     T.dv = t.dv;
     T.dvh = t.dvh;
+    T.dxp = ctx->periodic ? t.dxp : nullptr;
     T.pkt = t.pkt;
     T.seeds = t.seeds;
     T.growth = t.growth;
@@ -1399,7 +1401,7 @@ colatus_status run_ewald_kspace_jvp(colatus_t ctx, const float *pk) {
     C.src = masses_of(pk, nullptr);
     C.mode = 0;
     C.widx[0] = 6;
-    C.tdx = t.dx;
+    C.tdx = t.dxp;   // the tangent positions of this JVP (tan_pack_kernel)
     C.n_pad = t.n_pad;
     C.B = t.B;
     float2 *ph = static_cast<float2 *>(ctx->ph);
@@ -1433,7 +1435,7 @@ colatus_status run_ewald_kspace_jvp(colatus_t ctx, const float *pk) {
         }
         ewald_kvjp_kernel<float, float4, kTB><<<blocks_for(ctx->N, kEwFThreads), kEwFThreads * kEwFSlices,
                                                 ew_kvjp_smem<float, kTB>(ctx->ew.nk), ctx->stream>>>(
-            ctx->N, ph, ctx->pen, ctx->npen, ctx->nkv, wr, wl, C.src, t.dx + (size_t)b0 * t.n_pad, t.n_pad,
+            ctx->N, ph, ctx->pen, ctx->npen, ctx->nkv, wr, wl, C.src, t.dxp + (size_t)b0 * t.n_pad, t.n_pad,
             ntan, ctx->ew, t.lrt + (size_t)b0 * t.n_pad, t.n_pad);
         TRY(launched(ctx));
     }
@@ -1441,11 +1443,15 @@ colatus_status run_ewald_kspace_jvp(colatus_t ctx, const float *pk) {
 }
 
 // Pack positions (pair-interleaved pk) with the tangents and run the JVP.
-colatus_status run_jvp(colatus_t ctx, const float *pk) {
+// JVP of every tangent at the positions pk, the tangent positions formed
+// from the tangent state as `mode` says (TanDrift, drift time t_drift).
+colatus_status run_jvp(colatus_t ctx, const float *pk, int mode, float t_drift) {
     auto &t = ctx->tan;
+    // periodic: the reciprocal-space JVP reads the tangent positions as float4
+    if (ctx->periodic && !t.dxp) CU(cudaMalloc(&t.dxp, (size_t)t.B * t.n_pad * sizeof(float4)));
     const TangentState T = tan_state(ctx);
     dim3 grid(blocks_for(t.n_pad, 256), t.nchunk);
-    tan_pack_kernel<<<grid, 256, 0, ctx->stream>>>(pk, T, ctx->N, t.n_pad);
+    tan_pack_kernel<<<grid, 256, 0, ctx->stream>>>(pk, T, ctx->N, t.n_pad, mode, t_drift);
     TRY(launched(ctx));
     TRY(ensure_part(ctx, t.plan.part_bytes));
     if (ctx->periodic)
@@ -1627,6 +1633,7 @@ colatus_status colatus_set_config(colatus_t ctx, colatus_prec prec, colatus_sche
         ctx->acc_valid = false;
     if (scheme != ctx->scheme) ctx->tab_valid = false;   // the schedule's coefficients change
     ctx->spec_valid = false;
+    ctx->tan.open = false;   // the tangent's half kick too
     ctx->prec = prec;
     ctx->scheme = scheme;
     ctx->G = G;
@@ -1653,6 +1660,7 @@ colatus_status colatus_set_masses(colatus_t ctx, const void *m, int dtype, int o
     TRY(st);
     ctx->acc_valid = false;
     ctx->spec_valid = false;
+    ctx->tan.open = false;   // the tangent's half kick too
     return COLATUS_OK;
 }
 
@@ -1682,6 +1690,7 @@ colatus_status colatus_set_state(colatus_t ctx, const void *x, const void *v, in
     ctx->have_state = true;
     ctx->acc_valid = false;
     ctx->spec_valid = false;
+    ctx->tan.open = false;   // the tangent's half kick too
     return COLATUS_OK;
 }
 
@@ -2363,7 +2372,7 @@ colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, 
     }
     if (!ctx->have_state) return fail(ctx, COLATUS_E_STATE, "no state has been set");
     CU(cudaStreamSynchronize(ctx->stream));
-    void *old[] = {t.dx, t.dv, t.dvh, t.pkt, t.seeds, t.growth, t.lrt};
+    void *old[] = {t.dx, t.dv, t.dvh, t.dxp, t.pkt, t.seeds, t.growth, t.lrt};
     for (void *p : old)
         if (p) cudaFree(p);
     t = colatus_ctx::Tangent();
@@ -2434,29 +2443,32 @@ colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps) {
     DeviceGuard dg(ctx->device);
     auto &t = ctx->tan;
     if (!t.ready) return fail(ctx, COLATUS_E_STATE, "colatus_tangent_init first");
-    if (ctx->prec == COLATUS_FP64 || !is_kdk(ctx))
-        return fail(ctx, COLATUS_E_ARG, "the tangent model runs with FP32 precision and KDK");
+    if (ctx->prec == COLATUS_FP64)
+        return fail(ctx, COLATUS_E_ARG, "the tangent model runs with FP32 precision");
     if (t.last_step != ctx->host_step)
         return fail(ctx, COLATUS_E_STATE, "the state moved without its tangents; re-initialise");
     if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(ctx, COLATUS_E_ARG, "bad dt/nsteps");
     if (nsteps == 0) return COLATUS_OK;
-    if (t.open && t.tau != dt) t.open = false;
+    // KDK: the half kick dvh belongs to one step size; a new one re-opens
+    // from the tangent at the state's step (dx, dv), as the state does
+    const bool kdk = is_kdk(ctx);
+    if (t.open && (t.tau != dt || !kdk)) t.open = false;
     if (ctx->spec_valid && ctx->spec_tau != dt) ctx->spec_valid = false;
     const TangentState T = tan_state(ctx);
     dim3 grid(blocks_for(ctx->N, 256), t.nchunk);
     for (int64_t done = 0; done < nsteps;) {
         const int n = (int)std::min<int64_t>(kChunk, nsteps - done);
         TRY(need_table(ctx, dt, n, kTabPiece));
-        if (!t.open) {
-            // tangent opening at x^n: JVP on the packed state positions
+        if (kdk && !t.open) {
+            // KDK tangent opening at x^n: JVP on the packed state positions
             const ForcePlan &p = plan_f32(ctx);
             pack_f32_kernel<<<blocks_for(p.n_pad, 256), 256, 0, ctx->stream>>>(ctx->xs, ctx->pk[2],
                                                                                ctx->N, p.n_pad);
             TRY(launched(ctx));
-            TRY(run_jvp(ctx, ctx->pk[2]));
+            TRY(run_jvp(ctx, ctx->pk[2], TAN_AT_STATE, 0.f));
             tan_open_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part),
                                                            t.plan.L, t.plan.itile, T, ctx->table,
-                                                           kTabCap, ctx->host_step, dt, ctx->N, t.n_pad,
+                                                           kTabCap, ctx->host_step, ctx->N, t.n_pad,
                                                            tan_extra(ctx));
             TRY(launched(ctx));
             t.open = true;
@@ -2468,14 +2480,22 @@ colatus_status colatus_tangent_step(colatus_t ctx, double dt, int64_t nsteps) {
             ctx->spec_tau = dt;
         }
         for (int j = 0; j < n; ++j) {
+            // the step's force input pk[c] (x^{n+1} for KDK, x^{n+1/2} for
+            // DKD) is also the JVP's; one_step writes the next into pk[c ^ 1]
             const int c = ctx->cur;
             TRY(wait_table_at(ctx, j, n));
             TRY(one_step(ctx, j, dt));
-            TRY(run_jvp(ctx, ctx->pk[c]));
-            tan_step_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const float4 *>(ctx->part),
-                                                           t.plan.L, t.plan.itile, T, ctx->table,
-                                                           kTabCap, ctx->host_step + j, dt, ctx->N,
-                                                           t.n_pad, tan_extra(ctx));
+            if (kdk) {
+                TRY(run_jvp(ctx, ctx->pk[c], TAN_KDK_DRIFT, (float)dt));
+                tan_step_kernel<<<grid, 256, 0, ctx->stream>>>(
+                    static_cast<const float4 *>(ctx->part), t.plan.L, t.plan.itile, T, ctx->table, kTabCap,
+                    ctx->host_step + j, dt, ctx->N, t.n_pad, tan_extra(ctx));
+            } else {
+                TRY(run_jvp(ctx, ctx->pk[c], TAN_DKD_HALF, (float)(0.5 * dt)));
+                tan_dkd_step_kernel<<<grid, 256, 0, ctx->stream>>>(
+                    static_cast<const float4 *>(ctx->part), t.plan.L, t.plan.itile, T, ctx->table, kTabCap,
+                    ctx->host_step + j, dt, ctx->N, t.n_pad, tan_extra(ctx));
+            }
             TRY(launched(ctx));
         }
         done += n;
@@ -2561,6 +2581,7 @@ colatus_status colatus_autotune(colatus_t ctx, int reps, double out_ms[3], int *
     ctx->ev_used = used;
     ctx->tuned_shape = best_sh >= 0 ? best_sh : keep;
     ctx->spec_valid = false;   // the next step re-opens with the chosen kernel
+    ctx->tan.open = false;   // the tangent's half kick too
     if (chosen) *chosen = ctx->tuned_shape;
     return sync_and_check(ctx);
 }
@@ -2624,6 +2645,7 @@ colatus_status colatus_set_periodic(colatus_t ctx, double L, double alpha, int n
         if (ctx->periodic) {
             ctx->periodic = false;
             ctx->acc_valid = ctx->spec_valid = false;
+            ctx->tan.open = false;   // the tangent's half kick too
         }
         return COLATUS_OK;
     }

@@ -1,5 +1,5 @@
 // tangent.cuh -- tangent-linear (JVP) model of the Eq. 1 force and of the
-// KDK leapfrog, for finite-time Lyapunov growth of single tracers.
+// KDK and DKD leapfrogs, for finite-time Lyapunov growth of single tracers.
 //
 // For a perturbation dx of all positions, the force perturbation is
 //     dF_k = sum_{j != k} m_j J(d_kj) (dx_j - dx_k),
@@ -217,8 +217,12 @@ __device__ __forceinline__ void jvp_reduce(const float4 *__restrict__ part, cons
 
 // Tangent state per (tangent b, body i): dx, dv, dvh as float4 in
 // [B][N_pad] arrays; seeds[b] is the body whose own growth is recorded.
+// dx and dv are the tangent at the state's step; dvh (KDK) the half-kicked
+// velocity tangent of the step about to be taken.  The tangent position at
+// which a step's JVP is evaluated is formed when it is packed (TanDrift).
 struct TangentState {
     float4 *dx, *dv, *dvh;
+    float4 *dxp;              // [B][N_pad] the packed tangent positions as float4, or null
     float *pkt;               // [nchunk][N_pad / 2][32], pair-interleaved (jvp_f32x2_kernel)
     const long long *seeds;   // [B]
     float *growth;            // [cap][B]
@@ -226,9 +230,22 @@ struct TangentState {
     int B, nchunk;
 };
 
+// Tangent position packed for a JVP: the state's own (TAN_AT_STATE), the
+// KDK drift dx + tau dvh to x^{n+1} (TAN_KDK_DRIFT), or the DKD half drift
+// dx + (tau/2) dv to x^{n+1/2} (TAN_DKD_HALF), with the rounding of the
+// state's drift (drift1), so the tangent epilogues recompute it bit for bit.
+enum TanDrift { TAN_AT_STATE = 0, TAN_KDK_DRIFT = 1, TAN_DKD_HALF = 2 };
+
+__device__ __forceinline__ float4 tan_drifted(const TangentState &T, long long k, int mode, float t) {
+    const float4 d = T.dx[k];
+    if (mode == TAN_AT_STATE) return d;
+    const float4 w = mode == TAN_KDK_DRIFT ? T.dvh[k] : T.dv[k];
+    return make_float4(drift1(d.x, t, w.x), drift1(d.y, t, w.y), drift1(d.z, t, w.z), 0.f);
+}
+
 // Pack positions (pair-interleaved pk, padded) and tangent positions.
 __global__ void tan_pack_kernel(const float *__restrict__ pk, TangentState T, long long N,
-                                long long n_pad) {
+                                long long n_pad, int mode, float t_drift) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int chunk = blockIdx.y;
     if (i >= n_pad) return;
@@ -238,7 +255,8 @@ __global__ void tan_pack_kernel(const float *__restrict__ pk, TangentState T, lo
     for (int q = 0; q < kTB; ++q) {
         const long long b = (long long)chunk * kTB + q;
         float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < N && b < T.B) d = T.dx[b * n_pad + i];
+        if (i < N && b < T.B) d = tan_drifted(T, b * n_pad + i, mode, t_drift);
+        if (T.dxp && b < T.B) T.dxp[b * n_pad + i] = d;
         t[3 * q] = d.x;
         t[3 * q + 1] = d.y;
         t[3 * q + 2] = d.z;
@@ -252,8 +270,8 @@ __global__ void tan_pack_kernel(const float *__restrict__ pk, TangentState T, lo
     for (int c = 0; c < 3 * kTB; ++c) o[2 * (4 + c)] = t[c];
 }
 
-// Opening of the tangent: dvh = c1 dv + d1 dF(x^n);  dx' = dx + tau dvh.
-// Deformation term's tangent at the packed position of (chunk, i).
+// Deformation term's tangent at the packed position and tangent position
+// of (chunk, i).
 __device__ __forceinline__ void tan_defo(const TangentState &T, const Extra &D, int chunk,
                                          long long i, long long n_pad, float (&f)[kTC]) {
     if (!D.on) return;
@@ -262,8 +280,8 @@ __device__ __forceinline__ void tan_defo(const TangentState &T, const Extra &D, 
     for (int q = 0; q < kTB; ++q) {
         const long long b = (long long)chunk * kTB + q;
         if (b >= T.B) break;
-        const float4 d = T.dx[b * n_pad + i];
-        defo_jacobian<float>(D, x[0], x[2], x[4], d.x, d.y, d.z, f[3 * q], f[3 * q + 1], f[3 * q + 2]);
+        const float *d = x + 2 * (4 + 3 * q);
+        defo_jacobian<float>(D, x[0], x[2], x[4], d[0], d[2], d[4], f[3 * q], f[3 * q + 1], f[3 * q + 2]);
     }
 }
 
@@ -283,9 +301,10 @@ __device__ __forceinline__ void tan_kspace(const TangentState &T, const Extra &D
     }
 }
 
+// KDK opening of the tangent after the JVP at x^n: dvh = c1 dv + d1 dF(x^n).
 __global__ void tan_open_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
                                 TangentState T, const StepCoef *__restrict__ table, int tcap,
-                                long long step, double tau, long long N, long long n_pad, Extra D) {
+                                long long step, long long N, long long n_pad, Extra D) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int chunk = blockIdx.y;
     if (i >= N) return;
@@ -294,7 +313,7 @@ __global__ void tan_open_kernel(const float4 *__restrict__ part, ForceLaunch L, 
     tan_kspace(T, D, chunk, i, n_pad, f);
     tan_defo(T, D, chunk, i, n_pad, f);
     const StepCoef &e = table[step % tcap];
-    const float c1 = (float)e.c1, d1 = (float)e.d1, t = (float)tau;
+    const float c1 = (float)e.c1, d1 = (float)e.d1;
 #pragma unroll
     for (int q = 0; q < kTB; ++q) {
         const long long b = (long long)chunk * kTB + q;
@@ -304,14 +323,13 @@ __global__ void tan_open_kernel(const float4 *__restrict__ part, ForceLaunch L, 
         const float hx = kick2(c1, v.x, d1, f[3 * q]), hy = kick2(c1, v.y, d1, f[3 * q + 1]),
                     hz = kick2(c1, v.z, d1, f[3 * q + 2]);
         T.dvh[k] = make_float4(hx, hy, hz, 0.f);
-        const float4 x = T.dx[k];
-        T.dx[k] = make_float4(drift1(x.x, t, hx), drift1(x.y, t, hy), drift1(x.z, t, hz), 0.f);
     }
 }
 
-// Step of the tangent after the JVP at x^{n+1}: dv = c2 dvh + d2 dF; record
-// the seed body's |(dx, dv)|; open the next step with the next entry's
-// coefficients: dvh = c1' dv + d1' dF, dx += tau dvh.
+// KDK step of the tangent after the JVP at x^{n+1} (packed as
+// TAN_KDK_DRIFT): dx' = dx + tau dvh, dv' = c2 dvh + d2 dF; record the seed
+// body's |(dx', dv')|; the next step's half kick with the next entry's
+// coefficients: dvh = c1' dv' + d1' dF.
 __global__ void tan_step_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
                                 TangentState T, const StepCoef *__restrict__ table, int tcap,
                                 long long step, double tau, long long N, long long n_pad, Extra D) {
@@ -334,7 +352,7 @@ __global__ void tan_step_kernel(const float4 *__restrict__ part, ForceLaunch L, 
         const float4 h = T.dvh[k];
         const float vx = kick2(c2, h.x, d2, f[3 * q]), vy = kick2(c2, h.y, d2, f[3 * q + 1]),
                     vz = kick2(c2, h.z, d2, f[3 * q + 2]);
-        const float4 x = T.dx[k];
+        const float4 x = tan_drifted(T, k, TAN_KDK_DRIFT, t);
         T.dv[k] = make_float4(vx, vy, vz, 0.f);
         if (T.seeds[b] == i && T.cap > 0) {
             const long long r = (step - T.base) % T.cap;
@@ -344,7 +362,42 @@ __global__ void tan_step_kernel(const float4 *__restrict__ part, ForceLaunch L, 
         const float nx = kick2(c1n, vx, d1n, f[3 * q]), ny = kick2(c1n, vy, d1n, f[3 * q + 1]),
                     nz = kick2(c1n, vz, d1n, f[3 * q + 2]);
         T.dvh[k] = make_float4(nx, ny, nz, 0.f);
-        T.dx[k] = make_float4(drift1(x.x, t, nx), drift1(x.y, t, ny), drift1(x.z, t, nz), 0.f);
+        T.dx[k] = x;
+    }
+}
+
+// DKD step of the tangent (Eqs. 3-5 linearised; c, d at t^{n+1/2}) after the
+// JVP at x^{n+1/2} (packed as TAN_DKD_HALF):
+//   dxh = dx + (tau/2) dv;  dv' = c dv + d dF;  dx' = dxh + (tau/2) dv';
+// record the seed body's |(dx', dv')|.
+__global__ void tan_dkd_step_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
+                                    TangentState T, const StepCoef *__restrict__ table, int tcap,
+                                    long long step, double tau, long long N, long long n_pad, Extra D) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int chunk = blockIdx.y;
+    if (i >= N) return;
+    float f[kTC];
+    jvp_reduce(part, L, itile, chunk, i, f);
+    tan_kspace(T, D, chunk, i, n_pad, f);
+    tan_defo(T, D, chunk, i, n_pad, f);
+    const StepCoef &e = table[step % tcap];
+    const float c = (float)e.c, d = (float)e.d, h = (float)(0.5 * tau);
+#pragma unroll
+    for (int q = 0; q < kTB; ++q) {
+        const long long b = (long long)chunk * kTB + q;
+        if (b >= T.B) break;
+        const long long k = b * n_pad + i;
+        const float4 xh = tan_drifted(T, k, TAN_DKD_HALF, h);
+        const float4 v0 = T.dv[k];
+        const float vx = kick2(c, v0.x, d, f[3 * q]), vy = kick2(c, v0.y, d, f[3 * q + 1]),
+                    vz = kick2(c, v0.z, d, f[3 * q + 2]);
+        const float x1 = drift1(xh.x, h, vx), y1 = drift1(xh.y, h, vy), z1 = drift1(xh.z, h, vz);
+        T.dv[k] = make_float4(vx, vy, vz, 0.f);
+        T.dx[k] = make_float4(x1, y1, z1, 0.f);
+        if (T.seeds[b] == i && T.cap > 0) {
+            const long long r = (step - T.base) % T.cap;
+            T.growth[r * T.B + b] = sqrtf(x1 * x1 + y1 * y1 + z1 * z1 + vx * vx + vy * vy + vz * vz);
+        }
     }
 }
 

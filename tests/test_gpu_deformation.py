@@ -181,13 +181,15 @@ def test_trajectory_adjoint_with_deformation(prec, tol, scheme):
         assert rel(got, ref) < tol, k
 
 
-def test_tangent_growth_with_deformation():
+@pytest.mark.parametrize("scheme", ["kdk", "dkd"])
+def test_tangent_growth_with_deformation(scheme):
     ic = inputs.grid16(critical=True)
     defo = (0.3 * float(np.sum(ic.m)), XPSI)
     seeds = [7, 2049, 4000]
     n = 8
     d = np.array([0.5, -1.0, 2.0])
-    sim = B.Simulation(ic.m, ic.eps, LCDM_D, A_LATE, prec=B.FP32)
+    sim = B.Simulation(ic.m, ic.eps, LCDM_D, A_LATE, prec=B.FP32,
+                       scheme=B.KDK if scheme == "kdk" else B.DKD)
     try:
         sim.set_state(ic.x, ic.v)
         sim.set_deformation(*defo)
@@ -200,6 +202,6 @@ def test_tangent_growth_with_deformation():
         dx0 = np.zeros_like(ic.x)
         dx0[s] = d / np.linalg.norm(d)
         _, _, hist = oracle.tangent_run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, A_LATE, TAU, n,
-                                        dx0, np.zeros_like(ic.v), "kdk", defo=defo)
+                                        dx0, np.zeros_like(ic.v), scheme, defo=defo)
         ref = np.array([np.sqrt(np.sum(h[0][s] ** 2) + np.sum(h[1][s] ** 2)) for h in hist[1:]])
         np.testing.assert_allclose(growth[:, b], ref, rtol=1e-4)

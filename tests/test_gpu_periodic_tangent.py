@@ -1,7 +1,7 @@
 """GPU parity of the tangent-linear model under periodic boundaries (Sec. II;
 Ewald summation) against the oracle's FP64 tangent_run with box = L, for
-single-tracer seeds: the real-space periodic JVP kernel and the per-tangent
-reciprocal-space JVP."""
+single-tracer seeds, through KDK and DKD steps: the real-space periodic JVP
+kernel and the per-tangent reciprocal-space JVP."""
 import functools
 
 import numpy as np
@@ -27,21 +27,24 @@ def case():
 
 
 @functools.lru_cache(maxsize=None)
-def oracle_growth(seed):
+def oracle_growth(seed, scheme="kdk"):
     ic = case()
     dx0 = np.zeros_like(ic.x)
     dx0[seed] = D / np.linalg.norm(D)
     _, _, hist = oracle.tangent_run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, NSTEPS,
-                                    dx0, np.zeros_like(ic.v), "kdk", box=1.0)
+                                    dx0, np.zeros_like(ic.v), scheme, box=1.0)
     return np.array([np.sqrt(np.sum(h[0][seed] ** 2) + np.sum(h[1][seed] ** 2)) for h in hist[1:]])
 
 
-@pytest.mark.parametrize("seeds,check", [([5, 100, 215], [0, 1, 2]),
-                                         ([0, 3, 7, 50, 99, 120, 150, 180, 201], [0, 8])])
-def test_periodic_tracer_growth_matches_oracle_tangent(seeds, check):
-    # the second case has 9 tangents: a full chunk of 8 and a partial one
+@pytest.mark.parametrize("seeds,check,scheme", [([5, 100, 215], [0, 1, 2], "kdk"),
+                                                ([0, 3, 7, 50, 99, 120, 150, 180, 201], [0, 8], "kdk"),
+                                                ([5, 100, 215], [0, 2], "dkd")])
+def test_periodic_tracer_growth_matches_oracle_tangent(seeds, check, scheme):
+    # the second case has 9 tangents: a full chunk of 8 and a partial one;
+    # the third takes the paper's DKD steps (JVP at the half-drift positions)
     ic = case()
-    sim = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START, prec=B.FP32)
+    sch = B.KDK if scheme == "kdk" else B.DKD
+    sim = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START, prec=B.FP32, scheme=sch)
     try:
         sim.set_state(ic.x, ic.v)
         sim.set_periodic(1.0)
@@ -54,9 +57,9 @@ def test_periodic_tracer_growth_matches_oracle_tangent(seeds, check):
         sim.close()
     assert growth.shape == (NSTEPS, len(seeds))
     for b in check:
-        np.testing.assert_allclose(growth[:, b], oracle_growth(seeds[b]), rtol=1e-4)
+        np.testing.assert_allclose(growth[:, b], oracle_growth(seeds[b], scheme), rtol=1e-4)
     # the state advanced exactly as colatus_step advances it
-    sim = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START, prec=B.FP32)
+    sim = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START, prec=B.FP32, scheme=sch)
     try:
         sim.set_state(ic.x, ic.v)
         sim.set_periodic(1.0)
