@@ -391,6 +391,19 @@ colatus_status colatus_ensemble_forces(colatus_ens_t e, void *acc_out, int dtype
 /* nsteps KDK steps of size dt > 0 for every realisation (asynchronous). */
 colatus_status colatus_ensemble_step(colatus_ens_t e, double dt, int64_t nsteps);
 colatus_status colatus_ensemble_synchronize(colatus_ens_t e);
+/* Tracers of the ensemble (Sec. I: the velocities of single bodies at every
+ * step), as colatus_record_tracers for one system: record (x, v) of ntr
+ * bodies idx[0..ntr) (host int64 indices into the dense N_tot rows,
+ * distinct) after every subsequent step, graph replays included, into a
+ * device ring of capacity_steps records; ntr = 0 stops recording.  Replaces
+ * any earlier recording and drops the captured step graphs (recaptured at
+ * the next step).  Synchronises.  Errors: COLATUS_E_ARG. */
+colatus_status colatus_ensemble_record_tracers(colatus_ens_t e, const int64_t *idx, int ntr,
+                                               int64_t capacity_steps);
+/* The recorded tracers, oldest first, to host xv_out [nrec][ntr][6] floats
+ * (x, y, z, vx, vy, vz); *nrec_out = records copied (<= capacity); xv_out
+ * may be NULL to query *nrec_out.  Synchronises and reports device flags. */
+colatus_status colatus_ensemble_read_tracers(colatus_ens_t e, float *xv_out, int64_t *nrec_out);
 /* Synchronises; out[0] kernel launches (a 16-step graph counts its 33),
  * out[1] interactions enqueued, out[2] steps, out[3] interactions per step,
  * out[4]/out[5] milliseconds/number of force launches timed outside graphs

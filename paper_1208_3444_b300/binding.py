@@ -34,6 +34,7 @@ EXPORTS = ("colatus_init", "colatus_set_config", "colatus_set_masses", "colatus_
            "colatus_adjoint_backward", "colatus_forces_noalloc", "colatus_destroy",
            "colatus_ensemble_init", "colatus_ensemble_set_state", "colatus_ensemble_get_state",
            "colatus_ensemble_forces", "colatus_ensemble_step", "colatus_ensemble_synchronize",
+           "colatus_ensemble_record_tracers", "colatus_ensemble_read_tracers",
            "colatus_ensemble_stats", "colatus_ensemble_last_error", "colatus_ensemble_destroy",
            "colatus_tangent_init", "colatus_tangent_step", "colatus_tangent_read",
            "colatus_autotune", "colatus_set_tuning", "colatus_probe_pipes",
@@ -92,6 +93,8 @@ def lib():
         "colatus_ensemble_forces": [_vp, _vp, _int, _int],
         "colatus_ensemble_step": [_vp, _dbl, _i64],
         "colatus_ensemble_synchronize": [_vp],
+        "colatus_ensemble_record_tracers": [_vp, _vp, _int, _i64],
+        "colatus_ensemble_read_tracers": [_vp, _vp, _vp],
         "colatus_ensemble_stats": [_vp, _int, _vp],
         "colatus_tangent_init": [_vp, _vp, _int, _vp, _i64],
         "colatus_autotune": [_vp, _int, _vp, _vp],
@@ -616,6 +619,22 @@ class Ensemble:
 
     def synchronize(self):
         _echeck(lib().colatus_ensemble_synchronize(self.h), self.h)
+
+    def record_tracers(self, idx, capacity_steps):
+        """Record (x, v) of bodies idx (dense row indices) after every step."""
+        idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64).reshape(-1))
+        _echeck(lib().colatus_ensemble_record_tracers(self.h, idx.ctypes.data if idx.size else None,
+                                                      int(idx.size), int(capacity_steps)), self.h)
+        self.ntr = int(idx.size)
+
+    def read_tracers(self):
+        """Recorded tracers, oldest first: [nrec, ntr, 6] (x, y, z, vx, vy, vz)."""
+        n = ctypes.c_int64()
+        _echeck(lib().colatus_ensemble_read_tracers(self.h, None, ctypes.byref(n)), self.h)
+        out = np.empty((n.value, getattr(self, "ntr", 0), 6), dtype=np.float32)
+        if n.value and out.size:
+            _echeck(lib().colatus_ensemble_read_tracers(self.h, out.ctypes.data, ctypes.byref(n)), self.h)
+        return out
 
     def autotune(self, reps=3):
         """Time the force kernel's CTA shapes at the current state and keep

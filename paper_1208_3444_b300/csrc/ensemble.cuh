@@ -266,7 +266,7 @@ __global__ void ens_step_kernel(const float4 *__restrict__ part, EnsLaunch E, in
                                 float4 *__restrict__ vs, float4 *__restrict__ vh,
                                 float4 *__restrict__ acc, float *__restrict__ pk_out,
                                 const StepCoef *__restrict__ table, int j, double tau,
-                                long long Npad, int *flags, DevClock *clk) {
+                                long long Npad, int *flags, DevClock *clk, Tracers tr) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= Npad) return;
     const StepCoef &sc = table[j];
@@ -283,6 +283,7 @@ __global__ void ens_step_kernel(const float4 *__restrict__ part, EnsLaunch E, in
     acc[i] = make_float4(F.x, F.y, F.z, 0.f);
     xs[i] = x;
     vs[i] = make_float4(vx, vy, vz, 0.f);
+    record(tr, i, sc.step, x.x, x.y, x.z, vx, vy, vz);   // tr.slot is indexed by padded body
     const float nx = kick2(c2, vx, d2, F.x), ny = kick2(c2, vy, d2, F.y), nz = kick2(c2, vz, d2, F.z);
     vh[i] = make_float4(nx, ny, nz, 0.f);
     pk_store(pk_out, i, drift1(x.x, t, nx), drift1(x.y, t, ny), drift1(x.z, t, nz), x.w);

@@ -92,6 +92,11 @@ struct colatus_ensemble {
     size_t ev_used = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // per ping-pong parity
     double graph_tau[2] = {0.0, 0.0};
+    // tracer records (colatus_ensemble_record_tracers): slot per padded body
+    int *tslot = nullptr;
+    float *rec = nullptr;
+    long long rec_cap = 0, rec_base = 0;
+    int ntr = 0;
     char err[512] = {0};
 };
 
@@ -235,9 +240,9 @@ colatus_status ens_steps(colatus_ens_t e, double tau, int n) {
     for (int j = 0; j < n; ++j) {
         const int c = e->cur, nx = c ^ 1;
         if ((st = ens_force(e, e->pk[c])) != COLATUS_OK) return st;
-        ens_step_kernel<<<ens_blocks(e), 256, 0, e->stream>>>(e->part, e->E, kEnsTile, e->pk[c], e->xs,
-                                                             e->vs, e->vh, e->acc, e->pk[nx], e->table,
-                                                             j, tau, e->Npad, e->flags, e->clk);
+        ens_step_kernel<<<ens_blocks(e), 256, 0, e->stream>>>(
+            e->part, e->E, kEnsTile, e->pk[c], e->xs, e->vs, e->vh, e->acc, e->pk[nx], e->table, j, tau,
+            e->Npad, e->flags, e->clk, Tracers{e->tslot, e->rec, e->rec_cap, e->rec_base, e->ntr});
         if ((st = elaunched(e)) != COLATUS_OK) return st;
         e->cur = nx;
     }
@@ -279,7 +284,7 @@ void ens_free(colatus_ens_t e) {
         if (g) cudaGraphExecDestroy(g);
     for (cudaEvent_t v : e->ev) cudaEventDestroy(v);
     void *ptrs[] = {e->meta, e->xs, e->vs, e->vh, e->acc, e->pk[0], e->pk[1], e->pk[2],
-                    e->part, e->flags, e->clk, e->table, e->stage, e->stage2};
+                    e->part, e->flags, e->clk, e->table, e->stage, e->stage2, e->tslot, e->rec};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
@@ -574,6 +579,73 @@ colatus_status colatus_ensemble_synchronize(colatus_ens_t e) {
     if (!e) return COLATUS_E_ARG;
     DeviceGuard dg(e->device);
     return ens_check(e, true);
+}
+
+colatus_status colatus_ensemble_record_tracers(colatus_ens_t e, const int64_t *idx, int ntr,
+                                               int64_t capacity_steps) {
+    if (!e) return COLATUS_E_ARG;
+    DeviceGuard dg(e->device);
+    if (ntr < 0) return efail(e, COLATUS_E_ARG, "ntr must be >= 0");
+    if (ntr > 0 && (!idx || capacity_steps < 1))
+        return efail(e, COLATUS_E_ARG, "need indices and capacity_steps >= 1");
+    std::vector<int> slot;
+    if (ntr > 0) {
+        // dense index k of realisation r -> padded body body_off[r] + (k - user_off[r])
+        slot.assign(e->Npad, -1);
+        for (int q = 0; q < ntr; ++q) {
+            const long long k = idx[q];
+            if (k < 0 || k >= e->Ntot) return efail(e, COLATUS_E_ARG, "tracer index %lld out of range", k);
+            const int r = (int)(std::upper_bound(e->user_off.begin(), e->user_off.end(), k) -
+                                e->user_off.begin()) - 1;
+            const long long i = e->body_off[r] + (k - e->user_off[r]);
+            if (slot[i] >= 0) return efail(e, COLATUS_E_ARG, "duplicate tracer index");
+            slot[i] = q;
+        }
+    }
+    ECU(cudaStreamSynchronize(e->stream));
+    // the captured graphs hold the old buffers as kernel arguments
+    for (cudaGraphExec_t &g : e->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    if (e->tslot) cudaFree(e->tslot);
+    if (e->rec) cudaFree(e->rec);
+    e->tslot = nullptr;
+    e->rec = nullptr;
+    e->ntr = 0;
+    e->rec_cap = 0;
+    if (ntr == 0) return COLATUS_OK;
+    ECU(cudaMalloc(&e->tslot, (size_t)e->Npad * sizeof(int)));
+    ECU(cudaMalloc(&e->rec, (size_t)capacity_steps * ntr * 6 * sizeof(float)));
+    ECU(cudaMemcpy(e->tslot, slot.data(), (size_t)e->Npad * sizeof(int), cudaMemcpyHostToDevice));
+    e->ntr = ntr;
+    e->rec_cap = capacity_steps;
+    e->rec_base = e->host_step;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_ensemble_read_tracers(colatus_ens_t e, float *xv_out, int64_t *nrec_out) {
+    if (!e) return COLATUS_E_ARG;
+    DeviceGuard dg(e->device);
+    if (!nrec_out) return efail(e, COLATUS_E_ARG, "nrec_out is NULL");
+    TRY(ens_check(e, true));
+    if (e->ntr == 0) {
+        *nrec_out = 0;
+        return COLATUS_OK;
+    }
+    const long long total = e->host_step - e->rec_base;
+    const long long nrec = std::min(total, e->rec_cap);
+    *nrec_out = nrec;
+    if (!xv_out || nrec == 0) return COLATUS_OK;
+    const size_t row = (size_t)e->ntr * 6;
+    std::vector<float> ring((size_t)e->rec_cap * row);
+    ECU(cudaMemcpy(ring.data(), e->rec, ring.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    for (long long k = 0; k < nrec; ++k) {
+        const long long s = total - nrec + k;
+        std::memcpy(xv_out + k * row, ring.data() + (s % e->rec_cap) * row, row * sizeof(float));
+    }
+    return COLATUS_OK;
 }
 
 colatus_status colatus_ensemble_stats(colatus_ens_t e, int profile_on, double out[6]) {

@@ -171,3 +171,73 @@ def test_autotune_and_every_shape(masses):
             ens.set_tuning(3)
     finally:
         ens.close()
+
+
+def test_tracers_match_oracle_per_realisation():
+    # tracers in every realisation, at its first and last body among others;
+    # 20 steps: one 16-step graph replay and 4 direct steps
+    ics = critical_ensemble([512, 1000, 1729, 3000])
+    x, v, m, eps, Ns = concat(ics)
+    off = np.concatenate([[0], np.cumsum(Ns)])
+    local = {0: [0, 511, 100], 1: [3, 999], 2: [0, 864], 3: [2999, 1500, 7]}
+    idx = np.array([off[r] + k for r in local for k in local[r]])
+    n = 20
+    ens = B.Ensemble(Ns, m, eps, LCDM_D, inputs.A_START)
+    try:
+        ens.set_state(x, v)
+        ens.record_tracers(idx, 25)
+        ens.step(TAU, n)
+        rec = ens.read_tracers()
+        gx, gv, _, _ = ens.state()
+    finally:
+        ens.close()
+    assert rec.shape == (n, len(idx), 6)
+    # the last record is the state itself, bit for bit
+    assert np.array_equal(rec[-1, :, :3], gx[idx].astype(np.float32))
+    assert np.array_equal(rec[-1, :, 3:], gv[idx].astype(np.float32))
+    col = 0
+    rng = np.random.default_rng(1)
+    for r, ks in local.items():
+        ic = ics[r]
+        ref = oracle.run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n, "kdk", tracers=ks)
+        xp = ic.x * (1.0 + 6e-8 * rng.standard_normal(ic.x.shape))
+        pert = oracle.run(xp, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n, "kdk", tracers=ks)
+        got = rec[:, col:col + len(ks)]
+        chaos = np.abs(pert["tracers"] - ref["tracers"]).max(axis=(0, 1))
+        scale = np.abs(ref["tracers"]).max(axis=(0, 1))
+        err = np.abs(got - ref["tracers"]).max(axis=(0, 1))
+        assert np.all(err[:3] < np.maximum(1e-5, 10 * chaos[:3])), (r, err)
+        assert np.all(err[3:] < np.maximum(1e-5 * scale[3:], 10 * chaos[3:])), (r, err)
+        col += len(ks)
+
+
+def test_tracer_ring_and_rerecording_with_graphs():
+    ics = critical_ensemble([700, 1300])
+    x, v, m, eps, Ns = concat(ics)
+    ens = B.Ensemble(Ns, m, eps, LCDM_D, inputs.A_START)
+    try:
+        ens.set_state(x, v)
+        ens.record_tracers([5, 1999], 7)             # a ring shorter than the run
+        ens.step(TAU, 16)
+        ens.step(TAU, 4)
+        rec = ens.read_tracers()
+        gx, gv, _, _ = ens.state()
+        assert rec.shape == (7, 2, 6)                # the last 7 of 20 steps
+        assert np.array_equal(rec[-1, :, :3], gx[[5, 1999]].astype(np.float32))
+        # new tracers: the graphs captured with the old buffers are replaced
+        ens.record_tracers([700, 3], 40)
+        ens.step(TAU, 16)
+        rec2 = ens.read_tracers()
+        gx2, gv2, _, _ = ens.state()
+        assert rec2.shape == (16, 2, 6)
+        assert np.array_equal(rec2[-1, :, :3], gx2[[700, 3]].astype(np.float32))
+        assert np.array_equal(rec2[-1, :, 3:], gv2[[700, 3]].astype(np.float32))
+        ens.record_tracers([], 1)                    # stop recording
+        ens.step(TAU, 2)
+        assert ens.read_tracers().shape[0] == 0
+        with pytest.raises(B.ColatusError):
+            ens.record_tracers([3, 3], 5)
+        with pytest.raises(B.ColatusError):
+            ens.record_tracers([2000], 5)
+    finally:
+        ens.close()
