@@ -388,8 +388,15 @@ colatus_status colatus_ensemble_get_state(colatus_ens_t e, void *x, void *v, int
                                           int on_device, double *t, double *a);
 /* Comoving accelerations G a^-3 F of every body (N_tot x 3). */
 colatus_status colatus_ensemble_forces(colatus_ens_t e, void *acc_out, int dtype, int on_device);
-/* nsteps KDK steps of size dt > 0 for every realisation (asynchronous). */
+/* nsteps steps of size dt > 0 for every realisation (asynchronous), of the
+ * scheme set by colatus_ensemble_set_scheme (KDK by default). */
 colatus_status colatus_ensemble_step(colatus_ens_t e, double dt, int64_t nsteps);
+/* Integration scheme of the ensemble's steps, as colatus_set_config's for
+ * one system: COLATUS_DKD (Eqs. 3-5, the force at the half-drift
+ * positions), COLATUS_KDK or COLATUS_KDK_CANONICAL (Sec. II).  A change
+ * synchronises, drops the captured step graphs and re-opens the next step
+ * from the state.  Errors: COLATUS_E_ARG. */
+colatus_status colatus_ensemble_set_scheme(colatus_ens_t e, colatus_scheme scheme);
 colatus_status colatus_ensemble_synchronize(colatus_ens_t e);
 /* Tracers of the ensemble (Sec. I: the velocities of single bodies at every
  * step), as colatus_record_tracers for one system: record (x, v) of ntr

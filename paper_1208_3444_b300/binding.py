@@ -35,6 +35,7 @@ EXPORTS = ("colatus_init", "colatus_set_config", "colatus_set_masses", "colatus_
            "colatus_ensemble_init", "colatus_ensemble_set_state", "colatus_ensemble_get_state",
            "colatus_ensemble_forces", "colatus_ensemble_step", "colatus_ensemble_synchronize",
            "colatus_ensemble_record_tracers", "colatus_ensemble_read_tracers",
+           "colatus_ensemble_set_scheme",
            "colatus_ensemble_stats", "colatus_ensemble_last_error", "colatus_ensemble_destroy",
            "colatus_tangent_init", "colatus_tangent_step", "colatus_tangent_read",
            "colatus_autotune", "colatus_set_tuning", "colatus_probe_pipes",
@@ -94,6 +95,7 @@ def lib():
         "colatus_ensemble_step": [_vp, _dbl, _i64],
         "colatus_ensemble_synchronize": [_vp],
         "colatus_ensemble_record_tracers": [_vp, _vp, _int, _i64],
+        "colatus_ensemble_set_scheme": [_vp, _int],
         "colatus_ensemble_read_tracers": [_vp, _vp, _vp],
         "colatus_ensemble_stats": [_vp, _int, _vp],
         "colatus_tangent_init": [_vp, _vp, _int, _vp, _i64],
@@ -577,7 +579,7 @@ class Ensemble:
     """R independent realisations stepped together (colatus_ensemble_*).
     Arrays are dense concatenations of the realisations (N_tot rows)."""
 
-    def __init__(self, Ns, masses, eps_r, cosmo, a_start, G=1.0, stream=None):
+    def __init__(self, Ns, masses, eps_r, cosmo, a_start, G=1.0, stream=None, scheme=KDK):
         Ns = np.ascontiguousarray(np.asarray(Ns, dtype=np.int64))
         m = np.ascontiguousarray(np.asarray(masses, dtype=np.float64).reshape(-1))
         e = np.ascontiguousarray(np.asarray(eps_r, dtype=np.float64).reshape(-1))
@@ -592,6 +594,8 @@ class Ensemble:
                                          None if stream is None else int(stream))
         _echeck(st, None)
         self.h = h
+        if scheme != KDK:
+            self.set_scheme(scheme)
 
     def set_state(self, x, v=None):
         dev, dt, bufs = _same(x, v)
@@ -619,6 +623,10 @@ class Ensemble:
 
     def synchronize(self):
         _echeck(lib().colatus_ensemble_synchronize(self.h), self.h)
+
+    def set_scheme(self, scheme):
+        """DKD, KDK or KDK_CANONICAL for the following steps."""
+        _echeck(lib().colatus_ensemble_set_scheme(self.h, int(scheme)), self.h)
 
     def record_tracers(self, idx, capacity_steps):
         """Record (x, v) of bodies idx (dense row indices) after every step."""

@@ -188,22 +188,39 @@ __device__ __forceinline__ bool ens_real(const EnsLaunch &E, int itile, long lon
 }
 
 // Schedule of n steps from the clock (not advanced here; the step epilogue
-// advances it): entry j of `table` is step j of the chunk.
+// advances it): entry j of `table` is step j of the chunk.  The same
+// sequence as the single-system schedule (friedmann_table_kernel): DKD's
+// (c, d) at t^{n+1/2}, KDK's half kicks at t^n and t^{n+1}, or with
+// canonical != 0 the canonical leapfrog's (c1, d1, c2, d2) from the
+// integrals of dt/a and dt/a^2.
 __global__ void ens_table_kernel(Cosmo cosmo, const DevClock *clk, StepCoef *table, int n,
-                                 double tau, double G, int nsub) {
+                                 double tau, double G, int nsub, int canonical) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     double a = clk->a, t = clk->t;
     const long long step0 = clk->step;
     for (int j = 0; j < n; ++j) {
         bool bad = false;
         StepCoef s;
-        double K = 0.0, Dr = 0.0;   // canonical integrals: not computed for the drag scheme
+        double K1 = 0.0, K2 = 0.0, D = 0.0;
         s.a0 = a;
-        s.ah = friedmann_advance<false>(a, 0.5 * tau, cosmo, nsub, bad, K, Dr);
-        s.a1 = friedmann_advance<false>(s.ah, 0.5 * tau, cosmo, nsub, bad, K, Dr);
+        if (canonical) {
+            s.ah = friedmann_advance<true>(a, 0.5 * tau, cosmo, nsub, bad, K1, D);
+            s.a1 = friedmann_advance<true>(s.ah, 0.5 * tau, cosmo, nsub, bad, K2, D);
+        } else {
+            s.ah = friedmann_advance<false>(a, 0.5 * tau, cosmo, nsub, bad, K1, D);
+            s.a1 = friedmann_advance<false>(s.ah, 0.5 * tau, cosmo, nsub, bad, K2, D);
+        }
         kick_coef(s.ah, hubble_of(s.ah, cosmo, bad), tau, G, s.c, s.d);
-        kick_coef(s.a0, hubble_of(s.a0, cosmo, bad), 0.5 * tau, G, s.c1, s.d1);
-        kick_coef(s.a1, hubble_of(s.a1, cosmo, bad), 0.5 * tau, G, s.c2, s.d2);
+        if (canonical) {
+            const double Dt = D / tau;
+            s.c1 = Dt * (s.a0 * s.a0);
+            s.d1 = G * Dt * K1;
+            s.c2 = tau / (D * (s.a1 * s.a1));
+            s.d2 = G * K2 / (s.a1 * s.a1);
+        } else {
+            kick_coef(s.a0, hubble_of(s.a0, cosmo, bad), 0.5 * tau, G, s.c1, s.d1);
+            kick_coef(s.a1, hubble_of(s.a1, cosmo, bad), 0.5 * tau, G, s.c2, s.d2);
+        }
         t = t + tau;
         s.t1 = t;
         s.step = step0 + j;
@@ -245,28 +262,37 @@ __global__ void ens_forces_out_kernel(const float4 *__restrict__ part, EnsLaunch
 __global__ void ens_open_kernel(const float4 *__restrict__ xs, const float4 *__restrict__ vs,
                                 const float4 *__restrict__ acc, float4 *__restrict__ vh,
                                 float *__restrict__ pk_out, const StepCoef *__restrict__ table,
-                                double tau, EnsLaunch E, int itile, long long Npad) {
+                                double tau, EnsLaunch E, int itile, long long Npad, int dkd) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= Npad) return;
     if (!ens_real(E, itile, i)) {
         pk_store(pk_out, i, kEnsFar, kEnsFar, kEnsFar, 0.f);
         return;
     }
+    const float4 x = xs[i], v = vs[i];
+    if (dkd) {   // DKD opening: the half drift, no force
+        const float h = (float)(0.5 * tau);
+        pk_store(pk_out, i, drift1(x.x, h, v.x), drift1(x.y, h, v.y), drift1(x.z, h, v.z), x.w);
+        return;
+    }
     const float c1 = (float)table[0].c1, d1 = (float)table[0].d1, t = (float)tau;
-    const float4 x = xs[i], v = vs[i], F = acc[i];
+    const float4 F = acc[i];
     const float hx = kick2(c1, v.x, d1, F.x), hy = kick2(c1, v.y, d1, F.y), hz = kick2(c1, v.z, d1, F.z);
     vh[i] = make_float4(hx, hy, hz, 0.f);
     pk_store(pk_out, i, drift1(x.x, t, hx), drift1(x.y, t, hy), drift1(x.z, t, hz), x.w);
 }
 
-// KDK step j of a chunk after the force at x^{n+1} (pk_in): close the step,
-// open the next one (same coefficients, both at t^{n+1}).
+// KDK step j of a chunk after the force at x^{n+1} (pk_in): close the step
+// with (c2, d2), open the next one with (c1, d1) of entry j + 1 when
+// `next_entry` (the canonical scheme; the chunk's schedule then holds one
+// entry more) or else (c2, d2) again, which for the drag scheme are the same
+// numbers: both are the half kick at t^{n+1}.
 __global__ void ens_step_kernel(const float4 *__restrict__ part, EnsLaunch E, int itile,
                                 const float *__restrict__ pk_in, float4 *__restrict__ xs,
                                 float4 *__restrict__ vs, float4 *__restrict__ vh,
                                 float4 *__restrict__ acc, float *__restrict__ pk_out,
                                 const StepCoef *__restrict__ table, int j, double tau,
-                                long long Npad, int *flags, DevClock *clk, Tracers tr) {
+                                long long Npad, int *flags, DevClock *clk, Tracers tr, int next_entry) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= Npad) return;
     const StepCoef &sc = table[j];
@@ -276,6 +302,7 @@ __global__ void ens_step_kernel(const float4 *__restrict__ part, EnsLaunch E, in
         return;
     }
     const float c2 = (float)sc.c2, d2 = (float)sc.d2, t = (float)tau;
+    const float c1n = next_entry ? (float)table[j + 1].c1 : c2, d1n = next_entry ? (float)table[j + 1].d1 : d2;
     const float3 F = ens_reduce(part, E, itile, i);
     const float4 x = pk_load(pk_in, i);
     const float4 h = vh[i];
@@ -284,10 +311,40 @@ __global__ void ens_step_kernel(const float4 *__restrict__ part, EnsLaunch E, in
     xs[i] = x;
     vs[i] = make_float4(vx, vy, vz, 0.f);
     record(tr, i, sc.step, x.x, x.y, x.z, vx, vy, vz);   // tr.slot is indexed by padded body
-    const float nx = kick2(c2, vx, d2, F.x), ny = kick2(c2, vy, d2, F.y), nz = kick2(c2, vz, d2, F.z);
+    const float nx = kick2(c1n, vx, d1n, F.x), ny = kick2(c1n, vy, d1n, F.y), nz = kick2(c1n, vz, d1n, F.z);
     vh[i] = make_float4(nx, ny, nz, 0.f);
     pk_store(pk_out, i, drift1(x.x, t, nx), drift1(x.y, t, ny), drift1(x.z, t, nz), x.w);
     if (!finite3(x.x, x.y, x.z) || !finite3(vx, vy, vz)) atomicOr(&flags[FLAG_NONFINITE], 1);
+}
+
+// DKD step j of a chunk (Eqs. 3-5; c, d at t^{n+1/2}) after the force at
+// the half-drift positions x^{n+1/2} (pk_in): kick, second half drift,
+// record, and the next step's half drift into pk_out.
+__global__ void ens_dkd_step_kernel(const float4 *__restrict__ part, EnsLaunch E, int itile,
+                                    const float *__restrict__ pk_in, float4 *__restrict__ xs,
+                                    float4 *__restrict__ vs, float4 *__restrict__ acc,
+                                    float *__restrict__ pk_out, const StepCoef *__restrict__ table, int j,
+                                    double tau, long long Npad, int *flags, DevClock *clk, Tracers tr) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= Npad) return;
+    const StepCoef &sc = table[j];
+    if (i == 0) advance_clock(clk, sc, flags);
+    if (!ens_real(E, itile, i)) {
+        pk_store(pk_out, i, kEnsFar, kEnsFar, kEnsFar, 0.f);
+        return;
+    }
+    const float c = (float)sc.c, d = (float)sc.d, h = (float)(0.5 * tau);
+    const float3 F = ens_reduce(part, E, itile, i);
+    const float4 xh = pk_load(pk_in, i);
+    const float4 v0 = vs[i];
+    const float vx = kick2(c, v0.x, d, F.x), vy = kick2(c, v0.y, d, F.y), vz = kick2(c, v0.z, d, F.z);
+    const float x1 = drift1(xh.x, h, vx), y1 = drift1(xh.y, h, vy), z1 = drift1(xh.z, h, vz);
+    acc[i] = make_float4(F.x, F.y, F.z, 0.f);
+    xs[i] = make_float4(x1, y1, z1, xh.w);
+    vs[i] = make_float4(vx, vy, vz, 0.f);
+    record(tr, i, sc.step, x1, y1, z1, vx, vy, vz);
+    pk_store(pk_out, i, drift1(x1, h, vx), drift1(y1, h, vy), drift1(z1, h, vz), xh.w);
+    if (!finite3(x1, y1, z1) || !finite3(vx, vy, vz)) atomicOr(&flags[FLAG_NONFINITE], 1);
 }
 
 }  // namespace colatus

@@ -72,6 +72,7 @@ struct colatus_ensemble {
     std::vector<int> n_jt, tile_r;
     EnsLaunch E{};
     int shape = kEnsDefault;               // CTA shape of the force kernel (ens_variant)
+    colatus_scheme scheme = COLATUS_KDK;   // colatus_ensemble_set_scheme
     int shape_G[kEnsShapes] = {0}, shape_S[kEnsShapes] = {0};   // grid and S_max per shape
     void *meta = nullptr;                  // device descriptor arrays
     long long *d_user_off = nullptr;
@@ -234,15 +235,24 @@ colatus_status ens_force_at_state(colatus_ens_t e) {
 
 // n <= kEnsChunk steps: their schedule, then force + epilogue per step.
 colatus_status ens_steps(colatus_ens_t e, double tau, int n) {
-    ens_table_kernel<<<1, 1, 0, e->stream>>>(e->cosmo, e->clk, e->table, n, tau, e->G, kFriedmannSub);
+    const int canon = e->scheme == COLATUS_KDK_CANONICAL ? 1 : 0;
+    // the canonical closing kick needs the next step's opening coefficients
+    ens_table_kernel<<<1, 1, 0, e->stream>>>(e->cosmo, e->clk, e->table, n + canon, tau, e->G,
+                                             kFriedmannSub, canon);
     colatus_status st = elaunched(e);
     if (st != COLATUS_OK) return st;
+    const Tracers tr{e->tslot, e->rec, e->rec_cap, e->rec_base, e->ntr};
     for (int j = 0; j < n; ++j) {
         const int c = e->cur, nx = c ^ 1;
         if ((st = ens_force(e, e->pk[c])) != COLATUS_OK) return st;
-        ens_step_kernel<<<ens_blocks(e), 256, 0, e->stream>>>(
-            e->part, e->E, kEnsTile, e->pk[c], e->xs, e->vs, e->vh, e->acc, e->pk[nx], e->table, j, tau,
-            e->Npad, e->flags, e->clk, Tracers{e->tslot, e->rec, e->rec_cap, e->rec_base, e->ntr});
+        if (e->scheme == COLATUS_DKD)
+            ens_dkd_step_kernel<<<ens_blocks(e), 256, 0, e->stream>>>(
+                e->part, e->E, kEnsTile, e->pk[c], e->xs, e->vs, e->acc, e->pk[nx], e->table, j, tau,
+                e->Npad, e->flags, e->clk, tr);
+        else
+            ens_step_kernel<<<ens_blocks(e), 256, 0, e->stream>>>(
+                e->part, e->E, kEnsTile, e->pk[c], e->xs, e->vs, e->vh, e->acc, e->pk[nx], e->table, j, tau,
+                e->Npad, e->flags, e->clk, tr, canon);
         if ((st = elaunched(e)) != COLATUS_OK) return st;
         e->cur = nx;
     }
@@ -414,7 +424,7 @@ colatus_status colatus_ensemble_init(colatus_ens_t *out, int R, const int64_t *N
               A((void **)&e->pk[2], np * 16) &&
               A((void **)&e->part, (size_t)T * smax * kEnsTile * sizeof(float4)) &&
               A((void **)&e->flags, NUM_FLAGS * sizeof(int)) && A((void **)&e->clk, sizeof(DevClock)) &&
-              A((void **)&e->table, kEnsChunk * sizeof(StepCoef)) &&
+              A((void **)&e->table, (kEnsChunk + 1) * sizeof(StepCoef)) &&
               A((void **)&e->stage, (size_t)e->Ntot * 3 * sizeof(double)) &&
               A((void **)&e->stage2, (size_t)e->Ntot * 3 * sizeof(double));
     if (!ok) return bail(efail(e, COLATUS_E_OOM, "device allocation failed"));
@@ -553,11 +563,15 @@ colatus_status colatus_ensemble_step(colatus_ens_t e, double dt, int64_t nsteps)
     if (!e->have_state) return efail(e, COLATUS_E_STATE, "no state has been set");
     if (nsteps == 0) return COLATUS_OK;
     if (!e->spec_valid || e->spec_tau != dt) {
-        TRY(ens_force_at_state(e));
-        ens_table_kernel<<<1, 1, 0, e->stream>>>(e->cosmo, e->clk, e->table, 1, dt, e->G, kFriedmannSub);
+        // the opening: KDK's half kick (force at the state) and drift, or DKD's half drift
+        const bool dkd = e->scheme == COLATUS_DKD;
+        if (!dkd) TRY(ens_force_at_state(e));
+        ens_table_kernel<<<1, 1, 0, e->stream>>>(e->cosmo, e->clk, e->table, 1, dt, e->G, kFriedmannSub,
+                                                 e->scheme == COLATUS_KDK_CANONICAL ? 1 : 0);
         TRY(elaunched(e));
         ens_open_kernel<<<ens_blocks(e), 256, 0, e->stream>>>(e->xs, e->vs, e->acc, e->vh, e->pk[e->cur],
-                                                             e->table, dt, e->E, kEnsTile, e->Npad);
+                                                             e->table, dt, e->E, kEnsTile, e->Npad,
+                                                             dkd ? 1 : 0);
         TRY(elaunched(e));
         e->spec_valid = true;
         e->spec_tau = dt;
@@ -579,6 +593,24 @@ colatus_status colatus_ensemble_synchronize(colatus_ens_t e) {
     if (!e) return COLATUS_E_ARG;
     DeviceGuard dg(e->device);
     return ens_check(e, true);
+}
+
+colatus_status colatus_ensemble_set_scheme(colatus_ens_t e, colatus_scheme scheme) {
+    if (!e) return COLATUS_E_ARG;
+    DeviceGuard dg(e->device);
+    if (scheme != COLATUS_DKD && scheme != COLATUS_KDK && scheme != COLATUS_KDK_CANONICAL)
+        return efail(e, COLATUS_E_ARG, "bad scheme %d", (int)scheme);
+    if (scheme == e->scheme) return COLATUS_OK;
+    ECU(cudaStreamSynchronize(e->stream));
+    // the captured graphs hold the other scheme's kernels; the next step re-opens
+    for (cudaGraphExec_t &g : e->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    e->scheme = scheme;
+    e->spec_valid = false;
+    return COLATUS_OK;
 }
 
 colatus_status colatus_ensemble_record_tracers(colatus_ens_t e, const int64_t *idx, int ntr,

@@ -241,3 +241,74 @@ def test_tracer_ring_and_rerecording_with_graphs():
             ens.record_tracers([2000], 5)
     finally:
         ens.close()
+
+
+@pytest.mark.parametrize("scheme", ["dkd", "canonical"])
+def test_schemes_match_oracle_per_realisation(scheme):
+    # the paper's DKD (force at the half-drift positions) and the canonical
+    # KDK of Sec. II through the same graph replay and direct steps
+    ics = critical_ensemble([512, 1000, 1729])
+    x, v, m, eps, Ns = concat(ics)
+    n = 20
+    ens = B.Ensemble(Ns, m, eps, LCDM_D, inputs.A_START,
+                     scheme=B.DKD if scheme == "dkd" else B.KDK_CANONICAL)
+    try:
+        ens.set_state(x, v)
+        ens.step(TAU, 16)
+        ens.step(TAU, 4)
+        gx, gv, t, a = ens.state()
+    finally:
+        ens.close()
+    off = np.concatenate([[0], np.cumsum(Ns)])
+    rng = np.random.default_rng(2)
+    rms = lambda d: float(np.sqrt(np.mean(np.sum(d ** 2, axis=1))))
+    for r, ic in enumerate(ics):
+        ref = oracle.run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n, scheme)
+        # the oracle's own response to rounding-sized input changes (three
+        # samples): a close pair (two bodies of the 1729-body DKD run) can
+        # amplify it a hundredfold past the other bodies'
+        chaos_x = chaos_v = 0.0
+        for _ in range(3):
+            xp = ic.x * (1.0 + 6e-8 * rng.standard_normal(ic.x.shape))
+            pert = oracle.run(xp, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n, scheme)
+            chaos_x = max(chaos_x, np.abs(pert["x"] - ref["x"]).max())
+            chaos_v = max(chaos_v, rms(pert["v"] - ref["v"]))
+        err = np.abs(gx[off[r]:off[r + 1]] - ref["x"]).max(axis=1)
+        assert np.mean(err < 1e-5) > 0.99, r                  # all but the encounters
+        assert err.max() < max(1e-5, 10.0 * chaos_x), r
+        tol_v = max(1e-5 * rms(ref["v"]), 10.0 * chaos_v)
+        assert rms(gv[off[r]:off[r + 1]] - ref["v"]) < tol_v, r
+        assert a == pytest.approx(ref["schedule"]["a"][-1], rel=1e-13)
+
+
+def test_scheme_change_between_calls():
+    # 16 KDK steps, then 16 DKD steps, against the oracle's two legs; the
+    # change drops the KDK graph and re-opens from the state
+    ics = critical_ensemble([700, 1300])
+    x, v, m, eps, Ns = concat(ics)
+    ens = B.Ensemble(Ns, m, eps, LCDM_D, inputs.A_START)
+    try:
+        ens.set_state(x, v)
+        ens.step(TAU, 16)
+        a16 = ens.state()[3]
+        ens.set_scheme(B.DKD)
+        ens.step(TAU, 16)
+        gx, gv, _, _ = ens.state()
+        with pytest.raises(B.ColatusError):
+            ens.set_scheme(7)
+    finally:
+        ens.close()
+    off = np.concatenate([[0], np.cumsum(Ns)])
+    rng = np.random.default_rng(3)
+
+    def two_legs(x0, ic):
+        r1 = oracle.run(x0, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, 16, "kdk")
+        return r1, oracle.run(r1["x"], r1["v"], ic.m, ic.eps, 1.0, LCDM, r1["schedule"]["a"][-1], TAU, 16,
+                              "dkd")
+
+    for r, ic in enumerate(ics):
+        r1, r2 = two_legs(ic.x, ic)
+        assert r1["schedule"]["a"][-1] == pytest.approx(a16, rel=1e-13)
+        _, p2 = two_legs(ic.x * (1.0 + 6e-8 * rng.standard_normal(ic.x.shape)), ic)
+        chaos = np.abs(p2["x"] - r2["x"]).max()
+        assert np.abs(gx[off[r]:off[r + 1]] - r2["x"]).max() < max(1e-5, 10.0 * chaos), r
