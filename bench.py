@@ -646,7 +646,9 @@ def run_colatus(args, ws, rank, local):
                                  f"launched kernel has the captured shape: {same_shape}; sources "
                                  f"unchanged since the capture: {same_source}; algorithmic HBM "
                                  "bytes: 524288 (positions read once)"),
-                "kernel": "force_f32_kernel (FP32 compensated, stream-K)",
+                "kernel": ("force_sym_f32_kernel (FP32 compensated, every pair once, stream-K over "
+                           "the tile pairs)" if plan.get("kind") == "force_sym_f32"
+                           else "force_f32_kernel (FP32 compensated, stream-K)"),
                 "launched_plan": plan,
                 "interactions_per_s": achieved_int,
                 "int_per_sm_per_clk": achieved_int / (nsm * f_mhz * 1e6),

@@ -264,12 +264,13 @@ colatus_status colatus_stats(colatus_t ctx, double out[4]);
  * current precision, masses, boundaries and tuning, for measurement (the
  * Eq. 1 sum of the paper's Appendix A kernel; this names its launch shape):
  * out[0] kind (0 FP32 all-pairs, 1 FP64 all-pairs, 2 FP32 periodic real
- * space, 3 FP64 periodic real space), out[1] threads per CTA, out[2]
- * i-bodies per thread, out[3] j-tile bodies, out[4] compensated accumulation
- * (0/1), out[5] equal-mass form (0/1), out[6] persistent grid (CTAs),
- * out[7] work units (i-tile x j-tile), out[8] i-bodies per thread whose
- * 1/s^2 is an rcp on the MUFU pipe rather than a square of the rsqrt on the
- * FMA pipe.  Errors: COLATUS_E_ARG. */
+ * space, 3 FP64 periodic real space, 4 FP32 all-pairs with every pair
+ * evaluated once), out[1] threads per CTA, out[2] i-bodies per thread,
+ * out[3] j-tile bodies, out[4] compensated accumulation (0/1), out[5]
+ * equal-mass form (0/1), out[6] persistent grid (CTAs), out[7] work units
+ * (i-tile x j-tile; for kind 4 the tile pairs it <= jt), out[8] i-bodies per
+ * thread whose 1/s^2 is an rcp on the MUFU pipe rather than a square of the
+ * rsqrt on the FMA pipe.  Errors: COLATUS_E_ARG. */
 colatus_status colatus_force_plan(colatus_t ctx, int64_t out[9]);
 
 /* Kernel timing for measurement: with on != 0 every launch of the force
@@ -291,15 +292,21 @@ colatus_status colatus_profile_read(colatus_t ctx, double out[4]);
  * the totals. */
 colatus_status colatus_profile_read_kinds(colatus_t ctx, double out[6]);
 
-/* Force-kernel tuning.  The FP32 force kernel exists in three tile shapes
+/* Force-kernel tuning.  The FP32 force kernel exists in four tile shapes
  * (threads x i-bodies per thread, j-tile): 0 = 512 x 4, 512 bodies (one CTA
- * per SM); 1 = 256 x 4, 512 (two CTAs per SM); 2 = 128 x 2, 64 (small N).
- * colatus_autotune times reps launches of every shape that fits N on the
- * current state (for the context's FP32 precision and mass type), keeps the
- * fastest for this context and returns it in *chosen; out_ms[3] (may be NULL)
- * receives the mean milliseconds per launch (0 for shapes that do not fit).
- * colatus_set_tuning applies a known choice (-1: built-in choice). */
-colatus_status colatus_autotune(colatus_t ctx, int reps, double out_ms[3], int *chosen);
+ * per SM); 1 = 256 x 4, 512 (two CTAs per SM); 2 = 128 x 2, 64 (small N);
+ * 3 = 512 x 4 on 2048-body tiles with every pair evaluated once and applied
+ * to both bodies (Newton's third law: the same sum with about two thirds of
+ * the arithmetic).  Shape 3 fits from 2 tiles (N > 2048) while its partial
+ * sums, about N^2 / 2048 x 16 bytes (x 2 compensated), stay within 4 GiB
+ * (N up to about 2^19); it is the built-in choice from 8 tiles (N > 14336)
+ * on.  colatus_autotune times reps launches of every shape that fits N on
+ * the current state (for the context's FP32 precision and mass type), keeps
+ * the fastest for this context and returns it in *chosen; out_ms[4] (may be
+ * NULL) receives the mean milliseconds per launch (0 for shapes that do not
+ * fit).  colatus_set_tuning applies a known choice (-1: built-in choice);
+ * COLATUS_E_ARG for a shape that does not fit. */
+colatus_status colatus_autotune(colatus_t ctx, int reps, double out_ms[4], int *chosen);
 colatus_status colatus_set_tuning(colatus_t ctx, int shape);
 
 /* Vector-Jacobian product of the Eq. 1 acceleration at the current state:

@@ -495,7 +495,7 @@ class Simulation:
         """The force kernel launched for the current configuration (colatus_force_plan)."""
         out = np.zeros(9, dtype=np.int64)
         _check(lib().colatus_force_plan(self.h, out.ctypes.data), self.h)
-        kinds = ("force_f32", "force_f64", "ewald_f32", "ewald_f64")
+        kinds = ("force_f32", "force_f64", "ewald_f32", "ewald_f64", "force_sym_f32")
         return dict(kind=kinds[int(out[0])], threads=int(out[1]), ipt=int(out[2]), jt=int(out[3]),
                     comp=bool(out[4]), eqm=bool(out[5]), grid=int(out[6]), units=int(out[7]),
                     nrcp=int(out[8]))
@@ -528,8 +528,8 @@ class Simulation:
 
     def autotune(self, reps=3):
         """Time the FP32 force shapes on the current state; keep the fastest.
-        Returns (chosen shape, [ms per launch of shapes 0, 1, 2])."""
-        ms = np.zeros(3)
+        Returns (chosen shape, [ms per launch of shapes 0, 1, 2, 3])."""
+        ms = np.zeros(4)
         ch = ctypes.c_int()
         _check(lib().colatus_autotune(self.h, int(reps), ms.ctypes.data, ctypes.byref(ch)), self.h)
         return int(ch.value), ms.tolist()

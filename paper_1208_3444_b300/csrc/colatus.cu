@@ -15,6 +15,7 @@
 #include "ewald.cuh"
 #include "ewald_adjoint.cuh"
 #include "force.cuh"
+#include "force_sym.cuh"
 #include "integrate.cuh"
 #include "probe.cuh"
 #include "spectrum.cuh"
@@ -23,17 +24,26 @@
 using namespace colatus;
 
 // ------------------------------------------------------------------ kernels
-// FP32 force variants: three tile shapes, each plain or compensated (TwoSum
+// FP32 force variants: four tile shapes, each plain or compensated (TwoSum
 // fold), for general or equal masses.  Shapes (threads x i-bodies per
 // thread, j-tile): 0 = 512 x 4, 512 (one CTA per SM, 2048-body i-tiles) for
 // large N; 1 = 256 x 4, 512 (two CTAs per SM) for medium N; 2 = 128 x 2, 64
-// for small N.  Unroll depth and fold length per variant come from sweeps
-// on B300 (interactions per SM per clock).  colatus_autotune times the
-// shapes that fit N and keeps the fastest.
+// for small N; 3 = 512 x 4 on 2048-body tiles with every pair evaluated once
+// (force_sym.cuh: Newton's third law, 14 FP32 lane-ops per pair instead of
+// 2 x 11).  Unroll depth and fold length per variant come from sweeps on
+// B300 (interactions per SM per clock).  colatus_autotune times the shapes
+// that fit N and keeps the fastest.
 namespace {
 
 constexpr int kStages = 4;
-constexpr int kShapes = 3;
+constexpr int kShapes = 4;
+constexpr int kSymShape = 3;
+constexpr int kSymNT = 512, kSymIPT = 4, kSymUnr = 8;
+// The pair-once shape is the built-in choice from this many tiles up (fewer
+// tiles leave most CTAs less than one unit) and while its partial sums fit
+// kSymMaxBytes (they grow as N^2 / T: one column slot per tile pair).
+constexpr int kSymMinTiles = 8;
+constexpr size_t kSymMaxBytes = (size_t)4 << 30;
 
 struct F32Variant {
     int nt, ipt, jt;
@@ -43,6 +53,7 @@ struct F32Variant {
     const void *fn;
     void (*launch)(int grid, cudaStream_t, const float *, float4 *, int *, ForceLaunch, float,
                    float);
+    bool sym = false;   // each pair once (force_sym_f32_kernel)
 };
 
 template <int NT, int IPT, int JT, int FOLD, bool COMP, bool EQM, int MINB, int UNR, int NRCP>
@@ -59,6 +70,24 @@ F32Variant make_f32() {
     return F32Variant{NT, IPT, JT, COMP, EQM, NRCP, K::SMEM,
                       (const void *)force_f32_kernel<NT, IPT, JT, kStages, FOLD, COMP, EQM, MINB, UNR, NRCP>,
                       &launch_f32<NT, IPT, JT, FOLD, COMP, EQM, MINB, UNR, NRCP>};
+}
+
+template <bool COMP, bool EQM>
+void launch_sym(int grid, cudaStream_t st, const float *pk, float4 *part, int *flags, ForceLaunch L,
+                float eps2, float mass_eq) {
+    using K = SymKernel<kSymNT, kSymIPT, COMP>;
+    force_sym_f32_kernel<kSymNT, kSymIPT, COMP, EQM, kSymUnr><<<grid, kSymNT, K::SMEM, st>>>(
+        pk, part, flags, L, eps2, mass_eq);
+}
+
+template <bool COMP, bool EQM>
+F32Variant make_sym() {
+    using K = SymKernel<kSymNT, kSymIPT, COMP>;
+    F32Variant v{kSymNT, kSymIPT, K::T, COMP, EQM, 0, K::SMEM,
+                 (const void *)force_sym_f32_kernel<kSymNT, kSymIPT, COMP, EQM, kSymUnr>,
+                 &launch_sym<COMP, EQM>};
+    v.sym = true;
+    return v;
 }
 
 // index = 4 * shape + 2 * comp + eqm.  An optional last argument (NRCP)
@@ -83,6 +112,10 @@ const F32Variant &f32_variant(int v) {
         make_f32<128, 2, 64, 32, false, true, 4, 2>(),
         make_f32<128, 2, 64, 32, true, false, 4, 2>(),
         make_f32<128, 2, 64, 32, true, true, 4, 2>(),
+        make_sym<false, false>(),
+        make_sym<false, true>(),
+        make_sym<true, false>(),
+        make_sym<true, true>(),
     };
     return table[v];
 }
@@ -172,6 +205,7 @@ struct ForcePlan {
     int itile = 0, jt = 0;
     ForceLaunch L{};
     size_t part_bytes = 0;
+    bool fits = true;       // usable for this N (colatus_set_tuning, colatus_autotune)
 };
 
 // Launch geometry of a plan (n_pad, itile, jt set) on all SMs but one;
@@ -229,6 +263,7 @@ struct colatus_ctx {
     void *part = nullptr;
     size_t part_bytes = 0;
     int *flags = nullptr;
+    int *sym_tab = nullptr;        // tables of the pair-once force plans (force_sym.cuh)
     int *mstat = nullptr;          // [min, max] float bits of the masses
     DevClock *clk = nullptr;       // state clock (t, a, steps)
     DevClock *tclk = nullptr;      // schedule frontier
@@ -391,6 +426,7 @@ colatus_status launched(colatus_t ctx) {
 
 // ---- plans
 colatus_status build_plans(colatus_t ctx) {
+    SymTables st;
     for (int v = 0; v < NUM_F32_VARIANTS; ++v) {
         const F32Variant &fv = f32_variant(v);
         if (fv.smem > 48 * 1024)
@@ -403,7 +439,31 @@ colatus_status build_plans(colatus_t ctx) {
         p.itile = fv.nt * fv.ipt;
         p.jt = fv.jt;
         p.n_pad = round_up(ctx->N, std::max(p.itile, p.jt));
-        finish_plan(p, occ, ctx->num_sms, sizeof(float4) * (fv.comp ? 2 : 1));
+        if (!fv.sym) {
+            finish_plan(p, occ, ctx->num_sms, sizeof(float4) * (fv.comp ? 2 : 1));
+            p.fits = p.L.W >= p.L.G;
+            continue;
+        }
+        // pair-once plan: one set of tables for all four variants, the phase
+        // costs of the equal-mass form (11 lane-ops per diagonal interaction,
+        // 14 per symmetric pair), on all SMs but the schedule kernel's
+        if (st.tab.empty())
+            st = build_sym_tables(p.n_pad, p.itile, kSymNT / 32, (long long)occ * std::max(1, ctx->num_sms - 1),
+                                  11, 14);
+        const int pl = fv.comp ? 2 : 1;
+        p.L = ForceLaunch{};
+        p.L.W = st.U;
+        p.L.n_it = p.L.n_jt = st.n;
+        p.L.G = st.G;
+        p.L.S_max = st.S_row;
+        p.L.col_off = (long long)st.n * st.S_row * pl * p.itile;
+        p.part_bytes = (size_t)((long long)st.n * st.S_row + st.slots) * pl * p.itile * sizeof(float4);
+        p.fits = st.n >= 2 && p.part_bytes <= kSymMaxBytes;
+    }
+    if (!st.tab.empty()) {
+        CU(cudaMalloc(&ctx->sym_tab, st.tab.size() * sizeof(int)));
+        CU(cudaMemcpy(ctx->sym_tab, st.tab.data(), st.tab.size() * sizeof(int), cudaMemcpyHostToDevice));
+        for (int v = 4 * kSymShape; v < 4 * kSymShape + 4; ++v) ctx->plan32[v].L.sym = ctx->sym_tab;
     }
     int occ = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -481,11 +541,13 @@ colatus_status build_plans(colatus_t ctx) {
 // Built-in shape choice: the largest shape that still gives every CTA at
 // least four units; colatus_autotune / colatus_set_tuning override it.
 int default_shape(colatus_t ctx, int comp) {
-    for (int sh = 0; sh < kShapes - 1; ++sh) {
+    const ForcePlan &ps = ctx->plan32[4 * kSymShape + comp];
+    if (ps.fits && ps.L.n_it >= kSymMinTiles) return kSymShape;
+    for (int sh = 0; sh < 2; ++sh) {
         const ForcePlan &p = ctx->plan32[4 * sh + comp];
         if (p.L.W >= 4LL * p.L.G) return sh;
     }
-    return kShapes - 1;
+    return 2;
 }
 
 const ForcePlan &plan_f32(colatus_t ctx) {
@@ -926,7 +988,7 @@ colatus_status check_dtype(colatus_t ctx, int dtype) {
 void free_all(colatus_t ctx) {
     void *ptrs[] = {ctx->xs, ctx->vs, ctx->vh, ctx->acc, ctx->pk[0], ctx->pk[1], ctx->pk[2],
                     ctx->xs64, ctx->vs64, ctx->vh64, ctx->acc64, ctx->pos64[0], ctx->pos64[1],
-                    ctx->pos64[2], ctx->m64, ctx->part, ctx->flags, ctx->mstat, ctx->clk,
+                    ctx->pos64[2], ctx->m64, ctx->part, ctx->flags, ctx->sym_tab, ctx->mstat, ctx->clk,
                     ctx->tclk, ctx->table, ctx->stage, ctx->stage2, ctx->diag, ctx->tslot,
                     ctx->rec, ctx->kw, ctx->rho, ctx->rho_part, ctx->wcs, ctx->pen,
                     ctx->rchunk, ctx->fchunk, ctx->lr, ctx->ph, ctx->pot_part, ctx->lrv,
@@ -2534,13 +2596,13 @@ colatus_status colatus_set_tuning(colatus_t ctx, int shape) {
     if (shape < -1 || shape >= kShapes) return fail(ctx, COLATUS_E_ARG, "shape must be -1 .. %d", kShapes - 1);
     if (shape >= 0) {
         const ForcePlan &p = ctx->plan32[4 * shape];
-        if (p.L.W < p.L.G) return fail(ctx, COLATUS_E_ARG, "shape %d does not fit N", shape);
+        if (!p.fits) return fail(ctx, COLATUS_E_ARG, "shape %d does not fit N", shape);
     }
     ctx->tuned_shape = shape;
     return COLATUS_OK;
 }
 
-colatus_status colatus_autotune(colatus_t ctx, int reps, double out_ms[3], int *chosen) {
+colatus_status colatus_autotune(colatus_t ctx, int reps, double out_ms[4], int *chosen) {
     if (!ctx) return COLATUS_E_ARG;
     DeviceGuard dg(ctx->device);
     if (ctx->periodic) return fail(ctx, COLATUS_E_STATE, "%s is not built for periodic boundaries", "autotuning");
@@ -2555,7 +2617,7 @@ colatus_status colatus_autotune(colatus_t ctx, int reps, double out_ms[3], int *
     int best_sh = -1;
     for (int sh = 0; sh < kShapes; ++sh) {
         if (out_ms) out_ms[sh] = 0.0;
-        if (ctx->plan32[4 * sh].L.W < ctx->plan32[4 * sh].L.G) continue;   // does not fit
+        if (!ctx->plan32[4 * sh].fits) continue;   // does not fit
         ctx->tuned_shape = sh;
         TRY(force_at_state(ctx));                   // warm-up launch
         ctx->profiling = true;
@@ -2714,6 +2776,7 @@ colatus_status colatus_force_plan(colatus_t ctx, int64_t out[9]) {
     const bool f64 = ctx->prec == COLATUS_FP64;
     const ForcePlan &p = f64 ? plan_f64(ctx) : plan_f32(ctx);
     out[0] = (ctx->periodic ? 2 : 0) + (f64 ? 1 : 0);
+    if (!f64 && !ctx->periodic && f32_variant(p.variant).sym) out[0] = 4;
     if (f64) {
         out[1] = ctx->periodic ? kEw64NT : kF64NT;
         out[2] = ctx->periodic ? 1 : kF64IPT;

@@ -59,6 +59,11 @@ struct ForceLaunch {
     int n_jt;       // j-tiles
     int S_max;      // max segments any i-tile has
     int G;          // CTAs
+    // symmetric plans (force_sym.cuh) only, else null / 0: the plan's tables
+    // (device ints) and the float4 offset of the column slots in the
+    // segment buffer
+    const int *sym;
+    long long col_off;
 };
 
 // ---------------------------------------------------------------- FP32 kernel

@@ -6,6 +6,7 @@
 
 #include "common.cuh"
 #include "force.cuh"
+#include "force_sym.cuh"
 
 namespace colatus {
 
@@ -178,6 +179,7 @@ __global__ void pack_f64_kernel(const double4 *__restrict__ xs, double4 *__restr
 template <bool COMP>
 __device__ __forceinline__ float3 reduce_f32(const float4 *__restrict__ part, const ForceLaunch &L,
                                              int itile, long long i) {
+    if (L.sym) return reduce_sym_f32<COMP>(part, L, itile, i);   // each pair evaluated once
     const long long it = i / itile, il = i - it * itile;
     const long long G = L.G, W = L.W;
     const long long g0 = sk_owner(it * L.n_jt, W, G);

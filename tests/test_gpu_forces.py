@@ -120,7 +120,7 @@ def test_deterministic_repeat():
     assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3])
 @pytest.mark.parametrize("prec", [B.FP32, B.FP32_COMP])
 @pytest.mark.parametrize("workload", ["grid32", "plummer"])
 def test_every_tile_shape(shape, prec, workload):
@@ -143,7 +143,7 @@ def test_autotune_and_cache(tmp_path):
     try:
         sim.set_state(ic.x)
         shape, ms = sim.autotune(2)
-        assert shape in (0, 1, 2) and ms[shape] == min(m for m in ms if m > 0)
+        assert shape in (0, 1, 2, 3) and len(ms) == 4 and ms[shape] == min(m for m in ms if m > 0)
         got = sim.forces()
         path = str(tmp_path / "tune.json")
         rec = tuning.tuned(sim, path, ic.m, "gpu")
@@ -158,16 +158,22 @@ def test_autotune_and_cache(tmp_path):
 
 
 def test_force_plan_names_the_launched_kernel():
-    # the 32^3 equal-mass bodies take shape 0 (512 x 4, 512-body j-tiles) with
-    # the equal-mass form, every 1/s^2 from the rsqrt
+    # the 32^3 equal-mass bodies take shape 3 (every pair once, 512 x 4 on
+    # 2048-body tiles, the 136 tile pairs it <= jt) with the equal-mass form;
+    # shape 0 (512 x 4, 512-body j-tiles, every 1/s^2 from the rsqrt) on request
     ic = inputs.grid32()
-    for prec, comp, nrcp in ((B.FP32, False, 0), (B.FP32_COMP, True, 0)):
+    for prec, comp in ((B.FP32, False), (B.FP32_COMP, True)):
         sim = B.Simulation(ic.m, ic.eps, LCDM, 1.0, prec=prec)
         try:
             sim.set_state(ic.x)
             p = sim.force_plan()
+            sim.set_tuning(0)
+            p0 = sim.force_plan()
         finally:
             sim.close()
-        assert p["kind"] == "force_f32" and p["comp"] == comp and p["eqm"]
-        assert (p["threads"], p["ipt"], p["jt"], p["nrcp"]) == (512, 4, 512, nrcp)
-        assert p["units"] == (ic.N // 2048) * (ic.N // 512)
+        assert p["kind"] == "force_sym_f32" and p["comp"] == comp and p["eqm"]
+        assert (p["threads"], p["ipt"], p["jt"], p["nrcp"]) == (512, 4, 2048, 0)
+        assert p["units"] == 16 * 17 // 2
+        assert p0["kind"] == "force_f32" and p0["comp"] == comp and p0["eqm"]
+        assert (p0["threads"], p0["ipt"], p0["jt"], p0["nrcp"]) == (512, 4, 512, 0)
+        assert p0["units"] == (ic.N // 2048) * (ic.N // 512)
