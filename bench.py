@@ -283,6 +283,7 @@ def time_adjoint(B, inputs, torch, stream, nsteps=200, k=20):
                        stream=stream.cuda_stream)
     try:
         sim.set_state(ic.x, ic.v)
+        vplan = sim.vjp_plan()
         gv = np.zeros((ic.N, 3))
         gv[inputs.tracers(ic.N, 64, 7)] = 1.0
         # warm-up pass of the same shape: loads the adjoint kernels (lazy
@@ -313,7 +314,17 @@ def time_adjoint(B, inputs, torch, stream, nsteps=200, k=20):
     # the adjoint step: one VJP and one transposed update per step (plus the
     # final VJP at x_0), each bracketed by events on the launching stream
     adj = (bwd["vjp"][0] + bwd["adjoint_update"][0]) / nsteps
-    return {"N": ic.N, "steps": nsteps, "checkpoint_every": k, "prec": "fp32_comp",
+    # FP32 lane-ops per interaction of the VJP kernel the adjoint ran: the
+    # pair-once form takes 27 per pair in the tile pairs it < jt and 23 per
+    # ordered pair in the diagonal tiles; the per-ordered-pair equal-mass form
+    # 23, the general (scaled) form 25
+    if vplan["kind"] == "vjp_sym_eqm_f32":
+        t, nt = vplan["jt"], ic.N // vplan["jt"]
+        ops = ((nt * (nt + 1) // 2 - nt) * 27 + nt * 23) * float(t * t) / (float(ic.N) * ic.N)
+    else:
+        ops = 23.0 if vplan["kind"] == "vjp_eqm_f32" else 25.0
+    vrate = ic.N * ic.N / (vjp * 1e-3) / (torch.cuda.get_device_properties(0).multi_processor_count * 2.032e9)
+    return {"N": ic.N, "steps": nsteps, "checkpoint_every": k, "prec": "fp32_comp", "vjp_plan": vplan,
             "forward_ms_per_step": f, "backward_ms_per_step": b,
             "recompute_ms_per_step": rec, "vjp_ms_per_launch": vjp,
             "update_ms_per_launch": bwd["adjoint_update"][0] / max(1, bwd["adjoint_update"][1]),
@@ -322,12 +333,11 @@ def time_adjoint(B, inputs, torch, stream, nsteps=200, k=20):
             "adjoint_step_over_forward_step": adj / f,
             "backward_minus_recompute_forces_over_forward": (b - rec) / f,
             "backward_total_over_forward": b / f,
-            "vjp_interactions_per_sm_per_clk": ic.N * ic.N / (vjp * 1e-3) /
-            (torch.cuda.get_device_properties(0).multi_processor_count * 2.032e9),
-            "vjp_frac_of_lane_op_floor": ic.N * ic.N / (vjp * 1e-3) /
-            (torch.cuda.get_device_properties(0).multi_processor_count * 2.032e9) / (128.0 / 23.0),
-            "vjp_floor_note": "23 FP32 lane-ops per interaction (the equal-mass form the 32^3 adjoint "
-                              "takes; the general scaled form is 25) at 128 lane-ops/SM/clk"}
+            "vjp_interactions_per_sm_per_clk": vrate,
+            "vjp_lane_ops_per_interaction": ops,
+            "vjp_frac_of_lane_op_floor": vrate / (128.0 / ops),
+            "vjp_floor_note": "FP32 lane-ops per interaction of the launched VJP kernel (vjp_plan) at "
+                              "128 lane-ops/SM/clk"}
 
 
 def time_ensemble(B, inputs, torch, stream, nsteps=48):

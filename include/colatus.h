@@ -273,6 +273,19 @@ colatus_status colatus_stats(colatus_t ctx, double out[4]);
  * rsqrt on the FMA pipe.  Errors: COLATUS_E_ARG. */
 colatus_status colatus_force_plan(colatus_t ctx, int64_t out[9]);
 
+/* The VJP kernel that colatus_adjoint_backward launches for the current
+ * precision, masses, boundaries, deformation term and scheme, for
+ * measurement (the VJP of the Eq. 1 sum, see colatus_force_vjp; the
+ * equal-mass forms need equal masses, isolated boundaries, no Eq. 6 term, a
+ * KDK scheme and N a multiple of 1024; colatus_force_vjp itself always takes
+ * the general form): out[0] kind (0 FP32 general, 1 FP64, 2 FP32 periodic
+ * real space, 3 FP64 periodic real space, 4 FP32 equal-mass, 5 FP32
+ * equal-mass with every pair evaluated once, from 8 tiles of 1024 bodies),
+ * out[1] threads per CTA, out[2] i-bodies per thread, out[3] j-tile bodies,
+ * out[4] persistent grid (CTAs), out[5] work units (i-tile x j-tile; for
+ * kind 5 the tile pairs it <= jt).  Errors: COLATUS_E_ARG. */
+colatus_status colatus_vjp_plan(colatus_t ctx, int64_t out[6]);
+
 /* Kernel timing for measurement: with on != 0 every launch of the force
  * kernel, the VJP kernel and the adjoint's per-step update kernel is
  * bracketed by a pair of CUDA events recorded on the context's stream

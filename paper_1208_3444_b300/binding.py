@@ -42,7 +42,8 @@ EXPORTS = ("colatus_init", "colatus_set_config", "colatus_set_masses", "colatus_
            "colatus_set_deformation", "colatus_velocity_spectrum", "colatus_tracer_spectrum",
            "colatus_set_periodic", "colatus_periodic_params", "colatus_get_state_async",
            "colatus_wait_state", "colatus_selftest_wait", "colatus_profile_read_kinds",
-           "colatus_ensemble_autotune", "colatus_ensemble_set_tuning", "colatus_force_plan")
+           "colatus_ensemble_autotune", "colatus_ensemble_set_tuning", "colatus_force_plan",
+           "colatus_vjp_plan")
 
 
 class ColatusError(RuntimeError):
@@ -84,6 +85,7 @@ def lib():
         "colatus_ensemble_set_tuning": [_vp, _int],
         "colatus_forces_noalloc": [_vp, _i64, _dbl, _dbl, _dbl, _vp, _vp],
         "colatus_force_plan": [_vp, _vp],
+        "colatus_vjp_plan": [_vp, _vp],
         "colatus_force_vjp": [_vp, _vp, _vp, _vp, _int, _int],
         "colatus_adjoint_forward": [_vp, _dbl, _i64, _i64],
         "colatus_adjoint_backward": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _int, _int],
@@ -499,6 +501,14 @@ class Simulation:
         return dict(kind=kinds[int(out[0])], threads=int(out[1]), ipt=int(out[2]), jt=int(out[3]),
                     comp=bool(out[4]), eqm=bool(out[5]), grid=int(out[6]), units=int(out[7]),
                     nrcp=int(out[8]))
+
+    def vjp_plan(self):
+        """The VJP kernel the adjoint's backward pass launches (colatus_vjp_plan)."""
+        out = np.zeros(6, dtype=np.int64)
+        _check(lib().colatus_vjp_plan(self.h, out.ctypes.data), self.h)
+        kinds = ("vjp_f32", "vjp_f64", "ewald_vjp_f32", "ewald_vjp_f64", "vjp_eqm_f32", "vjp_sym_eqm_f32")
+        return dict(kind=kinds[int(out[0])], threads=int(out[1]), ipt=int(out[2]), jt=int(out[3]),
+                    grid=int(out[4]), units=int(out[5]))
 
     def profile_forces(self, on=True):
         colatus_profile_forces(self.h, on)

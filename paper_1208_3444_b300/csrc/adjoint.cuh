@@ -31,6 +31,7 @@
 
 #include "common.cuh"
 #include "force.cuh"
+#include "vjp_sym.cuh"
 
 namespace colatus {
 
@@ -535,6 +536,7 @@ __device__ __forceinline__ void pkw_store(float *pkw, long long i, float4 b, flo
 // Segment sums (fixed order) of a VJP launch: float4 (dL/dx, dL/dm).
 __device__ __forceinline__ float4 reduce_vjp_f32(const float4 *__restrict__ part,
                                                  const ForceLaunch &L, int itile, long long i) {
+    if (L.sym) return reduce_vjp_sym_f32(part, L, itile, i);   // each pair evaluated once
     const long long it = i / itile, il = i - it * itile;
     const long long g0 = sk_owner(it * L.n_jt, L.W, L.G);
     const long long g1 = sk_owner((it + 1) * L.n_jt - 1, L.W, L.G);

@@ -127,6 +127,11 @@ using F64K = F64Kernel<kF64NT, kF64IPT, kF64JT, kStages>;
 // SM, j-loop unrolled by 4 (the fastest of a sweep of about 30 shapes and
 // unroll depths on B300 at 32^3); FP64 128 x 1, 32-body tiles
 constexpr int kVjpNT = 256, kVjpIPT = 4, kVjpJT = 256, kVjpMINB = 1, kVjpUnr = 4;
+// Pair-once equal-mass VJP (vjp_sym.cuh): 256 threads x 4 i-bodies on
+// 1024-body tiles (the general VJP's padding), one CTA per SM (about 230
+// registers), rotation unrolled by 8; used from 8 tiles on, like the force's.
+constexpr int kVjpSymNT = 256, kVjpSymUnr = 8;
+using VjpSymK = VjpSymKernel<kVjpSymNT>;
 using VjpK = VjpKernel<kVjpNT, kVjpIPT, kVjpJT, kStages>;
 static_assert(kVjpIPT == 4, "the equal-mass VJP kernel shares the VJP's launch plan (4 i-bodies per thread)");
 constexpr int kV64NT = 128, kV64JT = 32;
@@ -298,6 +303,8 @@ struct colatus_ctx {
     ForcePlan plan32[NUM_F32_VARIANTS];
     ForcePlan plan64;
     ForcePlan plan_vjp32, plan_vjp64;
+    ForcePlan plan_vjp_sym;            // pair-once equal-mass VJP (fits: usable for this N)
+    int *vjp_sym_tab = nullptr;
     ForcePlan plan_ewvjp32, plan_ewvjp64;   // periodic VJP (real space)
 
     // periodic boundaries (colatus_set_periodic): Ewald parameters and buffers
@@ -487,6 +494,32 @@ colatus_status build_plans(colatus_t ctx) {
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &occ, vjp_f64_kernel<kV64NT, kV64JT, kStages>, kV64NT, Vjp64K::SMEM));
     if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "FP64 VJP kernel cannot be resident");
+    {
+        // the pair-once equal-mass VJP: tables with its phase costs (23
+        // lane-ops per diagonal interaction, 27 per symmetric pair)
+        auto fn = vjp_sym_eqm_f32_kernel<kVjpSymNT, kVjpSymUnr>;
+        CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, VjpSymK::SMEM));
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kVjpSymNT, VjpSymK::SMEM));
+        if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "pair-once VJP kernel cannot be resident");
+        ForcePlan &q = ctx->plan_vjp_sym;
+        q.itile = q.jt = VjpSymK::T;
+        q.n_pad = round_up(ctx->N, VjpSymK::T);
+        const SymTables st = build_sym_tables(q.n_pad, VjpSymK::T, VjpSymK::NW,
+                                              (long long)occ * std::max(1, ctx->num_sms - 1), 23, 27);
+        q.L = ForceLaunch{};
+        q.L.W = st.U;
+        q.L.n_it = q.L.n_jt = st.n;
+        q.L.G = st.G;
+        q.L.S_max = st.S_row;
+        q.L.col_off = (long long)st.n * st.S_row * q.itile;
+        q.part_bytes = (size_t)((long long)st.n * st.S_row + st.slots) * q.itile * sizeof(float4);
+        q.fits = st.n >= kSymMinTiles && q.part_bytes <= kSymMaxBytes;
+        if (q.fits) {
+            CU(cudaMalloc(&ctx->vjp_sym_tab, st.tab.size() * sizeof(int)));
+            CU(cudaMemcpy(ctx->vjp_sym_tab, st.tab.data(), st.tab.size() * sizeof(int), cudaMemcpyHostToDevice));
+            q.L.sym = ctx->vjp_sym_tab;
+        }
+    }
     ForcePlan &w = ctx->plan_vjp64;
     w.itile = Vjp64K::ITILE;
     w.jt = kV64JT;
@@ -992,7 +1025,7 @@ void free_all(colatus_t ctx) {
                     ctx->tclk, ctx->table, ctx->stage, ctx->stage2, ctx->diag, ctx->tslot,
                     ctx->rec, ctx->kw, ctx->rho, ctx->rho_part, ctx->wcs, ctx->pen,
                     ctx->rchunk, ctx->fchunk, ctx->lr, ctx->ph, ctx->pot_part, ctx->lrv,
-                    ctx->kwr, ctx->kwl, ctx->pk_ew};
+                    ctx->kwr, ctx->kwl, ctx->pk_ew, ctx->vjp_sym_tab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *tptrs[] = {ctx->tan.dx, ctx->tan.dv, ctx->tan.dvh, ctx->tan.dxp, ctx->tan.pkt,
@@ -1309,10 +1342,13 @@ colatus_status grow(colatus_t ctx, void **p, size_t *have, size_t need) {
     return COLATUS_OK;
 }
 
-// The VJP's launch plan: the periodic kernel's when the boundaries are periodic.
-const ForcePlan &vjp_plan(colatus_t ctx) {
+// The VJP's launch plan: the periodic kernel's when the boundaries are periodic;
+// eqm (the equal-mass VJP of the KDK adjoint): the pair-once kernel's where
+// it fits, which has the same padding.
+const ForcePlan &vjp_plan(colatus_t ctx, bool eqm = false) {
     const bool f64 = ctx->prec == COLATUS_FP64;
     if (ctx->periodic) return f64 ? ctx->plan_ewvjp64 : ctx->plan_ewvjp32;
+    if (eqm && !f64 && ctx->plan_vjp_sym.fits) return ctx->plan_vjp_sym;
     return f64 ? ctx->plan_vjp64 : ctx->plan_vjp32;
 }
 
@@ -1390,7 +1426,7 @@ colatus_status run_ewald_kspace_vjp(colatus_t ctx) {
 // equal-mass FP32 kernel, whose consumers need the forces at the positions).
 colatus_status run_vjp(colatus_t ctx, bool eqm = false) {
     const bool f64 = ctx->prec == COLATUS_FP64;
-    const ForcePlan &p = vjp_plan(ctx);
+    const ForcePlan &p = vjp_plan(ctx, eqm);
     TRY(ensure_part(ctx, p.part_bytes));
     TRY(prof_begin(ctx));
     if (ctx->periodic && f64)
@@ -1402,6 +1438,10 @@ colatus_status run_vjp(colatus_t ctx, bool eqm = false) {
             <<<p.L.G, kEwVjpNT, EwVjpK::SMEM, ctx->stream>>>(
                 static_cast<const float *>(ctx->adj.pkw), static_cast<float4 *>(ctx->part), ctx->flags,
                 p.L, (float)(ctx->eps * ctx->eps), ctx->ew);
+    else if (eqm && p.L.sym)
+        vjp_sym_eqm_f32_kernel<kVjpSymNT, kVjpSymUnr><<<p.L.G, kVjpSymNT, VjpSymK::SMEM, ctx->stream>>>(
+            static_cast<const float *>(ctx->adj.pkw), static_cast<float4 *>(ctx->part), ctx->flags, p.L,
+            (float)(ctx->eps * ctx->eps), ctx->mass_eq);
     else if (eqm)
         vjp_eqm_f32_kernel<kVjpNT, kVjpJT, kStages, kVjpMINB, kVjpUnr>
             <<<p.L.G, kVjpNT, VjpK::SMEM, ctx->stream>>>(
@@ -2198,9 +2238,9 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
     }
     const size_t body = f64 ? sizeof(double4) : sizeof(float4);
     const size_t plane = (size_t)ctx->n_alloc * body;
-    const ForcePlan &pv = vjp_plan(ctx);
+    const ForcePlan &pv0 = vjp_plan(ctx);
     const long long NS = a.nsteps;
-    const unsigned nbv = blocks_for(pv.n_pad, 256);
+    const unsigned nbv = blocks_for(pv0.n_pad, 256);
     // Equal masses, isolated boundaries, no deformation term and no padding in
     // the VJP's tiles: the equal-mass VJP, whose mass gradient takes the force
     // at each position; the recompute keeps them (seg_f, slot n - s0 for x_n).
@@ -2208,7 +2248,10 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
     // from the segment's positions and velocities (seg_v keeps the latter).
     const bool dkd = a.scheme == COLATUS_DKD;
     const bool eqm = !dkd && !f64 && ctx->eq_mass && !ctx->periodic && ctx->defo_C == 0.0 &&
-                     pv.n_pad == ctx->N;
+                     pv0.n_pad == ctx->N;
+    // the consumers' segment layout: the kernel run_vjp(ctx, eqm) launches
+    // (the pair-once one has the same padding, so pv0.n_pad stands for both)
+    const ForcePlan &pv = vjp_plan(ctx, eqm);
     if (eqm) TRY(grow(ctx, &a.seg_f, &a.segf_bytes, (size_t)(a.k + 1) * plane));
     if (dkd) TRY(grow(ctx, &a.seg_v, &a.segv_bytes, (size_t)a.k * plane));
     auto fslot = [&](long long j) {
@@ -2798,6 +2841,36 @@ colatus_status colatus_force_plan(colatus_t ctx, int64_t out[9]) {
     out[6] = p.L.G;
     out[7] = p.L.W;
     out[8] = f64 || ctx->periodic ? 0 : f32_variant(p.variant).nrcp;
+    return COLATUS_OK;
+}
+
+colatus_status colatus_vjp_plan(colatus_t ctx, int64_t out[6]) {
+    if (!ctx || !out) return COLATUS_E_ARG;
+    const bool f64 = ctx->prec == COLATUS_FP64;
+    const ForcePlan &p0 = vjp_plan(ctx);
+    const bool eqm = ctx->scheme != COLATUS_DKD && !f64 && ctx->eq_mass && !ctx->periodic &&
+                     ctx->defo_C == 0.0 && p0.n_pad == ctx->N;
+    const ForcePlan &p = vjp_plan(ctx, eqm);
+    if (ctx->periodic) {
+        out[0] = f64 ? 3 : 2;
+        out[1] = f64 ? kEwV64NT : kEwVjpNT;
+        out[2] = f64 ? 1 : kEwVjpIPT;
+    } else if (f64) {
+        out[0] = 1;
+        out[1] = kV64NT;
+        out[2] = 1;
+    } else if (eqm && p.L.sym) {
+        out[0] = 5;
+        out[1] = kVjpSymNT;
+        out[2] = VjpSymK::IPT;
+    } else {
+        out[0] = eqm ? 4 : 0;
+        out[1] = kVjpNT;
+        out[2] = kVjpIPT;
+    }
+    out[3] = p.jt;
+    out[4] = p.L.G;
+    out[5] = p.L.W;
     return COLATUS_OK;
 }
 

@@ -1,0 +1,308 @@
+// vjp_sym.cuh -- the equal-mass VJP of the all-pairs force with every pair
+// evaluated once.
+//
+// With every mass m, the VJP of Eq. 1 (see adjoint.cuh) at body i is
+//   dL/dx_i = m sum_j [ inv^3 u - 3 inv^5 (u . d) d ],
+//   dL/dm_i = -sum_j inv^3 (u . d) - w_i . P_i,
+// with d = x_j - x_i, u = w_j - w_i, inv = (|d|^2 + eps^2)^{-1/2} and P_i the
+// (G-less) force per unit mass that the forward pass computed.  Swapping i and
+// j flips both d and u, so the position term of the pair (i, j) is minus the
+// one of (j, i) and the mass term is the same for both: one evaluation of
+//   s = u - 3 inv^2 (u . d) d,   t = inv^3 s,   g = inv^3 (u . d)
+// adds (m t, -g) to body i and (-m t, -g) to body j.  That is 27 FP32 lane-ops
+// per pair and one MUFU.RSQ, against 2 x 23 when each ordered pair is taken
+// on its own (vjp_eqm_f32_kernel), and the self pair is exactly 0 (u = 0).
+//
+// Decomposition, tables and pipeline are those of force_sym.cuh (tile pairs
+// it <= jt, NW phases per unit, j-pairs rotating through the lanes with their
+// sums, column slots added by the consumers in fixed order); the bodies come
+// in the VJP's layout, 32 bytes per body, pair-interleaved
+// [x0 x1 y0 y1 z0 z1 m0 m1 wx0 wx1 wy0 wy1 wz0 wz1 0 0], and a j-tile is
+// split into (x0 x1 y0 y1), (z0 z1 wx0 wx1), (wy0 wy1 wz0 wz1), each 32-pair
+// block stored twice.  Segments hold float4 (dL/dx, dL/dm without the force
+// term), one plane, summed in FP32 like the other FP32 VJP kernels.
+#pragma once
+
+#include "force_sym.cuh"
+
+namespace colatus {
+
+template <int NT>
+struct VjpSymKernel {
+    static constexpr int IPT = 4;
+    static constexpr int NW = NT / 32;
+    static constexpr int T = NT * IPT;        // bodies per tile
+    static constexpr int TP = T / 2;          // j-pairs per tile
+    static constexpr int SLICE = TP / NW;     // j-pairs per warp slice
+    static constexpr int ROT = SLICE / 32;    // 32-round rotations per phase
+    static constexpr uint32_t TILE_BYTES = T * 32;
+    // staging tile, three doubled split arrays, the column accumulators
+    // [t_x t_y t_z g][TP] float2, one mbarrier
+    static constexpr int SMEM = TILE_BYTES + 3 * 2 * TP * 16 + 4 * TP * 8 + 16;
+    static_assert(SLICE % 32 == 0, "a warp slice is whole rotations");
+};
+
+// One 32-round rotation over a doubled block (see sym_rotation): every lane's
+// 4 i-bodies against every j-pair.  SYM: the j-side sums travel with their
+// j-pairs and end, in lane l, as those of j-pair base + l.
+template <bool SYM, int UNR>
+__device__ __forceinline__ void vjp_sym_rotation(const float4 *__restrict__ sA, const float4 *__restrict__ sB,
+                                                 const float4 *__restrict__ sC, int lane,
+                                                 const float2 (&nx)[4], const float2 (&ny)[4],
+                                                 const float2 (&nz)[4], const float2 (&nwx)[4],
+                                                 const float2 (&nwy)[4], const float2 (&nwz)[4],
+                                                 const float2 e2, float2 (&tx)[4], float2 (&ty)[4],
+                                                 float2 (&tz)[4], float2 (&tg)[4], float2 &jx, float2 &jy,
+                                                 float2 &jz, float2 &jg) {
+    const int src = (lane + 1) & 31;
+    const float2 n3 = make_float2(-3.f, -3.f);
+    const float4 *a = sA + lane, *b = sB + lane, *c = sC + lane;
+#pragma unroll(UNR)
+    for (int r = 0; r < 32; ++r) {
+        const float4 A = a[r];   // x0 x1 y0 y1
+        const float4 Bq = b[r];  // z0 z1 wx0 wx1
+        const float4 C = c[r];   // wy0 wy1 wz0 wz1
+        const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
+        const float2 zj = make_float2(Bq.x, Bq.y), wxj = make_float2(Bq.z, Bq.w);
+        const float2 wyj = make_float2(C.x, C.y), wzj = make_float2(C.z, C.w);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 dx = __fadd2_rn(xj, nx[k]);
+            const float2 dy = __fadd2_rn(yj, ny[k]);
+            const float2 dz = __fadd2_rn(zj, nz[k]);
+            float2 r2 = __ffma2_rn(dx, dx, e2);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            const float2 inv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+            const float2 inv2 = __fmul2_rn(inv, inv);
+            const float2 inv3 = __fmul2_rn(inv, inv2);
+            const float2 ux = __fadd2_rn(wxj, nwx[k]);
+            const float2 uy = __fadd2_rn(wyj, nwy[k]);
+            const float2 uz = __fadd2_rn(wzj, nwz[k]);
+            float2 du = __fmul2_rn(ux, dx);
+            du = __ffma2_rn(uy, dy, du);
+            du = __ffma2_rn(uz, dz, du);
+            const float2 q = __fmul2_rn(__fmul2_rn(inv2, du), n3);
+            const float2 sx = __ffma2_rn(q, dx, ux);
+            const float2 sy = __ffma2_rn(q, dy, uy);
+            const float2 sz = __ffma2_rn(q, dz, uz);
+            tx[k] = __ffma2_rn(inv3, sx, tx[k]);
+            ty[k] = __ffma2_rn(inv3, sy, ty[k]);
+            tz[k] = __ffma2_rn(inv3, sz, tz[k]);
+            tg[k] = __ffma2_rn(inv3, du, tg[k]);
+            if (SYM) {
+                jx = __ffma2_rn(inv3, sx, jx);
+                jy = __ffma2_rn(inv3, sy, jy);
+                jz = __ffma2_rn(inv3, sz, jz);
+                jg = __ffma2_rn(inv3, du, jg);
+            }
+        }
+        if (SYM) {
+            jx = shfl_float2(jx, src);
+            jy = shfl_float2(jy, src);
+            jz = shfl_float2(jz, src);
+            jg = shfl_float2(jg, src);
+        }
+    }
+}
+
+// Persistent pair-once equal-mass VJP kernel, FP32.  pkw: bodies and
+// co-vectors in the VJP layout (N_pad a multiple of T, and no zero-mass
+// padding: N_pad = N).  part: row segments [n][S_max][T] float4, then from
+// float4 offset L.col_off the column slots [slot][T] float4, each float4
+// (m sum t, -sum g) of the bodies it indexes (the column's position part
+// negated when written).  mass: the common mass m.
+template <int NT, int UNR>
+__global__ void __launch_bounds__(NT, 1)
+    vjp_sym_eqm_f32_kernel(const float *__restrict__ pkw, float4 *__restrict__ part, int *__restrict__ flags,
+                           ForceLaunch L, float eps2, float mass) {
+    using K = VjpSymKernel<NT>;
+    constexpr int NW = K::NW, T = K::T, TP = K::TP;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float4 *raw = reinterpret_cast<float4 *>(smem);   // staging: 2 T float4 (VJP layout)
+    float4 *sA = raw + 2 * T;                         // 2 TP float4 each, blocks doubled
+    float4 *sB = sA + 2 * TP;
+    float4 *sC = sB + 2 * TP;
+    float2 *acc = reinterpret_cast<float2 *>(sC + 2 * TP);   // [4][TP]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(acc + 4 * TP);
+
+    const int *tab = L.sym;
+    const int n = tab[0], U = tab[2];
+    const int *row_g0 = tab + kSymHdr;
+    const int *unit_g0 = row_g0 + 2 * n;
+    const int *unit_ko = unit_g0 + U;
+    const int *cta_pu = unit_ko + 2 * U;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = blockIdx.x;
+    int pu = cta_pu[g];
+    const int pu_end = cta_pu[g + 1];
+    if (pu >= pu_end) return;
+    long long u = pu / NW;
+    int it, jt;
+    sym_decode(u, n, it, jt);
+
+    for (int q = tid; q < 4 * TP; q += NT) acc[q] = make_float2(0.f, 0.f);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(bar, K::TILE_BYTES);
+        bulk_load(raw, pkw + (long long)jt * T * 8, K::TILE_BYTES, bar);
+    }
+    bool inflight = true;
+
+    const float2 e2 = make_float2(eps2, eps2);
+    float2 nx[4], ny[4], nz[4], nwx[4], nwy[4], nwz[4];
+    float hx[4], hy[4], hz[4], hg[4];
+    auto load_i = [&](int row) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long i = (long long)row * T + tid + k * NT;
+            const float *p = pkw + (i >> 1) * 16 + (i & 1);
+            const float x = __ldg(p), y = __ldg(p + 2), z = __ldg(p + 4);
+            const float wx = __ldg(p + 8), wy = __ldg(p + 10), wz = __ldg(p + 12);
+            nx[k] = make_float2(-x, -x);
+            ny[k] = make_float2(-y, -y);
+            nz[k] = make_float2(-z, -z);
+            nwx[k] = make_float2(-wx, -wx);
+            nwy[k] = make_float2(-wy, -wy);
+            nwz[k] = make_float2(-wz, -wz);
+            hx[k] = hy[k] = hz[k] = hg[k] = 0.f;
+        }
+    };
+    load_i(it);
+
+    uint32_t parity = 0;
+    bool bad = false;
+    while (pu < pu_end) {
+        const int uend = (int)min((long long)pu_end, (u + 1) * NW);
+        const int p0 = pu - (int)(u * NW), p1 = uend - (int)(u * NW);
+        const bool ok = mbar_wait_bounded(bar, parity);
+        if (__syncthreads_or(!ok)) {
+            bad = true;
+            break;
+        }
+        inflight = false;
+        parity ^= 1u;
+        for (int q = tid; q < TP; q += NT) {
+            const int e = 2 * q - (q & 31);   // entry of pair q in its doubled block
+            const float4 r0 = raw[4 * q], r1 = raw[4 * q + 1], r2 = raw[4 * q + 2], r3 = raw[4 * q + 3];
+            const float4 Bq = make_float4(r1.x, r1.y, r2.x, r2.y);
+            const float4 C = make_float4(r2.z, r2.w, r3.x, r3.y);
+            sA[e] = r0;
+            sA[e + 32] = r0;
+            sB[e] = Bq;
+            sB[e + 32] = Bq;
+            sC[e] = C;
+            sC[e + 32] = C;
+        }
+        __syncthreads();
+        int it_n = it, jt_n = jt + 1;
+        if (jt_n == n) {
+            ++it_n;
+            jt_n = it_n;
+        }
+        if (uend < pu_end) {
+            if (tid == 0) {
+                mbar_arrive_expect_tx(bar, K::TILE_BYTES);
+                bulk_load(raw, pkw + (long long)jt_n * T * 8, K::TILE_BYTES, bar);
+            }
+            inflight = true;
+        }
+        const bool sym = jt != it;
+        for (int p = p0; p < p1; ++p) {
+            const int slice = (warp + p) % NW;
+            float2 tx[4], ty[4], tz[4], tg[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) tx[k] = ty[k] = tz[k] = tg[k] = make_float2(0.f, 0.f);
+#pragma unroll 1
+            for (int s = 0; s < K::ROT; ++s) {
+                const int base = slice * K::SLICE + s * 32;
+                const float4 *bA = sA + 2 * base, *bB = sB + 2 * base, *bC = sC + 2 * base;
+                float2 jx = make_float2(0.f, 0.f), jy = jx, jz = jx, jg = jx;
+                if (sym) {
+                    vjp_sym_rotation<true, UNR>(bA, bB, bC, lane, nx, ny, nz, nwx, nwy, nwz, e2, tx, ty, tz,
+                                                tg, jx, jy, jz, jg);
+                    const int q = base + lane;
+                    acc[q] = __fadd2_rn(acc[q], jx);
+                    acc[TP + q] = __fadd2_rn(acc[TP + q], jy);
+                    acc[2 * TP + q] = __fadd2_rn(acc[2 * TP + q], jz);
+                    acc[3 * TP + q] = __fadd2_rn(acc[3 * TP + q], jg);
+                } else {
+                    vjp_sym_rotation<false, UNR>(bA, bB, bC, lane, nx, ny, nz, nwx, nwy, nwz, e2, tx, ty, tz,
+                                                 tg, jx, jy, jz, jg);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                hx[k] += tx[k].x + tx[k].y;
+                hy[k] += ty[k].x + ty[k].y;
+                hz[k] += tz[k].x + tz[k].y;
+                hg[k] += tg[k].x + tg[k].y;
+            }
+            __syncthreads();   // the slices change hands
+        }
+        if (sym) {
+            const int slot = unit_ko[u] + (g - unit_g0[u]);
+            float4 *dst = part + L.col_off + (long long)slot * T;
+            for (int q = tid; q < TP; q += NT) {
+                const float2 a = acc[q], b = acc[TP + q], c = acc[2 * TP + q], d = acc[3 * TP + q];
+                dst[2 * q] = make_float4(-mass * a.x, -mass * b.x, -mass * c.x, -d.x);
+                dst[2 * q + 1] = make_float4(-mass * a.y, -mass * b.y, -mass * c.y, -d.y);
+                acc[q] = acc[TP + q] = acc[2 * TP + q] = acc[3 * TP + q] = make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+        }
+        pu = uend;
+        ++u;
+        if (it_n != it || pu == pu_end) {
+            const int sidx = g - row_g0[it];
+            float4 *dst = part + ((long long)it * L.S_max + sidx) * T;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                dst[tid + k * NT] = make_float4(mass * hx[k], mass * hy[k], mass * hz[k], -hg[k]);
+            if (it_n != it && pu < pu_end) load_i(it_n);
+        }
+        it = it_n;
+        jt = jt_n;
+    }
+    if (bad && tid == 0) {
+        atomicOr(&flags[FLAG_TIMEOUT], 1);
+        if (inflight) mbar_wait_bounded(bar, parity);   // drain the copy in flight, bounded
+    }
+}
+
+// Consumer side: the VJP of body i (float4 dL/dx, dL/dm) of a pair-once plan,
+// its row segments then the column slots of the units (t', t), t' < t, in that
+// fixed order.
+__device__ __forceinline__ float4 reduce_vjp_sym_f32(const float4 *__restrict__ part, const ForceLaunch &L,
+                                                     int T, long long i) {
+    const int *tab = L.sym;
+    const int n = tab[0], U = tab[2];
+    const int *row_ns = tab + kSymHdr + n;
+    const int *unit_ko = tab + kSymHdr + 2 * n + U;
+    const int *unit_nk = unit_ko + U;
+    const long long t = i / T, il = i - t * T;
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto add = [&](const float4 *p) {
+        const float4 v = __ldg(p);
+        r.x += v.x;
+        r.y += v.y;
+        r.z += v.z;
+        r.w += v.w;
+    };
+    const float4 *p = part + t * L.S_max * (long long)T + il;
+    const int ns = row_ns[t];
+    for (int s = 0; s < ns; ++s) add(p + (long long)s * T);
+    const float4 *c = part + L.col_off + il;
+    for (long long tp = 0; tp < t; ++tp) {
+        const long long uu = sym_row_u0(tp, n) + (t - tp);
+        const int ko = unit_ko[uu], nk = unit_nk[uu];
+        for (int k = 0; k < nk; ++k) add(c + (long long)(ko + k) * T);
+    }
+    return r;
+}
+
+}  // namespace colatus

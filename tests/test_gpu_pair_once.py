@@ -156,3 +156,85 @@ def test_default_choice_from_eight_tiles():
             assert sim.force_plan()["kind"] == kind, N
         finally:
             sim.close()
+
+
+# ---- the pair-once equal-mass VJP (the KDK adjoint's kernel from 8 tiles of
+# 1024 bodies): gradients against the oracle's exact transpose of the steps
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def tracer_loss_grads(xT, vT, m, aT, tr):
+    """L = 1/2 sum_tracers m a^2 |v|^2 and its gradients at the final state."""
+    gv = np.zeros_like(vT)
+    gv[tr] = aT * aT * m[tr, None] * vT[tr]
+    gm = np.zeros_like(m)
+    gm[tr] = 0.5 * aT * aT * np.sum(vT[tr] ** 2, axis=1)
+    return gv, gm
+
+
+def adjoint_pair(ic, prec, n, k, tr):
+    sim = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START, prec=prec)
+    try:
+        sim.set_state(ic.x, ic.v)
+        plan = sim.vjp_plan()
+        sim.adjoint_forward(TAU, n, k)
+        xT, vT, t, aT = sim.state()
+        gvT, gmT = tracer_loss_grads(xT, vT, ic.m, aT, tr)
+        g = sim.adjoint_backward(None, gvT, gmT)
+    finally:
+        sim.close()
+    r = oracle.run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n, "kdk")
+    gvO, gmO = tracer_loss_grads(r["x"], r["v"], ic.m, r["schedule"]["a"][-1], tr)
+    gx, gv, gm = oracle.adjoint_run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n,
+                                    np.zeros_like(ic.x), gvO, gmO, scheme="kdk")
+    return plan, g, dict(gx=gx, gv=gv, gm=gm)
+
+
+@pytest.mark.parametrize("prec", [B.FP32, B.FP32_COMP])
+@pytest.mark.parametrize("k", [3, 1])
+def test_equal_mass_adjoint_pair_once_vjp(prec, k):
+    # 8192 equal-mass bodies at the background density (8 tiles of 1024), 8
+    # KDK steps; checkpoints every 3 (segments 3 + 3 + 2) or every step
+    ic = inputs.perturbed_grid(21, 0.1, 0.02, 41, zeldovich=True, count=8192,
+                               total_mass=inputs.CRITICAL_MATTER_DENSITY)
+    tr = inputs.tracers(ic.N, 64, 7)
+    plan, g, ref = adjoint_pair(ic, prec, 8, k, tr)
+    assert plan["kind"] == "vjp_sym_eqm_f32" and plan["units"] == 8 * 9 // 2
+    for key, got in zip(("gx", "gv", "gm"), g):
+        assert rel(got, ref[key]) < 1e-4, key
+
+
+def test_grid32_adjoint_pair_once_vjp():
+    # the adjoint configuration's workload (32^3, the benchmark's kernel and
+    # launch plan) over two steps, checkpoints every step
+    ic = inputs.grid32()
+    tr = inputs.tracers(ic.N, 64, 7)
+    plan, g, ref = adjoint_pair(ic, B.FP32_COMP, 2, 1, tr)
+    assert plan["kind"] == "vjp_sym_eqm_f32" and plan["units"] == 32 * 33 // 2
+    for key, got in zip(("gx", "gv", "gm"), g):
+        assert rel(got, ref[key]) < 1e-4, key
+
+
+def test_vjp_plan_kinds():
+    # the general form below 8 tiles, with unequal masses, for DKD and under
+    # the Eq. 6 term; FP64 its own kernel
+    x, m = system(8192, True, 3)
+    cases = [(dict(), "vjp_sym_eqm_f32"), (dict(scheme=B.DKD), "vjp_f32"),
+             (dict(prec=B.FP64), "vjp_f64")]
+    for kw, kind in cases:
+        sim = B.Simulation(m, 0.01, LCDM_D, 1.0, **{"prec": B.FP32, **kw})
+        try:
+            sim.set_state(x)
+            assert sim.vjp_plan()["kind"] == kind, kw
+        finally:
+            sim.close()
+    for N, mm, kind in ((7168, np.full(7168, 1 / 7168), "vjp_eqm_f32"),
+                        (8192, system(8192, False, 4)[1], "vjp_f32")):
+        sim = B.Simulation(inputs.f32(mm), 0.01, LCDM_D, 1.0, prec=B.FP32)
+        try:
+            sim.set_state(system(N, True, 5)[0])
+            assert sim.vjp_plan()["kind"] == kind, N
+        finally:
+            sim.close()
