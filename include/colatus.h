@@ -265,10 +265,11 @@ colatus_status colatus_stats(colatus_t ctx, double out[4]);
  * Eq. 1 sum of the paper's Appendix A kernel; this names its launch shape):
  * out[0] kind (0 FP32 all-pairs, 1 FP64 all-pairs, 2 FP32 periodic real
  * space, 3 FP64 periodic real space, 4 FP32 all-pairs with every pair
- * evaluated once), out[1] threads per CTA, out[2] i-bodies per thread,
+ * evaluated once, 5 FP32 periodic real space with every pair evaluated
+ * once), out[1] threads per CTA, out[2] i-bodies per thread,
  * out[3] j-tile bodies, out[4] compensated accumulation (0/1), out[5]
  * equal-mass form (0/1), out[6] persistent grid (CTAs), out[7] work units
- * (i-tile x j-tile; for kind 4 the tile pairs it <= jt), out[8] i-bodies per
+ * (i-tile x j-tile; for kinds 4 and 5 the tile pairs it <= jt), out[8] i-bodies per
  * thread whose 1/s^2 is an rcp on the MUFU pipe rather than a square of the
  * rsqrt on the FMA pipe.  Errors: COLATUS_E_ARG. */
 colatus_status colatus_force_plan(colatus_t ctx, int64_t out[9]);
@@ -318,7 +319,10 @@ colatus_status colatus_profile_read_kinds(colatus_t ctx, double out[6]);
  * the fastest for this context and returns it in *chosen; out_ms[4] (may be
  * NULL) receives the mean milliseconds per launch (0 for shapes that do not
  * fit).  colatus_set_tuning applies a known choice (-1: built-in choice);
- * COLATUS_E_ARG for a shape that does not fit. */
+ * COLATUS_E_ARG for a shape that does not fit.  Under periodic boundaries
+ * the real-space kernel comes in two forms: every pair once (1024-body
+ * tiles, from 8 tiles on; the built-in choice and shape 3) and every ordered
+ * pair (any other shape); colatus_autotune refuses periodic contexts. */
 colatus_status colatus_autotune(colatus_t ctx, int reps, double out_ms[4], int *chosen);
 colatus_status colatus_set_tuning(colatus_t ctx, int shape);
 

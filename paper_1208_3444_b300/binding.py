@@ -497,7 +497,7 @@ class Simulation:
         """The force kernel launched for the current configuration (colatus_force_plan)."""
         out = np.zeros(9, dtype=np.int64)
         _check(lib().colatus_force_plan(self.h, out.ctypes.data), self.h)
-        kinds = ("force_f32", "force_f64", "ewald_f32", "ewald_f64", "force_sym_f32")
+        kinds = ("force_f32", "force_f64", "ewald_f32", "ewald_f64", "force_sym_f32", "ewald_sym_f32")
         return dict(kind=kinds[int(out[0])], threads=int(out[1]), ipt=int(out[2]), jt=int(out[3]),
                     comp=bool(out[4]), eqm=bool(out[5]), grid=int(out[6]), units=int(out[7]),
                     nrcp=int(out[8]))

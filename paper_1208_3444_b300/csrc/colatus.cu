@@ -77,7 +77,7 @@ void launch_sym(int grid, cudaStream_t st, const float *pk, float4 *part, int *f
                 float eps2, float mass_eq) {
     using K = SymKernel<kSymNT, kSymIPT, COMP>;
     force_sym_f32_kernel<kSymNT, kSymIPT, COMP, EQM, kSymUnr><<<grid, kSymNT, K::SMEM, st>>>(
-        pk, part, flags, L, eps2, mass_eq);
+        pk, part, flags, L, eps2, mass_eq, PlummerPair::Args{});
 }
 
 template <bool COMP, bool EQM>
@@ -150,6 +150,12 @@ constexpr int kEwJvpMinB = 1;
 // 512 x 2 at one CTA per SM: 6 % faster than 256 x 2 at two, among eight
 // shapes timed on B300 at 32^3 (equal masses, compensated)
 constexpr int kEwNT = 512, kEwIPT = 2, kEwJT = 256, kEwFold = 32, kEwMinB = 1;
+// Pair-once real space (force_sym.cuh with EwaldPair): 512 threads x 2
+// i-bodies on 1024-body tiles, one CTA per SM; the built-in choice from 8
+// tiles on, like the isolated force's.
+constexpr int kEwSymNT = 512, kEwSymIPT = 2, kEwSymUnr = 2;
+using EwSymK = SymKernel<kEwSymNT, kEwSymIPT, false>;
+using EwSymKC = SymKernel<kEwSymNT, kEwSymIPT, true>;
 using EwK = EwaldF32Kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, false>;
 using EwKC = EwaldF32Kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, true>;
 constexpr int kEw64NT = 128, kEw64JT = 32;
@@ -331,6 +337,8 @@ struct colatus_ctx {
     size_t ph_bytes = 0;
     size_t kv_cap = 0;
     ForcePlan plan_ew32[2], plan_ew64;
+    ForcePlan plan_ew_sym[2];          // pair-once real space (plain, compensated)
+    int *ew_sym_tab = nullptr;
 
     // tangent model (colatus_tangent_*)
     struct Tangent {
@@ -556,6 +564,43 @@ colatus_status build_plans(colatus_t ctx) {
         e.n_pad = round_up(ctx->N, std::max(e.itile, e.jt));
         finish_plan(e, occ, ctx->num_sms, sizeof(float4) * (comp ? 2 : 1));
     }
+    {
+        // pair-once real space: tables with its phase costs (35 lane-ops per
+        // diagonal interaction, 38 per symmetric pair)
+        SymTables st;
+        for (int comp = 0; comp < 2; ++comp) {
+            const void *fn = comp ? (const void *)force_sym_f32_kernel<kEwSymNT, kEwSymIPT, true, false, kEwSymUnr, EwaldPair>
+                                  : (const void *)force_sym_f32_kernel<kEwSymNT, kEwSymIPT, false, false, kEwSymUnr, EwaldPair>;
+            const void *fe = comp ? (const void *)force_sym_f32_kernel<kEwSymNT, kEwSymIPT, true, true, kEwSymUnr, EwaldPair>
+                                  : (const void *)force_sym_f32_kernel<kEwSymNT, kEwSymIPT, false, true, kEwSymUnr, EwaldPair>;
+            const int smem = comp ? EwSymKC::SMEM : EwSymK::SMEM;
+            CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            CU(cudaFuncSetAttribute(fe, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kEwSymNT, smem));
+            if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "pair-once Ewald kernel cannot be resident");
+            ForcePlan &q = ctx->plan_ew_sym[comp];
+            q.itile = q.jt = EwSymK::T;
+            q.n_pad = round_up(ctx->N, EwSymK::T);
+            if (st.tab.empty())
+                st = build_sym_tables(q.n_pad, EwSymK::T, EwSymK::NW,
+                                      (long long)occ * std::max(1, ctx->num_sms - 1), 35, 38);
+            q.L = ForceLaunch{};
+            q.L.W = st.U;
+            q.L.n_it = q.L.n_jt = st.n;
+            q.L.G = st.G;
+            q.L.S_max = st.S_row;
+            q.L.col_off = (long long)st.n * st.S_row * (comp + 1) * q.itile;
+            q.part_bytes = (size_t)((long long)st.n * st.S_row + st.slots) * (comp + 1) * q.itile * sizeof(float4);
+            q.fits = st.n >= kSymMinTiles && q.part_bytes <= kSymMaxBytes;
+        }
+        if (ctx->plan_ew_sym[1].fits) {
+            CU(cudaMalloc(&ctx->ew_sym_tab, st.tab.size() * sizeof(int)));
+            CU(cudaMemcpy(ctx->ew_sym_tab, st.tab.data(), st.tab.size() * sizeof(int), cudaMemcpyHostToDevice));
+            ctx->plan_ew_sym[0].L.sym = ctx->plan_ew_sym[1].L.sym = ctx->ew_sym_tab;
+        } else {
+            ctx->plan_ew_sym[0].fits = false;
+        }
+    }
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &occ, ewald_f64_kernel<kEw64NT, kEw64JT, kStages>, kEw64NT, Ew64K::SMEM));
     if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "FP64 Ewald kernel cannot be resident");
@@ -584,7 +629,14 @@ int default_shape(colatus_t ctx, int comp) {
 }
 
 const ForcePlan &plan_f32(colatus_t ctx) {
-    if (ctx->periodic) return ctx->plan_ew32[ctx->prec == COLATUS_FP32_COMP ? 1 : 0];
+    if (ctx->periodic) {
+        // real space: the pair-once kernel where it fits (tuning shape 3 or the
+        // built-in choice), else the per-ordered-pair one (any other shape)
+        const int c = ctx->prec == COLATUS_FP32_COMP ? 1 : 0;
+        const ForcePlan &q = ctx->plan_ew_sym[c];
+        const bool sym = q.fits && (ctx->tuned_shape < 0 || ctx->tuned_shape == kSymShape);
+        return sym ? q : ctx->plan_ew32[c];
+    }
     const int comp = ctx->prec == COLATUS_FP32_COMP ? V_COMP : 0;
     const int sh = ctx->tuned_shape >= 0 ? ctx->tuned_shape : default_shape(ctx, comp);
     const ForcePlan *w = &ctx->plan32[4 * sh + comp];
@@ -828,7 +880,23 @@ colatus_status run_ewald_f32(colatus_t ctx, const ForcePlan &p, const float *pk)
     const bool eqm = ctx->eq_mass && p.n_pad == ctx->N;
     float4 *part = static_cast<float4 *>(ctx->part);
     const float me = ctx->mass_eq;
-    if (ctx->prec == COLATUS_FP32_COMP && eqm)
+    const bool comp = ctx->prec == COLATUS_FP32_COMP;
+    if (p.L.sym) {
+        // pair-once real space
+        const int smem = comp ? EwSymKC::SMEM : EwSymK::SMEM;
+        if (comp && eqm)
+            force_sym_f32_kernel<kEwSymNT, kEwSymIPT, true, true, kEwSymUnr, EwaldPair>
+                <<<p.L.G, kEwSymNT, smem, ctx->stream>>>(pkw, part, ctx->flags, p.L, eps2, me, ctx->ew);
+        else if (comp)
+            force_sym_f32_kernel<kEwSymNT, kEwSymIPT, true, false, kEwSymUnr, EwaldPair>
+                <<<p.L.G, kEwSymNT, smem, ctx->stream>>>(pkw, part, ctx->flags, p.L, eps2, me, ctx->ew);
+        else if (eqm)
+            force_sym_f32_kernel<kEwSymNT, kEwSymIPT, false, true, kEwSymUnr, EwaldPair>
+                <<<p.L.G, kEwSymNT, smem, ctx->stream>>>(pkw, part, ctx->flags, p.L, eps2, me, ctx->ew);
+        else
+            force_sym_f32_kernel<kEwSymNT, kEwSymIPT, false, false, kEwSymUnr, EwaldPair>
+                <<<p.L.G, kEwSymNT, smem, ctx->stream>>>(pkw, part, ctx->flags, p.L, eps2, me, ctx->ew);
+    } else if (ctx->prec == COLATUS_FP32_COMP && eqm)
         ewald_f32_kernel<kEwNT, kEwIPT, kEwJT, kStages, kEwFold, true, kEwMinB, true>
             <<<p.L.G, kEwNT, EwKC::SMEM, ctx->stream>>>(pkw, part, ctx->flags, p.L, eps2, ctx->ew, me);
     else if (ctx->prec == COLATUS_FP32_COMP)
@@ -1025,7 +1093,7 @@ void free_all(colatus_t ctx) {
                     ctx->tclk, ctx->table, ctx->stage, ctx->stage2, ctx->diag, ctx->tslot,
                     ctx->rec, ctx->kw, ctx->rho, ctx->rho_part, ctx->wcs, ctx->pen,
                     ctx->rchunk, ctx->fchunk, ctx->lr, ctx->ph, ctx->pot_part, ctx->lrv,
-                    ctx->kwr, ctx->kwl, ctx->pk_ew, ctx->vjp_sym_tab};
+                    ctx->kwr, ctx->kwl, ctx->pk_ew, ctx->vjp_sym_tab, ctx->ew_sym_tab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *tptrs[] = {ctx->tan.dx, ctx->tan.dv, ctx->tan.dvh, ctx->tan.dxp, ctx->tan.pkt,
@@ -1641,7 +1709,8 @@ colatus_status colatus_init(colatus_t *out, int64_t N, const double *masses, dou
     for (const ForcePlan &p : ctx->plan32) ctx->n_alloc = std::max(ctx->n_alloc, p.n_pad);
     for (const ForcePlan *p : {&ctx->plan64, &ctx->plan_vjp32, &ctx->plan_vjp64, &ctx->plan_ewvjp32,
                                &ctx->plan_ewvjp64, &ctx->plan_ew32[0],
-                               &ctx->plan_ew32[1], &ctx->plan_ew64})
+                               &ctx->plan_ew32[1], &ctx->plan_ew64, &ctx->plan_vjp_sym,
+                               &ctx->plan_ew_sym[0], &ctx->plan_ew_sym[1]})
         ctx->n_alloc = std::max(ctx->n_alloc, p->n_pad);
     ctx->eps = eps;
     ctx->cosmo = Cosmo{Omega_R, Omega_M, Omega_K, Omega_L, H0};
@@ -2820,14 +2889,15 @@ colatus_status colatus_force_plan(colatus_t ctx, int64_t out[9]) {
     const ForcePlan &p = f64 ? plan_f64(ctx) : plan_f32(ctx);
     out[0] = (ctx->periodic ? 2 : 0) + (f64 ? 1 : 0);
     if (!f64 && !ctx->periodic && f32_variant(p.variant).sym) out[0] = 4;
+    if (!f64 && ctx->periodic && p.L.sym) out[0] = 5;
     if (f64) {
         out[1] = ctx->periodic ? kEw64NT : kF64NT;
         out[2] = ctx->periodic ? 1 : kF64IPT;
         out[4] = 0;
         out[5] = 0;
     } else if (ctx->periodic) {
-        out[1] = kEwNT;
-        out[2] = kEwIPT;
+        out[1] = p.L.sym ? kEwSymNT : kEwNT;
+        out[2] = p.L.sym ? kEwSymIPT : kEwIPT;
         out[4] = ctx->prec == COLATUS_FP32_COMP ? 1 : 0;
         out[5] = ctx->eq_mass && p.n_pad == ctx->N ? 1 : 0;
     } else {

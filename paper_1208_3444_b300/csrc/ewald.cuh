@@ -42,6 +42,7 @@
 
 #include "common.cuh"
 #include "force.cuh"
+#include "force_sym.cuh"
 
 namespace colatus {
 
@@ -127,6 +128,25 @@ __device__ __forceinline__ float2 ewald_pair2(const float2 dx, const float2 dy, 
     const float2 br = __fadd2_rn(ip3, f);
     return EQM ? br : __fmul2_rn(mj, br);
 }
+
+// The real-space term as a pair policy of the pair-once kernel
+// (force_sym.cuh): the minimum image of the separation, then the mass-free
+// bracket of ewald_pair2.  The term is antisymmetric: the minimum image of
+// x_k - x_j is exactly minus that of x_j - x_k (the FMA-pipe rounding is odd,
+// ties at half a box go to the even integer 0 both ways) and the bracket
+// depends on |d| only.  35 FP32 lane-ops and 4 MUFU results per pair with one
+// side's accumulation, 38 with both.
+struct EwaldPair {
+    using Args = EwaldArgs;
+    __device__ __forceinline__ static float2 weight(float2 &dx, float2 &dy, float2 &dz, const float2 e2,
+                                                    const EwaldArgs &A) {
+        const float2 Lm = make_float2(-A.Lf, -A.Lf), iL = make_float2(A.invLf, A.invLf);
+        dx = min_image2(dx, iL, Lm);
+        dy = min_image2(dy, iL, Lm);
+        dz = min_image2(dz, iL, Lm);
+        return ewald_pair2<true>(dx, dy, dz, make_float2(0.f, 0.f), A, e2);
+    }
+};
 
 // pk: the bodies with positions wrapped into [0, L] (ewald_phase_kernel
 // writes them), so every separation rounds once from coordinates of the

@@ -8,6 +8,9 @@
 // FP32 lane-ops with equal masses (16 in general) and one MUFU.RSQ, against
 // 2 x 11 (2 x 12) when each ordered pair is evaluated separately.
 //
+// The pair term is a policy (PlummerPair here; EwaldPair in ewald.cuh for the
+// real-space part under periodic boundaries, whose term is as antisymmetric).
+//
 // Decomposition.  Bodies are cut into tiles of T = IPT NT.  The units are the
 // tile pairs (it, jt) with it <= jt, ordered i-major:
 //   u(it, jt) = row_u0(it) + jt - it,  row_u0(it) = it n - it (it - 1) / 2.
@@ -97,6 +100,25 @@ __device__ __forceinline__ float2 shfl_float2(float2 v, int src) {
     return make_float2(__uint_as_float((unsigned)b), __uint_as_float((unsigned)(b >> 32)));
 }
 
+// Pair terms.  A pair policy P gives, for the separation (dx, dy, dz) = x_j -
+// x_i of two j-bodies at once, the mass-free weight w with which the pair adds
+// m_j w d to body i and -m_i w d to body j; it may replace d by the
+// separation it uses (the minimum image under periodic boundaries).
+// PlummerPair: w = (|d|^2 + eps^2)^{-3/2} (Eq. 1), 8 FP32 lane-ops and one
+// MUFU.RSQ.
+struct PlummerPair {
+    struct Args {};
+    __device__ __forceinline__ static float2 weight(float2 &dx, float2 &dy, float2 &dz, const float2 e2,
+                                                    const Args &) {
+        float2 r2 = __ffma2_rn(dx, dx, e2);
+        r2 = __ffma2_rn(dy, dy, r2);
+        r2 = __ffma2_rn(dz, dz, r2);
+        const float2 inv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+        const float2 inv2 = __fmul2_rn(inv, inv);
+        return __fmul2_rn(inv, inv2);
+    }
+};
+
 // One 32-round rotation of a warp over the 32 j-pairs of one doubled block
 // (entries 32..63 repeat 0..31; the block's entries start at sA, sB + 64 blk):
 // every lane's IPT i-bodies against every j-pair, lane l taking entry l + r
@@ -105,13 +127,13 @@ __device__ __forceinline__ float2 shfl_float2(float2 v, int src) {
 // round) and so end, in lane l, as the sum of j-pair base + l (returned in
 // jx, jy, jz; they hold sum_k m_k w d, minus the force on j; without m_k for
 // EQM).
-template <int IPT, bool SYM, bool EQM, int UNR>
+template <class P, int IPT, bool SYM, bool EQM, int UNR>
 __device__ __forceinline__ void sym_rotation(const float4 *__restrict__ sA, const float4 *__restrict__ sB,
                                              int lane, const float2 (&nx)[IPT],
                                              const float2 (&ny)[IPT], const float2 (&nz)[IPT],
-                                             const float2 (&mi)[IPT], const float2 e2, float2 (&px)[IPT],
-                                             float2 (&py)[IPT], float2 (&pz)[IPT], float2 &jx, float2 &jy,
-                                             float2 &jz) {
+                                             const float2 (&mi)[IPT], const float2 e2, const typename P::Args &pa,
+                                             float2 (&px)[IPT], float2 (&py)[IPT], float2 (&pz)[IPT],
+                                             float2 &jx, float2 &jy, float2 &jz) {
     const int src = (lane + 1) & 31;
     const float4 *a = sA + lane, *b = sB + lane;
 #pragma unroll(UNR)
@@ -122,15 +144,10 @@ __device__ __forceinline__ void sym_rotation(const float4 *__restrict__ sA, cons
         const float2 zj = make_float2(B.x, B.y), mj = make_float2(B.z, B.w);
 #pragma unroll
         for (int k = 0; k < IPT; ++k) {
-            const float2 dx = __fadd2_rn(xj, nx[k]);
-            const float2 dy = __fadd2_rn(yj, ny[k]);
-            const float2 dz = __fadd2_rn(zj, nz[k]);
-            float2 r2 = __ffma2_rn(dx, dx, e2);
-            r2 = __ffma2_rn(dy, dy, r2);
-            r2 = __ffma2_rn(dz, dz, r2);
-            const float2 inv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-            const float2 inv2 = __fmul2_rn(inv, inv);
-            const float2 w = __fmul2_rn(inv, inv2);
+            float2 dx = __fadd2_rn(xj, nx[k]);
+            float2 dy = __fadd2_rn(yj, ny[k]);
+            float2 dz = __fadd2_rn(zj, nz[k]);
+            const float2 w = P::weight(dx, dy, dz, e2, pa);
             const float2 wi = EQM ? w : __fmul2_rn(mj, w);
             px[k] = __ffma2_rn(dx, wi, px[k]);
             py[k] = __ffma2_rn(dy, wi, py[k]);
@@ -150,17 +167,18 @@ __device__ __forceinline__ void sym_rotation(const float4 *__restrict__ sA, cons
     }
 }
 
-// Persistent symmetric force kernel, FP32.  pk: pair-interleaved bodies
+// Persistent symmetric force kernel, FP32, for the pair term P (pa: its
+// parameters).  pk: pair-interleaved bodies
 // (N_pad a multiple of T).  part: row segments [n][S_max][PLANES][T] float4,
 // then from float4 offset L.col_off the column slots [slot][PLANES][T]
 // float4 (for COMP the second plane holds the low words).  EQM: every body
 // has mass mass_eq and no zero-mass padding enters; segments are scaled by
 // mass_eq.  Both the row and column sums are forces on the bodies they index
 // (the column slots are negated when written).
-template <int NT, int IPT, bool COMP, bool EQM, int UNR>
+template <int NT, int IPT, bool COMP, bool EQM, int UNR, class P = PlummerPair>
 __global__ void __launch_bounds__(NT, 1)
     force_sym_f32_kernel(const float *__restrict__ pk, float4 *__restrict__ part, int *__restrict__ flags,
-                         ForceLaunch L, float eps2, float mass_eq) {
+                         ForceLaunch L, float eps2, float mass_eq, typename P::Args pa) {
     using K = SymKernel<NT, IPT, COMP>;
     constexpr int NW = K::NW, T = K::T, TP = K::TP, PL = K::PLANES;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -263,8 +281,8 @@ __global__ void __launch_bounds__(NT, 1)
                 const float4 *bA = sA + 2 * base, *bB = sB + 2 * base;   // the block's doubled entries
                 float2 jx = make_float2(0.f, 0.f), jy = jx, jz = jx;
                 if (sym) {
-                    sym_rotation<IPT, true, EQM, UNR>(bA, bB, lane, nx, ny, nz, mi, e2, px, py, pz, jx, jy,
-                                                      jz);
+                    sym_rotation<P, IPT, true, EQM, UNR>(bA, bB, lane, nx, ny, nz, mi, e2, pa, px, py, pz,
+                                                         jx, jy, jz);
                     const int q = base + lane;
                     float2 *h = acc + q;
                     if (COMP) {
@@ -289,8 +307,8 @@ __global__ void __launch_bounds__(NT, 1)
                         h[2 * TP] = __fadd2_rn(h[2 * TP], jz);
                     }
                 } else {
-                    sym_rotation<IPT, false, EQM, UNR>(bA, bB, lane, nx, ny, nz, mi, e2, px, py, pz, jx, jy,
-                                                       jz);
+                    sym_rotation<P, IPT, false, EQM, UNR>(bA, bB, lane, nx, ny, nz, mi, e2, pa, px, py, pz,
+                                                          jx, jy, jz);
                 }
             }
 #pragma unroll

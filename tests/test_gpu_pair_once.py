@@ -238,3 +238,68 @@ def test_vjp_plan_kinds():
             assert sim.vjp_plan()["kind"] == kind, N
         finally:
             sim.close()
+
+
+# ---- the pair-once real-space kernel under periodic boundaries (Ewald
+# summation; 1024-body tiles, the built-in choice from 8 tiles on)
+
+def periodic_forces(x, m, eps, L, prec, shape=-1, a=1.0, G=1.0):
+    sim = B.Simulation(m, eps, LCDM_D, a, prec=prec, G=G)
+    try:
+        sim.set_state(x)
+        sim.set_tuning(shape)
+        sim.set_periodic(L)
+        return sim.forces(), sim.force_plan()
+    finally:
+        sim.close()
+
+
+@pytest.mark.parametrize("prec", [B.FP32, B.FP32_COMP])
+@pytest.mark.parametrize("N,equal", [(8192, True), (8192, False), (9001, False)])
+def test_periodic_pair_once_forces_match_oracle(N, equal, prec):
+    rng = np.random.default_rng(950 + N)
+    L = 2.5
+    x = inputs.f32(L * rng.random((N, 3)))
+    m = inputs.f32(np.full(N, 1.0 / N) if equal else rng.lognormal(0.0, 0.5, N) / N)
+    eps, a, G = 0.01, 0.5, 1.3
+    got, plan = periodic_forces(x, m, eps, L, prec, a=a, G=G)
+    n = -(-N // 1024)
+    assert plan["kind"] == "ewald_sym_f32" and plan["units"] == n * (n + 1) // 2
+    assert plan["eqm"] == (equal and N % 1024 == 0)
+    rows = np.sort(np.random.default_rng(N).choice(N, 512, replace=False))
+    ref = oracle.ewald_forces(x, m, eps, L, G, rows=rows) / a ** 3
+    # the FP32 real-space term carries the error of its erfc (Abramowitz &
+    # Stegun 7.1.26, 1.5e-7 absolute), which compensated sums do not remove:
+    # at 9001 lognormal bodies both real-space forms measure 2.6e-6 against
+    # the converged FP64 sum (FP64 1e-14), so the oracle bound is 5e-6 in
+    # both FP32 modes here; the two forms must agree far closer
+    assert rel_rms(got[rows], ref) < 5e-6
+    got0, plan0 = periodic_forces(x, m, eps, L, prec, shape=2, a=a, G=G)   # any shape but 3
+    assert plan0["kind"] == "ewald_f32"
+    assert rel_rms(got, got0) < (2e-6 if prec == B.FP32 else 5e-7)
+
+
+@pytest.mark.parametrize("scheme", ["kdk", "dkd"])
+def test_periodic_pair_once_steps_match_per_pair_kernel(scheme):
+    # 8192 bodies of the 32^3 recipe in a periodic unit box, 6 steps with
+    # either real-space form: the two differ only in the order of the pair sums
+    ic = inputs.perturbed_grid(21, 0.1, 0.02, 43, zeldovich=True, count=8192,
+                               total_mass=inputs.CRITICAL_MATTER_DENSITY)
+    out = []
+    for shape in (3, 2):   # any shape but 3 takes the per-ordered-pair kernel
+        sim = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START, prec=B.FP32_COMP,
+                           scheme=B.KDK if scheme == "kdk" else B.DKD)
+        try:
+            sim.set_state(ic.x, ic.v)
+            sim.set_tuning(shape)
+            sim.set_periodic(1.0)
+            kind = sim.force_plan()["kind"]
+            sim.step(TAU, 6)
+            out.append((kind,) + tuple(sim.state()[:2]))
+        finally:
+            sim.close()
+    (k3, x3, v3), (k0, x0, v0) = out
+    assert k3 == "ewald_sym_f32" and k0 == "ewald_f32"
+    assert np.abs(x3 - x0).max() < 1e-6
+    vn = np.sqrt(np.mean(np.sum(v0 ** 2, axis=1)))
+    assert np.sqrt(np.mean(np.sum((v3 - v0) ** 2, axis=1))) < 5e-6 * vn
