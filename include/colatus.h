@@ -312,9 +312,10 @@ colatus_status colatus_profile_read_kinds(colatus_t ctx, double out[6]);
  * 3 = 512 x 4 on 2048-body tiles with every pair evaluated once and applied
  * to both bodies (Newton's third law: the same sum with about two thirds of
  * the arithmetic).  Shape 3 fits from 2 tiles (N > 2048) while its partial
- * sums, about N^2 / 2048 x 16 bytes (x 2 compensated), stay within 4 GiB
- * (N up to about 2^19); it is the built-in choice from 8 tiles (N > 14336)
- * on.  colatus_autotune times reps launches of every shape that fits N on
+ * sums, about N^2 / 2048 x 8 bytes (x 2 compensated), take at most an eighth
+ * of the device's memory (on a 288 GB B300: 17 GB at N = 2^21 in FP32, 34 GB
+ * compensated); it is the built-in choice from 8 tiles (N > 14336) on, and
+ * shape 0 the choice that needs no such buffer.  colatus_autotune times reps launches of every shape that fits N on
  * the current state (for the context's FP32 precision and mass type), keeps
  * the fastest for this context and returns it in *chosen; out_ms[4] (may be
  * NULL) receives the mean milliseconds per launch (0 for shapes that do not

@@ -40,10 +40,12 @@ constexpr int kShapes = 4;
 constexpr int kSymShape = 3;
 constexpr int kSymNT = 512, kSymIPT = 4, kSymUnr = 8;
 // The pair-once shape is the built-in choice from this many tiles up (fewer
-// tiles leave most CTAs less than one unit) and while its partial sums fit
-// kSymMaxBytes (they grow as N^2 / T: one column slot per tile pair).
+// tiles leave most CTAs less than one unit) and while its partial sums take
+// at most 1/kSymMemShare of the device's memory (they grow as N^2 / T: one
+// column slot per tile pair; 17 GB in FP32 at 2^21 bodies, an eighth of a
+// B300's 288 GB less 2 %).
 constexpr int kSymMinTiles = 8;
-constexpr size_t kSymMaxBytes = (size_t)4 << 30;
+constexpr int kSymMemShare = 8;
 
 struct F32Variant {
     int nt, ipt, jt;
@@ -236,6 +238,7 @@ struct colatus_ctx {
     bool own_stream = false;
 
     long long N = 0, n_alloc = 0;
+    size_t sym_max_bytes = 0;      // largest partial-sum buffer of a pair-once plan
     double eps = 0.0, G = 1.0;
     Cosmo cosmo{};
     colatus_prec prec = COLATUS_FP32;
@@ -440,6 +443,14 @@ colatus_status launched(colatus_t ctx) {
 }
 
 // ---- plans
+// Whether a pair-once plan of tiles of T bodies (pl planes) could fit the
+// partial-sum budget: its column slots alone, one per tile pair it < jt.
+bool sym_may_fit(colatus_t ctx, long long n_pad, int T, int pl) {
+    const long long n = n_pad / T;
+    const double slots = 0.5 * (double)n * (double)(n - 1);
+    return n >= 2 && slots * pl * T * sizeof(float4) <= (double)ctx->sym_max_bytes;
+}
+
 colatus_status build_plans(colatus_t ctx) {
     SymTables st;
     for (int v = 0; v < NUM_F32_VARIANTS; ++v) {
@@ -461,11 +472,16 @@ colatus_status build_plans(colatus_t ctx) {
         }
         // pair-once plan: one set of tables for all four variants, the phase
         // costs of the equal-mass form (11 lane-ops per diagonal interaction,
-        // 14 per symmetric pair), on all SMs but the schedule kernel's
+        // 14 per symmetric pair), on all SMs but the schedule kernel's; not
+        // built when even its column slots alone would not fit
+        const int pl = fv.comp ? 2 : 1;
+        if (!sym_may_fit(ctx, p.n_pad, p.itile, pl)) {
+            p.fits = false;
+            continue;
+        }
         if (st.tab.empty())
             st = build_sym_tables(p.n_pad, p.itile, kSymNT / 32, (long long)occ * std::max(1, ctx->num_sms - 1),
                                   11, 14);
-        const int pl = fv.comp ? 2 : 1;
         p.L = ForceLaunch{};
         p.L.W = st.U;
         p.L.n_it = p.L.n_jt = st.n;
@@ -473,7 +489,7 @@ colatus_status build_plans(colatus_t ctx) {
         p.L.S_max = st.S_row;
         p.L.col_off = (long long)st.n * st.S_row * pl * p.itile;
         p.part_bytes = (size_t)((long long)st.n * st.S_row + st.slots) * pl * p.itile * sizeof(float4);
-        p.fits = st.n >= 2 && p.part_bytes <= kSymMaxBytes;
+        p.fits = st.n >= 2 && p.part_bytes <= ctx->sym_max_bytes;
     }
     if (!st.tab.empty()) {
         CU(cudaMalloc(&ctx->sym_tab, st.tab.size() * sizeof(int)));
@@ -512,8 +528,10 @@ colatus_status build_plans(colatus_t ctx) {
         ForcePlan &q = ctx->plan_vjp_sym;
         q.itile = q.jt = VjpSymK::T;
         q.n_pad = round_up(ctx->N, VjpSymK::T);
-        const SymTables st = build_sym_tables(q.n_pad, VjpSymK::T, VjpSymK::NW,
-                                              (long long)occ * std::max(1, ctx->num_sms - 1), 23, 27);
+        const bool may = sym_may_fit(ctx, q.n_pad, VjpSymK::T, 1);
+        const SymTables st = may ? build_sym_tables(q.n_pad, VjpSymK::T, VjpSymK::NW,
+                                                    (long long)occ * std::max(1, ctx->num_sms - 1), 23, 27)
+                                 : SymTables{};
         q.L = ForceLaunch{};
         q.L.W = st.U;
         q.L.n_it = q.L.n_jt = st.n;
@@ -521,7 +539,7 @@ colatus_status build_plans(colatus_t ctx) {
         q.L.S_max = st.S_row;
         q.L.col_off = (long long)st.n * st.S_row * q.itile;
         q.part_bytes = (size_t)((long long)st.n * st.S_row + st.slots) * q.itile * sizeof(float4);
-        q.fits = st.n >= kSymMinTiles && q.part_bytes <= kSymMaxBytes;
+        q.fits = may && st.n >= kSymMinTiles && q.part_bytes <= ctx->sym_max_bytes;
         if (q.fits) {
             CU(cudaMalloc(&ctx->vjp_sym_tab, st.tab.size() * sizeof(int)));
             CU(cudaMemcpy(ctx->vjp_sym_tab, st.tab.data(), st.tab.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -581,6 +599,10 @@ colatus_status build_plans(colatus_t ctx) {
             ForcePlan &q = ctx->plan_ew_sym[comp];
             q.itile = q.jt = EwSymK::T;
             q.n_pad = round_up(ctx->N, EwSymK::T);
+            if (!sym_may_fit(ctx, q.n_pad, EwSymK::T, comp + 1)) {
+                q.fits = false;
+                continue;
+            }
             if (st.tab.empty())
                 st = build_sym_tables(q.n_pad, EwSymK::T, EwSymK::NW,
                                       (long long)occ * std::max(1, ctx->num_sms - 1), 35, 38);
@@ -591,14 +613,12 @@ colatus_status build_plans(colatus_t ctx) {
             q.L.S_max = st.S_row;
             q.L.col_off = (long long)st.n * st.S_row * (comp + 1) * q.itile;
             q.part_bytes = (size_t)((long long)st.n * st.S_row + st.slots) * (comp + 1) * q.itile * sizeof(float4);
-            q.fits = st.n >= kSymMinTiles && q.part_bytes <= kSymMaxBytes;
+            q.fits = st.n >= kSymMinTiles && q.part_bytes <= ctx->sym_max_bytes;
         }
-        if (ctx->plan_ew_sym[1].fits) {
+        if (ctx->plan_ew_sym[0].fits || ctx->plan_ew_sym[1].fits) {
             CU(cudaMalloc(&ctx->ew_sym_tab, st.tab.size() * sizeof(int)));
             CU(cudaMemcpy(ctx->ew_sym_tab, st.tab.data(), st.tab.size() * sizeof(int), cudaMemcpyHostToDevice));
             ctx->plan_ew_sym[0].L.sym = ctx->plan_ew_sym[1].L.sym = ctx->ew_sym_tab;
-        } else {
-            ctx->plan_ew_sym[0].fits = false;
         }
     }
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -1695,6 +1715,7 @@ colatus_status colatus_init(colatus_t *out, int64_t N, const double *masses, dou
         return bail(COLATUS_E_CUDA);
     }
     ctx->num_sms = prop.multiProcessorCount;
+    ctx->sym_max_bytes = prop.totalGlobalMem / kSymMemShare;
     ctx->tab_smem = (int)prop.sharedMemPerBlockOptin;
     if ((e = cudaFuncSetAttribute(friedmann_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   ctx->tab_smem)) != cudaSuccess) {
