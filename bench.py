@@ -37,16 +37,34 @@ FLOPS_PER_INTERACTION = 20          # Nyland et al. convention
 FP32_FLOP_PER_CLK_PER_SM = 256      # 128 FP32 lanes x FMA
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the 32^3 compensated equal-mass force kernel, from one ncu capture.  The
-# figure is reported only while the launched kernel has the captured shape and
-# its source files hash to the captured sources; otherwise traffic is null.
+# the 32^3 compensated equal-mass force kernel (the pair-once shape), from one
+# ncu capture.  The figure is reported only while the launched kernel has the
+# captured shape and its source files hash to the captured sources; otherwise
+# traffic is null.
 FORCE_KERNEL_TRAFFIC = {
-    "bytes": 540928,
-    "plan": dict(kind="force_f32", threads=512, ipt=4, jt=512, comp=True, eqm=True, nrcp=0),
-    "template": "force_f32_kernel<512, 4, 512, 4, 256, true, true, 1, 2, 0>",
-    "sources": ("paper_1208_3444_b300/csrc/force.cuh", "paper_1208_3444_b300/csrc/common.cuh"),
-    "sha256": "2a110c0e30d0ac10ca7214f3d281a896d648893e1486b1e3e8fae41e00051357",
+    "bytes": 564736,
+    "plan": dict(kind="force_sym_f32", threads=512, ipt=4, jt=2048, comp=True, eqm=True, nrcp=0),
+    "template": "force_sym_f32_kernel<512, 4, 1, 1, 8, PlummerPair>",
+    "sources": ('paper_1208_3444_b300/csrc/force_sym.cuh', 'paper_1208_3444_b300/csrc/force.cuh', 'paper_1208_3444_b300/csrc/common.cuh'),
+    "sha256": "80ba764fcd0a34e73e25fdf8147e3041c8ada110b2c5d063733fb1715b10e8af",
 }
+
+
+def pair_lane_ops(plan, N):
+    """FP32 lane-ops of the pair arithmetic per counted interaction (N^2 per
+    force) for the launched force kernel: 11 (equal masses) or 12 per ordered
+    pair; the pair-once form 14 or 16 per pair in the tile pairs it < jt and
+    11 or 12 per ordered pair in the diagonal tiles, over the padded bodies."""
+    eqm = plan.get("eqm")
+    one, both = (11, 14) if eqm else (12, 16)
+    t = plan["jt"]
+    if plan.get("kind") == "force_sym_f32":
+        n = -(-N // t)
+        work = ((n * (n + 1) // 2 - n) * both + n * one) * float(t) * t
+    else:
+        npad = -(-N // max(t, plan["threads"] * plan["ipt"])) * max(t, plan["threads"] * plan["ipt"])
+        work = one * float(npad) * npad
+    return work / (float(N) * N)
 
 
 def source_hash(paths):
@@ -257,6 +275,7 @@ def time_force_128(B, inputs, torch, launches=3):
     out = torch.empty((ic.N, 3), dtype=torch.float32, device="cuda")
     try:
         sim.set_state(ic.x)
+        plan = sim.force_plan()
         sim.forces(out)
         sim.synchronize()
         sim.profile_forces(True)
@@ -267,7 +286,7 @@ def time_force_128(B, inputs, torch, launches=3):
     finally:
         sim.close()
     return {"N": ic.N, "launches": n, "ms_per_launch": ms / n,
-            "interactions_per_s": ic.N * ic.N * n / (ms * 1e-3), "prec": "fp32"}
+            "interactions_per_s": ic.N * ic.N * n / (ms * 1e-3), "prec": "fp32", "plan": plan}
 
 
 def time_adjoint(B, inputs, torch, stream, nsteps=200, k=20):
@@ -665,10 +684,19 @@ def run_colatus(args, ws, rank, local):
                 "peak_basis": f"{nsm} SMs x {FP32_FLOP_PER_CLK_PER_SM} FP32 flop/clk x "
                               f"{f_mhz:.0f} MHz (median sampled SM clock); 20 flop/interaction",
                 "frac_at_max_clock": achieved / (nsm * FP32_FLOP_PER_CLK_PER_SM * fmax * 1e6 / 1e12),
-                "ms_per_launch": force_ms / nforce}
+                "ms_per_launch": force_ms / nforce,
+                # the same rate against the FP32 pipe: lane-ops the launched
+                # kernel's pair arithmetic needs per counted interaction (fewer
+                # than the convention's 20 flops when every pair is evaluated
+                # once, so frac may exceed 1 while the pipe stays below it)
+                "fp32_lane_ops_per_interaction": pair_lane_ops(plan, N),
+                "fp32_lane_op_frac": achieved_int / (nsm * f_mhz * 1e6) * pair_lane_ops(plan, N) / 128.0}
         if force128:
             a128 = force128["interactions_per_s"]
             force128["frac"] = a128 * FLOPS_PER_INTERACTION / 1e12 / peak
+            ops128 = pair_lane_ops(force128["plan"], force128["N"])
+            force128["fp32_lane_ops_per_interaction"] = ops128
+            force128["fp32_lane_op_frac"] = a128 / (nsm * f_mhz * 1e6) * ops128 / 128.0
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
             "warmup": W, "ms_per_step": step_ms_max / K, "higher_is_better": True,
@@ -703,6 +731,8 @@ def run_colatus(args, ws, rank, local):
             "force_128cubed_frac": force128["frac"] if force128 else None,
             "force_128cubed_ms": force128["ms_per_launch"] if force128 else None,
             "force_128cubed_interactions_per_s": force128["interactions_per_s"] if force128 else None,
+            "force_32cubed_fp32_lane_op_frac": roof["fp32_lane_op_frac"],
+            "force_128cubed_fp32_lane_op_frac": force128["fp32_lane_op_frac"] if force128 else None,
             "adjoint_step_over_forward_step": adjoint["adjoint_step_over_forward_step"],
             "vjp_frac_of_lane_op_floor": adjoint["vjp_frac_of_lane_op_floor"],
             "ensemble_frac_of_fp32_roofline": ensemble["frac_of_fp32_roofline"],
