@@ -389,7 +389,8 @@ def time_ensemble(B, inputs, torch, stream, nsteps=48):
             "ms_per_step": ms / nsteps, "interactions_per_s": pairs * nsteps / (ms * 1e-3),
             "graph_launches": nsteps // 16, "kernel_launches": st["launches"] - l0,
             "autotune": {"shape": shape, "ms_per_force": [round(float(t), 4) for t in tune_ms],
-                         "shapes": ["128x2, 4 CTAs/SM", "256x1, 4 CTAs/SM", "64x4, 8 CTAs/SM"]},
+                         "shapes": ["128x2, 4 CTAs/SM", "256x1, 4 CTAs/SM", "64x4, 8 CTAs/SM",
+                                    "128x4 on 512-body tiles, every pair once, 4 CTAs/SM"]},
             "interactions_per_sm_per_clk": pairs * nsteps / (ms * 1e-3) /
             (torch.cuda.get_device_properties(0).multi_processor_count * 2.032e9),
             "frac_of_fp32_roofline": pairs * nsteps / (ms * 1e-3) /

@@ -441,17 +441,23 @@ colatus_status colatus_ensemble_read_tracers(colatus_ens_t e, float *xv_out, int
  * out[4]/out[5] milliseconds/number of force launches timed outside graphs
  * since the last call; profile_on switches that timing on or off. */
 colatus_status colatus_ensemble_stats(colatus_ens_t e, int profile_on, double out[6]);
-/* Ensemble force-kernel tuning.  The kernel exists in three CTA shapes with
- * the same 256-body tiles (0: 128 threads x 2 bodies, 4 CTAs per SM; 1: 256 x 1,
- * 4 per SM; 2: 64 x 4, 8 per SM, the built-in choice).  colatus_ensemble_autotune times reps force
- * evaluations of every shape at the current state (state required; one
- * untimed launch first), writes the milliseconds per evaluation to out_ms[k]
- * (may be NULL), keeps the fastest and returns its index in *chosen (may be
- * NULL).  colatus_ensemble_set_tuning applies a known choice (-1: shape 2).
+/* Ensemble force-kernel tuning.  The kernel exists in four CTA shapes: three
+ * with the same 256-body tiles (0: 128 threads x 2 bodies, 4 CTAs per SM;
+ * 1: 256 x 1, 4 per SM; 2: 64 x 4, 8 per SM) and 3: 128 x 4 on 512-body
+ * tiles of each realisation with every pair evaluated once and applied to
+ * both bodies (Newton's third law), usable while its partial sums take at
+ * most an eighth of the device memory; shape 3 is the built-in choice where
+ * it is usable, else shape 2.
+ * colatus_ensemble_autotune times reps force evaluations of every usable
+ * shape at the current state (state required; one untimed launch first),
+ * writes the milliseconds per evaluation to out_ms[k] (0 for a shape that is
+ * not usable; out_ms may be NULL), keeps the fastest and returns its index
+ * in *chosen (may be NULL).  colatus_ensemble_set_tuning applies a known
+ * choice (-1: the built-in one; COLATUS_E_ARG for a shape that is not usable).
  * Either call synchronises the stream, drops the captured step graphs and
  * recomputes the step opening at the next colatus_ensemble_step; results
  * then follow the new shape's summation order (deterministic per shape). */
-colatus_status colatus_ensemble_autotune(colatus_ens_t e, int reps, double out_ms[3], int *chosen);
+colatus_status colatus_ensemble_autotune(colatus_ens_t e, int reps, double out_ms[4], int *chosen);
 colatus_status colatus_ensemble_set_tuning(colatus_ens_t e, int shape);
 const char *colatus_ensemble_last_error(colatus_ens_t e);
 void colatus_ensemble_destroy(colatus_ens_t e);

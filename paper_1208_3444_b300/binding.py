@@ -657,7 +657,7 @@ class Ensemble:
     def autotune(self, reps=3):
         """Time the force kernel's CTA shapes at the current state and keep
         the fastest: (milliseconds per evaluation of each shape, chosen)."""
-        ms = np.zeros(3)
+        ms = np.zeros(4)
         ch = ctypes.c_int(-1)
         _echeck(lib().colatus_ensemble_autotune(self.h, int(reps), ms.ctypes.data, ctypes.byref(ch)),
                 self.h)

@@ -11,6 +11,7 @@
 #include "colatus.h"
 #include "common.cuh"
 #include "diagnostics.cuh"
+#include "ens_sym.cuh"
 #include "ensemble.cuh"
 #include "ewald.cuh"
 #include "ewald_adjoint.cuh"

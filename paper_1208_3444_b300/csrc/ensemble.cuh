@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "force.cuh"
+#include "force_sym.cuh"
 #include "integrate.cuh"
 
 namespace colatus {
@@ -38,7 +39,14 @@ struct EnsLaunch {
     const int *tile_r;              // [T]   realisation of global i-tile t
     const long long *tile_u0;       // [T]   first unit of global i-tile t
     const float *meq;               // [R]   equal mass of realisation r (equal-mass kernel), or null
+    // the pair-once plan (ens_sym.cuh) only, else null / 0: its tables and
+    // the float4 offset of its column slots in the segment buffer
+    const int *sym;
+    long long sym_col_off;
 };
+
+constexpr int kEnsSymT = 512;   // bodies per tile of the pair-once plan
+
 
 constexpr float kEnsFar = 0x1p100f;   // coordinate of the padding bodies
 
@@ -157,20 +165,87 @@ __global__ void __launch_bounds__(NT, MINB)
     }
 }
 
+// Int tables of the ensemble's pair-once plan (EnsLaunch::sym):
+//   [0] R, [1] NW, [2] U tile pairs in all, [3] G CTAs, [4] TT tiles in all,
+//   [kSymHdr ...] ub[R + 1] (first tile pair of realisation r),
+//                 tb[R + 1] (first tile of realisation r),
+//                 row_g0[TT], row_ns[TT], unit_g0[U], unit_ko[U], unit_nk[U],
+//                 cta_pu[G + 1]
+// with the meanings of force_sym.cuh, tiles and tile pairs numbered over all
+// realisations.
+struct EnsSymTab {
+    const int *ub, *tb, *row_g0, *row_ns, *unit_g0, *unit_ko, *unit_nk, *cta_pu;
+    int R, NW, U, G, TT;
+    __host__ __device__ explicit EnsSymTab(const int *t) {
+        R = t[0];
+        NW = t[1];
+        U = t[2];
+        G = t[3];
+        TT = t[4];
+        ub = t + kSymHdr;
+        tb = ub + R + 1;
+        row_g0 = tb + R + 1;
+        row_ns = row_g0 + TT;
+        unit_g0 = row_ns + TT;
+        unit_ko = unit_g0 + U;
+        unit_nk = unit_ko + U;
+        cta_pu = unit_nk + U;
+    }
+};
+
+// Epilogue side: the (G-less, mass-free for EQM) force sum of body i (global
+// padded index, realisation r) of the pair-once plan with tiles of T bodies:
+// the row segments of its tile, then the column slots of the tile pairs
+// (t', t), t' < t, in that fixed order.
+__device__ __forceinline__ float3 ens_reduce_sym(const float4 *__restrict__ part, const EnsLaunch &E, int r,
+                                                 long long i, int T) {
+    const EnsSymTab S(E.sym);
+    const long long l = i - E.body_off[r];
+    const int t = (int)(l / T), il = (int)(l - (long long)t * T);
+    const int gt = S.tb[r] + t, nr = S.tb[r + 1] - S.tb[r];
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    const float4 *p = part + (long long)gt * E.S_max * T + il;
+    for (int s = 0; s < S.row_ns[gt]; ++s) {
+        const float4 v = __ldg(p + (long long)s * T);
+        fx += v.x;
+        fy += v.y;
+        fz += v.z;
+    }
+    const float4 *c = part + E.sym_col_off + il;
+    for (int tp = 0; tp < t; ++tp) {
+        const int uu = S.ub[r] + (int)sym_row_u0(tp, nr) + (t - tp);
+        const int ko = S.unit_ko[uu], nk = S.unit_nk[uu];
+        for (int k = 0; k < nk; ++k) {
+            const float4 v = __ldg(c + (long long)(ko + k) * T);
+            fx += v.x;
+            fy += v.y;
+            fz += v.z;
+        }
+    }
+    return make_float3(fx, fy, fz);
+}
+
 // Segment sum of body i (global padded index) in CTA order.
 __device__ __forceinline__ float3 ens_reduce(const float4 *__restrict__ part, const EnsLaunch &E,
                                              int itile, long long i) {
     const long long t = i / itile, il = i - t * itile;
     const int r = E.tile_r[t];
-    const long long g0 = sk_owner(E.tile_u0[t], E.W, E.G);
-    const long long g1 = sk_owner(E.tile_u0[t] + E.n_jt[r] - 1, E.W, E.G);
-    const float4 *p = part + t * E.S_max * (long long)itile + il;
     float fx = 0.f, fy = 0.f, fz = 0.f;
-    for (long long s = 0; s <= g1 - g0; ++s) {
-        const float4 v = __ldg(p + s * itile);
-        fx += v.x;
-        fy += v.y;
-        fz += v.z;
+    if (E.sym) {
+        const float3 f = ens_reduce_sym(part, E, r, i, kEnsSymT);   // each pair evaluated once
+        fx = f.x;
+        fy = f.y;
+        fz = f.z;
+    } else {
+        const long long g0 = sk_owner(E.tile_u0[t], E.W, E.G);
+        const long long g1 = sk_owner(E.tile_u0[t] + E.n_jt[r] - 1, E.W, E.G);
+        const float4 *p = part + t * E.S_max * (long long)itile + il;
+        for (long long s = 0; s <= g1 - g0; ++s) {
+            const float4 v = __ldg(p + s * itile);
+            fx += v.x;
+            fy += v.y;
+            fz += v.z;
+        }
     }
     if (E.meq) {
         const float m = E.meq[r];

@@ -23,14 +23,21 @@ constexpr int kEnsChunk = 16;           // steps per captured graph (even: ping-
 static_assert(kEnsTile == kEnsJT, "ensemble tiles pad realisations to one size");
 
 // CTA shapes of the ensemble force kernel (threads x i-bodies per thread,
-// CTAs per SM), all with 256-body i- and j-tiles, so that the padding and the
-// unit list do not depend on the shape.  Shape kEnsDefault is the built-in choice;
-// colatus_ensemble_autotune times all of them on the ensemble at hand.
-constexpr int kEnsShapes = 3, kEnsDefault = 2;
+// CTAs per SM): 0-2 with 256-body i- and j-tiles, so that the padding and the
+// unit list do not depend on the shape; 3 evaluates every pair once on
+// 512-body tiles of each realisation (ens_sym.cuh, its own work list over the
+// same storage).  The built-in choice is shape 3 where it fits (26 % faster
+// than shape 2 on the 64-realisation ensemble: 2.72 against 3.69 ms per
+// force), else kEnsDefault; colatus_ensemble_autotune times all of them on
+// the ensemble at hand.
+constexpr int kEnsShapes = 4, kEnsDefault = 2, kEnsSymShape = 3;
+constexpr int kEnsSymNT = 128, kEnsSymMinB = 4, kEnsSymUnr = 8;
+using EnsSymK = EnsSymKernel<kEnsSymNT>;
 struct EnsVariant {
     int nt;
     const void *fn[2];   // general masses, equal masses
     void (*launch[2])(int grid, cudaStream_t, const float *, float4 *, int *, EnsLaunch);
+    int smem;
 };
 
 template <int NT, int IPT, int MINB, int NRCP, bool EQM>
@@ -47,14 +54,25 @@ EnsVariant make_ens() {
     return EnsVariant{NT,
                       {(const void *)ens_force_kernel<NT, IPT, kEnsJT, kStages, kEnsFold, MINB, false, NRCP>,
                        (const void *)ens_force_kernel<NT, IPT, kEnsJT, kStages, kEnsFold, MINB, true, NRCP>},
-                      {&ens_launch<NT, IPT, MINB, NRCP, false>, &ens_launch<NT, IPT, MINB, NRCP, true>}};
+                      {&ens_launch<NT, IPT, MINB, NRCP, false>, &ens_launch<NT, IPT, MINB, NRCP, true>},
+                      EnsK::SMEM};
+}
+
+template <bool EQM>
+void ens_sym_launch(int grid, cudaStream_t st, const float *pk, float4 *part, int *flags, EnsLaunch E) {
+    ens_sym_force_kernel<kEnsSymNT, kEnsSymMinB, EQM, kEnsSymUnr><<<grid, kEnsSymNT, EnsSymK::SMEM, st>>>(pk, part, flags, E);
 }
 
 // 64 x 4 takes one rcp per four i-bodies: 3.69 ms per force on the
 // 64-realisation ensemble against 3.80 without it (and 3.75 for 128 x 2)
 const EnsVariant &ens_variant(int s) {
-    static const EnsVariant table[kEnsShapes] = {make_ens<128, 2, 4>(), make_ens<256, 1, 4>(),
-                                                 make_ens<64, 4, 8, 1>()};
+    static const EnsVariant table[kEnsShapes] = {
+        make_ens<128, 2, 4>(), make_ens<256, 1, 4>(), make_ens<64, 4, 8, 1>(),
+        EnsVariant{kEnsSymNT,
+                   {(const void *)ens_sym_force_kernel<kEnsSymNT, kEnsSymMinB, false, kEnsSymUnr>,
+                    (const void *)ens_sym_force_kernel<kEnsSymNT, kEnsSymMinB, true, kEnsSymUnr>},
+                   {&ens_sym_launch<false>, &ens_sym_launch<true>},
+                   EnsSymK::SMEM}};
     return table[s];
 }
 
@@ -73,7 +91,9 @@ struct colatus_ensemble {
     EnsLaunch E{};
     int shape = kEnsDefault;               // CTA shape of the force kernel (ens_variant)
     colatus_scheme scheme = COLATUS_KDK;   // colatus_ensemble_set_scheme
-    int shape_G[kEnsShapes] = {0}, shape_S[kEnsShapes] = {0};   // grid and S_max per shape
+    int shape_G[kEnsShapes] = {0}, shape_S[kEnsShapes] = {0};   // grid and S_max per shape (0: unusable)
+    int *sym_tab = nullptr;                // tables of the pair-once shape
+    long long sym_col_off = 0;
     void *meta = nullptr;                  // device descriptor arrays
     long long *d_user_off = nullptr;
     float4 *xs = nullptr, *vs = nullptr, *vh = nullptr, *acc = nullptr;
@@ -294,18 +314,29 @@ void ens_free(colatus_ens_t e) {
         if (g) cudaGraphExecDestroy(g);
     for (cudaEvent_t v : e->ev) cudaEventDestroy(v);
     void *ptrs[] = {e->meta, e->xs, e->vs, e->vh, e->acc, e->pk[0], e->pk[1], e->pk[2],
-                    e->part, e->flags, e->clk, e->table, e->stage, e->stage2, e->tslot, e->rec};
+                    e->part, e->flags, e->clk, e->table, e->stage, e->stage2, e->tslot, e->rec,
+                    e->sym_tab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
 }
 
-// Use CTA shape sh from now on: its grid and segment layout, new graphs, and
-// a new opening force (the old one was summed in the other shape's order).
-void ens_set_shape(colatus_ens_t e, int sh) {
+// The built-in shape: every pair once where it fits.
+int ens_default_shape(colatus_ens_t e) { return e->shape_G[kEnsSymShape] > 0 ? kEnsSymShape : kEnsDefault; }
+
+// The launch geometry and segment layout of CTA shape sh.
+void ens_apply_shape(colatus_ens_t e, int sh) {
     e->shape = sh;
     e->E.G = e->shape_G[sh];
     e->E.S_max = e->shape_S[sh];
+    e->E.sym = sh == kEnsSymShape ? e->sym_tab : nullptr;
+    e->E.sym_col_off = sh == kEnsSymShape ? e->sym_col_off : 0;
+}
+
+// Use CTA shape sh from now on: its grid and segment layout, new graphs, and
+// a new opening force (the old one was summed in the other shape's order).
+void ens_set_shape(colatus_ens_t e, int sh) {
+    ens_apply_shape(e, sh);
     for (cudaGraphExec_t &g : e->graph)
         if (g) {
             cudaGraphExecDestroy(g);
@@ -393,13 +424,41 @@ colatus_status colatus_ensemble_init(colatus_ens_t *out, int R, const int64_t *N
     E.T = T;
     // grid and segment count of every shape; part is sized for the largest
     long long smax = 1;
+    size_t part_bytes = 0;
+    EnsSymTables sym;
     for (int sh = 0; sh < kEnsShapes; ++sh) {
         const EnsVariant &v = ens_variant(sh);
         int occ = 0, occ2 = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn[0], v.nt, EnsK::SMEM) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, v.fn[1], v.nt, EnsK::SMEM) != cudaSuccess ||
+        if (v.smem > 48 * 1024 &&
+            (cudaFuncSetAttribute(v.fn[0], cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem) != cudaSuccess ||
+             cudaFuncSetAttribute(v.fn[1], cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem) != cudaSuccess))
+            return bail(efail(e, COLATUS_E_CUDA, "ensemble force kernel (shape %d): shared memory", sh));
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn[0], v.nt, v.smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, v.fn[1], v.nt, v.smem) != cudaSuccess ||
             std::min(occ, occ2) < 1)
             return bail(efail(e, COLATUS_E_CUDA, "ensemble force kernel (shape %d) cannot be resident", sh));
+        if (sh == kEnsSymShape) {
+            // every pair once: the tile pairs of 512-body tiles per realisation,
+            // phases split by the cost of the kernel's form (lane-ops per
+            // diagonal interaction and per symmetric pair); not usable if its
+            // partial sums would take more than an eighth of the device memory
+            std::vector<int> nt_r(R);
+            for (int r = 0; r < R; ++r)
+                nt_r[r] = (int)((e->body_off[r + 1] - e->body_off[r] + kEnsSymT - 1) / kEnsSymT);
+            sym = build_ens_sym_tables(nt_r, EnsSymK::NW, (long long)std::min(occ, occ2) * e->num_sms,
+                                       eqm ? 11 : 12, eqm ? 14 : 16);
+            const size_t b = (size_t)((long long)sym.TT * sym.S_row + sym.slots) * kEnsSymT * sizeof(float4);
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess)
+                return bail(efail(e, COLATUS_E_CUDA, "cudaMemGetInfo failed"));
+            if (b <= total_b / 8) {
+                e->shape_G[sh] = sym.G;
+                e->shape_S[sh] = sym.S_row;
+                e->sym_col_off = (long long)sym.TT * sym.S_row * kEnsSymT;
+                part_bytes = std::max(part_bytes, b);
+            }
+            continue;
+        }
         const long long G = std::min<long long>((long long)std::min(occ, occ2) * e->num_sms, E.W);
         long long sm = 1;
         for (int t = 0; t < T; ++t) {
@@ -411,6 +470,7 @@ colatus_status colatus_ensemble_init(colatus_ens_t *out, int R, const int64_t *N
         e->shape_S[sh] = (int)sm;
         smax = std::max(smax, sm);
     }
+    part_bytes = std::max(part_bytes, (size_t)((long long)T * smax * kEnsTile) * sizeof(float4));
     E.G = e->shape_G[kEnsDefault];
     E.S_max = e->shape_S[kEnsDefault];
     // device memory
@@ -422,7 +482,7 @@ colatus_status colatus_ensemble_init(colatus_ens_t *out, int R, const int64_t *N
               A((void **)&e->vh, np * 16) && A((void **)&e->acc, np * 16) &&
               A((void **)&e->pk[0], np * 16) && A((void **)&e->pk[1], np * 16) &&
               A((void **)&e->pk[2], np * 16) &&
-              A((void **)&e->part, (size_t)T * smax * kEnsTile * sizeof(float4)) &&
+              A((void **)&e->part, part_bytes) &&
               A((void **)&e->flags, NUM_FLAGS * sizeof(int)) && A((void **)&e->clk, sizeof(DevClock)) &&
               A((void **)&e->table, (kEnsChunk + 1) * sizeof(StepCoef)) &&
               A((void **)&e->stage, (size_t)e->Ntot * 3 * sizeof(double)) &&
@@ -458,6 +518,12 @@ colatus_status colatus_ensemble_init(colatus_ens_t *out, int R, const int64_t *N
     E.meq = eqm ? reinterpret_cast<const float *>(put(meq.data(), sizeof(float) * R)) : nullptr;
     colatus_status st = COLATUS_OK;
     cudaError_t ce = cudaMemcpy(e->meta, hm.data(), meta_bytes, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess && e->shape_G[kEnsSymShape] > 0) {
+        ce = cudaMalloc((void **)&e->sym_tab, sym.tab.size() * sizeof(int));
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy(e->sym_tab, sym.tab.data(), sym.tab.size() * sizeof(int), cudaMemcpyHostToDevice);
+    }
+    if (ce == cudaSuccess) ens_apply_shape(e, ens_default_shape(e));
     DevClock clk{0.0, a_start, 0, 0};
     if (ce == cudaSuccess) ce = cudaMemcpy(e->clk, &clk, sizeof(clk), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemset(e->flags, 0, NUM_FLAGS * sizeof(int));
@@ -705,12 +771,13 @@ colatus_status colatus_ensemble_set_tuning(colatus_ens_t e, int shape) {
     if (!e) return COLATUS_E_ARG;
     DeviceGuard dg(e->device);
     if (shape < -1 || shape >= kEnsShapes) return efail(e, COLATUS_E_ARG, "shape must be -1 .. %d", kEnsShapes - 1);
+    if (shape >= 0 && e->shape_G[shape] < 1) return efail(e, COLATUS_E_ARG, "shape %d does not fit", shape);
     TRY(ens_check(e, true));
-    ens_set_shape(e, shape < 0 ? kEnsDefault : shape);
+    ens_set_shape(e, shape < 0 ? ens_default_shape(e) : shape);
     return COLATUS_OK;
 }
 
-colatus_status colatus_ensemble_autotune(colatus_ens_t e, int reps, double out_ms[3], int *chosen) {
+colatus_status colatus_ensemble_autotune(colatus_ens_t e, int reps, double out_ms[4], int *chosen) {
     if (!e) return COLATUS_E_ARG;
     DeviceGuard dg(e->device);
     if (reps < 1) return efail(e, COLATUS_E_ARG, "reps must be >= 1");
@@ -726,9 +793,9 @@ colatus_status colatus_ensemble_autotune(colatus_ens_t e, int reps, double out_m
     const bool prof = e->profiling;
     e->profiling = false;
     for (int sh = 0; sh < kEnsShapes && st == COLATUS_OK; ++sh) {
-        e->E.G = e->shape_G[sh];
-        e->E.S_max = e->shape_S[sh];
-        e->shape = sh;
+        ms[sh] = 0.0;
+        if (e->shape_G[sh] < 1) continue;   // does not fit
+        ens_apply_shape(e, sh);
         st = ens_force(e, e->pk[2]);   // warm-up (lazy module loading)
         if (st == COLATUS_OK && cudaEventRecord(ev[0], e->stream) != cudaSuccess)
             st = efail(e, COLATUS_E_CUDA, "event record failed");
@@ -747,8 +814,8 @@ colatus_status colatus_ensemble_autotune(colatus_ens_t e, int reps, double out_m
     int best = 0;
     if (st == COLATUS_OK)
         for (int sh = 1; sh < kEnsShapes; ++sh)
-            if (ms[sh] < ms[best]) best = sh;
-    ens_set_shape(e, st == COLATUS_OK ? best : kEnsDefault);
+            if (e->shape_G[sh] > 0 && ms[sh] < ms[best]) best = sh;
+    ens_set_shape(e, st == COLATUS_OK ? best : ens_default_shape(e));
     if (st != COLATUS_OK) return st;
     for (int sh = 0; sh < kEnsShapes; ++sh)
         if (out_ms) out_ms[sh] = ms[sh];

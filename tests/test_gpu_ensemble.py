@@ -156,8 +156,8 @@ def test_autotune_and_every_shape(masses):
     try:
         ens.set_state(x, v)
         ms, chosen = ens.autotune(2)
-        assert np.all(ms > 0) and chosen == int(np.argmin(ms))
-        for shape in range(3):
+        assert len(ms) == 4 and np.all(ms > 0) and chosen == int(np.argmin(ms))
+        for shape in range(4):
             ens.set_tuning(shape)
             ens.set_state(x, v)                              # back to the initial positions
             a = ens.state()[3]                               # the clock has moved on
@@ -168,7 +168,7 @@ def test_autotune_and_every_shape(masses):
             ens.step(TAU, 17)                                # a fresh graph per shape
             assert np.all(np.isfinite(ens.state()[1]))
         with pytest.raises(B.ColatusError):
-            ens.set_tuning(3)
+            ens.set_tuning(4)
     finally:
         ens.close()
 
