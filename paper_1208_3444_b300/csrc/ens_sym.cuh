@@ -286,9 +286,8 @@ inline EnsSymTables build_ens_sym_tables(const std::vector<int> &n_r, int NW, lo
     auto owner = [&](long long q) {
         return (int)(std::upper_bound(start.begin(), start.end() - 1, q) - start.begin()) - 1;
     };
-    std::vector<int> row_g0(TT), row_ns(TT), unit_g0(U), unit_ko(U), unit_nk(U);
+    std::vector<int> row_g0(TT), row_ns(TT), col_start(TT + 1), unit_g0(U), unit_ko(U, 0), unit_nk(U);
     int S_row = 1;
-    long long ko = 0;
     for (int r = 0; r < R; ++r) {
         const int n = n_r[r];
         for (int it = 0; it < n; ++it) {
@@ -301,11 +300,23 @@ inline EnsSymTables build_ens_sym_tables(const std::vector<int> &n_r, int NW, lo
                 const long long u = u0 + (jt - it);
                 unit_g0[u] = owner(u * NW);
                 unit_nk[u] = it == jt ? 0 : owner(u * NW + NW - 1) - unit_g0[u] + 1;
+            }
+        }
+    }
+    // column slots numbered column by column within each realisation
+    long long ko = 0;
+    for (int r = 0; r < R; ++r) {
+        const int n = n_r[r];
+        for (int jt = 0; jt < n; ++jt) {
+            col_start[tb[r] + jt] = (int)ko;
+            for (int it = 0; it < jt; ++it) {
+                const long long u = ub[r] + sym_row_u0(it, n) + (jt - it);
                 unit_ko[u] = (int)ko;
                 ko += unit_nk[u];
             }
         }
     }
+    col_start[TT] = (int)ko;
     s.tab.assign(kSymHdr, 0);
     s.tab[0] = R;
     s.tab[1] = NW;
@@ -316,6 +327,7 @@ inline EnsSymTables build_ens_sym_tables(const std::vector<int> &n_r, int NW, lo
     s.tab.insert(s.tab.end(), tb.begin(), tb.end());
     s.tab.insert(s.tab.end(), row_g0.begin(), row_g0.end());
     s.tab.insert(s.tab.end(), row_ns.begin(), row_ns.end());
+    s.tab.insert(s.tab.end(), col_start.begin(), col_start.end());
     s.tab.insert(s.tab.end(), unit_g0.begin(), unit_g0.end());
     s.tab.insert(s.tab.end(), unit_ko.begin(), unit_ko.end());
     s.tab.insert(s.tab.end(), unit_nk.begin(), unit_nk.end());

@@ -169,12 +169,13 @@ __global__ void __launch_bounds__(NT, MINB)
 //   [0] R, [1] NW, [2] U tile pairs in all, [3] G CTAs, [4] TT tiles in all,
 //   [kSymHdr ...] ub[R + 1] (first tile pair of realisation r),
 //                 tb[R + 1] (first tile of realisation r),
-//                 row_g0[TT], row_ns[TT], unit_g0[U], unit_ko[U], unit_nk[U],
-//                 cta_pu[G + 1]
+//                 row_g0[TT], row_ns[TT], col_start[TT + 1], unit_g0[U],
+//                 unit_ko[U], unit_nk[U], cta_pu[G + 1]
 // with the meanings of force_sym.cuh, tiles and tile pairs numbered over all
-// realisations.
+// realisations (the column slots on the bodies of global tile t are the run
+// [col_start[t], col_start[t + 1])).
 struct EnsSymTab {
-    const int *ub, *tb, *row_g0, *row_ns, *unit_g0, *unit_ko, *unit_nk, *cta_pu;
+    const int *ub, *tb, *row_g0, *row_ns, *col_start, *unit_g0, *unit_ko, *unit_nk, *cta_pu;
     int R, NW, U, G, TT;
     __host__ __device__ explicit EnsSymTab(const int *t) {
         R = t[0];
@@ -186,7 +187,8 @@ struct EnsSymTab {
         tb = ub + R + 1;
         row_g0 = tb + R + 1;
         row_ns = row_g0 + TT;
-        unit_g0 = row_ns + TT;
+        col_start = row_ns + TT;
+        unit_g0 = col_start + TT + 1;
         unit_ko = unit_g0 + U;
         unit_nk = unit_ko + U;
         cta_pu = unit_nk + U;
@@ -195,33 +197,19 @@ struct EnsSymTab {
 
 // Epilogue side: the (G-less, mass-free for EQM) force sum of body i (global
 // padded index, realisation r) of the pair-once plan with tiles of T bodies:
-// the row segments of its tile, then the column slots of the tile pairs
-// (t', t), t' < t, in that fixed order.
+// the row segments of its tile, then the column slots on its tile, in that
+// fixed order.
 __device__ __forceinline__ float3 ens_reduce_sym(const float4 *__restrict__ part, const EnsLaunch &E, int r,
                                                  long long i, int T) {
     const EnsSymTab S(E.sym);
     const long long l = i - E.body_off[r];
     const int t = (int)(l / T), il = (int)(l - (long long)t * T);
-    const int gt = S.tb[r] + t, nr = S.tb[r + 1] - S.tb[r];
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-    const float4 *p = part + (long long)gt * E.S_max * T + il;
-    for (int s = 0; s < S.row_ns[gt]; ++s) {
-        const float4 v = __ldg(p + (long long)s * T);
-        fx += v.x;
-        fy += v.y;
-        fz += v.z;
-    }
-    const float4 *c = part + E.sym_col_off + il;
-    for (int tp = 0; tp < t; ++tp) {
-        const int uu = S.ub[r] + (int)sym_row_u0(tp, nr) + (t - tp);
-        const int ko = S.unit_ko[uu], nk = S.unit_nk[uu];
-        for (int k = 0; k < nk; ++k) {
-            const float4 v = __ldg(c + (long long)(ko + k) * T);
-            fx += v.x;
-            fy += v.y;
-            fz += v.z;
-        }
-    }
+    const int gt = S.tb[r] + t;
+    float fx = 0.f, fy = 0.f, fz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+    sym_sum_run<false>(part + (long long)gt * E.S_max * T + il, T, S.row_ns[gt], 0, fx, fy, fz, lx, ly, lz);
+    const int k0 = S.col_start[gt];
+    sym_sum_run<false>(part + E.sym_col_off + (long long)k0 * T + il, T, S.col_start[gt + 1] - k0, 0, fx, fy,
+                       fz, lx, ly, lz);
     return make_float3(fx, fy, fz);
 }
 

@@ -50,16 +50,84 @@ namespace colatus {
 
 // Layout of the int tables of a symmetric plan (ForceLaunch::sym):
 //   [0] n tiles, [1] NW phases per unit, [2] U units, [3] G CTAs,
-//   [kSymHdr ...]  row_g0[n], row_ns[n], unit_g0[U], unit_ko[U], unit_nk[U],
-//                  cta_pu[G + 1]
+//   [kSymHdr ...]  row_g0[n], row_ns[n], col_start[n + 1], unit_g0[U],
+//                  unit_ko[U], unit_nk[U], cta_pu[G + 1]
 // row_g0 / row_ns: first CTA and number of row segments of i-tile t;
 // unit_g0 / unit_ko / unit_nk: first CTA, first column slot and number of
-// column slots of unit u (0 for a diagonal unit); cta_pu: first phase-unit
-// (u NW + phase) of CTA g.
+// column slots of unit u (0 for a diagonal unit); the slots are numbered
+// column by column (tile jt, then it < jt, then CTA), so the slots on the
+// bodies of tile t are the one run [col_start[t], col_start[t + 1]);
+// cta_pu: first phase-unit (u NW + phase) of CTA g.
 constexpr int kSymHdr = 8;
 
 __host__ __device__ inline long long sym_row_u0(long long it, long long n) {
     return it * n - it * (it - 1) / 2;
+}
+
+struct SymTab {
+    const int *row_g0, *row_ns, *col_start, *unit_g0, *unit_ko, *unit_nk, *cta_pu;
+    int n, NW, U, G;
+    __host__ __device__ explicit SymTab(const int *t) {
+        n = t[0];
+        NW = t[1];
+        U = t[2];
+        G = t[3];
+        row_g0 = t + kSymHdr;
+        row_ns = row_g0 + n;
+        col_start = row_ns + n;
+        unit_g0 = col_start + n + 1;
+        unit_ko = unit_g0 + U;
+        unit_nk = unit_ko + U;
+        cta_pu = unit_nk + U;
+    }
+};
+
+// Sum of cnt float4 entries stride apart from p (x, y, z; with the low words
+// `lo` float4 further on when COMP, folded as reduce_f32 does), in order,
+// four independent loads at a time.
+template <bool COMP>
+__device__ __forceinline__ void sym_sum_run(const float4 *__restrict__ p, long long stride, int cnt, int lo,
+                                            float &hx, float &hy, float &hz, float &lx, float &ly, float &lz) {
+    int s = 0;
+    for (; s + 4 <= cnt; s += 4) {
+        float4 h[4], l[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            h[k] = __ldg(p + (s + k) * stride);
+            if (COMP) l[k] = __ldg(p + (s + k) * stride + lo);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (COMP) {
+                acc2_add(hx, lx, h[k].x);
+                acc2_add(hy, ly, h[k].y);
+                acc2_add(hz, lz, h[k].z);
+                lx += l[k].x;
+                ly += l[k].y;
+                lz += l[k].z;
+            } else {
+                hx += h[k].x;
+                hy += h[k].y;
+                hz += h[k].z;
+            }
+        }
+    }
+    for (; s < cnt; ++s) {
+        const float4 h = __ldg(p + s * stride);
+        if (COMP) {
+            const float4 l = __ldg(p + s * stride + lo);
+            acc2_add(hx, lx, h.x);
+            acc2_add(hy, ly, h.y);
+            acc2_add(hz, lz, h.z);
+            lx += l.x;
+            ly += l.y;
+            lz += l.z;
+        } else {
+            hx += h.x;
+            hy += h.y;
+            hz += h.z;
+        }
+    }
 }
 
 template <int NT, int IPT_, bool COMP>
@@ -188,12 +256,9 @@ __global__ void __launch_bounds__(NT, 1)
     float2 *acc = reinterpret_cast<float2 *>(sB + 2 * TP);   // [PL][3][TP]
     uint64_t *bar = reinterpret_cast<uint64_t *>(acc + PL * 3 * TP);
 
-    const int *tab = L.sym;
-    const int n = tab[0], U = tab[2];
-    const int *row_g0 = tab + kSymHdr;
-    const int *unit_g0 = row_g0 + 2 * n;
-    const int *unit_ko = unit_g0 + U;
-    const int *cta_pu = unit_ko + 2 * U;
+    const SymTab S(L.sym);
+    const int n = S.n;
+    const int *row_g0 = S.row_g0, *unit_g0 = S.unit_g0, *unit_ko = S.unit_ko, *cta_pu = S.cta_pu;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = blockIdx.x;
     int pu = cta_pu[g];
@@ -367,44 +432,20 @@ __global__ void __launch_bounds__(NT, 1)
 }
 
 // Epilogue side: the force on body i (FP32 partial sums of a symmetric plan),
-// its row segments then the column slots of the units (t', t), t' < t, in
-// that fixed order; COMP adds the low words separately, as reduce_f32 does.
+// its row segments then the column slots on its tile, in that fixed order;
+// COMP adds the low words separately, as reduce_f32 does.
 template <bool COMP>
 __device__ __forceinline__ float3 reduce_sym_f32(const float4 *__restrict__ part, const ForceLaunch &L,
                                                  int T, long long i) {
-    const int *tab = L.sym;
-    const int n = tab[0], U = tab[2];
-    const int *row_ns = tab + kSymHdr + n;
-    const int *unit_ko = tab + kSymHdr + 2 * n + U;
-    const int *unit_nk = unit_ko + U;
+    const SymTab S(L.sym);
     const long long t = i / T, il = i - t * T;
     const int PL = COMP ? 2 : 1;
     float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-    auto add = [&](const float4 *p) {
-        const float4 h = __ldg(p);
-        if (COMP) {
-            const float4 l = __ldg(p + T);
-            acc2_add(hx, lx, h.x);
-            acc2_add(hy, ly, h.y);
-            acc2_add(hz, lz, h.z);
-            lx += l.x;
-            ly += l.y;
-            lz += l.z;
-        } else {
-            hx += h.x;
-            hy += h.y;
-            hz += h.z;
-        }
-    };
-    const float4 *p = part + t * L.S_max * PL * (long long)T + il;
-    const int ns = row_ns[t];
-    for (int s = 0; s < ns; ++s) add(p + (long long)s * PL * T);
-    const float4 *c = part + L.col_off + il;
-    for (long long tp = 0; tp < t; ++tp) {
-        const long long uu = sym_row_u0(tp, n) + (t - tp);
-        const int ko = unit_ko[uu], nk = unit_nk[uu];
-        for (int k = 0; k < nk; ++k) add(c + (long long)(ko + k) * PL * T);
-    }
+    sym_sum_run<COMP>(part + t * L.S_max * PL * (long long)T + il, (long long)PL * T, S.row_ns[t], T, hx, hy,
+                      hz, lx, ly, lz);
+    const int k0 = S.col_start[t];
+    sym_sum_run<COMP>(part + L.col_off + (long long)k0 * PL * T + il, (long long)PL * T, S.col_start[t + 1] - k0,
+                      T, hx, hy, hz, lx, ly, lz);
     return COMP ? make_float3(hx + lx, hy + ly, hz + lz) : make_float3(hx, hy, hz);
 }
 
@@ -443,9 +484,8 @@ inline SymTables build_sym_tables(long long n_pad, int T, int NW, long long G_ta
     auto owner = [&](long long q) {
         return (int)(std::upper_bound(start.begin(), start.end() - 1, q) - start.begin()) - 1;
     };
-    std::vector<int> row_g0(n), row_ns(n), unit_g0(U), unit_ko(U), unit_nk(U);
+    std::vector<int> row_g0(n), row_ns(n), col_start(n + 1), unit_g0(U), unit_ko(U, 0), unit_nk(U);
     int S_row = 1;
-    long long ko = 0;
     for (int it = 0; it < n; ++it) {
         const long long a = sym_row_u0(it, n) * NW, b = sym_row_u0(it + 1, n) * NW - 1;
         row_g0[it] = owner(a);
@@ -455,10 +495,19 @@ inline SymTables build_sym_tables(long long n_pad, int T, int NW, long long G_ta
             const long long u = sym_row_u0(it, n) + (jt - it);
             unit_g0[u] = owner(u * NW);
             unit_nk[u] = it == jt ? 0 : owner(u * NW + NW - 1) - unit_g0[u] + 1;
+        }
+    }
+    // column slots numbered column by column
+    long long ko = 0;
+    for (int jt = 0; jt < n; ++jt) {
+        col_start[jt] = (int)ko;
+        for (int it = 0; it < jt; ++it) {
+            const long long u = sym_row_u0(it, n) + (jt - it);
             unit_ko[u] = (int)ko;
             ko += unit_nk[u];
         }
     }
+    col_start[n] = (int)ko;
     s.tab.assign(kSymHdr, 0);
     s.tab[0] = n;
     s.tab[1] = NW;
@@ -466,6 +515,7 @@ inline SymTables build_sym_tables(long long n_pad, int T, int NW, long long G_ta
     s.tab[3] = G;
     s.tab.insert(s.tab.end(), row_g0.begin(), row_g0.end());
     s.tab.insert(s.tab.end(), row_ns.begin(), row_ns.end());
+    s.tab.insert(s.tab.end(), col_start.begin(), col_start.end());
     s.tab.insert(s.tab.end(), unit_g0.begin(), unit_g0.end());
     s.tab.insert(s.tab.end(), unit_ko.begin(), unit_ko.end());
     s.tab.insert(s.tab.end(), unit_nk.begin(), unit_nk.end());

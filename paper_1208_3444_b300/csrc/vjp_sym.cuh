@@ -126,12 +126,9 @@ __global__ void __launch_bounds__(NT, 1)
     float2 *acc = reinterpret_cast<float2 *>(sC + 2 * TP);   // [4][TP]
     uint64_t *bar = reinterpret_cast<uint64_t *>(acc + 4 * TP);
 
-    const int *tab = L.sym;
-    const int n = tab[0], U = tab[2];
-    const int *row_g0 = tab + kSymHdr;
-    const int *unit_g0 = row_g0 + 2 * n;
-    const int *unit_ko = unit_g0 + U;
-    const int *cta_pu = unit_ko + 2 * U;
+    const SymTab S(L.sym);
+    const int n = S.n;
+    const int *row_g0 = S.row_g0, *unit_g0 = S.unit_g0, *unit_ko = S.unit_ko, *cta_pu = S.cta_pu;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = blockIdx.x;
     int pu = cta_pu[g];
@@ -275,33 +272,38 @@ __global__ void __launch_bounds__(NT, 1)
 }
 
 // Consumer side: the VJP of body i (float4 dL/dx, dL/dm) of a pair-once plan,
-// its row segments then the column slots of the units (t', t), t' < t, in that
-// fixed order.
+// its row segments then the column slots on its tile, in that fixed order,
+// four independent loads at a time.
 __device__ __forceinline__ float4 reduce_vjp_sym_f32(const float4 *__restrict__ part, const ForceLaunch &L,
                                                      int T, long long i) {
-    const int *tab = L.sym;
-    const int n = tab[0], U = tab[2];
-    const int *row_ns = tab + kSymHdr + n;
-    const int *unit_ko = tab + kSymHdr + 2 * n + U;
-    const int *unit_nk = unit_ko + U;
+    const SymTab S(L.sym);
     const long long t = i / T, il = i - t * T;
     float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-    auto add = [&](const float4 *p) {
-        const float4 v = __ldg(p);
-        r.x += v.x;
-        r.y += v.y;
-        r.z += v.z;
-        r.w += v.w;
+    auto run = [&](const float4 *p, int cnt) {
+        int s = 0;
+        for (; s + 4 <= cnt; s += 4) {
+            float4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = __ldg(p + (long long)(s + k) * T);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                r.x += v[k].x;
+                r.y += v[k].y;
+                r.z += v[k].z;
+                r.w += v[k].w;
+            }
+        }
+        for (; s < cnt; ++s) {
+            const float4 v = __ldg(p + (long long)s * T);
+            r.x += v.x;
+            r.y += v.y;
+            r.z += v.z;
+            r.w += v.w;
+        }
     };
-    const float4 *p = part + t * L.S_max * (long long)T + il;
-    const int ns = row_ns[t];
-    for (int s = 0; s < ns; ++s) add(p + (long long)s * T);
-    const float4 *c = part + L.col_off + il;
-    for (long long tp = 0; tp < t; ++tp) {
-        const long long uu = sym_row_u0(tp, n) + (t - tp);
-        const int ko = unit_ko[uu], nk = unit_nk[uu];
-        for (int k = 0; k < nk; ++k) add(c + (long long)(ko + k) * T);
-    }
+    run(part + t * L.S_max * (long long)T + il, S.row_ns[t]);
+    const int k0 = S.col_start[t];
+    run(part + L.col_off + (long long)k0 * T + il, S.col_start[t + 1] - k0);
     return r;
 }
 
