@@ -173,6 +173,9 @@ constexpr int kEwMaxNk = 63;   // shared memory of the k-space kernels in FP64; 
 constexpr int kEwRhoBlocksPerSM = 8;   // structure-factor blocks per SM (k chunks x body splits)
 
 constexpr long long kPadAlloc = 1024;   // buffers hold N rounded up to this
+// threads per block of the FP32 step epilogues (one body per thread; their
+// segment sums are L2-latency bound, so smaller blocks spread them over more SMs)
+constexpr int kEpiThreads = 256;
 constexpr int kChunk = 1024;            // steps enqueued per chunk of colatus_step
 constexpr int kTabCap = 4096;           // ring of look-ahead schedule entries
 constexpr int kLookahead = 256;         // schedule entries kept ahead of the state
@@ -1350,23 +1353,23 @@ colatus_status launch_step(colatus_t ctx, const StepBufs &b, int c, long long st
         TRY(run_force_f32(ctx, p, b.pk[c]));
         const float4 *part = static_cast<const float4 *>(ctx->part);
         const bool comp = ctx->prec == COLATUS_FP32_COMP;
-        const unsigned nb = blocks_for(p.n_pad, 256);
+        const unsigned nb = blocks_for(p.n_pad, kEpiThreads);
         if (is_kdk(ctx)) {
             if (comp)
-                kdk_step_f32_kernel<true><<<nb, 256, 0, ctx->stream>>>(
+                kdk_step_f32_kernel<true><<<nb, kEpiThreads, 0, ctx->stream>>>(
                     part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.vh, b.acc, b.pk[n], b.table, b.tcap,
                     step, tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk, D);
             else
-                kdk_step_f32_kernel<false><<<nb, 256, 0, ctx->stream>>>(
+                kdk_step_f32_kernel<false><<<nb, kEpiThreads, 0, ctx->stream>>>(
                     part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.vh, b.acc, b.pk[n], b.table, b.tcap,
                     step, tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk, D);
         } else {
             if (comp)
-                dkd_step_f32_kernel<true><<<nb, 256, 0, ctx->stream>>>(
+                dkd_step_f32_kernel<true><<<nb, kEpiThreads, 0, ctx->stream>>>(
                     part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.acc, b.pk[n], b.table, b.tcap, step,
                     tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk, D);
             else
-                dkd_step_f32_kernel<false><<<nb, 256, 0, ctx->stream>>>(
+                dkd_step_f32_kernel<false><<<nb, kEpiThreads, 0, ctx->stream>>>(
                     part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.acc, b.pk[n], b.table, b.tcap, step,
                     tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk, D);
         }

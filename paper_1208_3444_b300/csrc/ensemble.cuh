@@ -21,6 +21,7 @@
 #include "common.cuh"
 #include "force.cuh"
 #include "force_sym.cuh"
+#include "sym_reduce.cuh"
 #include "integrate.cuh"
 
 namespace colatus {

@@ -6,7 +6,7 @@
 
 #include "common.cuh"
 #include "force.cuh"
-#include "force_sym.cuh"
+#include "sym_reduce.cuh"
 
 namespace colatus {
 

@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(NT, 1)
 
 // Consumer side: the VJP of body i (float4 dL/dx, dL/dm) of a pair-once plan,
 // its row segments then the column slots on its tile, in that fixed order,
-// four independent loads at a time.
+// eight independent loads at a time.
 __device__ __forceinline__ float4 reduce_vjp_sym_f32(const float4 *__restrict__ part, const ForceLaunch &L,
                                                      int T, long long i) {
     const SymTab S(L.sym);
@@ -281,12 +281,12 @@ __device__ __forceinline__ float4 reduce_vjp_sym_f32(const float4 *__restrict__ 
     float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
     auto run = [&](const float4 *p, int cnt) {
         int s = 0;
-        for (; s + 4 <= cnt; s += 4) {
-            float4 v[4];
+        for (; s + 8 <= cnt; s += 8) {
+            float4 v[8];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] = __ldg(p + (long long)(s + k) * T);
+            for (int k = 0; k < 8; ++k) v[k] = __ldg(p + (long long)(s + k) * T);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < 8; ++k) {
                 r.x += v[k].x;
                 r.y += v[k].y;
                 r.z += v[k].z;
