@@ -279,12 +279,14 @@ colatus_status colatus_force_plan(colatus_t ctx, int64_t out[9]);
  * measurement (the VJP of the Eq. 1 sum, see colatus_force_vjp; the
  * equal-mass forms need equal masses, isolated boundaries, no Eq. 6 term, a
  * KDK scheme and N a multiple of 1024; colatus_force_vjp itself always takes
- * the general form): out[0] kind (0 FP32 general, 1 FP64, 2 FP32 periodic
+ * a form for any masses): out[0] kind (0 FP32 general, 1 FP64, 2 FP32 periodic
  * real space, 3 FP64 periodic real space, 4 FP32 equal-mass, 5 FP32
- * equal-mass with every pair evaluated once, from 8 tiles of 1024 bodies),
+ * equal-mass with every pair evaluated once, from 8 tiles of 1024 bodies,
+ * 6 FP32 any masses with every pair evaluated once, from 8 tiles: also the
+ * kernel of colatus_force_vjp then),
  * out[1] threads per CTA, out[2] i-bodies per thread, out[3] j-tile bodies,
  * out[4] persistent grid (CTAs), out[5] work units (i-tile x j-tile; for
- * kind 5 the tile pairs it <= jt).  Errors: COLATUS_E_ARG. */
+ * kinds 5 and 6 the tile pairs it <= jt).  Errors: COLATUS_E_ARG. */
 colatus_status colatus_vjp_plan(colatus_t ctx, int64_t out[6]);
 
 /* Kernel timing for measurement: with on != 0 every launch of the force

@@ -135,6 +135,9 @@ constexpr int kVjpNT = 256, kVjpIPT = 4, kVjpJT = 256, kVjpMINB = 1, kVjpUnr = 4
 // registers), rotation unrolled by 8; used from 8 tiles on, like the force's.
 constexpr int kVjpSymNT = 256, kVjpSymUnr = 8;
 using VjpSymK = VjpSymKernel<kVjpSymNT>;
+// Pair-once VJP for any masses (vjp_sym.cuh): the same shape and tiles.
+constexpr int kVjpGenNT = 256, kVjpGenUnr = 4;
+using VjpGenK = VjpSymGenKernel<kVjpGenNT>;
 using VjpK = VjpKernel<kVjpNT, kVjpIPT, kVjpJT, kStages>;
 static_assert(kVjpIPT == 4, "the equal-mass VJP kernel shares the VJP's launch plan (4 i-bodies per thread)");
 constexpr int kV64NT = 128, kV64JT = 32;
@@ -318,6 +321,8 @@ struct colatus_ctx {
     ForcePlan plan_vjp32, plan_vjp64;
     ForcePlan plan_vjp_sym;            // pair-once equal-mass VJP (fits: usable for this N)
     int *vjp_sym_tab = nullptr;
+    ForcePlan plan_vjp_gen;            // pair-once VJP for any masses
+    int *vjp_gen_tab = nullptr;
     ForcePlan plan_ewvjp32, plan_ewvjp64;   // periodic VJP (real space)
 
     // periodic boundaries (colatus_set_periodic): Ewald parameters and buffers
@@ -548,6 +553,36 @@ colatus_status build_plans(colatus_t ctx) {
             CU(cudaMalloc(&ctx->vjp_sym_tab, st.tab.size() * sizeof(int)));
             CU(cudaMemcpy(ctx->vjp_sym_tab, st.tab.data(), st.tab.size() * sizeof(int), cudaMemcpyHostToDevice));
             q.L.sym = ctx->vjp_sym_tab;
+        }
+    }
+    {
+        // the pair-once VJP for any masses: tables with its phase costs (33
+        // lane-ops per diagonal interaction, 40 per symmetric pair)
+        auto fn = vjp_sym_f32_kernel<kVjpGenNT, kVjpGenUnr, false>;
+        CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, VjpGenK::SMEM));
+        CU(cudaFuncSetAttribute(vjp_sym_f32_kernel<kVjpGenNT, kVjpGenUnr, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, VjpGenK::SMEM));
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kVjpGenNT, VjpGenK::SMEM));
+        if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "pair-once VJP kernel (any masses) cannot be resident");
+        ForcePlan &q = ctx->plan_vjp_gen;
+        q.itile = q.jt = VjpGenK::T;
+        q.n_pad = round_up(ctx->N, VjpGenK::T);
+        const bool may = sym_may_fit(ctx, q.n_pad, VjpGenK::T, 1);
+        const SymTables st = may ? build_sym_tables(q.n_pad, VjpGenK::T, VjpGenK::NW,
+                                                    (long long)occ * std::max(1, ctx->num_sms - 1), 33, 40)
+                                 : SymTables{};
+        q.L = ForceLaunch{};
+        q.L.W = st.U;
+        q.L.n_it = q.L.n_jt = st.n;
+        q.L.G = st.G;
+        q.L.S_max = st.S_row;
+        q.L.col_off = (long long)st.n * st.S_row * q.itile;
+        q.part_bytes = (size_t)((long long)st.n * st.S_row + st.slots) * q.itile * sizeof(float4);
+        q.fits = may && st.n >= kSymMinTiles && q.part_bytes <= ctx->sym_max_bytes;
+        if (q.fits) {
+            CU(cudaMalloc(&ctx->vjp_gen_tab, st.tab.size() * sizeof(int)));
+            CU(cudaMemcpy(ctx->vjp_gen_tab, st.tab.data(), st.tab.size() * sizeof(int), cudaMemcpyHostToDevice));
+            q.L.sym = ctx->vjp_gen_tab;
         }
     }
     ForcePlan &w = ctx->plan_vjp64;
@@ -1117,7 +1152,7 @@ void free_all(colatus_t ctx) {
                     ctx->tclk, ctx->table, ctx->stage, ctx->stage2, ctx->diag, ctx->tslot,
                     ctx->rec, ctx->kw, ctx->rho, ctx->rho_part, ctx->wcs, ctx->pen,
                     ctx->rchunk, ctx->fchunk, ctx->lr, ctx->ph, ctx->pot_part, ctx->lrv,
-                    ctx->kwr, ctx->kwl, ctx->pk_ew, ctx->vjp_sym_tab, ctx->ew_sym_tab};
+                    ctx->kwr, ctx->kwl, ctx->pk_ew, ctx->vjp_sym_tab, ctx->ew_sym_tab, ctx->vjp_gen_tab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *tptrs[] = {ctx->tan.dx, ctx->tan.dv, ctx->tan.dvh, ctx->tan.dxp, ctx->tan.pkt,
@@ -1435,13 +1470,16 @@ colatus_status grow(colatus_t ctx, void **p, size_t *have, size_t need) {
 }
 
 // The VJP's launch plan: the periodic kernel's when the boundaries are periodic;
-// eqm (the equal-mass VJP of the KDK adjoint): the pair-once kernel's where
-// it fits, which has the same padding.
+// in FP32 the pair-once kernels' where they fit (same padding as the
+// per-ordered-pair VJP): the equal-mass one for eqm (the KDK adjoint's), the
+// one for any masses otherwise.
 const ForcePlan &vjp_plan(colatus_t ctx, bool eqm = false) {
     const bool f64 = ctx->prec == COLATUS_FP64;
     if (ctx->periodic) return f64 ? ctx->plan_ewvjp64 : ctx->plan_ewvjp32;
-    if (eqm && !f64 && ctx->plan_vjp_sym.fits) return ctx->plan_vjp_sym;
-    return f64 ? ctx->plan_vjp64 : ctx->plan_vjp32;
+    if (f64) return ctx->plan_vjp64;
+    if (eqm && ctx->plan_vjp_sym.fits) return ctx->plan_vjp_sym;
+    if (!eqm && ctx->plan_vjp_gen.fits) return ctx->plan_vjp_gen;
+    return ctx->plan_vjp32;
 }
 
 // Per-body terms of the VJP consumers: the deformation term and, with
@@ -1539,6 +1577,14 @@ colatus_status run_vjp(colatus_t ctx, bool eqm = false) {
             <<<p.L.G, kVjpNT, VjpK::SMEM, ctx->stream>>>(
                 static_cast<const float *>(ctx->adj.pkw), static_cast<float4 *>(ctx->part),
                 ctx->flags, p.L, (float)(ctx->eps * ctx->eps));
+    else if (p.L.sym && ctx->eq_mass && p.n_pad == ctx->N)
+        vjp_sym_f32_kernel<kVjpGenNT, kVjpGenUnr, true><<<p.L.G, kVjpGenNT, VjpGenK::SMEM, ctx->stream>>>(
+            static_cast<const float *>(ctx->adj.pkw), static_cast<float4 *>(ctx->part), ctx->flags, p.L,
+            (float)(ctx->eps * ctx->eps), ctx->mass_eq);
+    else if (p.L.sym)
+        vjp_sym_f32_kernel<kVjpGenNT, kVjpGenUnr, false><<<p.L.G, kVjpGenNT, VjpGenK::SMEM, ctx->stream>>>(
+            static_cast<const float *>(ctx->adj.pkw), static_cast<float4 *>(ctx->part), ctx->flags, p.L,
+            (float)(ctx->eps * ctx->eps), 1.f);
     else if (f64)
         vjp_f64_kernel<kV64NT, kV64JT, kStages><<<p.L.G, kV64NT, Vjp64K::SMEM, ctx->stream>>>(
             static_cast<const double4 *>(ctx->adj.pkw), static_cast<double4 *>(ctx->part),
@@ -1734,7 +1780,7 @@ colatus_status colatus_init(colatus_t *out, int64_t N, const double *masses, dou
     for (const ForcePlan &p : ctx->plan32) ctx->n_alloc = std::max(ctx->n_alloc, p.n_pad);
     for (const ForcePlan *p : {&ctx->plan64, &ctx->plan_vjp32, &ctx->plan_vjp64, &ctx->plan_ewvjp32,
                                &ctx->plan_ewvjp64, &ctx->plan_ew32[0],
-                               &ctx->plan_ew32[1], &ctx->plan_ew64, &ctx->plan_vjp_sym,
+                               &ctx->plan_ew32[1], &ctx->plan_ew64, &ctx->plan_vjp_sym, &ctx->plan_vjp_gen,
                                &ctx->plan_ew_sym[0], &ctx->plan_ew_sym[1]})
         ctx->n_alloc = std::max(ctx->n_alloc, p->n_pad);
     ctx->eps = eps;
@@ -2958,6 +3004,10 @@ colatus_status colatus_vjp_plan(colatus_t ctx, int64_t out[6]) {
         out[0] = 5;
         out[1] = kVjpSymNT;
         out[2] = VjpSymK::IPT;
+    } else if (p.L.sym) {
+        out[0] = 6;
+        out[1] = kVjpGenNT;
+        out[2] = VjpGenK::IPT;
     } else {
         out[0] = eqm ? 4 : 0;
         out[1] = kVjpNT;

@@ -218,10 +218,12 @@ def test_grid32_adjoint_pair_once_vjp():
 
 
 def test_vjp_plan_kinds():
-    # the general form below 8 tiles, with unequal masses, for DKD and under
-    # the Eq. 6 term; FP64 its own kernel
+    # from 8 tiles of 1024 bodies: the equal-mass pair-once VJP for the KDK
+    # adjoint with equal masses, the pair-once VJP for any masses otherwise
+    # (DKD, unequal masses); below 8 tiles the per-ordered-pair kernels;
+    # FP64 its own kernel
     x, m = system(8192, True, 3)
-    cases = [(dict(), "vjp_sym_eqm_f32"), (dict(scheme=B.DKD), "vjp_f32"),
+    cases = [(dict(), "vjp_sym_eqm_f32"), (dict(scheme=B.DKD), "vjp_sym_f32"),
              (dict(prec=B.FP64), "vjp_f64")]
     for kw, kind in cases:
         sim = B.Simulation(m, 0.01, LCDM_D, 1.0, **{"prec": B.FP32, **kw})
@@ -231,7 +233,9 @@ def test_vjp_plan_kinds():
         finally:
             sim.close()
     for N, mm, kind in ((7168, np.full(7168, 1 / 7168), "vjp_eqm_f32"),
-                        (8192, system(8192, False, 4)[1], "vjp_f32")):
+                        (7168, system(7168, False, 4)[1], "vjp_f32"),
+                        (8192, system(8192, False, 4)[1], "vjp_sym_f32"),
+                        (8193, system(8193, False, 4)[1], "vjp_sym_f32")):
         sim = B.Simulation(inputs.f32(mm), 0.01, LCDM_D, 1.0, prec=B.FP32)
         try:
             sim.set_state(system(N, True, 5)[0])
@@ -303,3 +307,95 @@ def test_periodic_pair_once_steps_match_per_pair_kernel(scheme):
     assert np.abs(x3 - x0).max() < 1e-6
     vn = np.sqrt(np.mean(np.sum(v0 ** 2, axis=1)))
     assert np.sqrt(np.mean(np.sum((v3 - v0) ** 2, axis=1))) < 5e-6 * vn
+
+
+# ---- the pair-once VJP for any masses (colatus_force_vjp and the DKD adjoint
+# from 8 tiles of 1024 bodies)
+
+def vjp_system(N, seed, equal=False):
+    rng = np.random.default_rng(seed)
+    x = inputs.f32(rng.random((N, 3)))
+    m = np.full(N, 1.0 / N) if equal else rng.lognormal(0.0, 0.5, N) / N
+    w = inputs.f32(rng.standard_normal((N, 3)))
+    return x, inputs.f32(m), w
+
+
+@pytest.mark.parametrize("prec", [B.FP32, B.FP32_COMP])
+@pytest.mark.parametrize("N,equal", [(8192, False), (8192, True), (9001, False), (20481, False)])
+def test_force_vjp_pair_once_matches_oracle(N, equal, prec):
+    x, m, w = vjp_system(N, 340 + N, equal)
+    a, G, eps = 0.5, 1.3, 0.002
+    sim = B.Simulation(m, eps, LCDM_D, a, prec=prec, G=G)
+    try:
+        sim.set_state(x)
+        assert sim.vjp_plan()["kind"] == ("vjp_sym_eqm_f32" if equal and N % 1024 == 0 else "vjp_sym_f32")
+        gx, gm = sim.force_vjp(w)
+    finally:
+        sim.close()
+    rows = None if N <= SAMPLE_ABOVE else np.sort(np.random.default_rng(N).choice(N, 512, replace=False))
+    rx, rm = oracle.vjp(x, m, w, eps, G, rows=rows)
+    sel = slice(None) if rows is None else rows
+    assert rel(gx[sel], rx / a ** 3) < 1e-5
+    assert rel(gm[sel], rm / a ** 3) < 1e-5
+
+
+@pytest.mark.parametrize("case", ["massless", "tiny", "huge", "zero_covector", "coincident"])
+def test_force_vjp_pair_once_mass_edge_cases(case):
+    # massless bodies with co-vectors, masses of 1e-25 and of 3e11 / 3e21,
+    # zero co-vectors, and distinct bodies at one point (inv = 1/eps there)
+    N = 9000
+    x, m, w = vjp_system(N, 360)
+    m = m.astype(np.float64)
+    G = 1.3
+    if case == "massless":
+        m[[1500, 2500, 8999]] = 0.0
+    elif case == "tiny":
+        m[[1200, 4600]] = 1e-25
+    elif case == "huge":
+        m *= 1e15
+        m[4096:] *= 1e10
+        G = 1.3e-20
+    elif case == "zero_covector":
+        w[1000:5100] = 0.0
+        m[2000:2050] = 0.0
+    else:
+        x[[10, 3000, 8000]] = x[5]
+    m = inputs.f32(m)
+    a, eps = 0.5, 0.01
+    sim = B.Simulation(m, eps, LCDM_D, a, prec=B.FP32, G=G)
+    try:
+        sim.set_state(x)
+        assert sim.vjp_plan()["kind"] == "vjp_sym_f32"
+        gx, gm = sim.force_vjp(w)
+    finally:
+        sim.close()
+    rx, rm = oracle.vjp(x, m, w, eps, G)
+    assert rel(gx, rx / a ** 3) < 1e-5
+    assert rel(gm, rm / a ** 3) < 1e-5
+
+
+@pytest.mark.parametrize("prec", [B.FP32, B.FP32_COMP])
+@pytest.mark.parametrize("k", [3, 1])
+def test_dkd_adjoint_pair_once_vjp(prec, k):
+    # the paper's DKD scheme takes the VJP for any masses: 8192 bodies at the
+    # background density, 8 steps, against the oracle's DKD transpose
+    ic = inputs.perturbed_grid(21, 0.1, 0.02, 47, zeldovich=True, count=8192,
+                               total_mass=inputs.CRITICAL_MATTER_DENSITY)
+    tr = inputs.tracers(ic.N, 64, 7)
+    n = 8
+    sim = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START, prec=prec, scheme=B.DKD)
+    try:
+        sim.set_state(ic.x, ic.v)
+        assert sim.vjp_plan()["kind"] == "vjp_sym_f32"
+        sim.adjoint_forward(TAU, n, k)
+        xT, vT, t, aT = sim.state()
+        gvT, gmT = tracer_loss_grads(xT, vT, ic.m, aT, tr)
+        g = sim.adjoint_backward(None, gvT, gmT)
+    finally:
+        sim.close()
+    r = oracle.run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n, "dkd")
+    gvO, gmO = tracer_loss_grads(r["x"], r["v"], ic.m, r["schedule"]["a"][-1], tr)
+    ref = oracle.adjoint_run(ic.x, ic.v, ic.m, ic.eps, 1.0, LCDM, inputs.A_START, TAU, n,
+                             np.zeros_like(ic.x), gvO, gmO, scheme="dkd")
+    for key, got, want in zip(("gx", "gv", "gm"), g, ref):
+        assert rel(got, want) < 1e-4, key
