@@ -1294,6 +1294,19 @@ colatus_status force_at_state(colatus_t ctx) {
     return run_force_f32(ctx, p, ctx->pk[2]);
 }
 
+// forces_out_f32_kernel for plan p (its pair-once or ordered-pair sums).
+template <bool COMP>
+void launch_forces_out_f32(colatus_t ctx, const ForcePlan &p, void *out, int out_f64, float4 *acc,
+                           const float *pk) {
+    const float4 *part = static_cast<const float4 *>(ctx->part);
+    if (p.L.sym)
+        forces_out_f32_kernel<COMP, true><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
+            part, p.L, p.itile, ctx->N, ctx->clk, ctx->G, out, out_f64, acc, pk, extra_args(ctx));
+    else
+        forces_out_f32_kernel<COMP, false><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
+            part, p.L, p.itile, ctx->N, ctx->clk, ctx->G, out, out_f64, acc, pk, extra_args(ctx));
+}
+
 // Reduce the segments of the last force sum into acc and/or out.
 colatus_status force_output(colatus_t ctx, void *out, int out_f64, bool to_acc) {
     if (ctx->prec == COLATUS_FP64) {
@@ -1305,13 +1318,9 @@ colatus_status force_output(colatus_t ctx, void *out, int out_f64, bool to_acc) 
     }
     const ForcePlan &p = plan_f32(ctx);
     if (ctx->prec == COLATUS_FP32_COMP)
-        forces_out_f32_kernel<true><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
-            static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk, ctx->G, out,
-            out_f64, to_acc ? ctx->acc : nullptr, ctx->pk[2], extra_args(ctx));
+        launch_forces_out_f32<true>(ctx, p, out, out_f64, to_acc ? ctx->acc : nullptr, ctx->pk[2]);
     else
-        forces_out_f32_kernel<false><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
-            static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk, ctx->G, out,
-            out_f64, to_acc ? ctx->acc : nullptr, ctx->pk[2], extra_args(ctx));
+        launch_forces_out_f32<false>(ctx, p, out, out_f64, to_acc ? ctx->acc : nullptr, ctx->pk[2]);
     return launched(ctx);
 }
 
@@ -1365,6 +1374,23 @@ colatus_status launch_kdk_open(colatus_t ctx, const StepBufs &b, int c, long lon
     return launched(ctx);
 }
 
+// The FP32 step epilogue of plan p (SYM: its pair-once sums).
+template <bool COMP, bool SYM>
+void launch_step_f32(colatus_t ctx, const ForcePlan &p, const StepBufs &b, int c, long long step, double tau,
+                     const Extra &D) {
+    const int n = c ^ 1;
+    const float4 *part = static_cast<const float4 *>(ctx->part);
+    const unsigned nb = blocks_for(p.n_pad, kEpiThreads);
+    if (is_kdk(ctx))
+        kdk_step_f32_kernel<COMP, SYM><<<nb, kEpiThreads, 0, ctx->stream>>>(
+            part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.vh, b.acc, b.pk[n], b.table, b.tcap, step, tau, ctx->N,
+            p.n_pad, b.tr, ctx->flags, b.clk, D);
+    else
+        dkd_step_f32_kernel<COMP, SYM><<<nb, kEpiThreads, 0, ctx->stream>>>(
+            part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.acc, b.pk[n], b.table, b.tcap, step, tau, ctx->N, p.n_pad,
+            b.tr, ctx->flags, b.clk, D);
+}
+
 // One step: force on pk[c], then the fused epilogue that writes the state
 // (xs, vs), the next force input pk[c ^ 1] and, for KDK, vh and acc.
 colatus_status launch_step(colatus_t ctx, const StepBufs &b, int c, long long step, double tau) {
@@ -1386,27 +1412,17 @@ colatus_status launch_step(colatus_t ctx, const StepBufs &b, int c, long long st
     } else {
         const ForcePlan &p = plan_f32(ctx);
         TRY(run_force_f32(ctx, p, b.pk[c]));
-        const float4 *part = static_cast<const float4 *>(ctx->part);
         const bool comp = ctx->prec == COLATUS_FP32_COMP;
-        const unsigned nb = blocks_for(p.n_pad, kEpiThreads);
-        if (is_kdk(ctx)) {
+        if (p.L.sym) {
             if (comp)
-                kdk_step_f32_kernel<true><<<nb, kEpiThreads, 0, ctx->stream>>>(
-                    part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.vh, b.acc, b.pk[n], b.table, b.tcap,
-                    step, tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk, D);
+                launch_step_f32<true, true>(ctx, p, b, c, step, tau, D);
             else
-                kdk_step_f32_kernel<false><<<nb, kEpiThreads, 0, ctx->stream>>>(
-                    part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.vh, b.acc, b.pk[n], b.table, b.tcap,
-                    step, tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk, D);
+                launch_step_f32<false, true>(ctx, p, b, c, step, tau, D);
         } else {
             if (comp)
-                dkd_step_f32_kernel<true><<<nb, kEpiThreads, 0, ctx->stream>>>(
-                    part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.acc, b.pk[n], b.table, b.tcap, step,
-                    tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk, D);
+                launch_step_f32<true, false>(ctx, p, b, c, step, tau, D);
             else
-                dkd_step_f32_kernel<false><<<nb, kEpiThreads, 0, ctx->stream>>>(
-                    part, p.L, p.itile, b.pk[c], b.xs, b.vs, b.acc, b.pk[n], b.table, b.tcap, step,
-                    tau, ctx->N, p.n_pad, tr, ctx->flags, b.clk, D);
+                launch_step_f32<false, false>(ctx, p, b, c, step, tau, D);
         }
     }
     return launched(ctx);
@@ -2486,13 +2502,9 @@ colatus_status colatus_adjoint_backward(colatus_t ctx, const void *gx_T, const v
                     TRY(launched(ctx));
                     TRY(run_force_f32(ctx, p, b.pk[0]));
                     if (ctx->prec == COLATUS_FP32_COMP)
-                        forces_out_f32_kernel<true><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
-                            static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk,
-                            ctx->G, nullptr, 0, b.acc, b.pk[0], extra_args(ctx));
+                        launch_forces_out_f32<true>(ctx, p, nullptr, 0, b.acc, b.pk[0]);
                     else
-                        forces_out_f32_kernel<false><<<blocks_for(ctx->N, 256), 256, 0, ctx->stream>>>(
-                            static_cast<const float4 *>(ctx->part), p.L, p.itile, ctx->N, ctx->clk,
-                            ctx->G, nullptr, 0, b.acc, b.pk[0], extra_args(ctx));
+                        launch_forces_out_f32<false>(ctx, p, nullptr, 0, b.acc, b.pk[0]);
                 }
                 TRY(launched(ctx));
                 TRY(launch_kdk_open(ctx, b, 1, s0, a.tau));

@@ -173,13 +173,16 @@ __global__ void pack_f64_kernel(const double4 *__restrict__ xs, double4 *__restr
 }
 
 // ------------------------------------------------------- segment reduction
+// Loads in flight per thread in the pair-once epilogues' sums.
+constexpr int kSymEpiBatch = 4;
+
 // Sum the segments of body i's i-tile in CTA order (deterministic).  Loads
 // are issued four at a time so that several are in flight per thread; the
-// additions keep the fixed order.
+// additions keep the fixed order.  (Plans that evaluate each pair once sum
+// through reduce_sym_f32.)
 template <bool COMP>
 __device__ __forceinline__ float3 reduce_f32(const float4 *__restrict__ part, const ForceLaunch &L,
                                              int itile, long long i) {
-    if (L.sym) return reduce_sym_f32<COMP>(part, L, itile, i);   // each pair evaluated once
     const long long it = i / itile, il = i - it * itile;
     const long long G = L.G, W = L.W;
     const long long g0 = sk_owner(it * L.n_jt, W, G);
@@ -261,7 +264,9 @@ __device__ __forceinline__ double3 reduce_f64(const double4 *__restrict__ part, 
 
 // out (N x 3, float or double) = G a^-3 F at the device clock's a (the
 // comoving acceleration of Eq. 1); optionally cache the G-less F in acc.
-template <bool COMP>
+// SYM: the plan evaluates each pair once (reduce_sym_f32), else every ordered
+// pair (reduce_f32).
+template <bool COMP, bool SYM>
 __global__ void forces_out_f32_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
                                       long long N, const DevClock *__restrict__ clk, double G,
                                       void *out, int out_f64, float4 *__restrict__ acc,
@@ -270,7 +275,7 @@ __global__ void forces_out_f32_kernel(const float4 *__restrict__ part, ForceLaun
     if (i >= N) return;
     const double a = clk->a;
     const float scale = (float)(G / (a * a * a));
-    float3 f = reduce_f32<COMP>(part, L, itile, i);
+    float3 f = SYM ? reduce_sym_f32<COMP, kSymEpiBatch>(part, L, itile, i) : reduce_f32<COMP>(part, L, itile, i);
     if (D.on) {
         const float4 x = pk_load(pk, i);
         defo_force(D, x.x, x.y, x.z, f.x, f.y, f.z);
@@ -379,7 +384,8 @@ __global__ void kdk_open_f32_kernel(const float4 *__restrict__ xs, const float4 
 //   entry's coefficients: vh = c1' v^{n+1} + d1' F;  x^{n+2} = x^{n+1} + tau vh.
 // (For the drag scheme c1', d1' equal c2, d2 bit for bit: both are the half
 // kick at t^{n+1}.)
-template <bool COMP>
+// SYM as in forces_out_f32_kernel.
+template <bool COMP, bool SYM>
 __global__ void kdk_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
                                     const float *__restrict__ pk_in, float4 *__restrict__ xs,
                                     float4 *__restrict__ vs, float4 *__restrict__ vh,
@@ -397,7 +403,7 @@ __global__ void kdk_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
     if (i == 0) advance_clock(clk, sc, flags);
     const float c2 = (float)sc.c2, d2 = (float)sc.d2, t = (float)tau;
     const float c1n = (float)nc.c1, d1n = (float)nc.d1;
-    float3 F = reduce_f32<COMP>(part, L, itile, i);
+    float3 F = SYM ? reduce_sym_f32<COMP, kSymEpiBatch>(part, L, itile, i) : reduce_f32<COMP>(part, L, itile, i);
     const float4 x = pk_load(pk_in, i);
     defo_force(D, x.x, x.y, x.z, F.x, F.y, F.z);
     add_long_range(D, i, F.x, F.y, F.z);
@@ -431,7 +437,8 @@ __global__ void dkd_open_f32_kernel(const float4 *__restrict__ xs, const float4 
 // DKD step j (Eqs. 3-5), after the force at x^{n+1/2} (pk_in):
 //   v^{n+1} = c v^n + d F;  x^{n+1} = x^{n+1/2} + (tau/2) v^{n+1};  record;
 //   next half drift x^{n+3/2} = x^{n+1} + (tau/2) v^{n+1}.
-template <bool COMP>
+// SYM as in forces_out_f32_kernel.
+template <bool COMP, bool SYM>
 __global__ void dkd_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch L, int itile,
                                     const float *__restrict__ pk_in, float4 *__restrict__ xs,
                                     float4 *__restrict__ vs, float4 *__restrict__ acc,
@@ -447,7 +454,7 @@ __global__ void dkd_step_f32_kernel(const float4 *__restrict__ part, ForceLaunch
     const StepCoef &sc = table[step % tcap];
     if (i == 0) advance_clock(clk, sc, flags);
     const float c = (float)sc.c, d = (float)sc.d, h = (float)(0.5 * tau);
-    float3 F = reduce_f32<COMP>(part, L, itile, i);
+    float3 F = SYM ? reduce_sym_f32<COMP, kSymEpiBatch>(part, L, itile, i) : reduce_f32<COMP>(part, L, itile, i);
     const float4 xh = pk_load(pk_in, i);
     defo_force(D, xh.x, xh.y, xh.z, F.x, F.y, F.z);
     add_long_range(D, i, F.x, F.y, F.z);

@@ -563,33 +563,28 @@ __global__ void __launch_bounds__(NT, 1)
 }
 
 // Consumer side: the VJP of body i (float4 dL/dx, dL/dm) of a pair-once plan,
-// its row segments then the column slots on its tile, in that fixed order,
-// eight independent loads at a time.
+// its row segments then the column slots on its tile, in that fixed order.
 __device__ __forceinline__ float4 reduce_vjp_sym_f32(const float4 *__restrict__ part, const ForceLaunch &L,
                                                      int T, long long i) {
     const SymTab S(L.sym);
     const long long t = i / T, il = i - t * T;
     float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
     auto run = [&](const float4 *p, int cnt) {
-        int s = 0;
-        for (; s + 8 <= cnt; s += 8) {
-            float4 v[8];
+        // four loads at a time, the last batch predicated; the sum keeps its order
+        for (int s = 0; s < cnt; s += 4) {
+            float4 v[4];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] = __ldg(p + (long long)(s + k) * T);
+            for (int k = 0; k < 4; ++k)
+                if (s + k < cnt) v[k] = __ldg(p + (long long)(s + k) * T);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                r.x += v[k].x;
-                r.y += v[k].y;
-                r.z += v[k].z;
-                r.w += v[k].w;
+            for (int k = 0; k < 4; ++k) {
+                if (s + k < cnt) {
+                    r.x += v[k].x;
+                    r.y += v[k].y;
+                    r.z += v[k].z;
+                    r.w += v[k].w;
+                }
             }
-        }
-        for (; s < cnt; ++s) {
-            const float4 v = __ldg(p + (long long)s * T);
-            r.x += v.x;
-            r.y += v.y;
-            r.z += v.z;
-            r.w += v.w;
         }
     };
     run(part + t * L.S_max * (long long)T + il, S.row_ns[t]);
