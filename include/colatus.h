@@ -283,10 +283,12 @@ colatus_status colatus_force_plan(colatus_t ctx, int64_t out[9]);
  * real space, 3 FP64 periodic real space, 4 FP32 equal-mass, 5 FP32
  * equal-mass with every pair evaluated once, from 8 tiles of 1024 bodies,
  * 6 FP32 any masses with every pair evaluated once, from 8 tiles: also the
- * kernel of colatus_force_vjp then),
+ * kernel of colatus_force_vjp then, 7 FP32 periodic real space with every
+ * pair evaluated once, from 8 tiles of 1024 bodies under tuning shape 3 or
+ * the built-in choice, as the periodic force),
  * out[1] threads per CTA, out[2] i-bodies per thread, out[3] j-tile bodies,
  * out[4] persistent grid (CTAs), out[5] work units (i-tile x j-tile; for
- * kinds 5 and 6 the tile pairs it <= jt).  Errors: COLATUS_E_ARG. */
+ * kinds 5 to 7 the tile pairs it <= jt).  Errors: COLATUS_E_ARG. */
 colatus_status colatus_vjp_plan(colatus_t ctx, int64_t out[6]);
 
 /* Kernel timing for measurement: with on != 0 every launch of the force

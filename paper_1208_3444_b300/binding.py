@@ -507,7 +507,7 @@ class Simulation:
         out = np.zeros(6, dtype=np.int64)
         _check(lib().colatus_vjp_plan(self.h, out.ctypes.data), self.h)
         kinds = ("vjp_f32", "vjp_f64", "ewald_vjp_f32", "ewald_vjp_f64", "vjp_eqm_f32", "vjp_sym_eqm_f32",
-                 "vjp_sym_f32")
+                 "vjp_sym_f32", "ewald_vjp_sym_f32")
         return dict(kind=kinds[int(out[0])], threads=int(out[1]), ipt=int(out[2]), jt=int(out[3]),
                     grid=int(out[4]), units=int(out[5]))
 

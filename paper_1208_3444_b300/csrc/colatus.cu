@@ -170,6 +170,8 @@ using Ew64K = EwaldF64Kernel<kEw64NT, kEw64JT, kStages>;
 // the VJP layout; FP64 128 x 1, 32-body tiles.
 constexpr int kEwVjpNT = 256, kEwVjpIPT = 2, kEwVjpJT = 256, kEwVjpMinB = 1;
 using EwVjpK = EwaldVjpKernel<kEwVjpNT, kEwVjpIPT, kEwVjpJT, kStages>;
+// pair-once periodic VJP: the VJP for any masses with the real-space pair term
+constexpr int kEwVjpSymUnr = 2;
 constexpr int kEwV64NT = 128, kEwV64JT = 32;
 using EwVjp64K = EwaldVjp64Kernel<kEwV64NT, kEwV64JT, kStages>;
 constexpr int kEwMaxNk = 63;   // shared memory of the k-space kernels in FP64; a pencil fits one block
@@ -322,7 +324,9 @@ struct colatus_ctx {
     ForcePlan plan_vjp_sym;            // pair-once equal-mass VJP (fits: usable for this N)
     int *vjp_sym_tab = nullptr;
     ForcePlan plan_vjp_gen;            // pair-once VJP for any masses
+    ForcePlan plan_ewvjp_sym;          // pair-once periodic real-space VJP
     int *vjp_gen_tab = nullptr;
+    int *ewvjp_sym_tab = nullptr;
     ForcePlan plan_ewvjp32, plan_ewvjp64;   // periodic VJP (real space)
 
     // periodic boundaries (colatus_set_periodic): Ewald parameters and buffers
@@ -583,6 +587,37 @@ colatus_status build_plans(colatus_t ctx) {
             CU(cudaMalloc(&ctx->vjp_gen_tab, st.tab.size() * sizeof(int)));
             CU(cudaMemcpy(ctx->vjp_gen_tab, st.tab.data(), st.tab.size() * sizeof(int), cudaMemcpyHostToDevice));
             q.L.sym = ctx->vjp_gen_tab;
+        }
+    }
+    {
+        // the same kernel with the periodic real-space pair term: tables with
+        // its phase costs (68 lane-ops per diagonal interaction, 75 per
+        // symmetric pair)
+        auto fn = vjp_sym_f32_kernel<kVjpGenNT, kEwVjpSymUnr, false, EwaldVjpPair>;
+        CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, VjpGenK::SMEM));
+        CU(cudaFuncSetAttribute(vjp_sym_f32_kernel<kVjpGenNT, kEwVjpSymUnr, true, EwaldVjpPair>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, VjpGenK::SMEM));
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kVjpGenNT, VjpGenK::SMEM));
+        if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "pair-once periodic VJP kernel cannot be resident");
+        ForcePlan &q = ctx->plan_ewvjp_sym;
+        q.itile = q.jt = VjpGenK::T;
+        q.n_pad = round_up(ctx->N, VjpGenK::T);
+        const bool may = sym_may_fit(ctx, q.n_pad, VjpGenK::T, 1);
+        const SymTables st = may ? build_sym_tables(q.n_pad, VjpGenK::T, VjpGenK::NW,
+                                                    (long long)occ * std::max(1, ctx->num_sms - 1), 68, 75)
+                                 : SymTables{};
+        q.L = ForceLaunch{};
+        q.L.W = st.U;
+        q.L.n_it = q.L.n_jt = st.n;
+        q.L.G = st.G;
+        q.L.S_max = st.S_row;
+        q.L.col_off = (long long)st.n * st.S_row * q.itile;
+        q.part_bytes = (size_t)((long long)st.n * st.S_row + st.slots) * q.itile * sizeof(float4);
+        q.fits = may && st.n >= kSymMinTiles && q.part_bytes <= ctx->sym_max_bytes;
+        if (q.fits) {
+            CU(cudaMalloc(&ctx->ewvjp_sym_tab, st.tab.size() * sizeof(int)));
+            CU(cudaMemcpy(ctx->ewvjp_sym_tab, st.tab.data(), st.tab.size() * sizeof(int), cudaMemcpyHostToDevice));
+            q.L.sym = ctx->ewvjp_sym_tab;
         }
     }
     ForcePlan &w = ctx->plan_vjp64;
@@ -1152,7 +1187,8 @@ void free_all(colatus_t ctx) {
                     ctx->tclk, ctx->table, ctx->stage, ctx->stage2, ctx->diag, ctx->tslot,
                     ctx->rec, ctx->kw, ctx->rho, ctx->rho_part, ctx->wcs, ctx->pen,
                     ctx->rchunk, ctx->fchunk, ctx->lr, ctx->ph, ctx->pot_part, ctx->lrv,
-                    ctx->kwr, ctx->kwl, ctx->pk_ew, ctx->vjp_sym_tab, ctx->ew_sym_tab, ctx->vjp_gen_tab};
+                    ctx->kwr, ctx->kwl, ctx->pk_ew, ctx->vjp_sym_tab, ctx->ew_sym_tab, ctx->vjp_gen_tab,
+                    ctx->ewvjp_sym_tab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *tptrs[] = {ctx->tan.dx, ctx->tan.dv, ctx->tan.dvh, ctx->tan.dxp, ctx->tan.pkt,
@@ -1485,13 +1521,19 @@ colatus_status grow(colatus_t ctx, void **p, size_t *have, size_t need) {
     return COLATUS_OK;
 }
 
-// The VJP's launch plan: the periodic kernel's when the boundaries are periodic;
-// in FP32 the pair-once kernels' where they fit (same padding as the
-// per-ordered-pair VJP): the equal-mass one for eqm (the KDK adjoint's), the
-// one for any masses otherwise.
+// The VJP's launch plan: the periodic kernel's when the boundaries are periodic
+// (in FP32 the pair-once one where it fits, under tuning shape 3 or the
+// built-in choice, as the periodic force); in FP32 the pair-once kernels'
+// where they fit (same padding as the per-ordered-pair VJP): the equal-mass
+// one for eqm (the KDK adjoint's), the one for any masses otherwise.
 const ForcePlan &vjp_plan(colatus_t ctx, bool eqm = false) {
     const bool f64 = ctx->prec == COLATUS_FP64;
-    if (ctx->periodic) return f64 ? ctx->plan_ewvjp64 : ctx->plan_ewvjp32;
+    if (ctx->periodic && f64) return ctx->plan_ewvjp64;
+    if (ctx->periodic) {
+        const ForcePlan &q = ctx->plan_ewvjp_sym;
+        const bool sym = q.fits && (ctx->tuned_shape < 0 || ctx->tuned_shape == kSymShape);
+        return sym ? q : ctx->plan_ewvjp32;
+    }
     if (f64) return ctx->plan_vjp64;
     if (eqm && ctx->plan_vjp_sym.fits) return ctx->plan_vjp_sym;
     if (!eqm && ctx->plan_vjp_gen.fits) return ctx->plan_vjp_gen;
@@ -1579,6 +1621,16 @@ colatus_status run_vjp(colatus_t ctx, bool eqm = false) {
         ewald_vjp_f64_kernel<kEwV64NT, kEwV64JT, kStages><<<p.L.G, kEwV64NT, EwVjp64K::SMEM, ctx->stream>>>(
             static_cast<const double4 *>(ctx->adj.pkw), static_cast<double4 *>(ctx->part), ctx->flags,
             p.L, ctx->eps * ctx->eps, ctx->ew);
+    else if (ctx->periodic && p.L.sym && ctx->eq_mass && p.n_pad == ctx->N)
+        vjp_sym_f32_kernel<kVjpGenNT, kEwVjpSymUnr, true, EwaldVjpPair>
+            <<<p.L.G, kVjpGenNT, VjpGenK::SMEM, ctx->stream>>>(
+                static_cast<const float *>(ctx->adj.pkw), static_cast<float4 *>(ctx->part), ctx->flags, p.L,
+                (float)(ctx->eps * ctx->eps), ctx->mass_eq, ctx->ew);
+    else if (ctx->periodic && p.L.sym)
+        vjp_sym_f32_kernel<kVjpGenNT, kEwVjpSymUnr, false, EwaldVjpPair>
+            <<<p.L.G, kVjpGenNT, VjpGenK::SMEM, ctx->stream>>>(
+                static_cast<const float *>(ctx->adj.pkw), static_cast<float4 *>(ctx->part), ctx->flags, p.L,
+                (float)(ctx->eps * ctx->eps), 1.f, ctx->ew);
     else if (ctx->periodic)
         ewald_vjp_f32_kernel<kEwVjpNT, kEwVjpIPT, kEwVjpJT, kStages, kEwVjpMinB>
             <<<p.L.G, kEwVjpNT, EwVjpK::SMEM, ctx->stream>>>(
@@ -1596,11 +1648,11 @@ colatus_status run_vjp(colatus_t ctx, bool eqm = false) {
     else if (p.L.sym && ctx->eq_mass && p.n_pad == ctx->N)
         vjp_sym_f32_kernel<kVjpGenNT, kVjpGenUnr, true><<<p.L.G, kVjpGenNT, VjpGenK::SMEM, ctx->stream>>>(
             static_cast<const float *>(ctx->adj.pkw), static_cast<float4 *>(ctx->part), ctx->flags, p.L,
-            (float)(ctx->eps * ctx->eps), ctx->mass_eq);
+            (float)(ctx->eps * ctx->eps), ctx->mass_eq, PlummerVjpPair::Args{});
     else if (p.L.sym)
         vjp_sym_f32_kernel<kVjpGenNT, kVjpGenUnr, false><<<p.L.G, kVjpGenNT, VjpGenK::SMEM, ctx->stream>>>(
             static_cast<const float *>(ctx->adj.pkw), static_cast<float4 *>(ctx->part), ctx->flags, p.L,
-            (float)(ctx->eps * ctx->eps), 1.f);
+            (float)(ctx->eps * ctx->eps), 1.f, PlummerVjpPair::Args{});
     else if (f64)
         vjp_f64_kernel<kV64NT, kV64JT, kStages><<<p.L.G, kV64NT, Vjp64K::SMEM, ctx->stream>>>(
             static_cast<const double4 *>(ctx->adj.pkw), static_cast<double4 *>(ctx->part),
@@ -1797,7 +1849,7 @@ colatus_status colatus_init(colatus_t *out, int64_t N, const double *masses, dou
     for (const ForcePlan *p : {&ctx->plan64, &ctx->plan_vjp32, &ctx->plan_vjp64, &ctx->plan_ewvjp32,
                                &ctx->plan_ewvjp64, &ctx->plan_ew32[0],
                                &ctx->plan_ew32[1], &ctx->plan_ew64, &ctx->plan_vjp_sym, &ctx->plan_vjp_gen,
-                               &ctx->plan_ew_sym[0], &ctx->plan_ew_sym[1]})
+                               &ctx->plan_ew_sym[0], &ctx->plan_ew_sym[1], &ctx->plan_ewvjp_sym})
         ctx->n_alloc = std::max(ctx->n_alloc, p->n_pad);
     ctx->eps = eps;
     ctx->cosmo = Cosmo{Omega_R, Omega_M, Omega_K, Omega_L, H0};
@@ -3004,7 +3056,11 @@ colatus_status colatus_vjp_plan(colatus_t ctx, int64_t out[6]) {
     const bool eqm = ctx->scheme != COLATUS_DKD && !f64 && ctx->eq_mass && !ctx->periodic &&
                      ctx->defo_C == 0.0 && p0.n_pad == ctx->N;
     const ForcePlan &p = vjp_plan(ctx, eqm);
-    if (ctx->periodic) {
+    if (ctx->periodic && !f64 && p.L.sym) {
+        out[0] = 7;
+        out[1] = kVjpGenNT;
+        out[2] = VjpGenK::IPT;
+    } else if (ctx->periodic) {
         out[0] = f64 ? 3 : 2;
         out[1] = f64 ? kEwV64NT : kEwVjpNT;
         out[2] = f64 ? 1 : kEwVjpIPT;

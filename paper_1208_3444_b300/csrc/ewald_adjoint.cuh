@@ -87,6 +87,47 @@ __device__ __forceinline__ void ewald_pair_bc2(const float2 dx, const float2 dy,
     nc = __ffma2_rn(ip5, make_float2(3.f, 3.f), ce);
 }
 
+// Pair policy of the pair-once VJP (vjp_sym.cuh) for the real-space term:
+// the separation to its minimum image, then b and -c of ewald_pair_bc2
+// (finite at d = 0, where the series holds, so a body's own pair adds
+// exactly 0 with u' = 0); J u' = b u' + c (u'.d) d is formed once and added
+// to the row sums and, SYM, to the column sums.
+struct EwaldVjpPair {
+    using Args = EwaldArgs;
+    struct F {
+        float2 b, nc;
+    };
+    __device__ __forceinline__ static F factors(float2 &dx, float2 &dy, float2 &dz, const float2 e2,
+                                                const EwaldArgs &A) {
+        const float2 Lm = make_float2(-A.Lf, -A.Lf), iL = make_float2(A.invLf, A.invLf);
+        dx = min_image2(dx, iL, Lm);
+        dy = min_image2(dy, iL, Lm);
+        dz = min_image2(dz, iL, Lm);
+        F f;
+        ewald_pair_bc2(dx, dy, dz, A, e2, f.b, f.nc);
+        return f;
+    }
+    __device__ __forceinline__ static float2 bw(const F &f) { return f.b; }
+    template <bool SYM>
+    __device__ __forceinline__ static void position(const F &f, const float2 dx, const float2 dy, const float2 dz,
+                                                    const float2 ux, const float2 uy, const float2 uz,
+                                                    const float2 du, float2 &tx, float2 &ty, float2 &tz, float2 &jx,
+                                                    float2 &jy, float2 &jz) {
+        const float2 cdu = __fmul2_rn(make_float2(-f.nc.x, -f.nc.y), du);   // c (u'.d)
+        const float2 sx = __ffma2_rn(cdu, dx, __fmul2_rn(f.b, ux));
+        const float2 sy = __ffma2_rn(cdu, dy, __fmul2_rn(f.b, uy));
+        const float2 sz = __ffma2_rn(cdu, dz, __fmul2_rn(f.b, uz));
+        tx = __fadd2_rn(tx, sx);
+        ty = __fadd2_rn(ty, sy);
+        tz = __fadd2_rn(tz, sz);
+        if (SYM) {
+            jx = __fadd2_rn(jx, sx);
+            jy = __fadd2_rn(jy, sy);
+            jz = __fadd2_rn(jz, sz);
+        }
+    }
+};
+
 template <int NT, int IPT, int JT, int STAGES>
 struct EwaldVjpKernel {
     static constexpr int ITILE = NT * IPT;

@@ -282,16 +282,20 @@ __global__ void __launch_bounds__(NT, 1)
 // adds (inv^3 s, -inv^3 (w_j . d)) to body i and (-inv^3 s, inv^3 (w_i . d))
 // to body j: 40 FP32 lane-ops per pair and one MUFU.RSQ, against 2 x 25 for
 // the per-ordered-pair kernel's scaled form.  u' is formed as
-//   u' = m_i (w_j - w_i) + (m_i - m_j) w_i:
+//   u' = m_j (w_j - w_i) + (m_i - m_j) w_j:
 // the difference of the co-vectors first, so that with equal masses u' is
 // that difference times m (the second term exactly 0), its rounding as
-// well conditioned as in the equal-mass form, and a body's own pair exactly
-// 0.  The product form m_i w_j - m_j w_i would leave the rounding of m_j w_i,
-// an error that depends on i alone and so adds up coherently over every j
-// (measured: 50x the per-ordered-pair kernel's error in a DKD adjoint).
+// well conditioned as in the equal-mass form; a body's own pair and a
+// padding body j (zero mass and co-vector) give exactly 0.  The product form
+// m_i w_j - m_j w_i would leave the rounding of m_j w_i, an error that
+// depends on i alone and so adds up coherently over every j (measured: 50x
+// the per-ordered-pair kernel's error in a DKD adjoint).
 // EQM (every mass m, no padding): u' = m (w_j - w_i), the factor m applied to
 // the position sums when they are written, and w_j . d taken as
 // (w_j - w_i) . d + w_i . d: 31 lane-ops per pair.
+// The pair term is a policy P (J = b I + c d d^T): PlummerVjpPair here (Eq. 1),
+// EwaldVjpPair (ewald_adjoint.cuh) for the real-space term of the periodic
+// force, whose separations take the minimum image.
 
 template <int NT>
 struct VjpSymGenKernel {
@@ -309,17 +313,56 @@ struct VjpSymGenKernel {
     static_assert(SLICE % 32 == 0, "a warp slice is whole rotations");
 };
 
-template <bool SYM, bool EQM, int UNR>
+// Pair policy of Eq. 1: J(d) = inv^3 (I - 3 inv^2 d d^T), inv = (r^2+eps^2)^-1/2.
+// factors() fills the pair's factors (d unchanged); bw() is b, the weight of
+// the mass terms; position() adds J u' to the row sums t and, SYM, to the
+// column sums j, as inv^3 s with s = u' - 3 inv^2 (u'.d) d.
+struct PlummerVjpPair {
+    struct Args {};
+    struct F {
+        float2 inv2, inv3;
+    };
+    __device__ __forceinline__ static F factors(float2 &dx, float2 &dy, float2 &dz, const float2 e2, const Args &) {
+        float2 r2 = __ffma2_rn(dx, dx, e2);
+        r2 = __ffma2_rn(dy, dy, r2);
+        r2 = __ffma2_rn(dz, dz, r2);
+        const float2 inv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+        F f;
+        f.inv2 = __fmul2_rn(inv, inv);
+        f.inv3 = __fmul2_rn(inv, f.inv2);
+        return f;
+    }
+    __device__ __forceinline__ static float2 bw(const F &f) { return f.inv3; }
+    template <bool SYM>
+    __device__ __forceinline__ static void position(const F &f, const float2 dx, const float2 dy, const float2 dz,
+                                                    const float2 ux, const float2 uy, const float2 uz,
+                                                    const float2 du, float2 &tx, float2 &ty, float2 &tz, float2 &jx,
+                                                    float2 &jy, float2 &jz) {
+        const float2 q = __fmul2_rn(__fmul2_rn(f.inv2, du), make_float2(-3.f, -3.f));
+        const float2 sx = __ffma2_rn(q, dx, ux);
+        const float2 sy = __ffma2_rn(q, dy, uy);
+        const float2 sz = __ffma2_rn(q, dz, uz);
+        tx = __ffma2_rn(f.inv3, sx, tx);
+        ty = __ffma2_rn(f.inv3, sy, ty);
+        tz = __ffma2_rn(f.inv3, sz, tz);
+        if (SYM) {
+            jx = __ffma2_rn(f.inv3, sx, jx);
+            jy = __ffma2_rn(f.inv3, sy, jy);
+            jz = __ffma2_rn(f.inv3, sz, jz);
+        }
+    }
+};
+
+template <typename P, bool SYM, bool EQM, int UNR>
 __device__ __forceinline__ void vjp_gen_rotation(const float4 *__restrict__ sA, const float4 *__restrict__ sB,
                                                  const float4 *__restrict__ sC, const float2 *__restrict__ sD,
                                                  int lane, const float2 (&nx)[4], const float2 (&ny)[4],
                                                  const float2 (&nz)[4], const float2 (&mi)[4],
                                                  const float2 (&wix)[4], const float2 (&wiy)[4],
-                                                 const float2 (&wiz)[4], const float2 e2, float2 (&tx)[4],
-                                                 float2 (&ty)[4], float2 (&tz)[4], float2 (&tg)[4], float2 &jx,
-                                                 float2 &jy, float2 &jz, float2 &jg) {
+                                                 const float2 (&wiz)[4], const float2 e2, const typename P::Args &pa,
+                                                 float2 (&tx)[4], float2 (&ty)[4], float2 (&tz)[4], float2 (&tg)[4],
+                                                 float2 &jx, float2 &jy, float2 &jz, float2 &jg) {
     const int src = (lane + 1) & 31;
-    const float2 n3 = make_float2(-3.f, -3.f);
     const float4 *a = sA + lane, *b = sB + lane, *c = sC + lane;
     const float2 *dd = sD + lane;
 #pragma unroll(UNR)
@@ -333,15 +376,11 @@ __device__ __forceinline__ void vjp_gen_rotation(const float4 *__restrict__ sA, 
         const float2 wxj = make_float2(C.x, C.y), wyj = make_float2(C.z, C.w);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const float2 dx = __fadd2_rn(xj, nx[k]);
-            const float2 dy = __fadd2_rn(yj, ny[k]);
-            const float2 dz = __fadd2_rn(zj, nz[k]);
-            float2 r2 = __ffma2_rn(dx, dx, e2);
-            r2 = __ffma2_rn(dy, dy, r2);
-            r2 = __ffma2_rn(dz, dz, r2);
-            const float2 inv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-            const float2 inv2 = __fmul2_rn(inv, inv);
-            const float2 inv3 = __fmul2_rn(inv, inv2);
+            float2 dx = __fadd2_rn(xj, nx[k]);
+            float2 dy = __fadd2_rn(yj, ny[k]);
+            float2 dz = __fadd2_rn(zj, nz[k]);
+            const typename P::F f = P::factors(dx, dy, dz, e2, pa);
+            const float2 bw = P::bw(f);
             float2 wid = __fmul2_rn(wix[k], dx);
             wid = __ffma2_rn(wiy[k], dy, wid);
             wid = __ffma2_rn(wiz[k], dz, wid);
@@ -359,29 +398,18 @@ __device__ __forceinline__ void vjp_gen_rotation(const float4 *__restrict__ sA, 
                 wjd = __fmul2_rn(wxj, dx);
                 wjd = __ffma2_rn(wyj, dy, wjd);
                 wjd = __ffma2_rn(wzj, dz, wjd);
-                // u' = m_i (w_j - w_i) + (m_i - m_j) w_i
+                // u' = m_j (w_j - w_i) + (m_i - m_j) w_j
                 const float2 dm = __fadd2_rn(mi[k], make_float2(-mj.x, -mj.y));
-                ux = __ffma2_rn(mi[k], __fadd2_rn(wxj, make_float2(-wix[k].x, -wix[k].y)), __fmul2_rn(dm, wix[k]));
-                uy = __ffma2_rn(mi[k], __fadd2_rn(wyj, make_float2(-wiy[k].x, -wiy[k].y)), __fmul2_rn(dm, wiy[k]));
-                uz = __ffma2_rn(mi[k], __fadd2_rn(wzj, make_float2(-wiz[k].x, -wiz[k].y)), __fmul2_rn(dm, wiz[k]));
+                ux = __ffma2_rn(mj, __fadd2_rn(wxj, make_float2(-wix[k].x, -wix[k].y)), __fmul2_rn(dm, wxj));
+                uy = __ffma2_rn(mj, __fadd2_rn(wyj, make_float2(-wiy[k].x, -wiy[k].y)), __fmul2_rn(dm, wyj));
+                uz = __ffma2_rn(mj, __fadd2_rn(wzj, make_float2(-wiz[k].x, -wiz[k].y)), __fmul2_rn(dm, wzj));
                 du = __fmul2_rn(ux, dx);
                 du = __ffma2_rn(uy, dy, du);
                 du = __ffma2_rn(uz, dz, du);
             }
-            const float2 q = __fmul2_rn(__fmul2_rn(inv2, du), n3);
-            const float2 sx = __ffma2_rn(q, dx, ux);
-            const float2 sy = __ffma2_rn(q, dy, uy);
-            const float2 sz = __ffma2_rn(q, dz, uz);
-            tx[k] = __ffma2_rn(inv3, sx, tx[k]);
-            ty[k] = __ffma2_rn(inv3, sy, ty[k]);
-            tz[k] = __ffma2_rn(inv3, sz, tz[k]);
-            tg[k] = __ffma2_rn(inv3, wjd, tg[k]);
-            if (SYM) {
-                jx = __ffma2_rn(inv3, sx, jx);
-                jy = __ffma2_rn(inv3, sy, jy);
-                jz = __ffma2_rn(inv3, sz, jz);
-                jg = __ffma2_rn(inv3, wid, jg);
-            }
+            P::template position<SYM>(f, dx, dy, dz, ux, uy, uz, du, tx[k], ty[k], tz[k], jx, jy, jz);
+            tg[k] = __ffma2_rn(bw, wjd, tg[k]);
+            if (SYM) jg = __ffma2_rn(bw, wid, jg);
         }
         if (SYM) {
             jx = shfl_float2(jx, src);
@@ -398,10 +426,11 @@ __device__ __forceinline__ void vjp_gen_rotation(const float4 *__restrict__ sA, 
 // [n][S_max][T] float4, then from float4 offset L.col_off the column slots
 // [slot][T] float4, each float4 (dL/dx, dL/dm) of the bodies it indexes.
 // EQM: every body has mass `mass` and no padding enters (N_pad = N).
-template <int NT, int UNR, bool EQM>
+// P: the pair term (PlummerVjpPair, EwaldVjpPair) and its arguments pa.
+template <int NT, int UNR, bool EQM, typename P = PlummerVjpPair>
 __global__ void __launch_bounds__(NT, 1)
     vjp_sym_f32_kernel(const float *__restrict__ pkw, float4 *__restrict__ part, int *__restrict__ flags,
-                       ForceLaunch L, float eps2, float mass) {
+                       ForceLaunch L, float eps2, float mass, typename P::Args pa) {
     using K = VjpSymGenKernel<NT>;
     constexpr int NW = K::NW, T = K::T, TP = K::TP;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -510,16 +539,16 @@ __global__ void __launch_bounds__(NT, 1)
                 const float2 *bD = sD + 2 * base;
                 float2 jx = make_float2(0.f, 0.f), jy = jx, jz = jx, jg = jx;
                 if (sym) {
-                    vjp_gen_rotation<true, EQM, UNR>(bA, bB, bC, bD, lane, nx, ny, nz, mi, wix, wiy, wiz, e2, tx,
-                                                     ty, tz, tg, jx, jy, jz, jg);
+                    vjp_gen_rotation<P, true, EQM, UNR>(bA, bB, bC, bD, lane, nx, ny, nz, mi, wix, wiy, wiz, e2,
+                                                        pa, tx, ty, tz, tg, jx, jy, jz, jg);
                     const int q = base + lane;
                     acc[q] = __fadd2_rn(acc[q], jx);
                     acc[TP + q] = __fadd2_rn(acc[TP + q], jy);
                     acc[2 * TP + q] = __fadd2_rn(acc[2 * TP + q], jz);
                     acc[3 * TP + q] = __fadd2_rn(acc[3 * TP + q], jg);
                 } else {
-                    vjp_gen_rotation<false, EQM, UNR>(bA, bB, bC, bD, lane, nx, ny, nz, mi, wix, wiy, wiz, e2,
-                                                      tx, ty, tz, tg, jx, jy, jz, jg);
+                    vjp_gen_rotation<P, false, EQM, UNR>(bA, bB, bC, bD, lane, nx, ny, nz, mi, wix, wiy, wiz, e2,
+                                                         pa, tx, ty, tz, tg, jx, jy, jz, jg);
                 }
             }
 #pragma unroll

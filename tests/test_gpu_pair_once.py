@@ -339,6 +339,28 @@ def test_force_vjp_pair_once_matches_oracle(N, equal, prec):
     assert rel(gm[sel], rm / a ** 3) < 1e-5
 
 
+@pytest.mark.parametrize("N", [8192, 9001])
+def test_force_vjp_pair_once_uniform_covector_position_term_is_exactly_zero(N):
+    # equal masses and one co-vector for every body: u' = m_i w_j - m_j w_i = 0
+    # for every pair, so dL/dx is 0 in exact arithmetic.  The pair-once form
+    # computes u' from the co-vector difference, so it returns exactly 0: at
+    # 8192 in the equal-mass form, at 9001 in the form for any masses, where
+    # the 215 padding bodies (zero mass and co-vector) must add exactly 0 too.
+    # dL/dm = -sum_j inv^3 (w . d) does not vanish and is checked as usual.
+    x, m, _ = vjp_system(N, 370 + N, equal=True)
+    w = np.tile(inputs.f32(np.array([[0.3, -1.2, 0.7]])), (N, 1))
+    a, G, eps = 0.5, 1.3, 0.002
+    sim = B.Simulation(m, eps, LCDM_D, a, prec=B.FP32, G=G)
+    try:
+        sim.set_state(x)
+        gx, gm = sim.force_vjp(w)
+    finally:
+        sim.close()
+    assert np.count_nonzero(gx) == 0
+    _, rm = oracle.vjp(x, m, w, eps, G)
+    assert rel(gm, rm / a ** 3) < 1e-5
+
+
 @pytest.mark.parametrize("case", ["massless", "tiny", "huge", "zero_covector", "coincident"])
 def test_force_vjp_pair_once_mass_edge_cases(case):
     # massless bodies with co-vectors, masses of 1e-25 and of 3e11 / 3e21,
@@ -399,3 +421,96 @@ def test_dkd_adjoint_pair_once_vjp(prec, k):
                              np.zeros_like(ic.x), gvO, gmO, scheme="dkd")
     for key, got, want in zip(("gx", "gv", "gm"), g, ref):
         assert rel(got, want) < 1e-4, key
+
+
+# ---- the pair-once VJP under periodic boundaries (the real-space term of the
+# Ewald sum as its pair policy: minimum image, then b and c of the erfc form;
+# from 8 tiles of 1024 bodies)
+
+def periodic_force_vjp(x, m, w, eps, L, prec, shape=-1, a=1.0, G=1.0):
+    sim = B.Simulation(m, eps, LCDM_D, a, prec=prec, G=G)
+    try:
+        sim.set_state(x)
+        sim.set_tuning(shape)
+        sim.set_periodic(L)
+        gx, gm = sim.force_vjp(w)
+        return gx, gm, sim.vjp_plan()["kind"]
+    finally:
+        sim.close()
+
+
+@pytest.mark.parametrize("prec", [B.FP32, B.FP32_COMP])
+@pytest.mark.parametrize("N,equal", [(8192, True), (8192, False), (9001, False)])
+def test_periodic_force_vjp_pair_once_matches_oracle(N, equal, prec):
+    rng = np.random.default_rng(960 + N)
+    L = 2.5
+    x = inputs.f32(L * rng.random((N, 3)))
+    m = inputs.f32(np.full(N, 1.0 / N) if equal else rng.lognormal(0.0, 0.5, N) / N)
+    w = inputs.f32(rng.standard_normal((N, 3)))
+    eps, a, G = 0.01, 0.5, 1.3
+    gx, gm, kind = periodic_force_vjp(x, m, w, eps, L, prec, a=a, G=G)
+    assert kind == "ewald_vjp_sym_f32"
+    rows = np.sort(np.random.default_rng(N + 1).choice(N, 512, replace=False))
+    rx, rm = oracle.ewald_vjp(x, m, w, eps, L, G, rows=rows)
+    s = 1.0 / a ** 3
+    ex, em = rel(gx[rows], s * rx), rel(gm[rows], s * rm)
+    assert ex < 1e-5 and em < 1e-5, (ex, em)
+    # the per-ordered-pair real-space VJP (any tuning shape but 3): the two
+    # differ in the order of the pair sums and in how u' rounds
+    gx0, gm0, kind0 = periodic_force_vjp(x, m, w, eps, L, prec, shape=2, a=a, G=G)
+    assert kind0 == "ewald_vjp_f32"
+    dx, dm = rel(gx, gx0), rel(gm, gm0)
+    assert dx < 5e-6 and dm < 5e-6, (dx, dm)
+
+
+def test_periodic_vjp_plan_kinds():
+    x, m = system(8192, False, 6)
+    for kw, shape, kind in ((dict(), -1, "ewald_vjp_sym_f32"), (dict(scheme=B.DKD), 3, "ewald_vjp_sym_f32"),
+                            (dict(), 0, "ewald_vjp_f32"), (dict(prec=B.FP64), -1, "ewald_vjp_f64")):
+        sim = B.Simulation(m, 0.01, LCDM_D, 1.0, **{"prec": B.FP32, **kw})
+        try:
+            sim.set_state(x)
+            sim.set_tuning(shape)
+            sim.set_periodic(1.0)
+            assert sim.vjp_plan()["kind"] == kind, (kw, shape)
+        finally:
+            sim.close()
+    x, m = system(7168, False, 6)   # 7 tiles
+    sim = B.Simulation(m, 0.01, LCDM_D, 1.0, prec=B.FP32)
+    try:
+        sim.set_state(x)
+        sim.set_periodic(1.0)
+        assert sim.vjp_plan()["kind"] == "ewald_vjp_f32"
+    finally:
+        sim.close()
+
+
+@pytest.mark.parametrize("scheme", ["kdk", "dkd"])
+def test_periodic_adjoint_pair_once_matches_per_pair_kernel(scheme):
+    # 8192 bodies of the 32^3 recipe in the periodic unit box, 6 steps with
+    # checkpoints every 4, then the adjoint of a tracer loss: with the
+    # pair-once real-space force and VJP against the per-ordered-pair ones
+    # (both are checked against the oracle above and in the periodic tests)
+    ic = inputs.perturbed_grid(21, 0.1, 0.02, 43, zeldovich=True, count=8192,
+                               total_mass=inputs.CRITICAL_MATTER_DENSITY)
+    tr = inputs.tracers(ic.N, 64, 7)
+    out = []
+    for shape in (3, 2):
+        sim = B.Simulation(ic.m, ic.eps, LCDM_D, inputs.A_START, prec=B.FP32_COMP,
+                           scheme=B.KDK if scheme == "kdk" else B.DKD)
+        try:
+            sim.set_state(ic.x, ic.v)
+            sim.set_tuning(shape)
+            sim.set_periodic(1.0)
+            kind = sim.vjp_plan()["kind"]
+            sim.adjoint_forward(TAU, 6, 4)
+            xT, vT, t, aT = sim.state()
+            gvT, gmT = tracer_loss_grads(xT, vT, ic.m, aT, tr)
+            out.append((kind,) + tuple(sim.adjoint_backward(None, gvT, gmT)))
+        finally:
+            sim.close()
+    (k3, *g3), (k2, *g2) = out
+    assert k3 == "ewald_vjp_sym_f32" and k2 == "ewald_vjp_f32"
+    for key, a, b in zip(("gx", "gv", "gm"), g3, g2):
+        e = rel(a, b)
+        assert e < 2e-5, (key, e)
