@@ -542,6 +542,7 @@ def time_periodic(B, inputs, torch, stream, nsteps=10):
         torch.cuda.synchronize()
         vms, vn = sim.profile_read(vjp=True)
         sim.profile_forces(False)
+        vjp_kind = sim.vjp_plan()["kind"]
     finally:
         sim.close()
     ms = e0.elapsed_time(e1) / nsteps
@@ -551,7 +552,7 @@ def time_periodic(B, inputs, torch, stream, nsteps=10):
             "ms_per_step": ms, "interactions_per_s": pairs / (ms * 1e-3),
             "real_space_ms_per_launch": fms / n,
             "real_space_interactions_per_sm_per_clk": pairs / (fms / n * 1e-3) / (nsm * 2.032e9),
-            "vjp_call_ms": e2.elapsed_time(e3),
+            "vjp_call_ms": e2.elapsed_time(e3), "vjp_plan": vjp_kind,
             "vjp_real_space_ms": vms / max(1, vn),
             "vjp_real_space_interactions_per_sm_per_clk": pairs / (vms / max(1, vn) * 1e-3) /
             (nsm * 2.032e9),

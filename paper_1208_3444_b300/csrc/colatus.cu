@@ -136,7 +136,7 @@ constexpr int kVjpNT = 256, kVjpIPT = 4, kVjpJT = 256, kVjpMINB = 1, kVjpUnr = 4
 constexpr int kVjpSymNT = 256, kVjpSymUnr = 8;
 using VjpSymK = VjpSymKernel<kVjpSymNT>;
 // Pair-once VJP for any masses (vjp_sym.cuh): the same shape and tiles.
-constexpr int kVjpGenNT = 256, kVjpGenUnr = 4;
+constexpr int kVjpGenNT = 256, kVjpGenUnr = 8;
 using VjpGenK = VjpSymGenKernel<kVjpGenNT>;
 using VjpK = VjpKernel<kVjpNT, kVjpIPT, kVjpJT, kStages>;
 static_assert(kVjpIPT == 4, "the equal-mass VJP kernel shares the VJP's launch plan (4 i-bodies per thread)");
@@ -171,7 +171,7 @@ using Ew64K = EwaldF64Kernel<kEw64NT, kEw64JT, kStages>;
 constexpr int kEwVjpNT = 256, kEwVjpIPT = 2, kEwVjpJT = 256, kEwVjpMinB = 1;
 using EwVjpK = EwaldVjpKernel<kEwVjpNT, kEwVjpIPT, kEwVjpJT, kStages>;
 // pair-once periodic VJP: the VJP for any masses with the real-space pair term
-constexpr int kEwVjpSymUnr = 2;
+constexpr int kEwVjpSymUnr = 4;
 constexpr int kEwV64NT = 128, kEwV64JT = 32;
 using EwVjp64K = EwaldVjp64Kernel<kEwV64NT, kEwV64JT, kStages>;
 constexpr int kEwMaxNk = 63;   // shared memory of the k-space kernels in FP64; a pencil fits one block
