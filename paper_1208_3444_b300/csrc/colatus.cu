@@ -560,8 +560,9 @@ colatus_status build_plans(colatus_t ctx) {
         }
     }
     {
-        // the pair-once VJP for any masses: tables with its phase costs (33
-        // lane-ops per diagonal interaction, 40 per symmetric pair)
+        // the pair-once VJP for any masses: tables with its phase costs (36
+        // lane-ops per diagonal interaction, 40 per symmetric pair; 27 and 31
+        // in the equal-mass form)
         auto fn = vjp_sym_f32_kernel<kVjpGenNT, kVjpGenUnr, false>;
         CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, VjpGenK::SMEM));
         CU(cudaFuncSetAttribute(vjp_sym_f32_kernel<kVjpGenNT, kVjpGenUnr, true>,
@@ -573,7 +574,7 @@ colatus_status build_plans(colatus_t ctx) {
         q.n_pad = round_up(ctx->N, VjpGenK::T);
         const bool may = sym_may_fit(ctx, q.n_pad, VjpGenK::T, 1);
         const SymTables st = may ? build_sym_tables(q.n_pad, VjpGenK::T, VjpGenK::NW,
-                                                    (long long)occ * std::max(1, ctx->num_sms - 1), 33, 40)
+                                                    (long long)occ * std::max(1, ctx->num_sms - 1), 36, 40)
                                  : SymTables{};
         q.L = ForceLaunch{};
         q.L.W = st.U;
@@ -591,8 +592,8 @@ colatus_status build_plans(colatus_t ctx) {
     }
     {
         // the same kernel with the periodic real-space pair term: tables with
-        // its phase costs (68 lane-ops per diagonal interaction, 75 per
-        // symmetric pair)
+        // its phase costs (68 lane-ops per diagonal interaction, 72 per
+        // symmetric pair; 59 and 63 in the equal-mass form)
         auto fn = vjp_sym_f32_kernel<kVjpGenNT, kEwVjpSymUnr, false, EwaldVjpPair>;
         CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, VjpGenK::SMEM));
         CU(cudaFuncSetAttribute(vjp_sym_f32_kernel<kVjpGenNT, kEwVjpSymUnr, true, EwaldVjpPair>,
@@ -604,7 +605,7 @@ colatus_status build_plans(colatus_t ctx) {
         q.n_pad = round_up(ctx->N, VjpGenK::T);
         const bool may = sym_may_fit(ctx, q.n_pad, VjpGenK::T, 1);
         const SymTables st = may ? build_sym_tables(q.n_pad, VjpGenK::T, VjpGenK::NW,
-                                                    (long long)occ * std::max(1, ctx->num_sms - 1), 68, 75)
+                                                    (long long)occ * std::max(1, ctx->num_sms - 1), 68, 72)
                                  : SymTables{};
         q.L = ForceLaunch{};
         q.L.W = st.U;
