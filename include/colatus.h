@@ -251,6 +251,30 @@ colatus_status colatus_tracer_spectrum(colatus_t ctx, double dt, int window, int
  * cleared; the context stays usable), COLATUS_E_ARG for a bad limit. */
 colatus_status colatus_selftest_wait(colatus_t ctx, int64_t limit_cycles);
 
+/* Host-only self-test of the scheduling tables of the kernels that evaluate
+ * each pair once (Eq. 1 summed over unordered pairs, Newton's third law):
+ * builds the tables a context builds for n_pad bodies in tiles of T (the
+ * tile pairs it <= jt, NW phases each, split over G CTAs by the costs
+ * cost_diag : cost_sym of a diagonal and a symmetric phase), then replays
+ * every CTA's walk over them as the kernels take it.  It checks that every
+ * phase of every tile pair is taken exactly once, that every row segment and
+ * column slot is written exactly once and lies in bounds, and that each
+ * tile's column run holds exactly the slots of its tile pairs (t', t),
+ * t' < t, in order.  Needs no GPU.  T/2 a multiple of 32 NW, n_pad a
+ * multiple of T with at most 2048 tiles, G >= 1.  out (may be NULL): [0]
+ * tiles, [1] tile pairs, [2] CTAs, [3] most row segments of a tile, [4]
+ * column slots.  COLATUS_OK if all hold, COLATUS_E_STATE with the first
+ * failure in colatus_last_error(NULL), COLATUS_E_ARG for bad arguments. */
+colatus_status colatus_selftest_sym_tables(int64_t n_pad, int T, int NW, int G, int cost_diag, int cost_sym,
+                                           int64_t out[5]);
+
+/* The same for the ensemble's tables (colatus_ensemble_init, tile shape 3):
+ * R realisations of n_bodies[r] bodies (host array; 1 .. 2^26 each), stored
+ * padded to 256 and cut into 512-body tiles (at most 2048 in all).  out as
+ * above, [0] the tiles of all realisations. */
+colatus_status colatus_selftest_ens_sym_tables(int R, const int64_t *n_bodies, int G, int cost_diag,
+                                               int cost_sym, int64_t out[5]);
+
 /* Human-readable description of the last error on ctx ("" if none);
  * colatus_last_error(NULL) describes the last colatus_init failure. */
 const char *colatus_last_error(colatus_t ctx);

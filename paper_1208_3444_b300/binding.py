@@ -43,7 +43,7 @@ EXPORTS = ("colatus_init", "colatus_set_config", "colatus_set_masses", "colatus_
            "colatus_set_periodic", "colatus_periodic_params", "colatus_get_state_async",
            "colatus_wait_state", "colatus_selftest_wait", "colatus_profile_read_kinds",
            "colatus_ensemble_autotune", "colatus_ensemble_set_tuning", "colatus_force_plan",
-           "colatus_vjp_plan")
+           "colatus_vjp_plan", "colatus_selftest_sym_tables", "colatus_selftest_ens_sym_tables")
 
 
 class ColatusError(RuntimeError):
@@ -115,6 +115,8 @@ def lib():
         "colatus_periodic_params": [_vp, _vp, _vp, _vp],
         "colatus_tangent_step": [_vp, _dbl, _i64],
         "colatus_tangent_read": [_vp, _vp, _vp],
+        "colatus_selftest_sym_tables": [_i64, _int, _int, _int, _int, _int, _vp],
+        "colatus_selftest_ens_sym_tables": [_int, _vp, _int, _int, _int, _vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -402,6 +404,25 @@ def colatus_selftest_wait(h, limit_cycles):
     """Run the bounded-wait self-test; raises ColatusError (COLATUS_E_TIMEOUT)
     when the failure path works."""
     _check(lib().colatus_selftest_wait(h, int(limit_cycles)), h)
+
+
+def colatus_selftest_sym_tables(n_pad, T, NW, G, cost_diag, cost_sym):
+    """Host-only replay of the pair-once kernels' walk over their tables;
+    returns {tiles, tile_pairs, ctas, row_segments, column_slots} or raises
+    ColatusError (COLATUS_E_STATE names the first failure)."""
+    out = np.zeros(5, dtype=np.int64)
+    _check(lib().colatus_selftest_sym_tables(int(n_pad), int(T), int(NW), int(G), int(cost_diag),
+                                             int(cost_sym), out.ctypes.data), None)
+    return dict(zip(("tiles", "tile_pairs", "ctas", "row_segments", "column_slots"), map(int, out)))
+
+
+def colatus_selftest_ens_sym_tables(n_bodies, G, cost_diag, cost_sym):
+    """The same for the ensemble's tables of realisations of n_bodies[r] bodies."""
+    nb = np.ascontiguousarray(n_bodies, dtype=np.int64)
+    out = np.zeros(5, dtype=np.int64)
+    _check(lib().colatus_selftest_ens_sym_tables(len(nb), nb.ctypes.data, int(G), int(cost_diag),
+                                                 int(cost_sym), out.ctypes.data), None)
+    return dict(zip(("tiles", "tile_pairs", "ctas", "row_segments", "column_slots"), map(int, out)))
 
 
 def colatus_last_error(h=None):

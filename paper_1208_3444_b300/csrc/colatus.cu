@@ -3102,3 +3102,4 @@ colatus_status colatus_stats(colatus_t ctx, double out[4]) {
 // ---------------------------------------------------------------- ensembles
 #include "ensemble_api.cuh"
 #include "spectrum_api.cuh"
+#include "selftest_api.cuh"

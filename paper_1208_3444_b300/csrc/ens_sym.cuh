@@ -42,7 +42,7 @@ struct EnsSymKernel {
 };
 
 // Realisation of a tile pair / tile (binary search over a first-index table).
-__device__ __forceinline__ int ens_find_int(const int *off, int R, int u) {
+__host__ __device__ __forceinline__ int ens_find_int(const int *off, int R, int u) {
     int lo = 0, hi = R;   // off[lo] <= u < off[hi]
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;

@@ -100,7 +100,7 @@ struct SymKernel {
 };
 
 // Unit u -> (it, jt).
-__device__ __forceinline__ void sym_decode(long long u, int n, int &it, int &jt) {
+__host__ __device__ __forceinline__ void sym_decode(long long u, int n, int &it, int &jt) {
     const double b = 2.0 * n + 1.0;
     long long t = (long long)((b - sqrt(b * b - 8.0 * (double)u)) * 0.5);
     if (t < 0) t = 0;
