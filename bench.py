@@ -42,11 +42,11 @@ L2_FLUSH_BYTES = 256 << 20
 # captured shape and its source files hash to the captured sources; otherwise
 # traffic is null.
 FORCE_KERNEL_TRAFFIC = {
-    "bytes": 562944,
+    "bytes": 560640,
     "plan": dict(kind="force_sym_f32", threads=512, ipt=4, jt=2048, comp=True, eqm=True, nrcp=0),
     "template": "force_sym_f32_kernel<512, 4, 1, 1, 8, PlummerPair>",
     "sources": ('paper_1208_3444_b300/csrc/force_sym.cuh', 'paper_1208_3444_b300/csrc/force.cuh', 'paper_1208_3444_b300/csrc/common.cuh'),
-    "sha256": "ef43ac6365ea1f920893444d8ceed5a693d5ddaab40c22b79bd235d087f2d795",
+    "sha256": "a81010c292d8f7c882cac41e57a8e68d3db7635033e2db9b9cb0b0feda7fe70b",
 }
 
 
