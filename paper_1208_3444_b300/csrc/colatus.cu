@@ -483,7 +483,8 @@ colatus_status build_plans(colatus_t ctx) {
             p.fits = p.L.W >= p.L.G;
             continue;
         }
-        // pair-once plan: one set of tables for all four variants, the phase
+        // pair-once plan: one set of tables for all four variants (in
+        // sub-phases: one 32-pair block of every warp's slice), the phase
         // costs of the equal-mass form (11 lane-ops per diagonal interaction,
         // 14 per symmetric pair), on all SMs but the schedule kernel's; not
         // built when even its column slots alone would not fit
@@ -493,8 +494,8 @@ colatus_status build_plans(colatus_t ctx) {
             continue;
         }
         if (st.tab.empty())
-            st = build_sym_tables(p.n_pad, p.itile, kSymNT / 32, (long long)occ * std::max(1, ctx->num_sms - 1),
-                                  11, 14);
+            st = build_sym_tables(p.n_pad, p.itile, SymKernel<kSymNT, kSymIPT, false>::PH,
+                                  (long long)occ * std::max(1, ctx->num_sms - 1), 11, 14);
         p.L = ForceLaunch{};
         p.L.W = st.U;
         p.L.n_it = p.L.n_jt = st.n;
@@ -679,7 +680,7 @@ colatus_status build_plans(colatus_t ctx) {
                 continue;
             }
             if (st.tab.empty())
-                st = build_sym_tables(q.n_pad, EwSymK::T, EwSymK::NW,
+                st = build_sym_tables(q.n_pad, EwSymK::T, EwSymK::PH,
                                       (long long)occ * std::max(1, ctx->num_sms - 1), 35, 38);
             q.L = ForceLaunch{};
             q.L.W = st.U;

@@ -21,6 +21,10 @@
 // eps > 0).  Each unit is cut into NW phases (NW = warps per CTA); in phase p
 // warp w takes the j-slice (w + p) mod NW, so after NW phases every j-pair has
 // met every i-body of the tile and no two warps ever touch one slice at once.
+// A slice holds ROT blocks of 32 j-pairs, and the unit of scheduling is one
+// block of every warp's slice, a sub-phase: PH = NW ROT of them per unit, so
+// a CTA's share can end inside a phase.  The slices change hands (a barrier)
+// only after a phase's last block.
 // Inside a slice the 32 lanes rotate the j-pairs: in round r lane l takes
 // j-pair (l + r) mod 32, and the j-pair's running sum moves one lane down by
 // a warp shuffle after each round, so it stays with its j-pair.  At the end
@@ -49,7 +53,7 @@
 namespace colatus {
 
 // Layout of the int tables of a symmetric plan (ForceLaunch::sym):
-//   [0] n tiles, [1] NW phases per unit, [2] U units, [3] G CTAs,
+//   [0] n tiles, [1] PH sub-phases per unit, [2] U units, [3] G CTAs,
 //   [kSymHdr ...]  row_g0[n], row_ns[n], col_start[n + 1], unit_g0[U],
 //                  unit_ko[U], unit_nk[U], cta_pu[G + 1]
 // row_g0 / row_ns: first CTA and number of row segments of i-tile t;
@@ -57,7 +61,7 @@ namespace colatus {
 // column slots of unit u (0 for a diagonal unit); the slots are numbered
 // column by column (tile jt, then it < jt, then CTA), so the slots on the
 // bodies of tile t are the one run [col_start[t], col_start[t + 1]);
-// cta_pu: first phase-unit (u NW + phase) of CTA g.
+// cta_pu: first sub-phase (u PH + sub-phase) of CTA g.
 constexpr int kSymHdr = 8;
 
 __host__ __device__ inline long long sym_row_u0(long long it, long long n) {
@@ -66,7 +70,7 @@ __host__ __device__ inline long long sym_row_u0(long long it, long long n) {
 
 struct SymTab {
     const int *row_g0, *row_ns, *col_start, *unit_g0, *unit_ko, *unit_nk, *cta_pu;
-    int n, NW, U, G;
+    int n, NW, U, G;   // NW: the tables' phases per unit (PH of the kernel)
     __host__ __device__ explicit SymTab(const int *t) {
         n = t[0];
         NW = t[1];
@@ -90,6 +94,7 @@ struct SymKernel {
     static constexpr int TP = T / 2;          // j-pairs per tile
     static constexpr int SLICE = TP / NW;     // j-pairs per warp slice
     static constexpr int ROT = SLICE / 32;    // 32-round rotations per phase
+    static constexpr int PH = NW * ROT;       // sub-phases per unit, the tables' unit of work
     static constexpr uint32_t TILE_BYTES = T * 16;
     static constexpr int PLANES = COMP ? 2 : 1;
     // staging tile, the two halves (each 32-pair block stored twice, so that
@@ -200,7 +205,7 @@ __global__ void __launch_bounds__(NT, 1)
     force_sym_f32_kernel(const float *__restrict__ pk, float4 *__restrict__ part, int *__restrict__ flags,
                          ForceLaunch L, float eps2, float mass_eq, typename P::Args pa) {
     using K = SymKernel<NT, IPT, COMP>;
-    constexpr int NW = K::NW, T = K::T, TP = K::TP, PL = K::PLANES;
+    constexpr int NW = K::NW, T = K::T, TP = K::TP, PL = K::PLANES, PH = K::PH, ROT = K::ROT;
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *raw = reinterpret_cast<float4 *>(smem);   // staging: T float4 (pair-interleaved)
     float4 *sA = raw + T;                             // 2 TP float4: x0 x1 y0 y1, blocks doubled
@@ -216,7 +221,7 @@ __global__ void __launch_bounds__(NT, 1)
     int pu = cta_pu[g];
     const int pu_end = cta_pu[g + 1];
     if (pu >= pu_end) return;
-    long long u = pu / NW;
+    long long u = pu / PH;
     int it, jt;
     sym_decode(u, n, it, jt);
 
@@ -255,8 +260,8 @@ __global__ void __launch_bounds__(NT, 1)
     uint32_t parity = 0;
     bool bad = false;
     while (pu < pu_end) {
-        const int uend = (int)min((long long)pu_end, (u + 1) * NW);
-        const int p0 = pu - (int)(u * NW), p1 = uend - (int)(u * NW);
+        const int uend = (int)min((long long)pu_end, (u + 1) * PH);
+        const int p0 = pu - (int)(u * PH), p1 = uend - (int)(u * PH);
         const bool ok = mbar_wait_bounded(bar, parity);
         if (__syncthreads_or(!ok)) {
             bad = true;
@@ -287,13 +292,14 @@ __global__ void __launch_bounds__(NT, 1)
             inflight = true;
         }
         const bool sym = jt != it;
-        for (int p = p0; p < p1; ++p) {
+#pragma unroll 1
+        for (int ps = p0; ps < p1; ++ps) {
+            const int p = ps / ROT, s = ps - p * ROT;   // phase, block of the slice
             const int slice = (warp + p) % NW;
             float2 px[IPT], py[IPT], pz[IPT];
 #pragma unroll
             for (int k = 0; k < IPT; ++k) px[k] = py[k] = pz[k] = make_float2(0.f, 0.f);
-#pragma unroll 1
-            for (int s = 0; s < K::ROT; ++s) {
+            {
                 const int base = slice * K::SLICE + s * 32;
                 const float4 *bA = sA + 2 * base, *bB = sB + 2 * base;   // the block's doubled entries
                 float2 jx = make_float2(0.f, 0.f), jy = jx, jz = jx;
@@ -340,7 +346,9 @@ __global__ void __launch_bounds__(NT, 1)
                     hz[k] += pz[k].x + pz[k].y;
                 }
             }
-            __syncthreads();   // the slices change hands
+            // the slices change hands after a phase's last block; the range's
+            // end is a barrier too (the column slot and the next staging follow)
+            if (s == ROT - 1 || ps == p1 - 1) __syncthreads();
         }
         if (sym) {
             // this CTA's share of unit u on the j-tile's bodies: the column slot

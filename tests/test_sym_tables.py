@@ -9,10 +9,10 @@ exactly as a context or an ensemble does and replay every CTA's walk on the
 host.  They fail unless every phase is taken once, every row segment and
 column slot is written once and lies in bounds, and every tile's column run
 holds exactly the slots of its tile pairs.  The geometries below are the
-kernels': the force (2048-body tiles, 16 phases), the equal-mass VJP and the
-VJP for any masses (1024, 8), the periodic real space (1024, 16) and the
-periodic VJP (1024, 8), at the phase costs each plan uses, and the ensemble's
-512-body tiles per realisation.
+kernels': the force (2048-body tiles, 32 sub-phases: 16 warps' slices of two
+32-pair blocks each), the equal-mass VJP and the VJP for any masses (1024, 8),
+the periodic real space (1024, 16) and the periodic VJP (1024, 8), at the
+phase costs each plan uses, and the ensemble's 512-body tiles per realisation.
 """
 import numpy as np
 import pytest
@@ -22,8 +22,8 @@ from paper_1208_3444_b300 import inputs
 
 # (T, NW, cost_diag, cost_sym) of each pair-once plan
 GEOMETRIES = {
-    "force_eqm": (2048, 16, 11, 14),
-    "force": (2048, 16, 12, 16),
+    "force_eqm": (2048, 32, 11, 14),
+    "force": (2048, 32, 12, 16),
     "vjp_eqm": (1024, 8, 23, 27),
     "vjp_any_masses": (1024, 8, 36, 40),
     "ewald_force": (1024, 16, 35, 38),
@@ -53,8 +53,8 @@ def test_tables_replay(name, tiles, G):
 
 def test_tables_of_the_largest_workloads():
     # 128^3 = 2^21 bodies on 147 CTAs (the force), and 2^18 bodies with the VJP
-    r = B.colatus_selftest_sym_tables(1 << 21, 2048, 16, 147, 11, 14)
-    expect_shape(r, 1024, 147, 16)
+    r = B.colatus_selftest_sym_tables(1 << 21, 2048, 32, 147, 11, 14)
+    expect_shape(r, 1024, 147, 32)
     r = B.colatus_selftest_sym_tables(1 << 18, 1024, 8, 147, 36, 40)
     expect_shape(r, 256, 147, 8)
 
