@@ -42,11 +42,11 @@ L2_FLUSH_BYTES = 256 << 20
 # captured shape and its source files hash to the captured sources; otherwise
 # traffic is null.
 FORCE_KERNEL_TRAFFIC = {
-    "bytes": 560384,
+    "bytes": 560128,
     "plan": dict(kind="force_sym_f32", threads=512, ipt=4, jt=2048, comp=True, eqm=True, nrcp=0),
     "template": "force_sym_f32_kernel<512, 4, 1, 1, 8, PlummerPair>",
     "sources": ('paper_1208_3444_b300/csrc/force_sym.cuh', 'paper_1208_3444_b300/csrc/force.cuh', 'paper_1208_3444_b300/csrc/common.cuh'),
-    "sha256": "3e3f761b848701660c7120ebc84d5e8e8d2f5fdb0b25010df505b103b750bc37",
+    "sha256": "48db95745b2737294274299a46a4a1a42a1e03f396f9976f15ce4c687bdb924d",
 }
 
 

@@ -39,6 +39,11 @@ namespace {
 constexpr int kStages = 4;
 constexpr int kShapes = 4;
 constexpr int kSymShape = 3;
+// pair-once force: sub-phase tables below this many whole phases per CTA
+// (at 32^3, 15 phases per CTA: the slowest SM 4.7 % above the average with
+// whole phases, 1.9 % with sub-phases; at 2^21 bodies, 57000 phases per CTA,
+// the whole-phase loop is 2 % faster)
+constexpr long long kSubPhaseBelow = 64;
 constexpr int kSymNT = 512, kSymIPT = 4, kSymUnr = 8;
 // The pair-once shape is the built-in choice from this many tiles up (fewer
 // tiles leave most CTAs less than one unit) and while its partial sums take
@@ -56,7 +61,8 @@ struct F32Variant {
     const void *fn;
     void (*launch)(int grid, cudaStream_t, const float *, float4 *, int *, ForceLaunch, float,
                    float);
-    bool sym = false;   // each pair once (force_sym_f32_kernel)
+    bool sym = false;                // each pair once (force_sym_f32_kernel)
+    const void *fn_fine = nullptr;   // its instance for sub-phase tables
 };
 
 template <int NT, int IPT, int JT, int FOLD, bool COMP, bool EQM, int MINB, int UNR, int NRCP>
@@ -79,8 +85,12 @@ template <bool COMP, bool EQM>
 void launch_sym(int grid, cudaStream_t st, const float *pk, float4 *part, int *flags, ForceLaunch L,
                 float eps2, float mass_eq) {
     using K = SymKernel<kSymNT, kSymIPT, COMP>;
-    force_sym_f32_kernel<kSymNT, kSymIPT, COMP, EQM, kSymUnr><<<grid, kSymNT, K::SMEM, st>>>(
-        pk, part, flags, L, eps2, mass_eq, PlummerPair::Args{});
+    if (L.fine)
+        force_sym_f32_kernel<kSymNT, kSymIPT, COMP, EQM, kSymUnr, PlummerPair, true>
+            <<<grid, kSymNT, K::SMEM, st>>>(pk, part, flags, L, eps2, mass_eq, PlummerPair::Args{});
+    else
+        force_sym_f32_kernel<kSymNT, kSymIPT, COMP, EQM, kSymUnr, PlummerPair, false>
+            <<<grid, kSymNT, K::SMEM, st>>>(pk, part, flags, L, eps2, mass_eq, PlummerPair::Args{});
 }
 
 template <bool COMP, bool EQM>
@@ -90,6 +100,7 @@ F32Variant make_sym() {
                  (const void *)force_sym_f32_kernel<kSymNT, kSymIPT, COMP, EQM, kSymUnr>,
                  &launch_sym<COMP, EQM>};
     v.sym = true;
+    v.fn_fine = (const void *)force_sym_f32_kernel<kSymNT, kSymIPT, COMP, EQM, kSymUnr, PlummerPair, true>;
     return v;
 }
 
@@ -468,8 +479,11 @@ colatus_status build_plans(colatus_t ctx) {
     SymTables st;
     for (int v = 0; v < NUM_F32_VARIANTS; ++v) {
         const F32Variant &fv = f32_variant(v);
-        if (fv.smem > 48 * 1024)
+        if (fv.smem > 48 * 1024) {
             CU(cudaFuncSetAttribute(fv.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, fv.smem));
+            if (fv.fn_fine)
+                CU(cudaFuncSetAttribute(fv.fn_fine, cudaFuncAttributeMaxDynamicSharedMemorySize, fv.smem));
+        }
         int occ = 0;
         CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fv.fn, fv.nt, fv.smem));
         if (occ < 1) return fail(ctx, COLATUS_E_CUDA, "force variant %d cannot be resident", v);
@@ -483,25 +497,32 @@ colatus_status build_plans(colatus_t ctx) {
             p.fits = p.L.W >= p.L.G;
             continue;
         }
-        // pair-once plan: one set of tables for all four variants (in
-        // sub-phases: one 32-pair block of every warp's slice), the phase
+        // pair-once plan: one set of tables for all four variants, the phase
         // costs of the equal-mass form (11 lane-ops per diagonal interaction,
-        // 14 per symmetric pair), on all SMs but the schedule kernel's; not
-        // built when even its column slots alone would not fit
+        // 14 per symmetric pair), on all SMs but the schedule kernel's; in
+        // sub-phases (one 32-pair block of every warp's slice) where a CTA
+        // would get fewer than kSubPhaseBelow whole phases, so that shares end
+        // closer to their cost quantiles; not built when even its column slots
+        // alone would not fit
         const int pl = fv.comp ? 2 : 1;
         if (!sym_may_fit(ctx, p.n_pad, p.itile, pl)) {
             p.fits = false;
             continue;
         }
-        if (st.tab.empty())
-            st = build_sym_tables(p.n_pad, p.itile, SymKernel<kSymNT, kSymIPT, false>::PH,
-                                  (long long)occ * std::max(1, ctx->num_sms - 1), 11, 14);
+        if (st.tab.empty()) {
+            using SK = SymKernel<kSymNT, kSymIPT, false>;
+            const long long grid = (long long)occ * std::max(1, ctx->num_sms - 1);
+            const long long nt = p.n_pad / p.itile, phases = nt * (nt + 1) / 2 * SK::NW;
+            const int units = phases < kSubPhaseBelow * grid ? SK::PH : SK::NW;
+            st = build_sym_tables(p.n_pad, p.itile, units, grid, 11, 14);
+        }
         p.L = ForceLaunch{};
         p.L.W = st.U;
         p.L.n_it = p.L.n_jt = st.n;
         p.L.G = st.G;
         p.L.S_max = st.S_row;
         p.L.col_off = (long long)st.n * st.S_row * pl * p.itile;
+        p.L.fine = st.tab[1] != SymKernel<kSymNT, kSymIPT, false>::NW;   // the tables' granularity
         p.part_bytes = (size_t)((long long)st.n * st.S_row + st.slots) * pl * p.itile * sizeof(float4);
         p.fits = st.n >= 2 && p.part_bytes <= ctx->sym_max_bytes;
     }

@@ -64,6 +64,7 @@ struct ForceLaunch {
     // segment buffer
     const int *sym;
     long long col_off;
+    int fine;       // the symmetric tables are in sub-phases (force_sym.cuh)
 };
 
 // ---------------------------------------------------------------- FP32 kernel

@@ -21,10 +21,12 @@
 // eps > 0).  Each unit is cut into NW phases (NW = warps per CTA); in phase p
 // warp w takes the j-slice (w + p) mod NW, so after NW phases every j-pair has
 // met every i-body of the tile and no two warps ever touch one slice at once.
-// A slice holds ROT blocks of 32 j-pairs, and the unit of scheduling is one
-// block of every warp's slice, a sub-phase: PH = NW ROT of them per unit, so
-// a CTA's share can end inside a phase.  The slices change hands (a barrier)
-// only after a phase's last block.
+// A slice holds ROT blocks of 32 j-pairs.  The tables' unit of scheduling is
+// either a whole phase (NW per unit) or, where a CTA would get few phases,
+// one block of every warp's slice, a sub-phase (PH = NW ROT per unit), so a
+// CTA's share can end inside a phase.  The slices change hands (a barrier)
+// only after a phase's last block, and the i-side sums are folded into the
+// row's once per phase either way.
 // Inside a slice the 32 lanes rotate the j-pairs: in round r lane l takes
 // j-pair (l + r) mod 32, and the j-pair's running sum moves one lane down by
 // a warp shuffle after each round, so it stays with its j-pair.  At the end
@@ -53,7 +55,7 @@
 namespace colatus {
 
 // Layout of the int tables of a symmetric plan (ForceLaunch::sym):
-//   [0] n tiles, [1] PH sub-phases per unit, [2] U units, [3] G CTAs,
+//   [0] n tiles, [1] scheduling units per tile pair (NW or PH), [2] U units, [3] G CTAs,
 //   [kSymHdr ...]  row_g0[n], row_ns[n], col_start[n + 1], unit_g0[U],
 //                  unit_ko[U], unit_nk[U], cta_pu[G + 1]
 // row_g0 / row_ns: first CTA and number of row segments of i-tile t;
@@ -61,7 +63,7 @@ namespace colatus {
 // column slots of unit u (0 for a diagonal unit); the slots are numbered
 // column by column (tile jt, then it < jt, then CTA), so the slots on the
 // bodies of tile t are the one run [col_start[t], col_start[t + 1]);
-// cta_pu: first sub-phase (u PH + sub-phase) of CTA g.
+// cta_pu: first scheduling unit (u [1] + unit) of CTA g.
 constexpr int kSymHdr = 8;
 
 __host__ __device__ inline long long sym_row_u0(long long it, long long n) {
@@ -70,7 +72,7 @@ __host__ __device__ inline long long sym_row_u0(long long it, long long n) {
 
 struct SymTab {
     const int *row_g0, *row_ns, *col_start, *unit_g0, *unit_ko, *unit_nk, *cta_pu;
-    int n, NW, U, G;   // NW: the tables' phases per unit (PH of the kernel)
+    int n, NW, U, G;   // NW: the tables' scheduling units per tile pair
     __host__ __device__ explicit SymTab(const int *t) {
         n = t[0];
         NW = t[1];
@@ -94,7 +96,7 @@ struct SymKernel {
     static constexpr int TP = T / 2;          // j-pairs per tile
     static constexpr int SLICE = TP / NW;     // j-pairs per warp slice
     static constexpr int ROT = SLICE / 32;    // 32-round rotations per phase
-    static constexpr int PH = NW * ROT;       // sub-phases per unit, the tables' unit of work
+    static constexpr int PH = NW * ROT;       // sub-phases per unit (one 32-pair block each)
     static constexpr uint32_t TILE_BYTES = T * 16;
     static constexpr int PLANES = COMP ? 2 : 1;
     // staging tile, the two halves (each 32-pair block stored twice, so that
@@ -200,12 +202,14 @@ __device__ __forceinline__ void sym_rotation(const float4 *__restrict__ sA, cons
 // has mass mass_eq and no zero-mass padding enters; segments are scaled by
 // mass_eq.  Both the row and column sums are forces on the bodies they index
 // (the column slots are negated when written).
-template <int NT, int IPT, bool COMP, bool EQM, int UNR, class P = PlummerPair>
+// FINE: the tables are in sub-phases (NW ROT per tile pair), else in whole
+// phases (NW); the host builds them and sets ForceLaunch::fine together.
+template <int NT, int IPT, bool COMP, bool EQM, int UNR, class P = PlummerPair, bool FINE = false>
 __global__ void __launch_bounds__(NT, 1)
     force_sym_f32_kernel(const float *__restrict__ pk, float4 *__restrict__ part, int *__restrict__ flags,
                          ForceLaunch L, float eps2, float mass_eq, typename P::Args pa) {
     using K = SymKernel<NT, IPT, COMP>;
-    constexpr int NW = K::NW, T = K::T, TP = K::TP, PL = K::PLANES, PH = K::PH, ROT = K::ROT;
+    constexpr int NW = K::NW, T = K::T, TP = K::TP, PL = K::PLANES, ROT = K::ROT;
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *raw = reinterpret_cast<float4 *>(smem);   // staging: T float4 (pair-interleaved)
     float4 *sA = raw + T;                             // 2 TP float4: x0 x1 y0 y1, blocks doubled
@@ -218,6 +222,10 @@ __global__ void __launch_bounds__(NT, 1)
     const int *row_g0 = S.row_g0, *unit_g0 = S.unit_g0, *unit_ko = S.unit_ko, *cta_pu = S.cta_pu;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = blockIdx.x;
+    // scheduling units per tile pair: whole phases (NW) or sub-phases (NW ROT)
+    constexpr bool fine = FINE && ROT > 1;
+    constexpr int PH = fine ? K::PH : NW;
+    constexpr int BPU = fine ? 1 : ROT;   // 32-pair blocks per scheduling unit
     int pu = cta_pu[g];
     const int pu_end = cta_pu[g + 1];
     if (pu >= pu_end) return;
@@ -292,14 +300,22 @@ __global__ void __launch_bounds__(NT, 1)
             inflight = true;
         }
         const bool sym = jt != it;
+        // the i-side sums of a phase: folded into the row's sums once per
+        // phase (or at the end of the CTA's range), as many folds as with
+        // whole phases, so the plain FP32 row sums round no more
+        float2 px[IPT], py[IPT], pz[IPT];
 #pragma unroll 1
         for (int ps = p0; ps < p1; ++ps) {
-            const int p = ps / ROT, s = ps - p * ROT;   // phase, block of the slice
+            const int p = fine ? ps / ROT : ps;           // phase
+            const int sb = fine ? ps - p * ROT : 0;       // first block of the slice
             const int slice = (warp + p) % NW;
-            float2 px[IPT], py[IPT], pz[IPT];
+            const bool last = sb + BPU == ROT || ps == p1 - 1;
+            if (sb == 0 || ps == p0) {
 #pragma unroll
-            for (int k = 0; k < IPT; ++k) px[k] = py[k] = pz[k] = make_float2(0.f, 0.f);
-            {
+                for (int k = 0; k < IPT; ++k) px[k] = py[k] = pz[k] = make_float2(0.f, 0.f);
+            }
+#pragma unroll 1
+            for (int s = sb; s < sb + BPU; ++s) {
                 const int base = slice * K::SLICE + s * 32;
                 const float4 *bA = sA + 2 * base, *bB = sB + 2 * base;   // the block's doubled entries
                 float2 jx = make_float2(0.f, 0.f), jy = jx, jz = jx;
@@ -334,21 +350,23 @@ __global__ void __launch_bounds__(NT, 1)
                                                           jx, jy, jz);
                 }
             }
+            if (last) {
 #pragma unroll
-            for (int k = 0; k < IPT; ++k) {
-                if (COMP) {
-                    acc2_add(hx[k], lx[k], px[k].x + px[k].y);
-                    acc2_add(hy[k], ly[k], py[k].x + py[k].y);
-                    acc2_add(hz[k], lz[k], pz[k].x + pz[k].y);
-                } else {
-                    hx[k] += px[k].x + px[k].y;
-                    hy[k] += py[k].x + py[k].y;
-                    hz[k] += pz[k].x + pz[k].y;
+                for (int k = 0; k < IPT; ++k) {
+                    if (COMP) {
+                        acc2_add(hx[k], lx[k], px[k].x + px[k].y);
+                        acc2_add(hy[k], ly[k], py[k].x + py[k].y);
+                        acc2_add(hz[k], lz[k], pz[k].x + pz[k].y);
+                    } else {
+                        hx[k] += px[k].x + px[k].y;
+                        hy[k] += py[k].x + py[k].y;
+                        hz[k] += pz[k].x + pz[k].y;
+                    }
                 }
+                // the slices change hands after a phase's last block; the range's
+                // end is a barrier too (the column slot and the next staging follow)
+                __syncthreads();
             }
-            // the slices change hands after a phase's last block; the range's
-            // end is a barrier too (the column slot and the next staging follow)
-            if (s == ROT - 1 || ps == p1 - 1) __syncthreads();
         }
         if (sym) {
             // this CTA's share of unit u on the j-tile's bodies: the column slot
