@@ -10,6 +10,12 @@
  * out: N x 3 floats (acceleration at the initial state), N x 3 floats (x),
  *      N x 3 floats (v), double t, double a, COLATUS_NDIAG doubles
  *
+ *     c_client selftest
+ *
+ * runs the host-only self-tests of the pair-once scheduling tables (no GPU):
+ * the 32^3 force plan (2048-body tiles, 32 sub-phases, 147 CTAs) and the
+ * ensemble plan of four realisations, and prints each one's five figures.
+ *
  * Exit status: 0 on success, 1 on a file error, 2 + the colatus_status of
  * the first failing call otherwise (its message goes to stderr). */
 #include <stdio.h>
@@ -37,8 +43,21 @@ int main(int argc, char **argv) {
     colatus_status st;
     int ok;
 
+    if (argc == 2 && argv[1][0] == 's') {
+        int64_t r[5];
+        const int64_t sizes[4] = {1028, 4096, 4097, 32675};
+        st = colatus_selftest_sym_tables(32768, 2048, 32, 147, 11, 14, r);
+        if (st != COLATUS_OK) return fail(NULL, "colatus_selftest_sym_tables", st);
+        printf("sym %lld %lld %lld %lld %lld\n", (long long)r[0], (long long)r[1], (long long)r[2],
+               (long long)r[3], (long long)r[4]);
+        st = colatus_selftest_ens_sym_tables(4, sizes, 592, 11, 14, r);
+        if (st != COLATUS_OK) return fail(NULL, "colatus_selftest_ens_sym_tables", st);
+        printf("ens %lld %lld %lld %lld %lld\n", (long long)r[0], (long long)r[1], (long long)r[2],
+               (long long)r[3], (long long)r[4]);
+        return 0;
+    }
     if (argc != 3) {
-        fprintf(stderr, "usage: %s <in> <out>\n", argv[0]);
+        fprintf(stderr, "usage: %s <in> <out> | %s selftest\n", argv[0], argv[0]);
         return 1;
     }
     in = fopen(argv[1], "rb");

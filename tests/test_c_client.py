@@ -3,7 +3,9 @@ include/colatus.h and linked with libcolatus.so, no Python or C++ in between.
 
 * CPU: the header compiles as C99 with every warning an error, the program
   links, and without a GPU it fails cleanly with COLATUS_E_CUDA from
-  colatus_init (exit status 2 + 2) and the library's message.
+  colatus_init (exit status 2 + 2) and the library's message.  The host-only
+  self-tests of the pair-once tables run through the C ABI and return the
+  same figures as through the Python binding.
 * GPU: the Eq. 1 acceleration, 3 KDK steps with FP32 compensated forces, (t,
   a) and the diagnostics, read back through the C program's output file,
   against the FP64 oracle (force rel-RMS 1e-6, positions 1e-5 max abs,
@@ -69,6 +71,20 @@ def test_c_client_compiles_as_c99_and_fails_cleanly_without_gpu(tmp_path):
                        capture_output=True, text=True, timeout=120)
     assert r.returncode == 2 + 2, (r.returncode, r.stderr)     # COLATUS_E_CUDA from colatus_init
     assert "colatus_init" in r.stderr and "status 2" in r.stderr
+
+
+def test_c_client_runs_the_table_self_tests(tmp_path):
+    from paper_1208_3444_b300 import binding as B
+    exe = compile_client(tmp_path)
+    r = subprocess.run([exe, "selftest"], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    lines = dict((ln.split()[0], [int(t) for t in ln.split()[1:]]) for ln in r.stdout.splitlines())
+    keys = ("tiles", "tile_pairs", "ctas", "row_segments", "column_slots")
+    want = B.colatus_selftest_sym_tables(32768, 2048, 32, 147, 11, 14)
+    assert lines["sym"] == [want[k] for k in keys]
+    want = B.colatus_selftest_ens_sym_tables([1028, 4096, 4097, 32675], 592, 11, 14)
+    assert lines["ens"] == [want[k] for k in keys]
+    assert lines["sym"][:2] == [16, 136]
 
 
 @pytest.mark.gpu
