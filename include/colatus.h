@@ -95,8 +95,11 @@ colatus_status colatus_init(colatus_t *out, int64_t N, const double *masses, dou
                             double H0, double a_start);
 
 /* Precision, integrator, gravitational constant and stream (a cudaStream_t;
- * NULL keeps the library-owned stream).  Changing precision keeps the state
- * (converted).  Errors: COLATUS_E_ARG. */
+ * NULL keeps the library-owned stream).  The integrators: the paper's DKD
+ * leapfrog (Eqs. 3-5), KDK with the same drag coefficients, and the
+ * symplectic KDK of the canonical variables (Sec. II); G is the constant of
+ * Eq. 1.  Changing precision keeps the state (converted).  Errors:
+ * COLATUS_E_ARG. */
 colatus_status colatus_set_config(colatus_t ctx, colatus_prec prec, colatus_scheme scheme,
                                   double G, void *cuda_stream);
 
@@ -175,8 +178,9 @@ colatus_status colatus_wait_state(colatus_t ctx);
  * synchronises.  Errors: COLATUS_E_STATE (no state set), COLATUS_E_TIMEOUT. */
 colatus_status colatus_forces(colatus_t ctx, void *acc_out, int dtype, int on_device);
 
-/* Advance nsteps steps of size dt (> 0) with the configured scheme.  The
- * scale factor is advanced on the GPU in FP64 (RK4, 8 sub-steps per half
+/* Advance nsteps steps of size dt (> 0) with the configured scheme (Eqs.
+ * 3-5: drift, the Eq. 1 force, the kick with Hubble drag).  The scale factor
+ * of Eq. 2 is advanced on the GPU in FP64 (RK4, 8 sub-steps per half
  * step).  Asynchronous: device error flags are reported by the next
  * colatus_synchronize / colatus_get_state.  Errors: COLATUS_E_ARG,
  * COLATUS_E_STATE. */
@@ -226,7 +230,7 @@ colatus_status colatus_diagnostics(colatus_t ctx, double out[COLATUS_NDIAG]);
  * by a direct DFT with exactly reduced angles.  Output E is [ntr][T/2 + 1]
  * doubles, row-major.  Needs 2 <= T <= 2^24. */
 
-/* Spectrum of a velocity series v laid out [T][ntr][stride] (dtype
+/* Energy spectrum (Sec. I, Sec. IV) of a velocity series v laid out [T][ntr][stride] (dtype
  * elements; the three velocity components are the first three of each
  * stride).  on_device / out_on_device say where v and E_out live.  Runs on
  * cuda_stream (NULL: the legacy default stream) and synchronises it unless both
@@ -236,7 +240,7 @@ colatus_status colatus_velocity_spectrum(const void *v, int dtype, int on_device
                                          int detrend, double *E_out, int out_on_device,
                                          void *cuda_stream);
 
-/* Spectrum of the velocities recorded by colatus_record_tracers (the kept
+/* Energy spectrum (Sec. I, Sec. IV) of the velocities recorded by colatus_record_tracers (the kept
  * records, oldest first, read in place on the device); dt is the step size
  * the records were taken with.  *nrec_out = T used; E_out (host) may be NULL
  * to query it.  COLATUS_E_STATE if nothing is recorded.  Synchronises. */
@@ -366,7 +370,8 @@ colatus_status colatus_set_tuning(colatus_t ctx, int shape);
 colatus_status colatus_force_vjp(colatus_t ctx, const void *w, void *gx, void *gm, int dtype,
                                  int on_device);
 
-/* Forward pass of the discrete adjoint, for any of the three schemes:
+/* Forward pass of the discrete adjoint (the transpose of the steps of
+ * Eqs. 3-5 with the Eq. 1 force), for any of the three schemes:
  * advances the state by nsteps steps of size dt exactly as colatus_step
  * does, keeping a checkpoint of (x, v) every checkpoint_every steps (device
  * memory: nsteps / checkpoint_every checkpoints of N bodies, plus
@@ -439,10 +444,12 @@ colatus_status colatus_ensemble_set_state(colatus_ens_t e, const void *x, const 
                                           int on_device);
 colatus_status colatus_ensemble_get_state(colatus_ens_t e, void *x, void *v, int dtype,
                                           int on_device, double *t, double *a);
-/* Comoving accelerations G a^-3 F of every body (N_tot x 3). */
+/* Comoving accelerations G a^-3 F of every body (Eq. 1 within each
+ * realisation; N_tot x 3). */
 colatus_status colatus_ensemble_forces(colatus_ens_t e, void *acc_out, int dtype, int on_device);
-/* nsteps steps of size dt > 0 for every realisation (asynchronous), of the
- * scheme set by colatus_ensemble_set_scheme (KDK by default). */
+/* nsteps steps of size dt > 0 (Eqs. 3-5, the scale factor of Eq. 2) for
+ * every realisation (asynchronous), of the scheme set by
+ * colatus_ensemble_set_scheme (KDK by default). */
 colatus_status colatus_ensemble_step(colatus_ens_t e, double dt, int64_t nsteps);
 /* Integration scheme of the ensemble's steps, as colatus_set_config's for
  * one system: COLATUS_DKD (Eqs. 3-5, the force at the half-drift
@@ -503,7 +510,8 @@ void colatus_ensemble_destroy(colatus_ens_t e);
  * Initialising replaces any previous tangents. */
 colatus_status colatus_tangent_init(colatus_t ctx, const int64_t *seeds, int B, const double *dir,
                                     int64_t capacity_steps);
-/* Advance the state and its tangents by nsteps steps of size dt of the
+/* Advance the state and its tangents (the derivative of Eqs. 3-5 and of the
+ * Eq. 1 force, Sec. I's tracer trajectories) by nsteps steps of size dt of the
  * configured scheme (FP32 precision only; the step size and the scheme may
  * change between calls).  COLATUS_E_STATE if the state was stepped without
  * them. */
